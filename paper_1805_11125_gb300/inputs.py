@@ -1,0 +1,344 @@
+"""Seeded synthetic inputs for the Borexino-style binned likelihood (arXiv:1805.11125).
+
+This module builds only the *inputs* of the likelihood: the true-energy species shapes
+on the energy grid, the stopping-power table used by the Birks map, the random-trigger
+(pile-up) spectrum, the pulse-shape templates, the histogram axes, the true parameter
+vector and seeded parameter points.  It holds none of the likelihood's arithmetic: no
+quenching, no detector response, no pile-up convolution, no likelihood.  Poisson data
+are drawn by :func:`poisson_counts` from expected counts that the *caller* computes
+with its own model evaluator (the CPU oracle in tests, the CUDA path in the benchmark).
+
+The paper fixes no shapes, bin counts or species lists (Sec. 3 gives only Eq. 1-4);
+the recipe below is the synthetic stand-in for the Borexino Phase-II spectra:
+
+* grid: ``n_grid`` true-energy points ``E_i = (i + 1/2) * e_max / n_grid`` (0-3 MeV);
+* species shapes (sampled at ``E_i`` and normalised to unit sum):
+  - nu-e elastic-scattering recoil spectra of mono-energetic lines (Compton-edge-like),
+  - allowed beta- spectra ``p W (Q - T)^2`` with seeded endpoints ``Q ~ U(0.5, 3)`` MeV,
+  - one 11C-like beta+ spectrum (``Q = 0.96`` MeV shifted by the 1.022 MeV
+    annihilation energy),
+  - one alpha peak, a Gaussian at 0.4 MeV (sigma 0.02 MeV), already electron-equivalent,
+  - external-gamma tails ``exp(-E / slope)``;
+* stopping power ``S(E) = 1.9 (1 + (0.1 MeV / E)^0.95)`` MeV/cm on the grid;
+* pile-up spectrum of ``L = 400`` bins, ``g[d] ~ exp(-d w / 30) + 0.1 exp(-(d w - 100)^2 / 800)``
+  (``d w`` in photoelectrons), normalised to unit sum;
+* pulse-shape templates: bin-integrated Gaussians N(0.35, 0.08) for beta-like and
+  N(0.55, 0.08) for the beta+ species, renormalised to [0, 1);
+* rates: log-uniform fractions ``10^U(-2, 0)`` scaled to the stated total number of events.
+
+Parameter vector layout (``P = K + 7``):
+``[r_0 .. r_{K-1}, LY, a, b, c, kB, eps, s_r]``.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Dict, List, Optional
+
+import numpy as np
+from scipy.special import ndtr
+
+MASTER_SEED = 1805
+M_E = 0.51099895  # electron mass, MeV
+
+PARAM_TAIL = ("LY", "a", "b", "c", "kB", "eps", "s_r")
+N_TAIL = len(PARAM_TAIL)
+
+# true values of the response / pile-up / radial parameters
+TRUE_TAIL = dict(LY=500.0, a=1.1, b=2e-4, c=4.0, kB=0.011, eps=0.05, s_r=1.0)
+
+RAD_INTERNAL = 0
+RAD_EXTERNAL = 1
+
+
+@dataclasses.dataclass
+class ModelSpec:
+    """One dataset and its model inputs (host arrays, float64)."""
+
+    name: str
+    n_grid: int
+    e_max: float
+    shapes: np.ndarray              # [K, n_grid], each row sums to 1
+    stop_pow: np.ndarray            # [n_grid] MeV/cm
+    pileup: np.ndarray              # [L], sums to 1
+    width: float                    # npe per bin
+    m_lo: int                       # energy window [m_lo, m_hi) on the full axis [0, m_hi)
+    m_hi: int
+    tag_frac: Optional[np.ndarray] = None   # [K]; None -> single (untagged) spectrum
+    rad_class: Optional[np.ndarray] = None  # [K] int32 (0 internal, 1 external); None -> no radial term
+    n_rad: int = 0
+    r_fid: float = 3.0
+    r_iv: float = 4.25
+    att_len: float = 0.3
+    psd_prob: Optional[np.ndarray] = None   # [K, n_psd]; None -> no PSD term
+    theta_true: Optional[np.ndarray] = None
+    species: List[str] = dataclasses.field(default_factory=list)
+    counts: Dict[str, np.ndarray] = dataclasses.field(default_factory=dict)
+
+    @property
+    def K(self) -> int:
+        return int(self.shapes.shape[0])
+
+    @property
+    def P(self) -> int:
+        return self.K + N_TAIL
+
+    @property
+    def L(self) -> int:
+        return int(self.pileup.shape[0])
+
+    @property
+    def n_window(self) -> int:
+        return self.m_hi - self.m_lo
+
+    @property
+    def n_psd(self) -> int:
+        return 0 if self.psd_prob is None else int(self.psd_prob.shape[1])
+
+    def hist_sizes(self) -> Dict[str, int]:
+        """Histogram names and bin counts, in the order every evaluator concatenates them."""
+        out = {"sub": self.n_window}
+        if self.tag_frac is not None:
+            out["tag"] = self.n_window
+        if self.rad_class is not None and self.n_rad > 0:
+            out["rad"] = self.n_rad
+        if self.psd_prob is not None:
+            out["psd"] = self.n_psd
+        return out
+
+    @property
+    def n_bins_total(self) -> int:
+        return sum(self.hist_sizes().values())
+
+    def param_names(self) -> List[str]:
+        return [f"r_{s}" for s in self.species] + list(PARAM_TAIL)
+
+    def default_free(self) -> np.ndarray:
+        free = np.ones(self.P, dtype=np.uint8)
+        if self.rad_class is None or self.n_rad == 0:
+            free[self.K + PARAM_TAIL.index("s_r")] = 0
+        return free
+
+    def default_bounds(self):
+        lo = np.full(self.P, -np.inf)
+        hi = np.full(self.P, np.inf)
+        lo[: self.K] = 0.0                         # rates
+        t = {n: self.K + i for i, n in enumerate(PARAM_TAIL)}
+        lo[t["LY"]] = 50.0
+        lo[t["a"]] = 0.0
+        lo[t["b"]] = 0.0
+        lo[t["c"]] = 1e-3
+        lo[t["kB"]] = 0.0
+        lo[t["eps"]], hi[t["eps"]] = 0.0, 1.0
+        lo[t["s_r"]] = 0.05
+        return lo, hi
+
+    def counts_vector(self) -> np.ndarray:
+        return np.concatenate([self.counts[h] for h in self.hist_sizes()])
+
+    def with_counts(self, flat: np.ndarray) -> "ModelSpec":
+        """Copy of this spec with the flat data vector split back into histograms."""
+        new = dataclasses.replace(self, counts={})
+        o = 0
+        for h, n in self.hist_sizes().items():
+            new.counts[h] = np.ascontiguousarray(flat[o:o + n], dtype=np.float64)
+            o += n
+        assert o == flat.shape[0]
+        return new
+
+
+# ----------------------------------------------------------------------------------------
+# shapes (input construction only)
+# ----------------------------------------------------------------------------------------
+
+def grid_energies(n_grid: int, e_max: float) -> np.ndarray:
+    return (np.arange(n_grid) + 0.5) * (e_max / n_grid)
+
+
+def nu_recoil(E: np.ndarray, e_nu: float) -> np.ndarray:
+    """nu-e elastic-scattering recoil spectrum of a mono-energetic line (Compton-edge-like)."""
+    gL, gR = 0.73, 0.23
+    t_max = 2 * e_nu ** 2 / (M_E + 2 * e_nu)
+    f = gL ** 2 + gR ** 2 * (1 - E / e_nu) ** 2 - gL * gR * M_E * E / e_nu ** 2
+    return np.where(E <= t_max, np.maximum(f, 0.0), 0.0)
+
+
+def beta_allowed(E: np.ndarray, q: float) -> np.ndarray:
+    W = E + M_E
+    p = np.sqrt(np.maximum(W * W - M_E * M_E, 0.0))
+    return np.where(E < q, p * W * (q - E) ** 2, 0.0)
+
+
+def beta_plus_11c(E: np.ndarray) -> np.ndarray:
+    return beta_allowed(E - 2 * M_E, 0.96) * (E > 2 * M_E)
+
+
+def alpha_peak(E: np.ndarray, mu=0.4, sig=0.02) -> np.ndarray:
+    return np.exp(-0.5 * ((E - mu) / sig) ** 2)
+
+
+def external_tail(E: np.ndarray, slope: float) -> np.ndarray:
+    return np.exp(-E / slope)
+
+
+def stopping_power(E: np.ndarray) -> np.ndarray:
+    return 1.9 * (1.0 + (0.1 / E) ** 0.95)
+
+
+def pileup_spectrum(L: int, width: float) -> np.ndarray:
+    x = np.arange(L) * width
+    g = np.exp(-x / 30.0) + 0.1 * np.exp(-((x - 100.0) ** 2) / (2 * 20.0 ** 2))
+    return g / g.sum()
+
+
+def psd_template(n_psd: int, mean: float, sig: float = 0.08) -> np.ndarray:
+    edges = np.linspace(0.0, 1.0, n_psd + 1)
+    c = ndtr((edges - mean) / sig)
+    p = np.diff(c)
+    return p / p.sum()
+
+
+def _normalise(rows: np.ndarray) -> np.ndarray:
+    return rows / rows.sum(axis=1, keepdims=True)
+
+
+def species_library(n_grid: int = 2000, e_max: float = 3.0, seed: int = 0):
+    """The 15-shape library; its first 8 shapes are the 8-species single-spectrum set.
+
+    Returns (names, shapes[15, n_grid], is_external[15], is_beta_plus[15]).
+    """
+    rng = np.random.default_rng([MASTER_SEED, 101, seed])
+    E = grid_energies(n_grid, e_max)
+    q = rng.uniform(0.5, 3.0, size=6)
+    e_extra_line = rng.uniform(0.3, 1.5)
+    rows, names = [], []
+    for e_nu in (0.384, 0.862, 1.44):
+        rows.append(nu_recoil(E, e_nu)); names.append(f"nu{e_nu:g}")
+    for j in range(3):
+        rows.append(beta_allowed(E, q[j])); names.append(f"beta{j}")
+    rows.append(alpha_peak(E)); names.append("alpha")
+    rows.append(external_tail(E, 0.5)); names.append("ext0")
+    # the second half of the library
+    rows.append(beta_plus_11c(E)); names.append("c11")
+    for j in range(3, 6):
+        rows.append(beta_allowed(E, q[j])); names.append(f"beta{j}")
+    rows.append(nu_recoil(E, e_extra_line)); names.append("nu_x")
+    rows.append(external_tail(E, 0.35)); names.append("ext1")
+    rows.append(external_tail(E, 0.8)); names.append("ext2")
+    shapes = _normalise(np.array(rows))
+    is_ext = np.array([n.startswith("ext") for n in names])
+    is_bp = np.array([n == "c11" for n in names])
+    return names, shapes, is_ext, is_bp
+
+
+def _rates(rng, K: int, total: float) -> np.ndarray:
+    f = 10.0 ** rng.uniform(-2.0, 0.0, size=K)
+    return total * f / f.sum()
+
+
+def _theta(rates: np.ndarray) -> np.ndarray:
+    return np.concatenate([rates, [TRUE_TAIL[n] for n in PARAM_TAIL]])
+
+
+# ----------------------------------------------------------------------------------------
+# configurations
+# ----------------------------------------------------------------------------------------
+
+def single_spectrum(n_grid=2000, e_max=3.0, width=2.0, lo_npe=150.0, hi_npe=950.0,
+                    n_species=8, total=1e6, L=400, seed=0, name="single") -> ModelSpec:
+    """K species, one energy spectrum (no TFC split, no radial or pulse-shape term)."""
+    names, shapes, _, _ = species_library(n_grid, e_max, seed)
+    rng = np.random.default_rng([MASTER_SEED, 1, seed])
+    E = grid_energies(n_grid, e_max)
+    m_lo, m_hi = int(round(lo_npe / width)), int(round(hi_npe / width))
+    spec = ModelSpec(name=name, n_grid=n_grid, e_max=e_max,
+                     shapes=np.ascontiguousarray(shapes[:n_species]),
+                     stop_pow=stopping_power(E), pileup=pileup_spectrum(L, width),
+                     width=width, m_lo=m_lo, m_hi=m_hi, species=names[:n_species])
+    spec.theta_true = _theta(_rates(rng, n_species, total))
+    return spec
+
+
+def multivariate(n_grid=2000, e_max=3.0, width=1.0, lo_npe=100.0, hi_npe=1000.0,
+                 n_species=15, total=2e6, L=400, n_rad=60, n_psd=50, tag_eff=0.9,
+                 seed=0, name="multivariate") -> ModelSpec:
+    """TFC-subtracted + TFC-tagged spectra, a radial and a pulse-shape histogram (Eq. 3, Eq. 4)."""
+    names, shapes, is_ext, is_bp = species_library(n_grid, e_max, seed)
+    rng = np.random.default_rng([MASTER_SEED, 2, seed])
+    E = grid_energies(n_grid, e_max)
+    K = n_species
+    m_lo, m_hi = int(round(lo_npe / width)), int(round(hi_npe / width))
+    tag = np.where(is_bp[:K], tag_eff, 0.1)
+    psd = np.stack([psd_template(n_psd, 0.55 if bp else 0.35) for bp in is_bp[:K]])
+    spec = ModelSpec(name=name, n_grid=n_grid, e_max=e_max,
+                     shapes=np.ascontiguousarray(shapes[:K]), stop_pow=stopping_power(E),
+                     pileup=pileup_spectrum(L, width), width=width, m_lo=m_lo, m_hi=m_hi,
+                     tag_frac=tag.astype(np.float64),
+                     rad_class=np.where(is_ext[:K], RAD_EXTERNAL, RAD_INTERNAL).astype(np.int32),
+                     n_rad=n_rad, psd_prob=np.ascontiguousarray(psd), species=names[:K])
+    spec.theta_true = _theta(_rates(rng, K, total))
+    return spec
+
+
+def config(name: str) -> ModelSpec:
+    """The named workloads.
+
+    * ``plain``        K=8 single spectrum, 400 bins of 2 npe over 150-950 npe, 1e6 events.
+    * ``multivariate`` K=15, TFC-subtracted/tagged 900 bins of 1 npe over 100-1000 npe,
+                       60 radial bins, 50 pulse-shape bins, 22 parameters, 2e6 events.
+    * ``small_plain`` / ``small_mv`` reduced grids that the oracle evaluates in well under a
+      second but that still span several 128-row tiles and ragged tails.
+    """
+    if name == "plain":
+        return single_spectrum(name=name)
+    if name == "multivariate":
+        return multivariate(name=name)
+    if name == "small_plain":
+        return single_spectrum(n_grid=600, width=4.0, lo_npe=160.0, hi_npe=1100.0,
+                               n_species=5, total=2e5, L=100, name=name)
+    if name == "small_mv":
+        return multivariate(n_grid=520, width=3.0, lo_npe=120.0, hi_npe=900.0, n_species=9,
+                            total=3e5, L=90, n_rad=20, n_psd=16, name=name)
+    raise KeyError(name)
+
+
+def toy_batch(n_toys=4096, n_grid=2000, e_max=3.0, width=2.0, lo_npe=150.0, L=400,
+              bins=(400, 1200), species=(6, 15), events=(1e4, 1e7), seed=0) -> List[ModelSpec]:
+    """Pseudo-experiments of uneven size: bin count U{400..1200}, a random subset of 6-15
+    shapes of the 15-shape library, and log-uniform event counts 1e4-1e7 (single spectrum,
+    2 npe bins starting at 150 npe)."""
+    names, shapes, _, _ = species_library(n_grid, e_max, seed)
+    rng = np.random.default_rng([MASTER_SEED, 4, seed])
+    E = grid_energies(n_grid, e_max)
+    S = stopping_power(E)
+    g = pileup_spectrum(L, width)
+    m_lo = int(round(lo_npe / width))
+    out = []
+    for t in range(n_toys):
+        nb = int(rng.integers(bins[0], bins[1] + 1))
+        K = int(rng.integers(species[0], species[1] + 1))
+        sub = np.sort(rng.choice(len(names), size=K, replace=False))
+        total = 10.0 ** rng.uniform(np.log10(events[0]), np.log10(events[1]))
+        spec = ModelSpec(name=f"toy{t}", n_grid=n_grid, e_max=e_max,
+                         shapes=np.ascontiguousarray(shapes[sub]), stop_pow=S, pileup=g,
+                         width=width, m_lo=m_lo, m_hi=m_lo + nb,
+                         species=[names[j] for j in sub])
+        spec.theta_true = _theta(_rates(rng, K, total))
+        out.append(spec)
+    return out
+
+
+def parameter_points(theta: np.ndarray, n: int, rel: float = 0.02, seed: int = 0,
+                     free: Optional[np.ndarray] = None) -> np.ndarray:
+    """``n`` seeded points ``theta * (1 + rel * z)``, z ~ N(0, 1) per component (fixed
+    components untouched)."""
+    rng = np.random.default_rng([MASTER_SEED, 7, seed])
+    z = rng.standard_normal((n, theta.shape[0]))
+    if free is not None:
+        z[:, free == 0] = 0.0
+    return theta[None, :] * (1.0 + rel * z)
+
+
+def poisson_counts(mu: np.ndarray, seed: int = 0) -> np.ndarray:
+    """Poisson draws of expected counts ``mu`` (computed by the caller's model)."""
+    rng = np.random.default_rng([MASTER_SEED, 9, seed])
+    return rng.poisson(np.maximum(mu, 0.0)).astype(np.float64)

@@ -1,0 +1,331 @@
+"""Pins of the FP64 CPU oracle to facts fixed by the paper's definitions and by mathematics.
+
+Each test checks the oracle against something other than itself: a closed form,
+an independent quadrature, an invariant, brute force on tiny inputs, or central
+finite differences.  Passages: Eq. 1 (response convolution), Eq. 2 (pile-up), Eq. 3
+(TFC joint likelihood), Eq. 4 (multivariate likelihood) of arXiv:1805.11125 Sec. 3.
+"""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate, signal, special
+
+from oracle import oracle as O
+from paper_1805_11125_gb300 import inputs as I
+
+K_LY, K_A, K_B, K_C, K_KB, K_EPS, K_SR = range(7)
+
+
+def tail(spec, name):
+    return spec.K + I.PARAM_TAIL.index(name)
+
+
+def with_theta(spec, **kw):
+    th = spec.theta_true.copy()
+    for k, v in kw.items():
+        th[tail(spec, k)] = v
+    return th
+
+
+def gauss_bin_quad(lo, hi, mu, sig):
+    f = lambda x: math.exp(-0.5 * ((x - mu) / sig) ** 2) / (sig * math.sqrt(2 * math.pi))
+    pts = [p for p in (mu - sig, mu, mu + sig) if lo < p < hi]
+    val, _ = integrate.quad(f, lo, hi, points=pts or None, epsabs=0, epsrel=1e-13, limit=200)
+    return val
+
+
+# ---------------------------------------------------------------------------------- a1
+
+def test_a1_kb_zero_is_linear_light_yield():
+    """kB = 0: the Birks integral is the deposited energy itself, Q_i = E_i = (i + 1/2) dE."""
+    s = I.config("small_plain")
+    th = with_theta(s, kB=0.0)
+    Q, mu, sig, den = O.quench(s, th)
+    E = (np.arange(s.n_grid) + 0.5) * s.e_max / s.n_grid
+    np.testing.assert_allclose(Q, E, rtol=1e-13)
+    np.testing.assert_allclose(mu, 500.0 * E, rtol=1e-13)
+    a, b, c = 1.1, 2e-4, 4.0
+    np.testing.assert_allclose(sig ** 2, a * mu + b * mu ** 2 + c, rtol=1e-13)
+    np.testing.assert_allclose(den, special.ndtr(mu / sig), rtol=1e-13)
+
+
+def test_a1_constant_stopping_power_closed_form():
+    """Constant S: Q(E) = E / (1 + kB S) exactly."""
+    s = dataclasses.replace(I.config("small_plain"), stop_pow=np.full(600, 2.7))
+    kB = 0.011
+    Q, mu, _, _ = O.quench(s, with_theta(s, kB=kB))
+    E = (np.arange(s.n_grid) + 0.5) * s.e_max / s.n_grid
+    np.testing.assert_allclose(Q, E / (1 + kB * 2.7), rtol=1e-13)
+
+
+def test_a1_quenching_is_monotone_and_below_energy():
+    s = I.config("plain")
+    Q, _, _, _ = O.quench(s, s.theta_true)
+    E = (np.arange(s.n_grid) + 0.5) * s.e_max / s.n_grid
+    assert np.all(np.diff(Q) > 0) and np.all(Q < E)
+
+
+# ------------------------------------------------------------------------------- a2/a3
+
+def test_delta_spectrum_returns_response_column():
+    """A delta-function spectrum s = e_i0 returns column i0 of the response, which is
+    recomputed here by adaptive quadrature of the Gaussian density (no erfc)."""
+    s0 = I.config("small_plain")
+    for i0 in (37, 300, 555):
+        shapes = np.zeros((1, s0.n_grid)); shapes[0, i0] = 1.0
+        s = dataclasses.replace(s0, shapes=shapes, species=["delta"])
+        s.theta_true = np.concatenate([[1.0], s0.theta_true[s0.K:]])
+        th = with_theta(s, kB=0.0)
+        _, v = O.response(s, th, want_R=False)
+        E = (i0 + 0.5) * s.e_max / s.n_grid
+        mu = 500.0 * E
+        sig = math.sqrt(1.1 * mu + 2e-4 * mu * mu + 4.0)
+        norm = gauss_bin_quad(0.0, mu + 60 * sig, mu, sig)
+        col = np.array([gauss_bin_quad(m * s.width, (m + 1) * s.width, mu, sig) / norm
+                        for m in range(s.m_hi)])
+        big = col > 1e-12
+        np.testing.assert_allclose(v[big, 0], col[big], rtol=1e-9)
+        assert np.all(np.abs(v[~big, 0] - col[~big]) < 1e-14)
+
+
+def test_gaussian_convolved_with_gaussian_closed_form():
+    """kB = 0, a = b = 0, c = sr^2 and a Gaussian shape in E: the visible spectrum is the
+    bin-integrated Gaussian of variance (LY sigma_E)^2 + sr^2 (Eq. 1 closed form)."""
+    s0 = I.single_spectrum(n_grid=2000, width=4.0, lo_npe=200, hi_npe=800, n_species=1, L=10)
+    E = (np.arange(2000) + 0.5) * 3.0 / 2000
+    E0, sE, sr = 1.0, 0.05, 3.0
+    shape = np.exp(-0.5 * ((E - E0) / sE) ** 2)
+    s = dataclasses.replace(s0, shapes=(shape / shape.sum())[None, :])
+    th = s0.theta_true.copy()
+    th[tail(s, "kB")] = 0.0
+    th[tail(s, "a")] = 0.0
+    th[tail(s, "b")] = 0.0
+    th[tail(s, "c")] = sr * sr
+    _, v = O.response(s, th, want_R=False)
+    sig = math.sqrt((500 * sE) ** 2 + sr ** 2)
+    edges = np.arange(s.m_hi + 1) * s.width
+    z = (edges - 500 * E0) / sig
+    # upper-tail differences above the mean keep full relative precision
+    want = np.where(z[:-1] >= 0, special.ndtr(-z[:-1]) - special.ndtr(-z[1:]),
+                    special.ndtr(z[1:]) - special.ndtr(z[:-1]))
+    big = want > 1e-10 * want.max()
+    np.testing.assert_allclose(v[big, 0], want[big], rtol=1e-10)
+
+
+def test_count_conservation_away_from_edges():
+    """Each response column integrates to 1 over [0, inf); a spectrum far below the top of
+    the axis keeps all its events."""
+    s = I.config("small_plain")
+    s = dataclasses.replace(s, m_hi=400, m_lo=40)  # axis up to 1600 npe
+    _, v = O.response(s, s.theta_true, want_R=False)
+    np.testing.assert_allclose(v.sum(axis=0), 1.0, rtol=0, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------------- a5
+
+def _pile_spec(L=7, m_lo=0, m_hi=40, g=None):
+    s = I.config("small_plain")
+    g = np.full(L, 1.0 / L) if g is None else g
+    return dataclasses.replace(s, pileup=np.asarray(g, float), m_lo=m_lo, m_hi=m_hi)
+
+
+def test_pileup_eps_zero_is_identity():
+    s = _pile_spec(m_lo=5, m_hi=40)
+    x = np.random.default_rng(0).random(40)
+    np.testing.assert_array_equal(O.pileup(s, 0.0, x), x[5:40])
+
+
+@pytest.mark.parametrize("d", [0, 1, 6])
+def test_pileup_delta_kernel_is_exact_shift(d):
+    g = np.zeros(7); g[d] = 1.0
+    s = _pile_spec(g=g, m_lo=3, m_hi=40)
+    x = np.random.default_rng(1).random(40)
+    eps = 0.25
+    want = (1 - eps) * x + eps * np.concatenate([np.zeros(d), x[:40 - d]])
+    np.testing.assert_allclose(O.pileup(s, eps, x), want[3:40], rtol=1e-15, atol=1e-16)
+
+
+def test_pileup_conserves_total_and_matches_fft():
+    g = np.random.default_rng(2).random(9); g /= g.sum()
+    s = _pile_spec(g=g, L=9, m_lo=0, m_hi=60)
+    x = np.zeros(60); x[:45] = np.random.default_rng(3).random(45)
+    y = O.pileup(s, 1.0, x)
+    assert abs(y.sum() - x.sum()) < 1e-13
+    np.testing.assert_allclose(y, signal.fftconvolve(x, g)[:60], rtol=1e-12, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------------- a6
+
+def test_poisson_nll_special_cases():
+    assert O.poisson_nll([5.0, 7.0, 0.0], [5.0, 7.0, 0.0]) == 0.0
+    assert O.poisson_nll([0.0, 0.0], [2.5, 0.5]) == pytest.approx(3.0, rel=1e-15)
+    assert O.poisson_nll([1.0], [math.e]) == pytest.approx(math.e - 2.0, rel=1e-15)
+    assert O.poisson_nll([3.0], [0.0]) == math.inf
+
+
+def test_poisson_nll_brute_force_long_double():
+    rng = np.random.default_rng(4)
+    mu = 10 ** rng.uniform(-2, 6, size=2000)
+    n = rng.poisson(mu).astype(float)
+    nl, ml = n.astype(np.longdouble), mu.astype(np.longdouble)
+    terms = np.where(nl > 0, ml - nl + nl * np.log(np.where(nl > 0, nl, 1) / ml), ml)
+    want = float(np.sum(terms))
+    assert O.poisson_nll(n, mu) == pytest.approx(want, rel=1e-13)
+
+
+def test_baker_cousins_differs_by_data_constant():
+    """-lnL differences between parameter points equal those of sum(mu - n ln mu)."""
+    s = I.config("small_mv")
+    mu0 = O.expected(s, s.theta_true)
+    s = s.with_counts(I.poisson_counts(mu0, 11))
+    n = s.counts_vector()
+    th1 = s.theta_true * 1.01
+    mu1 = O.expected(s, th1)
+    plain = lambda mu: float(np.sum(mu.astype(np.longdouble) - n * np.log(mu.astype(np.longdouble))))
+    d_or = O.nll(s, th1) - O.nll(s, s.theta_true)
+    assert d_or == pytest.approx(plain(mu1) - plain(mu0), rel=1e-9, abs=1e-9)
+
+
+# ------------------------------------------------------------------ radial term (Eq. 4)
+
+def test_radial_probabilities_closed_form():
+    s = I.config("small_mv")
+    edges = np.linspace(0, s.r_fid, s.n_rad + 1)
+    p_int, dp_int = O.radial(s, 1.0, I.RAD_INTERNAL)
+    np.testing.assert_allclose(p_int, np.diff(edges ** 3) / s.r_fid ** 3, rtol=1e-13)
+    assert np.all(dp_int == 0)
+    for s_r in (0.6, 1.0, 1.7):
+        lam = s.att_len * s_r
+        F = lambda r: np.exp((r - s.r_iv) / lam) * (lam * r * r - 2 * lam ** 2 * r + 2 * lam ** 3)
+        want = np.diff(F(edges)); want /= want.sum()
+        p, dp = O.radial(s, s_r, I.RAD_EXTERNAL)
+        np.testing.assert_allclose(p, want, rtol=1e-12)
+        h = 1e-6 * s_r
+        pp, _ = O.radial(s, s_r + h, 1)
+        pm, _ = O.radial(s, s_r - h, 1)
+        np.testing.assert_allclose(dp, (pp - pm) / (2 * h), rtol=1e-6, atol=1e-12)
+
+
+# ------------------------------------------------------------- whole model, brute force
+
+def _tiny_spec():
+    rng = np.random.default_rng(5)
+    shapes = rng.random((2, 5)); shapes /= shapes.sum(axis=1, keepdims=True)
+    s = I.ModelSpec(name="tiny", n_grid=5, e_max=3.0, shapes=shapes, stop_pow=1.5 + rng.random(5),
+                    pileup=np.array([0.7, 0.3]), width=300.0, m_lo=1, m_hi=4,
+                    tag_frac=np.array([0.9, 0.1]), rad_class=np.array([0, 1], np.int32), n_rad=3,
+                    psd_prob=np.array([[0.6, 0.4], [0.2, 0.8]]), species=["a", "b"])
+    s.theta_true = np.array([3000.0, 1200.0, 480.0, 1.3, 3e-4, 6.0, 0.02, 0.1, 1.2])
+    s.counts = {"sub": np.array([400.0, 900.0, 150.0]), "tag": np.array([90.0, 300.0, 0.0]),
+                "rad": np.array([100.0, 500.0, 1900.0]), "psd": np.array([1500.0, 1000.0])}
+    return s
+
+
+def _tiny_brute_force(s, th):
+    K, N, M = s.K, s.n_grid, s.m_hi
+    r = th[:K]
+    LY, a, b, c, kB, eps, s_r = th[K:]
+    dE = s.e_max / N
+    Q, run = [], 0.0
+    for i in range(N):
+        x = dE / (1 + kB * s.stop_pow[i])
+        Q.append(run + 0.5 * x)
+        run += x
+    v = np.zeros((M, K))
+    for i in range(N):
+        mu = LY * Q[i]
+        sig = math.sqrt(a * mu + b * mu * mu + c)
+        norm = gauss_bin_quad(0.0, mu + 60 * sig, mu, sig)
+        for m in range(M):
+            R = gauss_bin_quad(m * s.width, (m + 1) * s.width, mu, sig) / norm
+            for k in range(K):
+                v[m, k] += R * s.shapes[k, i]
+    def pile(x):
+        out = []
+        for m in range(s.m_lo, s.m_hi):
+            conv = sum(s.pileup[d] * x[m - d] for d in range(min(m, s.L - 1) + 1))
+            out.append((1 - eps) * x[m] + eps * conv)
+        return np.array(out)
+    sub = pile(v @ (r * (1 - s.tag_frac)))
+    tag = pile(v @ (r * s.tag_frac))
+    A = np.array([r[k] * (1 - s.tag_frac[k]) * pile(v[:, k]).sum() for k in range(K)])
+    lam = s.att_len * s_r
+    edges = np.linspace(0, s.r_fid, s.n_rad + 1)
+    prad = []
+    for k in range(K):
+        f = (lambda x: x * x) if s.rad_class[k] == 0 else (lambda x: x * x * math.exp(-(s.r_iv - x) / lam))
+        bins = np.array([integrate.quad(f, edges[j], edges[j + 1], epsrel=1e-14)[0] for j in range(s.n_rad)])
+        prad.append(bins / bins.sum())
+    rad = sum(A[k] * prad[k] for k in range(K))
+    psd = A @ s.psd_prob
+    mu = np.concatenate([sub, tag, rad, psd])
+    n = s.counts_vector()
+    tot = np.longdouble(0)
+    for nj, mj in zip(n, mu):
+        tot += np.longdouble(mj) if nj == 0 else np.longdouble(mj) - nj + nj * np.log(np.longdouble(nj) / np.longdouble(mj))
+    return mu, float(tot)
+
+
+def test_tiny_model_brute_force():
+    """N = 5 grid points, 4 bins, 2 species with TFC, radial and pulse-shape terms, summed
+    by hand-written loops with quadrature in place of erfc (Eq. 1-4)."""
+    s = _tiny_spec()
+    for th in (s.theta_true, s.theta_true * np.array([1.1, 0.9, 1.05, 0.8, 1.5, 0.9, 1.3, 0.5, 0.7])):
+        mu_bf, nll_bf = _tiny_brute_force(s, th)
+        np.testing.assert_allclose(O.expected(s, th), mu_bf, rtol=1e-10)
+        assert O.nll(s, th) == pytest.approx(nll_bf, rel=1e-10)
+
+
+# ------------------------------------------------------------------------ gradient (a7)
+
+@pytest.mark.parametrize("name", ["small_plain", "small_mv"])
+def test_dual_gradient_matches_central_differences(name):
+    s = I.config(name)
+    s = s.with_counts(I.poisson_counts(O.expected(s, s.theta_true), 3))
+    th = I.parameter_points(s.theta_true, 1, rel=0.02, seed=5)[0]
+    f, g = O.nll(s, th, grad=True)
+    gfd = np.zeros_like(g)
+    for j in range(s.P):
+        h = 1e-5 * abs(th[j])
+        tp, tm = th.copy(), th.copy()
+        tp[j] += h; tm[j] -= h
+        gfd[j] = (O.nll(s, tp) - O.nll(s, tm)) / (2 * h)
+    scale = np.abs(g * th)
+    np.testing.assert_allclose(g * th, gfd * th, rtol=2e-6, atol=2e-7 * scale.max())
+
+
+def test_rate_gradient_is_linear_in_mu():
+    """sum_k r_k dNLL/dr_k = sum_bins (mu - n): every expected count is homogeneous of
+    degree one in the rates."""
+    s = I.config("small_mv")
+    s = s.with_counts(I.poisson_counts(O.expected(s, s.theta_true), 4))
+    th = s.theta_true * 1.03
+    _, g = O.nll(s, th, grad=True)
+    mu = O.expected(s, th)
+    lhs = float(np.dot(th[:s.K], g[:s.K]))
+    assert lhs == pytest.approx(float(np.sum(mu - s.counts_vector())), rel=1e-10)
+
+
+# ----------------------------------------------------------------------------- fit (a8)
+
+def test_fit_asimov_returns_truth():
+    s = I.config("small_plain")
+    s = s.with_counts(O.expected(s, s.theta_true))   # non-integer Asimov data
+    th0 = I.parameter_points(s.theta_true, 1, rel=0.05, seed=6, free=s.default_free())[0]
+    r = O.fit(s, th0, tol_edm=1e-16)
+    assert r["status"] == 0
+    assert r["nll"] < 1e-8
+    np.testing.assert_allclose(r["theta"], s.theta_true, rtol=1e-5)
+
+
+def test_fit_normalisation_invariant_at_optimum():
+    """With free rates at an interior optimum, sum(mu) = sum(n) over all bins."""
+    s = I.config("small_mv")
+    s = s.with_counts(I.poisson_counts(O.expected(s, s.theta_true), 8))
+    r = O.fit(s, s.theta_true, tol_edm=1e-14)
+    assert r["status"] == 0
+    assert np.all(r["theta"][:s.K] > 0)
+    mu = O.expected(s, r["theta"])
+    assert mu.sum() == pytest.approx(s.counts_vector().sum(), rel=1e-9)
