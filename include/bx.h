@@ -1,0 +1,170 @@
+/*
+ * bx.h -- C ABI of the GB300 (sm_103a) binned Poisson -lnL engine for the Borexino-style
+ * multivariate spectral fit of arXiv:1805.11125.
+ *
+ * What one evaluation computes (Sec. 3 of the paper; readings where the paper is silent
+ * are stated inline):
+ *   Eq. 1  every species' true-energy shape s_k[i] is mapped to the observable (npe) by
+ *          the response R[m,i]: Birks quenching Q_i = sum_{j<i} dE/(1+kB S_j) +
+ *          dE/(2(1+kB S_i)) (S = caller-supplied stopping power), mean mu_i = LY Q_i,
+ *          Gaussian resolution of variance a mu_i + b mu_i^2 + c, bin-integrated over
+ *          [m w, (m+1) w) and normalised to the mass above 0 npe;
+ *          v_k[m] = sum_i R[m,i] s_k[i].
+ *   Eq. 3  two energy spectra, TFC-vetoed (weight 1 - t_k) and TFC-tagged (weight t_k),
+ *          lambda_h[m] = sum_k r_k c_{h,k} v_k[m]; without tag fractions a single
+ *          spectrum with weight 1.
+ *   Eq. 2  pile-up with scale eps and random-trigger spectrum g (sum g = 1):
+ *          mu_h[m] = (1-eps) lambda_h[m] + eps sum_{d=0}^{min(m,L-1)} g[d] lambda_h[m-d].
+ *   Eq. 4  radial and pulse-shape histograms: window marginals of the TFC-vetoed species
+ *          spectra after pile-up, times radial bin probabilities (internal: uniform in
+ *          volume; external: exp(-(r_iv - r)/(att_len s_r)) r^2, in a sphere r_fid) and
+ *          caller-supplied pulse-shape bin probabilities.
+ *   -lnL  = sum over all bins of mu - n + n ln(n/mu)   (n ln(n/mu) := 0 at n = 0),
+ *          the Baker-Cousins form: it differs from sum(mu - n ln mu + ln n!) by the
+ *          data-only constant sum(n - n ln n + ln n!), so -2 lnL differences are equal.
+ *
+ * Parameter vector of a toy with K species (P = K + 7), FP64:
+ *   theta = [r_0 .. r_{K-1}, LY, a, b, c, kB, eps, s_r]
+ * r_k are expected event counts of species k (exposure folded in).
+ *
+ * Conventions for every call:
+ *   - status codes never abort; bx_last_error() gives a thread-local message;
+ *   - the caller owns every input array; bx_model_create copies them to the device;
+ *   - the library owns all device buffers of a model until bx_model_destroy;
+ *   - work runs on the CUDA stream given at creation (or bx_model_set_stream);
+ *   - host-pointer calls return after their results are in host memory;
+ *     device-pointer calls (device_ptrs = 1) return once the work is enqueued.
+ */
+#ifndef BX_H
+#define BX_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bx_model bx_model;                 /* opaque; owns device memory */
+
+typedef enum {
+    BX_OK = 0,
+    BX_EINVAL = -1,     /* invalid argument or model description */
+    BX_ENOMEM = -2,     /* device or host allocation failed */
+    BX_ECUDA = -3,      /* a CUDA call failed (message in bx_last_error) */
+    BX_EDOMAIN = -4,    /* expected count <= 0 in a bin with data, or sigma^2 <= 0: -lnL = +inf */
+    BX_ETIMEOUT = -5,   /* a device-side wait ran out of its time budget */
+    BX_ENOTCONV = -6    /* a fit did not converge within its iteration budget */
+} bx_status;
+
+typedef enum {
+    BX_FP64 = 0,        /* every step in FP64 on the CUDA cores (reference GPU form) */
+    BX_FP32 = 1,        /* mixed: response generated and contracted in FP32 on the CUDA cores
+                           (round-to-nearest, compensated accumulation); FP64 column
+                           normalisation, spectra assembly, -lnL sum and fit update */
+    BX_TF32X3 = 3       /* as BX_FP32, but the contraction runs on the tensor cores as
+                           TF32 hi*hi + hi*lo + lo*hi with FP32 accumulation in tensor
+                           memory (its accumulator does not round to nearest: see the
+                           error table of the documentation before using it for fits) */
+} bx_precision;
+
+enum { BX_RAD_INTERNAL = 0, BX_RAD_EXTERNAL = 1 };
+
+/* One dataset (toy) and its model.  All arrays are host FP64 (rad_class int32) and are
+ * copied at creation. */
+typedef struct {
+    int n_grid;                 /* true-energy points N; E_i = (i + 1/2) e_max / N */
+    double e_max;               /* MeV */
+    int n_species;              /* K, 1..16 */
+    const double* shapes;       /* [K][N], each row >= 0 (rows need not sum to 1) */
+    const double* stop_pow;     /* [N] stopping power on the grid, MeV/cm (> 0) */
+    const double* tag_frac;     /* [K] TFC tagging fraction t_k, or NULL: one spectrum */
+    int n_pileup;               /* L, 1..4096 */
+    const double* pileup;       /* [L] random-trigger spectrum in bins of `width` */
+    double width;               /* npe per bin */
+    int m_lo, m_hi;             /* energy window = bins [m_lo, m_hi) of the axis [0, m_hi) */
+    const double* counts_sub;   /* [m_hi - m_lo] vetoed (or single) spectrum data */
+    const double* counts_tag;   /* [m_hi - m_lo] tagged spectrum data (with tag_frac) */
+    int n_rad;                  /* radial bins over [0, r_fid), 0 = no radial term */
+    const int* rad_class;       /* [K] BX_RAD_INTERNAL / BX_RAD_EXTERNAL */
+    double r_fid, r_iv, att_len;/* fiducial radius, vessel radius, attenuation length (m) */
+    const double* counts_rad;   /* [n_rad] */
+    int n_psd;                  /* pulse-shape bins, 0 = no pulse-shape term */
+    const double* psd_prob;     /* [K][n_psd] bin probabilities of each species */
+    const double* counts_psd;   /* [n_psd] */
+} bx_model_desc;
+
+typedef struct {
+    int precision;              /* bx_precision */
+    int max_batch;              /* largest n of bx_nll_batch / bx_fit (>= 1) */
+    double band_sigmas;         /* response entries with |m w - mu_i| > band_sigmas sigma_i
+                                   are skipped (their mass is < 1e-15); 0 -> 8 */
+    double watchdog_s;          /* time budget of any device-side wait; 0 -> 2 s */
+} bx_options;
+
+/* Create a model of n_toys datasets (arrays copied to the device).  opts may be NULL
+ * (BX_FP32, max_batch 1).  cuda_stream is a cudaStream_t (NULL = legacy default). */
+int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_options* opts,
+                    void* cuda_stream, bx_model** out);
+void bx_model_destroy(bx_model* model);
+int bx_model_set_stream(bx_model* model, void* cuda_stream);
+/* P = 7 + max_t K_t: the row stride of every theta / grad array */
+int bx_model_n_params(const bx_model* model);
+/* bins of toy t: window (+ window if tagged) + n_rad + n_psd */
+int bx_model_n_bins(const bx_model* model, int toy);
+/* Sticky device status (BX_OK or BX_ETIMEOUT) after synchronising the model's stream. */
+int bx_model_status(bx_model* model);
+
+/* -lnL of toy 0 at theta[P] (host arrays). */
+int bx_nll(bx_model* model, const double* theta, double* nll);
+/* -lnL and its gradient grad[P] of toy 0 (host arrays).  The gradient comes from the
+ * hand-written adjoint (the paper minimises with numerical derivatives instead). */
+int bx_nll_grad(bx_model* model, const double* theta, double* nll, double* grad);
+/* Expected counts of every bin of toy `toy` at theta (host arrays), in the order:
+ * vetoed window, tagged window, radial, pulse shape. */
+int bx_expected(bx_model* model, int toy, const double* theta, double* mu);
+/* n independent evaluations: item j uses toy toy_idx[j] (host array; NULL = toy 0 for
+ * every item) at theta[j*P .. j*P + P_t).  nll[n]; grad[n*P] or NULL (no adjoint).
+ * device_ptrs = 0: theta/nll/grad are host memory, synchronous.
+ * device_ptrs = 1: theta/nll/grad are device memory; the call only enqueues work. */
+int bx_nll_batch(bx_model* model, int n, const int* toy_idx, const double* theta,
+                 double* nll, double* grad, int device_ptrs);
+
+/* Batched quasi-Newton fits (one NLL+gradient evaluation per fit per iteration; the
+ * paper minimises with TMinuit, Sec. 4). */
+typedef struct {
+    double tol_edm;             /* converged when EDM = g^T V g / 2 < tol_edm (0 -> 1e-7) */
+    int max_iter;               /* iteration budget per fit (0 -> 500) */
+    const unsigned char* free_mask; /* [P] 1 = free (NULL: all free except s_r when no radial term) */
+    const double* lo;           /* [P] lower bounds (NULL: rates >= 0, physical ranges) */
+    const double* hi;           /* [P] upper bounds (NULL: eps <= 1, otherwise none) */
+    int iters_per_launch;       /* iterations per captured CUDA graph launch (0 -> 16) */
+} bx_fit_opts;
+
+typedef struct {
+    double nll;                 /* -lnL at the returned theta */
+    double edm;                 /* estimated distance to minimum */
+    int iters;                  /* accepted quasi-Newton steps */
+    int n_evals;                /* NLL+gradient evaluations used */
+    int status;                 /* BX_OK, BX_ENOTCONV or BX_EDOMAIN */
+} bx_fit_result;
+
+/* n fits; item j fits toy toy_idx[j] (host, NULL = toy 0) from theta0[j*P..].
+ * theta_out[n*P], res[n] (host).  V (inverse Hessian estimate) stays on the device. */
+int bx_fit(bx_model* model, int n, const int* toy_idx, const double* theta0,
+           const bx_fit_opts* opts, double* theta_out, bx_fit_result* res);
+
+/* Diagnostic of the tensor-core path: multiplies a 128 x 32 FP32 matrix by a 16 x 32 one
+ * through the same TF32 hi/lo split, shared-memory operand layout, tcgen05.mma issue and
+ * tensor-memory read-back as the forward kernel, on the current device, and returns the
+ * largest relative error against an FP64 host product in *max_rel_err (expected ~1e-6). */
+int bx_selftest_tensor_core(double* max_rel_err);
+/* Diagnostic of the device watchdog: launches one warp that waits on an mbarrier nothing
+ * ever arrives on, bounded by budget_s (0 < budget_s <= 10).  Returns BX_ETIMEOUT when the
+ * wait ran out as designed (the CUDA context stays usable), BX_ECUDA on a CUDA error. */
+int bx_selftest_watchdog(double budget_s);
+
+const char* bx_last_error(void);
+const char* bx_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BX_H */

@@ -1,0 +1,485 @@
+// bx_api.cu -- host side of the C ABI (include/bx.h): argument validation, model
+// creation (device copies of every toy, set-up kernel), workspace, and the evaluation
+// driver that enqueues k_prep -> k_fwd_* -> k_mid -> [k_bwd_*] -> k_gather on the
+// model's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "bx_model.h"
+#include "bx_internal.cuh"
+
+using namespace bx;
+
+static thread_local std::string g_err;
+
+int bx_set_error(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CU(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return bx_set_error(BX_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                                __FILE__, __LINE__);                                              \
+    } while (0)
+
+extern "C" const char* bx_last_error(void) { return g_err.c_str(); }
+
+extern "C" const char* bx_status_string(int s) {
+    switch (s) {
+        case BX_OK: return "ok";
+        case BX_EINVAL: return "invalid argument";
+        case BX_ENOMEM: return "out of memory";
+        case BX_ECUDA: return "CUDA error";
+        case BX_EDOMAIN: return "expected count <= 0 where data are present (or sigma^2 <= 0)";
+        case BX_ETIMEOUT: return "device wait timed out";
+        case BX_ENOTCONV: return "fit did not converge";
+        default: return "unknown status";
+    }
+}
+
+// ------------------------------------------------------------------ model
+
+static int alloc_dev(bx_model* m, void** p, size_t bytes);
+
+static bool finite_nonneg(const double* a, size_t n) {
+    for (size_t j = 0; j < n; ++j)
+        if (!std::isfinite(a[j]) || a[j] < 0.0) return false;
+    return true;
+}
+
+static int validate_desc(const bx_model_desc& d, int t) {
+#define REQ(cond, ...) \
+    if (!(cond)) return bx_set_error(BX_EINVAL, __VA_ARGS__)
+    REQ(d.n_grid >= 1 && d.n_grid <= MAX_CB * BCOLS, "toy %d: n_grid %d out of [1, %d]", t, d.n_grid, MAX_CB * BCOLS);
+    REQ(std::isfinite(d.e_max) && d.e_max > 0.0, "toy %d: e_max must be > 0", t);
+    REQ(d.n_species >= 1 && d.n_species <= KMAX, "toy %d: n_species %d out of [1, %d]", t, d.n_species, KMAX);
+    REQ(d.shapes && finite_nonneg(d.shapes, (size_t)d.n_species * d.n_grid), "toy %d: shapes missing, negative or not finite", t);
+    REQ(d.stop_pow, "toy %d: stop_pow missing", t);
+    for (int i = 0; i < d.n_grid; ++i) REQ(std::isfinite(d.stop_pow[i]) && d.stop_pow[i] > 0.0, "toy %d: stop_pow[%d] must be > 0", t, i);
+    if (d.tag_frac)
+        for (int k = 0; k < d.n_species; ++k)
+            REQ(d.tag_frac[k] >= 0.0 && d.tag_frac[k] <= 1.0, "toy %d: tag_frac[%d] out of [0, 1]", t, k);
+    REQ(d.n_pileup >= 1 && d.n_pileup <= MAX_L, "toy %d: n_pileup %d out of [1, %d]", t, d.n_pileup, MAX_L);
+    REQ(d.pileup && finite_nonneg(d.pileup, d.n_pileup), "toy %d: pileup missing, negative or not finite", t);
+    REQ(std::isfinite(d.width) && d.width > 0.0, "toy %d: width must be > 0", t);
+    REQ(d.m_lo >= 0 && d.m_hi > d.m_lo && d.m_hi <= MAX_TILES * TM, "toy %d: window [%d, %d) invalid (m_hi <= %d)", t, d.m_lo, d.m_hi, MAX_TILES * TM);
+    const size_t nw = (size_t)(d.m_hi - d.m_lo);
+    REQ(d.counts_sub && finite_nonneg(d.counts_sub, nw), "toy %d: counts_sub missing, negative or not finite", t);
+    REQ(!d.tag_frac || (d.counts_tag && finite_nonneg(d.counts_tag, nw)), "toy %d: counts_tag required with tag_frac", t);
+    REQ(d.n_rad >= 0 && d.n_rad <= MAX_RAD, "toy %d: n_rad out of [0, %d]", t, MAX_RAD);
+    if (d.n_rad > 0) {
+        REQ(d.rad_class && d.counts_rad && finite_nonneg(d.counts_rad, d.n_rad), "toy %d: radial term needs rad_class and counts_rad", t);
+        for (int k = 0; k < d.n_species; ++k) REQ(d.rad_class[k] == 0 || d.rad_class[k] == 1, "toy %d: rad_class[%d] must be 0 or 1", t, k);
+        REQ(d.r_fid > 0.0 && d.r_iv >= d.r_fid && d.att_len > 0.0, "toy %d: radial geometry invalid", t);
+    }
+    REQ(d.n_psd >= 0 && d.n_psd <= MAX_PSD, "toy %d: n_psd out of [0, %d]", t, MAX_PSD);
+    if (d.n_psd > 0)
+        REQ(d.psd_prob && d.counts_psd && finite_nonneg(d.psd_prob, (size_t)d.n_species * d.n_psd) &&
+                finite_nonneg(d.counts_psd, d.n_psd),
+            "toy %d: pulse-shape term needs psd_prob and counts_psd", t);
+#undef REQ
+    return BX_OK;
+}
+
+static int alloc_dev(bx_model* m, void** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return bx_set_error(e == cudaErrorMemoryAllocation ? BX_ENOMEM : BX_ECUDA, "cudaMalloc(%zu): %s", bytes,
+                            cudaGetErrorString(e));
+    }
+    m->allocs.push_back(*p);
+    return BX_OK;
+}
+
+template <typename T>
+static int upload(bx_model* m, const T* src, size_t n, const T** dst) {
+    if (!src) {
+        *dst = nullptr;
+        return BX_OK;
+    }
+    void* p;
+    int st = alloc_dev(m, &p, n * sizeof(T));
+    if (st) return st;
+    CU(cudaMemcpyAsync(p, src, n * sizeof(T), cudaMemcpyHostToDevice, m->stream));
+    *dst = static_cast<const T*>(p);
+    return BX_OK;
+}
+
+static void free_model(bx_model* m) {
+    if (!m) return;
+    bx_fit_free(m);
+    for (void* p : m->allocs) cudaFree(p);
+    for (void* p : m->pinned) cudaFreeHost(p);
+    delete m;
+}
+
+extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_options* opts, void* cuda_stream,
+                               bx_model** out) {
+    if (!out) return bx_set_error(BX_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!descs || n_toys < 1) return bx_set_error(BX_EINVAL, "need at least one model description");
+    bx_options o{BX_FP32, 1, 8.0, 2.0};
+    if (opts) o = *opts;
+    if (o.precision != BX_FP64 && o.precision != BX_FP32 && o.precision != BX_TF32X3)
+        return bx_set_error(BX_EINVAL, "precision %d not supported (BX_FP64, BX_FP32 or BX_TF32X3)", o.precision);
+    if (o.max_batch < 1) return bx_set_error(BX_EINVAL, "max_batch must be >= 1");
+    if (o.band_sigmas == 0.0) o.band_sigmas = 8.0;
+    if (o.watchdog_s == 0.0) o.watchdog_s = 2.0;
+    if (!(o.band_sigmas >= 3.0 && o.band_sigmas <= 40.0)) return bx_set_error(BX_EINVAL, "band_sigmas out of [3, 40]");
+    if (!(o.watchdog_s > 0.0 && o.watchdog_s <= 600.0)) return bx_set_error(BX_EINVAL, "watchdog_s out of (0, 600]");
+    for (int t = 0; t < n_toys; ++t) {
+        int st = validate_desc(descs[t], t);
+        if (st) return st;
+    }
+    int dev = 0;
+    CU(cudaGetDevice(&dev));
+    int cc_major = 0, cc_minor = 0;
+    CU(cudaDeviceGetAttribute(&cc_major, cudaDevAttrComputeCapabilityMajor, dev));
+    CU(cudaDeviceGetAttribute(&cc_minor, cudaDevAttrComputeCapabilityMinor, dev));
+    if (cc_major != 10 || cc_minor != 3)
+        return bx_set_error(BX_ECUDA, "device compute capability %d.%d: this library is built for sm_103a only",
+                            cc_major, cc_minor);
+
+    if (o.precision == BX_TF32X3) {
+        // the tensor-core operand layout is verified once per process before first use
+        static int tc_checked = 0;   // 0 unknown, 1 ok, -1 failed
+        if (tc_checked == 0) {
+            double err = 1.0;
+            const int st = bx_selftest_tensor_core(&err);
+            if (st) return st;
+            tc_checked = err < 1e-5 ? 1 : -1;
+        }
+        if (tc_checked < 0)
+            return bx_set_error(BX_ECUDA, "tensor-core self-test failed: TF32X3 path disabled, use BX_FP64");
+    }
+    bx_model* m = new bx_model();
+    m->stream = static_cast<cudaStream_t>(cuda_stream);
+    m->n_toys = n_toys;
+    m->precision = o.precision;
+    m->cap = o.max_batch;
+    m->band = o.band_sigmas;
+    m->watchdog_ns = (unsigned long long)(o.watchdog_s * 1e9);
+    m->toys_h.resize(n_toys);
+    int st = BX_OK;
+    for (int t = 0; t < n_toys && !st; ++t) {
+        const bx_model_desc& d = descs[t];
+        Toy& T = m->toys_h[t];
+        T = Toy{};
+        T.K = d.n_species;
+        T.N = d.n_grid;
+        T.M = d.m_hi;
+        T.m_lo = d.m_lo;
+        T.nw = d.m_hi - d.m_lo;
+        T.L = d.n_pileup;
+        T.n_rad = d.n_rad;
+        T.n_psd = d.n_psd;
+        T.has_tag = d.tag_frac ? 1 : 0;
+        T.nb = T.nw * (1 + T.has_tag) + T.n_rad + T.n_psd;
+        T.P = T.K + 7;
+        T.n_tiles = (T.M + TM - 1) / TM;
+        T.n_cb = (T.N + BCOLS - 1) / BCOLS;
+        T.n_kb = (T.N + KB - 1) / KB;
+        T.dE = d.e_max / d.n_grid;
+        T.w = d.width;
+        T.r_fid = d.r_fid;
+        T.r_iv = d.r_iv;
+        T.att_len = d.att_len;
+        std::vector<double> cnt;
+        cnt.insert(cnt.end(), d.counts_sub, d.counts_sub + T.nw);
+        if (T.has_tag) cnt.insert(cnt.end(), d.counts_tag, d.counts_tag + T.nw);
+        if (T.n_rad) cnt.insert(cnt.end(), d.counts_rad, d.counts_rad + T.n_rad);
+        if (T.n_psd) cnt.insert(cnt.end(), d.counts_psd, d.counts_psd + T.n_psd);
+        if ((st = upload(m, d.shapes, (size_t)T.K * T.N, &T.shapes))) break;
+        if ((st = upload(m, d.stop_pow, (size_t)T.N, &T.stop_pow))) break;
+        if ((st = upload(m, d.tag_frac, (size_t)T.K, &T.tag))) break;
+        if ((st = upload(m, d.pileup, (size_t)T.L, &T.g))) break;
+        if ((st = upload(m, cnt.data(), cnt.size(), &T.cnt))) break;
+        if ((st = upload(m, T.n_rad ? d.rad_class : nullptr, (size_t)T.K, &T.rad_class))) break;
+        if ((st = upload(m, T.n_psd ? d.psd_prob : nullptr, (size_t)T.K * T.n_psd, &T.psd))) break;
+        void *s32, *stiles, *g32, *gg;
+        if ((st = alloc_dev(m, &s32, (size_t)T.K * T.N * sizeof(float)))) break;
+        if ((st = alloc_dev(m, &stiles, (size_t)T.n_kb * 2 * US * KB * sizeof(float)))) break;
+        if ((st = alloc_dev(m, &g32, (size_t)T.L * sizeof(float)))) break;
+        if ((st = alloc_dev(m, &gg, (size_t)T.M * sizeof(double)))) break;
+        T.shapes32 = static_cast<float*>(s32);
+        T.S_tiles = static_cast<float*>(stiles);
+        T.g32 = static_cast<float*>(g32);
+        T.Gg = static_cast<double*>(gg);
+        cudaError_t e = launch_setup_toy(T, static_cast<float*>(s32), static_cast<float*>(stiles),
+                                         static_cast<float*>(g32), static_cast<double*>(gg), m->stream);
+        if (e != cudaSuccess) st = bx_set_error(BX_ECUDA, "set-up kernel: %s", cudaGetErrorString(e));
+        m->Kmax = std::max(m->Kmax, T.K);
+        m->Nmax = std::max(m->Nmax, T.N);
+        m->Mmax = std::max(m->Mmax, T.M);
+        m->nwmax = std::max(m->nwmax, T.nw);
+        m->nbmax = std::max(m->nbmax, T.nb);
+        m->Lmax = std::max(m->Lmax, T.L);
+        m->max_tiles = std::max(m->max_tiles, T.n_tiles);
+        m->max_cb = std::max(m->max_cb, T.n_cb);
+        m->any_tag |= T.has_tag;
+        m->any_cols |= (T.n_rad > 0 || T.n_psd > 0) ? 1 : 0;
+    }
+    if (st) {
+        cudaStreamSynchronize(m->stream);
+        free_model(m);
+        return st;
+    }
+    m->P = m->Kmax + 7;
+    const int cap = m->cap;
+    Work& w = m->w;
+    w = Work{};
+    w.cap = cap;
+    w.Npad = ((m->Nmax + 127) / 128) * 128;
+    w.Mpad = ((m->Mmax + 127) / 128) * 128;
+    w.nbmax = m->nbmax;
+    w.pstride = m->P;
+    w.precision = m->precision;
+    w.band = m->band;
+    w.watchdog_ns = m->watchdog_ns;
+    w.max_tiles = m->max_tiles;
+    const size_t tv = m->precision == BX_FP64 ? sizeof(double) : sizeof(float);
+    const bool species = m->precision == BX_TF32X3;
+    struct A {
+        void** p;
+        size_t bytes;
+    } plan[] = {
+        {(void**)&w.toys, sizeof(Toy) * n_toys},
+        {(void**)&w.toy_of, sizeof(int) * cap},
+        {(void**)&w.col64, sizeof(Col64) * cap * w.Npad},
+        {(void**)&w.colq, sizeof(double2) * cap * w.Npad},
+        {(void**)&w.colf, sizeof(float4) * cap * w.Npad},
+        {(void**)&w.colg, sizeof(ColG) * cap * w.Npad},
+        {(void**)&w.colS, sizeof(double2) * cap * w.Npad},
+        {(void**)&w.aW, sizeof(double) * cap * w.Npad},
+        {(void**)&w.lam, sizeof(double) * cap * 2 * w.Mpad},
+        {(void**)&w.apart, m->any_cols && !species ? tv * cap * m->max_tiles * w.Npad : 16},
+        {(void**)&w.tile_cols, sizeof(int2) * cap * MAX_TILES},
+        {(void**)&w.cb_rows, sizeof(int2) * cap * MAX_CB},
+        {(void**)&w.v, species ? tv * cap * w.Mpad * US : 16},
+        {(void**)&w.rowW, tv * cap * 3 * w.Mpad},
+        {(void**)&w.coef, sizeof(double) * cap * 3 * KMAX},
+        {(void**)&w.gmid, sizeof(double) * cap * PMAX},
+        {(void**)&w.gpart, sizeof(double) * cap * MAX_CB * GPN},
+        {(void**)&w.nll, sizeof(double) * cap},
+        {(void**)&w.mu, sizeof(double) * cap * m->nbmax},
+        {(void**)&w.status, sizeof(int) * cap},
+        {(void**)&w.err, sizeof(unsigned)},
+        {(void**)&m->theta_d, sizeof(double) * cap * m->P},
+        {(void**)&m->nll_d, sizeof(double) * cap},
+        {(void**)&m->grad_d, sizeof(double) * cap * m->P},
+    };
+    for (auto& a : plan)
+        if ((st = alloc_dev(m, a.p, a.bytes))) break;
+    if (!st) {
+        cudaError_t e = cudaMemcpyAsync((void*)w.toys, m->toys_h.data(), sizeof(Toy) * n_toys, cudaMemcpyHostToDevice,
+                                        m->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.err, 0, sizeof(unsigned), m->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync((void*)w.toy_of, 0, sizeof(int) * cap, m->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+        if (e != cudaSuccess) st = bx_set_error(BX_ECUDA, "model upload: %s", cudaGetErrorString(e));
+    }
+    if (st) {
+        free_model(m);
+        return st;
+    }
+    m->toy_cached.assign(cap, 0);
+    *out = m;
+    return BX_OK;
+}
+
+extern "C" void bx_model_destroy(bx_model* m) {
+    if (!m) return;
+    cudaStreamSynchronize(m->stream);
+    free_model(m);
+}
+
+extern "C" int bx_model_set_stream(bx_model* m, void* s) {
+    if (!m) return bx_set_error(BX_EINVAL, "model is NULL");
+    m->stream = static_cast<cudaStream_t>(s);
+    return BX_OK;
+}
+
+extern "C" int bx_model_n_params(const bx_model* m) { return m ? m->P : 0; }
+
+extern "C" int bx_model_n_bins(const bx_model* m, int toy) {
+    if (!m || toy < 0 || toy >= m->n_toys) return 0;
+    return m->toys_h[toy].nb;
+}
+
+// Read and clear the sticky device error word (synchronises the stream).
+int bx_take_device_error(bx_model* m) {
+    unsigned err = 0;
+    CU(cudaStreamSynchronize(m->stream));
+    CU(cudaMemcpy(&err, m->w.err, sizeof err, cudaMemcpyDeviceToHost));
+    if (err) {
+        CU(cudaMemset(m->w.err, 0, sizeof(unsigned)));
+        return bx_set_error(BX_ETIMEOUT, "a device-side wait exceeded its time budget (error word 0x%x)", err);
+    }
+    return BX_OK;
+}
+
+extern "C" int bx_model_status(bx_model* m) {
+    if (!m) return bx_set_error(BX_EINVAL, "model is NULL");
+    return bx_take_device_error(m);
+}
+
+// ------------------------------------------------------------------ evaluation
+
+int bx_set_items(bx_model* m, int n, const int* toy_idx) {
+    if (n < 1 || n > m->cap) return bx_set_error(BX_EINVAL, "n = %d out of [1, max_batch = %d]", n, m->cap);
+    std::vector<int>& tmp = m->toy_tmp;
+    tmp.assign(n, 0);
+    if (toy_idx)
+        for (int j = 0; j < n; ++j) {
+            if (toy_idx[j] < 0 || toy_idx[j] >= m->n_toys)
+                return bx_set_error(BX_EINVAL, "toy_idx[%d] = %d out of [0, %d)", j, toy_idx[j], m->n_toys);
+            tmp[j] = toy_idx[j];
+        }
+    if (!std::equal(tmp.begin(), tmp.end(), m->toy_cached.begin())) {
+        // pageable source: the copy has consumed tmp when the call returns
+        CU(cudaMemcpyAsync((void*)m->w.toy_of, tmp.data(), sizeof(int) * n, cudaMemcpyHostToDevice, m->stream));
+        std::copy(tmp.begin(), tmp.end(), m->toy_cached.begin());
+    }
+    return BX_OK;
+}
+
+int bx_enqueue_eval(bx_model* m, int n, const double* theta_dev, int tstride, int want_grad, int want_mu,
+                    double* nll_dev, double* grad_dev) {
+    Work w = m->w;
+    w.theta = theta_dev;
+    w.tstride = tstride;
+    w.n_items = n;
+    cudaStream_t s = m->stream;
+    CU(launch_prep(w, n, s));
+    if (m->precision == BX_FP64) CU(launch_fwd_f64(w, n, m->max_tiles, m->any_tag, m->any_cols, s));
+    else if (m->precision == BX_FP32) CU(launch_fwd_f32(w, n, m->max_tiles, m->any_tag, m->any_cols, s));
+    else CU(launch_fwd_tc(w, n, m->max_tiles, s));
+    CU(launch_mid(w, n, m->Mmax, m->nwmax, m->Lmax, want_grad, want_mu, s));
+    if (want_grad) CU(launch_bwd(w, n, m->max_cb, s));
+    CU(launch_gather(w, n, nll_dev, grad_dev, want_grad, s));
+    return BX_OK;
+}
+
+static int eval_host(bx_model* m, int n, const int* toy_idx, const double* theta, int want_grad, int want_mu,
+                     double* nll, double* grad) {
+    int st = bx_set_items(m, n, toy_idx);
+    if (st) return st;
+    const int P = m->P;
+    for (int j = 0; j < n; ++j) {
+        const int t = m->toy_tmp[j];
+        for (int q = 0; q < m->toys_h[t].P; ++q)
+            if (!std::isfinite(theta[(size_t)j * P + q]))
+                return bx_set_error(BX_EINVAL, "theta[%d][%d] is not finite", j, q);
+    }
+    CU(cudaMemcpyAsync(m->theta_d, theta, sizeof(double) * n * P, cudaMemcpyHostToDevice, m->stream));
+    if ((st = bx_enqueue_eval(m, n, m->theta_d, P, want_grad, want_mu, m->nll_d, m->grad_d))) return st;
+    if (nll) CU(cudaMemcpyAsync(nll, m->nll_d, sizeof(double) * n, cudaMemcpyDeviceToHost, m->stream));
+    if (grad && want_grad)
+        CU(cudaMemcpyAsync(grad, m->grad_d, sizeof(double) * n * P, cudaMemcpyDeviceToHost, m->stream));
+    if ((st = bx_take_device_error(m))) return st;
+    if (nll)
+        for (int j = 0; j < n; ++j)
+            if (std::isinf(nll[j]))
+                return bx_set_error(BX_EDOMAIN, "item %d: expected count <= 0 in a bin with data, or invalid "
+                                                "response parameters", j);
+    return BX_OK;
+}
+
+extern "C" int bx_nll(bx_model* m, const double* theta, double* nll) {
+    if (!m || !theta || !nll) return bx_set_error(BX_EINVAL, "NULL argument");
+    return eval_host(m, 1, nullptr, theta, 0, 0, nll, nullptr);
+}
+
+extern "C" int bx_nll_grad(bx_model* m, const double* theta, double* nll, double* grad) {
+    if (!m || !theta || !nll || !grad) return bx_set_error(BX_EINVAL, "NULL argument");
+    return eval_host(m, 1, nullptr, theta, 1, 0, nll, grad);
+}
+
+extern "C" int bx_expected(bx_model* m, int toy, const double* theta, double* mu) {
+    if (!m || !theta || !mu) return bx_set_error(BX_EINVAL, "NULL argument");
+    if (toy < 0 || toy >= m->n_toys) return bx_set_error(BX_EINVAL, "toy %d out of range", toy);
+    double nll;
+    int st = eval_host(m, 1, &toy, theta, 0, 1, &nll, nullptr);
+    if (st && st != BX_EDOMAIN) return st;
+    CU(cudaMemcpyAsync(mu, m->w.mu, sizeof(double) * m->toys_h[toy].nb, cudaMemcpyDeviceToHost, m->stream));
+    CU(cudaStreamSynchronize(m->stream));
+    return BX_OK;
+}
+
+extern "C" int bx_nll_batch(bx_model* m, int n, const int* toy_idx, const double* theta, double* nll, double* grad,
+                            int device_ptrs) {
+    if (!m || !theta || !nll) return bx_set_error(BX_EINVAL, "NULL argument");
+    if (!device_ptrs) return eval_host(m, n, toy_idx, theta, grad != nullptr, 0, nll, grad);
+    int st = bx_set_items(m, n, toy_idx);
+    if (st) return st;
+    return bx_enqueue_eval(m, n, theta, m->P, grad != nullptr, 0, nll, grad ? grad : m->grad_d);
+}
+
+extern "C" int bx_selftest_watchdog(double budget_s) {
+    if (!(budget_s > 0.0 && budget_s <= 10.0)) return bx_set_error(BX_EINVAL, "budget_s out of (0, 10]");
+    unsigned* derr;
+    unsigned herr = 0;
+    CU(cudaMalloc(&derr, sizeof(unsigned)));
+    cudaError_t e = cudaMemset(derr, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = launch_watchdog_selftest(derr, (unsigned long long)(budget_s * 1e9), 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&herr, derr, sizeof herr, cudaMemcpyDeviceToHost);
+    cudaFree(derr);
+    if (e != cudaSuccess) return bx_set_error(BX_ECUDA, "watchdog self-test: %s", cudaGetErrorString(e));
+    if (herr & ERR_TIMEOUT) return bx_set_error(BX_ETIMEOUT, "watchdog self-test: the unsatisfiable wait timed out");
+    return BX_OK;
+}
+
+extern "C" int bx_selftest_tensor_core(double* max_rel_err) {
+    if (!max_rel_err) return bx_set_error(BX_EINVAL, "NULL argument");
+    // A[128][32], B[16][32]: values spanning several binades so the hi/lo split matters
+    std::vector<float> A(TM * KB), B(US * KB), D(TM * US);
+    unsigned s = 12345u;
+    auto rnd = [&]() { s = s * 1664525u + 1013904223u; return (float)((s >> 8) & 0xFFFFFF) / 16777216.0f; };
+    for (auto& x : A) x = rnd() * std::pow(2.0f, -(float)(int)(rnd() * 6));
+    for (auto& x : B) x = rnd();
+    float *dA, *dB, *dD;
+    unsigned* derr;
+    CU(cudaMalloc(&dA, A.size() * 4));
+    CU(cudaMalloc(&dB, B.size() * 4));
+    CU(cudaMalloc(&dD, D.size() * 4));
+    CU(cudaMalloc(&derr, 4));
+    CU(cudaMemcpy(dA, A.data(), A.size() * 4, cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(dB, B.data(), B.size() * 4, cudaMemcpyHostToDevice));
+    CU(cudaMemset(dD, 0, D.size() * 4));
+    CU(cudaMemset(derr, 0, 4));
+    cudaError_t e = launch_umma_selftest(dA, dB, dD, derr, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    unsigned herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(D.data(), dD, D.size() * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&herr, derr, 4, cudaMemcpyDeviceToHost);
+    cudaFree(dA); cudaFree(dB); cudaFree(dD); cudaFree(derr);
+    if (e != cudaSuccess) return bx_set_error(BX_ECUDA, "tensor-core self-test: %s", cudaGetErrorString(e));
+    if (herr) return bx_set_error(BX_ETIMEOUT, "tensor-core self-test: MMA completion wait timed out");
+    double worst = 0.0;
+    for (int r = 0; r < TM; ++r)
+        for (int n = 0; n < US; ++n) {
+            double ref = 0.0;
+            for (int c = 0; c < KB; ++c) ref += (double)A[r * KB + c] * (double)B[n * KB + c];
+            worst = std::max(worst, std::fabs(D[r * US + n] - ref) / std::fabs(ref));
+        }
+    *max_rel_err = worst;
+    return BX_OK;
+}

@@ -1,0 +1,103 @@
+// bx_fwd_f64.cu -- Eq. 1 forward in plain FP64 on the CUDA cores (the reference GPU form).
+//
+// Same rate-first reductions as the FP32 kernel (row sums lambda_h[m] = sum_i R[m,i] S_h[i]
+// and per-tile column sums a_t[i] = sum_m R[m,i] Gg[m]), with the exact bin mass:
+// unit = (row tile of TM output bins, item), thread = output bin.  For each chunk of
+// FCH64 columns of the tile's band, phase 1 evaluates the Gaussian tail mass at the TM + 1
+// bin edges of each column (one erfc per edge, shared by the two bins it bounds); phase 2
+// forms R[m,i] = (Phi(z_{m+1}) - Phi(z_m)) / Phi(mu_i/sigma_i) from those tails without
+// cancellation and accumulates the row sums; the column sums go through shared memory.
+#include <math.h>
+
+#include "bx_internal.cuh"
+
+namespace bx {
+
+constexpr int FCH64 = 16;   // columns per chunk
+
+template <bool TAG, bool COLS>
+__global__ void __launch_bounds__(TM) k_fwd_f64(Work w) {
+    const int tile = blockIdx.x, item = blockIdx.y, tid = threadIdx.x;
+    const Toy& T = w.toys[w.toy_of[item]];
+    if (tile >= T.n_tiles || w.status[item]) return;
+    const int m0 = tile * TM, M = T.M;
+    const int2 cr = w.tile_cols[(size_t)item * MAX_TILES + tile];
+    const size_t cbase = (size_t)item * w.Npad;
+
+    // tails, column-major so that thread = edge reads consecutive words
+    __shared__ double sT[FCH64 * (TM + 1)];
+    __shared__ unsigned char sF[FCH64 * (TM + 1)];   // 1: edge at or above the mean
+    __shared__ double2 sS[FCH64];
+    __shared__ double sNorm[FCH64];
+    __shared__ double colbuf[COLS ? TM : 1][FCH64 + 1];
+
+    const int m = m0 + tid;
+    const double gg = (COLS && m < M) ? T.Gg[m] : 0.0;
+    double ls = 0.0, lt = 0.0;
+    double* apart = static_cast<double*>(w.apart) + ((size_t)item * w.max_tiles + tile) * w.Npad;
+
+    for (int c0 = cr.x; c0 < cr.y; c0 += FCH64) {
+        for (int j = tid; j < FCH64 * (TM + 1); j += TM) {
+            const int c = j / (TM + 1), e = j % (TM + 1), i = c0 + c;
+            double t = 0.0;
+            unsigned char f = 0;
+            if (i < cr.y) {
+                const Col64 cc = w.col64[cbase + i];
+                const double z = ((double)(m0 + e) * T.w - cc.mu) / cc.sig;
+                if (z >= 0.0) {
+                    t = -0.5 * erfc(z * 0.70710678118654752440);   // -Q(z)
+                    f = 1;
+                } else {
+                    t = 0.5 * erfc(-z * 0.70710678118654752440);   // Phi(z)
+                }
+            }
+            sT[j] = t;
+            sF[j] = f;
+        }
+        if (tid < FCH64) {
+            const bool in = c0 + tid < cr.y;
+            sS[tid] = in ? w.colS[cbase + c0 + tid] : make_double2(0.0, 0.0);
+            sNorm[tid] = in ? w.col64[cbase + c0 + tid].norm : 0.0;
+        }
+        __syncthreads();
+        const int ncol = min(FCH64, cr.y - c0);
+        for (int c = 0; c < ncol; ++c) {
+            const int ja = c * (TM + 1) + tid;
+            // mass of [edge tid, edge tid+1]: same side -> difference of tails; straddling the
+            // mean -> 1 - Q(z_b) - Phi(z_a)
+            const double D = sT[ja + 1] - sT[ja] + ((!sF[ja] && sF[ja + 1]) ? 1.0 : 0.0);
+            const double R = D * sNorm[c];
+            ls = fma(R, sS[c].x, ls);
+            if (TAG) lt = fma(R, sS[c].y, lt);
+            if (COLS) colbuf[tid][c] = R * gg;
+        }
+        if (COLS) {
+            __syncthreads();
+            // column c = tid / 8 summed by 8 threads over 16 rows each
+            const int c = tid >> 3, part = tid & 7;
+            double s = 0.0;
+            for (int j = 0; j < TM / 8; ++j) s += colbuf[part * (TM / 8) + j][c];
+            s += __shfl_xor_sync(0xffffffffu, s, 1);
+            s += __shfl_xor_sync(0xffffffffu, s, 2);
+            s += __shfl_xor_sync(0xffffffffu, s, 4);
+            if (part == 0 && c < ncol) apart[c0 + c] = s;
+        }
+        __syncthreads();
+    }
+    if (m < M) {
+        double* lam = w.lam + (size_t)item * 2 * w.Mpad;
+        lam[m] = ls;
+        if (TAG) lam[w.Mpad + m] = lt;
+    }
+}
+
+cudaError_t launch_fwd_f64(const Work& w, int n, int max_tiles, int any_tag, int any_cols, cudaStream_t s) {
+    dim3 grid(max_tiles, n);
+    if (any_tag && any_cols) k_fwd_f64<true, true><<<grid, TM, 0, s>>>(w);
+    else if (any_tag) k_fwd_f64<true, false><<<grid, TM, 0, s>>>(w);
+    else if (any_cols) k_fwd_f64<false, true><<<grid, TM, 0, s>>>(w);
+    else k_fwd_f64<false, false><<<grid, TM, 0, s>>>(w);
+    return cudaGetLastError();
+}
+
+}  // namespace bx

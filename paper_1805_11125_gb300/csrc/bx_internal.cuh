@@ -1,0 +1,292 @@
+// bx_internal.cuh -- device-side data layout and PTX helpers of the binned -lnL engine.
+//
+// One evaluation (an "item" = one toy at one parameter point) runs as
+//   k_prep   per-column FP64 quantities of Eq. 1 (Birks map, mean, width, normalisation),
+//            the rate-weighted shapes S_h[i] = sum_k r_k c_{h,k} s_k[i] of the Eq. 3
+//            spectra, the window mass of every column, band limits, FP32 column parameters;
+//   k_fwd_*  response generated on the fly (Eq. 1) and reduced both ways: row sums
+//            lambda_h[m] = sum_i R[m,i] S_h[i] and, for the Eq. 4 terms, column sums
+//            a[i] = sum_m R[m,i] Gg[m] (the tensor-core variant instead contracts with every
+//            species shape, v[m][k] = sum_i R[m,i] s_k[i]);
+//   k_mid    Eq. 2 pile-up, Eq. 4 marginals, -lnL (FP64, compensated), adjoint row weights;
+//   k_bwd_*  adjoint of Eq. 1 per true-energy column: response parameters through the
+//            chain rule to LY, a, b, c, kB, and the rates through sum_m R[m,i] wt_h[m];
+//   k_gather final -lnL and gradient per item.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bx.h"
+
+namespace bx {
+
+constexpr int TM = 128;        // forward tile: output rows per unit (UMMA M)
+constexpr int KB = 32;         // forward k-block: true-energy columns per step
+constexpr int US = 16;         // UMMA N: species slots (K <= 16)
+constexpr int NACC = 4;        // rotating TMEM accumulators per forward unit
+constexpr int KMAX = 16;
+constexpr int PMAX = KMAX + 7;
+constexpr int BCOLS = 128;     // backward unit: true-energy columns (one per thread)
+constexpr int MAX_TILES = 64;  // rows per toy <= MAX_TILES * TM
+constexpr int MAX_CB = 64;     // columns per toy <= MAX_CB * BCOLS
+constexpr int MAX_RAD = 256;
+constexpr int MAX_PSD = 256;
+constexpr int MAX_L = 4096;
+
+// Gauss-Legendre 3-point rule on [-1, 1]: nodes 0, +-sqrt(3/5), weights 8/9, 5/9.  The
+// weights are applied as the exact integers 8 and 5 and the 1/9 is folded into the FP64
+// column factor: the FP32 roundings of 8/9 and 5/9 are both upward and would scale every
+// bin mass by 1 + 3e-8, a bias the likelihood cannot absorb.
+constexpr float GL_NODE_HALF = 0.38729833462074170f;   // 0.5 * sqrt(3/5): node offset in bin units
+constexpr float GL_W_MID = 8.0f;
+constexpr float GL_W_OUT = 5.0f;
+constexpr double GL_W_SCALE = 1.0 / 9.0;
+// sqrt(0.5 * log2(e)): exp(-z^2 / 2) = 2^(-(z * S_EX2)^2)
+constexpr double S_EX2 = 0.84932180028801904272;
+constexpr double INV_SQRT_2PI = 0.39894228040143267794;
+
+constexpr int GPN = 5 + KMAX;   // backward partials per column block: LY, a, b, c, kB, rates
+
+enum : unsigned { ERR_TIMEOUT = 1u, ERR_TMEM = 2u };
+
+// FP32 parameters of the outer Gauss-Legendre nodes of one column (see bx_resp.cuh).
+// kk = sqrt(3/5)/2 * hs is the outer-node offset in the scaled variable.
+struct __align__(16) ColG {
+    float kap, Ck2, c_lo, A;   // 2 ln2 kk, 2 * 2^(-kk^2), low part of (1/2 - frac(mu/w)) hs, (h/2) norm / (9 sqrt(2 pi))
+};
+
+// Device description of one toy (dataset + its fixed model inputs).
+struct Toy {
+    int K, N, M, m_lo, nw, L, n_rad, n_psd, has_tag, nb, P;
+    int n_tiles, n_cb, n_kb;
+    double dE, w, r_fid, r_iv, att_len;
+    const double* shapes;     // [K][N]
+    const float* shapes32;    // [K][N]
+    const float* S_tiles;     // [n_kb][2][US*KB]: TF32 hi | lo of the shapes, UMMA K-major
+    const double* stop_pow;   // [N]
+    const double* tag;        // [K] or nullptr
+    const double* g;          // [L]
+    const float* g32;         // [L]
+    const double* Gg;         // [M]: sum over window bins m' of g[m' - m] (0 <= m'-m < L)
+    const double* cnt;        // [nb] data, concatenated (vetoed, tagged, radial, PSD)
+    const int* rad_class;     // [K]
+    const double* psd;        // [K][n_psd]
+};
+
+// Per-column FP64 results of k_prep.
+struct Col64 {
+    double mu, sig, norm, mills;   // mean, width, 1/Phi(mu/sig), phi(mu/sig)/Phi(mu/sig)
+};
+
+// Workspace of a model: every array has `cap` item slots.
+struct Work {
+    int cap, Npad, Mpad, nbmax, pstride, n_items, max_tiles;
+    int precision;
+    double band;
+    unsigned long long watchdog_ns;
+    const Toy* toys;
+    const int* toy_of;        // [cap]
+    const double* theta;      // [n][tstride]
+    int tstride;
+    Col64* col64;             // [cap][Npad]
+    double2* colq;            // [cap][Npad]: Q_i, dQ_i/dkB
+    float4* colf;             // [cap][Npad]: (floor(mu/w), c_hi, hs_hi, hs_lo): hs = w/sig*S_EX2, c = (1/2 - frac(mu/w)) hs
+    ColG* colg;               // [cap][Npad]
+    double2* colS;            // [cap][Npad]: S_vetoed[i], S_tagged[i]
+    double* aW;               // [cap][Npad]: window mass sum_{m in W} R[m,i] (closed form)
+    double* lam;              // [cap][2][Mpad]: lambda_h[m] (rate-first forward)
+    void* apart;              // [cap][max_tiles][Npad] float/double: column sums of R Gg per tile
+    int2* tile_cols;          // [cap][MAX_TILES]: column range of each forward tile
+    int2* cb_rows;            // [cap][MAX_CB]: row range of each backward column block
+    void* v;                  // [cap][Mpad][US] float (TF32X3) or double (FP64)
+    void* rowW;               // [cap][3][Mpad] float or double: wt_sub, wt_tag, G_W
+    double* coef;             // [cap][3][KMAX]
+    double* gmid;             // [cap][PMAX]
+    double* gpart;            // [cap][MAX_CB][GPN]
+    double* nll;              // [cap]
+    double* mu;               // [cap][nbmax]
+    int* status;              // [cap]
+    unsigned* err;            // sticky error word
+};
+
+// ------------------------------------------------------------------ launchers (host)
+cudaError_t launch_setup_toy(const Toy& t, float* shapes32, float* S_tiles, float* g32, double* Gg,
+                             cudaStream_t s);
+cudaError_t launch_prep(const Work& w, int n, cudaStream_t s);
+cudaError_t launch_fwd_f64(const Work& w, int n, int max_tiles, int any_tag, int any_cols, cudaStream_t s);
+cudaError_t launch_fwd_tc(const Work& w, int n, int max_tiles, cudaStream_t s);
+cudaError_t launch_fwd_f32(const Work& w, int n, int max_tiles, int any_tag, int any_cols, cudaStream_t s);
+cudaError_t launch_mid(const Work& w, int n, int Mmax, int nwmax, int Lmax, int want_grad, int want_mu,
+                       cudaStream_t s);
+cudaError_t launch_bwd(const Work& w, int n, int max_cb, cudaStream_t s);
+cudaError_t launch_gather(const Work& w, int n, double* nll_out, double* grad_out, int want_grad, cudaStream_t s);
+cudaError_t launch_umma_selftest(const float* A, const float* B, float* D, unsigned* err, cudaStream_t s);
+cudaError_t launch_watchdog_selftest(unsigned* err, unsigned long long budget_ns, cudaStream_t s);
+
+// ------------------------------------------------------------------ device helpers
+#ifdef __CUDACC__
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase with the given parity; false when the time budget ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned long long budget_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer() - t0 > budget_ns) return false;
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// 1-D bulk copy global -> shared through the TMA unit; completes `bytes` on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// ---- tcgen05 (5th-generation tensor core, accumulators in tensor memory)
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor, no swizzle, K-major operand:
+// core matrices of 8 rows x 16 bytes; lbo = byte step between core matrices along K,
+// sbo = byte step between 8-row groups along M (or N).
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;
+    d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;
+    d |= (uint64_t)1 << 46;   // descriptor version 1 (tcgen05)
+    return d;                 // base offset 0, relative LBO, swizzle none
+}
+
+// Instruction descriptor of kind::tf32: D = F32, A = B = TF32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t umma_idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+// 32 lanes x 16 columns of 32-bit from tensor memory (warp w reads lanes 32w..32w+31).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* out) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) out[j] = __uint_as_float(r[j]);
+}
+
+// ---- compensated FP64 sums
+
+struct Neu {
+    double s, c;
+};
+__device__ __forceinline__ void neu_add(Neu& a, double x) {
+    double t = a.s + x;
+    a.c += fabs(a.s) >= fabs(x) ? (a.s - t) + x : (x - t) + a.s;
+    a.s = t;
+}
+__device__ __forceinline__ Neu neu_merge(Neu a, Neu b) {
+    neu_add(a, b.s);
+    a.c += b.c;
+    return a;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+#endif  // __CUDACC__
+
+}  // namespace bx

@@ -1,0 +1,399 @@
+// bx_mid.cu -- per-item assembly of the likelihood from the forward reductions.
+//
+// One CTA per item.  Inputs: the Eq. 3 spectra lambda_h[m] (rate-first forward) or the
+// species spectra v[m][k] (tensor-core forward, lambda_h = sum_k r_k c_{h,k} v_k), with
+// h = TFC-vetoed (c = 1 - t_k) and TFC-tagged (c = t_k), or one spectrum (c = 1);
+//   Eq. 2  mu_h = (1 - eps) lambda_h + eps (g * lambda_h) on the window (direct sum,
+//          compensated when it runs in FP32);
+//   Eq. 4  A_k = r_k c_{vetoed,k} sum_m v_k[m] G_W[m], G_W = (1 - eps) 1_W + eps Gg: the
+//          expected vetoed events of species k in the window after pile-up (rate-first:
+//          sum_m v_k G_W = sum_i s_k[i] ((1 - eps) aW[i] + eps a[i]), with the closed-form
+//          window mass aW[i] and the forward's column sums a[i]); radial bins
+//          sum_k A_k p_k[rho] (closed-form shell integrals) and pulse-shape bins
+//          sum_k A_k q_k[j];
+//   -lnL   sum of mu - n + n log1p((n - mu)/mu) in FP64 with Neumaier compensation
+//          inside each thread and TwoSum-style merging across the block.
+// With want_grad it also writes the adjoint inputs of the response stage: per row the
+// pile-up-correlated residual weights wt_h[m] and G_W[m], per species the coefficients
+// that turn them into dNLL/dR[m,i], and the gradient of eps, s_r and the parts of the
+// rate gradient that do not pass through the response (the rest comes from k_bwd_*).
+#include <math.h>
+
+#include "bx_internal.cuh"
+
+namespace bx {
+
+constexpr int MID_THREADS = 512;
+constexpr int MID_WARPS = MID_THREADS / 32;
+
+// Sum NV per-thread doubles over the block; result in out[0..NV) (all threads see it).
+template <int NV>
+__device__ void block_sum(double (&x)[NV], double* red, double* out) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        const double s = warp_sum(x[j]);
+        if (lane == 0) red[wid * NV + j] = s;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < NV; j += blockDim.x) {
+        double s = 0.0;
+        for (int q = 0; q < MID_WARPS; ++q) s += red[q * NV + j];
+        out[j] = s;
+    }
+    __syncthreads();
+}
+
+// Dot product acc += a b over a long, decaying sequence.  In FP32 the terms that fall below
+// half an ulp of the accumulator would all be rounded away, a one-sided loss of the pile-up
+// tail (-2e-8 relative in mu for a 400-bin kernel); Kahan compensation keeps them.
+struct Dot32 {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float a, float b) {
+        const float y = fmaf(a, b, -c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+struct Dot64 {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <typename TV> struct DotT { using type = Dot64; };
+template <> struct DotT<float> { using type = Dot32; };
+
+// Shell integral of r^2 exp((r - r_iv)/lam): F and dF/dlam.
+__device__ __forceinline__ void shell_F(double r, double r_iv, double lam, double& F, double& dF) {
+    const double e = exp((r - r_iv) / lam);
+    const double poly = lam * r * r - 2.0 * lam * lam * r + 2.0 * lam * lam * lam;
+    F = e * poly;
+    dF = e * (-(r - r_iv) / (lam * lam) * poly + (r * r - 4.0 * lam * r + 6.0 * lam * lam));
+}
+
+template <typename TV>
+__global__ void __launch_bounds__(MID_THREADS) k_mid(Work w, int want_grad, int want_mu) {
+    extern __shared__ double dsm[];
+    const int item = blockIdx.x, tid = threadIdx.x;
+    const Toy& T = w.toys[w.toy_of[item]];
+    const int K = T.K, M = T.M, nw = T.nw, m_lo = T.m_lo, L = T.L, H = T.has_tag ? 2 : 1;
+    const int nrad = T.n_rad, npsd = T.n_psd, nb = T.nb;
+    double* gmid = w.gmid + (size_t)item * PMAX;
+    if (w.status[item]) {
+        if (tid == 0) w.nll[item] = INFINITY;
+        if (tid < PMAX) gmid[tid] = 0.0;
+        return;
+    }
+    const double* th = w.theta + (size_t)item * w.tstride;
+    const double eps = th[K + 5], s_r = th[K + 6];
+    const TV* v = static_cast<const TV*>(w.v) + (size_t)item * w.Mpad * US;
+
+    double* lam = dsm;                                  // [H][M]
+    double* muw = lam + 2 * M;                          // [H][nw]
+    TV* lamT = reinterpret_cast<TV*>(muw + 2 * nw);     // [H][M], reused for wt after the pile-up
+    TV* puT = lamT + 2 * M;                             // [H][nw] pile-up convolution part
+    TV* wvT = puT + 2 * nw;                             // [H][nw] 1 - n/mu
+    TV* gT = wvT + 2 * nw;                              // [L]
+
+    __shared__ double s_rs[KMAX], s_rt[KMAX], s_SA[2 * KMAX], s_beta[KMAX], s_gr[2 * KMAX];
+    __shared__ double s_pint[MAX_RAD], s_pext[MAX_RAD], s_dpext[MAX_RAD], s_mur[MAX_RAD], s_wr[MAX_RAD];
+    __shared__ double s_mup[MAX_PSD], s_wp[MAX_PSD];
+    __shared__ double red[MID_WARPS * 2 * KMAX];
+    __shared__ double s_misc[8];
+    __shared__ int s_dom;
+
+    if (tid == 0) s_dom = 0;
+    if (tid < K) {
+        const double r = th[tid], t = T.tag ? T.tag[tid] : 0.0;
+        s_rs[tid] = r * (T.tag ? 1.0 - t : 1.0);
+        s_rt[tid] = r * t;
+    }
+    for (int d = tid; d < L; d += MID_THREADS) gT[d] = (TV)T.g[d];
+    __syncthreads();
+
+    // Eq. 3: the energy spectra on the full axis
+    const bool species = w.precision == BX_TF32X3;
+    const double* lamg = w.lam + (size_t)item * 2 * w.Mpad;
+    for (int m = tid; m < M; m += MID_THREADS) {
+        double ls = 0.0, lt = 0.0;
+        if (species) {
+            const TV* vr = v + (size_t)m * US;
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k)
+                if (k < K) {
+                    const double x = (double)vr[k];
+                    ls += s_rs[k] * x;
+                    lt += s_rt[k] * x;
+                }
+        } else {
+            ls = lamg[m];
+            lt = H == 2 ? lamg[w.Mpad + m] : 0.0;
+        }
+        lam[m] = ls;
+        lamT[m] = (TV)ls;
+        if (H == 2) {
+            lam[M + m] = lt;
+            lamT[M + m] = (TV)lt;
+        }
+    }
+    __syncthreads();
+
+    // Eq. 2 on the window
+    for (int idx = tid; idx < H * nw; idx += MID_THREADS) {
+        const int h = idx / nw, j = idx % nw, m = m_lo + j;
+        const TV* x = lamT + h * M;
+        const int dmax = min(m, L - 1);
+        typename DotT<TV>::type conv;
+        for (int d = 0; d <= dmax; ++d) conv.add(gT[d], x[m - d]);
+        const double cv = conv.value();
+        puT[idx] = (TV)cv;
+        muw[idx] = (1.0 - eps) * lam[h * M + m] + eps * cv;
+    }
+
+    // Eq. 4: window marginals of the vetoed species spectra after pile-up
+    const bool mv = nrad > 0 || npsd > 0;
+    if (mv) {
+        double part[2 * KMAX];
+#pragma unroll
+        for (int k = 0; k < 2 * KMAX; ++k) part[k] = 0.0;
+        if (species) {
+            for (int m = tid; m < M; m += MID_THREADS) {
+                const double inW = m >= m_lo ? 1.0 : 0.0, gg = T.Gg[m];
+                const double GW = (1.0 - eps) * inW + eps * gg, dG = gg - inW;
+                const TV* vr = v + (size_t)m * US;
+#pragma unroll
+                for (int k = 0; k < KMAX; ++k)
+                    if (k < K) {
+                        const double x = (double)vr[k];
+                        part[k] += x * GW;
+                        part[KMAX + k] += x * dG;
+                    }
+            }
+        } else {
+            // sum_m v_k[m] G_W[m] = sum_i s_k[i] ((1 - eps) aW[i] + eps a[i]), a[i] from the
+            // per-tile column sums of the forward (valid on each tile's band only)
+            const int2* tcols = w.tile_cols + (size_t)item * MAX_TILES;
+            const TV* ap = static_cast<const TV*>(w.apart) + (size_t)item * w.max_tiles * w.Npad;
+            const double* aWi = w.aW + (size_t)item * w.Npad;
+            for (int i = tid; i < T.N; i += MID_THREADS) {
+                double ag = 0.0;
+                for (int t = 0; t < T.n_tiles; ++t) {
+                    const int2 cr = tcols[t];
+                    if (i >= cr.x && i < cr.y) ag += (double)ap[(size_t)t * w.Npad + i];
+                }
+                const double aw = aWi[i];
+                const double GW = (1.0 - eps) * aw + eps * ag, dG = ag - aw;
+#pragma unroll
+                for (int k = 0; k < KMAX; ++k)
+                    if (k < K) {
+                        const double x = T.shapes[(size_t)k * T.N + i];
+                        part[k] += x * GW;
+                        part[KMAX + k] += x * dG;
+                    }
+            }
+        }
+        block_sum<2 * KMAX>(part, red, s_SA);   // s_SA[k] = sum v G_W, s_SA[KMAX+k] = sum v dG_W/deps
+    }
+    // radial bin probabilities (internal: uniform in volume; external: exponential from r_iv)
+    if (nrad > 0) {
+        const double lamA = T.att_len * s_r;
+        double Ft, dFt, F0, dF0;
+        shell_F(T.r_fid, T.r_iv, lamA, Ft, dFt);
+        shell_F(0.0, T.r_iv, lamA, F0, dF0);
+        const double tot = Ft - F0, dtot = dFt - dF0;
+        for (int b = tid; b < nrad; b += MID_THREADS) {
+            const double ra = T.r_fid * b / nrad, rb = T.r_fid * (b + 1) / nrad;
+            s_pint[b] = (rb * rb * rb - ra * ra * ra) / (T.r_fid * T.r_fid * T.r_fid);
+            double Fa, dFa, Fb, dFb;
+            shell_F(ra, T.r_iv, lamA, Fa, dFa);
+            shell_F(rb, T.r_iv, lamA, Fb, dFb);
+            const double p = (Fb - Fa) / tot;
+            s_pext[b] = p;
+            s_dpext[b] = ((dFb - dFa) / tot - p * dtot / tot) * T.att_len;
+        }
+    }
+    __syncthreads();
+    if (mv && tid == 0) {
+        double aint = 0.0, aext = 0.0;
+        for (int k = 0; k < K; ++k) {
+            const double A = s_rs[k] * s_SA[k];
+            if (nrad > 0 && T.rad_class[k] == BX_RAD_EXTERNAL) aext += A; else aint += A;
+        }
+        s_misc[0] = aint;
+        s_misc[1] = aext;
+    }
+    __syncthreads();
+    for (int b = tid; b < nrad; b += MID_THREADS) s_mur[b] = s_misc[0] * s_pint[b] + s_misc[1] * s_pext[b];
+    for (int j = tid; j < npsd; j += MID_THREADS) {
+        double s = 0.0;
+        for (int k = 0; k < K; ++k) s += s_rs[k] * s_SA[k] * T.psd[(size_t)k * npsd + j];
+        s_mup[j] = s;
+    }
+    __syncthreads();
+
+    // -lnL over every bin
+    Neu acc{0.0, 0.0};
+    double geps = 0.0;
+    int dom = 0;
+    const int nwin = H * nw;
+    for (int b = tid; b < nb; b += MID_THREADS) {
+        const double n = T.cnt[b];
+        double mu;
+        if (b < nwin) mu = muw[b];
+        else if (b < nwin + nrad) mu = s_mur[b - nwin];
+        else mu = s_mup[b - nwin - nrad];
+        double term;
+        if (n == 0.0) term = mu;
+        else if (mu > 0.0 && isfinite(mu)) term = (mu - n) + n * log1p((n - mu) / mu);
+        else { dom = 1; term = 0.0; }
+        neu_add(acc, term);
+        if (want_mu) w.mu[(size_t)item * w.nbmax + b] = mu;
+        if (want_grad) {
+            const double wb = (n == 0.0) ? 1.0 : 1.0 - n / mu;
+            if (b < nwin) {
+                const int h = b / nw, j = b % nw;
+                wvT[b] = (TV)wb;
+                geps += wb * ((double)puT[b] - lam[h * M + m_lo + j]);
+            } else if (b < nwin + nrad) s_wr[b - nwin] = wb;
+            else s_wp[b - nwin - nrad] = wb;
+        }
+    }
+    // merge the compensated partial sums
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        Neu other{__shfl_xor_sync(0xffffffffu, acc.s, o), __shfl_xor_sync(0xffffffffu, acc.c, o)};
+        acc = neu_merge(acc, other);
+        geps += __shfl_xor_sync(0xffffffffu, geps, o);
+    }
+    if (dom) s_dom = 1;
+    const int lane = tid & 31, wid = tid >> 5;
+    if (lane == 0) {
+        red[wid * 3 + 0] = acc.s;
+        red[wid * 3 + 1] = acc.c;
+        red[wid * 3 + 2] = geps;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        Neu tot{0.0, 0.0};
+        double ge = 0.0;
+        for (int q = 0; q < MID_WARPS; ++q) {
+            tot = neu_merge(tot, Neu{red[q * 3], red[q * 3 + 1]});
+            ge += red[q * 3 + 2];
+        }
+        w.nll[item] = s_dom ? INFINITY : tot.s + tot.c;
+        if (s_dom) w.status[item] = BX_EDOMAIN;
+        s_misc[2] = ge;
+    }
+    __syncthreads();
+    if (!want_grad || s_dom) {
+        if (tid < PMAX) gmid[tid] = 0.0;
+        return;
+    }
+
+    // ---- adjoint inputs
+    // beta_k = dNLL/dA_k = sum_rho w_rad p_k[rho] + sum_j w_psd q_k[j]
+    if (mv) {
+        for (int k = wid; k < K; k += MID_WARPS) {
+            double s = 0.0;
+            const bool ext = nrad > 0 && T.rad_class[k] == BX_RAD_EXTERNAL;
+            for (int b = lane; b < nrad; b += 32) s += s_wr[b] * (ext ? s_pext[b] : s_pint[b]);
+            for (int j = lane; j < npsd; j += 32) s += s_wp[j] * T.psd[(size_t)k * npsd + j];
+            s = warp_sum(s);
+            if (lane == 0) s_beta[k] = s;
+        }
+    } else if (tid < K) {
+        s_beta[tid] = 0.0;
+    }
+    __syncthreads();
+    // pile-up-correlated weights wt_h[m] (adjoint of Eq. 2) and G_W[m], written per row
+    TV* rowW = static_cast<TV*>(w.rowW) + (size_t)item * 3 * w.Mpad;
+    TV* wt = lamT;   // lambda copies are no longer needed
+    for (int idx = tid; idx < H * M; idx += MID_THREADS) {
+        const int h = idx / M, m = idx % M;
+        const TV* wh = wvT + h * nw;
+        const int d0 = max(0, m_lo - m), d1 = min(L - 1, M - 1 - m);
+        typename DotT<TV>::type acc;
+        for (int d = d0; d <= d1; ++d) acc.add(gT[d], wh[m + d - m_lo]);
+        const double direct = (m >= m_lo) ? (1.0 - eps) * (double)wh[m - m_lo] : 0.0;
+        const TV val = (TV)(direct + eps * acc.value());
+        wt[idx] = val;
+        rowW[(size_t)h * w.Mpad + m] = val;
+    }
+    for (int m = tid; m < M; m += MID_THREADS) {
+        if (H == 1) rowW[(size_t)w.Mpad + m] = (TV)0;
+        const double inW = m >= m_lo ? 1.0 : 0.0;
+        rowW[(size_t)2 * w.Mpad + m] = mv ? (TV)((1.0 - eps) * inW + eps * T.Gg[m]) : (TV)0;
+    }
+    __syncthreads();
+    // rate gradient, part through the spectra: sum_h c_{h,k} sum_m wt_h[m] v_k[m]; only the
+    // tensor-core path has v here, the rate-first path gets it from k_bwd_* as
+    // sum_h c_{h,k} sum_i s_k[i] sum_m R[m,i] wt_h[m]
+    if (species) {
+        double part[2 * KMAX];
+#pragma unroll
+        for (int k = 0; k < 2 * KMAX; ++k) part[k] = 0.0;
+        for (int m = tid; m < M; m += MID_THREADS) {
+            const double a0 = (double)wt[m], a1 = H == 2 ? (double)wt[M + m] : 0.0;
+            const TV* vr = v + (size_t)m * US;
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k)
+                if (k < K) {
+                    const double x = (double)vr[k];
+                    part[k] += a0 * x;
+                    part[KMAX + k] += a1 * x;
+                }
+        }
+        block_sum<2 * KMAX>(part, red, s_gr);
+    } else if (tid < 2 * KMAX) {
+        s_gr[tid] = 0.0;
+    }
+    __syncthreads();
+    double* coef = w.coef + (size_t)item * 3 * KMAX;
+    if (tid < K) {
+        const int k = tid;
+        const double t = T.tag ? T.tag[k] : 0.0, csub = T.tag ? 1.0 - t : 1.0;
+        gmid[k] = csub * s_gr[k] + (H == 2 ? t * s_gr[KMAX + k] : 0.0) + (mv ? s_beta[k] * csub * s_SA[k] : 0.0);
+        coef[k] = s_rs[k];
+        coef[KMAX + k] = s_rt[k];
+        coef[2 * KMAX + k] = mv ? s_beta[k] * s_rs[k] : 0.0;
+    }
+    if (tid >= K && tid < KMAX) {
+        coef[tid] = 0.0;
+        coef[KMAX + tid] = 0.0;
+        coef[2 * KMAX + tid] = 0.0;
+    }
+    if (tid == 0) {
+        double ge = s_misc[2];
+        if (mv)
+            for (int k = 0; k < K; ++k) ge += s_beta[k] * s_rs[k] * s_SA[KMAX + k];
+        double gs = 0.0;
+        for (int b = 0; b < nrad; ++b) gs += s_wr[b] * s_misc[1] * s_dpext[b];
+        for (int j = K; j < K + 5; ++j) gmid[j] = 0.0;
+        gmid[K + 5] = ge;
+        gmid[K + 6] = gs;
+        for (int j = K + 7; j < PMAX; ++j) gmid[j] = 0.0;
+    }
+}
+
+cudaError_t launch_mid(const Work& w, int n, int Mmax, int nwmax, int Lmax, int want_grad, int want_mu,
+                       cudaStream_t s) {
+    const bool f32 = w.precision != BX_FP64;
+    const size_t tv = f32 ? sizeof(float) : sizeof(double);
+    const size_t smem = (size_t)(2 * Mmax + 2 * nwmax) * sizeof(double) +
+                        (size_t)(2 * Mmax + 4 * nwmax + Lmax) * tv + 64;
+    cudaError_t e;
+    if (f32) {
+        e = cudaFuncSetAttribute(k_mid<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_mid<float><<<n, MID_THREADS, smem, s>>>(w, want_grad, want_mu);
+    } else {
+        e = cudaFuncSetAttribute(k_mid<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_mid<double><<<n, MID_THREADS, smem, s>>>(w, want_grad, want_mu);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace bx

@@ -1,0 +1,35 @@
+// bx_model.h -- host-side model object shared by the C-ABI translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "bx_internal.cuh"
+
+struct FitState;
+
+struct bx_model {
+    int n_toys = 0, precision = BX_FP32, cap = 1;
+    double band = 8.0;
+    unsigned long long watchdog_ns = 2000000000ull;
+    cudaStream_t stream = nullptr;
+    std::vector<bx::Toy> toys_h;
+    std::vector<void*> allocs;   // device allocations owned by the model
+    std::vector<void*> pinned;   // pinned host allocations owned by the model
+    bx::Work w{};
+    int Kmax = 0, Nmax = 0, Mmax = 0, nwmax = 0, nbmax = 0, Lmax = 0, max_tiles = 0, max_cb = 0, P = 0;
+    int any_tag = 0, any_cols = 0;   // some toy has a tagged spectrum / an Eq. 4 term
+    std::vector<int> toy_tmp, toy_cached;
+    double* theta_d = nullptr;
+    double* nll_d = nullptr;
+    double* grad_d = nullptr;
+    FitState* fit = nullptr;
+};
+
+int bx_set_error(int code, const char* fmt, ...);
+int bx_set_items(bx_model* m, int n, const int* toy_idx);
+int bx_enqueue_eval(bx_model* m, int n, const double* theta_dev, int tstride, int want_grad, int want_mu,
+                    double* nll_dev, double* grad_dev);
+int bx_take_device_error(bx_model* m);
+void bx_fit_free(bx_model* m);

@@ -1,0 +1,142 @@
+// bx_resp.cuh -- FP32 generation of the response entries (Eq. 1) without hardware
+// approximations: every operation is a round-to-nearest FMA/add/multiply, so the
+// rounding errors carry no systematic sign.
+//
+// Bin mass of the Gaussian of column i over output bin m, by 3-point Gauss-Legendre
+// quadrature of its density (nodes c, c -+ (h/2) sqrt(3/5), weights 8/9, 5/9, 5/9),
+// in the scaled variable t = z * S_EX2 so that exp(-z^2/2) = 2^(-t^2):
+//   p0  = 2^(-t0^2)                               centre node
+//   p-+ = p0 * 2^(-kk^2) * 2^(+-2 kk t0)          outer nodes, kk = sqrt(3/5)/2 * hs
+//   p- + p+ = p0 * Ck2 * cosh(z),  Ck2 = 2 * 2^(-kk^2),  z = 2 ln2 kk t0 = kap t0
+//   p- - p+ = p0 * Ck2 * sinh(z)
+//   R   = A * (8 p0 + 5 (p- + p+)),  A = (h/2) norm / (9 sqrt(2 pi))   (weights as exact integers)
+// The centre-node exponent t0^2 is formed in double-float (error-free transformations by FMA)
+// from double-float column parameters: in plain FP32 its rounding alone gives a relative
+// error q ln2 2^-24 in 2^(-q), ~3e-7 per entry.
+// 2^x (x <= 0) uses Cody-Waite reduction x = n + f, |f| <= 1/2, a degree-7 polynomial for
+// 2^f (coefficients fitted by weighted least squares on [-1/2, 1/2], approximation error
+// 4e-11) and the exponent field for 2^n.  cosh and sinh use their Taylor series through
+// z^10 / z^11 (truncation < 2e-9 for |z| <= 1); larger |z| (only for very narrow
+// resolutions) evaluates the two outer nodes directly with the same exp2.
+#pragma once
+
+#include "bx_internal.cuh"
+
+namespace bx {
+
+#ifdef __CUDACC__
+
+// 2^(xh + xl) for xh <= 0 (double-float argument, |xl| << 1).
+__device__ __forceinline__ float exp2_neg(float xh, float xl = 0.0f) {
+    xh = fmaxf(xh, -127.0f);
+    const float t = __fadd_rn(xh, 12582912.0f);   // 1.5 * 2^23: n = rint(xh) lands in the low bits
+    const float n = __fsub_rn(t, 12582912.0f);
+    const float f = __fadd_rn(__fsub_rn(xh, n), xl);   // |f| <= 1/2 + |xl|
+    float p = 1.520192109e-05f;
+    p = fmaf(p, f, 1.546929125e-04f);
+    p = fmaf(p, f, 1.333392225e-03f);
+    p = fmaf(p, f, 9.618027136e-03f);
+    p = fmaf(p, f, 5.550410226e-02f);
+    p = fmaf(p, f, 2.402265072e-01f);
+    p = fmaf(p, f, 6.931471825e-01f);
+    p = fmaf(p, f, 1.0f);
+    // 2^n from the exponent field: bits(t) = 0x4B400000 + n; n = -127 gives +0
+    const int e = (__float_as_int(t) - 0x4B400000 + 127) << 23;
+    return __fmul_rn(p, __int_as_float(e));
+}
+
+// Scaled centre-node position t0 = (m + 1/2 - mu/w) * hs of output bin m as a double-float
+// (th, tl): k = m - floor(mu/w) is an exact integer, hs = hs_hi + hs_lo and
+// c = (1/2 - frac(mu/w)) hs = c_hi + c_lo come from FP64; products and sums are error-free
+// transformations (TwoProduct by FMA, TwoSum), so th + tl carries ~2^-40 relative error.
+__device__ __forceinline__ void centre_df(float mf, const float4& cf, float c_lo, float& th, float& tl) {
+    const float k = __fsub_rn(mf, cf.x);
+    const float p = __fmul_rn(k, cf.z);
+    float e = fmaf(k, cf.z, -p);
+    e = fmaf(k, cf.w, e);
+    const float s = __fadd_rn(p, cf.y);
+    const float bb = __fsub_rn(s, p);
+    const float err = __fadd_rn(__fsub_rn(p, __fsub_rn(s, bb)), __fsub_rn(cf.y, bb));
+    th = s;
+    tl = __fadd_rn(__fadd_rn(err, e), c_lo);
+}
+
+// p0 = 2^(-t0^2) with the square and the reduction carried in double-float.
+__device__ __forceinline__ float centre_node(float th, float tl) {
+    const float qh = __fmul_rn(th, th);
+    const float qe = fmaf(th, th, -qh);
+    const float ql = fmaf(__fadd_rn(th, th), tl, qe);
+    return exp2_neg(-qh, -ql);
+}
+
+__device__ __forceinline__ float cosh_small(float s) {   // s = z^2
+    float c = 2.755731922e-07f;                          // 1/10!
+    c = fmaf(c, s, 2.480158730e-05f);                    // 1/8!
+    c = fmaf(c, s, 1.388888889e-03f);                    // 1/6!
+    c = fmaf(c, s, 4.166666667e-02f);                    // 1/4!
+    c = fmaf(c, s, 0.5f);
+    return fmaf(c, s, 1.0f);
+}
+
+__device__ __forceinline__ float sinh_small(float z, float s) {
+    float c = 2.505210839e-08f;                          // 1/11!
+    c = fmaf(c, s, 2.755731922e-06f);                    // 1/9!
+    c = fmaf(c, s, 1.984126984e-04f);                    // 1/7!
+    c = fmaf(c, s, 8.333333333e-03f);                    // 1/5!
+    c = fmaf(c, s, 1.666666667e-01f);                    // 1/3!
+    return z * fmaf(c, s, 1.0f);
+}
+
+// Outer-node sum S+ = p- + p+ and difference S- = p- - p+ (p-+ = 2^(-(t0 -+ kk)^2)).
+// Small |z|: from p0 and the series; otherwise (very narrow resolution only) directly.
+static __device__ __noinline__ void outer_direct(float t0, float kk, float& Sp, float& Sm) {
+    const float a = t0 - kk, b = t0 + kk;
+    const float pm = exp2_neg(-(a * a)), pp = exp2_neg(-(b * b));
+    Sp = pm + pp;
+    Sm = pm - pp;
+}
+
+constexpr float INV_2LN2 = 0.72134752044448170f;   // kk = kap / (2 ln 2)
+
+// Response entry of output bin `mf` (row index as float) and one column.
+// cf = (floor(mu/w), c_hi, hs_hi, hs_lo); cg = (kap, Ck2, c_lo, A / 9).
+__device__ __forceinline__ float resp_exact32(float mf, const float4& cf, const ColG& cg) {
+    float th, tl;
+    centre_df(mf, cf, cg.c_lo, th, tl);
+    const float p0 = centre_node(th, tl);
+    const float z = cg.kap * th;
+    float Sp;
+    if (fabsf(z) <= 1.0f) {
+        Sp = p0 * cg.Ck2 * cosh_small(z * z);
+    } else {
+        float Sm;
+        outer_direct(th, cg.kap * INV_2LN2, Sp, Sm);
+    }
+    return cg.A * fmaf(GL_W_OUT, Sp, GL_W_MID * p0);
+}
+
+// The three node sums of the adjoint: P0 = sum w_j p_j, P1 = sum w_j t_j p_j,
+// P2 = sum w_j t_j^2 p_j (t in the scaled variable, weights 8, 5, 5), same nodes as the forward.
+__device__ __forceinline__ void resp_adjoint32(float mf, const float4& cf, const ColG& cg, float& P0, float& P1,
+                                               float& P2) {
+    float t0, tl;
+    centre_df(mf, cf, cg.c_lo, t0, tl);
+    const float q0 = t0 * t0;
+    const float p0 = centre_node(t0, tl);
+    const float z = cg.kap * t0, kk = cg.kap * INV_2LN2;
+    float Sp, Sm;
+    if (fabsf(z) <= 1.0f) {
+        const float s = z * z, f = p0 * cg.Ck2;
+        Sp = f * cosh_small(s);
+        Sm = f * sinh_small(z, s);
+    } else {
+        outer_direct(t0, kk, Sp, Sm);
+    }
+    P0 = fmaf(GL_W_OUT, Sp, GL_W_MID * p0);
+    P1 = fmaf(GL_W_OUT, fmaf(t0, Sp, -kk * Sm), GL_W_MID * (t0 * p0));
+    P2 = fmaf(GL_W_OUT, fmaf(fmaf(kk, kk, q0), Sp, -2.0f * t0 * kk * Sm), GL_W_MID * (q0 * p0));
+}
+
+#endif  // __CUDACC__
+
+}  // namespace bx

@@ -1,0 +1,95 @@
+"""The C-ABI library builds for sm_103a, loads, exports every entry point of include/bx.h,
+and rejects invalid model descriptions on the host (no GPU needed)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1805_11125_gb300 import bx, build, inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    txt = open(os.path.join(ROOT, "include", "bx.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(bx_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_library_exports_every_header_symbol():
+    L = bx.lib()
+    names = header_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == {s[0] for s in bx.SIGNATURES}
+
+
+def test_build_is_sm103a_only():
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert os.path.exists(build.LIB)
+
+
+def test_status_strings():
+    L = bx.lib()
+    assert L.bx_status_string(0) == b"ok"
+    assert b"time" in L.bx_status_string(-5)
+
+
+def _desc_for(spec):
+    m = bx.Model.__new__(bx.Model)   # reuse the marshalling without creating
+    return m
+
+
+@pytest.mark.parametrize("mutate,msg", [
+    (lambda s: setattr(s, "n_species_override", 0), "n_species"),
+])
+def test_invalid_description_rejected_on_host(mutate, msg):
+    s = I.config("small_plain")
+    s = s.with_counts(np.ones(s.n_bins_total))
+    L = bx.lib()
+    d = bx.bx_model_desc()
+    shapes = np.ascontiguousarray(s.shapes)
+    d.n_grid, d.e_max, d.n_species = s.n_grid, s.e_max, 0      # K = 0 is invalid
+    d.shapes = shapes.ctypes.data
+    h = C.c_void_p()
+    st = L.bx_model_create(C.byref(d), 1, None, None, C.byref(h))
+    assert st == bx.BX_EINVAL
+    assert msg in L.bx_last_error().decode()
+
+
+def test_negative_counts_and_bad_window_rejected():
+    s = I.config("small_plain")
+    L = bx.lib()
+    keep = []
+
+    def make(**over):
+        d = bx.bx_model_desc()
+        arrs = dict(shapes=np.ascontiguousarray(s.shapes), stop=np.ascontiguousarray(s.stop_pow),
+                    g=np.ascontiguousarray(s.pileup), cnt=np.ones(s.n_window))
+        arrs.update(over.pop("arrays", {}))
+        keep.append(arrs)
+        d.n_grid, d.e_max, d.n_species = s.n_grid, s.e_max, s.K
+        d.shapes, d.stop_pow = arrs["shapes"].ctypes.data, arrs["stop"].ctypes.data
+        d.n_pileup, d.pileup = s.L, arrs["g"].ctypes.data
+        d.width, d.m_lo, d.m_hi = s.width, s.m_lo, s.m_hi
+        d.counts_sub = arrs["cnt"].ctypes.data
+        for k, v in over.items():
+            setattr(d, k, v)
+        return d
+
+    h = C.c_void_p()
+    bad = np.ones(s.n_window); bad[3] = -1.0
+    for d, frag in [(make(arrays=dict(cnt=bad)), "counts_sub"), (make(m_lo=10, m_hi=5), "window"),
+                    (make(width=0.0), "width"), (make(n_pileup=0), "n_pileup"),
+                    (make(arrays=dict(stop=np.zeros(s.n_grid))), "stop_pow")]:
+        st = L.bx_model_create(C.byref(d), 1, None, None, C.byref(h))
+        assert st == bx.BX_EINVAL, frag
+        assert frag in L.bx_last_error().decode()
+    # NULL output pointer
+    assert L.bx_model_create(C.byref(make()), 1, None, None, None) == bx.BX_EINVAL
+    # bad options
+    o = bx.bx_options(7, 1, 0.0, 0.0)
+    assert L.bx_model_create(C.byref(make()), 1, C.byref(o), None, C.byref(h)) == bx.BX_EINVAL
