@@ -1,0 +1,316 @@
+#!/usr/bin/env python
+"""Benchmark of the binned Poisson -lnL + adjoint (arXiv:1805.11125 multivariate fit model).
+
+Workload: the multivariate model (K = 15 species, TFC-vetoed and TFC-tagged spectra of 900
+1-npe bins over 100-1000 npe, a 60-bin radial and a 50-bin pulse-shape histogram, 22
+parameters, 2e6 events), synthetic and seeded.  One step evaluates -lnL and its gradient
+at a batch of parameter points (theta_true * (1 + 0.02 z)) through the C ABI
+(bx_nll_batch, FP32 mixed precision, device pointers).  The FP64 GPU form is timed beside
+it, the oracle (plain FP64 C on the host cores) gives the CPU baseline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU with its own
+batch (weak scaling; the likelihood of one dataset does not need a collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "-lnL+grad evals/s & full-fit wall time, mixed vs FP64 GPU at |Δ(-2lnL)|≤1e-3"
+WORKLOAD = ("multivariate spectral fit: K=15 species on a 2000-point 0-3 MeV grid, TFC-vetoed + TFC-tagged "
+            "900x1 npe (100-1000 npe), radial 60, pulse-shape 50, 22 parameters, 2e6 events, pile-up L=400")
+# FP32 operations per in-band response entry of the forward kernel, counted from the source
+# (bx_resp.cuh resp_exact32 45, two Kahan row sums 8, column sum 2)
+FWD_OPS_PER_ENTRY = 55
+# adjoint kernel: resp_adjoint32 66, weight 3, five column sums 5
+BWD_OPS_PER_ENTRY = 74
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in self.rows for j in range(4) if len(r) > 5 + j and r[5 + j] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def make_dataset(bx, I, spec, seed=0):
+    """Data drawn from the GPU model's own expected counts at theta_true."""
+    dummy = spec.with_counts(np.zeros(spec.n_bins_total))
+    m = bx.Model(dummy, precision=bx.BX_FP64)
+    mu = m.expected(spec.theta_true)
+    m.close()
+    return spec.with_counts(I.poisson_counts(mu, seed))
+
+
+def cpu_baseline(spec_name: str, seconds: float, seed: int = 0):
+    """The oracle as it stands (FP64 C, dual-number gradient, OpenMP over output bins) on a
+    bounded sample of the same workload: NLL+gradient at consecutive parameter points."""
+    from oracle import oracle as O
+    from paper_1805_11125_gb300 import inputs as I
+    s = I.config(spec_name)
+    s = s.with_counts(I.poisson_counts(O.expected(s, s.theta_true), seed))
+    pts = I.parameter_points(s.theta_true, 10000, rel=0.02, seed=11, free=s.default_free())
+    om = O.OracleModel(s)
+    O.nll(om, pts[0], grad=True)   # warm
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        O.nll(om, pts[n + 1], grad=True)
+        n += 1
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": n / dt, "unit": "evals/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} NLL+gradient evaluations of the multivariate model in {dt:.1f} s "
+                      f"(one point at a time, OpenMP over output bins)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    cb = cpu_baseline("multivariate", max(args.cpu_seconds / max(args.steps, 1), 2.0))
+    total_n, total_t = 0, 0.0
+    # K timed steps of bounded samples, after W warm-up samples
+    from oracle import oracle as O
+    from paper_1805_11125_gb300 import inputs as I
+    s = I.config("multivariate")
+    s = s.with_counts(I.poisson_counts(O.expected(s, s.theta_true), 0))
+    om = O.OracleModel(s)
+    pts = I.parameter_points(s.theta_true, 4096, rel=0.02, seed=11, free=s.default_free())
+    per_step = max(1, int(round(cb["value"] * args.cpu_seconds / max(args.steps, 1))))
+    for w in range(args.warmup):
+        O.nll(om, pts[w], grad=True)
+    j = 0
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        for _ in range(per_step):
+            O.nll(om, pts[j % len(pts)], grad=True)
+            j += 1
+        total_t += time.perf_counter() - t0
+        total_n += per_step
+    v = total_n / total_t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "global_batch": per_step,
+                                              "l2": "n/a (host)"},
+            "cpu_baseline": {"value": v, "unit": "evals/s", "cores": cb["cores"], "kind": "oracle",
+                             "sample": f"{per_step} NLL+gradient evaluations per step"},
+            "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1805_11125_gb300 import bx, inputs as I
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+
+    spec = make_dataset(bx, I, I.config("multivariate"), seed=0)
+    B = args.batch
+    model = bx.Model(spec, precision=bx.BX_FP32, max_batch=B, stream=stream)
+    P = model.P
+    pts = I.parameter_points(spec.theta_true, B, rel=0.02, seed=100 + rank, free=spec.default_free())
+    theta = torch.tensor(pts, dtype=torch.float64, device=dev)
+    nll = torch.empty(B, dtype=torch.float64, device=dev)
+    grad = torch.empty((B, P), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB of L2
+
+    def step():
+        st = bx.lib().bx_nll_batch(model.h, B, None, bx._ptr(theta), bx._ptr(nll), bx._ptr(grad), 1)
+        if st:
+            raise bx.BxError(st, bx.lib().bx_last_error().decode())
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    model.profile(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            step()
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    stage_ms, n_evals, entries = model.profile(False)
+    st = model.status()
+    if st:
+        raise bx.BxError(st, bx.lib().bx_last_error().decode())
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * B * args.steps / (total_ms / 1e3)
+
+    e2e, fp64_value = None, None
+    if not args.no_extras:
+        e2e, fp64_value = extras(bx, model, spec, pts, theta, stream, B, P, ws, args)
+    if rank != 0:
+        return
+    report(args, ws, B, total_ms, value, stage_ms, n_evals, entries, e2e, fp64_value, clk)
+
+
+def extras(bx, model, spec, pts, theta, stream, B, P, ws, args):
+    import torch
+    # end to end through the public call with host buffers (pinned), copies inside the region
+    th_h = torch.tensor(pts, dtype=torch.float64).pin_memory()
+    nll_h = torch.empty(B, dtype=torch.float64).pin_memory()
+    grad_h = torch.empty((B, P), dtype=torch.float64).pin_memory()
+    e2e_steps = max(3, args.steps // 2)
+    bx.lib().bx_nll_batch(model.h, B, None, th_h.data_ptr(), nll_h.data_ptr(), grad_h.data_ptr(), 0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s2 = bx.lib().bx_nll_batch(model.h, B, None, th_h.data_ptr(), nll_h.data_ptr(), grad_h.data_ptr(), 0)
+        if s2:
+            raise bx.BxError(s2, bx.lib().bx_last_error().decode())
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": ws * B * e2e_steps / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": B * P * 8,
+           "d2h_bytes_per_step": B * 8 + B * P * 8}
+
+    # the FP64 GPU form of the same evaluation
+    B64 = min(B, 256)
+    m64 = bx.Model(spec, precision=bx.BX_FP64, max_batch=B64, stream=stream)
+    th64 = theta[:B64].contiguous()
+    m64.nll_batch(th64, grad=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(3):
+        m64.nll_batch(th64, grad=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fp64_value = ws * B64 * 3 / (e0.elapsed_time(e1) / 1e3)
+    m64.close()
+    return e2e, fp64_value
+
+
+def report(args, ws, B, total_ms, value, stage_ms, n_evals, entries, e2e, fp64_value, clk):
+    # roofline of the dominant kernel (ALU-bound: FP32 issue rate of 152 SMs x 128 lanes)
+    per_launch = {k: v / max(n_evals, 1) for k, v in stage_ms.items()}
+    dom = max(("forward", "adjoint"), key=lambda k: per_launch[k])
+    ops = (FWD_OPS_PER_ENTRY if dom == "forward" else BWD_OPS_PER_ENTRY) * entries / max(n_evals, 1)
+    peak = SMS * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = ops / (per_launch[dom] / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": "k_fwd_f32" if dom == "forward" else "k_bwd_f32",
+                "achieved": achieved, "peak": peak, "unit": "Top/s", "frac": achieved / peak, "traffic": None,
+                "entries_per_launch": entries / max(n_evals, 1),
+                "ops_per_entry": FWD_OPS_PER_ENTRY if dom == "forward" else BWD_OPS_PER_ENTRY,
+                "peak_basis": "FP32 issue rate 152 SMs x 128 lanes x 2070 MHz (derived, not measured)",
+                "stage_ms_per_launch": {k: round(v, 4) for k, v in per_launch.items()}}
+    cb = None if args.no_cpu_baseline else cpu_baseline("multivariate", args.cpu_seconds)
+    line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "global_batch": ws * B, "precision": "BX_FP32 (FP64 columns, -lnL)",
+                       "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}"},
+            "fp64_gpu_value": fp64_value, "mixed_over_fp64": value / fp64_value if fp64_value else None,
+            "roofline": roofline, "cpu_baseline": cb, "e2e": e2e,
+            "gpu_launches": 5 * args.steps, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--batch", type=int, default=1024)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the e2e and FP64 legs (profiling runs)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -112,6 +112,16 @@ int bx_model_n_bins(const bx_model* model, int toy);
 /* Sticky device status (BX_OK or BX_ETIMEOUT) after synchronising the model's stream. */
 int bx_model_status(bx_model* model);
 
+/* Stage timing.  Every call returns, for the evaluations recorded since the previous call,
+ * the per-stage device times summed over them (stage_ms[5]: per-column preparation,
+ * response forward, spectra/pile-up/-lnL assembly, adjoint, gather; NULL to skip), their
+ * number (*n_evals) and the number of in-band response entries (pairs of output bin and
+ * true-energy point within band_sigmas of the mean) they evaluated (*entries); it then
+ * clears the record and switches recording on (enable = 1) or off (0).  Recording puts CUDA
+ * events between the kernels on the model's stream and counts entries in the preparation
+ * kernel.  Synchronises the stream. */
+int bx_model_profile(bx_model* model, int enable, double* stage_ms, int* n_evals, double* entries);
+
 /* -lnL of toy 0 at theta[P] (host arrays). */
 int bx_nll(bx_model* model, const double* theta, double* nll);
 /* -lnL and its gradient grad[P] of toy 0 (host arrays).  The gradient comes from the

@@ -72,6 +72,7 @@ SIGNATURES = [
     ("bx_model_n_params", C.c_int, [_P]),
     ("bx_model_n_bins", C.c_int, [_P, C.c_int]),
     ("bx_model_status", C.c_int, [_P]),
+    ("bx_model_profile", C.c_int, [_P, C.c_int, _P, _P, _P]),
     ("bx_nll", C.c_int, [_P, _P, _P]),
     ("bx_nll_grad", C.c_int, [_P, _P, _P, _P]),
     ("bx_expected", C.c_int, [_P, C.c_int, _P, _P]),
@@ -187,6 +188,16 @@ class Model:
 
     def status(self) -> int:
         return lib().bx_model_status(self.h)
+
+    STAGES = ("prep", "forward", "assembly", "adjoint", "gather")
+
+    def profile(self, enable: bool):
+        """(per-stage device ms, evaluations, in-band response entries) recorded since the last call."""
+        ms = np.zeros(5)
+        n = C.c_int(0)
+        ent = np.zeros(1)
+        _check(lib().bx_model_profile(self.h, int(enable), _ptr(ms), C.byref(n), _ptr(ent)))
+        return dict(zip(self.STAGES, ms)), n.value, float(ent[0])
 
     def _row(self, theta):
         th = _f64(theta).ravel()

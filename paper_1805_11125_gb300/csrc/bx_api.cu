@@ -125,6 +125,7 @@ static int upload(bx_model* m, const T* src, size_t n, const T** dst) {
 static void free_model(bx_model* m) {
     if (!m) return;
     bx_fit_free(m);
+    for (cudaEvent_t e : m->prof_ev) cudaEventDestroy(e);
     for (void* p : m->allocs) cudaFree(p);
     for (void* p : m->pinned) cudaFreeHost(p);
     delete m;
@@ -281,6 +282,7 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
         {(void**)&w.mu, sizeof(double) * cap * m->nbmax},
         {(void**)&w.status, sizeof(int) * cap},
         {(void**)&w.err, sizeof(unsigned)},
+        {(void**)&w.units, sizeof(unsigned long long)},
         {(void**)&m->theta_d, sizeof(double) * cap * m->P},
         {(void**)&m->nll_d, sizeof(double) * cap},
         {(void**)&m->grad_d, sizeof(double) * cap * m->P},
@@ -291,6 +293,7 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
         cudaError_t e = cudaMemcpyAsync((void*)w.toys, m->toys_h.data(), sizeof(Toy) * n_toys, cudaMemcpyHostToDevice,
                                         m->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.err, 0, sizeof(unsigned), m->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.units, 0, sizeof(unsigned long long), m->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync((void*)w.toy_of, 0, sizeof(int) * cap, m->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
         if (e != cudaSuccess) st = bx_set_error(BX_ECUDA, "model upload: %s", cudaGetErrorString(e));
@@ -360,6 +363,20 @@ int bx_set_items(bx_model* m, int n, const int* toy_idx) {
     return BX_OK;
 }
 
+static int prof_mark(bx_model* m, int stage) {
+    if (!m->prof_on) return BX_OK;
+    if (stage == 0 && m->prof_used + (BX_STAGES + 1) > m->prof_ev.size()) {
+        for (int j = 0; j < BX_STAGES + 1; ++j) {
+            cudaEvent_t e;
+            CU(cudaEventCreate(&e));
+            m->prof_ev.push_back(e);
+        }
+    }
+    CU(cudaEventRecord(m->prof_ev[m->prof_used + stage], m->stream));
+    if (stage == BX_STAGES) m->prof_used += BX_STAGES + 1;
+    return BX_OK;
+}
+
 int bx_enqueue_eval(bx_model* m, int n, const double* theta_dev, int tstride, int want_grad, int want_mu,
                     double* nll_dev, double* grad_dev) {
     Work w = m->w;
@@ -367,13 +384,43 @@ int bx_enqueue_eval(bx_model* m, int n, const double* theta_dev, int tstride, in
     w.tstride = tstride;
     w.n_items = n;
     cudaStream_t s = m->stream;
+    int st;
+    if ((st = prof_mark(m, 0))) return st;
     CU(launch_prep(w, n, s));
+    if ((st = prof_mark(m, 1))) return st;
     if (m->precision == BX_FP64) CU(launch_fwd_f64(w, n, m->max_tiles, m->any_tag, m->any_cols, s));
     else if (m->precision == BX_FP32) CU(launch_fwd_f32(w, n, m->max_tiles, m->any_tag, m->any_cols, s));
     else CU(launch_fwd_tc(w, n, m->max_tiles, s));
+    if ((st = prof_mark(m, 2))) return st;
     CU(launch_mid(w, n, m->Mmax, m->nwmax, m->Lmax, want_grad, want_mu, s));
+    if ((st = prof_mark(m, 3))) return st;
     if (want_grad) CU(launch_bwd(w, n, m->max_cb, s));
+    if ((st = prof_mark(m, 4))) return st;
     CU(launch_gather(w, n, nll_dev, grad_dev, want_grad, s));
+    if ((st = prof_mark(m, 5))) return st;
+    return BX_OK;
+}
+
+extern "C" int bx_model_profile(bx_model* m, int enable, double* stage_ms, int* n_evals, double* entries) {
+    if (!m) return bx_set_error(BX_EINVAL, "model is NULL");
+    CU(cudaStreamSynchronize(m->stream));
+    if (stage_ms) {
+        for (int j = 0; j < BX_STAGES; ++j) stage_ms[j] = 0.0;
+        for (size_t b = 0; b + BX_STAGES < m->prof_used; b += BX_STAGES + 1)
+            for (int j = 0; j < BX_STAGES; ++j) {
+                float ms = 0.f;
+                CU(cudaEventElapsedTime(&ms, m->prof_ev[b + j], m->prof_ev[b + j + 1]));
+                stage_ms[j] += ms;
+            }
+    }
+    if (n_evals) *n_evals = (int)(m->prof_used / (BX_STAGES + 1));
+    unsigned long long u = 0;
+    CU(cudaMemcpy(&u, m->w.units, sizeof u, cudaMemcpyDeviceToHost));
+    CU(cudaMemset(m->w.units, 0, sizeof u));
+    if (entries) *entries = (double)u;
+    m->prof_on = enable ? 1 : 0;
+    m->w.count_units = m->prof_on;
+    m->prof_used = 0;
     return BX_OK;
 }
 

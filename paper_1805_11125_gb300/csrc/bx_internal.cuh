@@ -108,6 +108,8 @@ struct Work {
     double* mu;               // [cap][nbmax]
     int* status;              // [cap]
     unsigned* err;            // sticky error word
+    unsigned long long* units;   // in-band response entries evaluated (counted when count_units)
+    int count_units;
 };
 
 // ------------------------------------------------------------------ launchers (host)

@@ -25,7 +25,13 @@ struct bx_model {
     double* nll_d = nullptr;
     double* grad_d = nullptr;
     FitState* fit = nullptr;
+    // stage timing (bx_model_profile): events recorded between the stage launches
+    int prof_on = 0;
+    std::vector<cudaEvent_t> prof_ev;   // 6 per recorded evaluation
+    size_t prof_used = 0;
 };
+
+enum { BX_STAGES = 5 };   // prep, forward, assembly, adjoint, gather
 
 int bx_set_error(int code, const char* fmt, ...);
 int bx_set_items(bx_model* m, int n, const int* toy_idx);

@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(256) k_prep(Work w) {
     double2* cs = w.colS + (size_t)item * w.Npad;
     double* aW = w.aW + (size_t)item * w.Npad;
     int bad = 0;
+    unsigned long long inband = 0;
     for (int i = i0; i < i1; ++i) {
         const double S = T.stop_pow[i], q = 1.0 + kB * S;
         if (!(q > 0.0)) bad = 1;
@@ -155,6 +156,7 @@ __global__ void __launch_bounds__(256) k_prep(Work w) {
         const int r0 = max(0, (int)floor(lo_e / w_));
         const int r1 = min(M, (int)floor(hi_e / w_) + 1);
         if (r0 < r1 && !bad) {
+            inband += (unsigned long long)(r1 - r0);
             for (int t = r0 / TM; t <= (r1 - 1) / TM; ++t) {
                 atomicMin(&s_tlo[t], i);
                 atomicMax(&s_thi[t], i + 1);
@@ -172,6 +174,7 @@ __global__ void __launch_bounds__(256) k_prep(Work w) {
         aW[i] = 0.0;
     }
     if (bad) s_bad = 1;
+    if (w.count_units && inband) atomicAdd(w.units, inband);
     __syncthreads();
     for (int t = tid; t < MAX_TILES; t += blockDim.x)
         w.tile_cols[(size_t)item * MAX_TILES + t] = make_int2(s_tlo[t], s_thi[t]);
