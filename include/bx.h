@@ -171,6 +171,26 @@ int bx_selftest_tensor_core(double* max_rel_err);
  * wait ran out as designed (the CUDA context stays usable), BX_ECUDA on a CUDA error. */
 int bx_selftest_watchdog(double budget_s);
 
+/* Allocation-free forward stage, for callers that cannot call cudaMalloc: a host process
+ * whose device memory belongs to another allocator or a budget fixed at start-up, a loop
+ * where cudaMalloc's implicit synchronisation would stall other streams, or a host that
+ * forbids allocation after initialisation.  (The paper has no counterpart; this is a
+ * deployment convenience.)
+ * Computes the Eq. 3 energy spectra before pile-up of one dataset at one parameter point,
+ *   lambda_h[m] = sum_i R[m,i] sum_k r_k c_{h,k} s_k[i],  m in [0, m_hi),
+ * with the same FP32 kernels as BX_FP32 (vetoed spectrum in lambda[0..m_hi), tagged in
+ * lambda[m_hi..2 m_hi) when tag_frac is given).  Every pointer is device memory owned by the
+ * caller: shapes [K][n_grid], stop_pow [n_grid], tag_frac [K] or NULL, theta [K + 7],
+ * lambda [m_hi] or [2][m_hi].  Limits of the fixed scratch: n_grid <= 4096, m_hi <= 4096,
+ * K <= 16 (BX_EINVAL beyond).  The work is enqueued on cuda_stream and the call returns.
+ * Its scratch is one 417 KiB static device array per device, whose address is looked up on
+ * the first call made on that device (make it before any stream capture); all calls share
+ * it, so calls that overlap on the GPU race.  Invalid response parameters (sigma^2 <= 0)
+ * leave lambda unwritten. */
+int bx_spectra_noalloc(int n_grid, double e_max, int n_species, const double* shapes,
+                       const double* stop_pow, const double* tag_frac, double width, int m_hi,
+                       const double* theta, double* lambda, void* cuda_stream);
+
 const char* bx_last_error(void);
 const char* bx_status_string(int status);
 

@@ -80,6 +80,7 @@ SIGNATURES = [
     ("bx_fit", C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P]),
     ("bx_selftest_tensor_core", C.c_int, [_P]),
     ("bx_selftest_watchdog", C.c_int, [C.c_double]),
+    ("bx_spectra_noalloc", C.c_int, [C.c_int, C.c_double, C.c_int, _P, _P, _P, C.c_double, C.c_int, _P, _P, _P]),
     ("bx_last_error", C.c_char_p, []),
     ("bx_status_string", C.c_char_p, [C.c_int]),
 ]
