@@ -137,27 +137,42 @@ int bx_expected(bx_model* model, int toy, const double* theta, double* mu);
 int bx_nll_batch(bx_model* model, int n, const int* toy_idx, const double* theta,
                  double* nll, double* grad, int device_ptrs);
 
-/* Batched quasi-Newton fits (one NLL+gradient evaluation per fit per iteration; the
- * paper minimises with TMinuit, Sec. 4). */
+/* Batched fits (the minimisation of Sec. 4; the paper uses TMinuit with numerical
+ * derivatives of -lnL).  Damped Newton iterations driven by the adjoint gradient: at every
+ * iterate the Hessian is re-measured by central differences of the gradient (all 2 n_free
+ * displaced points in one batched evaluation) and inverted with the smallest Levenberg
+ * damping that makes it positive definite; the line search evaluates 8 step lengths
+ * (1 .. 1/128) in one batched evaluation and takes the largest with sufficient decrease.
+ * Each fit therefore uses 8 + 2P evaluation slots: the model needs
+ * max_batch >= n (8 + 2P).  Converged when EDM = g^T V g / 2 < tol_edm with a fresh,
+ * at most lightly damped Hessian.  With BX_FP32 the gradient noise sets an EDM floor and
+ * the tolerance used is max(tol_edm, 1e-5) (distance to the optimum < ~0.005 sigma); an
+ * FP64 model started at the FP32 optimum refines it in a few iterations.  The iterations
+ * run as a captured CUDA graph. */
 typedef struct {
-    double tol_edm;             /* converged when EDM = g^T V g / 2 < tol_edm (0 -> 1e-7) */
-    int max_iter;               /* iteration budget per fit (0 -> 500) */
-    const unsigned char* free_mask; /* [P] 1 = free (NULL: all free except s_r when no radial term) */
-    const double* lo;           /* [P] lower bounds (NULL: rates >= 0, physical ranges) */
+    double tol_edm;             /* EDM tolerance (0 -> 1e-8) */
+    int max_iter;               /* evaluation budget per fit (0 -> 5000) */
+    const unsigned char* free_mask; /* [P] 1 = free (NULL: all free except s_r without radial term) */
+    const double* lo;           /* [P] lower bounds (NULL: rates >= 0, LY >= 50, a, b, kB >= 0,
+                                   c >= 1e-3, eps in [0, 1], s_r >= 0.05) */
     const double* hi;           /* [P] upper bounds (NULL: eps <= 1, otherwise none) */
-    int iters_per_launch;       /* iterations per captured CUDA graph launch (0 -> 16) */
+    int iters_per_launch;       /* evaluation rounds per graph replay (0 -> 4) */
 } bx_fit_opts;
+/* free_mask/lo/hi are given in the layout of a toy with max K species: slots 0..Kmax-1 are
+ * rates, Kmax..Kmax+6 the seven response/pile-up/radial parameters; a toy with K_t < Kmax
+ * species uses its first K_t rate slots. */
 
 typedef struct {
     double nll;                 /* -lnL at the returned theta */
     double edm;                 /* estimated distance to minimum */
-    int iters;                  /* accepted quasi-Newton steps */
+    int iters;                  /* accepted Newton steps */
     int n_evals;                /* NLL+gradient evaluations used */
     int status;                 /* BX_OK, BX_ENOTCONV or BX_EDOMAIN */
 } bx_fit_result;
 
 /* n fits; item j fits toy toy_idx[j] (host, NULL = toy 0) from theta0[j*P..].
- * theta_out[n*P], res[n] (host).  V (inverse Hessian estimate) stays on the device. */
+ * theta_out[n*P], res[n] (host).  Returns BX_OK when every fit converged, otherwise the
+ * first non-OK per-fit status (the results are filled in either case). */
 int bx_fit(bx_model* model, int n, const int* toy_idx, const double* theta0,
            const bx_fit_opts* opts, double* theta_out, bx_fit_result* res);
 

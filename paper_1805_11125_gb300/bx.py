@@ -249,6 +249,11 @@ class Model:
             _check(st)
         return (f, g) if grad else f
 
+    @property
+    def fit_slots(self) -> int:
+        """Evaluation slots one fit occupies (max_batch must be >= n_fits * fit_slots)."""
+        return 8 + 2 * self.P
+
     def fit(self, theta0, toy_idx=None, tol_edm: float = 0.0, max_iter: int = 0, free=None, lo=None, hi=None,
             iters_per_launch: int = 0):
         th0 = _f64(theta0)

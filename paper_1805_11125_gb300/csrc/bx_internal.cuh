@@ -110,7 +110,10 @@ struct Work {
     unsigned* err;            // sticky error word
     unsigned long long* units;   // in-band response entries evaluated (counted when count_units)
     int count_units;
+    const unsigned char* skip;   // [cap] or nullptr: items flagged 1 are not evaluated (-lnL = +inf)
 };
+
+constexpr int STATUS_SKIPPED = 1;   // item status of a skipped evaluation
 
 // ------------------------------------------------------------------ launchers (host)
 cudaError_t launch_setup_toy(const Toy& t, float* shapes32, float* S_tiles, float* g32, double* Gg,

@@ -383,14 +383,22 @@ cudaError_t launch_mid(const Work& w, int n, int Mmax, int nwmax, int Lmax, int 
     const size_t tv = f32 ? sizeof(float) : sizeof(double);
     const size_t smem = (size_t)(2 * Mmax + 2 * nwmax) * sizeof(double) +
                         (size_t)(2 * Mmax + 4 * nwmax + Lmax) * tv + 64;
+    // the attribute is set once per size (outside any stream capture that replays it)
+    static size_t set_f32 = 0, set_f64 = 0;
     cudaError_t e;
     if (f32) {
-        e = cudaFuncSetAttribute(k_mid<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
+        if (smem > set_f32) {
+            e = cudaFuncSetAttribute(k_mid<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            set_f32 = smem;
+        }
         k_mid<float><<<n, MID_THREADS, smem, s>>>(w, want_grad, want_mu);
     } else {
-        e = cudaFuncSetAttribute(k_mid<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
+        if (smem > set_f64) {
+            e = cudaFuncSetAttribute(k_mid<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            set_f64 = smem;
+        }
         k_mid<double><<<n, MID_THREADS, smem, s>>>(w, want_grad, want_mu);
     }
     return cudaGetLastError();

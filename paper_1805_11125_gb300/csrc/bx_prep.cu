@@ -80,6 +80,10 @@ __device__ void block_scan2(double& a, double& b, double* sh) {
 
 __global__ void __launch_bounds__(256) k_prep(Work w) {
     const int item = blockIdx.x, tid = threadIdx.x;
+    if (w.skip && w.skip[item]) {   // uniform for the block: no barrier is skipped unevenly
+        if (tid == 0) w.status[item] = STATUS_SKIPPED;
+        return;
+    }
     const Toy& T = w.toys[w.toy_of[item]];
     const int K = T.K, N = T.N, M = T.M;
     const double* th = w.theta + (size_t)item * w.tstride;
