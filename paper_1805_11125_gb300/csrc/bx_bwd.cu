@@ -16,7 +16,9 @@
 //              -(z_b phi(z_b) - z_a phi(z_a))/sigma, FP64 throughout.
 //   k_bwd_f32: the same integrals by the forward pass's 3-point Gauss-Legendre rule
 //              (integrands phi, t phi, (t^2 - 1) phi) in round-to-nearest FP32, column sums
-//              in FP32 per chunk of rows and FP64 across chunks, finalisation in FP64.
+//              in FP32 per chunk of rows and FP64 across chunks, the chain rule in FP64; the
+//              species sums and the rate products in FP32 (FP64 work is 64 FP32 operations'
+//              worth of issue on GB300 and would otherwise dominate the column epilogue).
 #include <math.h>
 
 #include "bx_internal.cuh"
@@ -162,14 +164,30 @@ __global__ void __launch_bounds__(BCOLS) k_bwd_f32(Work w) {
     const bool ok = i < T.N;
     const int2 rr = w.cb_rows[(size_t)item * MAX_CB + cb];
     const int r0 = max(rr.x, max(0, T.m_lo - T.L + 1)), r1 = min(rr.y, T.M);
-    double dSsub, dStag, dSA;
-    column_weights(w, T, item, i, ok, dSsub, dStag, dSA);
-    const float Ssub = (float)dSsub, Stag = (float)dStag, SA = (float)dSA;
+    __shared__ float sW[3][RCH];
+    __shared__ float s_coef[3][KMAX];   // vetoed, tagged and window coefficients per species
+    __shared__ float s_c[2][KMAX];      // c_{vetoed,k}, c_{tagged,k}
+    __shared__ double red[GPN * (BCOLS / 32)];
+    const double* coef = w.coef + (size_t)item * 3 * KMAX;
+    if (tid < 3 * KMAX) s_coef[tid / KMAX][tid % KMAX] = (float)coef[tid];
+    if (tid < KMAX) {
+        const double t = (T.tag && tid < T.K) ? T.tag[tid] : 0.0;
+        s_c[0][tid] = T.tag ? (float)(1.0 - t) : 1.f;
+        s_c[1][tid] = (float)t;
+    }
+    __syncthreads();
+    // dNLL/dR[m,i] = Ssub wt_sub[m] + Stag wt_tag[m] + SA G_W[m]: the species sums in FP32
+    float Ssub = 0.f, Stag = 0.f, SA = 0.f;
+    if (ok)
+        for (int k = 0; k < T.K; ++k) {
+            const float sk = T.shapes32[(size_t)k * T.N + i];
+            Ssub = fmaf(s_coef[0][k], sk, Ssub);
+            Stag = fmaf(s_coef[1][k], sk, Stag);
+            SA = fmaf(s_coef[2][k], sk, SA);
+        }
     const float4 cf = ok ? w.colf[(size_t)item * w.Npad + i] : make_float4(0.f, 0.f, 0.f, 0.f);
     const ColG cg = ok ? w.colg[(size_t)item * w.Npad + i] : ColG{0.f, 0.f, 0.f, 0.f};
     const float* rw = static_cast<const float*>(w.rowW) + (size_t)item * 3 * w.Mpad;
-    __shared__ float sW[3][RCH];
-    __shared__ double red[GPN * (BCOLS / 32)];
     double S0 = 0.0, S1 = 0.0, S2 = 0.0, Rs = 0.0, Rt = 0.0;
     for (int c0 = r0; c0 < r1; c0 += RCH) {
         const int nr = min(RCH, r1 - c0);
@@ -200,20 +218,57 @@ __global__ void __launch_bounds__(BCOLS) k_bwd_f32(Work w) {
         Rt += pt;
         __syncthreads();
     }
-    double g[GPN];
-#pragma unroll
-    for (int j = 0; j < GPN; ++j) g[j] = 0.0;
+    // chain rule through mu_i = LY Q_i(kB), sigma_i^2 = a mu_i + b mu_i^2 + c in FP64
+    double g5[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    float rho_s = 0.f, rho_t = 0.f;
     if (ok) {
         const Col64 cc = w.col64[(size_t)item * w.Npad + i];
-        const double A = 0.5 * (T.w / cc.sig) * cc.norm * INV_SQRT_2PI * GL_W_SCALE;   // R = A * P0
-        const double inv_sig = 1.0 / cc.sig;
+        const double2 q = w.colq[(size_t)item * w.Npad + i];
         const double* th = w.theta + (size_t)item * w.tstride;
+        const double LY = th[T.K], a = th[T.K + 1], b = th[T.K + 2];
+        const double isig = 1.0 / cc.sig;
+        const double A = (0.5 * INV_SQRT_2PI * GL_W_SCALE) * T.w * isig * cc.norm;   // R = A * P0
         // P1, P2 carry the node positions in units of z * S_EX2
-        chain_rule(cc, w.colq[(size_t)item * w.Npad + i], th, T.K, A * S0, A * inv_sig * (S1 / S_EX2),
-                   A * inv_sig * (S2 / (S_EX2 * S_EX2) - S0), g);
-        if (w.precision != BX_TF32X3) rate_part(T, i, A * Rs, A * Rt, g);
+        const double s0 = A * S0;
+        const double s1 = A * isig * (S1 * (1.0 / S_EX2));
+        const double s2 = A * isig * (S2 * (1.0 / (S_EX2 * S_EX2)) - S0);
+        const double dmu = s1 - cc.mills * isig * s0;
+        const double dsig = s2 + cc.mills * cc.mu * isig * isig * s0;
+        const double D = 0.5 * isig * dsig;
+        const double Gmu = dmu + D * (a + 2.0 * b * cc.mu);
+        g5[0] = Gmu * q.x;               // LY
+        g5[1] = D * cc.mu;               // a
+        g5[2] = D * cc.mu * cc.mu;       // b
+        g5[3] = D;                       // c
+        g5[4] = Gmu * LY * q.y;          // kB
+        rho_s = (float)(A * Rs);
+        rho_t = (float)(A * Rt);
     }
-    block_sum_gp(g, red, gp);
+    const int lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        const double v = warp_sum(g5[j]);
+        if (lane == 0) red[wid * GPN + j] = v;
+    }
+    // rate part sum_i s_k[i] (c_vetoed,k rho_vetoed[i] + c_tagged,k rho_tagged[i]) in FP32 within
+    // the warp (32 columns), FP64 from there on; the tensor-core path gets it from k_mid
+    const bool rates = w.precision != BX_TF32X3;
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        if (k < T.K && rates) {
+            const float sk = ok ? T.shapes32[(size_t)k * T.N + i] : 0.f;
+            const float v = warp_sum(sk * fmaf(s_c[0][k], rho_s, s_c[1][k] * rho_t));
+            if (lane == 0) red[wid * GPN + 5 + k] = (double)v;
+        } else if (lane == 0) {
+            red[wid * GPN + 5 + k] = 0.0;
+        }
+    }
+    __syncthreads();
+    if (tid < GPN) {
+        double v = 0.0;
+        for (int q = 0; q < BCOLS / 32; ++q) v += red[q * GPN + tid];
+        gp[tid] = v;
+    }
 }
 
 cudaError_t launch_bwd(const Work& w, int n, int max_cb, cudaStream_t s) {

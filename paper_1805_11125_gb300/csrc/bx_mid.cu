@@ -62,6 +62,32 @@ struct Dot64 {
     __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
     __device__ __forceinline__ double value() const { return s; }
 };
+// Compensated FP32 sum (value s + c): TwoProduct of each term by FMA, TwoSum into the
+// running sum, the same to merge partial sums across a warp.
+struct Sum32 {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float t = __fadd_rn(s, x), bb = __fsub_rn(t, s);
+        c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(x, bb)));
+        s = t;
+    }
+    // add a * (b + bl), bl a small correction of b
+    __device__ __forceinline__ void add_prod(float a, float b, float bl) {
+        const float p = __fmul_rn(a, b);
+        c = fmaf(a, bl, __fadd_rn(c, fmaf(a, b, -p)));
+        add(p);
+    }
+    __device__ __forceinline__ Sum32 warp_reduce() const {
+        Sum32 r = *this;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float os = __shfl_xor_sync(0xffffffffu, r.s, o), oc = __shfl_xor_sync(0xffffffffu, r.c, o);
+            r.add(os);
+            r.c = __fadd_rn(r.c, oc);
+        }
+        return r;
+    }
+};
 template <typename TV> struct DotT { using type = Dot64; };
 template <> struct DotT<float> { using type = Dot32; };
 
@@ -173,28 +199,74 @@ __global__ void __launch_bounds__(MID_THREADS) k_mid(Work w, int want_grad, int 
             }
         } else {
             // sum_m v_k[m] G_W[m] = sum_i s_k[i] ((1 - eps) aW[i] + eps a[i]), a[i] from the
-            // per-tile column sums of the forward (valid on each tile's band only)
+            // per-tile column sums of the forward (valid on each tile's band only).  Products
+            // and sums in compensated FP32 (TwoProduct, TwoSum): the terms are non-negative
+            // and the result is the FP64 sum to a few 1e-15 of its size, at FP32 issue cost.
             const int2* tcols = w.tile_cols + (size_t)item * MAX_TILES;
             const TV* ap = static_cast<const TV*>(w.apart) + (size_t)item * w.max_tiles * w.Npad;
             const double* aWi = w.aW + (size_t)item * w.Npad;
-            for (int i = tid; i < T.N; i += MID_THREADS) {
-                double ag = 0.0;
-                for (int t = 0; t < T.n_tiles; ++t) {
-                    const int2 cr = tcols[t];
-                    if (i >= cr.x && i < cr.y) ag += (double)ap[(size_t)t * w.Npad + i];
-                }
-                const double aw = aWi[i];
-                const double GW = (1.0 - eps) * aw + eps * ag, dG = ag - aw;
-#pragma unroll
-                for (int k = 0; k < KMAX; ++k)
-                    if (k < K) {
-                        const double x = T.shapes[(size_t)k * T.N + i];
-                        part[k] += x * GW;
-                        part[KMAX + k] += x * dG;
+            const int lane = tid & 31, wid = tid >> 5;
+            constexpr int KG = 8;   // species per pass over the columns (register budget)
+            if (sizeof(TV) == sizeof(double)) {   // FP64 model: plain FP64 products and sums
+                for (int i = tid; i < T.N; i += MID_THREADS) {
+                    double ag = 0.0;
+                    for (int t = 0; t < T.n_tiles; ++t) {
+                        const int2 cr = tcols[t];
+                        if (i >= cr.x && i < cr.y) ag += (double)ap[(size_t)t * w.Npad + i];
                     }
+                    const double aw = aWi[i];
+                    const double GW = (1.0 - eps) * aw + eps * ag, dG = ag - aw;
+#pragma unroll
+                    for (int k = 0; k < KMAX; ++k)
+                        if (k < K) {
+                            const double x = T.shapes[(size_t)k * T.N + i];
+                            part[k] += x * GW;
+                            part[KMAX + k] += x * dG;
+                        }
+                }
+#pragma unroll
+                for (int k = 0; k < 2 * KMAX; ++k) {
+                    const double r = warp_sum(part[k]);
+                    if (lane == 0) red[wid * 2 * KMAX + k] = r;
+                }
+            } else for (int k0 = 0; k0 < K; k0 += KG) {
+                Sum32 acc[2 * KG];
+                for (int i = tid; i < T.N; i += MID_THREADS) {
+                    double ag = 0.0;
+                    for (int t = 0; t < T.n_tiles; ++t) {
+                        const int2 cr = tcols[t];
+                        if (i >= cr.x && i < cr.y) ag += (double)ap[(size_t)t * w.Npad + i];
+                    }
+                    const double aw = aWi[i];
+                    const double GWd = (1.0 - eps) * aw + eps * ag;
+                    const float GW = (float)GWd, GWl = (float)(GWd - (double)GW), dG = (float)(ag - aw);
+#pragma unroll
+                    for (int k = 0; k < KG; ++k)
+                        if (k0 + k < K) {
+                            const float x = T.shapes32[(size_t)(k0 + k) * T.N + i];
+                            acc[k].add_prod(x, GW, GWl);
+                            acc[KG + k].add_prod(x, dG, 0.f);
+                        }
+                }
+#pragma unroll
+                for (int k = 0; k < KG; ++k) {
+                    const Sum32 r0 = acc[k].warp_reduce(), r1 = acc[KG + k].warp_reduce();
+                    if (lane == 0 && k0 + k < KMAX) {
+                        red[wid * 2 * KMAX + k0 + k] = (double)r0.s + (double)r0.c;
+                        red[wid * 2 * KMAX + KMAX + k0 + k] = (double)r1.s + (double)r1.c;
+                    }
+                }
             }
+            __syncthreads();
+            if (tid < 2 * KMAX) {
+                double v = 0.0;
+                for (int q = 0; q < MID_WARPS; ++q) v += red[q * 2 * KMAX + tid];
+                s_SA[tid] = v;
+            }
+            __syncthreads();
         }
-        block_sum<2 * KMAX>(part, red, s_SA);   // s_SA[k] = sum v G_W, s_SA[KMAX+k] = sum v dG_W/deps
+        // s_SA[k] = sum v G_W, s_SA[KMAX+k] = sum v dG_W/deps
+        if (species) block_sum<2 * KMAX>(part, red, s_SA);
     }
     // radial bin probabilities (internal: uniform in volume; external: exponential from r_iv)
     if (nrad > 0) {

@@ -5,12 +5,14 @@
 //   and the pile-up window marginal Gg[m] = sum_{m' in W, 0 <= m'-m < L} g[m'-m].
 // k_prep (once per item): Eq. 1's Birks map and resolution on the true-energy grid in
 //   FP64 (block-wide prefix sum), the column normalisation 1/Phi(mu/sigma), the FP32
-//   parameters of the generated response and the band limits of every tile.
+//   parameters of the generated response, the rate-weighted spectra of Eq. 3 and the band
+//   limits of every tile.
 #include <float.h>
 #include <limits.h>
 #include <math.h>
 
 #include "bx_internal.cuh"
+#include "bx_resp.cuh"
 
 namespace bx {
 
@@ -44,12 +46,18 @@ cudaError_t launch_setup_toy(const Toy& t, float* shapes32, float* S_tiles, floa
     return cudaGetLastError();
 }
 
-// Gaussian mass between standard scores a < b, from the tail away from the mean.
+// Upper tail Q(x) = 1 - Phi(x) = erfc(x / sqrt 2) / 2, taken as 0 from x = 9 on (Q(9) = 1.1e-19:
+// below the rounding of every sum it enters; 1 - Q(x) rounds to 1 in FP64 already from x = 8.3).
+constexpr double Q_CUT = 9.0;
+__device__ __forceinline__ double upper_tail(double x) {
+    return x >= Q_CUT ? 0.0 : 0.5 * erfc(x * 0.70710678118654752440);
+}
+
+// Gaussian mass between standard scores a < b, from the tails away from the mean.
 __device__ __forceinline__ double gauss_mass(double a, double b) {
-    const double r = 0.70710678118654752440;
-    if (a >= 0.0) return 0.5 * (erfc(a * r) - erfc(b * r));
-    if (b <= 0.0) return 0.5 * (erfc(-b * r) - erfc(-a * r));
-    return 1.0 - 0.5 * erfc(b * r) - 0.5 * erfc(-a * r);
+    if (a >= 0.0) return upper_tail(a) - upper_tail(b);
+    if (b <= 0.0) return upper_tail(-b) - upper_tail(-a);
+    return 1.0 - upper_tail(b) - upper_tail(-a);
 }
 
 // Block-wide exclusive scan of two doubles (256 threads).
@@ -78,6 +86,16 @@ __device__ void block_scan2(double& a, double& b, double* sh) {
     __syncthreads();
 }
 
+// FP64 work is what this stage costs (GB300 issues FP64 at 1/64 of its FP32 rate), so each
+// quantity is computed in the precision its consumer needs:
+//   FP64: the Birks prefix sums, mu, sigma, 1/Phi(mu/sigma) and phi/Phi (only where
+//         mu/sigma < 9: elsewhere 1 and < 1e-18), the window mass (erfc only for window
+//         edges within 9 sigma), the double-float split of the generator's parameters;
+//   FP32 (F32 = true, the mixed-precision modes): the rate-weighted spectra
+//         S_h[i] = sum_k r_k c_{h,k} s_k[i] with the rates as double-float pairs, the outer-node
+//         factor 2 * 2^(-kk^2) by the generator's own exp2; nothing for the FP64 path's
+//         generator (it works from mu and sigma).
+template <bool F32>
 __global__ void __launch_bounds__(256) k_prep(Work w) {
     const int item = blockIdx.x, tid = threadIdx.x;
     if (w.skip && w.skip[item]) {   // uniform for the block: no barrier is skipped unevenly
@@ -90,75 +108,110 @@ __global__ void __launch_bounds__(256) k_prep(Work w) {
     __shared__ double sh[32];
     __shared__ int s_bad;
     __shared__ int s_tlo[MAX_TILES], s_thi[MAX_TILES], s_rlo[MAX_CB], s_rhi[MAX_CB];
+    __shared__ float s_rate[4][KMAX];   // (vetoed hi, lo, tagged hi, lo)
     if (tid == 0) s_bad = 0;
     for (int j = tid; j < MAX_TILES; j += blockDim.x) { s_tlo[j] = INT_MAX; s_thi[j] = INT_MIN; }
     for (int j = tid; j < MAX_CB; j += blockDim.x) { s_rlo[j] = INT_MAX; s_rhi[j] = INT_MIN; }
+    if (F32 && tid < KMAX) {
+        double rs = 0.0, rt = 0.0;
+        if (tid < K) {
+            const double t = T.tag ? T.tag[tid] : 0.0;
+            rs = th[tid] * (T.tag ? 1.0 - t : 1.0);
+            rt = th[tid] * t;
+        }
+        const float rsh = (float)rs, rth = (float)rt;
+        s_rate[0][tid] = rsh;
+        s_rate[1][tid] = (float)(rs - (double)rsh);
+        s_rate[2][tid] = rth;
+        s_rate[3][tid] = (float)(rt - (double)rth);
+    }
     __syncthreads();
     if (tid < T.P && !isfinite(th[tid])) s_bad = 1;
     const double LY = th[K], a = th[K + 1], b = th[K + 2], c = th[K + 3], kB = th[K + 4];
     if (tid == 0 && (!(LY > 0.0) || (T.n_rad > 0 && !(th[K + 6] > 0.0)))) s_bad = 1;
 
-    // a1: Q_i = sum_{j<i} x_j + x_i / 2, x_j = dE / (1 + kB S_j); dQ_i/dkB likewise.
+    double2* cq = w.colq + (size_t)item * w.Npad;
+    // a1: Q_i = sum_{j<i} x_j + x_i / 2, x_j = dE / (1 + kB S_j); dQ_i/dkB likewise.  The
+    // increments are parked in colq between the two passes.
     const int per = (N + blockDim.x - 1) / blockDim.x;
-    const int i0 = tid * per, i1 = min(i0 + per, N);
+    const int i0 = min(tid * per, N), i1 = min(i0 + per, N);
+    int bad = 0;
     double sx = 0.0, sy = 0.0;
     for (int i = i0; i < i1; ++i) {
-        const double q = 1.0 + kB * T.stop_pow[i];
-        sx += T.dE / q;
-        sy += -T.dE * T.stop_pow[i] / (q * q);
+        const double S = T.stop_pow[i], q = 1.0 + kB * S;
+        if (!(q > 0.0)) bad = 1;
+        const double rq = 1.0 / q;
+        const double x = T.dE * rq, y = -x * S * rq;
+        cq[i] = make_double2(x, y);
+        sx += x;
+        sy += y;
     }
     double ex = sx, ey = sy;
     block_scan2(ex, ey, sh);
-    const double w_ = T.w, band = w.band;
+    const double w_ = T.w, inv_w = 1.0 / w_, band = w.band;
+    const double z_lo = T.m_lo * w_, z_hi = M * w_;
     Col64* col = w.col64 + (size_t)item * w.Npad;
-    double2* cq = w.colq + (size_t)item * w.Npad;
     float4* cf = w.colf + (size_t)item * w.Npad;
     ColG* cg = w.colg + (size_t)item * w.Npad;
     double2* cs = w.colS + (size_t)item * w.Npad;
     double* aW = w.aW + (size_t)item * w.Npad;
-    int bad = 0;
     unsigned long long inband = 0;
     for (int i = i0; i < i1; ++i) {
-        const double S = T.stop_pow[i], q = 1.0 + kB * S;
-        if (!(q > 0.0)) bad = 1;
-        const double x = T.dE / q, y = -T.dE * S / (q * q);
-        const double Q = ex + 0.5 * x, dQ = ey + 0.5 * y;
-        ex += x;
-        ey += y;
-        const double mu = LY * Q;
-        const double var = a * mu + b * mu * mu + c;
-        if (!(var > 0.0)) bad = 1;
-        const double sig = sqrt(fmax(var, 1e-300));
-        const double z = mu / sig;
-        const double Phi = 0.5 * erfc(-z * 0.70710678118654752440);
-        const double phi = INV_SQRT_2PI * exp(-0.5 * z * z);
-        const double norm = 1.0 / Phi;
-        col[i] = Col64{mu, sig, norm, phi / Phi};
+        const double2 xy = cq[i];
+        const double Q = ex + 0.5 * xy.x, dQ = ey + 0.5 * xy.y;
+        ex += xy.x;
+        ey += xy.y;
         cq[i] = make_double2(Q, dQ);
-        const double u = mu / w_;
-        const double jf = floor(u);
-        const double hs = w_ / sig * S_EX2, cc = (0.5 - (u - jf)) * hs;
-        const float hs_hi = (float)hs, c_hi = (float)cc;
-        cf[i] = make_float4((float)jf, c_hi, hs_hi, (float)(hs - (double)hs_hi));
-        const double kk = 0.38729833462074170 * hs;
-        cg[i] = ColG{(float)(2.0 * 0.69314718055994531 * kk), (float)(2.0 * exp2(-kk * kk)),
-                     (float)(cc - (double)c_hi), (float)(0.5 * (w_ / sig) * norm * INV_SQRT_2PI * GL_W_SCALE)};
-        // rate-weighted shapes of the vetoed (or single) and tagged spectra (Eq. 3)
-        double ssub = 0.0, stag = 0.0;
-        for (int k = 0; k < K; ++k) {
-            const double sk = T.shapes[(size_t)k * N + i] * th[k];
-            const double t = T.tag ? T.tag[k] : 0.0;
-            ssub += (T.tag ? 1.0 - t : 1.0) * sk;
-            stag += t * sk;
+        const double mu = LY * Q;
+        const double var = fma(fma(b, mu, a), mu, c);
+        if (!(var > 0.0)) bad = 1;
+        const double isig = rsqrt(fmax(var, 1e-300));
+        const double sig = var * isig;
+        const double z = mu * isig;
+        double norm = 1.0, mills = 0.0;
+        if (z < Q_CUT) {
+            const double Phi = z > 0.0 ? 1.0 - upper_tail(z) : upper_tail(-z);
+            norm = 1.0 / Phi;
+            mills = INV_SQRT_2PI * exp(-0.5 * z * z) * norm;
         }
-        cs[i] = make_double2(ssub, stag);
+        col[i] = Col64{mu, sig, norm, mills};
+        if (F32) {
+            const double u = mu * inv_w;
+            const double jf = floor(u);
+            const double hs = w_ * isig * S_EX2, cc = (0.5 - (u - jf)) * hs;
+            const float hs_hi = (float)hs, c_hi = (float)cc;
+            cf[i] = make_float4((float)jf, c_hi, hs_hi, (float)(hs - (double)hs_hi));
+            const double kk = 0.38729833462074170 * hs, kq = kk * kk;
+            const float kq_hi = (float)kq;
+            cg[i] = ColG{(float)(2.0 * 0.69314718055994531 * kk), 2.0f * exp2_neg(-kq_hi, (float)(kq_hi - kq)),
+                         (float)(cc - (double)c_hi), (float)((0.5 * INV_SQRT_2PI * GL_W_SCALE) * w_ * isig * norm)};
+        }
+        if (F32 && T.shapes32) {
+            // rate-weighted spectra of the vetoed (or single) and tagged events (Eq. 3)
+            float ss = 0.f, st = 0.f;
+            for (int k = 0; k < K; ++k) {
+                const float sk = T.shapes32[(size_t)k * N + i];
+                ss = fmaf(s_rate[0][k], sk, fmaf(s_rate[1][k], sk, ss));
+                st = fmaf(s_rate[2][k], sk, fmaf(s_rate[3][k], sk, st));
+            }
+            cs[i] = make_double2((double)ss, (double)st);
+        } else {   // FP64 model, or a descriptor without FP32 shapes
+            double ssub = 0.0, stag = 0.0;
+            for (int k = 0; k < K; ++k) {
+                const double sk = T.shapes[(size_t)k * N + i] * th[k];
+                const double t = T.tag ? T.tag[k] : 0.0;
+                ssub += (T.tag ? 1.0 - t : 1.0) * sk;
+                stag += t * sk;
+            }
+            cs[i] = make_double2(ssub, stag);
+        }
         // window mass of the column (Eq. 4 marginals)
-        aW[i] = gauss_mass((T.m_lo * w_ - mu) / sig, (M * w_ - mu) / sig) * norm;
+        aW[i] = gauss_mass((z_lo - mu) * isig, (z_hi - mu) * isig) * norm;
         // response band: rows whose bin lies within band * sigma of mu
         const double lo_e = fmin(fmax(mu - band * sig, -2.0 * w_), (M + 2.0) * w_);
         const double hi_e = fmin(fmax(mu + band * sig, -2.0 * w_), (M + 2.0) * w_);
-        const int r0 = max(0, (int)floor(lo_e / w_));
-        const int r1 = min(M, (int)floor(hi_e / w_) + 1);
+        const int r0 = max(0, (int)floor(lo_e * inv_w));
+        const int r1 = min(M, (int)floor(hi_e * inv_w) + 1);
         if (r0 < r1 && !bad) {
             inband += (unsigned long long)(r1 - r0);
             for (int t = r0 / TM; t <= (r1 - 1) / TM; ++t) {
@@ -172,8 +225,10 @@ __global__ void __launch_bounds__(256) k_prep(Work w) {
     for (int i = N + tid; i < w.Npad; i += blockDim.x) {
         col[i] = Col64{0.0, 1.0, 0.0, 0.0};
         cq[i] = make_double2(0.0, 0.0);
-        cf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        cg[i] = ColG{0.f, 0.f, 0.f, 0.f};
+        if (F32) {
+            cf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            cg[i] = ColG{0.f, 0.f, 0.f, 0.f};
+        }
         cs[i] = make_double2(0.0, 0.0);
         aW[i] = 0.0;
     }
@@ -188,7 +243,8 @@ __global__ void __launch_bounds__(256) k_prep(Work w) {
 }
 
 cudaError_t launch_prep(const Work& w, int n, cudaStream_t s) {
-    k_prep<<<n, 256, 0, s>>>(w);
+    if (w.precision == BX_FP64) k_prep<false><<<n, 256, 0, s>>>(w);
+    else k_prep<true><<<n, 256, 0, s>>>(w);
     return cudaGetLastError();
 }
 
