@@ -198,7 +198,7 @@ int bx_selftest_watchdog(double budget_s);
  * caller: shapes [K][n_grid], stop_pow [n_grid], tag_frac [K] or NULL, theta [K + 7],
  * lambda [m_hi] or [2][m_hi].  Limits of the fixed scratch: n_grid <= 4096, m_hi <= 4096,
  * K <= 16 (BX_EINVAL beyond).  The work is enqueued on cuda_stream and the call returns.
- * Its scratch is one 417 KiB static device array per device, whose address is looked up on
+ * Its scratch is one 481 KiB static device array per device, whose address is looked up on
  * the first call made on that device (make it before any stream capture); all calls share
  * it, so calls that overlap on the GPU race.  Invalid response parameters (sigma^2 <= 0)
  * leave lambda unwritten. */

@@ -268,9 +268,11 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
         {(void**)&w.colf, sizeof(float4) * cap * w.Npad},
         {(void**)&w.colg, sizeof(ColG) * cap * w.Npad},
         {(void**)&w.colS, sizeof(double2) * cap * w.Npad},
+        {(void**)&w.colS32, sizeof(float2) * cap * w.Npad},
         {(void**)&w.aW, sizeof(double) * cap * w.Npad},
+        {(void**)&w.colr, sizeof(int2) * cap * w.Npad},
         {(void**)&w.lam, sizeof(double) * cap * 2 * w.Mpad},
-        {(void**)&w.apart, m->any_cols && !species ? tv * cap * m->max_tiles * w.Npad : 16},
+        {(void**)&w.apart, m->any_cols && !species ? 2 * sizeof(float) * cap * m->max_tiles * w.Npad : 16},
         {(void**)&w.tile_cols, sizeof(int2) * cap * MAX_TILES},
         {(void**)&w.cb_rows, sizeof(int2) * cap * MAX_CB},
         {(void**)&w.v, species ? tv * cap * w.Mpad * US : 16},

@@ -19,6 +19,7 @@
 //              in FP32 per chunk of rows and FP64 across chunks, the chain rule in FP64; the
 //              species sums and the rate products in FP32 (FP64 work is 64 FP32 operations'
 //              worth of issue on GB300 and would otherwise dominate the column epilogue).
+#include <limits.h>
 #include <math.h>
 
 #include "bx_internal.cuh"
@@ -164,7 +165,6 @@ __global__ void __launch_bounds__(BCOLS) k_bwd_f32(Work w) {
     const bool ok = i < T.N;
     const int2 rr = w.cb_rows[(size_t)item * MAX_CB + cb];
     const int r0 = max(rr.x, max(0, T.m_lo - T.L + 1)), r1 = min(rr.y, T.M);
-    __shared__ float sW[3][RCH];
     __shared__ float s_coef[3][KMAX];   // vetoed, tagged and window coefficients per species
     __shared__ float s_c[2][KMAX];      // c_{vetoed,k}, c_{tagged,k}
     __shared__ double red[GPN * (BCOLS / 32)];
@@ -188,35 +188,46 @@ __global__ void __launch_bounds__(BCOLS) k_bwd_f32(Work w) {
     const float4 cf = ok ? w.colf[(size_t)item * w.Npad + i] : make_float4(0.f, 0.f, 0.f, 0.f);
     const ColG cg = ok ? w.colg[(size_t)item * w.Npad + i] : ColG{0.f, 0.f, 0.f, 0.f};
     const float* rw = static_cast<const float*>(w.rowW) + (size_t)item * 3 * w.Mpad;
+    // the warp's rows: the union of its 32 columns' bands, their weights staged 64 rows at a
+    // time in the warp's own shared memory (the warps of the block never wait for each other)
+    const int2 band = ok ? w.colr[(size_t)item * w.Npad + i] : make_int2(0, 0);
+    const bool live = band.x < band.y;
+    const int wr0 = max(r0, min(r1, __reduce_min_sync(0xffffffffu, live ? band.x : INT_MAX)));
+    const int wr1 = min(r1, __reduce_max_sync(0xffffffffu, live ? band.y : 0));
+    const int lane = tid & 31, wq = tid >> 5;
+    __shared__ float sW[BCOLS / 32][3][64];
     double S0 = 0.0, S1 = 0.0, S2 = 0.0, Rs = 0.0, Rt = 0.0;
-    for (int c0 = r0; c0 < r1; c0 += RCH) {
-        const int nr = min(RCH, r1 - c0);
-        for (int j = tid; j < nr; j += BCOLS) {
-            sW[0][j] = rw[c0 + j];
-            sW[1][j] = rw[(size_t)w.Mpad + c0 + j];
-            sW[2][j] = rw[(size_t)2 * w.Mpad + c0 + j];
-        }
-        __syncthreads();
+    for (int c0 = wr0; c0 < wr1; c0 += RCH) {
+        const int c1 = min(wr1, c0 + RCH);
         float p0 = 0.f, p1 = 0.f, p2 = 0.f, ps = 0.f, pt = 0.f;
-        if (ok) {
-            for (int j = 0; j < nr; ++j) {
-                const float ws = sW[0][j], wt = sW[1][j];
-                const float W = fmaf(ws, Ssub, fmaf(wt, Stag, sW[2][j] * SA));
-                float P0, P1, P2;
-                resp_adjoint32((float)(c0 + j), cf, cg, P0, P1, P2);
-                p0 = fmaf(W, P0, p0);
-                p1 = fmaf(W, P1, p1);
-                p2 = fmaf(W, P2, p2);
-                ps = fmaf(ws, P0, ps);
-                pt = fmaf(wt, P0, pt);
+        for (int s0 = c0; s0 < c1; s0 += 64) {
+            const int ns = min(64, c1 - s0);
+            for (int j = lane; j < ns; j += 32) {
+                sW[wq][0][j] = rw[s0 + j];
+                sW[wq][1][j] = rw[(size_t)w.Mpad + s0 + j];
+                sW[wq][2][j] = rw[(size_t)2 * w.Mpad + s0 + j];
             }
+            __syncwarp();
+            if (ok) {
+                for (int j = 0; j < ns; ++j) {
+                    const float ws = sW[wq][0][j], wt = sW[wq][1][j];
+                    const float W = fmaf(ws, Ssub, fmaf(wt, Stag, sW[wq][2][j] * SA));
+                    float P0, P1, P2;
+                    resp_adjoint32((float)(s0 + j), cf, cg, P0, P1, P2);
+                    p0 = fmaf(W, P0, p0);
+                    p1 = fmaf(W, P1, p1);
+                    p2 = fmaf(W, P2, p2);
+                    ps = fmaf(ws, P0, ps);
+                    pt = fmaf(wt, P0, pt);
+                }
+            }
+            __syncwarp();
         }
         S0 += p0;
         S1 += p1;
         S2 += p2;
         Rs += ps;
         Rt += pt;
-        __syncthreads();
     }
     // chain rule through mu_i = LY Q_i(kB), sigma_i^2 = a mu_i + b mu_i^2 + c in FP64
     double g5[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
@@ -244,7 +255,7 @@ __global__ void __launch_bounds__(BCOLS) k_bwd_f32(Work w) {
         rho_s = (float)(A * Rs);
         rho_t = (float)(A * Rt);
     }
-    const int lane = tid & 31, wid = tid >> 5;
+    const int wid = wq;
 #pragma unroll
     for (int j = 0; j < 5; ++j) {
         const double v = warp_sum(g5[j]);

@@ -5,13 +5,16 @@
 // and, for models with Eq. 4 terms, the response is also reduced over rows,
 //     a_t[i] = sum_{m in tile t} R[m,i] Gg[m],
 // from which k_mid forms every species' window marginal after pile-up.
-// Unit = (row tile of TM output bins, item); 64 threads, each owning bins m0 + t and
-// m0 + t + 64.  For every chunk of 32 true-energy columns of the tile's band the column
-// parameters are staged in shared memory; each thread generates the response of its two
-// bins with round-to-nearest FP32 arithmetic (bx_resp.cuh) and adds R S_h into
-// Kahan-compensated accumulators at every term, so a row sum of ~10^3 terms keeps an error
-// of a few roundings with no systematic sign.  Column sums go through a padded shared
-// buffer (conflict-free in both directions) once per chunk.
+// Unit = (row tile of TM output bins, item); 64 threads, warp q owning the two 32-row
+// groups m0 + 64q + [0, 32) and m0 + 64q + [32, 64), one row of each per thread.  The warps
+// never wait for each other: each stages 32 columns' parameters at a time in its own shared
+// memory and skips the columns whose band misses a row group, so the work follows each
+// column's own band rather than the union over the tile.
+// Each thread generates the response of its bins with round-to-nearest FP32 arithmetic
+// (bx_resp.cuh) and adds R S_h into Kahan-compensated accumulators at every term, so a row
+// sum of ~10^3 terms keeps an error of a few roundings with no systematic sign.  Column sums
+// of R Gg over a warp's 64 rows go through a padded warp-private shared buffer once per
+// 32 columns and are stored per half tile.
 #include <math.h>
 
 #include "bx_internal.cuh"
@@ -37,55 +40,82 @@ __global__ void __launch_bounds__(F32_THREADS) k_fwd_f32(Work w) {
     const int m0 = tile * TM, M = T.M;
     const int2 cr = w.tile_cols[(size_t)item * MAX_TILES + tile];
     const size_t cbase = (size_t)item * w.Npad;
-    __shared__ float4 sC[FCH32];
-    __shared__ ColG sG[FCH32];
-    __shared__ float2 sS[FCH32];
-    __shared__ float colbuf[COLS ? TM : 1][FCH32 + 1];
-    __shared__ float colhalf[2][FCH32];
+    const float4* colf = w.colf + cbase;
+    const ColG* colg = w.colg + cbase;
+    const float2* colS = w.colS32 + cbase;
+    const int2* colr = w.colr + cbase;
+    const int lane = tid & 31, q = tid >> 5, g = m0 + 64 * q;
+    // warp-private staging of 32 columns at a time (no block-wide barrier)
+    __shared__ float4 sC[2][FCH32];
+    __shared__ ColG sG[2][FCH32];
+    __shared__ float2 sS[2][FCH32];
+    __shared__ int2 sR[2][FCH32];
+    __shared__ float colbuf[COLS ? 2 : 1][COLS ? 64 : 1][FCH32 + 1];
+    float(*cb)[FCH32 + 1] = colbuf[COLS ? q : 0];
 
-    const int ra = m0 + tid, rb = m0 + tid + F32_THREADS;
+    const int ra = g + lane, rb = ra + 32;
     const float mfa = (float)ra, mfb = (float)rb;
     const float gga = (COLS && ra < M) ? (float)T.Gg[ra] : 0.f;
     const float ggb = (COLS && rb < M) ? (float)T.Gg[rb] : 0.f;
     float sa = 0.f, csa = 0.f, ta = 0.f, cta = 0.f, sb = 0.f, csb = 0.f, tb = 0.f, ctb = 0.f;
-    float* apart = static_cast<float*>(w.apart) + ((size_t)item * w.max_tiles + tile) * w.Npad;
+    float* apart = static_cast<float*>(w.apart) + (((size_t)item * w.max_tiles + tile) * 2 + q) * w.Npad;
 
     for (int c0 = cr.x; c0 < cr.y; c0 += FCH32) {
-        if (tid < FCH32) {
-            const bool in = c0 + tid < cr.y;
-            sC[tid] = in ? w.colf[cbase + c0 + tid] : make_float4(0.f, 0.f, 0.f, 0.f);
-            sG[tid] = in ? w.colg[cbase + c0 + tid] : ColG{0.f, 0.f, 0.f, 0.f};
-            const double2 S = in ? w.colS[cbase + c0 + tid] : make_double2(0.0, 0.0);
-            sS[tid] = make_float2((float)S.x, (float)S.y);
-        }
-        __syncthreads();
         const int ncol = min(FCH32, cr.y - c0);
+        {
+            const bool in = lane < ncol;
+            const int i = c0 + lane;
+            sC[q][lane] = in ? colf[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            sG[q][lane] = in ? colg[i] : ColG{0.f, 0.f, 0.f, 0.f};
+            sS[q][lane] = in ? colS[i] : make_float2(0.f, 0.f);
+            sR[q][lane] = in ? colr[i] : make_int2(0, 0);
+        }
+        __syncwarp();
         for (int c = 0; c < ncol; ++c) {
-            const float4 cf = sC[c];
-            const ColG cg = sG[c];
-            const float2 S = sS[c];
-            const float Ra = resp_exact32(mfa, cf, cg), Rb = resp_exact32(mfb, cf, cg);
-            kahan_fma(sa, csa, Ra, S.x);
-            kahan_fma(sb, csb, Rb, S.x);
-            if (TAG) {
-                kahan_fma(ta, cta, Ra, S.y);
-                kahan_fma(tb, ctb, Rb, S.y);
+            const int2 band = sR[q][c];
+            const bool inA = band.x < g + 32 && band.y > g;
+            const bool inB = band.x < g + 64 && band.y > g + 32;
+            if (!inA && !inB) {
+                if (COLS) {
+                    cb[lane][c] = 0.f;
+                    cb[lane + 32][c] = 0.f;
+                }
+                continue;
+            }
+            const float4 cf = sC[q][c];
+            const ColG cg = sG[q][c];
+            const float2 S = sS[q][c];
+            float Ra = 0.f, Rb = 0.f;
+            if (inA && inB) {   // the common case: two independent chains for the scheduler
+                Ra = resp_exact32(mfa, cf, cg);
+                Rb = resp_exact32(mfb, cf, cg);
+                kahan_fma(sa, csa, Ra, S.x);
+                kahan_fma(sb, csb, Rb, S.x);
+                if (TAG) {
+                    kahan_fma(ta, cta, Ra, S.y);
+                    kahan_fma(tb, ctb, Rb, S.y);
+                }
+            } else if (inA) {
+                Ra = resp_exact32(mfa, cf, cg);
+                kahan_fma(sa, csa, Ra, S.x);
+                if (TAG) kahan_fma(ta, cta, Ra, S.y);
+            } else {
+                Rb = resp_exact32(mfb, cf, cg);
+                kahan_fma(sb, csb, Rb, S.x);
+                if (TAG) kahan_fma(tb, ctb, Rb, S.y);
             }
             if (COLS) {
-                colbuf[tid][c] = Ra * gga;
-                colbuf[tid + F32_THREADS][c] = Rb * ggb;
+                cb[lane][c] = Ra * gga;
+                cb[lane + 32][c] = Rb * ggb;
             }
         }
+        __syncwarp();
         if (COLS) {
-            __syncthreads();
-            const int c = tid & 31, h = tid >> 5;
             float s = 0.f;
-            for (int j = 0; j < F32_THREADS; ++j) s += colbuf[h * F32_THREADS + j][c];
-            colhalf[h][c] = s;
-            __syncthreads();
-            if (tid < ncol) apart[c0 + tid] = colhalf[0][tid] + colhalf[1][tid];
+            for (int j = 0; j < 64; ++j) s += cb[j][lane];
+            if (lane < ncol) apart[c0 + lane] = s;
+            __syncwarp();
         }
-        __syncthreads();
     }
     double* lam = w.lam + (size_t)item * 2 * w.Mpad;
     if (ra < M) {

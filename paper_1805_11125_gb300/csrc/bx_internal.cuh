@@ -93,10 +93,13 @@ struct Work {
     double2* colq;            // [cap][Npad]: Q_i, dQ_i/dkB
     float4* colf;             // [cap][Npad]: (floor(mu/w), c_hi, hs_hi, hs_lo): hs = w/sig*S_EX2, c = (1/2 - frac(mu/w)) hs
     ColG* colg;               // [cap][Npad]
-    double2* colS;            // [cap][Npad]: S_vetoed[i], S_tagged[i]
+    double2* colS;            // [cap][Npad]: S_vetoed[i], S_tagged[i] (FP64 model)
+    float2* colS32;           // [cap][Npad]: the same for the mixed-precision modes
     double* aW;               // [cap][Npad]: window mass sum_{m in W} R[m,i] (closed form)
+    int2* colr;               // [cap][Npad]: band rows [r0, r1) of each column (empty: r0 >= r1)
     double* lam;              // [cap][2][Mpad]: lambda_h[m] (rate-first forward)
-    void* apart;              // [cap][max_tiles][Npad] float/double: column sums of R Gg per tile
+    void* apart;              // [cap][max_tiles][H][Npad]: column sums of R Gg per tile, FP64 (H = 1)
+                              // or per half tile (one warp's 64 rows), FP32 (H = 2)
     int2* tile_cols;          // [cap][MAX_TILES]: column range of each forward tile
     int2* cb_rows;            // [cap][MAX_CB]: row range of each backward column block
     void* v;                  // [cap][Mpad][US] float (TF32X3) or double (FP64)

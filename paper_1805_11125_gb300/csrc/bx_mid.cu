@@ -11,8 +11,10 @@
 //          window mass aW[i] and the forward's column sums a[i]); radial bins
 //          sum_k A_k p_k[rho] (closed-form shell integrals) and pulse-shape bins
 //          sum_k A_k q_k[j];
-//   -lnL   sum of mu - n + n log1p((n - mu)/mu) in FP64 with Neumaier compensation
-//          inside each thread and TwoSum-style merging across the block.
+//   -lnL   sum of mu - n + n log1p((n - mu)/mu): the terms in FP64, or for the
+//          mixed-precision modes in a cancellation-free FP32 form where |n - mu| <= mu/4;
+//          the sum in FP64 with Neumaier compensation inside each thread and TwoSum-style
+//          merging across the block.
 // With want_grad it also writes the adjoint inputs of the response stage: per row the
 // pile-up-correlated residual weights wt_h[m] and G_W[m], per species the coefficients
 // that turn them into dNLL/dR[m,i], and the gradient of eps, s_r and the parts of the
@@ -91,6 +93,26 @@ struct Sum32 {
 template <typename TV> struct DotT { using type = Dot64; };
 template <> struct DotT<float> { using type = Dot32; };
 
+// Baker-Cousins term (mu - n) + n ln(n/mu) (n > 0) and its weight 1 - n/mu in FP32, for
+// |x| <= 1/4 with x = (n - mu)/mu (every bin of a reasonable fit).  Written without
+// cancellation: the term is n (log1p(x) - x) + (n - mu) x, and with s = x / (2 + x),
+//   log1p(x) - x = 2 atanh(s) - x = -x^2 / (2 + x) + 2 (s^3/3 + s^5/5 + s^7/7 + s^9/9 + ...),
+// |s| <= 1/7, truncated after s^9 (next term < 1e-10); each piece has FP32 relative error, the
+// term (~(n - mu)^2 / 2mu, ~1/2) an absolute error ~1e-7 with no systematic sign.  Other bins
+// take the FP64 form.  Returns false when |x| > 1/4.
+__device__ __forceinline__ bool bc_term32(double n, double mu, double& term, double& wb) {
+    const float d = (float)(n - mu);
+    const float x = d / (float)mu;
+    if (!(fabsf(x) <= 0.25f)) return false;
+    const float r = 1.0f / (2.0f + x);
+    const float s = x * r, s2 = s * s;
+    const float series = fmaf(s2, fmaf(s2, fmaf(s2, 2.0f / 9.0f, 2.0f / 7.0f), 2.0f / 5.0f), 2.0f / 3.0f);
+    const float L = fmaf(s2 * s, series, -(x * x) * r);
+    term = (double)fmaf((float)n, L, d * x);
+    wb = (double)(-x);
+    return true;
+}
+
 // Shell integral of r^2 exp((r - r_iv)/lam): F and dF/dlam.
 __device__ __forceinline__ void shell_F(double r, double r_iv, double lam, double& F, double& dF) {
     const double e = exp((r - r_iv) / lam);
@@ -99,8 +121,11 @@ __device__ __forceinline__ void shell_F(double r, double r_iv, double lam, doubl
     dF = e * (-(r - r_iv) / (lam * lam) * poly + (r * r - 4.0 * lam * r + 6.0 * lam * lam));
 }
 
-template <typename TV>
-__global__ void __launch_bounds__(MID_THREADS) k_mid(Work w, int want_grad, int want_mu) {
+// SPECIES: the tensor-core forward's species-resolved spectra (else rate-first).  The
+// rate-first FP32 variant is held to 64 registers so that two CTAs share an SM.
+template <typename TV, bool SPECIES>
+__global__ void __launch_bounds__(MID_THREADS, (sizeof(TV) == sizeof(float) && !SPECIES) ? 2 : 1)
+    k_mid(Work w, int want_grad, int want_mu) {
     extern __shared__ double dsm[];
     const int item = blockIdx.x, tid = threadIdx.x;
     const Toy& T = w.toys[w.toy_of[item]];
@@ -140,7 +165,7 @@ __global__ void __launch_bounds__(MID_THREADS) k_mid(Work w, int want_grad, int 
     __syncthreads();
 
     // Eq. 3: the energy spectra on the full axis
-    const bool species = w.precision == BX_TF32X3;
+    constexpr bool species = SPECIES;
     const double* lamg = w.lam + (size_t)item * 2 * w.Mpad;
     for (int m = tid; m < M; m += MID_THREADS) {
         double ls = 0.0, lt = 0.0;
@@ -203,7 +228,8 @@ __global__ void __launch_bounds__(MID_THREADS) k_mid(Work w, int want_grad, int 
             // and sums in compensated FP32 (TwoProduct, TwoSum): the terms are non-negative
             // and the result is the FP64 sum to a few 1e-15 of its size, at FP32 issue cost.
             const int2* tcols = w.tile_cols + (size_t)item * MAX_TILES;
-            const TV* ap = static_cast<const TV*>(w.apart) + (size_t)item * w.max_tiles * w.Npad;
+            constexpr int HALF = sizeof(TV) == sizeof(float) ? 2 : 1;   // slots per tile
+            const TV* ap = static_cast<const TV*>(w.apart) + (size_t)item * w.max_tiles * HALF * w.Npad;
             const double* aWi = w.aW + (size_t)item * w.Npad;
             const int lane = tid & 31, wid = tid >> 5;
             constexpr int KG = 8;   // species per pass over the columns (register budget)
@@ -212,7 +238,8 @@ __global__ void __launch_bounds__(MID_THREADS) k_mid(Work w, int want_grad, int 
                     double ag = 0.0;
                     for (int t = 0; t < T.n_tiles; ++t) {
                         const int2 cr = tcols[t];
-                        if (i >= cr.x && i < cr.y) ag += (double)ap[(size_t)t * w.Npad + i];
+                        if (i >= cr.x && i < cr.y)
+                            for (int h = 0; h < HALF; ++h) ag += (double)ap[((size_t)t * HALF + h) * w.Npad + i];
                     }
                     const double aw = aWi[i];
                     const double GW = (1.0 - eps) * aw + eps * ag, dG = ag - aw;
@@ -232,12 +259,13 @@ __global__ void __launch_bounds__(MID_THREADS) k_mid(Work w, int want_grad, int 
             } else for (int k0 = 0; k0 < K; k0 += KG) {
                 Sum32 acc[2 * KG];
                 for (int i = tid; i < T.N; i += MID_THREADS) {
-                    double ag = 0.0;
+                    float agf = 0.f;   // a few positive terms; enters G_W with weight eps
                     for (int t = 0; t < T.n_tiles; ++t) {
                         const int2 cr = tcols[t];
-                        if (i >= cr.x && i < cr.y) ag += (double)ap[(size_t)t * w.Npad + i];
+                        if (i >= cr.x && i < cr.y)
+                            for (int h = 0; h < HALF; ++h) agf += (float)ap[((size_t)t * HALF + h) * w.Npad + i];
                     }
-                    const double aw = aWi[i];
+                    const double aw = aWi[i], ag = (double)agf;
                     const double GWd = (1.0 - eps) * aw + eps * ag;
                     const float GW = (float)GWd, GWl = (float)(GWd - (double)GW), dG = (float)(ag - aw);
 #pragma unroll
@@ -316,14 +344,17 @@ __global__ void __launch_bounds__(MID_THREADS) k_mid(Work w, int want_grad, int 
         if (b < nwin) mu = muw[b];
         else if (b < nwin + nrad) mu = s_mur[b - nwin];
         else mu = s_mup[b - nwin - nrad];
-        double term;
+        double term, wb = 1.0;
         if (n == 0.0) term = mu;
-        else if (mu > 0.0 && isfinite(mu)) term = (mu - n) + n * log1p((n - mu) / mu);
-        else { dom = 1; term = 0.0; }
+        else if (!(mu > 0.0 && isfinite(mu))) { dom = 1; term = 0.0; }
+        else if (sizeof(TV) == sizeof(float) && bc_term32(n, mu, term, wb)) {}
+        else {
+            term = (mu - n) + n * log1p((n - mu) / mu);
+            wb = 1.0 - n / mu;
+        }
         neu_add(acc, term);
         if (want_mu) w.mu[(size_t)item * w.nbmax + b] = mu;
         if (want_grad) {
-            const double wb = (n == 0.0) ? 1.0 : 1.0 - n / mu;
             if (b < nwin) {
                 const int h = b / nw, j = b % nw;
                 wvT[b] = (TV)wb;
@@ -449,31 +480,29 @@ __global__ void __launch_bounds__(MID_THREADS) k_mid(Work w, int want_grad, int 
     }
 }
 
+template <typename TV, bool SPECIES>
+static cudaError_t launch_mid_t(const Work& w, int n, size_t smem, int want_grad, int want_mu, cudaStream_t s) {
+    // the attribute is set once per size (outside any stream capture that replays it)
+    static size_t set = 0;
+    if (smem > set) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(k_mid<TV, SPECIES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        set = smem;
+    }
+    k_mid<TV, SPECIES><<<n, MID_THREADS, smem, s>>>(w, want_grad, want_mu);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_mid(const Work& w, int n, int Mmax, int nwmax, int Lmax, int want_grad, int want_mu,
                        cudaStream_t s) {
     const bool f32 = w.precision != BX_FP64;
     const size_t tv = f32 ? sizeof(float) : sizeof(double);
     const size_t smem = (size_t)(2 * Mmax + 2 * nwmax) * sizeof(double) +
                         (size_t)(2 * Mmax + 4 * nwmax + Lmax) * tv + 64;
-    // the attribute is set once per size (outside any stream capture that replays it)
-    static size_t set_f32 = 0, set_f64 = 0;
-    cudaError_t e;
-    if (f32) {
-        if (smem > set_f32) {
-            e = cudaFuncSetAttribute(k_mid<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            set_f32 = smem;
-        }
-        k_mid<float><<<n, MID_THREADS, smem, s>>>(w, want_grad, want_mu);
-    } else {
-        if (smem > set_f64) {
-            e = cudaFuncSetAttribute(k_mid<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            set_f64 = smem;
-        }
-        k_mid<double><<<n, MID_THREADS, smem, s>>>(w, want_grad, want_mu);
-    }
-    return cudaGetLastError();
+    if (!f32) return launch_mid_t<double, false>(w, n, smem, want_grad, want_mu, s);
+    if (w.precision == BX_TF32X3) return launch_mid_t<float, true>(w, n, smem, want_grad, want_mu, s);
+    return launch_mid_t<float, false>(w, n, smem, want_grad, want_mu, s);
 }
 
 }  // namespace bx

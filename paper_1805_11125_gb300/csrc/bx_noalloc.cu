@@ -45,7 +45,9 @@ struct NoAllocScratch {
     float4 colf[NA_MAX_GRID];
     ColG colg[NA_MAX_GRID];
     double2 colS[NA_MAX_GRID];
+    float2 colS32[NA_MAX_GRID];
     double aW[NA_MAX_GRID];
+    int2 colr[NA_MAX_GRID];
     int2 tile_cols[MAX_TILES];
     int2 cb_rows[MAX_CB];
 };
@@ -55,7 +57,7 @@ void* g_scratch_addr[NA_MAX_DEVICES] = {};
 
 }  // namespace
 
-// 417 KiB per device that loads the library, held until the process exits.
+// 481 KiB per device that loads the library, held until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
 
 static int noalloc_scratch(NoAllocScratch** out) {
@@ -133,7 +135,9 @@ extern "C" int bx_spectra_noalloc(int n_grid, double e_max, int n_species, const
     w.colf = scr->colf;
     w.colg = scr->colg;
     w.colS = scr->colS;
+    w.colS32 = scr->colS32;
     w.aW = scr->aW;
+    w.colr = scr->colr;
     w.tile_cols = scr->tile_cols;
     w.cb_rows = scr->cb_rows;
     w.lam = lambda;   // written directly: [2][m_hi] with tag fractions, [m_hi] without

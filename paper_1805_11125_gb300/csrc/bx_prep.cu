@@ -60,14 +60,14 @@ __device__ __forceinline__ double gauss_mass(double a, double b) {
     return 1.0 - upper_tail(b) - upper_tail(-a);
 }
 
-// Block-wide exclusive scan of two doubles (256 threads).
-__device__ void block_scan2(double& a, double& b, double* sh) {
+// Block-wide exclusive scan of two doubles (256 threads); ta, tb receive the block totals.
+__device__ void block_scan2(double& a, double& b, double& ta, double& tb, double* sh) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     double ia = a, ib = b;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        double ta = __shfl_up_sync(0xffffffffu, ia, o), tb = __shfl_up_sync(0xffffffffu, ib, o);
-        if (lane >= o) { ia += ta; ib += tb; }
+        double xa = __shfl_up_sync(0xffffffffu, ia, o), xb = __shfl_up_sync(0xffffffffu, ib, o);
+        if (lane >= o) { ia += xa; ib += xb; }
     }
     if (lane == 31) { sh[wid] = ia; sh[8 + wid] = ib; }
     __syncthreads();
@@ -75,29 +75,35 @@ __device__ void block_scan2(double& a, double& b, double* sh) {
         double wa = lane < 8 ? sh[lane] : 0.0, wb = lane < 8 ? sh[8 + lane] : 0.0;
 #pragma unroll
         for (int o = 1; o < 8; o <<= 1) {
-            double ta = __shfl_up_sync(0xffffffffu, wa, o), tb = __shfl_up_sync(0xffffffffu, wb, o);
-            if (lane >= o) { wa += ta; wb += tb; }
+            double xa = __shfl_up_sync(0xffffffffu, wa, o), xb = __shfl_up_sync(0xffffffffu, wb, o);
+            if (lane >= o) { wa += xa; wb += xb; }
         }
         if (lane < 8) { sh[16 + lane] = wa - sh[lane]; sh[24 + lane] = wb - sh[8 + lane]; }
     }
     __syncthreads();
     a = sh[16 + wid] + ia - a;
     b = sh[24 + wid] + ib - b;
+    ta = sh[16 + 7] + sh[7];
+    tb = sh[24 + 7] + sh[8 + 7];
     __syncthreads();
 }
 
+// One thread per true-energy column, the grid walked in chunks of 256 consecutive columns
+// (coalesced loads and stores; neighbouring lanes take the same branches), the Birks prefix
+// sum carried from chunk to chunk.  Tile and column-block bounds are reduced over the warp
+// (redux) before one shared atomic per warp and tile.
 // FP64 work is what this stage costs (GB300 issues FP64 at 1/64 of its FP32 rate), so each
 // quantity is computed in the precision its consumer needs:
 //   FP64: the Birks prefix sums, mu, sigma, 1/Phi(mu/sigma) and phi/Phi (only where
 //         mu/sigma < 9: elsewhere 1 and < 1e-18), the window mass (erfc only for window
 //         edges within 9 sigma), the double-float split of the generator's parameters;
-//   FP32 (F32 = true, the mixed-precision modes): the rate-weighted spectra
-//         S_h[i] = sum_k r_k c_{h,k} s_k[i] with the rates as double-float pairs, the outer-node
-//         factor 2 * 2^(-kk^2) by the generator's own exp2; nothing for the FP64 path's
-//         generator (it works from mu and sigma).
+//   FP32: the response band (a work bound, not a result); in the mixed-precision modes
+//         (F32 = true) also the rate-weighted spectra S_h[i] = sum_k r_k c_{h,k} s_k[i] with
+//         the rates as double-float pairs and the outer-node factor 2 * 2^(-kk^2) by the
+//         generator's own exp2; nothing for the FP64 path's generator (it works from mu, sigma).
 template <bool F32>
 __global__ void __launch_bounds__(256) k_prep(Work w) {
-    const int item = blockIdx.x, tid = threadIdx.x;
+    const int item = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
     if (w.skip && w.skip[item]) {   // uniform for the block: no barrier is skipped unevenly
         if (tid == 0) w.status[item] = STATUS_SKIPPED;
         return;
@@ -130,96 +136,119 @@ __global__ void __launch_bounds__(256) k_prep(Work w) {
     const double LY = th[K], a = th[K + 1], b = th[K + 2], c = th[K + 3], kB = th[K + 4];
     if (tid == 0 && (!(LY > 0.0) || (T.n_rad > 0 && !(th[K + 6] > 0.0)))) s_bad = 1;
 
-    double2* cq = w.colq + (size_t)item * w.Npad;
-    // a1: Q_i = sum_{j<i} x_j + x_i / 2, x_j = dE / (1 + kB S_j); dQ_i/dkB likewise.  The
-    // increments are parked in colq between the two passes.
-    const int per = (N + blockDim.x - 1) / blockDim.x;
-    const int i0 = min(tid * per, N), i1 = min(i0 + per, N);
-    int bad = 0;
-    double sx = 0.0, sy = 0.0;
-    for (int i = i0; i < i1; ++i) {
-        const double S = T.stop_pow[i], q = 1.0 + kB * S;
-        if (!(q > 0.0)) bad = 1;
-        const double rq = 1.0 / q;
-        const double x = T.dE * rq, y = -x * S * rq;
-        cq[i] = make_double2(x, y);
-        sx += x;
-        sy += y;
-    }
-    double ex = sx, ey = sy;
-    block_scan2(ex, ey, sh);
-    const double w_ = T.w, inv_w = 1.0 / w_, band = w.band;
+    const double w_ = T.w, inv_w = 1.0 / w_;
     const double z_lo = T.m_lo * w_, z_hi = M * w_;
+    const float wf = (float)w_, inv_wf = (float)inv_w, bandf = (float)w.band;
+    const float e_min = -2.0f * wf, e_max = (M + 2.0f) * wf;
     Col64* col = w.col64 + (size_t)item * w.Npad;
+    double2* cq = w.colq + (size_t)item * w.Npad;
     float4* cf = w.colf + (size_t)item * w.Npad;
     ColG* cg = w.colg + (size_t)item * w.Npad;
     double2* cs = w.colS + (size_t)item * w.Npad;
+    float2* cs32 = w.colS32 + (size_t)item * w.Npad;
     double* aW = w.aW + (size_t)item * w.Npad;
+    int2* cr = w.colr + (size_t)item * w.Npad;
+    int bad = 0;
     unsigned long long inband = 0;
-    for (int i = i0; i < i1; ++i) {
-        const double2 xy = cq[i];
-        const double Q = ex + 0.5 * xy.x, dQ = ey + 0.5 * xy.y;
-        ex += xy.x;
-        ey += xy.y;
-        cq[i] = make_double2(Q, dQ);
-        const double mu = LY * Q;
-        const double var = fma(fma(b, mu, a), mu, c);
-        if (!(var > 0.0)) bad = 1;
-        const double isig = rsqrt(fmax(var, 1e-300));
-        const double sig = var * isig;
-        const double z = mu * isig;
-        double norm = 1.0, mills = 0.0;
-        if (z < Q_CUT) {
-            const double Phi = z > 0.0 ? 1.0 - upper_tail(z) : upper_tail(-z);
-            norm = 1.0 / Phi;
-            mills = INV_SQRT_2PI * exp(-0.5 * z * z) * norm;
+    double carry_x = 0.0, carry_y = 0.0;
+    for (int c0 = 0; c0 < N; c0 += 256) {
+        const int i = c0 + tid;
+        const bool in = i < N;
+        // a1: Q_i = sum_{j<i} x_j + x_i / 2, x_j = dE / (1 + kB S_j); dQ_i/dkB likewise
+        double x = 0.0, y = 0.0;
+        if (in) {
+            const double S = T.stop_pow[i], q = 1.0 + kB * S;
+            if (!(q > 0.0)) bad = 1;
+            const double rq = 1.0 / q;
+            x = T.dE * rq;
+            y = -x * S * rq;
         }
-        col[i] = Col64{mu, sig, norm, mills};
-        if (F32) {
-            const double u = mu * inv_w;
-            const double jf = floor(u);
-            const double hs = w_ * isig * S_EX2, cc = (0.5 - (u - jf)) * hs;
-            const float hs_hi = (float)hs, c_hi = (float)cc;
-            cf[i] = make_float4((float)jf, c_hi, hs_hi, (float)(hs - (double)hs_hi));
-            const double kk = 0.38729833462074170 * hs, kq = kk * kk;
-            const float kq_hi = (float)kq;
-            cg[i] = ColG{(float)(2.0 * 0.69314718055994531 * kk), 2.0f * exp2_neg(-kq_hi, (float)(kq_hi - kq)),
-                         (float)(cc - (double)c_hi), (float)((0.5 * INV_SQRT_2PI * GL_W_SCALE) * w_ * isig * norm)};
+        double ex = x, ey = y, tx, ty;
+        block_scan2(ex, ey, tx, ty, sh);
+        int r0 = 0, r1 = 0;
+        bool valid = false;
+        if (in) {
+            const double Q = carry_x + ex + 0.5 * x, dQ = carry_y + ey + 0.5 * y;
+            cq[i] = make_double2(Q, dQ);
+            const double mu = LY * Q;
+            const double var = fma(fma(b, mu, a), mu, c);
+            const bool ok = var > 0.0;
+            if (!ok) bad = 1;
+            const double isig = rsqrt(fmax(var, 1e-300));
+            const double sig = var * isig;
+            const double z = mu * isig;
+            double norm = 1.0, mills = 0.0;
+            if (z < Q_CUT) {
+                const double Phi = z > 0.0 ? 1.0 - upper_tail(z) : upper_tail(-z);
+                norm = 1.0 / Phi;
+                mills = INV_SQRT_2PI * exp(-0.5 * z * z) * norm;
+            }
+            col[i] = Col64{mu, sig, norm, mills};
+            if (F32) {
+                const double u = mu * inv_w;
+                const double jf = floor(u);
+                const double hs = w_ * isig * S_EX2, cc = (0.5 - (u - jf)) * hs;
+                const float hs_hi = (float)hs, c_hi = (float)cc;
+                cf[i] = make_float4((float)jf, c_hi, hs_hi, (float)(hs - (double)hs_hi));
+                const double kk = 0.38729833462074170 * hs, kq = kk * kk;
+                const float kq_hi = (float)kq;
+                cg[i] = ColG{(float)(2.0 * 0.69314718055994531 * kk), 2.0f * exp2_neg(-kq_hi, (float)(kq_hi - kq)),
+                             (float)(cc - (double)c_hi),
+                             (float)((0.5 * INV_SQRT_2PI * GL_W_SCALE) * w_ * isig * norm)};
+            }
+            if (F32 && T.shapes32) {
+                // rate-weighted spectra of the vetoed (or single) and tagged events (Eq. 3)
+                float ss = 0.f, st = 0.f;
+                for (int k = 0; k < K; ++k) {
+                    const float sk = T.shapes32[(size_t)k * N + i];
+                    ss = fmaf(s_rate[0][k], sk, fmaf(s_rate[1][k], sk, ss));
+                    st = fmaf(s_rate[2][k], sk, fmaf(s_rate[3][k], sk, st));
+                }
+                cs32[i] = make_float2(ss, st);
+            } else {   // FP64 model, or a descriptor without FP32 shapes
+                double ssub = 0.0, stag = 0.0;
+                for (int k = 0; k < K; ++k) {
+                    const double sk = T.shapes[(size_t)k * N + i] * th[k];
+                    const double t = T.tag ? T.tag[k] : 0.0;
+                    ssub += (T.tag ? 1.0 - t : 1.0) * sk;
+                    stag += t * sk;
+                }
+                if (F32) cs32[i] = make_float2((float)ssub, (float)stag);
+                else cs[i] = make_double2(ssub, stag);
+            }
+            // window mass of the column (Eq. 4 marginals)
+            aW[i] = gauss_mass((z_lo - mu) * isig, (z_hi - mu) * isig) * norm;
+            // response band: rows whose bin lies within band * sigma of mu
+            const float muf = (float)mu, sigf = (float)sig;
+            const float lo_e = fminf(fmaxf(muf - bandf * sigf, e_min), e_max);
+            const float hi_e = fminf(fmaxf(muf + bandf * sigf, e_min), e_max);
+            r0 = max(0, (int)floorf(lo_e * inv_wf));
+            r1 = min(M, (int)floorf(hi_e * inv_wf) + 1);
+            valid = ok && r0 < r1;
+            if (valid) inband += (unsigned long long)(r1 - r0);
+            cr[i] = valid ? make_int2(r0, r1) : make_int2(0, 0);
         }
-        if (F32 && T.shapes32) {
-            // rate-weighted spectra of the vetoed (or single) and tagged events (Eq. 3)
-            float ss = 0.f, st = 0.f;
-            for (int k = 0; k < K; ++k) {
-                const float sk = T.shapes32[(size_t)k * N + i];
-                ss = fmaf(s_rate[0][k], sk, fmaf(s_rate[1][k], sk, ss));
-                st = fmaf(s_rate[2][k], sk, fmaf(s_rate[3][k], sk, st));
+        carry_x += tx;
+        carry_y += ty;
+        // tile column ranges and column-block row ranges, reduced over the warp first
+        const unsigned full = 0xffffffffu;
+        const int t0 = valid ? r0 / TM : INT_MAX, t1 = valid ? (r1 - 1) / TM : INT_MIN;
+        const int tmin = __reduce_min_sync(full, t0), tmax = __reduce_max_sync(full, t1);
+        for (int t = tmin; t <= tmax; ++t) {
+            const bool touch = valid && t >= t0 && t <= t1;
+            const int lo = __reduce_min_sync(full, touch ? i : INT_MAX);
+            const int hi = __reduce_max_sync(full, touch ? i + 1 : INT_MIN);
+            if (lane == 0 && lo != INT_MAX) {
+                atomicMin(&s_tlo[t], lo);
+                atomicMax(&s_thi[t], hi);
             }
-            cs[i] = make_double2((double)ss, (double)st);
-        } else {   // FP64 model, or a descriptor without FP32 shapes
-            double ssub = 0.0, stag = 0.0;
-            for (int k = 0; k < K; ++k) {
-                const double sk = T.shapes[(size_t)k * N + i] * th[k];
-                const double t = T.tag ? T.tag[k] : 0.0;
-                ssub += (T.tag ? 1.0 - t : 1.0) * sk;
-                stag += t * sk;
-            }
-            cs[i] = make_double2(ssub, stag);
         }
-        // window mass of the column (Eq. 4 marginals)
-        aW[i] = gauss_mass((z_lo - mu) * isig, (z_hi - mu) * isig) * norm;
-        // response band: rows whose bin lies within band * sigma of mu
-        const double lo_e = fmin(fmax(mu - band * sig, -2.0 * w_), (M + 2.0) * w_);
-        const double hi_e = fmin(fmax(mu + band * sig, -2.0 * w_), (M + 2.0) * w_);
-        const int r0 = max(0, (int)floor(lo_e * inv_w));
-        const int r1 = min(M, (int)floor(hi_e * inv_w) + 1);
-        if (r0 < r1 && !bad) {
-            inband += (unsigned long long)(r1 - r0);
-            for (int t = r0 / TM; t <= (r1 - 1) / TM; ++t) {
-                atomicMin(&s_tlo[t], i);
-                atomicMax(&s_thi[t], i + 1);
-            }
-            atomicMin(&s_rlo[i / BCOLS], r0);
-            atomicMax(&s_rhi[i / BCOLS], r1);
+        // a warp's 32 columns lie in one column block (BCOLS is a multiple of 32)
+        const int rlo = __reduce_min_sync(full, valid ? r0 : INT_MAX);
+        const int rhi = __reduce_max_sync(full, valid ? r1 : INT_MIN);
+        if (lane == 0 && rlo != INT_MAX) {
+            atomicMin(&s_rlo[(c0 + tid) / BCOLS], rlo);
+            atomicMax(&s_rhi[(c0 + tid) / BCOLS], rhi);
         }
     }
     for (int i = N + tid; i < w.Npad; i += blockDim.x) {
@@ -229,8 +258,10 @@ __global__ void __launch_bounds__(256) k_prep(Work w) {
             cf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
             cg[i] = ColG{0.f, 0.f, 0.f, 0.f};
         }
-        cs[i] = make_double2(0.0, 0.0);
+        if (F32) cs32[i] = make_float2(0.f, 0.f);
+        else cs[i] = make_double2(0.0, 0.0);
         aW[i] = 0.0;
+        cr[i] = make_int2(0, 0);
     }
     if (bad) s_bad = 1;
     if (w.count_units && inband) atomicAdd(w.units, inband);
