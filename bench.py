@@ -225,12 +225,15 @@ def run_ours(args):
         total_ms = float(t.item())
     value = ws * B * args.steps / (total_ms / 1e3)
 
-    e2e, fp64_value = None, None
+    e2e, fp64_value, fits = None, None, None
     if not args.no_extras:
         e2e, fp64_value = extras(bx, model, spec, pts, theta, stream, B, P, ws, args)
+        fits = fit_times(bx, I, spec, stream)
+        if args.toys > 0:
+            fits["batched_toys"] = toy_fits(bx, I, args.toys, stream)
     if rank != 0:
         return
-    report(args, ws, B, total_ms, value, stage_ms, n_evals, entries, e2e, fp64_value, clk)
+    report(args, ws, B, total_ms, value, stage_ms, n_evals, entries, e2e, fp64_value, clk, fits)
 
 
 def extras(bx, model, spec, pts, theta, stream, B, P, ws, args):
@@ -268,7 +271,63 @@ def extras(bx, model, spec, pts, theta, stream, B, P, ws, args):
     return e2e, fp64_value
 
 
-def report(args, ws, B, total_ms, value, stage_ms, n_evals, entries, e2e, fp64_value, clk):
+def toy_fits(bx, I, n_toys, stream):
+    """Batched pseudo-experiments: n_toys ragged toys (bins U{400..1200} of 2 npe from 150 npe,
+    6-15 of the 15 library shapes, 1e4-1e7 events, Poisson data at theta_true), every toy
+    fitted from theta_true (1 + 0.05 z) in one bx_fit call (FP32, one CUDA graph replayed
+    until every fit has finished).  Wall time of the call (host clock, warm model)."""
+    base = I.toy_batch(n_toys=n_toys, seed=7)
+    gen = bx.Model([b.with_counts(np.zeros(b.n_bins_total)) for b in base], precision=bx.BX_FP32)
+    specs = [b.with_counts(I.poisson_counts(gen.expected(b.theta_true, t), 1000 + t)) for t, b in enumerate(base)]
+    gen.close()
+    P = 7 + max(t.K for t in specs)
+    th0 = np.zeros((n_toys, P))
+    for t, sp in enumerate(specs):
+        th0[t, : sp.P] = I.parameter_points(sp.theta_true, 1, rel=0.05, seed=300 + t, free=sp.default_free())[0]
+    m = bx.Model(specs, precision=bx.BX_FP32, max_batch=n_toys * (8 + 2 * P), stream=stream)
+    warm = min(n_toys, 64)
+    m.fit(th0[:warm], toy_idx=np.arange(warm))   # workspace set-up (the graph is re-captured for n)
+    t0 = time.perf_counter()
+    out, info, st = m.fit(th0, toy_idx=np.arange(n_toys))
+    wall = time.perf_counter() - t0
+    m.close()
+    ok = sum(1 for r in info if r["status"] == bx.BX_OK)
+    evals = sum(r["n_evals"] for r in info)
+    return {"toys": n_toys, "wall_s": wall, "fits_per_s": n_toys / wall, "converged": ok,
+            "evals": int(evals), "evals_per_s": evals / wall, "precision": "BX_FP32",
+            "recipe": "bins U{400..1200} x 2 npe from 150 npe, 6-15 species, 1e4-1e7 events, start theta_true (1 + 0.05 z)"}
+
+
+def fit_times(bx, I, spec, stream):
+    """Full-fit wall time of one multivariate fit started at theta_true (1 + 0.1 z): FP32, FP64,
+    and FP32 polished by FP64 (host wall clock around bx_fit, second call on a warm model)."""
+    th0 = I.parameter_points(spec.theta_true, 1, rel=0.1, seed=200, free=spec.default_free())
+    out = {"start": "theta_true * (1 + 0.1 z), 21 free parameters", "timing": "warm model, host wall clock"}
+    models = {}
+    for name, prec in (("fp32", bx.BX_FP32), ("fp64", bx.BX_FP64)):
+        m = bx.Model(spec, precision=prec, max_batch=8 + 2 * spec.P, stream=stream)
+        m.fit(th0)   # first call: workspace and graph set-up
+        t0 = time.perf_counter()
+        th, info, st = m.fit(th0)
+        out[name + "_s"] = time.perf_counter() - t0
+        out[name + "_status"] = int(st)
+        out[name + "_evals"] = int(info[0]["n_evals"])
+        out[name + "_nll"] = float(info[0]["nll"])
+        models[name] = (m, th)
+    m64, _ = models["fp64"]
+    th32 = models["fp32"][1]
+    t0 = time.perf_counter()
+    th, info, st = m64.fit(th32)
+    out["mixed_s"] = out["fp32_s"] + (time.perf_counter() - t0)
+    out["mixed_status"] = int(st)
+    out["mixed_nll"] = float(info[0]["nll"])
+    out["d2nll_fp32_vs_fp64"] = 2.0 * abs(out["fp32_nll"] - out["fp64_nll"])
+    for m, _ in models.values():
+        m.close()
+    return out
+
+
+def report(args, ws, B, total_ms, value, stage_ms, n_evals, entries, e2e, fp64_value, clk, fits=None):
     # roofline of the dominant kernel (ALU-bound: FP32 issue rate of 152 SMs x 128 lanes)
     per_launch = {k: v / max(n_evals, 1) for k, v in stage_ms.items()}
     dom = max(("forward", "adjoint"), key=lambda k: per_launch[k])
@@ -288,7 +347,7 @@ def report(args, ws, B, total_ms, value, stage_ms, n_evals, entries, e2e, fp64_v
             "config": {"workload": WORKLOAD, "global_batch": ws * B, "precision": "BX_FP32 (FP64 columns, -lnL)",
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}"},
             "fp64_gpu_value": fp64_value, "mixed_over_fp64": value / fp64_value if fp64_value else None,
-            "roofline": roofline, "cpu_baseline": cb, "e2e": e2e,
+            "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "fit": fits,
             "gpu_launches": 5 * args.steps, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
@@ -302,7 +361,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the e2e and FP64 legs (profiling runs)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the e2e, FP64 and fit legs (profiling runs)")
+    ap.add_argument("--toys", type=int, default=4096, help="batched toy fits in the fit leg (0: none)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

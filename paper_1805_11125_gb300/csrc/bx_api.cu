@@ -255,6 +255,7 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
     w.band = m->band;
     w.watchdog_ns = m->watchdog_ns;
     w.max_tiles = m->max_tiles;
+    w.max_cb = m->max_cb;
     const size_t tv = m->precision == BX_FP64 ? sizeof(double) : sizeof(float);
     const bool species = m->precision == BX_TF32X3;
     struct A {

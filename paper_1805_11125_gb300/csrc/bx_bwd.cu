@@ -85,7 +85,8 @@ __device__ __forceinline__ void column_weights(const Work& w, const Toy& T, int 
 }
 
 __global__ void __launch_bounds__(BCOLS) k_bwd_f64(Work w) {
-    const int cb = blockIdx.x, item = blockIdx.y, tid = threadIdx.x;
+    // 1D item-major grid (a y dimension would cap the batch at 65535 items)
+    const int cb = blockIdx.x % w.max_cb, item = blockIdx.x / w.max_cb, tid = threadIdx.x;
     const Toy& T = w.toys[w.toy_of[item]];
     if (cb >= T.n_cb) return;
     double* gp = w.gpart + ((size_t)item * MAX_CB + cb) * GPN;
@@ -153,7 +154,8 @@ __global__ void __launch_bounds__(BCOLS) k_bwd_f64(Work w) {
 }
 
 __global__ void __launch_bounds__(BCOLS) k_bwd_f32(Work w) {
-    const int cb = blockIdx.x, item = blockIdx.y, tid = threadIdx.x;
+    // 1D item-major grid (a y dimension would cap the batch at 65535 items)
+    const int cb = blockIdx.x % w.max_cb, item = blockIdx.x / w.max_cb, tid = threadIdx.x;
     const Toy& T = w.toys[w.toy_of[item]];
     if (cb >= T.n_cb) return;
     double* gp = w.gpart + ((size_t)item * MAX_CB + cb) * GPN;
@@ -283,7 +285,7 @@ __global__ void __launch_bounds__(BCOLS) k_bwd_f32(Work w) {
 }
 
 cudaError_t launch_bwd(const Work& w, int n, int max_cb, cudaStream_t s) {
-    dim3 grid(max_cb, n);
+    const unsigned grid = (unsigned)n * (unsigned)w.max_cb;   // decoded with w.max_cb
     if (w.precision == BX_FP64) k_bwd_f64<<<grid, BCOLS, 0, s>>>(w);
     else k_bwd_f32<<<grid, BCOLS, 0, s>>>(w);
     return cudaGetLastError();

@@ -34,7 +34,8 @@ __device__ __forceinline__ void kahan_fma(float& acc, float& cmp, float a, float
 
 template <bool TAG, bool COLS>
 __global__ void __launch_bounds__(F32_THREADS) k_fwd_f32(Work w) {
-    const int tile = blockIdx.x, item = blockIdx.y, tid = threadIdx.x;
+    // 1D item-major grid (a y dimension would cap the batch at 65535 items)
+    const int tile = blockIdx.x % w.max_tiles, item = blockIdx.x / w.max_tiles, tid = threadIdx.x;
     const Toy& T = w.toys[w.toy_of[item]];
     if (tile >= T.n_tiles || w.status[item]) return;
     const int m0 = tile * TM, M = T.M;
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(F32_THREADS) k_fwd_f32(Work w) {
 }
 
 cudaError_t launch_fwd_f32(const Work& w, int n, int max_tiles, int any_tag, int any_cols, cudaStream_t s) {
-    dim3 grid(max_tiles, n);
+    const unsigned grid = (unsigned)n * (unsigned)w.max_tiles;   // decoded with w.max_tiles
     if (any_tag && any_cols) k_fwd_f32<true, true><<<grid, F32_THREADS, 0, s>>>(w);
     else if (any_tag) k_fwd_f32<true, false><<<grid, F32_THREADS, 0, s>>>(w);
     else if (any_cols) k_fwd_f32<false, true><<<grid, F32_THREADS, 0, s>>>(w);

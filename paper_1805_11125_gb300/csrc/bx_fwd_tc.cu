@@ -90,7 +90,8 @@ __device__ __forceinline__ void issue_kblock(uint32_t dslot, const float* Rhi, c
 __global__ void __launch_bounds__(TM, 3) k_fwd_tc(Work w) {
     extern __shared__ unsigned char smem_raw[];
     SmemTC& sm = *reinterpret_cast<SmemTC*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    const int tile = blockIdx.x, item = blockIdx.y, tid = threadIdx.x, warp = tid >> 5;
+    // 1D item-major grid (a y dimension would cap the batch at 65535 items)
+    const int tile = blockIdx.x % w.max_tiles, item = blockIdx.x / w.max_tiles, tid = threadIdx.x, warp = tid >> 5;
     const Toy& T = w.toys[w.toy_of[item]];
     if (tile >= T.n_tiles || w.status[item]) return;
     const int m0 = tile * TM, M = T.M;
@@ -234,7 +235,7 @@ cudaError_t launch_fwd_tc(const Work& w, int n, int max_tiles, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    dim3 grid(max_tiles, n);
+    const unsigned grid = (unsigned)n * (unsigned)w.max_tiles;   // decoded with w.max_tiles
     k_fwd_tc<<<grid, TM, smem, s>>>(w);
     return cudaGetLastError();
 }

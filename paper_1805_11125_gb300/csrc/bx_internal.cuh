@@ -81,7 +81,7 @@ struct Col64 {
 
 // Workspace of a model: every array has `cap` item slots.
 struct Work {
-    int cap, Npad, Mpad, nbmax, pstride, n_items, max_tiles;
+    int cap, Npad, Mpad, nbmax, pstride, n_items, max_tiles, max_cb;
     int precision;
     double band;
     unsigned long long watchdog_ns;
