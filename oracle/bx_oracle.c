@@ -24,6 +24,14 @@
  *         mu_h[m] = (1 - eps) lambda_h[m] + eps sum_{d=0}^{min(m, L-1)} g[d] lambda_h[m-d]
  *   a6  -lnL = sum over all bins of  mu - n + n ln(n / mu)   (n ln(n/mu) := 0 at n = 0),
  *       summed with Neumaier compensation                     (Eq. 3, Eq. 4)
+ *   2D  (the discrimination regime: Eq. 4's radial and pulse-shape information as 2D
+ *       energy x radius and energy x pulse-shape histograms instead of 1D marginals;
+ *       reading: templates s_k[i] q_k[b] (1 + amp u[i,b]) with the caller's smooth field u,
+ *       normalised per species over each slice set)
+ *         T_r[i,b] = sum_k r_k (1 - t_k) s_k[i] q_k[b] (1 + amp u[i,b]) / N_k(set of b)
+ *         Y[m,b]   = sum_i R[m,i] T_r[i,b],  then Eq. 2 on every slice b
+ *       with q_k[b] the radial bin probability of slice b (internal / external as for the
+ *       radial term) or the pulse-shape bin probability.
  *
  * Gradients come from forward-mode dual numbers carried through the same definition
  * (independent of any hand-written adjoint).  The fit is a damped Newton iteration on
@@ -87,6 +95,12 @@ typedef struct {
     const double* n_rad_counts;        /* [n_rad] */
     int n_psd; const double* psd_prob; /* [K][n_psd]; n_psd = 0 -> none */
     const double* n_psd_counts;        /* [n_psd] */
+    int n_r2, n_p2;                    /* 2D slices: radial (uses rad_class), pulse shape */
+    const double* field;               /* [n_grid][n_r2 + n_p2] */
+    double amp;
+    const double* psd2;                /* [K][n_p2] */
+    const double* n_r2_counts;         /* [n_r2][m_hi - m_lo] */
+    const double* n_p2_counts;         /* [n_p2][m_hi - m_lo] */
 } om_model;
 
 enum { OM_OK = 0, OM_EINVAL = -1, OM_ENOMEM = -2, OM_EDOMAIN = -4, OM_ENOTCONV = -6 };
@@ -95,12 +109,16 @@ int om_n_params(const om_model* m) { return m->K + 7; }
 
 int om_n_bins(const om_model* m) {
     int nw = m->m_hi - m->m_lo;
-    return nw + (m->tag_frac ? nw : 0) + (m->n_rad > 0 && m->rad_class ? m->n_rad : 0) + (m->n_psd > 0 && m->psd_prob ? m->n_psd : 0);
+    return nw + (m->tag_frac ? nw : 0) + (m->n_rad > 0 && m->rad_class ? m->n_rad : 0) + (m->n_psd > 0 && m->psd_prob ? m->n_psd : 0) +
+           (m->n_r2 + m->n_p2) * nw;
 }
 
 static int check_model(const om_model* m) {
     if (!m || m->n_grid < 1 || m->K < 1 || m->K + 7 > OPMAX || m->L < 1 || m->width <= 0 ||
         m->m_lo < 0 || m->m_hi <= m->m_lo || !m->shapes || !m->stop_pow || !m->pileup)
+        return OM_EINVAL;
+    if (m->n_r2 < 0 || m->n_p2 < 0 || (m->n_r2 + m->n_p2 > 0 && !m->field) || (m->n_r2 > 0 && !m->rad_class) ||
+        (m->n_p2 > 0 && !m->psd2))
         return OM_EINVAL;
     return OM_OK;
 }
@@ -125,14 +143,14 @@ static void gauss_legendre(int n, double* x, double* w) {
  * volume, external density exp(-(R_iv - r) / (att_len * s_r)) in a fiducial sphere of
  * radius r_fid): p[rho] = int_{bin} r^2 f(r) dr / int_0^{r_fid} r^2 f(r) dr, integrals by
  * 24-point Gauss-Legendre per bin. */
-static void radial_probs(const om_model* m, dual s_r, int cls, dual* p) {
+static void radial_probs_n(const om_model* m, int nbins, dual s_r, int cls, dual* p) {
     enum { NGL = 24 };
     double gx[NGL], gw[NGL];
     gauss_legendre(NGL, gx, gw);
     dual lam = dscale(s_r, m->att_len);
     dual tot = dc(0.0);
-    double h = m->r_fid / m->n_rad;
-    for (int b = 0; b < m->n_rad; ++b) {
+    double h = m->r_fid / nbins;
+    for (int b = 0; b < nbins; ++b) {
         dual acc = dc(0.0);
         double c0 = (b + 0.5) * h;
         for (int q = 0; q < NGL; ++q) {
@@ -144,8 +162,9 @@ static void radial_probs(const om_model* m, dual s_r, int cls, dual* p) {
         p[b] = acc;
         tot = dadd(tot, acc);
     }
-    for (int b = 0; b < m->n_rad; ++b) p[b] = ddiv(p[b], tot);
+    for (int b = 0; b < nbins; ++b) p[b] = ddiv(p[b], tot);
 }
+static void radial_probs(const om_model* m, dual s_r, int cls, dual* p) { radial_probs_n(m, m->n_rad, s_r, cls, p); }
 
 /* Neumaier-compensated accumulator on every dual component */
 typedef struct { dual s, c; } nsum;
@@ -199,13 +218,15 @@ static int stage_a1(const om_model* m, const dual* th, work* w) {
     return st;
 }
 
-/* a2 + a3: v_k[m] = sum_i R[m,i] s_k[i] for every m in [0, m_hi). */
-static void stage_a23(const om_model* m, work* w, double* R_out) {
-    int N = m->n_grid, K = m->K, M = m->m_hi;
+/* a2 + a3: v_k[m] = sum_i R[m,i] s_k[i] for every m in [0, m_hi); with 2D slices also
+ * Y[m][b] = sum_i R[m,i] T_r[i][b] (T_r: [N][B2], Y: [M][B2]). */
+static void stage_a23(const om_model* m, work* w, double* R_out, const dual* Tr, dual* Y) {
+    int N = m->n_grid, K = m->K, M = m->m_hi, B2 = m->n_r2 + m->n_p2;
     #pragma omp parallel for schedule(dynamic, 4)
     for (int r = 0; r < M; ++r) {
         dual* vr = w->v + (size_t)r * K;
         for (int k = 0; k < K; ++k) vr[k] = dc(0.0);
+        if (Y) for (int b = 0; b < B2; ++b) Y[(size_t)r * B2 + b] = dc(0.0);
         for (int i = 0; i < N; ++i) {
             dual za = ddiv(dsub(dc(r * m->width), w->mu[i]), w->sig[i]);
             dual zb = ddiv(dsub(dc((r + 1) * m->width), w->mu[i]), w->sig[i]);
@@ -215,8 +236,43 @@ static void stage_a23(const om_model* m, work* w, double* R_out) {
                 double s = m->shapes[(size_t)k * N + i];
                 if (s != 0.0) daxpy(&vr[k], s, &R);
             }
+            if (Y)
+                for (int b = 0; b < B2; ++b) dacc(&Y[(size_t)r * B2 + b], dmul(R, Tr[(size_t)i * B2 + b]));
         }
     }
+}
+
+/* 2D templates, rate-weighted: T_r[i][b] = sum_k r_k (1 - t_k) s_k[i] q_k[b] (1 + amp u[i][b]) / N_k,
+ * N_k = sum_i sum_{b in the set of b} s_k[i] q_k[b] (1 + amp u[i][b]) (radial set, pulse-shape set). */
+static int stage_2d_templates(const om_model* m, const dual* th, dual* Tr) {
+    int N = m->n_grid, K = m->K, nR = m->n_r2, nP = m->n_p2, B2 = nR + nP;
+    dual* q = calloc((size_t)B2, sizeof(dual));
+    if (!q) return OM_ENOMEM;
+    for (size_t j = 0; j < (size_t)N * B2; ++j) Tr[j] = dc(0.0);
+    for (int k = 0; k < K; ++k) {
+        if (nR > 0) radial_probs_n(m, nR, th[K + 6], m->rad_class[k], q);
+        for (int j = 0; j < nP; ++j) q[nR + j] = dc(m->psd2[(size_t)k * nP + j]);
+        dual NR = dc(0.0), NPs = dc(0.0);
+        for (int i = 0; i < N; ++i) {
+            double s = m->shapes[(size_t)k * N + i];
+            for (int b = 0; b < B2; ++b) {
+                dual t = dscale(q[b], s * (1.0 + m->amp * m->field[(size_t)i * B2 + b]));
+                if (b < nR) dacc(&NR, t); else dacc(&NPs, t);
+            }
+        }
+        double ck = m->tag_frac ? 1.0 - m->tag_frac[k] : 1.0;
+        dual fR = nR > 0 ? ddiv(dscale(th[k], ck), NR) : dc(0.0);
+        dual fP = nP > 0 ? ddiv(dscale(th[k], ck), NPs) : dc(0.0);
+        for (int b = 0; b < B2; ++b) {
+            dual coef = dmul(b < nR ? fR : fP, q[b]);
+            for (int i = 0; i < N; ++i) {
+                double x = m->shapes[(size_t)k * N + i] * (1.0 + m->amp * m->field[(size_t)i * B2 + b]);
+                if (x != 0.0) daxpy(&Tr[(size_t)i * B2 + b], x, &coef);
+            }
+        }
+    }
+    free(q);
+    return OM_OK;
 }
 
 /* a5 on one spectrum x[0..M): y[j] = (1-eps) x[m] + eps sum_{d=0}^{min(m,L-1)} g[d] x[m-d], m = m_lo + j */
@@ -248,11 +304,18 @@ static int evaluate(const om_model* m, const double* theta, int want_grad,
     dual* lam = calloc(M, sizeof(dual));
     dual* A = calloc(K, sizeof(dual));
     dual* tmp = calloc(nw, sizeof(dual));
-    if (!w.Q || !w.mu || !w.sig || !w.den || !w.v || !mu || !lam || !A || !tmp) { st = OM_ENOMEM; goto done; }
+    const int B2 = m->n_r2 + m->n_p2;
+    dual* Tr = B2 > 0 ? calloc((size_t)N * B2, sizeof(dual)) : NULL;
+    dual* Y = B2 > 0 ? calloc((size_t)M * B2, sizeof(dual)) : NULL;
+    if (!w.Q || !w.mu || !w.sig || !w.den || !w.v || !mu || !lam || !A || !tmp || (B2 > 0 && (!Tr || !Y))) {
+        st = OM_ENOMEM;
+        goto done;
+    }
 
     st = stage_a1(m, th, &w);
     if (st) goto done;
-    stage_a23(m, &w, NULL);
+    if (B2 > 0 && (st = stage_2d_templates(m, th, Tr))) goto done;
+    stage_a23(m, &w, NULL, Tr, Y);
 
     /* a4 + a5 for the energy spectra */
     int o = 0;
@@ -297,15 +360,22 @@ static int evaluate(const om_model* m, const double* theta, int want_grad,
         }
         o += m->n_psd;
     }
+    /* 2D slices: Eq. 2 on every slice of Y, slice-major */
+    for (int b = 0; b < B2; ++b) {
+        pileup_window(m, eps, Y + b, B2, mu + o);
+        o += nw;
+    }
     if (mu_out) for (int j = 0; j < nb; ++j) mu_out[j] = mu[j].v;
 
     /* a6 */
     if (nll_out) {
-        const double* cnt[4]; int len[4]; int nh = 0;
+        const double* cnt[6]; int len[6]; int nh = 0;
         cnt[nh] = m->n_sub; len[nh++] = nw;
         if (m->tag_frac) { cnt[nh] = m->n_tag; len[nh++] = nw; }
         if (has_rad) { cnt[nh] = m->n_rad_counts; len[nh++] = m->n_rad; }
         if (has_psd) { cnt[nh] = m->n_psd_counts; len[nh++] = m->n_psd; }
+        if (m->n_r2 > 0) { cnt[nh] = m->n_r2_counts; len[nh++] = m->n_r2 * nw; }
+        if (m->n_p2 > 0) { cnt[nh] = m->n_p2_counts; len[nh++] = m->n_p2 * nw; }
         nsum acc; acc.s = dc(0.0); acc.c = dc(0.0);
         int jj = 0, dom = 0;
         for (int h = 0; h < nh; ++h)
@@ -322,7 +392,7 @@ static int evaluate(const om_model* m, const double* theta, int want_grad,
         }
     }
 done:
-    work_free(&w); free(mu); free(lam); free(A); free(tmp);
+    work_free(&w); free(mu); free(lam); free(A); free(tmp); free(Tr); free(Y);
     return st;
 }
 
@@ -369,7 +439,7 @@ int om_response(const om_model* m, const double* theta, double* R, double* v) {
     w.den = calloc(N, sizeof(dual)); w.v = calloc((size_t)M * K, sizeof(dual));
     st = stage_a1(m, th, &w);
     if (!st) {
-        stage_a23(m, &w, R);
+        stage_a23(m, &w, R, NULL, NULL);
         if (v) for (size_t j = 0; j < (size_t)M * K; ++j) v[j] = w.v[j].v;
     }
     work_free(&w);

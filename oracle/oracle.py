@@ -10,7 +10,8 @@ Functions follow the paper's steps (arXiv:1805.11125 Sec. 3):
 ``quench`` (Eq. 1 parameters), ``response`` (Eq. 1), ``pileup`` (Eq. 2),
 ``expected`` (Eq. 1-4 expected counts), ``nll`` (Eq. 3-4 with dual-number gradient),
 ``poisson_nll`` (the binned Poisson sum alone), ``radial`` (Eq. 4 radial term) and
-``fit`` (the minimisation of Sec. 4).
+``fit`` (the minimisation of Sec. 4).  Models with 2D energy x radius / energy x pulse-shape
+histograms (the discrimination regime) are evaluated through the same entry points.
 """
 from __future__ import annotations
 
@@ -56,6 +57,8 @@ class _Model(C.Structure):
         ("r_fid", C.c_double), ("r_iv", C.c_double), ("att_len", C.c_double),
         ("n_rad_counts", C.c_void_p),
         ("n_psd", C.c_int), ("psd_prob", C.c_void_p), ("n_psd_counts", C.c_void_p),
+        ("n_r2", C.c_int), ("n_p2", C.c_int), ("field", C.c_void_p), ("amp", C.c_double),
+        ("psd2", C.c_void_p), ("n_r2_counts", C.c_void_p), ("n_p2_counts", C.c_void_p),
     ]
 
 
@@ -97,6 +100,8 @@ class OracleModel:
             "psd_prob": _arr(s.psd_prob),
             "n_sub": _arr(s.counts.get("sub")), "n_tag": _arr(s.counts.get("tag")),
             "n_rad": _arr(s.counts.get("rad")), "n_psd": _arr(s.counts.get("psd")),
+            "field": _arr(s.field2d), "psd2": _arr(s.psd2d_prob),
+            "n_r2": _arr(s.counts.get("r2d")), "n_p2": _arr(s.counts.get("p2d")),
         }
         k = self._keep
         has_rad = s.rad_class is not None and s.n_rad > 0
@@ -106,7 +111,9 @@ class OracleModel:
             m_lo=s.m_lo, m_hi=s.m_hi, n_sub=_ptr(k["n_sub"]), n_tag=_ptr(k["n_tag"]),
             n_rad=s.n_rad if has_rad else 0, rad_class=_ptr(k["rad_class"]), r_fid=s.r_fid,
             r_iv=s.r_iv, att_len=s.att_len, n_rad_counts=_ptr(k["n_rad"]),
-            n_psd=s.n_psd, psd_prob=_ptr(k["psd_prob"]), n_psd_counts=_ptr(k["n_psd"]))
+            n_psd=s.n_psd, psd_prob=_ptr(k["psd_prob"]), n_psd_counts=_ptr(k["n_psd"]),
+            n_r2=s.n_rad2d, n_p2=s.n_psd2d, field=_ptr(k["field"]), amp=s.field_amp, psd2=_ptr(k["psd2"]),
+            n_r2_counts=_ptr(k["n_r2"]), n_p2_counts=_ptr(k["n_p2"]))
         self.ref = C.byref(self.c)
 
     @property

@@ -70,6 +70,12 @@ class ModelSpec:
     r_iv: float = 4.25
     att_len: float = 0.3
     psd_prob: Optional[np.ndarray] = None   # [K, n_psd]; None -> no PSD term
+    # 2D histograms (energy x radius, energy x pulse shape): n_rad2d / n_psd2d slices of the
+    # energy window each, templates s_k[i] q_k[b] (1 + field_amp u[i, b]) per slice set
+    n_rad2d: int = 0                        # radial slices (uses rad_class, r_fid, r_iv, att_len)
+    psd2d_prob: Optional[np.ndarray] = None  # [K, n_psd2d] pulse-shape bin probabilities
+    field2d: Optional[np.ndarray] = None     # [n_grid, n_rad2d + n_psd2d] smooth field u in [-1, 1]
+    field_amp: float = 0.0
     theta_true: Optional[np.ndarray] = None
     species: List[str] = dataclasses.field(default_factory=list)
     counts: Dict[str, np.ndarray] = dataclasses.field(default_factory=dict)
@@ -94,6 +100,14 @@ class ModelSpec:
     def n_psd(self) -> int:
         return 0 if self.psd_prob is None else int(self.psd_prob.shape[1])
 
+    @property
+    def n_psd2d(self) -> int:
+        return 0 if self.psd2d_prob is None else int(self.psd2d_prob.shape[1])
+
+    @property
+    def n_slices2d(self) -> int:
+        return self.n_rad2d + self.n_psd2d
+
     def hist_sizes(self) -> Dict[str, int]:
         """Histogram names and bin counts, in the order every evaluator concatenates them."""
         out = {"sub": self.n_window}
@@ -103,6 +117,10 @@ class ModelSpec:
             out["rad"] = self.n_rad
         if self.psd_prob is not None:
             out["psd"] = self.n_psd
+        if self.n_rad2d > 0:
+            out["r2d"] = self.n_rad2d * self.n_window    # slice-major: [rho][window bin]
+        if self.n_psd2d > 0:
+            out["p2d"] = self.n_psd2d * self.n_window    # slice-major: [j][window bin]
         return out
 
     @property
@@ -114,7 +132,7 @@ class ModelSpec:
 
     def default_free(self) -> np.ndarray:
         free = np.ones(self.P, dtype=np.uint8)
-        if self.rad_class is None or self.n_rad == 0:
+        if self.rad_class is None or (self.n_rad == 0 and self.n_rad2d == 0):
             free[self.K + PARAM_TAIL.index("s_r")] = 0
         return free
 
@@ -188,6 +206,21 @@ def pileup_spectrum(L: int, width: float) -> np.ndarray:
     x = np.arange(L) * width
     g = np.exp(-x / 30.0) + 0.1 * np.exp(-((x - 100.0) ** 2) / (2 * 20.0 ** 2))
     return g / g.sum()
+
+
+def smooth_field(n_grid: int, n_cols: int, seed: int = 0, n_modes: int = 4) -> np.ndarray:
+    """Seeded smooth field u[i, b] in [-1, 1] on (true-energy point, slice): a sum of a few
+    low-frequency products of cosines with random phases, scaled to max |u| = 1.  It makes
+    the 2D templates non-separable in (energy, slice)."""
+    rng = np.random.default_rng([MASTER_SEED, 21, seed])
+    x = (np.arange(n_grid) + 0.5) / n_grid
+    y = (np.arange(n_cols) + 0.5) / max(n_cols, 1)
+    u = np.zeros((n_grid, n_cols))
+    for _ in range(n_modes):
+        fx, fy = rng.uniform(0.5, 3.0), rng.uniform(0.5, 3.0)
+        px, py, a = rng.uniform(0, 2 * np.pi), rng.uniform(0, 2 * np.pi), rng.uniform(0.5, 1.0)
+        u += a * np.cos(2 * np.pi * fx * x + px)[:, None] * np.cos(2 * np.pi * fy * y + py)[None, :]
+    return u / np.abs(u).max()
 
 
 def psd_template(n_psd: int, mean: float, sig: float = 0.08) -> np.ndarray:
@@ -279,14 +312,42 @@ def multivariate(n_grid=2000, e_max=3.0, width=1.0, lo_npe=100.0, hi_npe=1000.0,
     return spec
 
 
+def discrimination(n_grid=2000, e_max=3.0, width=1.0, lo_npe=100.0, hi_npe=1000.0,
+                   n_species=15, total=2e6, L=400, n_rad2d=60, n_psd2d=50, tag_eff=0.9, amp=0.05,
+                   seed=0, name="discrimination") -> ModelSpec:
+    """TFC-subtracted + TFC-tagged energy spectra and the 2D energy x radius and energy x
+    pulse-shape histograms of the TFC-subtracted events (the discrimination regime)."""
+    names, shapes, is_ext, is_bp = species_library(n_grid, e_max, seed)
+    rng = np.random.default_rng([MASTER_SEED, 3, seed])
+    E = grid_energies(n_grid, e_max)
+    K = n_species
+    m_lo, m_hi = int(round(lo_npe / width)), int(round(hi_npe / width))
+    tag = np.where(is_bp[:K], tag_eff, 0.1)
+    psd = np.stack([psd_template(n_psd2d, 0.55 if bp else 0.35) for bp in is_bp[:K]])
+    spec = ModelSpec(name=name, n_grid=n_grid, e_max=e_max,
+                     shapes=np.ascontiguousarray(shapes[:K]), stop_pow=stopping_power(E),
+                     pileup=pileup_spectrum(L, width), width=width, m_lo=m_lo, m_hi=m_hi,
+                     tag_frac=tag.astype(np.float64),
+                     rad_class=np.where(is_ext[:K], RAD_EXTERNAL, RAD_INTERNAL).astype(np.int32),
+                     n_rad2d=n_rad2d, psd2d_prob=np.ascontiguousarray(psd),
+                     field2d=np.ascontiguousarray(smooth_field(n_grid, n_rad2d + n_psd2d, seed)),
+                     field_amp=amp, species=names[:K])
+    spec.theta_true = _theta(_rates(rng, K, total))
+    return spec
+
+
 def config(name: str) -> ModelSpec:
     """The named workloads.
 
     * ``plain``        K=8 single spectrum, 400 bins of 2 npe over 150-950 npe, 1e6 events.
     * ``multivariate`` K=15, TFC-subtracted/tagged 900 bins of 1 npe over 100-1000 npe,
                        60 radial bins, 50 pulse-shape bins, 22 parameters, 2e6 events.
-    * ``small_plain`` / ``small_mv`` reduced grids that the oracle evaluates in well under a
-      second but that still span several 128-row tiles and ragged tails.
+    * ``discrimination`` K=15, TFC-subtracted/tagged 900 bins of 1 npe over 100-1000 npe and
+                       the 2D energy x radius (900 x 60) and energy x pulse-shape (900 x 50)
+                       histograms, 22 parameters, 2e6 events.
+    * ``small_plain`` / ``small_mv`` / ``small_2d`` reduced grids that the oracle evaluates in
+      well under a second (a few seconds for ``small_2d``) but that still span several
+      128-row tiles and ragged tails.
     """
     if name == "plain":
         return single_spectrum(name=name)
@@ -295,6 +356,11 @@ def config(name: str) -> ModelSpec:
     if name == "small_plain":
         return single_spectrum(n_grid=600, width=4.0, lo_npe=160.0, hi_npe=1100.0,
                                n_species=5, total=2e5, L=100, name=name)
+    if name == "discrimination":
+        return discrimination(name=name)
+    if name == "small_2d":
+        return discrimination(n_grid=520, width=3.0, lo_npe=120.0, hi_npe=900.0, n_species=9,
+                              total=3e5, L=90, n_rad2d=12, n_psd2d=10, name=name)
     if name == "small_mv":
         return multivariate(n_grid=520, width=3.0, lo_npe=120.0, hi_npe=900.0, n_species=9,
                             total=3e5, L=90, n_rad=20, n_psd=16, name=name)

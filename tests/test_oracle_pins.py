@@ -329,3 +329,68 @@ def test_fit_normalisation_invariant_at_optimum():
     assert np.all(r["theta"][:s.K] > 0)
     mu = O.expected(s, r["theta"])
     assert mu.sum() == pytest.approx(s.counts_vector().sum(), rel=1e-9)
+
+
+# ------------------------------------------------------------- 2D histograms (discrimination)
+
+def _split_2d(s, mu):
+    nw = s.n_window
+    o = {}
+    off = 0
+    for h, n in s.hist_sizes().items():
+        o[h] = mu[off:off + n]
+        off += n
+    return o["sub"], o["r2d"].reshape(s.n_rad2d, nw), o["p2d"].reshape(s.n_psd2d, nw)
+
+
+def test_2d_without_field_marginalises_to_the_vetoed_spectrum():
+    """With amp = 0 the templates factorise, sum_b q_k[b] = 1 and N_k = 1: summed over its
+    radial (or pulse-shape) slices the 2D histogram is the TFC-vetoed energy spectrum, bin by bin."""
+    s = dataclasses.replace(I.config("small_2d"), field_amp=0.0)
+    sub, r2, p2 = _split_2d(s, O.expected(s, s.theta_true))
+    np.testing.assert_allclose(r2.sum(axis=0), sub, rtol=1e-12)
+    np.testing.assert_allclose(p2.sum(axis=0), sub, rtol=1e-12)
+
+
+def test_2d_without_field_marginalises_to_the_eq4_terms():
+    """With amp = 0, summed over the energy window the 2D histograms are the Eq. 4 radial and
+    pulse-shape terms of the same species (the already pinned 1D marginal model)."""
+    s2 = dataclasses.replace(I.config("small_2d"), field_amp=0.0)
+    _, r2, p2 = _split_2d(s2, O.expected(s2, s2.theta_true))
+    s1 = dataclasses.replace(s2, n_rad2d=0, psd2d_prob=None, field2d=None, n_rad=s2.n_rad2d,
+                             psd_prob=s2.psd2d_prob)
+    mu1 = O.expected(s1, s2.theta_true)
+    nw = s1.n_window
+    rad, psd = mu1[2 * nw:2 * nw + s1.n_rad], mu1[2 * nw + s1.n_rad:]
+    np.testing.assert_allclose(r2.sum(axis=1), rad, rtol=1e-9)
+    np.testing.assert_allclose(p2.sum(axis=1), psd, rtol=1e-9)
+
+
+def test_2d_field_is_non_separable_and_normalised():
+    """The field makes the slices differ in energy shape (a true dense contraction), while
+    each species keeps its total: the 2D spectra are linear in the rates."""
+    s = I.config("small_2d")
+    _, r2, _ = _split_2d(s, O.expected(s, s.theta_true))
+    s0 = dataclasses.replace(s, field_amp=0.0)
+    _, r20, _ = _split_2d(s0, O.expected(s0, s.theta_true))
+    ratio = r2 / r20
+    assert np.ptp(ratio[:, 100:200], axis=1).max() > 1e-3     # energy dependence differs per slice
+    th2 = s.theta_true.copy()
+    th2[:s.K] *= 1.7
+    _, r2b, p2b = _split_2d(s, O.expected(s, th2))
+    np.testing.assert_allclose(r2b, 1.7 * r2, rtol=1e-12)
+
+
+def test_2d_dual_gradient_matches_central_differences():
+    s = I.config("small_2d")
+    s = s.with_counts(I.poisson_counts(O.expected(s, s.theta_true), 13))
+    th = I.parameter_points(s.theta_true, 1, rel=0.02, seed=15)[0]
+    f, g = O.nll(s, th, grad=True)
+    gfd = np.zeros_like(g)
+    for j in range(s.P):
+        h = 1e-5 * abs(th[j])
+        tp, tm = th.copy(), th.copy()
+        tp[j] += h; tm[j] -= h
+        gfd[j] = (O.nll(s, tp) - O.nll(s, tm)) / (2 * h)
+    scale = np.abs(g * th)
+    np.testing.assert_allclose(g * th, gfd * th, rtol=2e-6, atol=2e-7 * scale.max())
