@@ -89,6 +89,21 @@ typedef struct {
     int n_psd;                  /* pulse-shape bins, 0 = no pulse-shape term */
     const double* psd_prob;     /* [K][n_psd] bin probabilities of each species */
     const double* counts_psd;   /* [n_psd] */
+    /* 2D histograms of the TFC-vetoed events (the discrimination regime: Eq. 4's radial
+     * and pulse-shape information binned against energy instead of as 1D marginals).
+     * Slice b of the 2D energy x radius histogram is the energy window of the events in
+     * radial bin b (rad_class and the radial geometry as for n_rad), likewise for pulse
+     * shape.  Species templates s_k[i] q_k[b] (1 + field_amp u[i][b]), normalised per
+     * species over each slice set; Eq. 2 on every slice.  Requires BX_FP32, n_rad = n_psd = 0
+     * and n_rad2d + n_psd2d + 1 + (tag_frac != NULL) <= 128 slices; all toys of a model
+     * are either 2D or not. */
+    int n_rad2d;                /* radial slices over [0, r_fid) (0: no energy x radius histogram) */
+    int n_psd2d;                /* pulse-shape slices (0: no energy x pulse-shape histogram) */
+    const double* psd2d_prob;   /* [K][n_psd2d] pulse-shape bin probabilities */
+    const double* field2d;      /* [N][n_rad2d + n_psd2d] template modulation u, |u| <= 1 */
+    double field_amp;           /* 0 <= field_amp < 1 */
+    const double* counts_rad2d; /* [n_rad2d][m_hi - m_lo] */
+    const double* counts_psd2d; /* [n_psd2d][m_hi - m_lo] */
 } bx_model_desc;
 
 typedef struct {
@@ -107,7 +122,7 @@ void bx_model_destroy(bx_model* model);
 int bx_model_set_stream(bx_model* model, void* cuda_stream);
 /* P = 7 + max_t K_t: the row stride of every theta / grad array */
 int bx_model_n_params(const bx_model* model);
-/* bins of toy t: window (+ window if tagged) + n_rad + n_psd */
+/* bins of toy t: window (+ window if tagged) + n_rad + n_psd + (n_rad2d + n_psd2d) window */
 int bx_model_n_bins(const bx_model* model, int toy);
 /* Sticky device status (BX_OK or BX_ETIMEOUT) after synchronising the model's stream. */
 int bx_model_status(bx_model* model);

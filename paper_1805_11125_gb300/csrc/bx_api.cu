@@ -88,6 +88,26 @@ static int validate_desc(const bx_model_desc& d, int t) {
         REQ(d.r_fid > 0.0 && d.r_iv >= d.r_fid && d.att_len > 0.0, "toy %d: radial geometry invalid", t);
     }
     REQ(d.n_psd >= 0 && d.n_psd <= MAX_PSD, "toy %d: n_psd out of [0, %d]", t, MAX_PSD);
+    REQ(d.n_rad2d >= 0 && d.n_psd2d >= 0, "toy %d: n_rad2d, n_psd2d must be >= 0", t);
+    if (d.n_rad2d + d.n_psd2d > 0) {
+        const int n_sl = 1 + (d.tag_frac ? 1 : 0) + d.n_rad2d + d.n_psd2d;
+        REQ(n_sl <= NSL, "toy %d: %d slices (TFC spectra + 2D) exceed %d", t, n_sl, NSL);
+        REQ(d.n_rad == 0 && d.n_psd == 0, "toy %d: 2D histograms replace the n_rad / n_psd terms", t);
+        REQ(d.field2d && std::isfinite(d.field_amp) && d.field_amp >= 0.0 && d.field_amp < 1.0,
+            "toy %d: 2D histograms need field2d and 0 <= field_amp < 1", t);
+        for (size_t j = 0; j < (size_t)d.n_grid * (d.n_rad2d + d.n_psd2d); ++j)
+            REQ(std::isfinite(d.field2d[j]) && std::fabs(d.field2d[j]) <= 1.0, "toy %d: field2d must lie in [-1, 1]", t);
+        if (d.n_rad2d > 0) {
+            REQ(d.rad_class && d.counts_rad2d && finite_nonneg(d.counts_rad2d, (size_t)d.n_rad2d * nw),
+                "toy %d: energy x radius histogram needs rad_class and counts_rad2d", t);
+            for (int k = 0; k < d.n_species; ++k) REQ(d.rad_class[k] == 0 || d.rad_class[k] == 1, "toy %d: rad_class[%d] must be 0 or 1", t, k);
+            REQ(d.r_fid > 0.0 && d.r_iv >= d.r_fid && d.att_len > 0.0, "toy %d: radial geometry invalid", t);
+        }
+        if (d.n_psd2d > 0)
+            REQ(d.psd2d_prob && d.counts_psd2d && finite_nonneg(d.psd2d_prob, (size_t)d.n_species * d.n_psd2d) &&
+                    finite_nonneg(d.counts_psd2d, (size_t)d.n_psd2d * nw),
+                "toy %d: energy x pulse-shape histogram needs psd2d_prob and counts_psd2d", t);
+    }
     if (d.n_psd > 0)
         REQ(d.psd_prob && d.counts_psd && finite_nonneg(d.psd_prob, (size_t)d.n_species * d.n_psd) &&
                 finite_nonneg(d.counts_psd, d.n_psd),
@@ -145,10 +165,14 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
     if (o.watchdog_s == 0.0) o.watchdog_s = 2.0;
     if (!(o.band_sigmas >= 3.0 && o.band_sigmas <= 40.0)) return bx_set_error(BX_EINVAL, "band_sigmas out of [3, 40]");
     if (!(o.watchdog_s > 0.0 && o.watchdog_s <= 600.0)) return bx_set_error(BX_EINVAL, "watchdog_s out of (0, 600]");
+    int n2d = 0;
     for (int t = 0; t < n_toys; ++t) {
         int st = validate_desc(descs[t], t);
         if (st) return st;
+        n2d += descs[t].n_rad2d + descs[t].n_psd2d > 0 ? 1 : 0;
     }
+    if (n2d != 0 && n2d != n_toys) return bx_set_error(BX_EINVAL, "toys of one model are either all 2D or none");
+    if (n2d && o.precision != BX_FP32) return bx_set_error(BX_EINVAL, "2D histograms need BX_FP32");
     int dev = 0;
     CU(cudaGetDevice(&dev));
     int cc_major = 0, cc_minor = 0;
@@ -192,7 +216,11 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
         T.n_rad = d.n_rad;
         T.n_psd = d.n_psd;
         T.has_tag = d.tag_frac ? 1 : 0;
-        T.nb = T.nw * (1 + T.has_tag) + T.n_rad + T.n_psd;
+        T.n_r2 = d.n_rad2d;
+        T.n_p2 = d.n_psd2d;
+        T.b_r2 = 1 + T.has_tag;
+        T.n_sl = (T.n_r2 + T.n_p2 > 0) ? T.b_r2 + T.n_r2 + T.n_p2 : 0;
+        T.nb = T.nw * (1 + T.has_tag) + T.n_rad + T.n_psd + (T.n_r2 + T.n_p2) * T.nw;
         T.P = T.K + 7;
         T.n_tiles = (T.M + TM - 1) / TM;
         T.n_cb = (T.N + BCOLS - 1) / BCOLS;
@@ -207,6 +235,8 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
         if (T.has_tag) cnt.insert(cnt.end(), d.counts_tag, d.counts_tag + T.nw);
         if (T.n_rad) cnt.insert(cnt.end(), d.counts_rad, d.counts_rad + T.n_rad);
         if (T.n_psd) cnt.insert(cnt.end(), d.counts_psd, d.counts_psd + T.n_psd);
+        if (T.n_r2) cnt.insert(cnt.end(), d.counts_rad2d, d.counts_rad2d + (size_t)T.n_r2 * T.nw);
+        if (T.n_p2) cnt.insert(cnt.end(), d.counts_psd2d, d.counts_psd2d + (size_t)T.n_p2 * T.nw);
         if ((st = upload(m, d.shapes, (size_t)T.K * T.N, &T.shapes))) break;
         if ((st = upload(m, d.stop_pow, (size_t)T.N, &T.stop_pow))) break;
         if ((st = upload(m, d.tag_frac, (size_t)T.K, &T.tag))) break;
@@ -214,6 +244,24 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
         if ((st = upload(m, cnt.data(), cnt.size(), &T.cnt))) break;
         if ((st = upload(m, T.n_rad ? d.rad_class : nullptr, (size_t)T.K, &T.rad_class))) break;
         if ((st = upload(m, T.n_psd ? d.psd_prob : nullptr, (size_t)T.K * T.n_psd, &T.psd))) break;
+        if (T.n_sl) {
+            // template modulation per (column, slice) and its per-species column sums
+            std::vector<float> ut((size_t)T.N * NSL, 0.f);
+            std::vector<double> U2((size_t)T.K * NSL, 0.0);
+            const int B2 = T.n_r2 + T.n_p2;
+            for (int i = 0; i < T.N; ++i)
+                for (int b = 0; b < T.n_sl; ++b) {
+                    const double u = b < T.b_r2 ? 1.0 : 1.0 + d.field_amp * d.field2d[(size_t)i * B2 + (b - T.b_r2)];
+                    ut[(size_t)i * NSL + b] = (float)u;
+                    for (int k = 0; k < T.K; ++k) U2[(size_t)k * NSL + b] += d.shapes[(size_t)k * T.N + i] * u;
+                }
+            if ((st = upload(m, ut.data(), ut.size(), &T.ut))) break;
+            if ((st = upload(m, U2.data(), U2.size(), &T.U2))) break;
+            if ((st = upload(m, T.n_p2 ? d.psd2d_prob : nullptr, (size_t)T.K * T.n_p2, &T.psd2))) break;
+            if (T.n_r2 && !T.rad_class && (st = upload(m, d.rad_class, (size_t)T.K, &T.rad_class))) break;
+            // the host copies are released when the model stream has consumed them
+            CU(cudaStreamSynchronize(m->stream));
+        }
         void *s32, *stiles, *g32, *gg;
         if ((st = alloc_dev(m, &s32, (size_t)T.K * T.N * sizeof(float)))) break;
         if ((st = alloc_dev(m, &stiles, (size_t)T.n_kb * 2 * US * KB * sizeof(float)))) break;
@@ -236,6 +284,7 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
         m->max_cb = std::max(m->max_cb, T.n_cb);
         m->any_tag |= T.has_tag;
         m->any_cols |= (T.n_rad > 0 || T.n_psd > 0) ? 1 : 0;
+        m->is2d |= T.n_sl > 0 ? 1 : 0;
     }
     if (st) {
         cudaStreamSynchronize(m->stream);
@@ -256,6 +305,11 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
     w.watchdog_ns = m->watchdog_ns;
     w.max_tiles = m->max_tiles;
     w.max_cb = m->max_cb;
+    w.tr_kb = w.Npad / KB;
+    w.row_kb = w.Mpad / KB;
+    w.win_kb = (m->nwmax + KB - 1) / KB;
+    w.win_tiles = (m->nwmax + TM - 1) / TM;
+    w.Lmax = m->Lmax;
     const size_t tv = m->precision == BX_FP64 ? sizeof(double) : sizeof(float);
     const bool species = m->precision == BX_TF32X3;
     struct A {
@@ -286,6 +340,14 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
         {(void**)&w.status, sizeof(int) * cap},
         {(void**)&w.err, sizeof(unsigned)},
         {(void**)&w.units, sizeof(unsigned long long)},
+        {(void**)&w.coef2d, m->is2d ? sizeof(float) * cap * 3 * KMAX * NSL : 16},
+        {(void**)&w.tr2d, m->is2d ? sizeof(float) * cap * (w.Npad / KB) * 2 * NSL * KB : 16},
+        {(void**)&w.y2d, m->is2d ? sizeof(float) * cap * (w.Mpad / KB) * 2 * NSL * KB : 16},
+        {(void**)&w.w2d, m->is2d ? sizeof(float) * cap * ((m->nwmax + KB - 1) / KB) * 2 * NSL * KB : 16},
+        {(void**)&w.wt2d, m->is2d ? sizeof(float) * cap * (w.Mpad / KB) * 2 * NSL * KB : 16},
+        {(void**)&w.nll2d, m->is2d ? sizeof(double) * cap * MAX_TILES * 2 : 16},
+        {(void**)&w.geps2d, m->is2d ? sizeof(double) * cap * MAX_TILES : 16},
+        {(void**)&w.gpart2d, m->is2d ? sizeof(double) * cap * MAX_CB * (GPN + 1) : 16},
         {(void**)&m->theta_d, sizeof(double) * cap * m->P},
         {(void**)&m->nll_d, sizeof(double) * cap},
         {(void**)&m->grad_d, sizeof(double) * cap * m->P},
@@ -391,6 +453,16 @@ int bx_enqueue_eval(bx_model* m, int n, const double* theta_dev, int tstride, in
     if ((st = prof_mark(m, 0))) return st;
     CU(launch_prep(w, n, s));
     if ((st = prof_mark(m, 1))) return st;
+    if (m->is2d) {
+        CU(launch_eval2d(w, n, want_grad, want_mu, 1, s));
+        if ((st = prof_mark(m, 2))) return st;
+        CU(launch_eval2d(w, n, want_grad, want_mu, 2, s));
+        if ((st = prof_mark(m, 3))) return st;
+        if (want_grad) CU(launch_eval2d(w, n, want_grad, want_mu, 3, s));
+        if ((st = prof_mark(m, 4))) return st;
+        CU(launch_gather2d(w, n, nll_dev, grad_dev, want_grad, s));
+        return prof_mark(m, 5);
+    }
     if (m->precision == BX_FP64) CU(launch_fwd_f64(w, n, m->max_tiles, m->any_tag, m->any_cols, s));
     else if (m->precision == BX_FP32) CU(launch_fwd_f32(w, n, m->max_tiles, m->any_tag, m->any_cols, s));
     else CU(launch_fwd_tc(w, n, m->max_tiles, s));

@@ -33,6 +33,7 @@ constexpr int MAX_CB = 64;     // columns per toy <= MAX_CB * BCOLS
 constexpr int MAX_RAD = 256;
 constexpr int MAX_PSD = 256;
 constexpr int MAX_L = 4096;
+constexpr int NSL = 128;       // 2D model: slices per contraction (UMMA N), TFC spectra included
 
 // Gauss-Legendre 3-point rule on [-1, 1]: nodes 0, +-sqrt(3/5), weights 8/9, 5/9.  The
 // weights are applied as the exact integers 8 and 5 and the 1/9 is folded into the FP64
@@ -72,6 +73,12 @@ struct Toy {
     const double* cnt;        // [nb] data, concatenated (vetoed, tagged, radial, PSD)
     const int* rad_class;     // [K]
     const double* psd;        // [K][n_psd]
+    // 2D model (n_sl > 0): slices b = 0 vetoed, [1 tagged], then n_r2 radial and n_p2
+    // pulse-shape slices of the vetoed events; counts are slice-major [n_sl][nw]
+    int n_sl, n_r2, n_p2, b_r2;   // b_r2: first radial slice
+    const float* ut;              // [N][NSL]: template modulation 1 + amp u[i][b] (1 for the TFC slices)
+    const double* U2;             // [K][NSL]: sum_i s_k[i] ut[i][b] (slice-set normalisation)
+    const double* psd2;           // [K][n_p2]
 };
 
 // Per-column FP64 results of k_prep.
@@ -114,6 +121,16 @@ struct Work {
     unsigned long long* units;   // in-band response entries evaluated (counted when count_units)
     int count_units;
     const unsigned char* skip;   // [cap] or nullptr: items flagged 1 are not evaluated (-lnL = +inf)
+    // 2D model buffers (UMMA K-major tiles of TF32 hi | lo halves, NSL slices x KB)
+    float* coef2d;            // [cap][3][KMAX][NSL]: r_k dT/dr_k, dT/dr_k, dT/ds_r coefficients
+    float* tr2d;              // [cap][tr_kb][2][NSL][KB]: rate-weighted templates over true energy
+    float* y2d;               // [cap][row_kb][2][NSL][KB]: Y = R T_r over output rows
+    float* w2d;               // [cap][win_kb][2][NSL][KB]: 1 - n/mu over window rows
+    float* wt2d;              // [cap][row_kb][2][NSL][KB]: pile-up-correlated weights over rows
+    double* nll2d;            // [cap][MAX_TILES][2]: compensated -lnL partials per window tile
+    double* geps2d;           // [cap][MAX_TILES]
+    double* gpart2d;          // [cap][MAX_CB][GPN + 1]: response, rate and s_r partials
+    int tr_kb, row_kb, win_kb, win_tiles, Lmax;
 };
 
 constexpr int STATUS_SKIPPED = 1;   // item status of a skipped evaluation
@@ -129,6 +146,8 @@ cudaError_t launch_mid(const Work& w, int n, int Mmax, int nwmax, int Lmax, int 
                        cudaStream_t s);
 cudaError_t launch_bwd(const Work& w, int n, int max_cb, cudaStream_t s);
 cudaError_t launch_gather(const Work& w, int n, double* nll_out, double* grad_out, int want_grad, cudaStream_t s);
+cudaError_t launch_eval2d(const Work& w, int n, int want_grad, int want_mu, int stage, cudaStream_t s);
+cudaError_t launch_gather2d(const Work& w, int n, double* nll_out, double* grad_out, int want_grad, cudaStream_t s);
 cudaError_t launch_umma_selftest(const float* A, const float* B, float* D, unsigned* err, cudaStream_t s);
 cudaError_t launch_watchdog_selftest(unsigned* err, unsigned long long budget_ns, cudaStream_t s);
 
@@ -272,6 +291,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* out) {
     for (int j = 0; j < 16; ++j) out[j] = __uint_as_float(r[j]);
 }
 
+// 32 lanes x 8 columns of 32-bit from tensor memory (warp w % 4 reads lanes 32 (w % 4) + 0..31).
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* out) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 8; ++j) out[j] = __uint_as_float(r[j]);
+}
+
 // ---- compensated FP64 sums
 
 struct Neu {
@@ -287,6 +318,37 @@ __device__ __forceinline__ Neu neu_merge(Neu a, Neu b) {
     a.c += b.c;
     return a;
 }
+
+// Baker-Cousins term (mu - n) + n ln(n/mu) (n > 0) and its weight 1 - n/mu in FP32, for
+// |x| <= 1/4 with x = (n - mu)/mu (every bin of a reasonable fit).  Written without
+// cancellation: the term is n (log1p(x) - x) + (n - mu) x, and with s = x / (2 + x),
+//   log1p(x) - x = 2 atanh(s) - x = -x^2 / (2 + x) + 2 (s^3/3 + s^5/5 + s^7/7 + s^9/9 + ...),
+// |s| <= 1/7, truncated after s^9 (next term < 1e-10); each piece has FP32 relative error, the
+// term (~(n - mu)^2 / 2mu, ~1/2) an absolute error ~1e-7 with no systematic sign.  Other bins
+// take the FP64 form.  Returns false when |x| > 1/4.
+__device__ __forceinline__ bool bc_term32(double n, double mu, double& term, double& wb) {
+    const float d = (float)(n - mu);
+    const float x = d / (float)mu;
+    if (!(fabsf(x) <= 0.25f)) return false;
+    const float r = 1.0f / (2.0f + x);
+    const float s = x * r, s2 = s * s;
+    const float series = fmaf(s2, fmaf(s2, fmaf(s2, 2.0f / 9.0f, 2.0f / 7.0f), 2.0f / 5.0f), 2.0f / 3.0f);
+    const float L = fmaf(s2 * s, series, -(x * x) * r);
+    term = (double)fmaf((float)n, L, d * x);
+    wb = (double)(-x);
+    return true;
+}
+
+// Shell integral of r^2 exp((r - r_iv)/lam): F and dF/dlam.
+__device__ __forceinline__ void shell_F(double r, double r_iv, double lam, double& F, double& dF) {
+    const double e = exp((r - r_iv) / lam);
+    const double poly = lam * r * r - 2.0 * lam * lam * r + 2.0 * lam * lam * lam;
+    F = e * poly;
+    dF = e * (-(r - r_iv) / (lam * lam) * poly + (r * r - 4.0 * lam * r + 6.0 * lam * lam));
+}
+
+// SPECIES: the tensor-core forward's species-resolved spectra (else rate-first).  The
+// rate-first FP32 variant is held to 64 registers so that two CTAs share an SM.
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T x) {

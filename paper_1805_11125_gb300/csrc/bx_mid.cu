@@ -93,36 +93,6 @@ struct Sum32 {
 template <typename TV> struct DotT { using type = Dot64; };
 template <> struct DotT<float> { using type = Dot32; };
 
-// Baker-Cousins term (mu - n) + n ln(n/mu) (n > 0) and its weight 1 - n/mu in FP32, for
-// |x| <= 1/4 with x = (n - mu)/mu (every bin of a reasonable fit).  Written without
-// cancellation: the term is n (log1p(x) - x) + (n - mu) x, and with s = x / (2 + x),
-//   log1p(x) - x = 2 atanh(s) - x = -x^2 / (2 + x) + 2 (s^3/3 + s^5/5 + s^7/7 + s^9/9 + ...),
-// |s| <= 1/7, truncated after s^9 (next term < 1e-10); each piece has FP32 relative error, the
-// term (~(n - mu)^2 / 2mu, ~1/2) an absolute error ~1e-7 with no systematic sign.  Other bins
-// take the FP64 form.  Returns false when |x| > 1/4.
-__device__ __forceinline__ bool bc_term32(double n, double mu, double& term, double& wb) {
-    const float d = (float)(n - mu);
-    const float x = d / (float)mu;
-    if (!(fabsf(x) <= 0.25f)) return false;
-    const float r = 1.0f / (2.0f + x);
-    const float s = x * r, s2 = s * s;
-    const float series = fmaf(s2, fmaf(s2, fmaf(s2, 2.0f / 9.0f, 2.0f / 7.0f), 2.0f / 5.0f), 2.0f / 3.0f);
-    const float L = fmaf(s2 * s, series, -(x * x) * r);
-    term = (double)fmaf((float)n, L, d * x);
-    wb = (double)(-x);
-    return true;
-}
-
-// Shell integral of r^2 exp((r - r_iv)/lam): F and dF/dlam.
-__device__ __forceinline__ void shell_F(double r, double r_iv, double lam, double& F, double& dF) {
-    const double e = exp((r - r_iv) / lam);
-    const double poly = lam * r * r - 2.0 * lam * lam * r + 2.0 * lam * lam * lam;
-    F = e * poly;
-    dF = e * (-(r - r_iv) / (lam * lam) * poly + (r * r - 4.0 * lam * r + 6.0 * lam * lam));
-}
-
-// SPECIES: the tensor-core forward's species-resolved spectra (else rate-first).  The
-// rate-first FP32 variant is held to 64 registers so that two CTAs share an SM.
 template <typename TV, bool SPECIES>
 __global__ void __launch_bounds__(MID_THREADS, (sizeof(TV) == sizeof(float) && !SPECIES) ? 2 : 1)
     k_mid(Work w, int want_grad, int want_mu) {

@@ -20,6 +20,7 @@ struct bx_model {
     bx::Work w{};
     int Kmax = 0, Nmax = 0, Mmax = 0, nwmax = 0, nbmax = 0, Lmax = 0, max_tiles = 0, max_cb = 0, P = 0;
     int any_tag = 0, any_cols = 0;   // some toy has a tagged spectrum / an Eq. 4 term
+    int is2d = 0;                    // the toys carry 2D histograms (bx_2d.cu path)
     std::vector<int> toy_tmp, toy_cached;
     double* theta_d = nullptr;
     double* nll_d = nullptr;
