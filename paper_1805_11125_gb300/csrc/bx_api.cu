@@ -341,7 +341,7 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
         {(void**)&w.err, sizeof(unsigned)},
         {(void**)&w.units, sizeof(unsigned long long)},
         {(void**)&w.coef2d, m->is2d ? sizeof(float) * cap * 3 * KMAX * NSL : 16},
-        {(void**)&w.tr2d, m->is2d ? sizeof(float) * cap * (w.Npad / KB) * 2 * NSL * KB : 16},
+        {(void**)&w.tr2d, m->is2d ? sizeof(float) * cap * (w.Npad / KB) * 3 * NSL * KB : 16},
         {(void**)&w.y2d, m->is2d ? sizeof(float) * cap * (w.Mpad / KB) * 2 * NSL * KB : 16},
         {(void**)&w.w2d, m->is2d ? sizeof(float) * cap * ((m->nwmax + KB - 1) / KB) * 2 * NSL * KB : 16},
         {(void**)&w.wt2d, m->is2d ? sizeof(float) * cap * (w.Mpad / KB) * 2 * NSL * KB : 16},

@@ -404,7 +404,7 @@ extern "C" int bx_fit(bx_model* m, int n, const int* toy_idx, const double* thet
                 static const double dh[7] = {INFINITY, INFINITY, INFINITY, INFINITY, INFINITY, 1.0, INFINITY};
                 l = dl[p - T.K];
                 h = dh[p - T.K];
-                f = (p - T.K == 6) ? (T.n_rad > 0) : 1;
+                f = (p - T.K == 6) ? (T.n_rad > 0 || T.n_r2 > 0) : 1;
             }
             if (o.lo) l = o.lo[q];
             if (o.hi) h = o.hi[q];

@@ -123,7 +123,7 @@ struct Work {
     const unsigned char* skip;   // [cap] or nullptr: items flagged 1 are not evaluated (-lnL = +inf)
     // 2D model buffers (UMMA K-major tiles of TF32 hi | lo halves, NSL slices x KB)
     float* coef2d;            // [cap][3][KMAX][NSL]: r_k dT/dr_k, dT/dr_k, dT/ds_r coefficients
-    float* tr2d;              // [cap][tr_kb][2][NSL][KB]: rate-weighted templates over true energy
+    float* tr2d;              // [cap][tr_kb][3][NSL][KB]: rate-weighted templates (hi | mid | lo)
     float* y2d;               // [cap][row_kb][2][NSL][KB]: Y = R T_r over output rows
     float* w2d;               // [cap][win_kb][2][NSL][KB]: 1 - n/mu over window rows
     float* wt2d;              // [cap][row_kb][2][NSL][KB]: pile-up-correlated weights over rows

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(256) k_prep(Work w) {
     __syncthreads();
     if (tid < T.P && !isfinite(th[tid])) s_bad = 1;
     const double LY = th[K], a = th[K + 1], b = th[K + 2], c = th[K + 3], kB = th[K + 4];
-    if (tid == 0 && (!(LY > 0.0) || (T.n_rad > 0 && !(th[K + 6] > 0.0)))) s_bad = 1;
+    if (tid == 0 && (!(LY > 0.0) || ((T.n_rad > 0 || T.n_r2 > 0) && !(th[K + 6] > 0.0)))) s_bad = 1;
 
     const double w_ = T.w, inv_w = 1.0 / w_;
     const double z_lo = T.m_lo * w_, z_hi = M * w_;

@@ -93,3 +93,25 @@ def test_negative_counts_and_bad_window_rejected():
     # bad options
     o = bx.bx_options(7, 1, 0.0, 0.0)
     assert L.bx_model_create(C.byref(make()), 1, C.byref(o), None, C.byref(h)) == bx.BX_EINVAL
+
+
+def test_2d_model_rejections_on_host():
+    """2D histograms: BX_FP32 only, at most 128 slices, not together with the 1D Eq. 4 terms
+    (all checked before any device is touched)."""
+    import dataclasses
+    s = I.config("small_2d")
+    s = s.with_counts(np.ones(s.n_bins_total))
+    for prec in (bx.BX_FP64, bx.BX_TF32X3):
+        with pytest.raises(bx.BxError) as e:
+            bx.Model(s, precision=prec)
+        assert e.value.status == bx.BX_EINVAL and "BX_FP32" in str(e.value)
+    big = dataclasses.replace(s, n_rad2d=120, field2d=np.zeros((s.n_grid, 120 + s.n_psd2d)))   # 132 slices
+    big = big.with_counts(np.ones(big.n_bins_total))
+    with pytest.raises(bx.BxError) as e:
+        bx.Model(big, precision=bx.BX_FP32)
+    assert e.value.status == bx.BX_EINVAL and "slices" in str(e.value)
+    both = dataclasses.replace(s, n_rad=10)
+    both = both.with_counts(np.ones(both.n_bins_total))
+    with pytest.raises(bx.BxError) as e:
+        bx.Model(both, precision=bx.BX_FP32)
+    assert e.value.status == bx.BX_EINVAL

@@ -1,6 +1,6 @@
 """GPU path vs the FP64 CPU oracle, element by element, through the C ABI.
 
-Tolerances (derived from the arithmetic of each precision mode, see DESIGN.md):
+Tolerances (derived from the arithmetic of each precision mode):
   * expected counts per bin: relative 1e-5 on bins with mu >= 1e-3 max(mu), absolute
     1e-8 max(mu) below (FP64 path: 1e-10 relative);
   * -lnL: |Delta(-2 lnL)| <= 1e-3 (FP64 path: 1e-7).  The tensor-core mode BX_TF32X3 is held
