@@ -242,6 +242,15 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
         if ((st = upload(m, d.tag_frac, (size_t)T.K, &T.tag))) break;
         if ((st = upload(m, d.pileup, (size_t)T.L, &T.g))) break;
         if ((st = upload(m, cnt.data(), cnt.size(), &T.cnt))) break;
+        {
+            std::vector<float2> c32(cnt.size());
+            for (size_t j = 0; j < cnt.size(); ++j) {
+                const float h = (float)cnt[j];
+                c32[j] = make_float2(h, (float)(cnt[j] - (double)h));
+            }
+            if ((st = upload(m, c32.data(), c32.size(), &T.cnt32))) break;
+            CU(cudaStreamSynchronize(m->stream));   // c32 is released at the end of this scope
+        }
         if ((st = upload(m, T.n_rad ? d.rad_class : nullptr, (size_t)T.K, &T.rad_class))) break;
         if ((st = upload(m, T.n_psd ? d.psd_prob : nullptr, (size_t)T.K * T.n_psd, &T.psd))) break;
         if (T.n_sl) {

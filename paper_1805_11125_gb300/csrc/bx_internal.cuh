@@ -70,7 +70,8 @@ struct Toy {
     const double* g;          // [L]
     const float* g32;         // [L]
     const double* Gg;         // [M]: sum over window bins m' of g[m' - m] (0 <= m'-m < L)
-    const double* cnt;        // [nb] data, concatenated (vetoed, tagged, radial, PSD)
+    const double* cnt;        // [nb] data, concatenated (vetoed, tagged, radial, PSD, 2D slices)
+    const float2* cnt32;      // [nb] the same as FP32 pairs hi + lo
     const int* rad_class;     // [K]
     const double* psd;        // [K][n_psd]
     // 2D model (n_sl > 0): slices b = 0 vetoed, [1 tagged], then n_r2 radial and n_p2
@@ -349,6 +350,33 @@ __device__ __forceinline__ void shell_F(double r, double r_iv, double lam, doubl
 
 // SPECIES: the tensor-core forward's species-resolved spectra (else rate-first).  The
 // rate-first FP32 variant is held to 64 registers so that two CTAs share an SM.
+
+// Compensated FP32 sum (value s + c): TwoProduct of each term by FMA, TwoSum into the
+// running sum, the same to merge partial sums across a warp.
+struct Sum32 {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float t = __fadd_rn(s, x), bb = __fsub_rn(t, s);
+        c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(x, bb)));
+        s = t;
+    }
+    // add a * (b + bl), bl a small correction of b
+    __device__ __forceinline__ void add_prod(float a, float b, float bl) {
+        const float p = __fmul_rn(a, b);
+        c = fmaf(a, bl, __fadd_rn(c, fmaf(a, b, -p)));
+        add(p);
+    }
+    __device__ __forceinline__ Sum32 warp_reduce() const {
+        Sum32 r = *this;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float os = __shfl_xor_sync(0xffffffffu, r.s, o), oc = __shfl_xor_sync(0xffffffffu, r.c, o);
+            r.add(os);
+            r.c = __fadd_rn(r.c, oc);
+        }
+        return r;
+    }
+};
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T x) {

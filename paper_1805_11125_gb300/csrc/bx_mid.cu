@@ -64,32 +64,6 @@ struct Dot64 {
     __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
     __device__ __forceinline__ double value() const { return s; }
 };
-// Compensated FP32 sum (value s + c): TwoProduct of each term by FMA, TwoSum into the
-// running sum, the same to merge partial sums across a warp.
-struct Sum32 {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float x) {
-        const float t = __fadd_rn(s, x), bb = __fsub_rn(t, s);
-        c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(x, bb)));
-        s = t;
-    }
-    // add a * (b + bl), bl a small correction of b
-    __device__ __forceinline__ void add_prod(float a, float b, float bl) {
-        const float p = __fmul_rn(a, b);
-        c = fmaf(a, bl, __fadd_rn(c, fmaf(a, b, -p)));
-        add(p);
-    }
-    __device__ __forceinline__ Sum32 warp_reduce() const {
-        Sum32 r = *this;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float os = __shfl_xor_sync(0xffffffffu, r.s, o), oc = __shfl_xor_sync(0xffffffffu, r.c, o);
-            r.add(os);
-            r.c = __fadd_rn(r.c, oc);
-        }
-        return r;
-    }
-};
 template <typename TV> struct DotT { using type = Dot64; };
 template <> struct DotT<float> { using type = Dot32; };
 
