@@ -38,6 +38,10 @@ FWD_OPS_PER_ENTRY = 55
 # adjoint kernel: resp_adjoint32 66, weight 3, five column sums 5
 BWD_OPS_PER_ENTRY = 74
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+# DRAM bytes (read + write) per evaluation item of the two candidate dominant kernels, from one
+# ncu capture at 512 items (profiles/multivariate_fp32_b512_launches_and_kernels.md); the
+# traffic scales with the items of a launch.
+TRAFFIC_PER_ITEM = {"k_fwd_f32": 48.886e6 / 512, "k_bwd_f32": 100.154e6 / 512}
 
 
 def dist_env():
@@ -231,7 +235,7 @@ def run_ours(args):
         fits = fit_times(bx, I, spec, stream)
         if args.toys > 0:
             fits["batched_toys"] = toy_fits(bx, I, args.toys, stream)
-        disc = discrimination_leg(bx, I, stream)
+        disc = discrimination_leg(bx, I, stream, B=args.batch2d) if args.batch2d > 0 else None
     if rank != 0:
         return
     report(args, ws, B, total_ms, value, stage_ms, n_evals, entries, e2e, fp64_value, clk, fits, disc)
@@ -400,7 +404,8 @@ def report(args, ws, B, total_ms, value, stage_ms, n_evals, entries, e2e, fp64_v
     peak = SMS * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
     achieved = ops / (per_launch[dom] / 1e3) / 1e12
     roofline = {"bound": "alu", "kernel": "k_fwd_f32" if dom == "forward" else "k_bwd_f32",
-                "achieved": achieved, "peak": peak, "unit": "Top/s", "frac": achieved / peak, "traffic": None,
+                "achieved": achieved, "peak": peak, "unit": "Top/s", "frac": achieved / peak,
+                "traffic": TRAFFIC_PER_ITEM["k_fwd_f32" if dom == "forward" else "k_bwd_f32"] * B,
                 "entries_per_launch": entries / max(n_evals, 1),
                 "ops_per_entry": FWD_OPS_PER_ENTRY if dom == "forward" else BWD_OPS_PER_ENTRY,
                 "peak_basis": "FP32 issue rate 152 SMs x 128 lanes x 2070 MHz (derived, not measured)",
@@ -428,6 +433,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the e2e, FP64 and fit legs (profiling runs)")
     ap.add_argument("--toys", type=int, default=4096, help="batched toy fits in the fit leg (0: none)")
+    ap.add_argument("--batch2d", type=int, default=256, help="batch of the 2D-model leg (0: none)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
