@@ -44,6 +44,20 @@ SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 TRAFFIC_PER_ITEM = {"k_fwd_f32": 48.886e6 / 512, "k_bwd_f32": 100.154e6 / 512}
 
 
+def job_throughput(local_ms: float, items_per_rank: int, steps: int, ws: int, device=None):
+    """Whole-job evaluations/s of a weak-scaling replica run: every rank evaluated
+    items_per_rank x steps items in local_ms; the job took the slowest rank's time (MAX over
+    ranks; needs an initialised process group when ws > 1).  Returns (value, max_ms)."""
+    max_ms = float(local_ms)
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([max_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        max_ms = float(t.item())
+    return ws * items_per_rank * steps / (max_ms / 1e3), max_ms
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -222,12 +236,7 @@ def run_ours(args):
     st = model.status()
     if st:
         raise bx.BxError(st, bx.lib().bx_last_error().decode())
-    total_ms = sum(a.elapsed_time(b) for a, b in evs)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * B * args.steps / (total_ms / 1e3)
+    value, total_ms = job_throughput(sum(a.elapsed_time(b) for a, b in evs), B, args.steps, ws, dev)
 
     e2e, fp64_value, fits, disc = None, None, None, None
     if not args.no_extras:
