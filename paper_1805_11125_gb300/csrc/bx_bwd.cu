@@ -15,7 +15,8 @@
 //   k_bwd_f64: exact bin mass from erfc tails and exact derivatives -(phi(z_b) - phi(z_a))/sigma,
 //              -(z_b phi(z_b) - z_a phi(z_a))/sigma, FP64 throughout.
 //   k_bwd_f32: the same integrals by the forward pass's 3-point Gauss-Legendre rule
-//              (integrands phi, t phi, (t^2 - 1) phi) in round-to-nearest FP32, column sums
+//              (integrands phi, t phi, (t^2 - 1) phi) in round-to-nearest FP32, down each
+//              column by the row recurrence of bx_resp.cuh (adj_run), column sums
 //              in FP32 per chunk of rows and FP64 across chunks, the chain rule in FP64; the
 //              species sums and the rate products in FP32 (FP64 work is 64 FP32 operations'
 //              worth of issue on GB300 and would otherwise dominate the column epilogue).
@@ -189,6 +190,7 @@ __global__ void __launch_bounds__(BCOLS) k_bwd_f32(Work w) {
         }
     const float4 cf = ok ? w.colf[(size_t)item * w.Npad + i] : make_float4(0.f, 0.f, 0.f, 0.f);
     const ColG cg = ok ? w.colg[(size_t)item * w.Npad + i] : ColG{0.f, 0.f, 0.f, 0.f};
+    const AdjCol ac = adj_col(cf, cg);
     const float* rw = static_cast<const float*>(w.rowW) + (size_t)item * 3 * w.Mpad;
     // the warp's rows: the union of its 32 columns' bands, their weights staged 64 rows at a
     // time in the warp's own shared memory (the warps of the block never wait for each other)
@@ -211,16 +213,13 @@ __global__ void __launch_bounds__(BCOLS) k_bwd_f32(Work w) {
             }
             __syncwarp();
             if (ok) {
-                for (int j = 0; j < ns; ++j) {
-                    const float ws = sW[wq][0][j], wt = sW[wq][1][j];
-                    const float W = fmaf(ws, Ssub, fmaf(wt, Stag, sW[wq][2][j] * SA));
-                    float P0, P1, P2;
-                    resp_adjoint32((float)(s0 + j), cf, cg, P0, P1, P2);
-                    p0 = fmaf(W, P0, p0);
-                    p1 = fmaf(W, P1, p1);
-                    p2 = fmaf(W, P2, p2);
-                    ps = fmaf(ws, P0, ps);
-                    pt = fmaf(wt, P0, pt);
+                for (int j = 0; j < ns; j += ADJ_RUN) {
+                    auto wts = [&](int k, float& ws, float& wt, float& W) {
+                        ws = sW[wq][0][j + k];
+                        wt = sW[wq][1][j + k];
+                        W = fmaf(ws, Ssub, fmaf(wt, Stag, sW[wq][2][j + k] * SA));
+                    };
+                    adj_run((float)(s0 + j), min(ADJ_RUN, ns - j), cf, cg, ac, wts, p0, p1, p2, ps, pt);
                 }
             }
             __syncwarp();

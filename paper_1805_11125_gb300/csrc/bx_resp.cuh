@@ -137,6 +137,85 @@ __device__ __forceinline__ void resp_adjoint32(float mf, const float4& cf, const
     P2 = fmaf(GL_W_OUT, fmaf(fmaf(kk, kk, q0), Sp, -2.0f * t0 * kk * Sm), GL_W_MID * (q0 * p0));
 }
 
+// Row recurrence of the adjoint's node sums down one column.  From row m to m + 1 the centre
+// node moves by hs in the scaled variable, so
+//   p0(m+1) = p0(m) rho(m),   rho(m) = 2^-(2 t0(m) hs + hs^2),   rho(m+1) = rho(m) C,  C = 2^(-2 hs^2),
+// and (cosh z, sinh z) of the outer nodes (z = kap t0) rotate by the fixed step kap hs.  A run of
+// ADJ_RUN rows starts from the exact evaluation of its first row (as resp_adjoint32), so the
+// FP32 recurrence error stays below ~1e-6 of an entry (it only enters gradient sums); columns
+// narrow enough for |z| > 1 within the run take the exact form row by row.
+constexpr int ADJ_RUN = 8;
+
+struct AdjCol {
+    float hs, hs2, C, A, B, kk;   // hs, hs^2, 2^(-2 hs^2), cosh and sinh of kap hs, kap / (2 ln 2)
+};
+
+__device__ __forceinline__ AdjCol adj_col(const float4& cf, const ColG& cg) {
+    AdjCol a;
+    a.hs = cf.z;
+    a.hs2 = cf.z * cf.z;
+    a.C = exp2_neg(-2.0f * a.hs2);
+    const float d = cg.kap * cf.z, d2 = d * d;
+    a.A = cosh_small(d2);
+    a.B = sinh_small(d, d2);
+    a.kk = cg.kap * INV_2LN2;
+    return a;
+}
+
+// Adds W[j] (P0, P1, P2) and the row weights' P0 sums of rows mf .. mf + n - 1 (n <= ADJ_RUN)
+// into the accumulators; W[j] = ws[j] Ssub + wt[j] Stag + wg[j] SA.
+template <typename WF>
+__device__ __forceinline__ void adj_run(float mf, int n, const float4& cf, const ColG& cg, const AdjCol& ac, WF&& wts,
+                                        float& p0s, float& p1s, float& p2s, float& pss, float& pts) {
+    float th, tl;
+    centre_df(mf, cf, cg.c_lo, th, tl);
+    const float z0 = cg.kap * th, z1 = cg.kap * fmaf((float)(ADJ_RUN - 1), ac.hs, th);
+    if (fabsf(z0) <= 1.0f && fabsf(z1) <= 1.0f) {
+        float p = centre_node(th, tl);
+        float rho = exp2_neg(-fmaf(2.0f * th, ac.hs, ac.hs2));
+        const float s = z0 * z0;
+        float ch = cosh_small(s), sh = sinh_small(z0, s);
+        float t = th;
+#pragma unroll
+        for (int k = 0; k < ADJ_RUN; ++k) {
+            if (k < n) {
+                float ws, wt, W;
+                wts(k, ws, wt, W);
+                const float f = p * cg.Ck2, Sp = f * ch, Sm = f * sh, q0 = t * t;
+                const float P0 = fmaf(GL_W_OUT, Sp, GL_W_MID * p);
+                const float P1 = fmaf(GL_W_OUT, fmaf(t, Sp, -ac.kk * Sm), GL_W_MID * (t * p));
+                const float P2 = fmaf(GL_W_OUT, fmaf(fmaf(ac.kk, ac.kk, q0), Sp, -2.0f * t * ac.kk * Sm), GL_W_MID * (q0 * p));
+                p0s = fmaf(W, P0, p0s);
+                p1s = fmaf(W, P1, p1s);
+                p2s = fmaf(W, P2, p2s);
+                pss = fmaf(ws, P0, pss);
+                pts = fmaf(wt, P0, pts);
+                p *= rho;
+                rho *= ac.C;
+                t += ac.hs;
+                const float c2 = fmaf(ch, ac.A, sh * ac.B);
+                sh = fmaf(sh, ac.A, ch * ac.B);
+                ch = c2;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < ADJ_RUN; ++k) {
+            if (k < n) {
+                float ws, wt, W;
+                wts(k, ws, wt, W);
+                float P0, P1, P2;
+                resp_adjoint32(mf + (float)k, cf, cg, P0, P1, P2);
+                p0s = fmaf(W, P0, p0s);
+                p1s = fmaf(W, P1, p1s);
+                p2s = fmaf(W, P2, p2s);
+                pss = fmaf(ws, P0, pss);
+                pts = fmaf(wt, P0, pts);
+            }
+        }
+    }
+}
+
 #endif  // __CUDACC__
 
 }  // namespace bx
