@@ -280,6 +280,30 @@ class Model:
         return out, info, st
 
 
+    def profile_scan(self, param: int, values, theta_start, toy: int = 0, free=None, tol_edm: float = 0.0,
+                     max_iter: int = 0):
+        """Profile likelihood of one parameter: for every value v in ``values`` the fit of all
+        other free parameters with theta[param] held at v, all scan points as one batch of fits
+        (one bx_fit call; max_batch >= len(values) * fit_slots).  ``free``: the free mask of
+        the toy's layout (default: the spec's default_free()).  Returns (nll[len], theta[len, P],
+        info) with nll the minimised -lnL at each value."""
+        spec = self.specs[toy]
+        vals = np.asarray(values, dtype=np.float64)
+        fr = (spec.default_free() if free is None else np.asarray(free)).astype(np.uint8).copy()
+        fr[param] = 0
+        # the options' free mask is in the layout of a toy with the model's largest K
+        Kmax = self.P - 7
+        mask = np.zeros(self.P, dtype=np.uint8)
+        mask[: spec.K] = fr[: spec.K]
+        mask[Kmax:] = fr[spec.K:]
+        th0 = np.zeros((len(vals), self.P))
+        th0[:, : spec.P] = np.asarray(theta_start, dtype=np.float64)[: spec.P]
+        th0[:, param] = vals
+        out, info, _ = self.fit(th0, toy_idx=np.full(len(vals), toy), tol_edm=tol_edm, max_iter=max_iter,
+                                free=mask)
+        return np.array([r["nll"] for r in info]), out, info
+
+
 # C-named conveniences -------------------------------------------------------------------
 
 def bx_model_create(specs, precision=BX_FP32, max_batch=1, **kw) -> Model:

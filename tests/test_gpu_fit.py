@@ -104,3 +104,34 @@ def test_batched_fits_of_different_toys():
         assert ref["status"] == 0
         js = [j for j, tt in enumerate(toys) if tt == t]
         _check_against(ref, out[js], [info[j] for j in js], specs[t].P, specs[t].default_free().astype(bool), 2)
+
+
+@pytest.mark.parametrize("prec", [bx.BX_FP64, bx.BX_FP32])
+def test_profile_likelihood_scan_matches_the_oracle(prec):
+    """Profile of one rate (the paper's use of the fit: limits on rare-signal rates): at each
+    scan value the other 20 parameters are refitted; the GPU's minimised -lnL at each point
+    agrees with the oracle's constrained fit and the profile is minimal at the global fit."""
+    s = dataset("small_mv")
+    ref = O.fit(s, s.theta_true, tol_edm=1e-14)
+    j = 1
+    sig = np.sqrt(ref["cov"][j, j])
+    vals = ref["theta"][j] + sig * np.array([-2.0, -1.0, 0.0, 1.0, 2.0])
+    m = bx.Model(s, precision=prec, max_batch=len(vals) * (8 + 2 * s.P))
+    nll, th, info = m.profile_scan(j, vals, ref["theta"], tol_edm=1e-8, max_iter=5000)
+    assert all(r["status"] == bx.BX_OK for r in info), info
+    assert np.all(th[:, j] == vals)
+    free = s.default_free().copy()
+    free[j] = 0
+    tol = 1e-3 if prec == bx.BX_FP64 else max(1e-3, s.P * 0.05 ** 2)
+    for k, v in enumerate(vals):
+        t0 = ref["theta"].copy()
+        t0[j] = v
+        r = O.fit(s, t0, free=free, tol_edm=1e-14)
+        assert r["status"] == 0
+        assert 2 * abs(nll[k] - r["nll"]) <= tol, (k, nll[k], r["nll"])
+    d2 = 2 * (nll - nll.min())
+    assert int(np.argmin(nll)) == 2
+    # quadratic near the optimum (Delta(-2 lnL) = 1 at one sigma), rising beyond
+    np.testing.assert_allclose(d2[[1, 3]], [1.0, 1.0], rtol=0.1)
+    assert d2[0] > d2[1] and d2[4] > d2[3]
+    m.close()
