@@ -239,6 +239,15 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
         if (T.n_p2) cnt.insert(cnt.end(), d.counts_psd2d, d.counts_psd2d + (size_t)T.n_p2 * T.nw);
         if ((st = upload(m, d.shapes, (size_t)T.K * T.N, &T.shapes))) break;
         if ((st = upload(m, d.stop_pow, (size_t)T.N, &T.stop_pow))) break;
+        {
+            std::vector<float2> s32v(T.N);
+            for (int i = 0; i < T.N; ++i) {
+                const float h = (float)d.stop_pow[i];
+                s32v[i] = make_float2(h, (float)(d.stop_pow[i] - (double)h));
+            }
+            if ((st = upload(m, s32v.data(), s32v.size(), &T.stop32))) break;
+            CU(cudaStreamSynchronize(m->stream));
+        }
         if ((st = upload(m, d.tag_frac, (size_t)T.K, &T.tag))) break;
         if ((st = upload(m, d.pileup, (size_t)T.L, &T.g))) break;
         if ((st = upload(m, cnt.data(), cnt.size(), &T.cnt))) break;

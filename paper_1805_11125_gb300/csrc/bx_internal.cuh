@@ -66,6 +66,7 @@ struct Toy {
     const float* shapes32;    // [K][N]
     const float* S_tiles;     // [n_kb][2][US*KB]: TF32 hi | lo of the shapes, UMMA K-major
     const double* stop_pow;   // [N]
+    const float2* stop32;     // [N]: the same as FP32 pairs hi + lo (nullptr: split on the fly)
     const double* tag;        // [K] or nullptr
     const double* g;          // [L]
     const float* g32;         // [L]

@@ -11,6 +11,7 @@
 #include <limits.h>
 #include <math.h>
 
+#include "bx_df.cuh"
 #include "bx_internal.cuh"
 #include "bx_resp.cuh"
 
@@ -273,9 +274,251 @@ __global__ void __launch_bounds__(256) k_prep(Work w) {
     if (tid == 0) w.status[item] = s_bad ? (int)BX_EDOMAIN : 0;
 }
 
+// Block-wide exclusive scan of two double-floats (256 threads); ta, tb receive the totals.
+__device__ void block_scan_df(df& a, df& b, df& ta, df& tb, float* sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    df ia = a, ib = b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const df xa{__shfl_up_sync(0xffffffffu, ia.h, o), __shfl_up_sync(0xffffffffu, ia.l, o)};
+        const df xb{__shfl_up_sync(0xffffffffu, ib.h, o), __shfl_up_sync(0xffffffffu, ib.l, o)};
+        if (lane >= o) {
+            ia = df_add(xa, ia);
+            ib = df_add(xb, ib);
+        }
+    }
+    // exclusive within the warp: the inclusive value of the previous lane
+    df ea{__shfl_up_sync(0xffffffffu, ia.h, 1), __shfl_up_sync(0xffffffffu, ia.l, 1)};
+    df eb{__shfl_up_sync(0xffffffffu, ib.h, 1), __shfl_up_sync(0xffffffffu, ib.l, 1)};
+    if (lane == 0) ea = eb = df{0.f, 0.f};
+    if (lane == 31) {
+        sh[4 * wid] = ia.h; sh[4 * wid + 1] = ia.l; sh[4 * wid + 2] = ib.h; sh[4 * wid + 3] = ib.l;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        df wa = lane < 8 ? df{sh[4 * lane], sh[4 * lane + 1]} : df{0.f, 0.f};
+        df wb = lane < 8 ? df{sh[4 * lane + 2], sh[4 * lane + 3]} : df{0.f, 0.f};
+        const df oa = wa, ob = wb;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            const df xa{__shfl_up_sync(0xffffffffu, wa.h, o), __shfl_up_sync(0xffffffffu, wa.l, o)};
+            const df xb{__shfl_up_sync(0xffffffffu, wb.h, o), __shfl_up_sync(0xffffffffu, wb.l, o)};
+            if (lane >= o) {
+                wa = df_add(xa, wa);
+                wb = df_add(xb, wb);
+            }
+        }
+        if (lane < 8) {   // exclusive warp prefixes at 32.., totals at 64..
+            const df pa = df_add(wa, df_neg(oa)), pb = df_add(wb, df_neg(ob));
+            sh[32 + 4 * lane] = pa.h; sh[33 + 4 * lane] = pa.l; sh[34 + 4 * lane] = pb.h; sh[35 + 4 * lane] = pb.l;
+        }
+        if (lane == 7) { sh[64] = wa.h; sh[65] = wa.l; sh[66] = wb.h; sh[67] = wb.l; }
+    }
+    __syncthreads();
+    a = df_add(df{sh[32 + 4 * wid], sh[33 + 4 * wid]}, ea);
+    b = df_add(df{sh[34 + 4 * wid], sh[35 + 4 * wid]}, eb);
+    ta = df{sh[64], sh[65]};
+    tb = df{sh[66], sh[67]};
+    __syncthreads();
+}
+
+// The per-column stage of the mixed-precision modes in double-float FP32 (bx_df.cuh, ~2^-44
+// relative): the Birks prefix sums, 1/(1 + kB S), mu, sigma^2, 1/sigma by one Newton step, the
+// generator's split constants.  FP64 only where a column's Gaussian reaches 0 npe or a window
+// edge within 9 sigma (1/Phi, phi/Phi, erfc of the window mass) and for the FP64 copies of
+// mu, sigma, Q, dQ/dkB that the adjoint's chain rule reads.  Same outputs as k_prep<true>.
+__global__ void __launch_bounds__(256) k_prep32(Work w) {
+    const int item = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
+    if (w.skip && w.skip[item]) {
+        if (tid == 0) w.status[item] = STATUS_SKIPPED;
+        return;
+    }
+    const Toy& T = w.toys[w.toy_of[item]];
+    const int K = T.K, N = T.N, M = T.M;
+    const double* th = w.theta + (size_t)item * w.tstride;
+    __shared__ float sh[72];
+    __shared__ int s_bad;
+    __shared__ int s_tlo[MAX_TILES], s_thi[MAX_TILES], s_rlo[MAX_CB], s_rhi[MAX_CB];
+    __shared__ float s_rate[4][KMAX];
+    __shared__ df s_par[9];   // LY, a, b, c, kB, dE, w S_EX2, 1/w, A's constant factor
+    if (tid == 0) s_bad = 0;
+    for (int j = tid; j < MAX_TILES; j += blockDim.x) { s_tlo[j] = INT_MAX; s_thi[j] = INT_MIN; }
+    for (int j = tid; j < MAX_CB; j += blockDim.x) { s_rlo[j] = INT_MAX; s_rhi[j] = INT_MIN; }
+    if (tid < KMAX) {
+        double rs = 0.0, rt = 0.0;
+        if (tid < K) {
+            const double t = T.tag ? T.tag[tid] : 0.0;
+            rs = th[tid] * (T.tag ? 1.0 - t : 1.0);
+            rt = th[tid] * t;
+        }
+        const float rsh = (float)rs, rth = (float)rt;
+        s_rate[0][tid] = rsh;
+        s_rate[1][tid] = (float)(rs - (double)rsh);
+        s_rate[2][tid] = rth;
+        s_rate[3][tid] = (float)(rt - (double)rth);
+    }
+    if (tid < 9) {
+        const double v = tid < 5    ? th[K + tid]
+                         : tid == 5 ? T.dE
+                         : tid == 6 ? T.w * S_EX2
+                         : tid == 7 ? 1.0 / T.w
+                                    : 0.5 * INV_SQRT_2PI * GL_W_SCALE * T.w;
+        s_par[tid] = df_from(v);
+    }
+    __syncthreads();
+    if (tid < T.P && !isfinite(th[tid])) s_bad = 1;
+    if (tid == 0 && (!(th[K] > 0.0) || ((T.n_rad > 0 || T.n_r2 > 0) && !(th[K + 6] > 0.0)))) s_bad = 1;
+    const df LY = s_par[0], pa = s_par[1], pb = s_par[2], pc = s_par[3], kB = s_par[4], dE = s_par[5];
+    const df wS = s_par[6], iw = s_par[7], cAw = s_par[8];
+    const double w_ = T.w;
+    const float wf = (float)w_, inv_wf = iw.h, bandf = (float)w.band;
+    const float e_min = -2.0f * wf, e_max = (M + 2.0f) * wf;
+    const float zlo_f = (float)(T.m_lo * w_), zhi_f = (float)(M * w_);
+    Col64* col = w.col64 + (size_t)item * w.Npad;
+    double2* cq = w.colq + (size_t)item * w.Npad;
+    float4* cf = w.colf + (size_t)item * w.Npad;
+    ColG* cg = w.colg + (size_t)item * w.Npad;
+    float2* cs32 = w.colS32 + (size_t)item * w.Npad;
+    double* aW = w.aW + (size_t)item * w.Npad;
+    int2* cr = w.colr + (size_t)item * w.Npad;
+    const df gln{0.38729834f, (float)(0.38729833462074170 - (double)0.38729834f)};   // sqrt(3/5) / 2
+    const df ln4{1.3862944f, (float)(1.3862943611198906 - (double)1.3862944f)};      // 2 ln 2
+    int bad = 0;
+    unsigned long long inband = 0;
+    df carry_x{0.f, 0.f}, carry_y{0.f, 0.f};
+    for (int c0 = 0; c0 < N; c0 += 256) {
+        const int i = c0 + tid;
+        const bool in = i < N;
+        df S{0.f, 0.f}, x{0.f, 0.f}, y{0.f, 0.f};
+        if (in) {
+            if (T.stop32) {
+                const float2 s2 = T.stop32[i];
+                S = df{s2.x, s2.y};
+            } else {
+                S = df_from(T.stop_pow[i]);
+            }
+            const df q = df_addf(df_mul(kB, S), 1.0f);
+            if (!(q.h > 0.f)) bad = 1;
+            const df rq = df_recip(q);
+            x = df_mul(dE, rq);
+            y = df_neg(df_mul(df_mul(x, S), rq));
+        }
+        df ex = x, ey = y, tx, ty;
+        block_scan_df(ex, ey, tx, ty, sh);
+        int r0 = 0, r1 = 0;
+        bool valid = false;
+        if (in) {
+            const df Q = df_add(df_add(carry_x, ex), df{0.5f * x.h, 0.5f * x.l});
+            const df dQ = df_add(df_add(carry_y, ey), df{0.5f * y.h, 0.5f * y.l});
+            cq[i] = make_double2(df_to_double(Q), df_to_double(dQ));
+            const df mu = df_mul(LY, Q);
+            const df var = df_add(df_mul(df_add(df_mul(pb, mu), pa), mu), pc);
+            const bool ok = var.h > 0.f;
+            if (!ok) bad = 1;
+            const df isig = df_rsqrt(ok ? var : df{1.f, 0.f});
+            const df sig = df_mul(var, isig);
+            const df z = df_mul(mu, isig);
+            const double mud = df_to_double(mu), sigd = df_to_double(sig);
+            double norm = 1.0, mills = 0.0;
+            if (z.h < (float)Q_CUT) {
+                const double zd = df_to_double(z);
+                const double Phi = zd > 0.0 ? 1.0 - upper_tail(zd) : upper_tail(-zd);
+                norm = 1.0 / Phi;
+                mills = INV_SQRT_2PI * exp(-0.5 * zd * zd) * norm;
+            }
+            col[i] = Col64{mud, sigd, norm, mills};
+            // generator constants: t0 = (m + 1/2 - mu/w) hs = (m - jf) hs + c
+            const df u = df_mul(mu, iw);
+            float jf = floorf(u.h);
+            if (u.h == jf && u.l < 0.f) jf -= 1.0f;
+            const df frac = df_addf(u, -jf);
+            const df hs = df_mul(wS, isig);
+            const df cc = df_mul(df_addf(df_neg(frac), 0.5f), hs);
+            cf[i] = make_float4(jf, cc.h, hs.h, hs.l);
+            const df kk = df_mul(gln, hs), kq = df_mul(kk, kk);
+            const df Ad = df_mul(df_mul(cAw, isig), df_from(norm));
+            cg[i] = ColG{df_mul(ln4, kk).h, 2.0f * exp2_neg(-kq.h, -kq.l), cc.l, Ad.h};
+            // rate-weighted spectra of the vetoed (or single) and tagged events (Eq. 3)
+            if (T.shapes32) {
+                float ss = 0.f, st = 0.f;
+                for (int k = 0; k < K; ++k) {
+                    const float sk = T.shapes32[(size_t)k * N + i];
+                    ss = fmaf(s_rate[0][k], sk, fmaf(s_rate[1][k], sk, ss));
+                    st = fmaf(s_rate[2][k], sk, fmaf(s_rate[3][k], sk, st));
+                }
+                cs32[i] = make_float2(ss, st);
+            } else {   // a descriptor without FP32 shapes
+                double ssub = 0.0, stag = 0.0;
+                for (int k = 0; k < K; ++k) {
+                    const double sk = T.shapes[(size_t)k * N + i] * th[k];
+                    const double t = T.tag ? T.tag[k] : 0.0;
+                    ssub += (T.tag ? 1.0 - t : 1.0) * sk;
+                    stag += t * sk;
+                }
+                cs32[i] = make_float2((float)ssub, (float)stag);
+            }
+            // window mass: erfc only for window edges within 9 sigma
+            const float za = (zlo_f - mu.h) * isig.h, zb = (zhi_f - mu.h) * isig.h;
+            double mass;
+            if (za <= -9.0f && zb >= 9.0f) mass = 1.0;
+            else if (za >= 9.0f || zb <= -9.0f) mass = 0.0;
+            else {
+                const double isd = df_to_double(isig);
+                mass = gauss_mass((T.m_lo * w_ - mud) * isd, (M * w_ - mud) * isd);
+            }
+            aW[i] = mass * norm;
+            // response band
+            const float lo_e = fminf(fmaxf(mu.h - bandf * sig.h, e_min), e_max);
+            const float hi_e = fminf(fmaxf(mu.h + bandf * sig.h, e_min), e_max);
+            r0 = max(0, (int)floorf(lo_e * inv_wf));
+            r1 = min(M, (int)floorf(hi_e * inv_wf) + 1);
+            valid = ok && r0 < r1;
+            if (valid) inband += (unsigned long long)(r1 - r0);
+            cr[i] = valid ? make_int2(r0, r1) : make_int2(0, 0);
+        }
+        carry_x = df_add(carry_x, tx);
+        carry_y = df_add(carry_y, ty);
+        const unsigned full = 0xffffffffu;
+        const int t0 = valid ? r0 / TM : INT_MAX, t1 = valid ? (r1 - 1) / TM : INT_MIN;
+        const int tmin = __reduce_min_sync(full, t0), tmax = __reduce_max_sync(full, t1);
+        for (int t = tmin; t <= tmax; ++t) {
+            const bool touch = valid && t >= t0 && t <= t1;
+            const int lo = __reduce_min_sync(full, touch ? i : INT_MAX);
+            const int hi = __reduce_max_sync(full, touch ? i + 1 : INT_MIN);
+            if (lane == 0 && lo != INT_MAX) {
+                atomicMin(&s_tlo[t], lo);
+                atomicMax(&s_thi[t], hi);
+            }
+        }
+        const int rlo = __reduce_min_sync(full, valid ? r0 : INT_MAX);
+        const int rhi = __reduce_max_sync(full, valid ? r1 : INT_MIN);
+        if (lane == 0 && rlo != INT_MAX) {
+            atomicMin(&s_rlo[(c0 + tid) / BCOLS], rlo);
+            atomicMax(&s_rhi[(c0 + tid) / BCOLS], rhi);
+        }
+    }
+    for (int i = N + tid; i < w.Npad; i += blockDim.x) {
+        col[i] = Col64{0.0, 1.0, 0.0, 0.0};
+        cq[i] = make_double2(0.0, 0.0);
+        cf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        cg[i] = ColG{0.f, 0.f, 0.f, 0.f};
+        cs32[i] = make_float2(0.f, 0.f);
+        aW[i] = 0.0;
+        cr[i] = make_int2(0, 0);
+    }
+    if (bad) s_bad = 1;
+    if (w.count_units && inband) atomicAdd(w.units, inband);
+    __syncthreads();
+    for (int t = tid; t < MAX_TILES; t += blockDim.x)
+        w.tile_cols[(size_t)item * MAX_TILES + t] = make_int2(s_tlo[t], s_thi[t]);
+    for (int j = tid; j < MAX_CB; j += blockDim.x)
+        w.cb_rows[(size_t)item * MAX_CB + j] = make_int2(s_rlo[j], s_rhi[j]);
+    if (tid == 0) w.status[item] = s_bad ? (int)BX_EDOMAIN : 0;
+}
+
 cudaError_t launch_prep(const Work& w, int n, cudaStream_t s) {
     if (w.precision == BX_FP64) k_prep<false><<<n, 256, 0, s>>>(w);
-    else k_prep<true><<<n, 256, 0, s>>>(w);
+    else k_prep32<<<n, 256, 0, s>>>(w);
     return cudaGetLastError();
 }
 
