@@ -284,11 +284,12 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
         if ((st = alloc_dev(m, &s32, (size_t)T.K * T.N * sizeof(float)))) break;
         if ((st = alloc_dev(m, &stiles, (size_t)T.n_kb * 2 * US * KB * sizeof(float)))) break;
         if ((st = alloc_dev(m, &g32, (size_t)T.L * sizeof(float)))) break;
-        if ((st = alloc_dev(m, &gg, (size_t)T.M * sizeof(double)))) break;
+        if ((st = alloc_dev(m, &gg, (size_t)T.M * (sizeof(double) + sizeof(float))))) break;
         T.shapes32 = static_cast<float*>(s32);
         T.S_tiles = static_cast<float*>(stiles);
         T.g32 = static_cast<float*>(g32);
         T.Gg = static_cast<double*>(gg);
+        T.Gg32 = reinterpret_cast<float*>(static_cast<double*>(gg) + T.M);
         cudaError_t e = launch_setup_toy(T, static_cast<float*>(s32), static_cast<float*>(stiles),
                                          static_cast<float*>(g32), static_cast<double*>(gg), m->stream);
         if (e != cudaSuccess) st = bx_set_error(BX_ECUDA, "set-up kernel: %s", cudaGetErrorString(e));
@@ -319,6 +320,7 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
     w.nbmax = m->nbmax;
     w.pstride = m->P;
     w.precision = m->precision;
+    w.lam_pairs = m->precision == BX_FP32;
     w.band = m->band;
     w.watchdog_ns = m->watchdog_ns;
     w.max_tiles = m->max_tiles;

@@ -57,7 +57,18 @@ __device__ __forceinline__ df df_from(double x) {
     const float h = (float)x;
     return df{h, (float)(x - (double)h)};
 }
-__device__ __forceinline__ double df_to_double(df a) { return (double)a.h + (double)a.l; }
+// Exact float -> double through the bit fields (integer pipe; the conversion instruction
+// shares GB300's FP64 pipe): zero and normal floats; subnormal, infinite and NaN inputs take
+// the conversion instruction.
+__device__ __forceinline__ double f2d(float x) {
+    const unsigned u = __float_as_uint(x), e = (u >> 23) & 0xffu;
+    if (e - 1u >= 0xfeu) {   // e == 0 or e == 255
+        if ((u << 1) == 0u) return __hiloint2double((int)u, 0);
+        return (double)x;
+    }
+    return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3)), (int)(u << 29));
+}
+__device__ __forceinline__ double df_to_double(df a) { return f2d(a.h) + f2d(a.l); }
 
 }  // namespace bx
 

@@ -17,6 +17,7 @@
 // 32 columns and are stored per half tile.
 #include <math.h>
 
+#include "bx_df.cuh"
 #include "bx_internal.cuh"
 #include "bx_resp.cuh"
 
@@ -119,6 +120,22 @@ __global__ void __launch_bounds__(F32_THREADS) k_fwd_f32(Work w) {
         }
     }
     double* lam = w.lam + (size_t)item * 2 * w.Mpad;
+    if (w.lam_pairs) {   // the Kahan sum s - c as a normalised FP32 pair
+        float2* lp = reinterpret_cast<float2*>(lam);
+        const auto pair = [](float sum, float comp) {
+            const df p = df_two_sum(sum, -comp);
+            return make_float2(p.h, p.l);
+        };
+        if (ra < M) {
+            lp[ra] = pair(sa, csa);
+            if (TAG) lp[w.Mpad + ra] = pair(ta, cta);
+        }
+        if (rb < M) {
+            lp[rb] = pair(sb, csb);
+            if (TAG) lp[w.Mpad + rb] = pair(tb, ctb);
+        }
+        return;
+    }
     if (ra < M) {
         lam[ra] = (double)sa - (double)csa;
         if (TAG) lam[w.Mpad + ra] = (double)ta - (double)cta;

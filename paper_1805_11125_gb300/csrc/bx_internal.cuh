@@ -71,6 +71,7 @@ struct Toy {
     const double* g;          // [L]
     const float* g32;         // [L]
     const double* Gg;         // [M]: sum over window bins m' of g[m' - m] (0 <= m'-m < L)
+    const float* Gg32;        // [M]: the same in FP32, stored after Gg
     const double* cnt;        // [nb] data, concatenated (vetoed, tagged, radial, PSD, 2D slices)
     const float2* cnt32;      // [nb] the same as FP32 pairs hi + lo
     const int* rad_class;     // [K]
@@ -104,9 +105,11 @@ struct Work {
     ColG* colg;               // [cap][Npad]
     double2* colS;            // [cap][Npad]: S_vetoed[i], S_tagged[i] (FP64 model)
     float2* colS32;           // [cap][Npad]: the same for the mixed-precision modes
-    double* aW;               // [cap][Npad]: window mass sum_{m in W} R[m,i] (closed form)
+    double* aW;               // [cap][Npad]: window mass sum_{m in W} R[m,i] (closed form) times 1/Phi;
+                              // as FP32 pairs (hi, lo) in the same bytes in the mixed-precision modes
     int2* colr;               // [cap][Npad]: band rows [r0, r1) of each column (empty: r0 >= r1)
-    double* lam;              // [cap][2][Mpad]: lambda_h[m] (rate-first forward)
+    double* lam;              // [cap][2][Mpad]: lambda_h[m] (rate-first forward); FP32 pairs when lam_pairs
+    int lam_pairs;            // rate-first mixed precision: the forward writes lam as FP32 pairs
     void* apart;              // [cap][max_tiles][H][Npad]: column sums of R Gg per tile, FP64 (H = 1)
                               // or per half tile (one warp's 64 rows), FP32 (H = 2)
     int2* tile_cols;          // [cap][MAX_TILES]: column range of each forward tile

@@ -21,6 +21,7 @@
 // rate gradient that do not pass through the response (the rest comes from k_bwd_*).
 #include <math.h>
 
+#include "bx_df.cuh"
 #include "bx_internal.cuh"
 
 namespace bx {
@@ -168,16 +169,13 @@ __global__ void __launch_bounds__(MID_THREADS, (sizeof(TV) == sizeof(float) && !
             }
         } else {
             // sum_m v_k[m] G_W[m] = sum_i s_k[i] ((1 - eps) aW[i] + eps a[i]), a[i] from the
-            // per-tile column sums of the forward (valid on each tile's band only).  Products
-            // and sums in compensated FP32 (TwoProduct, TwoSum): the terms are non-negative
-            // and the result is the FP64 sum to a few 1e-15 of its size, at FP32 issue cost.
+            // per-tile column sums of the forward (valid on each tile's band only)
             const int2* tcols = w.tile_cols + (size_t)item * MAX_TILES;
             constexpr int HALF = sizeof(TV) == sizeof(float) ? 2 : 1;   // slots per tile
             const TV* ap = static_cast<const TV*>(w.apart) + (size_t)item * w.max_tiles * HALF * w.Npad;
             const double* aWi = w.aW + (size_t)item * w.Npad;
             const int lane = tid & 31, wid = tid >> 5;
-            constexpr int KG = 8;   // species per pass over the columns (register budget)
-            if (sizeof(TV) == sizeof(double)) {   // FP64 model: plain FP64 products and sums
+            {   // FP64 model (the rate-first FP32 mode runs k_mid32)
                 for (int i = tid; i < T.N; i += MID_THREADS) {
                     double ag = 0.0;
                     for (int t = 0; t < T.n_tiles; ++t) {
@@ -199,34 +197,6 @@ __global__ void __launch_bounds__(MID_THREADS, (sizeof(TV) == sizeof(float) && !
                 for (int k = 0; k < 2 * KMAX; ++k) {
                     const double r = warp_sum(part[k]);
                     if (lane == 0) red[wid * 2 * KMAX + k] = r;
-                }
-            } else for (int k0 = 0; k0 < K; k0 += KG) {
-                Sum32 acc[2 * KG];
-                for (int i = tid; i < T.N; i += MID_THREADS) {
-                    float agf = 0.f;   // a few positive terms; enters G_W with weight eps
-                    for (int t = 0; t < T.n_tiles; ++t) {
-                        const int2 cr = tcols[t];
-                        if (i >= cr.x && i < cr.y)
-                            for (int h = 0; h < HALF; ++h) agf += (float)ap[((size_t)t * HALF + h) * w.Npad + i];
-                    }
-                    const double aw = aWi[i], ag = (double)agf;
-                    const double GWd = (1.0 - eps) * aw + eps * ag;
-                    const float GW = (float)GWd, GWl = (float)(GWd - (double)GW), dG = (float)(ag - aw);
-#pragma unroll
-                    for (int k = 0; k < KG; ++k)
-                        if (k0 + k < K) {
-                            const float x = T.shapes32[(size_t)(k0 + k) * T.N + i];
-                            acc[k].add_prod(x, GW, GWl);
-                            acc[KG + k].add_prod(x, dG, 0.f);
-                        }
-                }
-#pragma unroll
-                for (int k = 0; k < KG; ++k) {
-                    const Sum32 r0 = acc[k].warp_reduce(), r1 = acc[KG + k].warp_reduce();
-                    if (lane == 0 && k0 + k < KMAX) {
-                        red[wid * 2 * KMAX + k0 + k] = (double)r0.s + (double)r0.c;
-                        red[wid * 2 * KMAX + KMAX + k0 + k] = (double)r1.s + (double)r1.c;
-                    }
                 }
             }
             __syncthreads();
@@ -424,6 +394,295 @@ __global__ void __launch_bounds__(MID_THREADS, (sizeof(TV) == sizeof(float) && !
     }
 }
 
+// Baker-Cousins term from double-float n and mu, in FP32 where |x| <= 1/4 (the series of
+// bc_term32), else in FP64; the term goes into a compensated FP32 sum, wb = 1 - n/mu.
+__device__ __forceinline__ void bc_term_df(df n, df mu, Sum32& acc, float& wb) {
+    const float d = df_add(n, df_neg(mu)).h;
+    const float x = d / mu.h;
+    if (fabsf(x) <= 0.25f) {
+        const float r = 1.0f / (2.0f + x);
+        const float s = x * r, s2 = s * s;
+        const float series = fmaf(s2, fmaf(s2, fmaf(s2, 2.0f / 9.0f, 2.0f / 7.0f), 2.0f / 5.0f), 2.0f / 3.0f);
+        const float L = fmaf(s2 * s, series, -(x * x) * r);
+        acc.add(fmaf(n.h, L, d * x));
+        wb = -x;
+        return;
+    }
+    const double nd = df_to_double(n), md = df_to_double(mu);
+    const df t = df_from((md - nd) + nd * log1p((nd - md) / md));
+    acc.add(t.h);
+    acc.c = __fadd_rn(acc.c, t.l);
+    wb = (float)(1.0 - nd / md);
+}
+
+// The assembly of the rate-first mixed-precision mode (BX_FP32): the quantities of k_mid with
+// every per-bin and per-column step in FP32 or double-float FP32 (value hi + lo, ~2^-44
+// relative) instead of FP64, GB300's FP64 rate being 1/64 of its FP32 rate.  The forward
+// hands over lambda_h as FP32 pairs, the column stage the window masses aW; -lnL is a
+// compensated FP32 sum (TwoSum per term, merged across the block in FP64).  FP64 remains for
+// the radial and pulse-shape marginals (one value per bin, ~100 bins) and for the
+// Baker-Cousins terms with |n - mu| > mu / 4.
+__global__ void __launch_bounds__(MID_THREADS, 2) k_mid32(Work w, int want_grad, int want_mu) {
+    extern __shared__ double dsm[];
+    const int item = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const Toy& T = w.toys[w.toy_of[item]];
+    const int K = T.K, M = T.M, nw = T.nw, m_lo = T.m_lo, L = T.L, H = T.has_tag ? 2 : 1;
+    const int nrad = T.n_rad, npsd = T.n_psd, nb = T.nb;
+    double* gmid = w.gmid + (size_t)item * PMAX;
+    if (w.status[item]) {
+        if (tid == 0) w.nll[item] = INFINITY;
+        if (tid < PMAX) gmid[tid] = 0.0;
+        return;
+    }
+    const double* th = w.theta + (size_t)item * w.tstride;
+    const double eps = th[K + 5], s_r = th[K + 6];
+    const df epsd = df_from(eps), omed = df_from(1.0 - eps);
+    const float epsf = epsd.h, omef = omed.h;
+    const float2* lamg = reinterpret_cast<const float2*>(w.lam + (size_t)item * 2 * w.Mpad);
+
+    float2* muw = reinterpret_cast<float2*>(dsm);    // [H][nw] mu as FP32 pairs
+    float* lamT = reinterpret_cast<float*>(muw + 2 * nw);   // [H][M], reused for wt after the pile-up
+    float* puT = lamT + 2 * M;                       // [H][nw] pile-up convolution part
+    float* wvT = puT + 2 * nw;                       // [H][nw] 1 - n/mu
+    float* gT = wvT + 2 * nw;                        // [L]
+
+    __shared__ double s_rs[KMAX], s_rt[KMAX], s_SA[2 * KMAX], s_beta[KMAX];
+    __shared__ double s_pint[MAX_RAD], s_pext[MAX_RAD], s_dpext[MAX_RAD], s_mur[MAX_RAD], s_wr[MAX_RAD];
+    __shared__ double s_mup[MAX_PSD], s_wp[MAX_PSD];
+    __shared__ double red[MID_WARPS * 2 * KMAX];
+    __shared__ double s_misc[8];
+    __shared__ int s_dom;
+
+    if (tid == 0) s_dom = 0;
+    if (tid < K) {
+        const double r = th[tid], t = T.tag ? T.tag[tid] : 0.0;
+        s_rs[tid] = r * (T.tag ? 1.0 - t : 1.0);
+        s_rt[tid] = r * t;
+    }
+    for (int d = tid; d < L; d += MID_THREADS) gT[d] = T.g32[d];
+    for (int m = tid; m < M; m += MID_THREADS) {
+        lamT[m] = lamg[m].x;
+        if (H == 2) lamT[M + m] = lamg[w.Mpad + m].x;
+    }
+    __syncthreads();
+
+    // Eq. 2 on the window: mu = (1 - eps) lambda + eps (g * lambda), the convolution a
+    // compensated FP32 dot product, the mix in double-float
+    for (int idx = tid; idx < H * nw; idx += MID_THREADS) {
+        const int h = idx / nw, j = idx % nw, m = m_lo + j;
+        const float* x = lamT + h * M;
+        const int dmax = min(m, L - 1);
+        Dot32 conv;
+        for (int d = 0; d <= dmax; ++d) conv.add(gT[d], x[m - d]);
+        const float cv = __fsub_rn(conv.s, conv.c);
+        puT[idx] = cv;
+        const float2 l2 = lamg[(size_t)h * w.Mpad + m];
+        const df mu = df_add(df_mul(omed, df{l2.x, l2.y}), df_mulf(epsd, cv));
+        muw[idx] = make_float2(mu.h, mu.l);
+    }
+
+    // Eq. 4: sum_m v_k[m] G_W[m] = sum_i s_k[i] ((1 - eps) aW[i] + eps a[i]), a[i] from the
+    // per-tile column sums of the forward (valid on each tile's band only).  Products and sums
+    // in compensated FP32 (TwoProduct, TwoSum): the terms are non-negative and the result is
+    // the exact sum to a few 1e-15 of its size.
+    const bool mv = nrad > 0 || npsd > 0;
+    if (mv) {
+        const int2* tcols = w.tile_cols + (size_t)item * MAX_TILES;
+        const float* ap = static_cast<const float*>(w.apart) + (size_t)item * w.max_tiles * 2 * w.Npad;
+        const float2* aW2 = reinterpret_cast<const float2*>(w.aW + (size_t)item * w.Npad);
+        constexpr int KG = 8;   // species per pass over the columns (register budget)
+        for (int k0 = 0; k0 < K; k0 += KG) {
+            Sum32 acc[2 * KG];
+            for (int i = tid; i < T.N; i += MID_THREADS) {
+                float agf = 0.f;   // a few positive terms; enters G_W with weight eps
+                for (int t = 0; t < T.n_tiles; ++t) {
+                    const int2 cr = tcols[t];
+                    if (i >= cr.x && i < cr.y) agf += ap[((size_t)t * 2) * w.Npad + i] + ap[((size_t)t * 2 + 1) * w.Npad + i];
+                }
+                const float2 a2 = aW2[i];
+                const df aw{a2.x, a2.y};
+                // G_W = aW + eps (a - aW): eps (a - aW) in FP32 is ~5e-9 of G_W
+                const float dG = df_addf(df_neg(aw), agf).h;
+                const df GW = df_addf(aw, epsf * dG);
+#pragma unroll
+                for (int k = 0; k < KG; ++k)
+                    if (k0 + k < K) {
+                        const float x = T.shapes32[(size_t)(k0 + k) * T.N + i];
+                        acc[k].add_prod(x, GW.h, GW.l);
+                        acc[KG + k].add_prod(x, dG, 0.f);
+                    }
+            }
+#pragma unroll
+            for (int k = 0; k < KG; ++k) {
+                const Sum32 r0 = acc[k].warp_reduce(), r1 = acc[KG + k].warp_reduce();
+                if (lane == 0 && k0 + k < KMAX) {
+                    red[wid * 2 * KMAX + k0 + k] = (double)r0.s + (double)r0.c;
+                    red[wid * 2 * KMAX + KMAX + k0 + k] = (double)r1.s + (double)r1.c;
+                }
+            }
+        }
+        __syncthreads();
+        if (tid < 2 * KMAX) {   // s_SA[k] = sum v G_W, s_SA[KMAX + k] = sum v dG_W/deps
+            double v = 0.0;
+            for (int q = 0; q < MID_WARPS; ++q) v += red[q * 2 * KMAX + tid];
+            s_SA[tid] = v;
+        }
+    }
+    // radial bin probabilities (internal: uniform in volume; external: exponential from r_iv)
+    if (nrad > 0) {
+        const double lamA = T.att_len * s_r;
+        double Ft, dFt, F0, dF0;
+        shell_F(T.r_fid, T.r_iv, lamA, Ft, dFt);
+        shell_F(0.0, T.r_iv, lamA, F0, dF0);
+        const double tot = Ft - F0, dtot = dFt - dF0;
+        for (int b = tid; b < nrad; b += MID_THREADS) {
+            const double ra = T.r_fid * b / nrad, rb = T.r_fid * (b + 1) / nrad;
+            s_pint[b] = (rb * rb * rb - ra * ra * ra) / (T.r_fid * T.r_fid * T.r_fid);
+            double Fa, dFa, Fb, dFb;
+            shell_F(ra, T.r_iv, lamA, Fa, dFa);
+            shell_F(rb, T.r_iv, lamA, Fb, dFb);
+            const double p = (Fb - Fa) / tot;
+            s_pext[b] = p;
+            s_dpext[b] = ((dFb - dFa) / tot - p * dtot / tot) * T.att_len;
+        }
+    }
+    __syncthreads();
+    if (mv && tid == 0) {
+        double aint = 0.0, aext = 0.0;
+        for (int k = 0; k < K; ++k) {
+            const double A = s_rs[k] * s_SA[k];
+            if (nrad > 0 && T.rad_class[k] == BX_RAD_EXTERNAL) aext += A; else aint += A;
+        }
+        s_misc[0] = aint;
+        s_misc[1] = aext;
+    }
+    __syncthreads();
+    for (int b = tid; b < nrad; b += MID_THREADS) s_mur[b] = s_misc[0] * s_pint[b] + s_misc[1] * s_pext[b];
+    for (int j = tid; j < npsd; j += MID_THREADS) {
+        double v = 0.0;
+        for (int k = 0; k < K; ++k) v += s_rs[k] * s_SA[k] * T.psd[(size_t)k * npsd + j];
+        s_mup[j] = v;
+    }
+    __syncthreads();
+
+    // -lnL over every bin
+    Sum32 acc;
+    float geps = 0.f;
+    int dom = 0;
+    const int nwin = H * nw;
+    for (int b = tid; b < nb; b += MID_THREADS) {
+        const float2 n2 = T.cnt32[b];
+        const df n{n2.x, n2.y};
+        df mu;
+        if (b < nwin) {
+            const float2 m2 = muw[b];
+            mu = df{m2.x, m2.y};
+        } else {
+            mu = df_from(b < nwin + nrad ? s_mur[b - nwin] : s_mup[b - nwin - nrad]);
+        }
+        float wb = 1.0f;
+        if (n.h == 0.f) {
+            acc.add(mu.h);
+            acc.c = __fadd_rn(acc.c, mu.l);
+        } else if (!(mu.h > 0.f && isfinite(mu.h))) {
+            dom = 1;
+        } else {
+            bc_term_df(n, mu, acc, wb);
+        }
+        if (want_mu) w.mu[(size_t)item * w.nbmax + b] = df_to_double(mu);
+        if (want_grad) {
+            if (b < nwin) {
+                const int h = b / nw, j = b % nw;
+                wvT[b] = wb;
+                geps = fmaf(wb, puT[b] - lamT[h * M + m_lo + j], geps);
+            } else if (b < nwin + nrad) s_wr[b - nwin] = (double)wb;
+            else s_wp[b - nwin - nrad] = (double)wb;
+        }
+    }
+    acc = acc.warp_reduce();
+    geps = warp_sum(geps);
+    if (dom) s_dom = 1;
+    if (lane == 0) {
+        red[wid * 3 + 0] = (double)acc.s;
+        red[wid * 3 + 1] = (double)acc.c;
+        red[wid * 3 + 2] = (double)geps;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        Neu tot{0.0, 0.0};
+        double ge = 0.0;
+        for (int q = 0; q < MID_WARPS; ++q) {
+            tot = neu_merge(tot, Neu{red[q * 3], red[q * 3 + 1]});
+            ge += red[q * 3 + 2];
+        }
+        w.nll[item] = s_dom ? INFINITY : tot.s + tot.c;
+        if (s_dom) w.status[item] = BX_EDOMAIN;
+        s_misc[2] = ge;
+    }
+    __syncthreads();
+    if (!want_grad || s_dom) {
+        if (tid < PMAX) gmid[tid] = 0.0;
+        return;
+    }
+
+    // ---- adjoint inputs
+    // beta_k = dNLL/dA_k = sum_rho w_rad p_k[rho] + sum_j w_psd q_k[j]
+    if (mv) {
+        for (int k = wid; k < K; k += MID_WARPS) {
+            double v = 0.0;
+            const bool ext = nrad > 0 && T.rad_class[k] == BX_RAD_EXTERNAL;
+            for (int b = lane; b < nrad; b += 32) v += s_wr[b] * (ext ? s_pext[b] : s_pint[b]);
+            for (int j = lane; j < npsd; j += 32) v += s_wp[j] * T.psd[(size_t)k * npsd + j];
+            v = warp_sum(v);
+            if (lane == 0) s_beta[k] = v;
+        }
+    } else if (tid < K) {
+        s_beta[tid] = 0.0;
+    }
+    __syncthreads();
+    // pile-up-correlated weights wt_h[m] (adjoint of Eq. 2) and G_W[m], per row, in FP32
+    float* rowW = static_cast<float*>(w.rowW) + (size_t)item * 3 * w.Mpad;
+    for (int idx = tid; idx < H * M; idx += MID_THREADS) {
+        const int h = idx / M, m = idx % M;
+        const float* wh = wvT + h * nw;
+        const int d0 = max(0, m_lo - m), d1 = min(L - 1, M - 1 - m);
+        Dot32 a;
+        for (int d = d0; d <= d1; ++d) a.add(gT[d], wh[m + d - m_lo]);
+        const float direct = m >= m_lo ? omef * wh[m - m_lo] : 0.f;
+        rowW[(size_t)h * w.Mpad + m] = fmaf(epsf, __fsub_rn(a.s, a.c), direct);
+    }
+    for (int m = tid; m < M; m += MID_THREADS) {
+        if (H == 1) rowW[(size_t)w.Mpad + m] = 0.f;
+        rowW[(size_t)2 * w.Mpad + m] = mv ? fmaf(epsf, T.Gg32[m], m >= m_lo ? omef : 0.f) : 0.f;
+    }
+    // the rate gradient through the spectra comes from the adjoint kernel
+    double* coef = w.coef + (size_t)item * 3 * KMAX;
+    if (tid < K) {
+        const int k = tid;
+        const double csub = T.tag ? 1.0 - T.tag[k] : 1.0;
+        gmid[k] = mv ? s_beta[k] * csub * s_SA[k] : 0.0;
+        coef[k] = s_rs[k];
+        coef[KMAX + k] = s_rt[k];
+        coef[2 * KMAX + k] = mv ? s_beta[k] * s_rs[k] : 0.0;
+    }
+    if (tid >= K && tid < KMAX) {
+        coef[tid] = 0.0;
+        coef[KMAX + tid] = 0.0;
+        coef[2 * KMAX + tid] = 0.0;
+    }
+    if (tid == 0) {
+        double ge = s_misc[2];
+        if (mv)
+            for (int k = 0; k < K; ++k) ge += s_beta[k] * s_rs[k] * s_SA[KMAX + k];
+        double gs = 0.0;
+        for (int b = 0; b < nrad; ++b) gs += s_wr[b] * s_misc[1] * s_dpext[b];
+        for (int j = K; j < K + 5; ++j) gmid[j] = 0.0;
+        gmid[K + 5] = ge;
+        gmid[K + 6] = gs;
+        for (int j = K + 7; j < PMAX; ++j) gmid[j] = 0.0;
+    }
+}
+
 template <typename TV, bool SPECIES>
 static cudaError_t launch_mid_t(const Work& w, int n, size_t smem, int want_grad, int want_mu, cudaStream_t s) {
     // the attribute is set once per size (outside any stream capture that replays it)
@@ -446,7 +705,16 @@ cudaError_t launch_mid(const Work& w, int n, int Mmax, int nwmax, int Lmax, int 
                         (size_t)(2 * Mmax + 4 * nwmax + Lmax) * tv + 64;
     if (!f32) return launch_mid_t<double, false>(w, n, smem, want_grad, want_mu, s);
     if (w.precision == BX_TF32X3) return launch_mid_t<float, true>(w, n, smem, want_grad, want_mu, s);
-    return launch_mid_t<float, false>(w, n, smem, want_grad, want_mu, s);
+    // k_mid32: mu pairs [2][nw], then FP32 lambda [2][M], pile-up part, weights [2][nw] each, g [L]
+    const size_t smem32 = (size_t)2 * nwmax * sizeof(float2) + (size_t)(2 * Mmax + 4 * nwmax + Lmax) * sizeof(float);
+    static size_t set32 = 0;
+    if (smem32 > set32) {
+        const cudaError_t e = cudaFuncSetAttribute(k_mid32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32);
+        if (e != cudaSuccess) return e;
+        set32 = smem32;
+    }
+    k_mid32<<<n, MID_THREADS, smem32, s>>>(w, want_grad, want_mu);
+    return cudaGetLastError();
 }
 
 }  // namespace bx

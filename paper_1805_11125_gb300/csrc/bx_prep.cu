@@ -2,7 +2,8 @@
 //
 // k_setup_toy (once per toy at model creation): FP32 copies of the shapes, the shapes
 //   split into TF32 hi/lo tiles in the tensor-core operand layout, FP32 pile-up spectrum,
-//   and the pile-up window marginal Gg[m] = sum_{m' in W, 0 <= m'-m < L} g[m'-m].
+//   and the pile-up window marginal Gg[m] = sum_{m' in W, 0 <= m'-m < L} g[m'-m] (FP64, then
+//   an FP32 copy after it).
 // k_prep (once per item): Eq. 1's Birks map and resolution on the true-energy grid in
 //   FP64 (block-wide prefix sum), the column normalisation 1/Phi(mu/sigma), the FP32
 //   parameters of the generated response, the rate-weighted spectra of Eq. 3 and the band
@@ -38,6 +39,7 @@ __global__ void k_setup_toy(Toy t, float* shapes32, float* S_tiles, float* g32, 
         const int hi = min(m + t.L - 1, t.M - 1);
         for (int mp = lo; mp <= hi; ++mp) s += t.g[mp - m];
         Gg[m] = s;
+        reinterpret_cast<float*>(Gg + t.M)[m] = (float)s;
     }
 }
 
@@ -274,6 +276,15 @@ __global__ void __launch_bounds__(256) k_prep(Work w) {
     if (tid == 0) w.status[item] = s_bad ? (int)BX_EDOMAIN : 0;
 }
 
+// The mixed-precision column stage takes a Gaussian tail in FP32 from Z_F32 standard deviations
+// on: Q(3) = 1.3e-3, so FP32's relative error (a few 1e-7, the argument's rounding included)
+// stays below 1e-9 absolute; nearer the mean it takes the FP64 tail.
+constexpr float Z_F32 = 3.0f;
+constexpr float INV_SQRT_2PI_F = 0.39894228f;
+__device__ __forceinline__ float upper_tail32(float x) {
+    return x >= (float)Q_CUT ? 0.f : 0.5f * erfcf(x * 0.70710678f);
+}
+
 // Block-wide exclusive scan of two double-floats (256 threads); ta, tb receive the totals.
 __device__ void block_scan_df(df& a, df& b, df& ta, df& tb, float* sh) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -340,7 +351,7 @@ __global__ void __launch_bounds__(256) k_prep32(Work w) {
     __shared__ int s_bad;
     __shared__ int s_tlo[MAX_TILES], s_thi[MAX_TILES], s_rlo[MAX_CB], s_rhi[MAX_CB];
     __shared__ float s_rate[4][KMAX];
-    __shared__ df s_par[9];   // LY, a, b, c, kB, dE, w S_EX2, 1/w, A's constant factor
+    __shared__ df s_par[11];   // LY, a, b, c, kB, dE, w S_EX2, 1/w, A's constant factor, window edges
     if (tid == 0) s_bad = 0;
     for (int j = tid; j < MAX_TILES; j += blockDim.x) { s_tlo[j] = INT_MAX; s_thi[j] = INT_MIN; }
     for (int j = tid; j < MAX_CB; j += blockDim.x) { s_rlo[j] = INT_MAX; s_rhi[j] = INT_MIN; }
@@ -357,29 +368,30 @@ __global__ void __launch_bounds__(256) k_prep32(Work w) {
         s_rate[2][tid] = rth;
         s_rate[3][tid] = (float)(rt - (double)rth);
     }
-    if (tid < 9) {
+    if (tid < 11) {
         const double v = tid < 5    ? th[K + tid]
                          : tid == 5 ? T.dE
                          : tid == 6 ? T.w * S_EX2
                          : tid == 7 ? 1.0 / T.w
-                                    : 0.5 * INV_SQRT_2PI * GL_W_SCALE * T.w;
+                         : tid == 8 ? 0.5 * INV_SQRT_2PI * GL_W_SCALE * T.w
+                         : tid == 9 ? T.m_lo * T.w
+                                    : T.M * T.w;
         s_par[tid] = df_from(v);
     }
     __syncthreads();
     if (tid < T.P && !isfinite(th[tid])) s_bad = 1;
     if (tid == 0 && (!(th[K] > 0.0) || ((T.n_rad > 0 || T.n_r2 > 0) && !(th[K + 6] > 0.0)))) s_bad = 1;
     const df LY = s_par[0], pa = s_par[1], pb = s_par[2], pc = s_par[3], kB = s_par[4], dE = s_par[5];
-    const df wS = s_par[6], iw = s_par[7], cAw = s_par[8];
+    const df wS = s_par[6], iw = s_par[7], cAw = s_par[8], zlo = s_par[9], zhi = s_par[10];
     const double w_ = T.w;
     const float wf = (float)w_, inv_wf = iw.h, bandf = (float)w.band;
     const float e_min = -2.0f * wf, e_max = (M + 2.0f) * wf;
-    const float zlo_f = (float)(T.m_lo * w_), zhi_f = (float)(M * w_);
     Col64* col = w.col64 + (size_t)item * w.Npad;
     double2* cq = w.colq + (size_t)item * w.Npad;
     float4* cf = w.colf + (size_t)item * w.Npad;
     ColG* cg = w.colg + (size_t)item * w.Npad;
     float2* cs32 = w.colS32 + (size_t)item * w.Npad;
-    double* aW = w.aW + (size_t)item * w.Npad;
+    float2* aW2 = reinterpret_cast<float2*>(w.aW + (size_t)item * w.Npad);   // FP32 pairs in this mode
     int2* cr = w.colr + (size_t)item * w.Npad;
     const df gln{0.38729834f, (float)(0.38729833462074170 - (double)0.38729834f)};   // sqrt(3/5) / 2
     const df ln4{1.3862944f, (float)(1.3862943611198906 - (double)1.3862944f)};      // 2 ln 2
@@ -420,11 +432,18 @@ __global__ void __launch_bounds__(256) k_prep32(Work w) {
             const df z = df_mul(mu, isig);
             const double mud = df_to_double(mu), sigd = df_to_double(sig);
             double norm = 1.0, mills = 0.0;
-            if (z.h < (float)Q_CUT) {
+            df normd{1.f, 0.f};
+            if (z.h < Z_F32) {
                 const double zd = df_to_double(z);
                 const double Phi = zd > 0.0 ? 1.0 - upper_tail(zd) : upper_tail(-zd);
                 norm = 1.0 / Phi;
                 mills = INV_SQRT_2PI * exp(-0.5 * zd * zd) * norm;
+                normd = df_from(norm);
+            } else if (z.h < (float)Q_CUT) {   // Q(z) <= 1.3e-3
+                const float q = upper_tail32(z.h), qn = q / (1.0f - q);
+                normd = df_fast(1.0f, qn);
+                norm = df_to_double(normd);
+                mills = f2d(INV_SQRT_2PI_F * exp2f(-0.72134752f * df_mul(z, z).h) * (1.0f + qn));
             }
             col[i] = Col64{mud, sigd, norm, mills};
             // generator constants: t0 = (m + 1/2 - mu/w) hs = (m - jf) hs + c
@@ -436,7 +455,7 @@ __global__ void __launch_bounds__(256) k_prep32(Work w) {
             const df cc = df_mul(df_addf(df_neg(frac), 0.5f), hs);
             cf[i] = make_float4(jf, cc.h, hs.h, hs.l);
             const df kk = df_mul(gln, hs), kq = df_mul(kk, kk);
-            const df Ad = df_mul(df_mul(cAw, isig), df_from(norm));
+            const df Ad = df_mul(df_mul(cAw, isig), normd);
             cg[i] = ColG{df_mul(ln4, kk).h, 2.0f * exp2_neg(-kq.h, -kq.l), cc.l, Ad.h};
             // rate-weighted spectra of the vetoed (or single) and tagged events (Eq. 3)
             if (T.shapes32) {
@@ -457,16 +476,18 @@ __global__ void __launch_bounds__(256) k_prep32(Work w) {
                 }
                 cs32[i] = make_float2((float)ssub, (float)stag);
             }
-            // window mass: erfc only for window edges within 9 sigma
-            const float za = (zlo_f - mu.h) * isig.h, zb = (zhi_f - mu.h) * isig.h;
-            double mass;
-            if (za <= -9.0f && zb >= 9.0f) mass = 1.0;
-            else if (za >= 9.0f || zb <= -9.0f) mass = 0.0;
-            else {
-                const double isd = df_to_double(isig);
-                mass = gauss_mass((T.m_lo * w_ - mud) * isd, (M * w_ - mud) * isd);
-            }
-            aW[i] = mass * norm;
+            // window mass times 1/Phi, as an FP32 pair; FP64 only for an edge within 3 sigma of mu
+            const df zad = df_mul(df_add(zlo, df_neg(mu)), isig), zbd = df_mul(df_add(zhi, df_neg(mu)), isig);
+            const float za = zad.h, zb = zbd.h;
+            df mass;
+            if (za <= -(float)Q_CUT && zb >= (float)Q_CUT) mass = df{1.f, 0.f};
+            else if (za >= (float)Q_CUT || zb <= -(float)Q_CUT) mass = df{0.f, 0.f};
+            else if (fabsf(za) < Z_F32 || fabsf(zb) < Z_F32) mass = df_from(gauss_mass(df_to_double(zad), df_to_double(zbd)));
+            else if (za >= 0.f) mass = df{upper_tail32(za) - upper_tail32(zb), 0.f};
+            else if (zb <= 0.f) mass = df{upper_tail32(-zb) - upper_tail32(-za), 0.f};
+            else mass = df_two_sum(1.0f, -(upper_tail32(zb) + upper_tail32(-za)));
+            const df aw = df_mul(mass, normd);
+            aW2[i] = make_float2(aw.h, aw.l);
             // response band
             const float lo_e = fminf(fmaxf(mu.h - bandf * sig.h, e_min), e_max);
             const float hi_e = fminf(fmaxf(mu.h + bandf * sig.h, e_min), e_max);
@@ -503,7 +524,7 @@ __global__ void __launch_bounds__(256) k_prep32(Work w) {
         cf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         cg[i] = ColG{0.f, 0.f, 0.f, 0.f};
         cs32[i] = make_float2(0.f, 0.f);
-        aW[i] = 0.0;
+        aW2[i] = make_float2(0.f, 0.f);
         cr[i] = make_int2(0, 0);
     }
     if (bad) s_bad = 1;
