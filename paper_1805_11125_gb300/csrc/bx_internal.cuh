@@ -324,22 +324,37 @@ __device__ __forceinline__ Neu neu_merge(Neu a, Neu b) {
     return a;
 }
 
-// Baker-Cousins term (mu - n) + n ln(n/mu) (n > 0) and its weight 1 - n/mu in FP32, for
-// |x| <= 1/4 with x = (n - mu)/mu (every bin of a reasonable fit).  Written without
-// cancellation: the term is n (log1p(x) - x) + (n - mu) x, and with s = x / (2 + x),
-//   log1p(x) - x = 2 atanh(s) - x = -x^2 / (2 + x) + 2 (s^3/3 + s^5/5 + s^7/7 + s^9/9 + ...),
-// |s| <= 1/7, truncated after s^9 (next term < 1e-10); each piece has FP32 relative error, the
-// term (~(n - mu)^2 / 2mu, ~1/2) an absolute error ~1e-7 with no systematic sign.  Other bins
-// take the FP64 form.  Returns false when |x| > 1/4.
+// log1p(x) - x in FP32 without cancellation for BC_XLO <= x <= BC_XHI.  With s = x / (2 + x)
+// (|s| <= 1/3), log1p(x) = 2 atanh(s), so
+//   log1p(x) - x = -x^2 / (2 + x) + 2 (s^3/3 + s^5/5 + ... + s^19/19) + O(2 s^21 / 21),
+// the truncation below 1e-11; the two parts have the same sign for x < 0 and the series is
+// under a tenth of the first part for x > 0, so the result carries FP32 relative error.
+constexpr float BC_XLO = -0.5f, BC_XHI = 1.0f;
+__device__ __forceinline__ float log1p_minus_x32(float x) {
+    const float r = 1.0f / (2.0f + x);
+    const float s = x * r, s2 = s * s;
+    float p = 2.0f / 19.0f;
+    p = fmaf(s2, p, 2.0f / 17.0f);
+    p = fmaf(s2, p, 2.0f / 15.0f);
+    p = fmaf(s2, p, 2.0f / 13.0f);
+    p = fmaf(s2, p, 2.0f / 11.0f);
+    p = fmaf(s2, p, 2.0f / 9.0f);
+    p = fmaf(s2, p, 2.0f / 7.0f);
+    p = fmaf(s2, p, 2.0f / 5.0f);
+    p = fmaf(s2, p, 2.0f / 3.0f);
+    return fmaf(s2 * s, p, -(x * x) * r);
+}
+
+// Baker-Cousins term (mu - n) + n ln(n/mu) (n > 0) and its weight 1 - n/mu in FP32 for
+// x = (n - mu)/mu in [BC_XLO, BC_XHI] (every bin of a reasonable fit): written as
+// n (log1p(x) - x) + (n - mu) x, a sum of two terms within a factor ~3 of the result, so the
+// term carries an FP32 relative error with no systematic sign.  Other bins take the FP64
+// form.  Returns false outside the range.
 __device__ __forceinline__ bool bc_term32(double n, double mu, double& term, double& wb) {
     const float d = (float)(n - mu);
     const float x = d / (float)mu;
-    if (!(fabsf(x) <= 0.25f)) return false;
-    const float r = 1.0f / (2.0f + x);
-    const float s = x * r, s2 = s * s;
-    const float series = fmaf(s2, fmaf(s2, fmaf(s2, 2.0f / 9.0f, 2.0f / 7.0f), 2.0f / 5.0f), 2.0f / 3.0f);
-    const float L = fmaf(s2 * s, series, -(x * x) * r);
-    term = (double)fmaf((float)n, L, d * x);
+    if (!(x >= BC_XLO && x <= BC_XHI)) return false;
+    term = (double)fmaf((float)n, log1p_minus_x32(x), d * x);
     wb = (double)(-x);
     return true;
 }

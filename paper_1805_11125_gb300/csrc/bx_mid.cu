@@ -12,7 +12,7 @@
 //          sum_k A_k p_k[rho] (closed-form shell integrals) and pulse-shape bins
 //          sum_k A_k q_k[j];
 //   -lnL   sum of mu - n + n log1p((n - mu)/mu): the terms in FP64, or for the
-//          mixed-precision modes in a cancellation-free FP32 form where |n - mu| <= mu/4;
+//          mixed-precision modes in a cancellation-free FP32 form where mu/2 <= n <= 2 mu;
 //          the sum in FP64 with Neumaier compensation inside each thread and TwoSum-style
 //          merging across the block.
 // With want_grad it also writes the adjoint inputs of the response stage: per row the
@@ -68,10 +68,33 @@ struct Dot64 {
 template <typename TV> struct DotT { using type = Dot64; };
 template <> struct DotT<float> { using type = Dot32; };
 
+// Radial bin probabilities of the Eq. 4 marginal: internal events uniform in volume,
+// external ones exponential in depth from r_iv (attenuation length att_len s_r), with the
+// shell integrals at the nrad + 1 bin edges and at r = 0 taken once each.  Called by the whole
+// block (one barrier inside).
+__device__ void radial_probs(const Toy& T, double s_r, double* sF, double* sdF, double* pint, double* pext,
+                             double* dpext) {
+    const int nrad = T.n_rad;
+    const double lamA = T.att_len * s_r;
+    for (int e = threadIdx.x; e <= nrad + 1; e += blockDim.x) {
+        const double r = e < nrad ? T.r_fid * e / nrad : (e == nrad ? T.r_fid : 0.0);
+        shell_F(r, T.r_iv, lamA, sF[e], sdF[e]);
+    }
+    __syncthreads();
+    const double tot = sF[nrad] - sF[nrad + 1], dtot = sdF[nrad] - sdF[nrad + 1];
+    for (int b = threadIdx.x; b < nrad; b += blockDim.x) {
+        const double ra = T.r_fid * b / nrad, rb = T.r_fid * (b + 1) / nrad;
+        pint[b] = (rb * rb * rb - ra * ra * ra) / (T.r_fid * T.r_fid * T.r_fid);
+        const double p = (sF[b + 1] - sF[b]) / tot;
+        pext[b] = p;
+        dpext[b] = ((sdF[b + 1] - sdF[b]) / tot - p * dtot / tot) * T.att_len;
+    }
+}
+
 template <typename TV, bool SPECIES>
 __global__ void __launch_bounds__(MID_THREADS, (sizeof(TV) == sizeof(float) && !SPECIES) ? 2 : 1)
     k_mid(Work w, int want_grad, int want_mu) {
-    extern __shared__ double dsm[];
+    extern __shared__ __align__(16) double dsm[];
     const int item = blockIdx.x, tid = threadIdx.x;
     const Toy& T = w.toys[w.toy_of[item]];
     const int K = T.K, M = T.M, nw = T.nw, m_lo = T.m_lo, L = T.L, H = T.has_tag ? 2 : 1;
@@ -95,6 +118,7 @@ __global__ void __launch_bounds__(MID_THREADS, (sizeof(TV) == sizeof(float) && !
 
     __shared__ double s_rs[KMAX], s_rt[KMAX], s_SA[2 * KMAX], s_beta[KMAX], s_gr[2 * KMAX];
     __shared__ double s_pint[MAX_RAD], s_pext[MAX_RAD], s_dpext[MAX_RAD], s_mur[MAX_RAD], s_wr[MAX_RAD];
+    __shared__ double s_F[MAX_RAD + 2], s_dF[MAX_RAD + 2];
     __shared__ double s_mup[MAX_PSD], s_wp[MAX_PSD];
     __shared__ double red[MID_WARPS * 2 * KMAX];
     __shared__ double s_misc[8];
@@ -211,23 +235,7 @@ __global__ void __launch_bounds__(MID_THREADS, (sizeof(TV) == sizeof(float) && !
         if (species) block_sum<2 * KMAX>(part, red, s_SA);
     }
     // radial bin probabilities (internal: uniform in volume; external: exponential from r_iv)
-    if (nrad > 0) {
-        const double lamA = T.att_len * s_r;
-        double Ft, dFt, F0, dF0;
-        shell_F(T.r_fid, T.r_iv, lamA, Ft, dFt);
-        shell_F(0.0, T.r_iv, lamA, F0, dF0);
-        const double tot = Ft - F0, dtot = dFt - dF0;
-        for (int b = tid; b < nrad; b += MID_THREADS) {
-            const double ra = T.r_fid * b / nrad, rb = T.r_fid * (b + 1) / nrad;
-            s_pint[b] = (rb * rb * rb - ra * ra * ra) / (T.r_fid * T.r_fid * T.r_fid);
-            double Fa, dFa, Fb, dFb;
-            shell_F(ra, T.r_iv, lamA, Fa, dFa);
-            shell_F(rb, T.r_iv, lamA, Fb, dFb);
-            const double p = (Fb - Fa) / tot;
-            s_pext[b] = p;
-            s_dpext[b] = ((dFb - dFa) / tot - p * dtot / tot) * T.att_len;
-        }
-    }
+    if (nrad > 0) radial_probs(T, s_r, s_F, s_dF, s_pint, s_pext, s_dpext);
     __syncthreads();
     if (mv && tid == 0) {
         double aint = 0.0, aext = 0.0;
@@ -394,17 +402,98 @@ __global__ void __launch_bounds__(MID_THREADS, (sizeof(TV) == sizeof(float) && !
     }
 }
 
-// Baker-Cousins term from double-float n and mu, in FP32 where |x| <= 1/4 (the series of
-// bc_term32), else in FP64; the term goes into a compensated FP32 sum, wb = 1 - n/mu.
+// Register-blocked pile-up sums: PR consecutive outputs per thread, g read four taps at a
+// time, a sliding window of the other operand in registers.  Plain FP32 partial sums over 32
+// taps are folded into a Kahan pair: the partials are of the size of their terms, so no tail
+// term falls below the accumulator's rounding (the one-sided loss a plain running sum has).
+constexpr int PR = 4;
+constexpr int PBLK = 8;   // chunks of PR taps per partial sum
+struct Kahan4 {
+    float s[PR], c[PR], p[PR];
+    __device__ __forceinline__ Kahan4() {
+#pragma unroll
+        for (int j = 0; j < PR; ++j) s[j] = c[j] = p[j] = 0.f;
+    }
+    __device__ __forceinline__ void fold() {
+#pragma unroll
+        for (int j = 0; j < PR; ++j) {
+            const float y = __fsub_rn(p[j], c[j]);
+            const float t = __fadd_rn(s[j], y);
+            c[j] = __fsub_rn(__fsub_rn(t, s[j]), y);
+            s[j] = t;
+            p[j] = 0.f;
+        }
+    }
+    __device__ __forceinline__ float value(int j) const { return __fsub_rn(s[j], c[j]); }
+};
+
+// Convolution out_j = sum_{d < dend} g[d] x[base + j - d], j < PR.  g: 16-byte aligned, zero
+// from L up to a multiple of PR; x readable (zero) from base - dend - 10 to base + PR - 1.
+__device__ __forceinline__ void conv_block(const float* g, const float* x, int base, int dend, Kahan4& k) {
+    float xw[2 * PR - 1];   // xw[t] = x[base - d0 - 3 + t]
+#pragma unroll
+    for (int t = 0; t < 2 * PR - 1; ++t) xw[t] = x[base - 3 + t];
+    int cnt = 0;
+    for (int d0 = 0; d0 < dend; d0 += PR) {
+        const float4 g4 = *reinterpret_cast<const float4*>(g + d0);
+        const float gg[PR] = {g4.x, g4.y, g4.z, g4.w};
+#pragma unroll
+        for (int t = 0; t < PR; ++t)
+#pragma unroll
+            for (int j = 0; j < PR; ++j) k.p[j] = fmaf(gg[t], xw[3 + j - t], k.p[j]);
+#pragma unroll
+        for (int t = 2 * PR - 2; t >= PR; --t) xw[t] = xw[t - PR];
+#pragma unroll
+        for (int t = 0; t < PR; ++t) xw[t] = x[base - d0 - 7 + t];
+        if (++cnt == PBLK) {
+            k.fold();
+            cnt = 0;
+        }
+    }
+    k.fold();
+}
+
+// Correlation out_j = sum_{d0s <= d < dend} g[d] y[base + j + d], j < PR, d0s a multiple of
+// PR.  y readable (zero) from base + d0s to base + dend + 9.
+__device__ __forceinline__ void corr_block(const float* g, const float* y, int base, int d0s, int dend, Kahan4& k) {
+    float yw[2 * PR - 1];   // yw[t] = y[base + d0 + t]
+#pragma unroll
+    for (int t = 0; t < 2 * PR - 1; ++t) yw[t] = y[base + d0s + t];
+    int cnt = 0;
+    for (int d0 = d0s; d0 < dend; d0 += PR) {
+        const float4 g4 = *reinterpret_cast<const float4*>(g + d0);
+        const float gg[PR] = {g4.x, g4.y, g4.z, g4.w};
+#pragma unroll
+        for (int t = 0; t < PR; ++t)
+#pragma unroll
+            for (int j = 0; j < PR; ++j) k.p[j] = fmaf(gg[t], yw[j + t], k.p[j]);
+#pragma unroll
+        for (int t = 0; t < PR - 1; ++t) yw[t] = yw[t + PR];
+#pragma unroll
+        for (int t = PR - 1; t < 2 * PR - 1; ++t) yw[t] = y[base + d0 + PR + t];
+        if (++cnt == PBLK) {
+            k.fold();
+            cnt = 0;
+        }
+    }
+    k.fold();
+}
+
+// Zero padding of the pile-up operands in shared memory
+constexpr int PAD_LAM = 16;   // before each lambda row (and 4 after)
+constexpr int PAD_WV = 8;     // before each weight row (and 16 after)
+__host__ __device__ constexpr int mid32_lrow(int M) { return PAD_LAM + M + 4; }
+__host__ __device__ constexpr int mid32_wrow(int nw) { return PAD_WV + nw + 16; }
+__host__ __device__ constexpr int mid32_gn(int L) { return ((L + PR - 1) / PR) * PR + PR; }
+
+// Baker-Cousins term from double-float n and mu, in FP32 for x = (n - mu)/mu in
+// [BC_XLO, BC_XHI] (as bc_term32), else in FP64; the term goes into a compensated FP32 sum,
+// wb = 1 - n/mu.
 __device__ __forceinline__ void bc_term_df(df n, df mu, Sum32& acc, float& wb) {
     const float d = df_add(n, df_neg(mu)).h;
     const float x = d / mu.h;
-    if (fabsf(x) <= 0.25f) {
-        const float r = 1.0f / (2.0f + x);
-        const float s = x * r, s2 = s * s;
-        const float series = fmaf(s2, fmaf(s2, fmaf(s2, 2.0f / 9.0f, 2.0f / 7.0f), 2.0f / 5.0f), 2.0f / 3.0f);
-        const float L = fmaf(s2 * s, series, -(x * x) * r);
-        acc.add(fmaf(n.h, L, d * x));
+    if (x >= BC_XLO && x <= BC_XHI) {
+        acc.add(fmaf(n.h, log1p_minus_x32(x), d * x));
         wb = -x;
         return;
     }
@@ -421,9 +510,9 @@ __device__ __forceinline__ void bc_term_df(df n, df mu, Sum32& acc, float& wb) {
 // hands over lambda_h as FP32 pairs, the column stage the window masses aW; -lnL is a
 // compensated FP32 sum (TwoSum per term, merged across the block in FP64).  FP64 remains for
 // the radial and pulse-shape marginals (one value per bin, ~100 bins) and for the
-// Baker-Cousins terms with |n - mu| > mu / 4.
+// Baker-Cousins terms outside mu/2 <= n <= 2 mu.
 __global__ void __launch_bounds__(MID_THREADS, 2) k_mid32(Work w, int want_grad, int want_mu) {
-    extern __shared__ double dsm[];
+    extern __shared__ __align__(16) double dsm[];
     const int item = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const Toy& T = w.toys[w.toy_of[item]];
     const int K = T.K, M = T.M, nw = T.nw, m_lo = T.m_lo, L = T.L, H = T.has_tag ? 2 : 1;
@@ -436,18 +525,25 @@ __global__ void __launch_bounds__(MID_THREADS, 2) k_mid32(Work w, int want_grad,
     }
     const double* th = w.theta + (size_t)item * w.tstride;
     const double eps = th[K + 5], s_r = th[K + 6];
-    const df epsd = df_from(eps), omed = df_from(1.0 - eps);
-    const float epsf = epsd.h, omef = omed.h;
+    __shared__ float s_eps[4];   // eps and 1 - eps as FP32 pairs
+    if (tid == 0) {
+        const df e = df_from(eps), o = df_from(1.0 - eps);
+        s_eps[0] = e.h; s_eps[1] = e.l; s_eps[2] = o.h; s_eps[3] = o.l;
+    }
     const float2* lamg = reinterpret_cast<const float2*>(w.lam + (size_t)item * 2 * w.Mpad);
 
-    float2* muw = reinterpret_cast<float2*>(dsm);    // [H][nw] mu as FP32 pairs
-    float* lamT = reinterpret_cast<float*>(muw + 2 * nw);   // [H][M], reused for wt after the pile-up
-    float* puT = lamT + 2 * M;                       // [H][nw] pile-up convolution part
-    float* wvT = puT + 2 * nw;                       // [H][nw] 1 - n/mu
-    float* gT = wvT + 2 * nw;                        // [L]
+    const int lrow = mid32_lrow(M), wrow = mid32_wrow(nw), gn = mid32_gn(L);
+    float2* muw = reinterpret_cast<float2*>(dsm);          // [H][nw] mu as FP32 pairs
+    float* gT = reinterpret_cast<float*>(muw + 2 * nw);     // [gn] g, zero-padded (16-byte aligned)
+    float* lamP = gT + gn;                                  // [H][lrow] FP32 lambda, zero-padded
+    float* puT = lamP + 2 * lrow;                           // [H][nw] pile-up convolution part
+    float* wvP = puT + 2 * nw;                              // [H][wrow] 1 - n/mu, zero-padded
+    float2* colGW = reinterpret_cast<float2*>(wvP + 2 * wrow);   // [N] G_W per column (8-byte aligned)
+    float* coldG = reinterpret_cast<float*>(colGW + T.N);        // [N] dG_W/deps per column
 
     __shared__ double s_rs[KMAX], s_rt[KMAX], s_SA[2 * KMAX], s_beta[KMAX];
     __shared__ double s_pint[MAX_RAD], s_pext[MAX_RAD], s_dpext[MAX_RAD], s_mur[MAX_RAD], s_wr[MAX_RAD];
+    __shared__ double s_F[MAX_RAD + 2], s_dF[MAX_RAD + 2];
     __shared__ double s_mup[MAX_PSD], s_wp[MAX_PSD];
     __shared__ double red[MID_WARPS * 2 * KMAX];
     __shared__ double s_misc[8];
@@ -459,93 +555,78 @@ __global__ void __launch_bounds__(MID_THREADS, 2) k_mid32(Work w, int want_grad,
         s_rs[tid] = r * (T.tag ? 1.0 - t : 1.0);
         s_rt[tid] = r * t;
     }
-    for (int d = tid; d < L; d += MID_THREADS) gT[d] = T.g32[d];
-    for (int m = tid; m < M; m += MID_THREADS) {
-        lamT[m] = lamg[m].x;
-        if (H == 2) lamT[M + m] = lamg[w.Mpad + m].x;
+    for (int d = tid; d < gn; d += MID_THREADS) gT[d] = d < L ? T.g32[d] : 0.f;
+    for (int q = tid; q < 2 * lrow; q += MID_THREADS) {
+        const int h = q / lrow, m = q % lrow - PAD_LAM;
+        lamP[q] = (h < H && m >= 0 && m < M) ? lamg[(size_t)h * w.Mpad + m].x : 0.f;
     }
+    for (int q = tid; q < 2 * wrow; q += MID_THREADS) wvP[q] = 0.f;
     __syncthreads();
+    const df epsd{s_eps[0], s_eps[1]}, omed{s_eps[2], s_eps[3]};
+    const float epsf = epsd.h, omef = omed.h;
 
-    // Eq. 2 on the window: mu = (1 - eps) lambda + eps (g * lambda), the convolution a
-    // compensated FP32 dot product, the mix in double-float
-    for (int idx = tid; idx < H * nw; idx += MID_THREADS) {
-        const int h = idx / nw, j = idx % nw, m = m_lo + j;
-        const float* x = lamT + h * M;
-        const int dmax = min(m, L - 1);
-        Dot32 conv;
-        for (int d = 0; d <= dmax; ++d) conv.add(gT[d], x[m - d]);
-        const float cv = __fsub_rn(conv.s, conv.c);
-        puT[idx] = cv;
-        const float2 l2 = lamg[(size_t)h * w.Mpad + m];
-        const df mu = df_add(df_mul(omed, df{l2.x, l2.y}), df_mulf(epsd, cv));
-        muw[idx] = make_float2(mu.h, mu.l);
+    // Eq. 2 on the window: mu = (1 - eps) lambda + eps (g * lambda), the convolution in
+    // compensated FP32 (conv_block), the mix in double-float
+    const int ngw = (nw + PR - 1) / PR;
+    for (int q = tid; q < H * ngw; q += MID_THREADS) {
+        const int h = q / ngw, j0 = (q % ngw) * PR, m0 = m_lo + j0;
+        Kahan4 k;
+        conv_block(gT, lamP + h * lrow + PAD_LAM, m0, min(L, m0 + PR), k);
+#pragma unroll
+        for (int j = 0; j < PR; ++j)
+            if (j0 + j < nw) {
+                const float cv = k.value(j);
+                puT[h * nw + j0 + j] = cv;
+                const float2 l2 = lamg[(size_t)h * w.Mpad + m0 + j];
+                const df mu = df_add(df_mul(omed, df{l2.x, l2.y}), df_mulf(epsd, cv));
+                muw[h * nw + j0 + j] = make_float2(mu.h, mu.l);
+            }
     }
 
     // Eq. 4: sum_m v_k[m] G_W[m] = sum_i s_k[i] ((1 - eps) aW[i] + eps a[i]), a[i] from the
-    // per-tile column sums of the forward (valid on each tile's band only).  Products and sums
-    // in compensated FP32 (TwoProduct, TwoSum): the terms are non-negative and the result is
-    // the exact sum to a few 1e-15 of its size.
+    // per-tile column sums of the forward (valid on each tile's band only).  G_W per column
+    // first (double-float), then one warp per species, its lanes splitting the columns;
+    // products and sums in compensated FP32 (TwoProduct, TwoSum): the terms are non-negative
+    // and the result is the exact sum to a few 1e-15 of its size.
     const bool mv = nrad > 0 || npsd > 0;
     if (mv) {
         const int2* tcols = w.tile_cols + (size_t)item * MAX_TILES;
         const float* ap = static_cast<const float*>(w.apart) + (size_t)item * w.max_tiles * 2 * w.Npad;
         const float2* aW2 = reinterpret_cast<const float2*>(w.aW + (size_t)item * w.Npad);
-        constexpr int KG = 8;   // species per pass over the columns (register budget)
-        for (int k0 = 0; k0 < K; k0 += KG) {
-            Sum32 acc[2 * KG];
-            for (int i = tid; i < T.N; i += MID_THREADS) {
-                float agf = 0.f;   // a few positive terms; enters G_W with weight eps
-                for (int t = 0; t < T.n_tiles; ++t) {
-                    const int2 cr = tcols[t];
-                    if (i >= cr.x && i < cr.y) agf += ap[((size_t)t * 2) * w.Npad + i] + ap[((size_t)t * 2 + 1) * w.Npad + i];
-                }
-                const float2 a2 = aW2[i];
-                const df aw{a2.x, a2.y};
-                // G_W = aW + eps (a - aW): eps (a - aW) in FP32 is ~5e-9 of G_W
-                const float dG = df_addf(df_neg(aw), agf).h;
-                const df GW = df_addf(aw, epsf * dG);
-#pragma unroll
-                for (int k = 0; k < KG; ++k)
-                    if (k0 + k < K) {
-                        const float x = T.shapes32[(size_t)(k0 + k) * T.N + i];
-                        acc[k].add_prod(x, GW.h, GW.l);
-                        acc[KG + k].add_prod(x, dG, 0.f);
-                    }
+        for (int i = tid; i < T.N; i += MID_THREADS) {
+            float agf = 0.f;   // a few positive terms; enters G_W with weight eps
+            for (int t = 0; t < T.n_tiles; ++t) {
+                const int2 cr = tcols[t];
+                if (i >= cr.x && i < cr.y) agf += ap[((size_t)t * 2) * w.Npad + i] + ap[((size_t)t * 2 + 1) * w.Npad + i];
             }
-#pragma unroll
-            for (int k = 0; k < KG; ++k) {
-                const Sum32 r0 = acc[k].warp_reduce(), r1 = acc[KG + k].warp_reduce();
-                if (lane == 0 && k0 + k < KMAX) {
-                    red[wid * 2 * KMAX + k0 + k] = (double)r0.s + (double)r0.c;
-                    red[wid * 2 * KMAX + KMAX + k0 + k] = (double)r1.s + (double)r1.c;
-                }
-            }
+            const float2 a2 = aW2[i];
+            const df aw{a2.x, a2.y};
+            // G_W = aW + eps (a - aW): eps (a - aW) in FP32 is ~5e-9 of G_W
+            const float dG = df_addf(df_neg(aw), agf).h;
+            const df GW = df_addf(aw, epsf * dG);
+            colGW[i] = make_float2(GW.h, GW.l);
+            coldG[i] = dG;
         }
         __syncthreads();
-        if (tid < 2 * KMAX) {   // s_SA[k] = sum v G_W, s_SA[KMAX + k] = sum v dG_W/deps
-            double v = 0.0;
-            for (int q = 0; q < MID_WARPS; ++q) v += red[q * 2 * KMAX + tid];
-            s_SA[tid] = v;
+        for (int k = wid; k < K; k += MID_WARPS) {
+            Sum32 a0, a1;
+            const float* sk = T.shapes32 + (size_t)k * T.N;
+            for (int i = lane; i < T.N; i += 32) {
+                const float x = sk[i];
+                const float2 g2 = colGW[i];
+                a0.add_prod(x, g2.x, g2.y);
+                a1.add_prod(x, coldG[i], 0.f);
+            }
+            a0 = a0.warp_reduce();
+            a1 = a1.warp_reduce();
+            if (lane == 0) {   // s_SA[k] = sum v G_W, s_SA[KMAX + k] = sum v dG_W/deps
+                s_SA[k] = (double)a0.s + (double)a0.c;
+                s_SA[KMAX + k] = (double)a1.s + (double)a1.c;
+            }
         }
     }
     // radial bin probabilities (internal: uniform in volume; external: exponential from r_iv)
-    if (nrad > 0) {
-        const double lamA = T.att_len * s_r;
-        double Ft, dFt, F0, dF0;
-        shell_F(T.r_fid, T.r_iv, lamA, Ft, dFt);
-        shell_F(0.0, T.r_iv, lamA, F0, dF0);
-        const double tot = Ft - F0, dtot = dFt - dF0;
-        for (int b = tid; b < nrad; b += MID_THREADS) {
-            const double ra = T.r_fid * b / nrad, rb = T.r_fid * (b + 1) / nrad;
-            s_pint[b] = (rb * rb * rb - ra * ra * ra) / (T.r_fid * T.r_fid * T.r_fid);
-            double Fa, dFa, Fb, dFb;
-            shell_F(ra, T.r_iv, lamA, Fa, dFa);
-            shell_F(rb, T.r_iv, lamA, Fb, dFb);
-            const double p = (Fb - Fa) / tot;
-            s_pext[b] = p;
-            s_dpext[b] = ((dFb - dFa) / tot - p * dtot / tot) * T.att_len;
-        }
-    }
+    if (nrad > 0) radial_probs(T, s_r, s_F, s_dF, s_pint, s_pext, s_dpext);
     __syncthreads();
     if (mv && tid == 0) {
         double aint = 0.0, aext = 0.0;
@@ -593,8 +674,8 @@ __global__ void __launch_bounds__(MID_THREADS, 2) k_mid32(Work w, int want_grad,
         if (want_grad) {
             if (b < nwin) {
                 const int h = b / nw, j = b % nw;
-                wvT[b] = wb;
-                geps = fmaf(wb, puT[b] - lamT[h * M + m_lo + j], geps);
+                wvP[h * wrow + PAD_WV + j] = wb;
+                geps = fmaf(wb, puT[b] - lamP[h * lrow + PAD_LAM + m_lo + j], geps);
             } else if (b < nwin + nrad) s_wr[b - nwin] = (double)wb;
             else s_wp[b - nwin - nrad] = (double)wb;
         }
@@ -640,16 +721,24 @@ __global__ void __launch_bounds__(MID_THREADS, 2) k_mid32(Work w, int want_grad,
         s_beta[tid] = 0.0;
     }
     __syncthreads();
-    // pile-up-correlated weights wt_h[m] (adjoint of Eq. 2) and G_W[m], per row, in FP32
+    // pile-up-correlated weights wt_h[m] (adjoint of Eq. 2) and G_W[m], per row, in FP32:
+    // wt_h[m] = (1 - eps) w_h[m] [m in W] + eps sum_d g[d] w_h[m + d]
     float* rowW = static_cast<float*>(w.rowW) + (size_t)item * 3 * w.Mpad;
-    for (int idx = tid; idx < H * M; idx += MID_THREADS) {
-        const int h = idx / M, m = idx % M;
-        const float* wh = wvT + h * nw;
-        const int d0 = max(0, m_lo - m), d1 = min(L - 1, M - 1 - m);
-        Dot32 a;
-        for (int d = d0; d <= d1; ++d) a.add(gT[d], wh[m + d - m_lo]);
-        const float direct = m >= m_lo ? omef * wh[m - m_lo] : 0.f;
-        rowW[(size_t)h * w.Mpad + m] = fmaf(epsf, __fsub_rn(a.s, a.c), direct);
+    const int ngm = (M + PR - 1) / PR;
+    for (int q = tid; q < H * ngm; q += MID_THREADS) {
+        const int h = q / ngm, m0 = (q % ngm) * PR, base = m0 - m_lo;   // window index at d = 0
+        const int d0s = max(0, -(base + PR - 1)) / PR * PR, dend = min(L, nw - base);
+        const float* wh = wvP + h * wrow + PAD_WV;
+        Kahan4 k;
+        if (dend > d0s) corr_block(gT, wh, base, d0s, dend, k);
+#pragma unroll
+        for (int j = 0; j < PR; ++j) {
+            const int m = m0 + j;
+            if (m < M) {
+                const float direct = m >= m_lo ? omef * wh[m - m_lo] : 0.f;
+                rowW[(size_t)h * w.Mpad + m] = fmaf(epsf, k.value(j), direct);
+            }
+        }
     }
     for (int m = tid; m < M; m += MID_THREADS) {
         if (H == 1) rowW[(size_t)w.Mpad + m] = 0.f;
@@ -705,8 +794,11 @@ cudaError_t launch_mid(const Work& w, int n, int Mmax, int nwmax, int Lmax, int 
                         (size_t)(2 * Mmax + 4 * nwmax + Lmax) * tv + 64;
     if (!f32) return launch_mid_t<double, false>(w, n, smem, want_grad, want_mu, s);
     if (w.precision == BX_TF32X3) return launch_mid_t<float, true>(w, n, smem, want_grad, want_mu, s);
-    // k_mid32: mu pairs [2][nw], then FP32 lambda [2][M], pile-up part, weights [2][nw] each, g [L]
-    const size_t smem32 = (size_t)2 * nwmax * sizeof(float2) + (size_t)(2 * Mmax + 4 * nwmax + Lmax) * sizeof(float);
+    // k_mid32: mu pairs [2][nw], g, lambda rows, pile-up part [2][nw], weight rows (zero-padded),
+    // G_W and dG_W/deps per column
+    const size_t smem32 = (size_t)2 * nwmax * sizeof(float2) +
+                          (size_t)(mid32_gn(Lmax) + 2 * mid32_lrow(Mmax) + 2 * nwmax + 2 * mid32_wrow(nwmax)) * sizeof(float) +
+                          (size_t)w.Npad * (sizeof(float2) + sizeof(float));
     static size_t set32 = 0;
     if (smem32 > set32) {
         const cudaError_t e = cudaFuncSetAttribute(k_mid32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32);
