@@ -282,7 +282,7 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
         }
         void *s32, *stiles, *g32, *gg;
         if ((st = alloc_dev(m, &s32, (size_t)T.K * T.N * sizeof(float)))) break;
-        if ((st = alloc_dev(m, &stiles, (size_t)T.n_kb * 2 * US * KB * sizeof(float)))) break;
+        if ((st = alloc_dev(m, &stiles, (size_t)T.n_kb * 3 * US * KB * sizeof(float)))) break;
         if ((st = alloc_dev(m, &g32, (size_t)T.L * sizeof(float)))) break;
         if ((st = alloc_dev(m, &gg, (size_t)T.M * (sizeof(double) + sizeof(float))))) break;
         T.shapes32 = static_cast<float*>(s32);

@@ -24,7 +24,6 @@ namespace bx {
 constexpr int TM = 128;        // forward tile: output rows per unit (UMMA M)
 constexpr int KB = 32;         // forward k-block: true-energy columns per step
 constexpr int US = 16;         // UMMA N: species slots (K <= 16)
-constexpr int NACC = 4;        // rotating TMEM accumulators per forward unit
 constexpr int KMAX = 16;
 constexpr int PMAX = KMAX + 7;
 constexpr int BCOLS = 128;     // backward unit: true-energy columns (one per thread)
@@ -64,7 +63,7 @@ struct Toy {
     double dE, w, r_fid, r_iv, att_len;
     const double* shapes;     // [K][N]
     const float* shapes32;    // [K][N]
-    const float* S_tiles;     // [n_kb][2][US*KB]: TF32 hi | lo of the shapes, UMMA K-major
+    const float* S_tiles;     // [n_kb][3][US*KB]: shapes split in three (split3), UMMA K-major
     const double* stop_pow;   // [N]
     const float2* stop32;     // [N]: the same as FP32 pairs hi + lo (nullptr: split on the fly)
     const double* tag;        // [K] or nullptr
@@ -262,6 +261,27 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint
 }
 
 // Instruction descriptor of kind::tf32: D = F32, A = B = TF32, both K-major, M x N.
+// Three-part split x = hi + mid + lo of a row (or slice) of a k-block whose largest value is
+// mx: hi = rint(x / 2^e) 2^e with 2^e = 2^(exponent of mx - 7), so |hi / 2^e| <= 256; mid and
+// lo are the TF32 roundings of what remains (x - hi and x - hi - mid are exact in FP32).
+// All hi of the row share the grid 2^e: a product of two hi parts is an integer below 2^16
+// times 2^(e_A + e_B), and any sum of 32 of them is exact in FP32 whatever order or rounding
+// the accumulator uses.  Rows whose largest value is below 2^-100 put everything into mid, lo.
+struct Grid {
+    float inv, scale;
+};
+__device__ __forceinline__ Grid hi_grid(float mx) {
+    const int e = ((__float_as_int(mx) >> 23) & 0xFF) - 127 - 7;
+    if (!(mx > 7.8886091e-31f)) return Grid{0.f, 0.f};   // 2^-100
+    return Grid{__int_as_float((127 - e) << 23), __int_as_float((127 + e) << 23)};
+}
+__device__ __forceinline__ void split3(float x, Grid g, float& hi, float& mid, float& lo) {
+    hi = rintf(x * g.inv) * g.scale;
+    const float r = x - hi;
+    mid = tf32_rna(r);
+    lo = tf32_rna(r - mid);
+}
+
 __host__ __device__ constexpr uint32_t umma_idesc_tf32(int M, int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }

@@ -1,7 +1,8 @@
 // bx_prep.cu -- model set-up and the per-column stage of every evaluation.
 //
 // k_setup_toy (once per toy at model creation): FP32 copies of the shapes, the shapes
-//   split into TF32 hi/lo tiles in the tensor-core operand layout, FP32 pile-up spectrum,
+//   split in three (hi on a grid per species row and k-block, TF32 mid and lo) in the
+//   tensor-core operand layout, FP32 pile-up spectrum,
 //   and the pile-up window marginal Gg[m] = sum_{m' in W, 0 <= m'-m < L} g[m'-m] (FP64, then
 //   an FP32 copy after it).
 // k_prep (once per item): Eq. 1's Birks map and resolution on the true-energy grid in
@@ -21,16 +22,29 @@ namespace bx {
 __global__ void k_setup_toy(Toy t, float* shapes32, float* S_tiles, float* g32, double* Gg) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
     for (int j = tid; j < t.K * t.N; j += nt) shapes32[j] = (float)t.shapes[j];
-    // S tile of k-block kb: half h (0 = hi, 1 = lo), species row n, column c
-    const int per_kb = 2 * US * KB;
-    for (int j = tid; j < t.n_kb * per_kb; j += nt) {
-        const int kb = j / per_kb, r = j % per_kb, h = r / (US * KB), e = r % (US * KB);
-        const int n = e / KB, c = e % KB, i = kb * KB + c;
-        const float s = (n < t.K && i < t.N) ? (float)t.shapes[(size_t)n * t.N + i] : 0.f;
-        const float hi = tf32_rna(s);
-        const float val = h == 0 ? hi : tf32_rna(s - hi);
-        // K-major, no swizzle: 8x(4 x 4 B) core matrices; K step 256 B, 8-row step 128 B
-        S_tiles[(size_t)kb * per_kb + h * US * KB + (c / 4) * (US * 4) + n * 4 + (c % 4)] = val;
+    // species tile of k-block kb for the tensor-core forward: part p (hi | mid | lo), species
+    // row n split on its own grid over the k-block (split3), column c; K-major, no swizzle:
+    // 8 x (4 x 4 B) core matrices, K step US * 16 B, 8-row step 128 B
+    const int per_kb = 3 * US * KB;
+    for (int j = tid; j < t.n_kb * US; j += nt) {
+        const int kb = j / US, n = j % US;
+        float v[KB];
+        float mx = 0.f;
+        for (int c = 0; c < KB; ++c) {
+            const int i = kb * KB + c;
+            v[c] = (n < t.K && i < t.N) ? (float)t.shapes[(size_t)n * t.N + i] : 0.f;
+            mx = fmaxf(mx, fabsf(v[c]));
+        }
+        const Grid g = hi_grid(mx);
+        float* tile = S_tiles + (size_t)kb * per_kb;
+        for (int c = 0; c < KB; ++c) {
+            float hi, mid, lo;
+            split3(v[c], g, hi, mid, lo);
+            const int o = (c / 4) * (US * 4) + n * 4 + (c % 4);
+            tile[o] = hi;
+            tile[US * KB + o] = mid;
+            tile[2 * US * KB + o] = lo;
+        }
     }
     for (int d = tid; d < t.L; d += nt) g32[d] = (float)t.g[d];
     for (int m = tid; m < t.M; m += nt) {

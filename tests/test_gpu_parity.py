@@ -3,11 +3,14 @@
 Tolerances (derived from the arithmetic of each precision mode):
   * expected counts per bin: relative 1e-5 on bins with mu >= 1e-3 max(mu), absolute
     1e-8 max(mu) below (FP64 path: 1e-10 relative);
-  * -lnL: |Delta(-2 lnL)| <= 1e-3 (FP64 path: 1e-7).  The tensor-core mode BX_TF32X3 is held
-    to its documented error model instead: its FP32 accumulator truncates, a relative bias b
-    (|b| <= 2e-6) of every expected count, so |Delta(-2 lnL)| <= 1e-3 + 2 |b| |sum(mu - n)|;
+  * mean signed relative error over the bins with mu >= 1e-3 max(mu): <= 5e-8 in the
+    mixed-precision modes (no systematic error: the Baker-Cousins sum turns a bias b into
+    Delta(-2 lnL) ~ 2 b |sum(mu - n)|);
+  * -lnL: |Delta(-2 lnL)| <= 1e-3 (FP64 path: 1e-7);
   * gradient: |Delta g_j| |theta_j| <= tol (1 + |g_j theta_j|), the change of -lnL predicted
-    for a relative step of one in theta_j: tol = 1e-9 (FP64), 1e-3 (FP32), 3e-2 (TF32X3).
+    for a relative step of one in theta_j: tol = 1e-9 (FP64), 1e-3 (FP32, TF32X3).
+The tensor-core mode BX_TF32X3 is held to the same bounds as BX_FP32: its contraction makes
+the dominant hi * hi products exact in the FP32 accumulator (split3).
 """
 import dataclasses
 
@@ -21,16 +24,13 @@ from tests._util import dataset, per_bin_ok, points
 pytestmark = pytest.mark.gpu
 
 PRECS = [bx.BX_FP64, bx.BX_FP32, bx.BX_TF32X3]
-TOL = {bx.BX_FP64: dict(rel=1e-10, abs=1e-12, d2nll=1e-7, grad=1e-9, bias=0.0),
-       bx.BX_FP32: dict(rel=1e-5, abs=1e-8, d2nll=1e-3, grad=1e-3, bias=0.0),
-       bx.BX_TF32X3: dict(rel=1e-5, abs=1e-8, d2nll=1e-3, grad=3e-2, bias=2e-6)}
+TOL = {bx.BX_FP64: dict(rel=1e-10, abs=1e-12, d2nll=1e-7, grad=1e-9, bias=1e-12),
+       bx.BX_FP32: dict(rel=1e-5, abs=1e-8, d2nll=1e-3, grad=1e-3, bias=5e-8),
+       bx.BX_TF32X3: dict(rel=1e-5, abs=1e-8, d2nll=1e-3, grad=1e-3, bias=5e-8)}
 
 
 def d2nll_tol(prec, spec, theta):
-    t = TOL[prec]
-    if not t["bias"]:
-        return t["d2nll"]
-    return t["d2nll"] + 2 * t["bias"] * abs(float(np.sum(O.expected(spec, theta) - spec.counts_vector())))
+    return TOL[prec]["d2nll"]
 
 
 _models = {}
@@ -54,8 +54,11 @@ def test_expected_counts_per_bin(name, prec):
     s = dataset(name)
     m = model(name, prec)
     for th in [s.theta_true] + list(points(s, 2, seed=3)):
-        ok, wr, wa = per_bin_ok(m.expected(th), O.expected(s, th), rel=TOL[prec]["rel"], abs_frac=TOL[prec]["abs"])
+        mg, mo = m.expected(th), O.expected(s, th)
+        ok, wr, wa = per_bin_ok(mg, mo, rel=TOL[prec]["rel"], abs_frac=TOL[prec]["abs"])
         assert ok, (wr, wa)
+        big = mo >= 1e-3 * mo.max()
+        assert abs(float(np.mean((mg[big] - mo[big]) / mo[big]))) <= TOL[prec]["bias"]
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -68,6 +71,26 @@ def test_nll_and_gradient(name, prec):
         fo, go = O.nll(s, th, grad=True)
         assert 2 * abs(f - fo) <= d2nll_tol(prec, s, th), (f, fo)
         ok, worst = grad_ok(g[: s.P], go, th, TOL[prec]["grad"])
+        assert ok, worst
+
+
+@pytest.mark.parametrize("prec", [bx.BX_FP32, bx.BX_TF32X3])
+def test_nll_far_from_the_optimum(prec):
+    """Points 6% (rms) away from theta_true, where hundreds of bins have |n - mu| between mu/4
+    and mu (the wider range of the FP32 Baker-Cousins series) and -lnL is ~1e5:
+    |Delta(-2 lnL)| within 1e-3 plus 2e-8 of -lnL (FP32 relative rounding of larger terms)."""
+    s = dataset("multivariate")
+    m = model("multivariate", prec)
+    n = s.counts_vector()
+    th = I.parameter_points(s.theta_true, 3, rel=0.06, seed=41, free=s.default_free())
+    for t in th:
+        mo = O.expected(s, t)
+        x = (n - mo) / mo
+        assert np.count_nonzero((np.abs(x) > 0.25) & (x >= -0.5) & (x <= 1.0)) > 300
+        f, g = m.nll_grad(t)
+        fo, go = O.nll(s, t, grad=True)
+        assert 2 * abs(f - fo) <= 1e-3 + 2e-8 * abs(fo), (f, fo)
+        ok, worst = grad_ok(g[: s.P], go, t, TOL[prec]["grad"])
         assert ok, worst
 
 
