@@ -239,16 +239,16 @@ def run_ours(args):
         raise bx.BxError(st, bx.lib().bx_last_error().decode())
     value, total_ms = job_throughput(sum(a.elapsed_time(b) for a, b in evs), B, args.steps, ws, dev)
 
-    e2e, fp64_value, fits, disc = None, None, None, None
+    e2e, fp64_value, tc_value, fits, disc = None, None, None, None, None
     if not args.no_extras:
-        e2e, fp64_value = extras(bx, model, spec, pts, theta, stream, B, P, ws, args)
+        e2e, fp64_value, tc_value = extras(bx, model, spec, pts, theta, stream, B, P, ws, args)
         fits = fit_times(bx, I, spec, stream)
         if args.toys > 0:
             fits["batched_toys"] = toy_fits(bx, I, args.toys, stream)
         disc = discrimination_leg(bx, I, stream, B=args.batch2d) if args.batch2d > 0 else None
     if rank != 0:
         return
-    report(args, ws, B, total_ms, value, stage_ms, n_evals, entries, e2e, fp64_value, clk, fits, disc)
+    report(args, ws, B, total_ms, value, stage_ms, n_evals, entries, e2e, fp64_value, tc_value, clk, fits, disc)
 
 
 def extras(bx, model, spec, pts, theta, stream, B, P, ws, args):
@@ -283,7 +283,19 @@ def extras(bx, model, spec, pts, theta, stream, B, P, ws, args):
     torch.cuda.synchronize()
     fp64_value = ws * B64 * 3 / (e0.elapsed_time(e1) / 1e3)
     m64.close()
-    return e2e, fp64_value
+
+    # the tensor-core species-resolved form (BX_TF32X3) of the same evaluation
+    mtc = bx.Model(spec, precision=bx.BX_TF32X3, max_batch=B, stream=stream)
+    mtc.nll_batch(theta, grad=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(5):
+        mtc.nll_batch(theta, grad=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    tc_value = ws * B * 5 / (e0.elapsed_time(e1) / 1e3)
+    mtc.close()
+    return e2e, fp64_value, tc_value
 
 
 def toy_fits(bx, I, n_toys, stream):
@@ -406,7 +418,8 @@ def fit_times(bx, I, spec, stream):
     return out
 
 
-def report(args, ws, B, total_ms, value, stage_ms, n_evals, entries, e2e, fp64_value, clk, fits=None, disc=None):
+def report(args, ws, B, total_ms, value, stage_ms, n_evals, entries, e2e, fp64_value, tc_value, clk, fits=None,
+           disc=None):
     # roofline of the dominant kernel (ALU-bound: FP32 issue rate of 152 SMs x 128 lanes)
     per_launch = {k: v / max(n_evals, 1) for k, v in stage_ms.items()}
     dom = max(("forward", "adjoint"), key=lambda k: per_launch[k])
@@ -427,6 +440,7 @@ def report(args, ws, B, total_ms, value, stage_ms, n_evals, entries, e2e, fp64_v
             "config": {"workload": WORKLOAD, "global_batch": ws * B, "precision": "BX_FP32 (FP64 columns, -lnL)",
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}"},
             "fp64_gpu_value": fp64_value, "mixed_over_fp64": value / fp64_value if fp64_value else None,
+            "tf32x3_gpu_value": tc_value,
             "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "fit": fits, "discrimination_2d": disc,
             "gpu_launches": 5 * args.steps, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)

@@ -12,9 +12,9 @@
 //          sum_k A_k p_k[rho] (closed-form shell integrals) and pulse-shape bins
 //          sum_k A_k q_k[j];
 //   -lnL   sum of mu - n + n log1p((n - mu)/mu): the terms in FP64, or for the
-//          mixed-precision modes in a cancellation-free FP32 form where mu/2 <= n <= 2 mu;
-//          the sum in FP64 with Neumaier compensation inside each thread and TwoSum-style
-//          merging across the block.
+//          mixed-precision modes in a cancellation-free FP32 form where mu/2 <= n <= 2 mu
+//          and in double-float elsewhere; the sum in FP64 with Neumaier compensation inside
+//          each thread (k_mid32: compensated FP32) and TwoSum-style merging across the block.
 // With want_grad it also writes the adjoint inputs of the response stage: per row the
 // pile-up-correlated residual weights wt_h[m] and G_W[m], per species the coefficients
 // that turn them into dNLL/dR[m,i], and the gradient of eps, s_r and the parts of the
@@ -67,6 +67,16 @@ struct Dot64 {
 };
 template <typename TV> struct DotT { using type = Dot64; };
 template <> struct DotT<float> { using type = Dot32; };
+
+// bc_term_far on FP64 arguments (the TF32X3 assembly)
+__device__ __forceinline__ bool bc_term_far_d(double n, double mu, double& term, double& wb) {
+    df t;
+    float wf;
+    if (!bc_term_far(df_from(n), df_from(mu), t, wf)) return false;
+    term = df_to_double(t);
+    wb = (double)wf;
+    return true;
+}
 
 // Radial bin probabilities of the Eq. 4 marginal: internal events uniform in volume,
 // external ones exponential in depth from r_iv (attenuation length att_len s_r), with the
@@ -270,6 +280,7 @@ __global__ void __launch_bounds__(MID_THREADS, (sizeof(TV) == sizeof(float) && !
         if (n == 0.0) term = mu;
         else if (!(mu > 0.0 && isfinite(mu))) { dom = 1; term = 0.0; }
         else if (sizeof(TV) == sizeof(float) && bc_term32(n, mu, term, wb)) {}
+        else if (sizeof(TV) == sizeof(float) && bc_term_far_d(n, mu, term, wb)) {}
         else {
             term = (mu - n) + n * log1p((n - mu) / mu);
             wb = 1.0 - n / mu;
@@ -487,8 +498,8 @@ __host__ __device__ constexpr int mid32_wrow(int nw) { return PAD_WV + nw + 16; 
 __host__ __device__ constexpr int mid32_gn(int L) { return ((L + PR - 1) / PR) * PR + PR; }
 
 // Baker-Cousins term from double-float n and mu, in FP32 for x = (n - mu)/mu in
-// [BC_XLO, BC_XHI] (as bc_term32), else in FP64; the term goes into a compensated FP32 sum,
-// wb = 1 - n/mu.
+// [BC_XLO, BC_XHI] (as bc_term32), else in double-float (bc_term_far); the term goes into a
+// compensated FP32 sum, wb = 1 - n/mu.
 __device__ __forceinline__ void bc_term_df(df n, df mu, Sum32& acc, float& wb) {
     const float d = df_add(n, df_neg(mu)).h;
     const float x = d / mu.h;
@@ -497,11 +508,14 @@ __device__ __forceinline__ void bc_term_df(df n, df mu, Sum32& acc, float& wb) {
         wb = -x;
         return;
     }
-    const double nd = df_to_double(n), md = df_to_double(mu);
-    const df t = df_from((md - nd) + nd * log1p((nd - md) / md));
+    df t;
+    if (!bc_term_far(n, mu, t, wb)) {   // n/mu beyond [1e-30, 1e30]: FP64
+        const double nd = df_to_double(n), md = df_to_double(mu);
+        t = df_from((md - nd) + nd * log1p((nd - md) / md));
+        wb = (float)(1.0 - nd / md);
+    }
     acc.add(t.h);
     acc.c = __fadd_rn(acc.c, t.l);
-    wb = (float)(1.0 - nd / md);
 }
 
 // The assembly of the rate-first mixed-precision mode (BX_FP32): the quantities of k_mid with
@@ -509,8 +523,7 @@ __device__ __forceinline__ void bc_term_df(df n, df mu, Sum32& acc, float& wb) {
 // relative) instead of FP64, GB300's FP64 rate being 1/64 of its FP32 rate.  The forward
 // hands over lambda_h as FP32 pairs, the column stage the window masses aW; -lnL is a
 // compensated FP32 sum (TwoSum per term, merged across the block in FP64).  FP64 remains for
-// the radial and pulse-shape marginals (one value per bin, ~100 bins) and for the
-// Baker-Cousins terms outside mu/2 <= n <= 2 mu.
+// the radial and pulse-shape marginals (one value per bin, ~100 bins).
 __global__ void __launch_bounds__(MID_THREADS, 2) k_mid32(Work w, int want_grad, int want_mu) {
     extern __shared__ __align__(16) double dsm[];
     const int item = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
