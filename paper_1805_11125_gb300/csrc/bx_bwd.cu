@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(BCOLS) k_bwd_f64(Work w) {
     block_sum_gp(g, red, gp);
 }
 
-__global__ void __launch_bounds__(BCOLS) k_bwd_f32(Work w) {
+__global__ void __launch_bounds__(BCOLS, 7) k_bwd_f32(Work w) {
     // 1D item-major grid (a y dimension would cap the batch at 65535 items)
     const int cb = blockIdx.x % w.max_cb, item = blockIdx.x / w.max_cb, tid = threadIdx.x;
     const Toy& T = w.toys[w.toy_of[item]];
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(BCOLS) k_bwd_f32(Work w) {
     double S0 = 0.0, S1 = 0.0, S2 = 0.0, Rs = 0.0, Rt = 0.0;
     for (int c0 = wr0; c0 < wr1; c0 += RCH) {
         const int c1 = min(wr1, c0 + RCH);
-        float p0 = 0.f, p1 = 0.f, p2 = 0.f, ps = 0.f, pt = 0.f;
+        AdjSums bs;
         for (int s0 = c0; s0 < c1; s0 += 64) {
             const int ns = min(64, c1 - s0);
             for (int j = lane; j < ns; j += 32) {
@@ -219,11 +219,13 @@ __global__ void __launch_bounds__(BCOLS) k_bwd_f32(Work w) {
                         wt = sW[wq][1][j + k];
                         W = fmaf(ws, Ssub, fmaf(wt, Stag, sW[wq][2][j + k] * SA));
                     };
-                    adj_run((float)(s0 + j), min(ADJ_RUN, ns - j), cf, cg, ac, wts, p0, p1, p2, ps, pt);
+                    adj_run((float)(s0 + j), min(ADJ_RUN, ns - j), cf, cg, ac, wts, bs);
                 }
             }
             __syncwarp();
         }
+        float p0, p1, p2, ps, pt;
+        bs.node(cg.Ck2, ac.kk, p0, p1, p2, ps, pt);
         S0 += p0;
         S1 += p1;
         S2 += p2;

@@ -5,10 +5,10 @@
 //   tensor-core operand layout, FP32 pile-up spectrum,
 //   and the pile-up window marginal Gg[m] = sum_{m' in W, 0 <= m'-m < L} g[m'-m] (FP64, then
 //   an FP32 copy after it).
-// k_prep (once per item): Eq. 1's Birks map and resolution on the true-energy grid in
-//   FP64 (block-wide prefix sum), the column normalisation 1/Phi(mu/sigma), the FP32
-//   parameters of the generated response, the rate-weighted spectra of Eq. 3 and the band
-//   limits of every tile.
+// k_prep (FP64 model) and k_prep32 (mixed-precision modes), once per item: Eq. 1's Birks map
+//   and resolution on the true-energy grid (block-wide prefix sum), the column normalisation
+//   1/Phi(mu/sigma), the window masses, the rate-weighted spectra of Eq. 3 and the band limits
+//   of every tile; k_prep32 also the FP32 parameters of the generated response.
 #include <float.h>
 #include <limits.h>
 #include <math.h>
@@ -109,16 +109,11 @@ __device__ void block_scan2(double& a, double& b, double& ta, double& tb, double
 // (coalesced loads and stores; neighbouring lanes take the same branches), the Birks prefix
 // sum carried from chunk to chunk.  Tile and column-block bounds are reduced over the warp
 // (redux) before one shared atomic per warp and tile.
-// FP64 work is what this stage costs (GB300 issues FP64 at 1/64 of its FP32 rate), so each
-// quantity is computed in the precision its consumer needs:
-//   FP64: the Birks prefix sums, mu, sigma, 1/Phi(mu/sigma) and phi/Phi (only where
-//         mu/sigma < 9: elsewhere 1 and < 1e-18), the window mass (erfc only for window
-//         edges within 9 sigma), the double-float split of the generator's parameters;
-//   FP32: the response band (a work bound, not a result); in the mixed-precision modes
-//         (F32 = true) also the rate-weighted spectra S_h[i] = sum_k r_k c_{h,k} s_k[i] with
-//         the rates as double-float pairs and the outer-node factor 2 * 2^(-kk^2) by the
-//         generator's own exp2; nothing for the FP64 path's generator (it works from mu, sigma).
-template <bool F32>
+// The FP64 model's column stage: every quantity in FP64 -- the Birks prefix sums, mu, sigma,
+// 1/Phi(mu/sigma) and phi/Phi (only where mu/sigma < 9: elsewhere 1 and < 1e-18), the window
+// mass (erfc only for window edges within 9 sigma), the rate-weighted spectra
+// S_h[i] = sum_k r_k c_{h,k} s_k[i]; FP32 only for the response band (a work bound, not a
+// result).  The FP64 generator works from mu and sigma.
 __global__ void __launch_bounds__(256) k_prep(Work w) {
     const int item = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
     if (w.skip && w.skip[item]) {   // uniform for the block: no barrier is skipped unevenly
@@ -131,38 +126,21 @@ __global__ void __launch_bounds__(256) k_prep(Work w) {
     __shared__ double sh[32];
     __shared__ int s_bad;
     __shared__ int s_tlo[MAX_TILES], s_thi[MAX_TILES], s_rlo[MAX_CB], s_rhi[MAX_CB];
-    __shared__ float s_rate[4][KMAX];   // (vetoed hi, lo, tagged hi, lo)
     if (tid == 0) s_bad = 0;
     for (int j = tid; j < MAX_TILES; j += blockDim.x) { s_tlo[j] = INT_MAX; s_thi[j] = INT_MIN; }
     for (int j = tid; j < MAX_CB; j += blockDim.x) { s_rlo[j] = INT_MAX; s_rhi[j] = INT_MIN; }
-    if (F32 && tid < KMAX) {
-        double rs = 0.0, rt = 0.0;
-        if (tid < K) {
-            const double t = T.tag ? T.tag[tid] : 0.0;
-            rs = th[tid] * (T.tag ? 1.0 - t : 1.0);
-            rt = th[tid] * t;
-        }
-        const float rsh = (float)rs, rth = (float)rt;
-        s_rate[0][tid] = rsh;
-        s_rate[1][tid] = (float)(rs - (double)rsh);
-        s_rate[2][tid] = rth;
-        s_rate[3][tid] = (float)(rt - (double)rth);
-    }
     __syncthreads();
     if (tid < T.P && !isfinite(th[tid])) s_bad = 1;
     const double LY = th[K], a = th[K + 1], b = th[K + 2], c = th[K + 3], kB = th[K + 4];
     if (tid == 0 && (!(LY > 0.0) || ((T.n_rad > 0 || T.n_r2 > 0) && !(th[K + 6] > 0.0)))) s_bad = 1;
 
-    const double w_ = T.w, inv_w = 1.0 / w_;
+    const double w_ = T.w;
     const double z_lo = T.m_lo * w_, z_hi = M * w_;
-    const float wf = (float)w_, inv_wf = (float)inv_w, bandf = (float)w.band;
+    const float wf = (float)w_, inv_wf = (float)(1.0 / w_), bandf = (float)w.band;
     const float e_min = -2.0f * wf, e_max = (M + 2.0f) * wf;
     Col64* col = w.col64 + (size_t)item * w.Npad;
     double2* cq = w.colq + (size_t)item * w.Npad;
-    float4* cf = w.colf + (size_t)item * w.Npad;
-    ColG* cg = w.colg + (size_t)item * w.Npad;
     double2* cs = w.colS + (size_t)item * w.Npad;
-    float2* cs32 = w.colS32 + (size_t)item * w.Npad;
     double* aW = w.aW + (size_t)item * w.Npad;
     int2* cr = w.colr + (size_t)item * w.Npad;
     int bad = 0;
@@ -201,38 +179,15 @@ __global__ void __launch_bounds__(256) k_prep(Work w) {
                 mills = INV_SQRT_2PI * exp(-0.5 * z * z) * norm;
             }
             col[i] = Col64{mu, sig, norm, mills};
-            if (F32) {
-                const double u = mu * inv_w;
-                const double jf = floor(u);
-                const double hs = w_ * isig * S_EX2, cc = (0.5 - (u - jf)) * hs;
-                const float hs_hi = (float)hs, c_hi = (float)cc;
-                cf[i] = make_float4((float)jf, c_hi, hs_hi, (float)(hs - (double)hs_hi));
-                const double kk = 0.38729833462074170 * hs, kq = kk * kk;
-                const float kq_hi = (float)kq;
-                cg[i] = ColG{(float)(2.0 * 0.69314718055994531 * kk), 2.0f * exp2_neg(-kq_hi, (float)(kq_hi - kq)),
-                             (float)(cc - (double)c_hi),
-                             (float)((0.5 * INV_SQRT_2PI * GL_W_SCALE) * w_ * isig * norm)};
+            // rate-weighted spectra of the vetoed (or single) and tagged events (Eq. 3)
+            double ssub = 0.0, stag = 0.0;
+            for (int k = 0; k < K; ++k) {
+                const double sk = T.shapes[(size_t)k * N + i] * th[k];
+                const double t = T.tag ? T.tag[k] : 0.0;
+                ssub += (T.tag ? 1.0 - t : 1.0) * sk;
+                stag += t * sk;
             }
-            if (F32 && T.shapes32) {
-                // rate-weighted spectra of the vetoed (or single) and tagged events (Eq. 3)
-                float ss = 0.f, st = 0.f;
-                for (int k = 0; k < K; ++k) {
-                    const float sk = T.shapes32[(size_t)k * N + i];
-                    ss = fmaf(s_rate[0][k], sk, fmaf(s_rate[1][k], sk, ss));
-                    st = fmaf(s_rate[2][k], sk, fmaf(s_rate[3][k], sk, st));
-                }
-                cs32[i] = make_float2(ss, st);
-            } else {   // FP64 model, or a descriptor without FP32 shapes
-                double ssub = 0.0, stag = 0.0;
-                for (int k = 0; k < K; ++k) {
-                    const double sk = T.shapes[(size_t)k * N + i] * th[k];
-                    const double t = T.tag ? T.tag[k] : 0.0;
-                    ssub += (T.tag ? 1.0 - t : 1.0) * sk;
-                    stag += t * sk;
-                }
-                if (F32) cs32[i] = make_float2((float)ssub, (float)stag);
-                else cs[i] = make_double2(ssub, stag);
-            }
+            cs[i] = make_double2(ssub, stag);
             // window mass of the column (Eq. 4 marginals)
             aW[i] = gauss_mass((z_lo - mu) * isig, (z_hi - mu) * isig) * norm;
             // response band: rows whose bin lies within band * sigma of mu
@@ -271,12 +226,7 @@ __global__ void __launch_bounds__(256) k_prep(Work w) {
     for (int i = N + tid; i < w.Npad; i += blockDim.x) {
         col[i] = Col64{0.0, 1.0, 0.0, 0.0};
         cq[i] = make_double2(0.0, 0.0);
-        if (F32) {
-            cf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-            cg[i] = ColG{0.f, 0.f, 0.f, 0.f};
-        }
-        if (F32) cs32[i] = make_float2(0.f, 0.f);
-        else cs[i] = make_double2(0.0, 0.0);
+        cs[i] = make_double2(0.0, 0.0);
         aW[i] = 0.0;
         cr[i] = make_int2(0, 0);
     }
@@ -350,8 +300,9 @@ __device__ void block_scan_df(df& a, df& b, df& ta, df& tb, float* sh) {
 // The per-column stage of the mixed-precision modes in double-float FP32 (bx_df.cuh, ~2^-44
 // relative): the Birks prefix sums, 1/(1 + kB S), mu, sigma^2, 1/sigma by one Newton step, the
 // generator's split constants.  FP64 only where a column's Gaussian reaches 0 npe or a window
-// edge within 9 sigma (1/Phi, phi/Phi, erfc of the window mass) and for the FP64 copies of
-// mu, sigma, Q, dQ/dkB that the adjoint's chain rule reads.  Same outputs as k_prep<true>.
+// edge within Z_F32 = 3 sigma (1/Phi, phi/Phi, erfc of the window mass; FP32 tails beyond),
+// and for the FP64 copies of mu, sigma, Q, dQ/dkB that the adjoint's chain rule reads (formed
+// on the integer pipe, f2d).  The window masses go out as FP32 pairs.
 __global__ void __launch_bounds__(256) k_prep32(Work w) {
     const int item = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
     if (w.skip && w.skip[item]) {
@@ -552,7 +503,7 @@ __global__ void __launch_bounds__(256) k_prep32(Work w) {
 }
 
 cudaError_t launch_prep(const Work& w, int n, cudaStream_t s) {
-    if (w.precision == BX_FP64) k_prep<false><<<n, 256, 0, s>>>(w);
+    if (w.precision == BX_FP64) k_prep<<<n, 256, 0, s>>>(w);
     else k_prep32<<<n, 256, 0, s>>>(w);
     return cudaGetLastError();
 }

@@ -147,7 +147,7 @@ __device__ __forceinline__ void resp_adjoint32(float mf, const float4& cf, const
 constexpr int ADJ_RUN = 8;
 
 struct AdjCol {
-    float hs, hs2, C, A, B, kk;   // hs, hs^2, 2^(-2 hs^2), cosh and sinh of kap hs, kap / (2 ln 2)
+    float hs, hs2, C, A, B, kk, iCk2;   // hs, hs^2, 2^(-2 hs^2), cosh and sinh of kap hs, kap / (2 ln 2), 1 / Ck2
 };
 
 __device__ __forceinline__ AdjCol adj_col(const float4& cf, const ColG& cg) {
@@ -159,37 +159,68 @@ __device__ __forceinline__ AdjCol adj_col(const float4& cf, const ColG& cg) {
     a.A = cosh_small(d2);
     a.B = sinh_small(d, d2);
     a.kk = cg.kap * INV_2LN2;
+    a.iCk2 = cg.Ck2 > 0.f ? 1.0f / cg.Ck2 : 0.f;
     return a;
 }
 
-// Adds W[j] (P0, P1, P2) and the row weights' P0 sums of rows mf .. mf + n - 1 (n <= ADJ_RUN)
-// into the accumulators; W[j] = ws[j] Ssub + wt[j] Stag + wg[j] SA.
+// Weighted node sums of one column accumulated in a basis that needs no per-row assembly of
+// the node sums: with u = p0 cosh z and v = p0 sinh z (p-+ = p0 Ck2 (cosh z -+ sinh z) / 2),
+//   P0 = 5 Ck2 u + 8 p0,  P1 = 5 Ck2 (t u - kk v) + 8 t p0,
+//   P2 = 5 Ck2 ((kk^2 + t^2) u - 2 kk t v) + 8 t^2 p0,
+// so sum_m W P_j follows from the sums of W u, W v, W p0 and their first and second moments in
+// t (AdjSums::node), and sum_m w P0 from the sums of w u and w p0.
+struct AdjSums {
+    float A0 = 0.f, A1 = 0.f, A2 = 0.f, B0 = 0.f, B1 = 0.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+    float Es = 0.f, Fs = 0.f, Et = 0.f, Ft = 0.f;
+    __device__ __forceinline__ void add(float t, float p, float u, float v, float ws, float wt, float W) {
+        const float a = W * u, b = W * v, c = W * p;
+        A0 += a;
+        const float ta = t * a;
+        A1 += ta;
+        A2 = fmaf(t, ta, A2);
+        B0 += b;
+        B1 = fmaf(t, b, B1);
+        C0 += c;
+        const float tc = t * c;
+        C1 += tc;
+        C2 = fmaf(t, tc, C2);
+        const float sp = ws * p, tp = wt * p;
+        Fs += sp;
+        Es = fmaf(ws, u, Es);
+        Ft += tp;
+        Et = fmaf(wt, u, Et);
+    }
+    // (sum W P0, sum W P1, sum W P2, sum ws P0, sum wt P0) of the rows added so far
+    __device__ __forceinline__ void node(float Ck2, float kk, float& p0, float& p1, float& p2, float& ps, float& pt) const {
+        const float o = GL_W_OUT * Ck2;
+        p0 = fmaf(o, A0, GL_W_MID * C0);
+        p1 = fmaf(o, fmaf(-kk, B0, A1), GL_W_MID * C1);
+        p2 = fmaf(o, fmaf(kk * kk, A0, fmaf(-2.0f * kk, B1, A2)), GL_W_MID * C2);
+        ps = fmaf(o, Es, GL_W_MID * Fs);
+        pt = fmaf(o, Et, GL_W_MID * Ft);
+    }
+};
+
+// Adds rows mf .. mf + n - 1 (n <= ADJ_RUN) of one column into the basis sums;
+// wts(k, ws, wt, W) gives row k's weights, W = ws Ssub + wt Stag + wg SA.
 template <typename WF>
 __device__ __forceinline__ void adj_run(float mf, int n, const float4& cf, const ColG& cg, const AdjCol& ac, WF&& wts,
-                                        float& p0s, float& p1s, float& p2s, float& pss, float& pts) {
+                                        AdjSums& s) {
     float th, tl;
     centre_df(mf, cf, cg.c_lo, th, tl);
     const float z0 = cg.kap * th, z1 = cg.kap * fmaf((float)(ADJ_RUN - 1), ac.hs, th);
     if (fabsf(z0) <= 1.0f && fabsf(z1) <= 1.0f) {
         float p = centre_node(th, tl);
         float rho = exp2_neg(-fmaf(2.0f * th, ac.hs, ac.hs2));
-        const float s = z0 * z0;
-        float ch = cosh_small(s), sh = sinh_small(z0, s);
+        const float q = z0 * z0;
+        float ch = cosh_small(q), sh = sinh_small(z0, q);
         float t = th;
 #pragma unroll
         for (int k = 0; k < ADJ_RUN; ++k) {
             if (k < n) {
                 float ws, wt, W;
                 wts(k, ws, wt, W);
-                const float f = p * cg.Ck2, Sp = f * ch, Sm = f * sh, q0 = t * t;
-                const float P0 = fmaf(GL_W_OUT, Sp, GL_W_MID * p);
-                const float P1 = fmaf(GL_W_OUT, fmaf(t, Sp, -ac.kk * Sm), GL_W_MID * (t * p));
-                const float P2 = fmaf(GL_W_OUT, fmaf(fmaf(ac.kk, ac.kk, q0), Sp, -2.0f * t * ac.kk * Sm), GL_W_MID * (q0 * p));
-                p0s = fmaf(W, P0, p0s);
-                p1s = fmaf(W, P1, p1s);
-                p2s = fmaf(W, P2, p2s);
-                pss = fmaf(ws, P0, pss);
-                pts = fmaf(wt, P0, pts);
+                s.add(t, p, p * ch, p * sh, ws, wt, W);
                 p *= rho;
                 rho *= ac.C;
                 t += ac.hs;
@@ -204,13 +235,22 @@ __device__ __forceinline__ void adj_run(float mf, int n, const float4& cf, const
             if (k < n) {
                 float ws, wt, W;
                 wts(k, ws, wt, W);
-                float P0, P1, P2;
-                resp_adjoint32(mf + (float)k, cf, cg, P0, P1, P2);
-                p0s = fmaf(W, P0, p0s);
-                p1s = fmaf(W, P1, p1s);
-                p2s = fmaf(W, P2, p2s);
-                pss = fmaf(ws, P0, pss);
-                pts = fmaf(wt, P0, pts);
+                float t0, t1;
+                centre_df(mf + (float)k, cf, cg.c_lo, t0, t1);
+                const float p0 = centre_node(t0, t1);
+                const float z = cg.kap * t0;
+                float u, v;
+                if (fabsf(z) <= 1.0f) {
+                    const float q = z * z;
+                    u = p0 * cosh_small(q);
+                    v = p0 * sinh_small(z, q);
+                } else {   // outer nodes directly: u = (p- + p+) / Ck2, v = (p- - p+) / Ck2
+                    float Sp, Sm;
+                    outer_direct(t0, ac.kk, Sp, Sm);
+                    u = Sp * ac.iCk2;
+                    v = Sm * ac.iCk2;
+                }
+                s.add(t0, p0, u, v, ws, wt, W);
             }
         }
     }
