@@ -33,11 +33,11 @@ METRIC = "-lnL+grad evals/s & full-fit wall time, mixed vs FP64 GPU at |Δ(-2lnL
 WORKLOAD = ("multivariate spectral fit: K=15 species on a 2000-point 0-3 MeV grid, TFC-vetoed + TFC-tagged "
             "900x1 npe (100-1000 npe), radial 60, pulse-shape 50, 22 parameters, 2e6 events, pile-up L=400")
 # FP32 operations per in-band response entry of the forward kernel, counted from the source
-# (bx_resp.cuh resp_exact32 45, two Kahan row sums 8, column sum 2)
-FWD_OPS_PER_ENTRY = 55
-# adjoint kernel per entry of a run of 8 rows (bx_resp.cuh adj_run): recurrence 7, outer nodes 4,
-# node sums 13, weight 3, five column sums 5, plus the exact start of the run (58) / 8
-BWD_OPS_PER_ENTRY = 39
+# (bx_resp.cuh resp_shape32 44, two Kahan row sums 8, column sum 2)
+FWD_OPS_PER_ENTRY = 54
+# adjoint kernel per entry of a run of 8 rows (bx_resp.cuh adj_run): recurrence 7, outer-node
+# products 2, basis sums 19 (AdjSums::add), weight 3, plus the exact start of the run (58) / 8
+BWD_OPS_PER_ENTRY = 38
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # DRAM bytes (read + write) per evaluation item of the two candidate dominant kernels, from one
 # ncu capture at 512 items (profiles/multivariate_fp32_b512_launches_and_kernels.md); the

@@ -1,7 +1,9 @@
 // bx_fwd_f32.cu -- Eq. 1 forward in FP32 on the CUDA cores (the mixed-precision path).
 //
 // Rate-first form: the Eq. 3 spectra are contracted directly,
-//     lambda_h[m] = sum_i R[m,i] S_h[i],   S_h[i] = sum_k r_k c_{h,k} s_k[i]   (k_prep),
+//     lambda_h[m] = sum_i (R[m,i] / A_i) (A_i S_h[i]),   S_h[i] = sum_k r_k c_{h,k} s_k[i],
+// with the column amplitude A_i folded into the spectra by k_prep32 (one rounding of the
+// double-float product instead of two, and one multiply less per entry),
 // and, for models with Eq. 4 terms, the response is also reduced over rows,
 //     a_t[i] = sum_{m in tile t} R[m,i] Gg[m],
 // from which k_mid forms every species' window marginal after pile-up.
@@ -89,8 +91,8 @@ __global__ void __launch_bounds__(F32_THREADS) k_fwd_f32(Work w) {
             const float2 S = sS[q][c];
             float Ra = 0.f, Rb = 0.f;
             if (inA && inB) {   // the common case: two independent chains for the scheduler
-                Ra = resp_exact32(mfa, cf, cg);
-                Rb = resp_exact32(mfb, cf, cg);
+                Ra = resp_shape32(mfa, cf, cg);
+                Rb = resp_shape32(mfb, cf, cg);
                 kahan_fma(sa, csa, Ra, S.x);
                 kahan_fma(sb, csb, Rb, S.x);
                 if (TAG) {
@@ -98,11 +100,11 @@ __global__ void __launch_bounds__(F32_THREADS) k_fwd_f32(Work w) {
                     kahan_fma(tb, ctb, Rb, S.y);
                 }
             } else if (inA) {
-                Ra = resp_exact32(mfa, cf, cg);
+                Ra = resp_shape32(mfa, cf, cg);
                 kahan_fma(sa, csa, Ra, S.x);
                 if (TAG) kahan_fma(ta, cta, Ra, S.y);
             } else {
-                Rb = resp_exact32(mfb, cf, cg);
+                Rb = resp_shape32(mfb, cf, cg);
                 kahan_fma(sb, csb, Rb, S.x);
                 if (TAG) kahan_fma(tb, ctb, Rb, S.y);
             }
@@ -115,7 +117,7 @@ __global__ void __launch_bounds__(F32_THREADS) k_fwd_f32(Work w) {
         if (COLS) {
             float s = 0.f;
             for (int j = 0; j < 64; ++j) s += cb[j][lane];
-            if (lane < ncol) apart[c0 + lane] = s;
+            if (lane < ncol) apart[c0 + lane] = s * sG[q][lane].A;
             __syncwarp();
         }
     }

@@ -103,7 +103,7 @@ struct Work {
     float4* colf;             // [cap][Npad]: (floor(mu/w), c_hi, hs_hi, hs_lo): hs = w/sig*S_EX2, c = (1/2 - frac(mu/w)) hs
     ColG* colg;               // [cap][Npad]
     double2* colS;            // [cap][Npad]: S_vetoed[i], S_tagged[i] (FP64 model)
-    float2* colS32;           // [cap][Npad]: the same for the mixed-precision modes
+    float2* colS32;           // [cap][Npad]: A_i S_h[i] (vetoed, tagged) in FP32 for the rate-first FP32 forward
     double* aW;               // [cap][Npad]: window mass sum_{m in W} R[m,i] (closed form) times 1/Phi;
                               // as FP32 pairs (hi, lo) in the same bytes in the mixed-precision modes
     int2* colr;               // [cap][Npad]: band rows [r0, r1) of each column (empty: r0 >= r1)

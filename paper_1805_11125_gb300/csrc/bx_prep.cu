@@ -422,7 +422,8 @@ __global__ void __launch_bounds__(256) k_prep32(Work w) {
             const df kk = df_mul(gln, hs), kq = df_mul(kk, kk);
             const df Ad = df_mul(df_mul(cAw, isig), normd);
             cg[i] = ColG{df_mul(ln4, kk).h, 2.0f * exp2_neg(-kq.h, -kq.l), cc.l, Ad.h};
-            // rate-weighted spectra of the vetoed (or single) and tagged events (Eq. 3)
+            // rate-weighted spectra of the vetoed (or single) and tagged events (Eq. 3), times the
+            // column amplitude A (the FP32 forward generates R / A)
             if (T.shapes32) {
                 float ss = 0.f, st = 0.f;
                 for (int k = 0; k < K; ++k) {
@@ -430,7 +431,7 @@ __global__ void __launch_bounds__(256) k_prep32(Work w) {
                     ss = fmaf(s_rate[0][k], sk, fmaf(s_rate[1][k], sk, ss));
                     st = fmaf(s_rate[2][k], sk, fmaf(s_rate[3][k], sk, st));
                 }
-                cs32[i] = make_float2(ss, st);
+                cs32[i] = make_float2(df_mulf(Ad, ss).h, df_mulf(Ad, st).h);
             } else {   // a descriptor without FP32 shapes
                 double ssub = 0.0, stag = 0.0;
                 for (int k = 0; k < K; ++k) {
@@ -439,7 +440,7 @@ __global__ void __launch_bounds__(256) k_prep32(Work w) {
                     ssub += (T.tag ? 1.0 - t : 1.0) * sk;
                     stag += t * sk;
                 }
-                cs32[i] = make_float2((float)ssub, (float)stag);
+                cs32[i] = make_float2(df_mul(Ad, df_from(ssub)).h, df_mul(Ad, df_from(stag)).h);
             }
             // window mass times 1/Phi, as an FP32 pair; FP64 only for an edge within 3 sigma of mu
             const df zad = df_mul(df_add(zlo, df_neg(mu)), isig), zbd = df_mul(df_add(zhi, df_neg(mu)), isig);

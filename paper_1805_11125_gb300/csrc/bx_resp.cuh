@@ -98,9 +98,10 @@ static __device__ __noinline__ void outer_direct(float t0, float kk, float& Sp, 
 
 constexpr float INV_2LN2 = 0.72134752044448170f;   // kk = kap / (2 ln 2)
 
-// Response entry of output bin `mf` (row index as float) and one column.
+// Response entry of output bin `mf` (row index as float) and one column, divided by the
+// column's amplitude A: the node sum 8 p0 + 5 (p- + p+).
 // cf = (floor(mu/w), c_hi, hs_hi, hs_lo); cg = (kap, Ck2, c_lo, A / 9).
-__device__ __forceinline__ float resp_exact32(float mf, const float4& cf, const ColG& cg) {
+__device__ __forceinline__ float resp_shape32(float mf, const float4& cf, const ColG& cg) {
     float th, tl;
     centre_df(mf, cf, cg.c_lo, th, tl);
     const float p0 = centre_node(th, tl);
@@ -112,7 +113,11 @@ __device__ __forceinline__ float resp_exact32(float mf, const float4& cf, const 
         float Sm;
         outer_direct(th, cg.kap * INV_2LN2, Sp, Sm);
     }
-    return cg.A * fmaf(GL_W_OUT, Sp, GL_W_MID * p0);
+    return fmaf(GL_W_OUT, Sp, GL_W_MID * p0);
+}
+// Response entry R[m, i] of output bin `mf` and one column.
+__device__ __forceinline__ float resp_exact32(float mf, const float4& cf, const ColG& cg) {
+    return cg.A * resp_shape32(mf, cf, cg);
 }
 
 // The three node sums of the adjoint: P0 = sum w_j p_j, P1 = sum w_j t_j p_j,
