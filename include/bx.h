@@ -183,6 +183,9 @@ typedef struct {
     int iters;                  /* accepted Newton steps */
     int n_evals;                /* NLL+gradient evaluations used */
     int status;                 /* BX_OK, BX_ENOTCONV or BX_EDOMAIN */
+    int n_at_bound;             /* free parameters held at a bound at the returned theta */
+    double damping;             /* Levenberg damping of the last fresh Hessian (scaled units;
+                                   0: positive definite as measured) */
 } bx_fit_result;
 
 /* n fits; item j fits toy toy_idx[j] (host, NULL = toy 0) from theta0[j*P..].
@@ -192,9 +195,10 @@ int bx_fit(bx_model* model, int n, const int* toy_idx, const double* theta0,
            const bx_fit_opts* opts, double* theta_out, bx_fit_result* res);
 
 /* Diagnostic of the tensor-core path: multiplies a 128 x 32 FP32 matrix by a 16 x 32 one
- * through the same TF32 hi/lo split, shared-memory operand layout, tcgen05.mma issue and
- * tensor-memory read-back as the forward kernel, on the current device, and returns the
- * largest relative error against an FP64 host product in *max_rel_err (expected ~1e-6). */
+ * through the same three-part operand split (hi on a per-row power-of-two grid, TF32 mid and
+ * lo), shared-memory operand layout, tcgen05.mma issue and tensor-memory drain as the forward
+ * kernel, on the current device, and returns the largest relative error against an FP64 host
+ * product in *max_rel_err (expected ~1e-7). */
 int bx_selftest_tensor_core(double* max_rel_err);
 /* Diagnostic of the device watchdog: launches one warp that waits on an mbarrier nothing
  * ever arrives on, bounded by budget_s (0 < budget_s <= 10).  Returns BX_ETIMEOUT when the

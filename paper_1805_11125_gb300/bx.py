@@ -54,7 +54,7 @@ class bx_fit_opts(C.Structure):
 
 class bx_fit_result(C.Structure):
     _fields_ = [("nll", C.c_double), ("edm", C.c_double), ("iters", C.c_int), ("n_evals", C.c_int),
-                ("status", C.c_int)]
+                ("status", C.c_int), ("n_at_bound", C.c_int), ("damping", C.c_double)]
 
 
 class BxError(RuntimeError):
@@ -276,7 +276,8 @@ class Model:
         st = lib().bx_fit(self.h, n, _ptr(ti), _ptr(th0), C.byref(o), _ptr(out), C.cast(res, _P))
         if st not in (BX_OK, BX_ENOTCONV):
             _check(st)
-        info = [dict(nll=r.nll, edm=r.edm, iters=r.iters, n_evals=r.n_evals, status=r.status) for r in res]
+        info = [dict(nll=r.nll, edm=r.edm, iters=r.iters, n_evals=r.n_evals, status=r.status,
+                     n_at_bound=r.n_at_bound, damping=r.damping) for r in res]
         return out, info, st
 
 

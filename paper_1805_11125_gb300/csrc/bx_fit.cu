@@ -70,8 +70,8 @@ constexpr double EDM_FLOOR_FP32 = 1e-5;
 constexpr double HSIG_FP32 = 1.0;
 
 struct FitCtl {
-    int phase, iters, evals, status, max_evals, fails;
-    double edm, edm0, tol, mu_min, mu_used, hrel, mu_conv, hsig;
+    int phase, iters, evals, status, max_evals, fails, n_bound;
+    double edm, edm0, tol, mu_min, mu_used, hrel, mu_conv, hsig, mu_fresh;
 };
 
 struct FitDev {
@@ -226,7 +226,13 @@ __global__ void k_fit(FitDev F) {
         } else {
             c.mu_used = mu;
             c.edm = -0.5 * gd;
-            if (fresh) c.edm0 = c.edm;
+            if (fresh) {
+                c.edm0 = c.edm;
+                c.mu_fresh = mu;
+                int nb = 0;
+                for (int i = 0; i < Pt; ++i) nb += (fr[i] && !act[i]) ? 1 : 0;
+                c.n_bound = nb;
+            }
             if (fresh && c.edm < c.tol && mu <= c.mu_conv) {
                 c.phase = PH_DONE;
                 c.status = BX_OK;
@@ -431,9 +437,9 @@ extern "C" int bx_fit(bx_model* m, int n, const int* toy_idx, const double* thet
         }
         skip[(size_t)j * S] = 0;
         const bool f64 = m->precision == BX_FP64;
-        ctl[j] = FitCtl{PH_START, 0, 1, BX_ENOTCONV, o.max_iter, 0, INFINITY, INFINITY,
+        ctl[j] = FitCtl{PH_START, 0, 1, BX_ENOTCONV, o.max_iter, 0, 0, INFINITY, INFINITY,
                         f64 ? o.tol_edm : std::max(o.tol_edm, EDM_FLOOR_FP32), 0.0, 0.0, hrel,
-                        f64 ? MU_CONV_FP64 : MU_CONV_FP32, f64 ? 0.0 : HSIG_FP32};
+                        f64 ? MU_CONV_FP64 : MU_CONV_FP32, f64 ? 0.0 : HSIG_FP32, 0.0};
     }
     FitDev& D = s->dev;
     CUF(cudaStreamSynchronize(m->stream));   // slot composition uploaded on the model stream
@@ -473,6 +479,8 @@ extern "C" int bx_fit(bx_model* m, int n, const int* toy_idx, const double* thet
         res[j].iters = ctl[j].iters;
         res[j].n_evals = ctl[j].evals;
         res[j].status = ctl[j].phase == PH_DONE ? ctl[j].status : BX_ENOTCONV;
+        res[j].n_at_bound = ctl[j].n_bound;
+        res[j].damping = ctl[j].mu_fresh;
         if (res[j].status != BX_OK && worst == BX_OK) worst = res[j].status;
     }
     if (worst != BX_OK) bx_set_error(worst, "bx_fit: not every fit converged (see the per-fit status)");

@@ -47,6 +47,16 @@ def test_asimov_fit_returns_truth(prec):
     out, info, st = m.fit(th0, tol_edm=1e-8, max_iter=5000)
     assert st == bx.BX_OK, info
     _check_against(ref, out, info, s.P, s.default_free().astype(bool), 4, nsig=NSIG[prec])
+    # diagnostics: the parameters held at a bound are the free ones on a bound of the returned
+    # theta (here the weakly constrained resolution constant c may end on its lower bound);
+    # a converged fit's last Hessian needed at most the damping with which convergence may be
+    # declared (1e-2 FP64, 1e-1 FP32, scaled units)
+    lo, hi = s.default_bounds()
+    free = s.default_free().astype(bool)
+    for j, r in enumerate(info):
+        th = out[j, : s.P]
+        assert r["n_at_bound"] == int(np.count_nonzero(free & ((th <= lo) | (th >= hi)))), r
+        assert 0.0 <= r["damping"] <= (1e-2 if prec == bx.BX_FP64 else 1e-1), r
 
 
 @pytest.mark.parametrize("prec", [bx.BX_FP64, bx.BX_FP32])
