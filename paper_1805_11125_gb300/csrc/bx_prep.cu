@@ -240,9 +240,9 @@ __global__ void __launch_bounds__(256) k_prep(Work w) {
     if (tid == 0) w.status[item] = s_bad ? (int)BX_EDOMAIN : 0;
 }
 
-// The mixed-precision column stage takes a Gaussian tail in FP32 from Z_F32 standard deviations
-// on: Q(3) = 1.3e-3, so FP32's relative error (a few 1e-7, the argument's rounding included)
-// stays below 1e-9 absolute; nearer the mean it takes the FP64 tail.
+// The mixed-precision column stage takes the normalisation's Gaussian tail in FP32 from Z_F32
+// standard deviations on: Q(3) = 1.3e-3, so FP32's relative error (a few 1e-7, the argument's
+// rounding included) stays below 1e-9 absolute; nearer the mean it takes the FP64 tail.
 constexpr float Z_F32 = 3.0f;
 constexpr float INV_SQRT_2PI_F = 0.39894228f;
 __device__ __forceinline__ float upper_tail32(float x) {
@@ -299,10 +299,10 @@ __device__ void block_scan_df(df& a, df& b, df& ta, df& tb, float* sh) {
 
 // The per-column stage of the mixed-precision modes in double-float FP32 (bx_df.cuh, ~2^-44
 // relative): the Birks prefix sums, 1/(1 + kB S), mu, sigma^2, 1/sigma by one Newton step, the
-// generator's split constants.  FP64 only where a column's Gaussian reaches 0 npe or a window
-// edge within Z_F32 = 3 sigma (1/Phi, phi/Phi, erfc of the window mass; FP32 tails beyond),
-// and for the FP64 copies of mu, sigma, Q, dQ/dkB that the adjoint's chain rule reads (formed
-// on the integer pipe, f2d).  The window masses go out as FP32 pairs.
+// generator's split constants.  FP64 only where a column's Gaussian reaches 0 npe within
+// Z_F32 = 3 sigma (1/Phi, phi/Phi; FP32 tails beyond) and for the FP64 copies of mu, sigma, Q,
+// dQ/dkB that the adjoint's chain rule reads (formed on the integer pipe, f2d).  The window
+// masses come from FP32 tails and go out as FP32 pairs.
 __global__ void __launch_bounds__(256) k_prep32(Work w) {
     const int item = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
     if (w.skip && w.skip[item]) {
@@ -442,16 +442,18 @@ __global__ void __launch_bounds__(256) k_prep32(Work w) {
                 }
                 cs32[i] = make_float2(df_mul(Ad, df_from(ssub)).h, df_mul(Ad, df_from(stag)).h);
             }
-            // window mass times 1/Phi, as an FP32 pair; FP64 only for an edge within 3 sigma of mu
+            // window mass times 1/Phi, as an FP32 pair, from FP32 tails on the side away from the
+            // mean: the masses enter only the Eq. 4 marginals, where an FP32 tail's rounding
+            // (<= ~6e-8 of the mass) averages over the several hundred columns near the window's
+            // edges to ~1e-9 of a marginal bin
             const df zad = df_mul(df_add(zlo, df_neg(mu)), isig), zbd = df_mul(df_add(zhi, df_neg(mu)), isig);
             const float za = zad.h, zb = zbd.h;
             df mass;
             if (za <= -(float)Q_CUT && zb >= (float)Q_CUT) mass = df{1.f, 0.f};
             else if (za >= (float)Q_CUT || zb <= -(float)Q_CUT) mass = df{0.f, 0.f};
-            else if (fabsf(za) < Z_F32 || fabsf(zb) < Z_F32) mass = df_from(gauss_mass(df_to_double(zad), df_to_double(zbd)));
-            else if (za >= 0.f) mass = df{upper_tail32(za) - upper_tail32(zb), 0.f};
-            else if (zb <= 0.f) mass = df{upper_tail32(-zb) - upper_tail32(-za), 0.f};
-            else mass = df_two_sum(1.0f, -(upper_tail32(zb) + upper_tail32(-za)));
+            else if (za >= 0.f) mass = df_two_sum(upper_tail32(za), -upper_tail32(zb));
+            else if (zb <= 0.f) mass = df_two_sum(upper_tail32(-zb), -upper_tail32(-za));
+            else mass = df_add(df_two_sum(1.0f, -upper_tail32(zb)), df{-upper_tail32(-za), 0.f});
             const df aw = df_mul(mass, normd);
             aW2[i] = make_float2(aw.h, aw.l);
             // response band
