@@ -172,6 +172,10 @@ typedef struct {
                                    c >= 1e-3, eps in [0, 1], s_r >= 0.05) */
     const double* hi;           /* [P] upper bounds (NULL: eps <= 1, otherwise none) */
     int iters_per_launch;       /* evaluation rounds per graph replay (0 -> 4) */
+    double* cov_out;            /* [n][P][P] host, or NULL: per fit the inverse Hessian of -lnL
+                                   at the last fresh Hessian (the covariance of the estimates at a
+                                   converged fit); rows and columns of fixed parameters and of
+                                   parameters held at a bound are 0 */
 } bx_fit_opts;
 /* free_mask/lo/hi are given in the layout of a toy with max K species: slots 0..Kmax-1 are
  * rates, Kmax..Kmax+6 the seven response/pile-up/radial parameters; a toy with K_t < Kmax

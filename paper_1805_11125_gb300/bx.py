@@ -49,7 +49,7 @@ class bx_options(C.Structure):
 
 class bx_fit_opts(C.Structure):
     _fields_ = [("tol_edm", C.c_double), ("max_iter", C.c_int), ("free_mask", _P), ("lo", _P), ("hi", _P),
-                ("iters_per_launch", C.c_int)]
+                ("iters_per_launch", C.c_int), ("cov_out", _P)]
 
 
 class bx_fit_result(C.Structure):
@@ -261,7 +261,10 @@ class Model:
         return 8 + 2 * self.P
 
     def fit(self, theta0, toy_idx=None, tol_edm: float = 0.0, max_iter: int = 0, free=None, lo=None, hi=None,
-            iters_per_launch: int = 0):
+            iters_per_launch: int = 0, want_cov: bool = False):
+        """n fits (one row of theta0 each) on the device; returns (theta[n, P], info, status).
+        info[j]: nll, edm, iters, n_evals, status, n_at_bound, damping, and with want_cov the
+        inverse Hessian of -lnL ("cov", P x P; zero rows for fixed and bound-held parameters)."""
         th0 = _f64(theta0)
         th0 = th0[None, :] if th0.ndim == 1 else th0
         n = th0.shape[0]
@@ -270,7 +273,8 @@ class Model:
         ti = None if toy_idx is None else np.ascontiguousarray(toy_idx, dtype=np.int32)
         fr = None if free is None else np.ascontiguousarray(free, dtype=np.uint8)
         l, h = _f64(lo), _f64(hi)
-        o = bx_fit_opts(tol_edm, max_iter, _ptr(fr), _ptr(l), _ptr(h), iters_per_launch)
+        cov = np.zeros((n, self.P, self.P)) if want_cov else None
+        o = bx_fit_opts(tol_edm, max_iter, _ptr(fr), _ptr(l), _ptr(h), iters_per_launch, _ptr(cov))
         out = np.zeros((n, self.P))
         res = (bx_fit_result * n)()
         st = lib().bx_fit(self.h, n, _ptr(ti), _ptr(th0), C.byref(o), _ptr(out), C.cast(res, _P))
@@ -278,6 +282,9 @@ class Model:
             _check(st)
         info = [dict(nll=r.nll, edm=r.edm, iters=r.iters, n_evals=r.n_evals, status=r.status,
                      n_at_bound=r.n_at_bound, damping=r.damping) for r in res]
+        if want_cov:
+            for j in range(n):
+                info[j]["cov"] = cov[j]
         return out, info, st
 
 
@@ -306,6 +313,34 @@ class Model:
 
 
 # C-named conveniences -------------------------------------------------------------------
+
+def toy_study(spec, n_toys: int, theta_true=None, precision: int = BX_FP32, seed: int = 0, start=None,
+              free=None, tol_edm: float = 0.0, max_iter: int = 0, stream=None) -> dict:
+    """Toy-based sensitivity with the batched fit engine: n_toys pseudo-experiments, the
+    Poisson counts of the expected counts at theta_true (computed by the FP64 GPU model), all
+    fitted in one bx_fit call from ``start`` (default theta_true).  Returns theta[n, P],
+    sigma[n, P] (square roots of the inverse Hessian's diagonal at each fit), pull[n, P] =
+    (theta - theta_true) / sigma (NaN where sigma = 0: fixed or bound-held parameters),
+    status[n] and nll[n]."""
+    from . import inputs as _inputs
+    th_true = np.asarray(spec.theta_true if theta_true is None else theta_true, dtype=np.float64)
+    gen = Model(spec.with_counts(np.zeros(spec.n_bins_total)), precision=BX_FP64, stream=stream)
+    mu = gen.expected(th_true)
+    gen.close()
+    toys = [spec.with_counts(_inputs.poisson_counts(mu, seed + t)) for t in range(n_toys)]
+    P = spec.P
+    m = Model(toys, precision=precision, max_batch=n_toys * (8 + 2 * P), stream=stream)
+    th0 = np.tile(th_true if start is None else np.asarray(start, dtype=np.float64), (n_toys, 1))
+    out, info, _ = m.fit(th0, toy_idx=np.arange(n_toys), free=free, tol_edm=tol_edm, max_iter=max_iter,
+                         want_cov=True)
+    m.close()
+    theta = out[:, :P]
+    sig = np.sqrt(np.maximum(np.array([np.diag(r["cov"])[:P] for r in info]), 0.0))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        pull = np.where(sig > 0, (theta - th_true[None, :]) / sig, np.nan)
+    return dict(theta=theta, sigma=sig, pull=pull, status=np.array([r["status"] for r in info]),
+                nll=np.array([r["nll"] for r in info]))
+
 
 def bx_model_create(specs, precision=BX_FP32, max_batch=1, **kw) -> Model:
     return Model(specs, precision=precision, max_batch=max_batch, **kw)

@@ -483,6 +483,7 @@ extern "C" int bx_fit(bx_model* m, int n, const int* toy_idx, const double* thet
         res[j].damping = ctl[j].mu_fresh;
         if (res[j].status != BX_OK && worst == BX_OK) worst = res[j].status;
     }
+    if (o.cov_out) CUF(cudaMemcpy(o.cov_out, D.V, (size_t)n * P * P * 8, cudaMemcpyDeviceToHost));
     if (worst != BX_OK) bx_set_error(worst, "bx_fit: not every fit converged (see the per-fit status)");
     return worst;
 }

@@ -145,3 +145,49 @@ def test_profile_likelihood_scan_matches_the_oracle(prec):
     np.testing.assert_allclose(d2[[1, 3]], [1.0, 1.0], rtol=0.1)
     assert d2[0] > d2[1] and d2[4] > d2[3]
     m.close()
+
+
+def test_fit_covariance_matches_the_oracle():
+    """The inverse Hessian returned with a fit (FP64) against the oracle's at its optimum:
+    standard deviations within 1e-3 relative, correlation coefficients within 1e-3, on the
+    parameters free in both (neither fixed nor held at a bound)."""
+    s = dataset("small_mv")
+    ref = O.fit(s, s.theta_true, tol_edm=1e-14)
+    assert ref["status"] == 0
+    m = bx.Model(s, precision=bx.BX_FP64, max_batch=8 + 2 * s.P)
+    out, info, st = m.fit(s.theta_true, tol_edm=1e-12, max_iter=5000, want_cov=True)
+    assert st == bx.BX_OK
+    cg, co = info[0]["cov"][: s.P, : s.P], ref["cov"]
+    live = (np.diag(cg) > 0) & (np.diag(co) > 0)
+    assert np.count_nonzero(live) >= s.P - 3
+    sg, so = np.sqrt(np.diag(cg)[live]), np.sqrt(np.diag(co)[live])
+    np.testing.assert_allclose(sg, so, rtol=1e-3)
+    rg = cg[np.ix_(live, live)] / np.outer(sg, sg)
+    ro = co[np.ix_(live, live)] / np.outer(so, so)
+    assert np.max(np.abs(rg - ro)) <= 1e-3
+
+
+@pytest.mark.parametrize("prec", [bx.BX_FP64, bx.BX_FP32])
+def test_toy_study_pulls(prec):
+    """Toy-based sensitivity (bx.toy_study): 96 Poisson toys of the small multivariate model,
+    rates free and the response held (a calibrated detector), fitted in one call.  The pulls
+    (theta - theta_true) / sigma of the rates the model determines well (sigma / theta < 0.1
+    by the oracle's inverse Hessian on Asimov data) have mean 0 and width 1 within their
+    statistical spread: mean within 4 / sqrt(n), width within 20 %."""
+    s = I.config("small_mv")
+    fr = np.zeros(s.P, dtype=np.uint8)
+    fr[: s.K] = 1
+    asimov = s.with_counts(O.expected(s, s.theta_true))
+    ref = O.fit(asimov, s.theta_true, free=fr, tol_edm=1e-14)
+    rel = np.sqrt(np.maximum(np.diag(ref["cov"]), 0.0))[: s.K] / s.theta_true[: s.K]
+    good = np.nonzero(rel < 0.1)[0]
+    assert len(good) >= 4
+    n = 96
+    r = bx.toy_study(s, n, precision=prec, seed=500, free=fr)
+    ok = r["status"] == bx.BX_OK
+    assert np.count_nonzero(ok) >= 0.95 * n
+    for k in good:
+        p = r["pull"][ok, k]
+        assert np.all(np.isfinite(p))
+        assert abs(float(np.mean(p))) <= 4.0 / np.sqrt(len(p)), (k, float(np.mean(p)))
+        assert 0.8 <= float(np.std(p)) <= 1.2, (k, float(np.std(p)))
