@@ -13,6 +13,9 @@
  *       reading: Birks quenching on a caller-supplied stopping-power table)
  *         Q_i   = sum_{j<i} dE/(1 + kB S_j) + dE/(2 (1 + kB S_i))
  *         mu_i  = LY Q_i,      sigma_i^2 = a mu_i + b mu_i^2 + c
+ *       with species-specific quenching (the "next" response variant: alpha or gamma
+ *       species quench differently) species k uses kB quench[k]; the species are grouped by
+ *       multiplier and every group has its own map and response (a2)
  *   a2  response of Eq. 1, bin-integrated Gaussian in npe, normalised to the mass above 0:
  *         R[m,i] = (Phi(z_{m+1,i}) - Phi(z_{m,i})) / Phi(mu_i / sigma_i),
  *         z_{m,i} = (m w - mu_i) / sigma_i
@@ -101,7 +104,31 @@ typedef struct {
     const double* psd2;                /* [K][n_p2] */
     const double* n_r2_counts;         /* [n_r2][m_hi - m_lo] */
     const double* n_p2_counts;         /* [n_p2][m_hi - m_lo] */
+    const double* quench;              /* [K] Birks multiplier per species (species k quenches with
+                                          kB quench[k]); NULL -> 1 for every species */
 } om_model;
+
+enum { OM_MAX_SETS = 4 };
+
+/* Species-specific quenching (reading: a species' Birks constant is kB times its own
+ * multiplier, e.g. ~1e2 for alpha particles on the electron stopping-power table): the species
+ * are grouped by multiplier, and each group ("set") has its own Birks map and response.
+ * Returns the number of sets (<= OM_MAX_SETS, 0 if there are more), their multipliers xi[]
+ * and each species' set in set_of[]. */
+static int quench_sets(const om_model* m, double* xi, int* set_of) {
+    int n = 0;
+    for (int k = 0; k < m->K; ++k) {
+        const double q = m->quench ? m->quench[k] : 1.0;
+        int c = 0;
+        while (c < n && xi[c] != q) ++c;
+        if (c == n) {
+            if (n == OM_MAX_SETS) return 0;
+            xi[n++] = q;
+        }
+        set_of[k] = c;
+    }
+    return n;
+}
 
 enum { OM_OK = 0, OM_EINVAL = -1, OM_ENOMEM = -2, OM_EDOMAIN = -4, OM_ENOTCONV = -6 };
 
@@ -120,6 +147,14 @@ static int check_model(const om_model* m) {
     if (m->n_r2 < 0 || m->n_p2 < 0 || (m->n_r2 + m->n_p2 > 0 && !m->field) || (m->n_r2 > 0 && !m->rad_class) ||
         (m->n_p2 > 0 && !m->psd2))
         return OM_EINVAL;
+    if (m->quench) {
+        for (int k = 0; k < m->K; ++k)
+            if (!(m->quench[k] >= 0.0) || !isfinite(m->quench[k])) return OM_EINVAL;
+        double xi[OM_MAX_SETS];
+        int set_of[OPMAX];
+        const int n = quench_sets(m, xi, set_of);
+        if (n == 0 || (n > 1 && m->n_r2 + m->n_p2 > 0)) return OM_EINVAL;   /* 2D slices: one set only */
+    }
     return OM_OK;
 }
 
@@ -198,10 +233,11 @@ typedef struct {
 
 static void work_free(work* w) { free(w->Q); free(w->mu); free(w->sig); free(w->den); free(w->v); }
 
-/* a1: quenching + light yield + resolution; returns OM_EDOMAIN if sigma^2 <= 0 anywhere. */
-static int stage_a1(const om_model* m, const dual* th, work* w) {
+/* a1: quenching + light yield + resolution for the species of Birks multiplier xi (kB xi);
+ * returns OM_EDOMAIN if sigma^2 <= 0 anywhere. */
+static int stage_a1(const om_model* m, const dual* th, work* w, double xi) {
     int N = m->n_grid, K = m->K;
-    dual LY = th[K], a = th[K + 1], b = th[K + 2], c = th[K + 3], kB = th[K + 4];
+    dual LY = th[K], a = th[K + 1], b = th[K + 2], c = th[K + 3], kB = dscale(th[K + 4], xi);
     double dE = m->e_max / N;
     dual run = dc(0.0);
     int st = OM_OK;
@@ -218,14 +254,16 @@ static int stage_a1(const om_model* m, const dual* th, work* w) {
     return st;
 }
 
-/* a2 + a3: v_k[m] = sum_i R[m,i] s_k[i] for every m in [0, m_hi); with 2D slices also
- * Y[m][b] = sum_i R[m,i] T_r[i][b] (T_r: [N][B2], Y: [M][B2]). */
-static void stage_a23(const om_model* m, work* w, double* R_out, const dual* Tr, dual* Y) {
+/* a2 + a3: v_k[m] = sum_i R[m,i] s_k[i] for every m in [0, m_hi) and the species of set c
+ * (set_of NULL: every species); with 2D slices also Y[m][b] = sum_i R[m,i] T_r[i][b]
+ * (T_r: [N][B2], Y: [M][B2]). */
+static void stage_a23(const om_model* m, work* w, double* R_out, const dual* Tr, dual* Y, const int* set_of, int c) {
     int N = m->n_grid, K = m->K, M = m->m_hi, B2 = m->n_r2 + m->n_p2;
     #pragma omp parallel for schedule(dynamic, 4)
     for (int r = 0; r < M; ++r) {
         dual* vr = w->v + (size_t)r * K;
-        for (int k = 0; k < K; ++k) vr[k] = dc(0.0);
+        for (int k = 0; k < K; ++k)
+            if (!set_of || set_of[k] == c) vr[k] = dc(0.0);
         if (Y) for (int b = 0; b < B2; ++b) Y[(size_t)r * B2 + b] = dc(0.0);
         for (int i = 0; i < N; ++i) {
             dual za = ddiv(dsub(dc(r * m->width), w->mu[i]), w->sig[i]);
@@ -233,6 +271,7 @@ static void stage_a23(const om_model* m, work* w, double* R_out, const dual* Tr,
             dual R = ddiv(gauss_mass(za, zb), w->den[i]);
             if (R_out) R_out[(size_t)r * N + i] = R.v;
             for (int k = 0; k < K; ++k) {
+                if (set_of && set_of[k] != c) continue;
                 double s = m->shapes[(size_t)k * N + i];
                 if (s != 0.0) daxpy(&vr[k], s, &R);
             }
@@ -312,10 +351,17 @@ static int evaluate(const om_model* m, const double* theta, int want_grad,
         goto done;
     }
 
-    st = stage_a1(m, th, &w);
-    if (st) goto done;
-    if (B2 > 0 && (st = stage_2d_templates(m, th, Tr))) goto done;
-    stage_a23(m, &w, NULL, Tr, Y);
+    {
+        double xi[OM_MAX_SETS];
+        int set_of[OPMAX];
+        const int nset = quench_sets(m, xi, set_of);
+        if (B2 > 0 && (st = stage_2d_templates(m, th, Tr))) goto done;
+        for (int c = 0; c < nset; ++c) {   /* one Birks map and response per set of species */
+            st = stage_a1(m, th, &w, xi[c]);
+            if (st) goto done;
+            stage_a23(m, &w, NULL, Tr, Y, set_of, c);
+        }
+    }
 
     /* a4 + a5 for the energy spectra */
     int o = 0;
@@ -415,7 +461,7 @@ int om_quench(const om_model* m, const double* theta, double* Q, double* mu, dou
     for (int j = 0; j < K + 7; ++j) th[j] = dc(theta[j]);
     work w; memset(&w, 0, sizeof w);
     w.Q = calloc(N, sizeof(dual)); w.mu = calloc(N, sizeof(dual)); w.sig = calloc(N, sizeof(dual)); w.den = calloc(N, sizeof(dual));
-    st = stage_a1(m, th, &w);
+    st = stage_a1(m, th, &w, 1.0);   /* the map of unit Birks multiplier */
     for (int i = 0; i < N; ++i) {
         if (Q) Q[i] = w.Q[i].v;
         if (mu) mu[i] = w.mu[i].v;
@@ -426,8 +472,8 @@ int om_quench(const om_model* m, const double* theta, double* Q, double* mu, dou
     return st;
 }
 
-/* a2 + a3 values: the response matrix R [m_hi][n_grid] (may be NULL) and the species
- * spectra v [m_hi][K] (may be NULL). */
+/* a2 + a3 values: the response matrix R [m_hi][n_grid] of the first set of species (may be
+ * NULL) and the species spectra v [m_hi][K] (may be NULL). */
 int om_response(const om_model* m, const double* theta, double* R, double* v) {
     int st = check_model(m); if (st) return st;
     NP = 0;
@@ -437,11 +483,14 @@ int om_response(const om_model* m, const double* theta, double* R, double* v) {
     work w;
     w.Q = calloc(N, sizeof(dual)); w.mu = calloc(N, sizeof(dual)); w.sig = calloc(N, sizeof(dual));
     w.den = calloc(N, sizeof(dual)); w.v = calloc((size_t)M * K, sizeof(dual));
-    st = stage_a1(m, th, &w);
-    if (!st) {
-        stage_a23(m, &w, R, NULL, NULL);
-        if (v) for (size_t j = 0; j < (size_t)M * K; ++j) v[j] = w.v[j].v;
+    double xi[OM_MAX_SETS];
+    int set_of[OPMAX];
+    const int nset = quench_sets(m, xi, set_of);
+    for (int c = 0; c < nset && !st; ++c) {   /* R of the first set */
+        st = stage_a1(m, th, &w, xi[c]);
+        if (!st) stage_a23(m, &w, c == 0 ? R : NULL, NULL, NULL, set_of, c);
     }
+    if (!st && v) for (size_t j = 0; j < (size_t)M * K; ++j) v[j] = w.v[j].v;
     work_free(&w);
     return st;
 }

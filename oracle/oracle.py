@@ -59,6 +59,7 @@ class _Model(C.Structure):
         ("n_psd", C.c_int), ("psd_prob", C.c_void_p), ("n_psd_counts", C.c_void_p),
         ("n_r2", C.c_int), ("n_p2", C.c_int), ("field", C.c_void_p), ("amp", C.c_double),
         ("psd2", C.c_void_p), ("n_r2_counts", C.c_void_p), ("n_p2_counts", C.c_void_p),
+        ("quench", C.c_void_p),
     ]
 
 
@@ -102,6 +103,7 @@ class OracleModel:
             "n_rad": _arr(s.counts.get("rad")), "n_psd": _arr(s.counts.get("psd")),
             "field": _arr(s.field2d), "psd2": _arr(s.psd2d_prob),
             "n_r2": _arr(s.counts.get("r2d")), "n_p2": _arr(s.counts.get("p2d")),
+            "quench": _arr(getattr(s, "quench", None)),
         }
         k = self._keep
         has_rad = s.rad_class is not None and s.n_rad > 0
@@ -113,7 +115,7 @@ class OracleModel:
             r_iv=s.r_iv, att_len=s.att_len, n_rad_counts=_ptr(k["n_rad"]),
             n_psd=s.n_psd, psd_prob=_ptr(k["psd_prob"]), n_psd_counts=_ptr(k["n_psd"]),
             n_r2=s.n_rad2d, n_p2=s.n_psd2d, field=_ptr(k["field"]), amp=s.field_amp, psd2=_ptr(k["psd2"]),
-            n_r2_counts=_ptr(k["n_r2"]), n_p2_counts=_ptr(k["n_p2"]))
+            n_r2_counts=_ptr(k["n_r2"]), n_p2_counts=_ptr(k["n_p2"]), quench=_ptr(k["quench"]))
         self.ref = C.byref(self.c)
 
     @property

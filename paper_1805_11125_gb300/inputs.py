@@ -76,6 +76,8 @@ class ModelSpec:
     psd2d_prob: Optional[np.ndarray] = None  # [K, n_psd2d] pulse-shape bin probabilities
     field2d: Optional[np.ndarray] = None     # [n_grid, n_rad2d + n_psd2d] smooth field u in [-1, 1]
     field_amp: float = 0.0
+    # species-specific quenching: species k quenches with kB * quench[k] (None -> 1 for all)
+    quench: Optional[np.ndarray] = None
     theta_true: Optional[np.ndarray] = None
     species: List[str] = dataclasses.field(default_factory=list)
     counts: Dict[str, np.ndarray] = dataclasses.field(default_factory=dict)
@@ -312,6 +314,27 @@ def multivariate(n_grid=2000, e_max=3.0, width=1.0, lo_npe=100.0, hi_npe=1000.0,
     return spec
 
 
+def quenched(alpha_true: float = 2.3, alpha_quench: float = 150.0, gamma_quench: Optional[float] = None,
+             name: str = "quenched", **kw) -> ModelSpec:
+    """The multivariate model with species-specific quenching: the alpha species is a peak at
+    its true energy (alpha_true MeV, 30 keV wide) quenched with kB * alpha_quench, which puts it
+    near 0.5 MeV electron-equivalent; with gamma_quench the external (gamma) species quench with
+    kB * gamma_quench.  Every other species quenches with kB."""
+    spec = multivariate(name=name, **kw)
+    E = grid_energies(spec.n_grid, spec.e_max)
+    names = list(spec.species)
+    q = np.ones(spec.K)
+    if "alpha" in names:
+        ia = names.index("alpha")
+        a = alpha_peak(E, mu=alpha_true, sig=0.03)
+        spec.shapes[ia] = a / a.sum()
+        q[ia] = alpha_quench
+    if gamma_quench is not None:
+        q[spec.rad_class == RAD_EXTERNAL] = gamma_quench
+    spec.quench = q
+    return spec
+
+
 def discrimination(n_grid=2000, e_max=3.0, width=1.0, lo_npe=100.0, hi_npe=1000.0,
                    n_species=15, total=2e6, L=400, n_rad2d=60, n_psd2d=50, tag_eff=0.9, amp=0.05,
                    seed=0, name="discrimination") -> ModelSpec:
@@ -345,6 +368,9 @@ def config(name: str) -> ModelSpec:
     * ``discrimination`` K=15, TFC-subtracted/tagged 900 bins of 1 npe over 100-1000 npe and
                        the 2D energy x radius (900 x 60) and energy x pulse-shape (900 x 50)
                        histograms, 22 parameters, 2e6 events.
+    * ``quenched`` the multivariate model with species-specific quenching (the alpha species
+                  at its true energy, quenched with 150 kB); ``small_quenched`` its reduced
+                  grid, with the external (gamma) species quenched with 1.3 kB as well.
     * ``small_plain`` / ``small_mv`` / ``small_2d`` reduced grids that the oracle evaluates in
       well under a second (a few seconds for ``small_2d``) but that still span several
       128-row tiles and ragged tails.
@@ -364,6 +390,11 @@ def config(name: str) -> ModelSpec:
     if name == "small_mv":
         return multivariate(n_grid=520, width=3.0, lo_npe=120.0, hi_npe=900.0, n_species=9,
                             total=3e5, L=90, n_rad=20, n_psd=16, name=name)
+    if name == "quenched":
+        return quenched(name=name)
+    if name == "small_quenched":
+        return quenched(n_grid=520, width=3.0, lo_npe=120.0, hi_npe=900.0, n_species=12, total=3e5, L=90,
+                        n_rad=20, n_psd=16, gamma_quench=1.3, name=name)
     raise KeyError(name)
 
 

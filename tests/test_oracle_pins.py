@@ -394,3 +394,84 @@ def test_2d_dual_gradient_matches_central_differences():
         gfd[j] = (O.nll(s, tp) - O.nll(s, tm)) / (2 * h)
     scale = np.abs(g * th)
     np.testing.assert_allclose(g * th, gfd * th, rtol=2e-6, atol=2e-7 * scale.max())
+
+
+# ------------------------------------------------- species-specific quenching (Eq. 1, next)
+
+def _quench_spec(counts=True):
+    s = I.config("small_quenched")
+    if counts:
+        s = s.with_counts(I.poisson_counts(O.expected(s, s.theta_true), 3))
+    return s
+
+
+def test_quench_of_one_is_the_base_model():
+    """Multipliers of 1 for every species reproduce the model without species quenching bit
+    for bit."""
+    s = _quench_spec()
+    base = dataclasses.replace(s, quench=None)
+    ones = dataclasses.replace(s, quench=np.ones(s.K))
+    np.testing.assert_array_equal(O.expected(ones, s.theta_true), O.expected(base, s.theta_true))
+
+
+def test_common_quench_is_a_rescaled_birks_constant():
+    """One multiplier q for every species is the base model with kB replaced by q kB."""
+    s = _quench_spec()
+    q = 3.5
+    scaled = dataclasses.replace(s, quench=np.full(s.K, q))
+    base = dataclasses.replace(s, quench=None)
+    th = s.theta_true.copy()
+    th2 = th.copy()
+    th2[tail(s, "kB")] = th[tail(s, "kB")] * q
+    np.testing.assert_allclose(O.expected(scaled, th), O.expected(base, th2), rtol=1e-13, atol=0)
+
+
+def test_quench_sets_decompose_into_base_models():
+    """Expected counts are linear in the rates, so a model with three quenching groups is the
+    sum, over the groups, of the base model with kB scaled by the group's multiplier and only
+    that group's rates kept (every bin: vetoed, tagged, radial, pulse shape)."""
+    s = _quench_spec()
+    base = dataclasses.replace(s, quench=None)
+    th = s.theta_true.copy()
+    total = np.zeros(s.n_bins_total)
+    for q in np.unique(s.quench):
+        t = th.copy()
+        t[: s.K] = np.where(s.quench == q, th[: s.K], 0.0)
+        t[tail(s, "kB")] = th[tail(s, "kB")] * q
+        total += O.expected(base, t)
+    np.testing.assert_allclose(O.expected(s, th), total, rtol=1e-12, atol=1e-12 * total.max())
+
+
+def test_alpha_is_quenched_to_low_visible_energy():
+    """The alpha peak at 2.3 MeV true energy, quenched with 150 kB, appears between 0.3 and
+    0.7 MeV electron-equivalent (Birks' law with the electron stopping-power table): the
+    vetoed spectrum of the alpha species alone peaks there."""
+    s = _quench_spec(counts=False)
+    th = s.theta_true.copy()
+    ia = s.species.index("alpha")
+    th[: s.K] = 0.0
+    th[ia] = 1e5
+    mu = O.expected(s, th)[: s.n_window]
+    m_peak = s.m_lo + int(np.argmax(mu))
+    e_vis = m_peak * s.width / th[tail(s, "LY")]
+    assert 0.3 < e_vis < 0.7, e_vis
+
+
+def test_quench_dual_gradient_matches_central_differences():
+    s = _quench_spec()
+    th = I.parameter_points(s.theta_true, 1, rel=0.02, seed=9, free=s.default_free())[0]
+    f, g = O.nll(s, th, grad=True)
+    for j in [0, s.species.index("alpha"), s.species.index("ext0"), tail(s, "LY"), tail(s, "kB"), tail(s, "c")]:
+        h = 1e-5 * abs(th[j])
+        tp, tm = th.copy(), th.copy()
+        tp[j] += h
+        tm[j] -= h
+        fd = (O.nll(s, tp) - O.nll(s, tm)) / (2 * h)
+        assert abs(fd - g[j]) * abs(th[j]) <= 1e-6 * (1 + abs(g[j] * th[j])), (j, fd, g[j])
+
+
+def test_quench_with_2d_slices_is_rejected():
+    s = I.config("small_2d")
+    s = dataclasses.replace(s, quench=np.where(np.arange(s.K) == 0, 2.0, 1.0))
+    with pytest.raises(RuntimeError):
+        O.expected(s, s.theta_true)
