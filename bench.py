@@ -246,6 +246,7 @@ def run_ours(args):
         if args.toys > 0:
             fits["batched_toys"] = toy_fits(bx, I, args.toys, stream)
         disc = discrimination_leg(bx, I, stream, B=args.batch2d) if args.batch2d > 0 else None
+        fits["quenched"] = quenched_leg(bx, I, stream, B=args.batch) if args.quenched else None
     if rank != 0:
         return
     report(args, ws, B, total_ms, value, stage_ms, n_evals, entries, e2e, fp64_value, tc_value, clk, fits, disc)
@@ -389,6 +390,55 @@ def discrimination_leg(bx, I, stream, B=256, steps=5):
             "fit": {"wall_s": fit_s, "status": int(st), "evals": int(info[0]["n_evals"])}}
 
 
+def quenched_leg(bx, I, stream, B=1024, steps=5):
+    """Species-specific quenching (the alpha species at 2.3 MeV true energy, quenched with
+    150 kB; its own Birks map and response columns): -lnL + gradient evaluations/s of the
+    multivariate model with this response at the main leg's batch, FP32, and one FP32 fit."""
+    import torch
+    s = make_dataset(bx, I, I.config("quenched"), seed=0)
+    m = bx.Model(s, precision=bx.BX_FP32, max_batch=B, stream=stream)
+    pts = I.parameter_points(s.theta_true, B, rel=0.02, seed=410, free=s.default_free())
+    dev = torch.device("cuda", torch.cuda.current_device())
+    theta = torch.tensor(pts, dtype=torch.float64, device=dev)
+    nll = torch.empty(B, dtype=torch.float64, device=dev)
+    grad = torch.empty((B, m.P), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def step():
+        st = bx.lib().bx_nll_batch(m.h, B, None, bx._ptr(theta), bx._ptr(nll), bx._ptr(grad), 1)
+        if st:
+            raise bx.BxError(st, bx.lib().bx_last_error().decode())
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    m.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    total = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1)
+    stage_ms, n_evals, _ = m.profile(False)
+    per = {k: v / max(n_evals, 1) for k, v in stage_ms.items()}
+    m.close()
+    mf = bx.Model(s, precision=bx.BX_FP32, max_batch=8 + 2 * s.P, stream=stream)
+    th0 = I.parameter_points(s.theta_true, 1, rel=0.05, seed=411, free=s.default_free())
+    mf.fit(th0)
+    t0 = time.perf_counter()
+    _, info, st = mf.fit(th0)
+    fit_s = time.perf_counter() - t0
+    mf.close()
+    return {"workload": "multivariate with species-specific quenching (alpha at 2.3 MeV, 150 kB): 2 quenching "
+                        "groups of 2000 response columns", "global_batch": B,
+            "value": B * steps / (total / 1e3), "unit": "evals/s", "ms_per_step": total / steps,
+            "stage_ms_per_launch": {k: round(v, 4) for k, v in per.items()},
+            "fit": {"wall_s": fit_s, "status": int(st), "evals": int(info[0]["n_evals"])}}
+
+
 def fit_times(bx, I, spec, stream):
     """Full-fit wall time of one multivariate fit started at theta_true (1 + 0.1 z): FP32, FP64,
     and FP32 polished by FP64 (host wall clock around bx_fit, second call on a warm model)."""
@@ -458,6 +508,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the e2e, FP64 and fit legs (profiling runs)")
     ap.add_argument("--toys", type=int, default=4096, help="batched toy fits in the fit leg (0: none)")
     ap.add_argument("--batch2d", type=int, default=256, help="batch of the 2D-model leg (0: none)")
+    ap.add_argument("--quenched", type=int, default=1, help="species-quenching leg (0: none)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -104,6 +104,13 @@ typedef struct {
     double field_amp;           /* 0 <= field_amp < 1 */
     const double* counts_rad2d; /* [n_rad2d][m_hi - m_lo] */
     const double* counts_psd2d; /* [n_psd2d][m_hi - m_lo] */
+    /* Species-specific quenching (alpha or gamma species quench differently from electrons,
+     * Eq. 1's Birks parameter): species k quenches with kB * quench[k] on the same
+     * stopping-power table.  The species are grouped by multiplier (at most 4 groups), and
+     * every group has its own Birks map and response columns.  More than one group requires
+     * BX_FP32 or BX_FP64 and no 2D histograms, and needs (groups - 1) * ceil(n_grid / 128) * 128
+     * + n_grid <= 8192 columns. */
+    const double* quench;       /* [K] Birks multiplier per species (>= 0), or NULL: 1 for all */
 } bx_model_desc;
 
 typedef struct {

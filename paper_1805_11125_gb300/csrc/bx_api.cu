@@ -62,6 +62,23 @@ static bool finite_nonneg(const double* a, size_t n) {
     return true;
 }
 
+// Groups of species by Birks multiplier (species-specific quenching): returns the number of
+// groups (0 if there are more than MAX_SETS), their multipliers and each species' group.
+static int quench_groups(const bx_model_desc& d, double* xi, int* set_of) {
+    int n = 0;
+    for (int k = 0; k < d.n_species; ++k) {
+        const double q = d.quench ? d.quench[k] : 1.0;
+        int c = 0;
+        while (c < n && xi[c] != q) ++c;
+        if (c == n) {
+            if (n == MAX_SETS) return 0;
+            xi[n++] = q;
+        }
+        set_of[k] = c;
+    }
+    return n;
+}
+
 static int validate_desc(const bx_model_desc& d, int t) {
 #define REQ(cond, ...) \
     if (!(cond)) return bx_set_error(BX_EINVAL, __VA_ARGS__)
@@ -88,6 +105,20 @@ static int validate_desc(const bx_model_desc& d, int t) {
         REQ(d.r_fid > 0.0 && d.r_iv >= d.r_fid && d.att_len > 0.0, "toy %d: radial geometry invalid", t);
     }
     REQ(d.n_psd >= 0 && d.n_psd <= MAX_PSD, "toy %d: n_psd out of [0, %d]", t, MAX_PSD);
+    if (d.quench) {
+        for (int k = 0; k < d.n_species; ++k)
+            REQ(std::isfinite(d.quench[k]) && d.quench[k] >= 0.0, "toy %d: quench[%d] must be finite and >= 0", t, k);
+        double xi[MAX_SETS];
+        int set_of[KMAX];
+        const int ng = quench_groups(d, xi, set_of);
+        REQ(ng >= 1, "toy %d: more than %d quenching groups", t, MAX_SETS);
+        if (ng > 1) {
+            REQ(d.n_rad2d + d.n_psd2d == 0, "toy %d: quenching groups with 2D histograms are not supported", t);
+            const int ncs = (d.n_grid + BCOLS - 1) / BCOLS * BCOLS;
+            REQ((ng - 1) * ncs + d.n_grid <= MAX_CB * BCOLS, "toy %d: %d quenching groups of %d columns exceed %d",
+                t, ng, d.n_grid, MAX_CB * BCOLS);
+        }
+    }
     REQ(d.n_rad2d >= 0 && d.n_psd2d >= 0, "toy %d: n_rad2d, n_psd2d must be >= 0", t);
     if (d.n_rad2d + d.n_psd2d > 0) {
         const int n_sl = 1 + (d.tag_frac ? 1 : 0) + d.n_rad2d + d.n_psd2d;
@@ -172,6 +203,12 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
         n2d += descs[t].n_rad2d + descs[t].n_psd2d > 0 ? 1 : 0;
     }
     if (n2d != 0 && n2d != n_toys) return bx_set_error(BX_EINVAL, "toys of one model are either all 2D or none");
+    for (int t = 0; t < n_toys; ++t) {
+        double xi[MAX_SETS];
+        int set_of[KMAX];
+        if (quench_groups(descs[t], xi, set_of) > 1 && o.precision == BX_TF32X3)
+            return bx_set_error(BX_EINVAL, "toy %d: quenching groups need BX_FP32 or BX_FP64", t);
+    }
     if (n2d && o.precision != BX_FP32) return bx_set_error(BX_EINVAL, "2D histograms need BX_FP32");
     int dev = 0;
     CU(cudaGetDevice(&dev));
@@ -223,7 +260,10 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
         T.nb = T.nw * (1 + T.has_tag) + T.n_rad + T.n_psd + (T.n_r2 + T.n_p2) * T.nw;
         T.P = T.K + 7;
         T.n_tiles = (T.M + TM - 1) / TM;
-        T.n_cb = (T.N + BCOLS - 1) / BCOLS;
+        T.n_set = quench_groups(d, T.xi, T.set_of);
+        T.Ncs = T.n_set > 1 ? (T.N + BCOLS - 1) / BCOLS * BCOLS : T.N;
+        T.Next = (T.n_set - 1) * T.Ncs + T.N;
+        T.n_cb = (T.Next + BCOLS - 1) / BCOLS;
         T.n_kb = (T.N + KB - 1) / KB;
         T.dE = d.e_max / d.n_grid;
         T.w = d.width;
@@ -294,7 +334,7 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
                                          static_cast<float*>(g32), static_cast<double*>(gg), m->stream);
         if (e != cudaSuccess) st = bx_set_error(BX_ECUDA, "set-up kernel: %s", cudaGetErrorString(e));
         m->Kmax = std::max(m->Kmax, T.K);
-        m->Nmax = std::max(m->Nmax, T.N);
+        m->Nmax = std::max(m->Nmax, T.Next);
         m->Mmax = std::max(m->Mmax, T.M);
         m->nwmax = std::max(m->nwmax, T.nw);
         m->nbmax = std::max(m->nbmax, T.nb);
@@ -321,6 +361,8 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
     w.pstride = m->P;
     w.precision = m->precision;
     w.lam_pairs = m->precision == BX_FP32;
+    w.multi_set = 0;
+    for (const Toy& T : m->toys_h) w.multi_set |= T.n_set > 1 ? 1 : 0;
     w.band = m->band;
     w.watchdog_ns = m->watchdog_ns;
     w.max_tiles = m->max_tiles;
@@ -348,7 +390,7 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
         {(void**)&w.colr, sizeof(int2) * cap * w.Npad},
         {(void**)&w.lam, sizeof(double) * cap * 2 * w.Mpad},
         {(void**)&w.apart, m->any_cols && !species ? 2 * sizeof(float) * cap * m->max_tiles * w.Npad : 16},
-        {(void**)&w.tile_cols, sizeof(int2) * cap * MAX_TILES},
+        {(void**)&w.tile_cols, sizeof(int2) * cap * MAX_SETS * MAX_TILES},
         {(void**)&w.cb_rows, sizeof(int2) * cap * MAX_CB},
         {(void**)&w.v, species ? tv * cap * w.Mpad * US : 16},
         {(void**)&w.rowW, tv * cap * 3 * w.Mpad},

@@ -44,11 +44,18 @@ __device__ __forceinline__ void chain_rule(const Col64& cc, const double2& q, co
     g[4] = Gmu * LY * q.y;                  // kB
 }
 
-// rate part: g[5 + k] = s_k[i] (c_vetoed,k rho_vetoed + c_tagged,k rho_tagged)
-__device__ __forceinline__ void rate_part(const Toy& T, int i, double rs, double rt, double (&g)[GPN]) {
+// A column's place among the quenching groups: column ie is grid point ig of group grp;
+// species k contributes to it only if it belongs to that group.
+template <bool MULTI>
+__device__ __forceinline__ bool in_group(const Toy& T, int k, int grp) { return !MULTI || T.set_of[k] == grp; }
+
+// rate part: g[5 + k] = s_k[i] (c_vetoed,k rho_vetoed + c_tagged,k rho_tagged) for the species of
+// the column's group (grid point i, group grp)
+template <bool MULTI>
+__device__ __forceinline__ void rate_part(const Toy& T, int i, int grp, double rs, double rt, double (&g)[GPN]) {
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
-        if (k < T.K) {
+        if (k < T.K && in_group<MULTI>(T, k, grp)) {
             const double t = T.tag ? T.tag[k] : 0.0;
             g[5 + k] = T.shapes[(size_t)k * T.N + i] * ((T.tag ? 1.0 - t : 1.0) * rs + t * rt);
         } else {
@@ -72,12 +79,14 @@ __device__ __forceinline__ void block_sum_gp(double (&g)[GPN], double* red, doub
     }
 }
 
-__device__ __forceinline__ void column_weights(const Work& w, const Toy& T, int item, int i, bool ok, double& Ssub,
-                                               double& Stag, double& SA) {
+template <bool MULTI>
+__device__ __forceinline__ void column_weights(const Work& w, const Toy& T, int item, int i, int grp, bool ok,
+                                               double& Ssub, double& Stag, double& SA) {
     const double* coef = w.coef + (size_t)item * 3 * KMAX;
     Ssub = Stag = SA = 0.0;
     if (!ok) return;
     for (int k = 0; k < T.K; ++k) {
+        if (!in_group<MULTI>(T, k, grp)) continue;
         const double s = T.shapes[(size_t)k * T.N + i];
         Ssub += coef[k] * s;
         Stag += coef[KMAX + k] * s;
@@ -85,6 +94,7 @@ __device__ __forceinline__ void column_weights(const Work& w, const Toy& T, int 
     }
 }
 
+template <bool MULTI>
 __global__ void __launch_bounds__(BCOLS) k_bwd_f64(Work w) {
     // 1D item-major grid (a y dimension would cap the batch at 65535 items)
     const int cb = blockIdx.x % w.max_cb, item = blockIdx.x / w.max_cb, tid = threadIdx.x;
@@ -95,12 +105,17 @@ __global__ void __launch_bounds__(BCOLS) k_bwd_f64(Work w) {
         if (tid < GPN) gp[tid] = 0.0;
         return;
     }
-    const int i = cb * BCOLS + tid;
-    const bool ok = i < T.N;
+    const int i = cb * BCOLS + tid;   // column (of quenching group grp, grid point ig)
+    const int grp = MULTI ? i / T.Ncs : 0, ig = MULTI ? i - grp * T.Ncs : i;
+    const bool ok = MULTI ? (i < T.Next && ig < T.N) : i < T.N;
     const int2 rr = w.cb_rows[(size_t)item * MAX_CB + cb];
+    if (MULTI && rr.x >= rr.y) {   // no column of this block has support in its quenching group
+        if (tid < GPN) gp[tid] = 0.0;
+        return;
+    }
     const int r0 = max(rr.x, max(0, T.m_lo - T.L + 1)), r1 = min(rr.y, T.M);
     double Ssub, Stag, SA;
-    column_weights(w, T, item, i, ok, Ssub, Stag, SA);
+    column_weights<MULTI>(w, T, item, ig, grp, ok, Ssub, Stag, SA);
     const Col64 cc = ok ? w.col64[(size_t)item * w.Npad + i] : Col64{0.0, 1.0, 0.0, 0.0};
     const double* rw = static_cast<const double*>(w.rowW) + (size_t)item * 3 * w.Mpad;
     __shared__ double sW[3][RCH];
@@ -149,11 +164,12 @@ __global__ void __launch_bounds__(BCOLS) k_bwd_f64(Work w) {
         const double* th = w.theta + (size_t)item * w.tstride;
         chain_rule(cc, w.colq[(size_t)item * w.Npad + i], th, T.K, cc.norm * S0, cc.norm * S1 * inv_sig,
                    cc.norm * S2 * inv_sig, g);
-        rate_part(T, i, cc.norm * Rs, cc.norm * Rt, g);
+        rate_part<MULTI>(T, ig, grp, cc.norm * Rs, cc.norm * Rt, g);
     }
     block_sum_gp(g, red, gp);
 }
 
+template <bool MULTI>
 __global__ void __launch_bounds__(BCOLS, 7) k_bwd_f32(Work w) {
     // 1D item-major grid (a y dimension would cap the batch at 65535 items)
     const int cb = blockIdx.x % w.max_cb, item = blockIdx.x / w.max_cb, tid = threadIdx.x;
@@ -164,9 +180,14 @@ __global__ void __launch_bounds__(BCOLS, 7) k_bwd_f32(Work w) {
         if (tid < GPN) gp[tid] = 0.0;
         return;
     }
-    const int i = cb * BCOLS + tid;
-    const bool ok = i < T.N;
+    const int i = cb * BCOLS + tid;   // column (of quenching group grp, grid point ig)
+    const int grp = MULTI ? i / T.Ncs : 0, ig = MULTI ? i - grp * T.Ncs : i;
+    const bool ok = MULTI ? (i < T.Next && ig < T.N) : i < T.N;
     const int2 rr = w.cb_rows[(size_t)item * MAX_CB + cb];
+    if (MULTI && rr.x >= rr.y) {   // no column of this block has support in its quenching group
+        if (tid < GPN) gp[tid] = 0.0;
+        return;
+    }
     const int r0 = max(rr.x, max(0, T.m_lo - T.L + 1)), r1 = min(rr.y, T.M);
     __shared__ float s_coef[3][KMAX];   // vetoed, tagged and window coefficients per species
     __shared__ float s_c[2][KMAX];      // c_{vetoed,k}, c_{tagged,k}
@@ -183,7 +204,8 @@ __global__ void __launch_bounds__(BCOLS, 7) k_bwd_f32(Work w) {
     float Ssub = 0.f, Stag = 0.f, SA = 0.f;
     if (ok)
         for (int k = 0; k < T.K; ++k) {
-            const float sk = T.shapes32[(size_t)k * T.N + i];
+            if (!in_group<MULTI>(T, k, grp)) continue;
+            const float sk = T.shapes32[(size_t)k * T.N + ig];
             Ssub = fmaf(s_coef[0][k], sk, Ssub);
             Stag = fmaf(s_coef[1][k], sk, Stag);
             SA = fmaf(s_coef[2][k], sk, SA);
@@ -270,7 +292,7 @@ __global__ void __launch_bounds__(BCOLS, 7) k_bwd_f32(Work w) {
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
         if (k < T.K && rates) {
-            const float sk = ok ? T.shapes32[(size_t)k * T.N + i] : 0.f;
+            const float sk = (ok && in_group<MULTI>(T, k, grp)) ? T.shapes32[(size_t)k * T.N + ig] : 0.f;
             const float v = warp_sum(sk * fmaf(s_c[0][k], rho_s, s_c[1][k] * rho_t));
             if (lane == 0) red[wid * GPN + 5 + k] = (double)v;
         } else if (lane == 0) {
@@ -287,8 +309,13 @@ __global__ void __launch_bounds__(BCOLS, 7) k_bwd_f32(Work w) {
 
 cudaError_t launch_bwd(const Work& w, int n, int max_cb, cudaStream_t s) {
     const unsigned grid = (unsigned)n * (unsigned)w.max_cb;   // decoded with w.max_cb
-    if (w.precision == BX_FP64) k_bwd_f64<<<grid, BCOLS, 0, s>>>(w);
-    else k_bwd_f32<<<grid, BCOLS, 0, s>>>(w);
+    if (w.precision == BX_FP64) {
+        if (w.multi_set) k_bwd_f64<true><<<grid, BCOLS, 0, s>>>(w);
+        else k_bwd_f64<false><<<grid, BCOLS, 0, s>>>(w);
+    } else {
+        if (w.multi_set) k_bwd_f32<true><<<grid, BCOLS, 0, s>>>(w);
+        else k_bwd_f32<false><<<grid, BCOLS, 0, s>>>(w);
+    }
     return cudaGetLastError();
 }
 

@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(F32_THREADS) k_fwd_f32(Work w) {
     const Toy& T = w.toys[w.toy_of[item]];
     if (tile >= T.n_tiles || w.status[item]) return;
     const int m0 = tile * TM, M = T.M;
-    const int2 cr = w.tile_cols[(size_t)item * MAX_TILES + tile];
+    const int NGRP = T.n_set > 1 ? T.n_set : 1;   // quenching groups: one column range each
     const size_t cbase = (size_t)item * w.Npad;
     const float4* colf = w.colf + cbase;
     const ColG* colg = w.colg + cbase;
@@ -64,6 +64,8 @@ __global__ void __launch_bounds__(F32_THREADS) k_fwd_f32(Work w) {
     float sa = 0.f, csa = 0.f, ta = 0.f, cta = 0.f, sb = 0.f, csb = 0.f, tb = 0.f, ctb = 0.f;
     float* apart = static_cast<float*>(w.apart) + (((size_t)item * w.max_tiles + tile) * 2 + q) * w.Npad;
 
+    for (int grp = 0; grp < NGRP; ++grp) {
+    const int2 cr = tile_range(w, item, grp, tile);
     for (int c0 = cr.x; c0 < cr.y; c0 += FCH32) {
         const int ncol = min(FCH32, cr.y - c0);
         {
@@ -120,6 +122,7 @@ __global__ void __launch_bounds__(F32_THREADS) k_fwd_f32(Work w) {
             if (lane < ncol) apart[c0 + lane] = s * sG[q][lane].A;
             __syncwarp();
         }
+    }
     }
     double* lam = w.lam + (size_t)item * 2 * w.Mpad;
     if (w.lam_pairs) {   // the Kahan sum s - c as a normalised FP32 pair

@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(TM) k_fwd_f64(Work w) {
     const Toy& T = w.toys[w.toy_of[item]];
     if (tile >= T.n_tiles || w.status[item]) return;
     const int m0 = tile * TM, M = T.M;
-    const int2 cr = w.tile_cols[(size_t)item * MAX_TILES + tile];
+    const int NGRP = T.n_set > 1 ? T.n_set : 1;   // quenching groups: one column range each
     const size_t cbase = (size_t)item * w.Npad;
 
     // tails, column-major so that thread = edge reads consecutive words
@@ -37,6 +37,8 @@ __global__ void __launch_bounds__(TM) k_fwd_f64(Work w) {
     double ls = 0.0, lt = 0.0;
     double* apart = static_cast<double*>(w.apart) + ((size_t)item * w.max_tiles + tile) * w.Npad;
 
+    for (int grp = 0; grp < NGRP; ++grp) {
+    const int2 cr = tile_range(w, item, grp, tile);
     for (int c0 = cr.x; c0 < cr.y; c0 += FCH64) {
         for (int j = tid; j < FCH64 * (TM + 1); j += TM) {
             const int c = j / (TM + 1), e = j % (TM + 1), i = c0 + c;
@@ -84,6 +86,7 @@ __global__ void __launch_bounds__(TM) k_fwd_f64(Work w) {
             if (part == 0 && c < ncol) apart[c0 + c] = s;
         }
         __syncthreads();
+    }
     }
     if (m < M) {
         double* lam = w.lam + (size_t)item * 2 * w.Mpad;

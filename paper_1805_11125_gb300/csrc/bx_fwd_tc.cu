@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_fwd_tc(Work w) {
     const Toy& T = w.toys[w.toy_of[item]];
     if (tile >= T.n_tiles || w.status[item]) return;
     const int m0 = tile * TM, r = tid & (TM - 1), h = tid >> 7, warp = tid >> 5;
-    const int2 cr = w.tile_cols[(size_t)item * MAX_TILES + tile];
+    const int2 cr = tile_range(w, item, 0, tile);   // one quenching group
     const int kb0 = cr.x < cr.y ? cr.x / KB : 0;
     const int nblk = cr.x < cr.y ? (cr.y - 1) / KB + 1 - kb0 : 0;
     const float4* colf = w.colf + (size_t)item * w.Npad;

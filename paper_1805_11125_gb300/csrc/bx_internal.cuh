@@ -57,9 +57,17 @@ struct __align__(16) ColG {
 };
 
 // Device description of one toy (dataset + its fixed model inputs).
+constexpr int MAX_SETS = 4;   // groups of species-specific quenching
+
 struct Toy {
     int K, N, M, m_lo, nw, L, n_rad, n_psd, has_tag, nb, P;
     int n_tiles, n_cb, n_kb;
+    // species-specific quenching: group c of species (Birks multiplier xi[c]) owns the response
+    // columns [c Ncs, c Ncs + N); Next = (n_set - 1) Ncs + N columns in use (n_set = 1: Ncs =
+    // Next = N, the plain model)
+    int n_set, Ncs, Next;
+    int set_of[KMAX];
+    double xi[MAX_SETS];
     double dE, w, r_fid, r_iv, att_len;
     const double* shapes;     // [K][N]
     const float* shapes32;    // [K][N]
@@ -109,9 +117,11 @@ struct Work {
     int2* colr;               // [cap][Npad]: band rows [r0, r1) of each column (empty: r0 >= r1)
     double* lam;              // [cap][2][Mpad]: lambda_h[m] (rate-first forward); FP32 pairs when lam_pairs
     int lam_pairs;            // rate-first mixed precision: the forward writes lam as FP32 pairs
+    int multi_set;            // some toy has several quenching groups (selects the kernels that handle them)
     void* apart;              // [cap][max_tiles][H][Npad]: column sums of R Gg per tile, FP64 (H = 1)
                               // or per half tile (one warp's 64 rows), FP32 (H = 2)
-    int2* tile_cols;          // [cap][MAX_TILES]: column range of each forward tile
+    int2* tile_cols;          // [cap][MAX_SETS][MAX_TILES]: column range of each forward tile, per
+                              // quenching group (tile_range); only the toy's groups are written
     int2* cb_rows;            // [cap][MAX_CB]: row range of each backward column block
     void* v;                  // [cap][Mpad][US] float (TF32X3) or double (FP64)
     void* rowW;               // [cap][3][Mpad] float or double: wt_sub, wt_tag, G_W
@@ -136,6 +146,14 @@ struct Work {
     double* gpart2d;          // [cap][MAX_CB][GPN + 1]: response, rate and s_r partials
     int tr_kb, row_kb, win_kb, win_tiles, Lmax;
 };
+
+#ifdef __CUDACC__
+// Column range [x, y) of forward tile t of an item's quenching group grp.
+__device__ __forceinline__ int2 tile_range(const Work& w, int item, int grp, int t) {
+    return w.tile_cols[((size_t)item * MAX_SETS + grp) * MAX_TILES + t];
+}
+#endif
+
 
 constexpr int STATUS_SKIPPED = 1;   // item status of a skipped evaluation
 

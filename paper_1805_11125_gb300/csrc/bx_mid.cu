@@ -204,24 +204,28 @@ __global__ void __launch_bounds__(MID_THREADS, (sizeof(TV) == sizeof(float) && !
         } else {
             // sum_m v_k[m] G_W[m] = sum_i s_k[i] ((1 - eps) aW[i] + eps a[i]), a[i] from the
             // per-tile column sums of the forward (valid on each tile's band only)
-            const int2* tcols = w.tile_cols + (size_t)item * MAX_TILES;
             constexpr int HALF = sizeof(TV) == sizeof(float) ? 2 : 1;   // slots per tile
             const TV* ap = static_cast<const TV*>(w.apart) + (size_t)item * w.max_tiles * HALF * w.Npad;
             const double* aWi = w.aW + (size_t)item * w.Npad;
             const int lane = tid & 31, wid = tid >> 5;
             {   // FP64 model (the rate-first FP32 mode runs k_mid32)
-                for (int i = tid; i < T.N; i += MID_THREADS) {
+                // column ie = grp Ncs + i of quenching group grp carries the species of that group
+                const int NS = T.n_set > 1 ? T.n_set : 1;
+                for (int ie = tid; ie < T.Next; ie += MID_THREADS) {
+                    const int grp = ie / T.Ncs, i = ie - grp * T.Ncs;
+                    if (i >= T.N) continue;
+                    const int2* tcols = w.tile_cols + ((size_t)item * MAX_SETS + grp) * MAX_TILES;
                     double ag = 0.0;
                     for (int t = 0; t < T.n_tiles; ++t) {
                         const int2 cr = tcols[t];
-                        if (i >= cr.x && i < cr.y)
-                            for (int h = 0; h < HALF; ++h) ag += (double)ap[((size_t)t * HALF + h) * w.Npad + i];
+                        if (ie >= cr.x && ie < cr.y)
+                            for (int h = 0; h < HALF; ++h) ag += (double)ap[((size_t)t * HALF + h) * w.Npad + ie];
                     }
-                    const double aw = aWi[i];
+                    const double aw = aWi[ie];
                     const double GW = (1.0 - eps) * aw + eps * ag, dG = ag - aw;
 #pragma unroll
                     for (int k = 0; k < KMAX; ++k)
-                        if (k < K) {
+                        if (k < K && (NS == 1 || T.set_of[k] == grp)) {
                             const double x = T.shapes[(size_t)k * T.N + i];
                             part[k] += x * GW;
                             part[KMAX + k] += x * dG;
@@ -551,8 +555,8 @@ __global__ void __launch_bounds__(MID_THREADS, 2) k_mid32(Work w, int want_grad,
     float* lamP = gT + gn;                                  // [H][lrow] FP32 lambda, zero-padded
     float* puT = lamP + 2 * lrow;                           // [H][nw] pile-up convolution part
     float* wvP = puT + 2 * nw;                              // [H][wrow] 1 - n/mu, zero-padded
-    float2* colGW = reinterpret_cast<float2*>(wvP + 2 * wrow);   // [N] G_W per column (8-byte aligned)
-    float* coldG = reinterpret_cast<float*>(colGW + T.N);        // [N] dG_W/deps per column
+    float2* colGW = reinterpret_cast<float2*>(wvP + 2 * wrow);   // [Next] G_W per column (8-byte aligned)
+    float* coldG = reinterpret_cast<float*>(colGW + T.Next);     // [Next] dG_W/deps per column
 
     __shared__ double s_rs[KMAX], s_rt[KMAX], s_SA[2 * KMAX], s_beta[KMAX];
     __shared__ double s_pint[MAX_RAD], s_pext[MAX_RAD], s_dpext[MAX_RAD], s_mur[MAX_RAD], s_wr[MAX_RAD];
@@ -603,10 +607,10 @@ __global__ void __launch_bounds__(MID_THREADS, 2) k_mid32(Work w, int want_grad,
     // and the result is the exact sum to a few 1e-15 of its size.
     const bool mv = nrad > 0 || npsd > 0;
     if (mv) {
-        const int2* tcols = w.tile_cols + (size_t)item * MAX_TILES;
         const float* ap = static_cast<const float*>(w.apart) + (size_t)item * w.max_tiles * 2 * w.Npad;
         const float2* aW2 = reinterpret_cast<const float2*>(w.aW + (size_t)item * w.Npad);
-        for (int i = tid; i < T.N; i += MID_THREADS) {
+        for (int i = tid; i < T.Next; i += MID_THREADS) {   // every column of every quenching group
+            const int2* tcols = w.tile_cols + ((size_t)item * MAX_SETS + (T.n_set > 1 ? i / T.Ncs : 0)) * MAX_TILES;
             float agf = 0.f;   // a few positive terms; enters G_W with weight eps
             for (int t = 0; t < T.n_tiles; ++t) {
                 const int2 cr = tcols[t];
@@ -624,11 +628,12 @@ __global__ void __launch_bounds__(MID_THREADS, 2) k_mid32(Work w, int want_grad,
         for (int k = wid; k < K; k += MID_WARPS) {
             Sum32 a0, a1;
             const float* sk = T.shapes32 + (size_t)k * T.N;
+            const int off = T.n_set > 1 ? T.set_of[k] * T.Ncs : 0;   // the columns of k's quenching group
             for (int i = lane; i < T.N; i += 32) {
                 const float x = sk[i];
-                const float2 g2 = colGW[i];
+                const float2 g2 = colGW[off + i];
                 a0.add_prod(x, g2.x, g2.y);
-                a1.add_prod(x, coldG[i], 0.f);
+                a1.add_prod(x, coldG[off + i], 0.f);
             }
             a0 = a0.warp_reduce();
             a1 = a1.warp_reduce();

@@ -100,6 +100,10 @@ extern "C" int bx_spectra_noalloc(int n_grid, double e_max, int n_species, const
     Toy T{};
     T.K = n_species;
     T.N = n_grid;
+    T.n_set = 1;
+    T.Ncs = T.Next = n_grid;
+    T.set_of[0] = 0;
+    T.xi[0] = 1.0;
     T.M = m_hi;
     T.m_lo = 0;
     T.nw = m_hi;

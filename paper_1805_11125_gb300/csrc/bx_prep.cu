@@ -114,6 +114,7 @@ __device__ void block_scan2(double& a, double& b, double& ta, double& tb, double
 // mass (erfc only for window edges within 9 sigma), the rate-weighted spectra
 // S_h[i] = sum_k r_k c_{h,k} s_k[i]; FP32 only for the response band (a work bound, not a
 // result).  The FP64 generator works from mu and sigma.
+template <bool MULTI>
 __global__ void __launch_bounds__(256) k_prep(Work w) {
     const int item = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
     if (w.skip && w.skip[item]) {   // uniform for the block: no barrier is skipped unevenly
@@ -125,9 +126,12 @@ __global__ void __launch_bounds__(256) k_prep(Work w) {
     const double* th = w.theta + (size_t)item * w.tstride;
     __shared__ double sh[32];
     __shared__ int s_bad;
-    __shared__ int s_tlo[MAX_TILES], s_thi[MAX_TILES], s_rlo[MAX_CB], s_rhi[MAX_CB];
+    __shared__ int s_tlo[MAX_SETS][MAX_TILES], s_thi[MAX_SETS][MAX_TILES], s_rlo[MAX_CB], s_rhi[MAX_CB];
     if (tid == 0) s_bad = 0;
-    for (int j = tid; j < MAX_TILES; j += blockDim.x) { s_tlo[j] = INT_MAX; s_thi[j] = INT_MIN; }
+    for (int j = tid; j < MAX_SETS * MAX_TILES; j += blockDim.x) {
+        s_tlo[j / MAX_TILES][j % MAX_TILES] = INT_MAX;
+        s_thi[j / MAX_TILES][j % MAX_TILES] = INT_MIN;
+    }
     for (int j = tid; j < MAX_CB; j += blockDim.x) { s_rlo[j] = INT_MAX; s_rhi[j] = INT_MIN; }
     __syncthreads();
     if (tid < T.P && !isfinite(th[tid])) s_bad = 1;
@@ -145,26 +149,46 @@ __global__ void __launch_bounds__(256) k_prep(Work w) {
     int2* cr = w.colr + (size_t)item * w.Npad;
     int bad = 0;
     unsigned long long inband = 0;
+    // species-specific quenching: one pass per group grp of species, with Birks constant
+    // kB xi[grp], into the group's columns [grp Ncs, grp Ncs + N)
+    const int NS = MULTI ? T.n_set : 1;
+    for (int grp = 0; grp < NS; ++grp) {
+    const int off = grp * T.Ncs;
+    const double xi = MULTI ? T.xi[grp] : 1.0, kBc = kB * xi;
     double carry_x = 0.0, carry_y = 0.0;
     for (int c0 = 0; c0 < N; c0 += 256) {
-        const int i = c0 + tid;
+        const int i = c0 + tid, ie = off + i;
         const bool in = i < N;
         // a1: Q_i = sum_{j<i} x_j + x_i / 2, x_j = dE / (1 + kB S_j); dQ_i/dkB likewise
         double x = 0.0, y = 0.0;
         if (in) {
-            const double S = T.stop_pow[i], q = 1.0 + kB * S;
+            const double S = T.stop_pow[i], q = 1.0 + kBc * S;
             if (!(q > 0.0)) bad = 1;
             const double rq = 1.0 / q;
             x = T.dE * rq;
-            y = -x * S * rq;
+            y = -x * S * rq * xi;   // dx / dkB
         }
         double ex = x, ey = y, tx, ty;
         block_scan2(ex, ey, tx, ty, sh);
         int r0 = 0, r1 = 0;
         bool valid = false;
-        if (in) {
+        bool live = in;
+        if (MULTI && in) {   // a group's column without support: only the scan above is needed
+            bool nz = false;
+            for (int k = 0; k < K; ++k)
+                if (T.set_of[k] == grp) nz |= T.shapes[(size_t)k * N + i] != 0.0;
+            if (!nz) {
+                live = false;
+                col[ie] = Col64{0.0, 1.0, 0.0, 0.0};
+                cq[ie] = make_double2(0.0, 0.0);
+                cs[ie] = make_double2(0.0, 0.0);
+                aW[ie] = 0.0;
+                cr[ie] = make_int2(0, 0);
+            }
+        }
+        if (live) {
             const double Q = carry_x + ex + 0.5 * x, dQ = carry_y + ey + 0.5 * y;
-            cq[i] = make_double2(Q, dQ);
+            cq[ie] = make_double2(Q, dQ);
             const double mu = LY * Q;
             const double var = fma(fma(b, mu, a), mu, c);
             const bool ok = var > 0.0;
@@ -178,27 +202,30 @@ __global__ void __launch_bounds__(256) k_prep(Work w) {
                 norm = 1.0 / Phi;
                 mills = INV_SQRT_2PI * exp(-0.5 * z * z) * norm;
             }
-            col[i] = Col64{mu, sig, norm, mills};
+            col[ie] = Col64{mu, sig, norm, mills};
             // rate-weighted spectra of the vetoed (or single) and tagged events (Eq. 3)
             double ssub = 0.0, stag = 0.0;
+            bool nz = false;   // a species of this group has support in the column
             for (int k = 0; k < K; ++k) {
+                if (MULTI && T.set_of[k] != grp) continue;
+                nz |= T.shapes[(size_t)k * N + i] != 0.0;
                 const double sk = T.shapes[(size_t)k * N + i] * th[k];
                 const double t = T.tag ? T.tag[k] : 0.0;
                 ssub += (T.tag ? 1.0 - t : 1.0) * sk;
                 stag += t * sk;
             }
-            cs[i] = make_double2(ssub, stag);
+            cs[ie] = make_double2(ssub, stag);
             // window mass of the column (Eq. 4 marginals)
-            aW[i] = gauss_mass((z_lo - mu) * isig, (z_hi - mu) * isig) * norm;
+            aW[ie] = gauss_mass((z_lo - mu) * isig, (z_hi - mu) * isig) * norm;
             // response band: rows whose bin lies within band * sigma of mu
             const float muf = (float)mu, sigf = (float)sig;
             const float lo_e = fminf(fmaxf(muf - bandf * sigf, e_min), e_max);
             const float hi_e = fminf(fmaxf(muf + bandf * sigf, e_min), e_max);
             r0 = max(0, (int)floorf(lo_e * inv_wf));
             r1 = min(M, (int)floorf(hi_e * inv_wf) + 1);
-            valid = ok && r0 < r1;
+            valid = ok && r0 < r1 && (!MULTI || nz);   // a group's columns without support are skipped
             if (valid) inband += (unsigned long long)(r1 - r0);
-            cr[i] = valid ? make_int2(r0, r1) : make_int2(0, 0);
+            cr[ie] = valid ? make_int2(r0, r1) : make_int2(0, 0);
         }
         carry_x += tx;
         carry_y += ty;
@@ -208,22 +235,26 @@ __global__ void __launch_bounds__(256) k_prep(Work w) {
         const int tmin = __reduce_min_sync(full, t0), tmax = __reduce_max_sync(full, t1);
         for (int t = tmin; t <= tmax; ++t) {
             const bool touch = valid && t >= t0 && t <= t1;
-            const int lo = __reduce_min_sync(full, touch ? i : INT_MAX);
-            const int hi = __reduce_max_sync(full, touch ? i + 1 : INT_MIN);
+            const int lo = __reduce_min_sync(full, touch ? ie : INT_MAX);
+            const int hi = __reduce_max_sync(full, touch ? ie + 1 : INT_MIN);
             if (lane == 0 && lo != INT_MAX) {
-                atomicMin(&s_tlo[t], lo);
-                atomicMax(&s_thi[t], hi);
+                atomicMin(&s_tlo[grp][t], lo);
+                atomicMax(&s_thi[grp][t], hi);
             }
         }
         // a warp's 32 columns lie in one column block (BCOLS is a multiple of 32)
         const int rlo = __reduce_min_sync(full, valid ? r0 : INT_MAX);
         const int rhi = __reduce_max_sync(full, valid ? r1 : INT_MIN);
-        if (lane == 0 && rlo != INT_MAX) {
-            atomicMin(&s_rlo[(c0 + tid) / BCOLS], rlo);
-            atomicMax(&s_rhi[(c0 + tid) / BCOLS], rhi);
+        if (lane == 0 && rlo != INT_MAX) {   // off: a multiple of BCOLS
+            atomicMin(&s_rlo[ie / BCOLS], rlo);
+            atomicMax(&s_rhi[ie / BCOLS], rhi);
         }
     }
-    for (int i = N + tid; i < w.Npad; i += blockDim.x) {
+    }
+    // padding: the columns between groups and after the last one
+    for (int i = tid; i < w.Npad; i += blockDim.x) {
+        const int cpad = i / T.Ncs;
+        if (cpad < NS && i - cpad * T.Ncs < N) continue;
         col[i] = Col64{0.0, 1.0, 0.0, 0.0};
         cq[i] = make_double2(0.0, 0.0);
         cs[i] = make_double2(0.0, 0.0);
@@ -233,8 +264,9 @@ __global__ void __launch_bounds__(256) k_prep(Work w) {
     if (bad) s_bad = 1;
     if (w.count_units && inband) atomicAdd(w.units, inband);
     __syncthreads();
-    for (int t = tid; t < MAX_TILES; t += blockDim.x)
-        w.tile_cols[(size_t)item * MAX_TILES + t] = make_int2(s_tlo[t], s_thi[t]);
+    for (int j = tid; j < NS * MAX_TILES; j += blockDim.x)
+        w.tile_cols[(size_t)item * MAX_SETS * MAX_TILES + j] = make_int2(s_tlo[j / MAX_TILES][j % MAX_TILES],
+                                                                         s_thi[j / MAX_TILES][j % MAX_TILES]);
     for (int j = tid; j < MAX_CB; j += blockDim.x)
         w.cb_rows[(size_t)item * MAX_CB + j] = make_int2(s_rlo[j], s_rhi[j]);
     if (tid == 0) w.status[item] = s_bad ? (int)BX_EDOMAIN : 0;
@@ -303,7 +335,8 @@ __device__ void block_scan_df(df& a, df& b, df& ta, df& tb, float* sh) {
 // Z_F32 = 3 sigma (1/Phi, phi/Phi; FP32 tails beyond) and for the FP64 copies of mu, sigma, Q,
 // dQ/dkB that the adjoint's chain rule reads (formed on the integer pipe, f2d).  The window
 // masses come from FP32 tails and go out as FP32 pairs.
-__global__ void __launch_bounds__(256) k_prep32(Work w) {
+template <bool MULTI>
+__global__ void __launch_bounds__(256, 3) k_prep32(Work w) {
     const int item = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
     if (w.skip && w.skip[item]) {
         if (tid == 0) w.status[item] = STATUS_SKIPPED;
@@ -314,11 +347,14 @@ __global__ void __launch_bounds__(256) k_prep32(Work w) {
     const double* th = w.theta + (size_t)item * w.tstride;
     __shared__ float sh[72];
     __shared__ int s_bad;
-    __shared__ int s_tlo[MAX_TILES], s_thi[MAX_TILES], s_rlo[MAX_CB], s_rhi[MAX_CB];
+    __shared__ int s_tlo[MAX_SETS][MAX_TILES], s_thi[MAX_SETS][MAX_TILES], s_rlo[MAX_CB], s_rhi[MAX_CB];
     __shared__ float s_rate[4][KMAX];
     __shared__ df s_par[11];   // LY, a, b, c, kB, dE, w S_EX2, 1/w, A's constant factor, window edges
     if (tid == 0) s_bad = 0;
-    for (int j = tid; j < MAX_TILES; j += blockDim.x) { s_tlo[j] = INT_MAX; s_thi[j] = INT_MIN; }
+    for (int j = tid; j < MAX_SETS * MAX_TILES; j += blockDim.x) {
+        s_tlo[j / MAX_TILES][j % MAX_TILES] = INT_MAX;
+        s_thi[j / MAX_TILES][j % MAX_TILES] = INT_MIN;
+    }
     for (int j = tid; j < MAX_CB; j += blockDim.x) { s_rlo[j] = INT_MAX; s_rhi[j] = INT_MIN; }
     if (tid < KMAX) {
         double rs = 0.0, rt = 0.0;
@@ -362,9 +398,16 @@ __global__ void __launch_bounds__(256) k_prep32(Work w) {
     const df ln4{1.3862944f, (float)(1.3862943611198906 - (double)1.3862944f)};      // 2 ln 2
     int bad = 0;
     unsigned long long inband = 0;
+    // species-specific quenching: one pass per group grp of species, with Birks constant
+    // kB xi[grp], into the group's columns [grp Ncs, grp Ncs + N)
+    const int NS = MULTI ? T.n_set : 1;
+    for (int grp = 0; grp < NS; ++grp) {
+    const int off = grp * T.Ncs;
+    const df xid = MULTI ? df_from(T.xi[grp]) : df{1.f, 0.f};
+    const df kBc = MULTI ? df_mul(kB, xid) : kB;
     df carry_x{0.f, 0.f}, carry_y{0.f, 0.f};
     for (int c0 = 0; c0 < N; c0 += 256) {
-        const int i = c0 + tid;
+        const int i = c0 + tid, ie = off + i;
         const bool in = i < N;
         df S{0.f, 0.f}, x{0.f, 0.f}, y{0.f, 0.f};
         if (in) {
@@ -374,20 +417,37 @@ __global__ void __launch_bounds__(256) k_prep32(Work w) {
             } else {
                 S = df_from(T.stop_pow[i]);
             }
-            const df q = df_addf(df_mul(kB, S), 1.0f);
+            const df q = df_addf(df_mul(kBc, S), 1.0f);
             if (!(q.h > 0.f)) bad = 1;
             const df rq = df_recip(q);
             x = df_mul(dE, rq);
-            y = df_neg(df_mul(df_mul(x, S), rq));
+            y = df_neg(df_mul(df_mul(x, S), rq));   // dx / d(kB xi)
+            if (MULTI) y = df_mul(y, xid);            // dx / dkB
         }
         df ex = x, ey = y, tx, ty;
         block_scan_df(ex, ey, tx, ty, sh);
         int r0 = 0, r1 = 0;
         bool valid = false;
-        if (in) {
+        bool live = in;
+        if (MULTI && in) {   // a group's column without support: only the scan above is needed
+            bool nz = false;
+            for (int k = 0; k < K; ++k)
+                if (T.set_of[k] == grp) nz |= T.shapes[(size_t)k * N + i] != 0.0;
+            if (!nz) {
+                live = false;
+                col[ie] = Col64{0.0, 1.0, 0.0, 0.0};
+                cq[ie] = make_double2(0.0, 0.0);
+                cf[ie] = make_float4(0.f, 0.f, 0.f, 0.f);
+                cg[ie] = ColG{0.f, 0.f, 0.f, 0.f};
+                cs32[ie] = make_float2(0.f, 0.f);
+                aW2[ie] = make_float2(0.f, 0.f);
+                cr[ie] = make_int2(0, 0);
+            }
+        }
+        if (live) {
             const df Q = df_add(df_add(carry_x, ex), df{0.5f * x.h, 0.5f * x.l});
             const df dQ = df_add(df_add(carry_y, ey), df{0.5f * y.h, 0.5f * y.l});
-            cq[i] = make_double2(df_to_double(Q), df_to_double(dQ));
+            cq[ie] = make_double2(df_to_double(Q), df_to_double(dQ));
             const df mu = df_mul(LY, Q);
             const df var = df_add(df_mul(df_add(df_mul(pb, mu), pa), mu), pc);
             const bool ok = var.h > 0.f;
@@ -410,7 +470,7 @@ __global__ void __launch_bounds__(256) k_prep32(Work w) {
                 norm = df_to_double(normd);
                 mills = f2d(INV_SQRT_2PI_F * exp2f(-0.72134752f * df_mul(z, z).h) * (1.0f + qn));
             }
-            col[i] = Col64{mud, sigd, norm, mills};
+            col[ie] = Col64{mud, sigd, norm, mills};
             // generator constants: t0 = (m + 1/2 - mu/w) hs = (m - jf) hs + c
             const df u = df_mul(mu, iw);
             float jf = floorf(u.h);
@@ -418,29 +478,34 @@ __global__ void __launch_bounds__(256) k_prep32(Work w) {
             const df frac = df_addf(u, -jf);
             const df hs = df_mul(wS, isig);
             const df cc = df_mul(df_addf(df_neg(frac), 0.5f), hs);
-            cf[i] = make_float4(jf, cc.h, hs.h, hs.l);
+            cf[ie] = make_float4(jf, cc.h, hs.h, hs.l);
             const df kk = df_mul(gln, hs), kq = df_mul(kk, kk);
             const df Ad = df_mul(df_mul(cAw, isig), normd);
-            cg[i] = ColG{df_mul(ln4, kk).h, 2.0f * exp2_neg(-kq.h, -kq.l), cc.l, Ad.h};
+            cg[ie] = ColG{df_mul(ln4, kk).h, 2.0f * exp2_neg(-kq.h, -kq.l), cc.l, Ad.h};
             // rate-weighted spectra of the vetoed (or single) and tagged events (Eq. 3), times the
             // column amplitude A (the FP32 forward generates R / A)
+            bool nz = false;   // a species of this group has support in the column
             if (T.shapes32) {
                 float ss = 0.f, st = 0.f;
                 for (int k = 0; k < K; ++k) {
+                    if (MULTI && T.set_of[k] != grp) continue;
                     const float sk = T.shapes32[(size_t)k * N + i];
+                    nz |= sk != 0.f;
                     ss = fmaf(s_rate[0][k], sk, fmaf(s_rate[1][k], sk, ss));
                     st = fmaf(s_rate[2][k], sk, fmaf(s_rate[3][k], sk, st));
                 }
-                cs32[i] = make_float2(df_mulf(Ad, ss).h, df_mulf(Ad, st).h);
+                cs32[ie] = make_float2(df_mulf(Ad, ss).h, df_mulf(Ad, st).h);
             } else {   // a descriptor without FP32 shapes
                 double ssub = 0.0, stag = 0.0;
                 for (int k = 0; k < K; ++k) {
+                    if (MULTI && T.set_of[k] != grp) continue;
+                    nz |= T.shapes[(size_t)k * N + i] != 0.0;
                     const double sk = T.shapes[(size_t)k * N + i] * th[k];
                     const double t = T.tag ? T.tag[k] : 0.0;
                     ssub += (T.tag ? 1.0 - t : 1.0) * sk;
                     stag += t * sk;
                 }
-                cs32[i] = make_float2(df_mul(Ad, df_from(ssub)).h, df_mul(Ad, df_from(stag)).h);
+                cs32[ie] = make_float2(df_mul(Ad, df_from(ssub)).h, df_mul(Ad, df_from(stag)).h);
             }
             // window mass times 1/Phi, as an FP32 pair, from FP32 tails on the side away from the
             // mean: the masses enter only the Eq. 4 marginals, where an FP32 tail's rounding
@@ -455,15 +520,15 @@ __global__ void __launch_bounds__(256) k_prep32(Work w) {
             else if (zb <= 0.f) mass = df_two_sum(upper_tail32(-zb), -upper_tail32(-za));
             else mass = df_add(df_two_sum(1.0f, -upper_tail32(zb)), df{-upper_tail32(-za), 0.f});
             const df aw = df_mul(mass, normd);
-            aW2[i] = make_float2(aw.h, aw.l);
+            aW2[ie] = make_float2(aw.h, aw.l);
             // response band
             const float lo_e = fminf(fmaxf(mu.h - bandf * sig.h, e_min), e_max);
             const float hi_e = fminf(fmaxf(mu.h + bandf * sig.h, e_min), e_max);
             r0 = max(0, (int)floorf(lo_e * inv_wf));
             r1 = min(M, (int)floorf(hi_e * inv_wf) + 1);
-            valid = ok && r0 < r1;
+            valid = ok && r0 < r1 && (!MULTI || nz);   // a group's columns without support are skipped
             if (valid) inband += (unsigned long long)(r1 - r0);
-            cr[i] = valid ? make_int2(r0, r1) : make_int2(0, 0);
+            cr[ie] = valid ? make_int2(r0, r1) : make_int2(0, 0);
         }
         carry_x = df_add(carry_x, tx);
         carry_y = df_add(carry_y, ty);
@@ -472,21 +537,25 @@ __global__ void __launch_bounds__(256) k_prep32(Work w) {
         const int tmin = __reduce_min_sync(full, t0), tmax = __reduce_max_sync(full, t1);
         for (int t = tmin; t <= tmax; ++t) {
             const bool touch = valid && t >= t0 && t <= t1;
-            const int lo = __reduce_min_sync(full, touch ? i : INT_MAX);
-            const int hi = __reduce_max_sync(full, touch ? i + 1 : INT_MIN);
+            const int lo = __reduce_min_sync(full, touch ? ie : INT_MAX);
+            const int hi = __reduce_max_sync(full, touch ? ie + 1 : INT_MIN);
             if (lane == 0 && lo != INT_MAX) {
-                atomicMin(&s_tlo[t], lo);
-                atomicMax(&s_thi[t], hi);
+                atomicMin(&s_tlo[grp][t], lo);
+                atomicMax(&s_thi[grp][t], hi);
             }
         }
         const int rlo = __reduce_min_sync(full, valid ? r0 : INT_MAX);
         const int rhi = __reduce_max_sync(full, valid ? r1 : INT_MIN);
-        if (lane == 0 && rlo != INT_MAX) {
-            atomicMin(&s_rlo[(c0 + tid) / BCOLS], rlo);
-            atomicMax(&s_rhi[(c0 + tid) / BCOLS], rhi);
+        if (lane == 0 && rlo != INT_MAX) {   // a warp's 32 columns lie in one block (off: a multiple of BCOLS)
+            atomicMin(&s_rlo[ie / BCOLS], rlo);
+            atomicMax(&s_rhi[ie / BCOLS], rhi);
         }
     }
-    for (int i = N + tid; i < w.Npad; i += blockDim.x) {
+    }
+    // padding: the columns between groups and after the last one
+    for (int i = tid; i < w.Npad; i += blockDim.x) {
+        const int cpad = i / T.Ncs;
+        if (cpad < NS && i - cpad * T.Ncs < N) continue;
         col[i] = Col64{0.0, 1.0, 0.0, 0.0};
         cq[i] = make_double2(0.0, 0.0);
         cf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -498,16 +567,22 @@ __global__ void __launch_bounds__(256) k_prep32(Work w) {
     if (bad) s_bad = 1;
     if (w.count_units && inband) atomicAdd(w.units, inband);
     __syncthreads();
-    for (int t = tid; t < MAX_TILES; t += blockDim.x)
-        w.tile_cols[(size_t)item * MAX_TILES + t] = make_int2(s_tlo[t], s_thi[t]);
+    for (int j = tid; j < NS * MAX_TILES; j += blockDim.x)
+        w.tile_cols[(size_t)item * MAX_SETS * MAX_TILES + j] = make_int2(s_tlo[j / MAX_TILES][j % MAX_TILES],
+                                                                         s_thi[j / MAX_TILES][j % MAX_TILES]);
     for (int j = tid; j < MAX_CB; j += blockDim.x)
         w.cb_rows[(size_t)item * MAX_CB + j] = make_int2(s_rlo[j], s_rhi[j]);
     if (tid == 0) w.status[item] = s_bad ? (int)BX_EDOMAIN : 0;
 }
 
 cudaError_t launch_prep(const Work& w, int n, cudaStream_t s) {
-    if (w.precision == BX_FP64) k_prep<<<n, 256, 0, s>>>(w);
-    else k_prep32<<<n, 256, 0, s>>>(w);
+    if (w.precision == BX_FP64) {
+        if (w.multi_set) k_prep<true><<<n, 256, 0, s>>>(w);
+        else k_prep<false><<<n, 256, 0, s>>>(w);
+    } else {
+        if (w.multi_set) k_prep32<true><<<n, 256, 0, s>>>(w);
+        else k_prep32<false><<<n, 256, 0, s>>>(w);
+    }
     return cudaGetLastError();
 }
 

@@ -327,6 +327,7 @@ def quenched(alpha_true: float = 2.3, alpha_quench: float = 150.0, gamma_quench:
     if "alpha" in names:
         ia = names.index("alpha")
         a = alpha_peak(E, mu=alpha_true, sig=0.03)
+        a[a < 1e-12 * a.max()] = 0.0   # the peak's support: +-7.4 sigma
         spec.shapes[ia] = a / a.sum()
         q[ia] = alpha_quench
     if gamma_quench is not None:

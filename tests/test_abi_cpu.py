@@ -115,3 +115,29 @@ def test_2d_model_rejections_on_host():
     with pytest.raises(bx.BxError) as e:
         bx.Model(both, precision=bx.BX_FP32)
     assert e.value.status == bx.BX_EINVAL
+
+
+def test_quenching_group_rejections_on_host():
+    """Species-specific quenching: multipliers finite and >= 0, at most four groups, and more
+    than one group only with BX_FP32 / BX_FP64 and without 2D histograms (all checked before
+    any device is touched)."""
+    import dataclasses
+    s = I.config("small_quenched")
+    s = s.with_counts(np.ones(s.n_bins_total))
+    with pytest.raises(bx.BxError) as e:
+        bx.Model(s, precision=bx.BX_TF32X3)
+    assert e.value.status == bx.BX_EINVAL and "quenching" in str(e.value)
+    neg = dataclasses.replace(s, quench=np.where(np.arange(s.K) == 1, -1.0, 1.0))
+    with pytest.raises(bx.BxError) as e:
+        bx.Model(neg, precision=bx.BX_FP32)
+    assert e.value.status == bx.BX_EINVAL and "quench" in str(e.value)
+    five = dataclasses.replace(s, quench=1.0 + np.minimum(np.arange(s.K), 4).astype(float))
+    with pytest.raises(bx.BxError) as e:
+        bx.Model(five, precision=bx.BX_FP32)
+    assert e.value.status == bx.BX_EINVAL and "groups" in str(e.value)
+    s2 = I.config("small_2d")
+    s2 = dataclasses.replace(s2, quench=np.where(np.arange(s2.K) == 0, 2.0, 1.0))
+    s2 = s2.with_counts(np.ones(s2.n_bins_total))
+    with pytest.raises(bx.BxError) as e:
+        bx.Model(s2, precision=bx.BX_FP32)
+    assert e.value.status == bx.BX_EINVAL and "2D" in str(e.value)
