@@ -106,6 +106,11 @@ typedef struct {
     const double* n_p2_counts;         /* [n_p2][m_hi - m_lo] */
     const double* quench;              /* [K] Birks multiplier per species (species k quenches with
                                           kB quench[k]); NULL -> 1 for every species */
+    int n_es; const int* es_edges;     /* energy slices of Eq. 4 (its sums over radial and
+                                          pulse-shape terms): slice s is the window bins
+                                          [es_edges[s], es_edges[s+1]), edges from 0 to m_hi - m_lo;
+                                          n_es = 0 -> one slice, the whole window.  The radial and
+                                          pulse-shape counts are then [n_es][n_rad], [n_es][n_psd] */
 } om_model;
 
 enum { OM_MAX_SETS = 4 };
@@ -134,10 +139,12 @@ enum { OM_OK = 0, OM_EINVAL = -1, OM_ENOMEM = -2, OM_EDOMAIN = -4, OM_ENOTCONV =
 
 int om_n_params(const om_model* m) { return m->K + 7; }
 
+static int n_slices(const om_model* m) { return m->n_es > 0 ? m->n_es : 1; }
+
 int om_n_bins(const om_model* m) {
-    int nw = m->m_hi - m->m_lo;
-    return nw + (m->tag_frac ? nw : 0) + (m->n_rad > 0 && m->rad_class ? m->n_rad : 0) + (m->n_psd > 0 && m->psd_prob ? m->n_psd : 0) +
-           (m->n_r2 + m->n_p2) * nw;
+    int nw = m->m_hi - m->m_lo, S = n_slices(m);
+    return nw + (m->tag_frac ? nw : 0) + S * (m->n_rad > 0 && m->rad_class ? m->n_rad : 0) +
+           S * (m->n_psd > 0 && m->psd_prob ? m->n_psd : 0) + (m->n_r2 + m->n_p2) * nw;
 }
 
 static int check_model(const om_model* m) {
@@ -154,6 +161,12 @@ static int check_model(const om_model* m) {
         int set_of[OPMAX];
         const int n = quench_sets(m, xi, set_of);
         if (n == 0 || (n > 1 && m->n_r2 + m->n_p2 > 0)) return OM_EINVAL;   /* 2D slices: one set only */
+    }
+    if (m->n_es < 0 || (m->n_es > 0 && (!m->es_edges || m->n_r2 + m->n_p2 > 0))) return OM_EINVAL;
+    if (m->n_es > 0) {   /* the slices partition the window */
+        if (m->es_edges[0] != 0 || m->es_edges[m->n_es] != m->m_hi - m->m_lo) return OM_EINVAL;
+        for (int q = 0; q < m->n_es; ++q)
+            if (m->es_edges[q + 1] <= m->es_edges[q]) return OM_EINVAL;
     }
     return OM_OK;
 }
@@ -341,7 +354,7 @@ static int evaluate(const om_model* m, const double* theta, int want_grad,
     int nb = om_n_bins(m);
     dual* mu = calloc(nb, sizeof(dual));
     dual* lam = calloc(M, sizeof(dual));
-    dual* A = calloc(K, sizeof(dual));
+    dual* A = calloc((size_t)K * n_slices(m), sizeof(dual));
     dual* tmp = calloc(nw, sizeof(dual));
     const int B2 = m->n_r2 + m->n_p2;
     dual* Tr = B2 > 0 ? calloc((size_t)N * B2, sizeof(dual)) : NULL;
@@ -377,34 +390,44 @@ static int evaluate(const om_model* m, const double* theta, int want_grad,
         pileup_window(m, eps, lam, 1, mu + o);
         o += nw;
     }
-    /* Eq. 4 terms: window marginal A_k of each TFC-vetoed species spectrum after pile-up */
+    /* Eq. 4 terms, per energy slice s: the marginal A_k^(s) of each TFC-vetoed species
+     * spectrum after pile-up over the slice's window bins, times the species' radial and
+     * pulse-shape bin probabilities (the same in every slice).  Radial histograms of all
+     * slices first (slice-major), then the pulse-shape histograms. */
     int has_rad = m->n_rad > 0 && m->rad_class, has_psd = m->n_psd > 0 && m->psd_prob;
+    const int S = n_slices(m);
     if (has_rad || has_psd) {
         for (int k = 0; k < K; ++k) {
             pileup_window(m, eps, w.v + k, K, tmp);
-            dual s = dc(0.0);
-            for (int j = 0; j < nw; ++j) s = dadd(s, tmp[j]);
             double ck = m->tag_frac ? 1.0 - m->tag_frac[k] : 1.0;
-            A[k] = dscale(dmul(th[k], s), ck);             /* expected vetoed events of k in the window */
+            for (int q = 0; q < S; ++q) {
+                const int j0 = m->n_es > 0 ? m->es_edges[q] : 0, j1 = m->n_es > 0 ? m->es_edges[q + 1] : nw;
+                dual s = dc(0.0);
+                for (int j = j0; j < j1; ++j) s = dadd(s, tmp[j]);
+                A[(size_t)q * K + k] = dscale(dmul(th[k], s), ck);   /* vetoed events of k in slice q */
+            }
         }
     }
     if (has_rad) {
         dual* p = calloc(m->n_rad, sizeof(dual));
-        for (int b = 0; b < m->n_rad; ++b) mu[o + b] = dc(0.0);
+        for (int b = 0; b < S * m->n_rad; ++b) mu[o + b] = dc(0.0);
         for (int k = 0; k < K; ++k) {
             radial_probs(m, s_r, m->rad_class[k], p);
-            for (int b = 0; b < m->n_rad; ++b) mu[o + b] = dadd(mu[o + b], dmul(A[k], p[b]));
+            for (int q = 0; q < S; ++q)
+                for (int b = 0; b < m->n_rad; ++b)
+                    mu[o + q * m->n_rad + b] = dadd(mu[o + q * m->n_rad + b], dmul(A[(size_t)q * K + k], p[b]));
         }
         free(p);
-        o += m->n_rad;
+        o += S * m->n_rad;
     }
     if (has_psd) {
-        for (int b = 0; b < m->n_psd; ++b) {
-            dual s = dc(0.0);
-            for (int k = 0; k < K; ++k) s = dadd(s, dscale(A[k], m->psd_prob[(size_t)k * m->n_psd + b]));
-            mu[o + b] = s;
-        }
-        o += m->n_psd;
+        for (int q = 0; q < S; ++q)
+            for (int b = 0; b < m->n_psd; ++b) {
+                dual s = dc(0.0);
+                for (int k = 0; k < K; ++k) s = dadd(s, dscale(A[(size_t)q * K + k], m->psd_prob[(size_t)k * m->n_psd + b]));
+                mu[o + q * m->n_psd + b] = s;
+            }
+        o += S * m->n_psd;
     }
     /* 2D slices: Eq. 2 on every slice of Y, slice-major */
     for (int b = 0; b < B2; ++b) {
@@ -418,8 +441,8 @@ static int evaluate(const om_model* m, const double* theta, int want_grad,
         const double* cnt[6]; int len[6]; int nh = 0;
         cnt[nh] = m->n_sub; len[nh++] = nw;
         if (m->tag_frac) { cnt[nh] = m->n_tag; len[nh++] = nw; }
-        if (has_rad) { cnt[nh] = m->n_rad_counts; len[nh++] = m->n_rad; }
-        if (has_psd) { cnt[nh] = m->n_psd_counts; len[nh++] = m->n_psd; }
+        if (has_rad) { cnt[nh] = m->n_rad_counts; len[nh++] = S * m->n_rad; }
+        if (has_psd) { cnt[nh] = m->n_psd_counts; len[nh++] = S * m->n_psd; }
         if (m->n_r2 > 0) { cnt[nh] = m->n_r2_counts; len[nh++] = m->n_r2 * nw; }
         if (m->n_p2 > 0) { cnt[nh] = m->n_p2_counts; len[nh++] = m->n_p2 * nw; }
         nsum acc; acc.s = dc(0.0); acc.c = dc(0.0);

@@ -60,6 +60,7 @@ class _Model(C.Structure):
         ("n_r2", C.c_int), ("n_p2", C.c_int), ("field", C.c_void_p), ("amp", C.c_double),
         ("psd2", C.c_void_p), ("n_r2_counts", C.c_void_p), ("n_p2_counts", C.c_void_p),
         ("quench", C.c_void_p),
+        ("n_es", C.c_int), ("es_edges", C.c_void_p),
     ]
 
 
@@ -104,6 +105,7 @@ class OracleModel:
             "field": _arr(s.field2d), "psd2": _arr(s.psd2d_prob),
             "n_r2": _arr(s.counts.get("r2d")), "n_p2": _arr(s.counts.get("p2d")),
             "quench": _arr(getattr(s, "quench", None)),
+            "es_edges": _arr(getattr(s, "eslices", None), np.int32),
         }
         k = self._keep
         has_rad = s.rad_class is not None and s.n_rad > 0
@@ -115,7 +117,8 @@ class OracleModel:
             r_iv=s.r_iv, att_len=s.att_len, n_rad_counts=_ptr(k["n_rad"]),
             n_psd=s.n_psd, psd_prob=_ptr(k["psd_prob"]), n_psd_counts=_ptr(k["n_psd"]),
             n_r2=s.n_rad2d, n_p2=s.n_psd2d, field=_ptr(k["field"]), amp=s.field_amp, psd2=_ptr(k["psd2"]),
-            n_r2_counts=_ptr(k["n_r2"]), n_p2_counts=_ptr(k["n_p2"]), quench=_ptr(k["quench"]))
+            n_r2_counts=_ptr(k["n_r2"]), n_p2_counts=_ptr(k["n_p2"]), quench=_ptr(k["quench"]),
+            n_es=0 if k["es_edges"] is None else len(k["es_edges"]) - 1, es_edges=_ptr(k["es_edges"]))
         self.ref = C.byref(self.c)
 
     @property

@@ -78,6 +78,10 @@ class ModelSpec:
     field_amp: float = 0.0
     # species-specific quenching: species k quenches with kB * quench[k] (None -> 1 for all)
     quench: Optional[np.ndarray] = None
+    # energy slices of Eq. 4's radial and pulse-shape terms: slice s is the window bins
+    # [eslices[s], eslices[s+1]), edges from 0 to n_window (None -> one slice, the window);
+    # the radial and pulse-shape histograms are then one per slice, slice-major
+    eslices: Optional[np.ndarray] = None
     theta_true: Optional[np.ndarray] = None
     species: List[str] = dataclasses.field(default_factory=list)
     counts: Dict[str, np.ndarray] = dataclasses.field(default_factory=dict)
@@ -107,6 +111,10 @@ class ModelSpec:
         return 0 if self.psd2d_prob is None else int(self.psd2d_prob.shape[1])
 
     @property
+    def n_eslices(self) -> int:
+        return 1 if self.eslices is None else len(self.eslices) - 1
+
+    @property
     def n_slices2d(self) -> int:
         return self.n_rad2d + self.n_psd2d
 
@@ -116,9 +124,9 @@ class ModelSpec:
         if self.tag_frac is not None:
             out["tag"] = self.n_window
         if self.rad_class is not None and self.n_rad > 0:
-            out["rad"] = self.n_rad
+            out["rad"] = self.n_eslices * self.n_rad      # slice-major: [energy slice][radial bin]
         if self.psd_prob is not None:
-            out["psd"] = self.n_psd
+            out["psd"] = self.n_eslices * self.n_psd      # slice-major: [energy slice][pulse-shape bin]
         if self.n_rad2d > 0:
             out["r2d"] = self.n_rad2d * self.n_window    # slice-major: [rho][window bin]
         if self.n_psd2d > 0:
@@ -336,6 +344,18 @@ def quenched(alpha_true: float = 2.3, alpha_quench: float = 150.0, gamma_quench:
     return spec
 
 
+def sliced(edges_npe=(100.0, 250.0, 500.0, 1000.0), name: str = "sliced", **kw) -> ModelSpec:
+    """The multivariate model with Eq. 4's radial and pulse-shape terms in several energy
+    slices: one radial and one pulse-shape histogram of the TFC-vetoed events per slice of
+    the window, the slices given by their npe edges (the first and last on the window's)."""
+    spec = multivariate(name=name, **kw)
+    e = np.array([int(round(x / spec.width)) - spec.m_lo for x in edges_npe], dtype=np.int32)
+    if e[0] != 0 or e[-1] != spec.n_window or np.any(np.diff(e) <= 0):
+        raise ValueError("energy slice edges must rise from the window's low to its high edge")
+    spec.eslices = e
+    return spec
+
+
 def discrimination(n_grid=2000, e_max=3.0, width=1.0, lo_npe=100.0, hi_npe=1000.0,
                    n_species=15, total=2e6, L=400, n_rad2d=60, n_psd2d=50, tag_eff=0.9, amp=0.05,
                    seed=0, name="discrimination") -> ModelSpec:
@@ -372,6 +392,9 @@ def config(name: str) -> ModelSpec:
     * ``quenched`` the multivariate model with species-specific quenching (the alpha species
                   at its true energy, quenched with 150 kB); ``small_quenched`` its reduced
                   grid, with the external (gamma) species quenched with 1.3 kB as well.
+    * ``sliced``   the multivariate model with the radial and pulse-shape terms in three
+                  energy slices (100-250, 250-500, 500-1000 npe: Eq. 4's sums over radial
+                  and pulse-shape terms); ``small_sliced`` its reduced grid.
     * ``small_plain`` / ``small_mv`` / ``small_2d`` reduced grids that the oracle evaluates in
       well under a second (a few seconds for ``small_2d``) but that still span several
       128-row tiles and ragged tails.
@@ -393,6 +416,11 @@ def config(name: str) -> ModelSpec:
                             total=3e5, L=90, n_rad=20, n_psd=16, name=name)
     if name == "quenched":
         return quenched(name=name)
+    if name == "sliced":
+        return sliced(name=name)
+    if name == "small_sliced":
+        return sliced(edges_npe=(120.0, 300.0, 540.0, 900.0), n_grid=520, width=3.0, lo_npe=120.0, hi_npe=900.0,
+                      n_species=9, total=3e5, L=90, n_rad=20, n_psd=16, name=name)
     if name == "small_quenched":
         return quenched(n_grid=520, width=3.0, lo_npe=120.0, hi_npe=900.0, n_species=12, total=3e5, L=90,
                         n_rad=20, n_psd=16, gamma_quench=1.3, name=name)

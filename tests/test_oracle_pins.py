@@ -475,3 +475,85 @@ def test_quench_with_2d_slices_is_rejected():
     s = dataclasses.replace(s, quench=np.where(np.arange(s.K) == 0, 2.0, 1.0))
     with pytest.raises(RuntimeError):
         O.expected(s, s.theta_true)
+
+
+# ---- energy slices of Eq. 4's radial and pulse-shape terms
+
+def _sliced_spec(counts=True):
+    s = I.config("small_sliced")
+    if counts:
+        s = s.with_counts(I.poisson_counts(O.expected(s, s.theta_true), 5))
+    return s
+
+
+def _split(spec, mu):
+    out, o = {}, 0
+    for h, n in spec.hist_sizes().items():
+        out[h] = mu[o:o + n]
+        o += n
+    return out
+
+
+def test_one_energy_slice_is_the_base_model():
+    """A single slice spanning the window reproduces the model without slices bit for bit."""
+    s = _sliced_spec(counts=False)
+    one = dataclasses.replace(s, eslices=np.array([0, s.n_window], dtype=np.int32))
+    base = dataclasses.replace(s, eslices=None)
+    np.testing.assert_array_equal(O.expected(one, s.theta_true), O.expected(base, s.theta_true))
+
+
+def test_energy_slices_sum_to_the_window_marginals():
+    """The slices partition the window, so the radial (pulse-shape) histograms of all slices
+    add up to the single-slice histogram, bin by bin; the energy spectra are unchanged."""
+    s = _sliced_spec(counts=False)
+    base = dataclasses.replace(s, eslices=None)
+    th = I.parameter_points(s.theta_true, 1, rel=0.03, seed=21, free=s.default_free())[0]
+    sl, b = _split(s, O.expected(s, th)), _split(base, O.expected(base, th))
+    S = s.n_eslices
+    assert S == 3
+    np.testing.assert_array_equal(sl["sub"], b["sub"])
+    np.testing.assert_array_equal(sl["tag"], b["tag"])
+    np.testing.assert_allclose(sl["rad"].reshape(S, s.n_rad).sum(axis=0), b["rad"], rtol=1e-12)
+    np.testing.assert_allclose(sl["psd"].reshape(S, s.n_psd).sum(axis=0), b["psd"], rtol=1e-12)
+
+
+def test_energy_slice_histograms_hold_the_vetoed_events_of_the_slice():
+    """Radial and pulse-shape probabilities each sum to 1 per species, so each slice's radial
+    and pulse-shape histograms both hold the TFC-vetoed events of that slice's window bins:
+    the Eq. 4 marginals checked against the Eq. 3 spectrum after Eq. 2."""
+    s = _sliced_spec(counts=False)
+    th = I.parameter_points(s.theta_true, 1, rel=0.03, seed=22, free=s.default_free())[0]
+    h = _split(s, O.expected(s, th))
+    e = s.eslices
+    for q in range(s.n_eslices):
+        ev = h["sub"][e[q]:e[q + 1]].sum()
+        np.testing.assert_allclose(h["rad"][q * s.n_rad:(q + 1) * s.n_rad].sum(), ev, rtol=1e-11)
+        np.testing.assert_allclose(h["psd"][q * s.n_psd:(q + 1) * s.n_psd].sum(), ev, rtol=1e-11)
+
+
+def test_energy_slice_dual_gradient_matches_central_differences():
+    s = _sliced_spec()
+    th = I.parameter_points(s.theta_true, 1, rel=0.02, seed=23, free=s.default_free())[0]
+    f, g = O.nll(s, th, grad=True)
+    for j in [0, 3, s.K - 1, tail(s, "LY"), tail(s, "kB"), tail(s, "eps"), tail(s, "s_r")]:
+        h = 1e-5 * abs(th[j])
+        tp, tm = th.copy(), th.copy()
+        tp[j] += h
+        tm[j] -= h
+        fd = (O.nll(s, tp) - O.nll(s, tm)) / (2 * h)
+        assert abs(fd - g[j]) * abs(th[j]) <= 1e-6 * (1 + abs(g[j] * th[j])), (j, fd, g[j])
+
+
+@pytest.mark.parametrize("edges", [[1, 60, 260], [0, 60, 259], [0, 60, 60, 260], [0, 140, 60, 260]])
+def test_bad_energy_slice_edges_are_rejected(edges):
+    s = _sliced_spec(counts=False)
+    bad = dataclasses.replace(s, eslices=np.array(edges, dtype=np.int32))
+    with pytest.raises(RuntimeError):
+        O.expected(bad, s.theta_true)
+
+
+def test_energy_slices_with_2d_slices_are_rejected():
+    s = I.config("small_2d")
+    s = dataclasses.replace(s, eslices=np.array([0, 50, s.n_window], dtype=np.int32))
+    with pytest.raises(RuntimeError):
+        O.expected(s, s.theta_true)
