@@ -111,6 +111,17 @@ typedef struct {
      * BX_FP32 or BX_FP64 and no 2D histograms, and needs (groups - 1) * ceil(n_grid / 128) * 128
      * + n_grid <= 8192 columns. */
     const double* quench;       /* [K] Birks multiplier per species (>= 0), or NULL: 1 for all */
+    /* Energy slices of the Eq. 4 terms (its sums over several radial and pulse-shape terms):
+     * slice s covers the window bins [eslice_edges[s], eslice_edges[s+1]) (window-relative,
+     * eslice_edges[0] = 0, eslice_edges[n_eslice] = m_hi - m_lo, strictly rising).  Each slice
+     * has its own radial and pulse-shape histogram: A_k^(s), the TFC-vetoed events of
+     * species k in the slice after pile-up, times the species' bin probabilities (the same
+     * in every slice).  counts_rad is then [n_eslice][n_rad] and counts_psd
+     * [n_eslice][n_psd].  n_eslice = 0 (or 1 with edges {0, m_hi - m_lo}) is one slice, the
+     * whole window.  At most 4 slices, n_eslice * n_rad <= 256 and n_eslice * n_psd <= 256;
+     * more than one slice requires BX_FP32 or BX_FP64 and no 2D histograms. */
+    int n_eslice;
+    const int* eslice_edges;    /* [n_eslice + 1], or NULL with n_eslice = 0 */
 } bx_model_desc;
 
 typedef struct {
@@ -129,7 +140,7 @@ void bx_model_destroy(bx_model* model);
 int bx_model_set_stream(bx_model* model, void* cuda_stream);
 /* P = 7 + max_t K_t: the row stride of every theta / grad array */
 int bx_model_n_params(const bx_model* model);
-/* bins of toy t: window (+ window if tagged) + n_rad + n_psd + (n_rad2d + n_psd2d) window */
+/* bins of toy t: window (+ window if tagged) + slices * (n_rad + n_psd) + (n_rad2d + n_psd2d) window */
 int bx_model_n_bins(const bx_model* model, int toy);
 /* Sticky device status (BX_OK or BX_ETIMEOUT) after synchronising the model's stream. */
 int bx_model_status(bx_model* model);

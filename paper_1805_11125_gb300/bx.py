@@ -40,6 +40,7 @@ class bx_model_desc(C.Structure):
         ("n_rad2d", C.c_int), ("n_psd2d", C.c_int), ("psd2d_prob", _P), ("field2d", _P),
         ("field_amp", C.c_double), ("counts_rad2d", _P), ("counts_psd2d", _P),
         ("quench", _P),
+        ("n_eslice", C.c_int), ("eslice_edges", _P),
     ]
 
 
@@ -153,7 +154,7 @@ class Model:
                      rcls=arr(s.rad_class, np.int32), rad=arr(s.counts.get("rad")), psd=arr(s.psd_prob),
                      psdc=arr(s.counts.get("psd")), psd2=arr(s.psd2d_prob), field=arr(s.field2d),
                      r2c=arr(s.counts.get("r2d")), p2c=arr(s.counts.get("p2d")),
-                     quench=arr(getattr(s, "quench", None)))
+                     quench=arr(getattr(s, "quench", None)), es=arr(getattr(s, "eslices", None), np.int32))
             self._keep.append(k)
             has_rad = s.rad_class is not None and s.n_rad > 0
             d.n_grid, d.e_max, d.n_species = s.n_grid, s.e_max, s.K
@@ -169,6 +170,8 @@ class Model:
             d.field2d, d.field_amp = _ptr(k["field"]), s.field_amp
             d.counts_rad2d, d.counts_psd2d = _ptr(k["r2c"]), _ptr(k["p2c"])
             d.quench = _ptr(k["quench"])
+            d.n_eslice = 0 if k["es"] is None else len(k["es"]) - 1
+            d.eslice_edges = _ptr(k["es"])
         opts = bx_options(precision, max_batch, band_sigmas, watchdog_s)
         h = C.c_void_p()
         _check(lib().bx_model_create(C.cast(descs, _P), len(specs), C.byref(opts), _stream_handle(stream),

@@ -119,6 +119,17 @@ static int validate_desc(const bx_model_desc& d, int t) {
                 t, ng, d.n_grid, MAX_CB * BCOLS);
         }
     }
+    REQ(d.n_eslice >= 0 && d.n_eslice <= MAX_ES, "toy %d: n_eslice %d out of [0, %d]", t, d.n_eslice, MAX_ES);
+    if (d.n_eslice > 0) {
+        REQ(d.eslice_edges, "toy %d: n_eslice > 0 needs eslice_edges", t);
+        REQ(d.eslice_edges[0] == 0 && d.eslice_edges[d.n_eslice] == (int)nw,
+            "toy %d: energy slices must start at 0 and end at the window's %d bins", t, (int)nw);
+        for (int q = 0; q < d.n_eslice; ++q)
+            REQ(d.eslice_edges[q + 1] > d.eslice_edges[q], "toy %d: eslice_edges must rise strictly", t);
+        REQ(d.n_eslice * d.n_rad <= MAX_RAD && d.n_eslice * d.n_psd <= MAX_PSD,
+            "toy %d: energy slices x bins exceed %d", t, MAX_RAD);
+        if (d.n_eslice > 1) REQ(d.n_rad2d + d.n_psd2d == 0, "toy %d: energy slices with 2D histograms are not supported", t);
+    }
     REQ(d.n_rad2d >= 0 && d.n_psd2d >= 0, "toy %d: n_rad2d, n_psd2d must be >= 0", t);
     if (d.n_rad2d + d.n_psd2d > 0) {
         const int n_sl = 1 + (d.tag_frac ? 1 : 0) + d.n_rad2d + d.n_psd2d;
@@ -208,6 +219,8 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
         int set_of[KMAX];
         if (quench_groups(descs[t], xi, set_of) > 1 && o.precision == BX_TF32X3)
             return bx_set_error(BX_EINVAL, "toy %d: quenching groups need BX_FP32 or BX_FP64", t);
+        if (descs[t].n_eslice > 1 && o.precision == BX_TF32X3)
+            return bx_set_error(BX_EINVAL, "toy %d: energy slices need BX_FP32 or BX_FP64", t);
     }
     if (n2d && o.precision != BX_FP32) return bx_set_error(BX_EINVAL, "2D histograms need BX_FP32");
     int dev = 0;
@@ -257,7 +270,12 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
         T.n_p2 = d.n_psd2d;
         T.b_r2 = 1 + T.has_tag;
         T.n_sl = (T.n_r2 + T.n_p2 > 0) ? T.b_r2 + T.n_r2 + T.n_p2 : 0;
-        T.nb = T.nw * (1 + T.has_tag) + T.n_rad + T.n_psd + (T.n_r2 + T.n_p2) * T.nw;
+        T.n_es = d.n_eslice > 1 ? d.n_eslice : 1;
+        for (int q = 0; q < T.n_es; ++q) {
+            T.es_lo[q] = T.m_lo + (d.n_eslice > 1 ? d.eslice_edges[q] : 0);
+            T.es_hi[q] = T.m_lo + (d.n_eslice > 1 ? d.eslice_edges[q + 1] : T.nw);
+        }
+        T.nb = T.nw * (1 + T.has_tag) + T.n_es * (T.n_rad + T.n_psd) + (T.n_r2 + T.n_p2) * T.nw;
         T.P = T.K + 7;
         T.n_tiles = (T.M + TM - 1) / TM;
         T.n_set = quench_groups(d, T.xi, T.set_of);
@@ -273,8 +291,8 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
         std::vector<double> cnt;
         cnt.insert(cnt.end(), d.counts_sub, d.counts_sub + T.nw);
         if (T.has_tag) cnt.insert(cnt.end(), d.counts_tag, d.counts_tag + T.nw);
-        if (T.n_rad) cnt.insert(cnt.end(), d.counts_rad, d.counts_rad + T.n_rad);
-        if (T.n_psd) cnt.insert(cnt.end(), d.counts_psd, d.counts_psd + T.n_psd);
+        if (T.n_rad) cnt.insert(cnt.end(), d.counts_rad, d.counts_rad + (size_t)T.n_es * T.n_rad);
+        if (T.n_psd) cnt.insert(cnt.end(), d.counts_psd, d.counts_psd + (size_t)T.n_es * T.n_psd);
         if (T.n_r2) cnt.insert(cnt.end(), d.counts_rad2d, d.counts_rad2d + (size_t)T.n_r2 * T.nw);
         if (T.n_p2) cnt.insert(cnt.end(), d.counts_psd2d, d.counts_psd2d + (size_t)T.n_p2 * T.nw);
         if ((st = upload(m, d.shapes, (size_t)T.K * T.N, &T.shapes))) break;
@@ -324,12 +342,12 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
         if ((st = alloc_dev(m, &s32, (size_t)T.K * T.N * sizeof(float)))) break;
         if ((st = alloc_dev(m, &stiles, (size_t)T.n_kb * 3 * US * KB * sizeof(float)))) break;
         if ((st = alloc_dev(m, &g32, (size_t)T.L * sizeof(float)))) break;
-        if ((st = alloc_dev(m, &gg, (size_t)T.M * (sizeof(double) + sizeof(float))))) break;
+        if ((st = alloc_dev(m, &gg, (size_t)T.n_es * T.M * (sizeof(double) + sizeof(float))))) break;
         T.shapes32 = static_cast<float*>(s32);
         T.S_tiles = static_cast<float*>(stiles);
         T.g32 = static_cast<float*>(g32);
         T.Gg = static_cast<double*>(gg);
-        T.Gg32 = reinterpret_cast<float*>(static_cast<double*>(gg) + T.M);
+        T.Gg32 = reinterpret_cast<float*>(static_cast<double*>(gg) + (size_t)T.n_es * T.M);
         cudaError_t e = launch_setup_toy(T, static_cast<float*>(s32), static_cast<float*>(stiles),
                                          static_cast<float*>(g32), static_cast<double*>(gg), m->stream);
         if (e != cudaSuccess) st = bx_set_error(BX_ECUDA, "set-up kernel: %s", cudaGetErrorString(e));
@@ -362,7 +380,11 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
     w.precision = m->precision;
     w.lam_pairs = m->precision == BX_FP32;
     w.multi_set = 0;
-    for (const Toy& T : m->toys_h) w.multi_set |= T.n_set > 1 ? 1 : 0;
+    w.nes = 1;
+    for (const Toy& T : m->toys_h) {
+        w.multi_set |= T.n_set > 1 ? 1 : 0;
+        w.nes = std::max(w.nes, T.n_es);
+    }
     w.band = m->band;
     w.watchdog_ns = m->watchdog_ns;
     w.max_tiles = m->max_tiles;
@@ -386,15 +408,15 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
         {(void**)&w.colg, sizeof(ColG) * cap * w.Npad},
         {(void**)&w.colS, sizeof(double2) * cap * w.Npad},
         {(void**)&w.colS32, sizeof(float2) * cap * w.Npad},
-        {(void**)&w.aW, sizeof(double) * cap * w.Npad},
+        {(void**)&w.aW, sizeof(double) * cap * w.nes * w.Npad},
         {(void**)&w.colr, sizeof(int2) * cap * w.Npad},
         {(void**)&w.lam, sizeof(double) * cap * 2 * w.Mpad},
-        {(void**)&w.apart, m->any_cols && !species ? 2 * sizeof(float) * cap * m->max_tiles * w.Npad : 16},
+        {(void**)&w.apart, m->any_cols && !species ? 2 * sizeof(float) * cap * m->max_tiles * w.nes * w.Npad : 16},
         {(void**)&w.tile_cols, sizeof(int2) * cap * MAX_SETS * MAX_TILES},
         {(void**)&w.cb_rows, sizeof(int2) * cap * MAX_CB},
         {(void**)&w.v, species ? tv * cap * w.Mpad * US : 16},
-        {(void**)&w.rowW, tv * cap * 3 * w.Mpad},
-        {(void**)&w.coef, sizeof(double) * cap * 3 * KMAX},
+        {(void**)&w.rowW, tv * cap * (2 + w.nes) * w.Mpad},
+        {(void**)&w.coef, sizeof(double) * cap * (2 + w.nes) * KMAX},
         {(void**)&w.gmid, sizeof(double) * cap * PMAX},
         {(void**)&w.gpart, sizeof(double) * cap * MAX_CB * GPN},
         {(void**)&w.nll, sizeof(double) * cap},

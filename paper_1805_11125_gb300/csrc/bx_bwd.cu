@@ -79,18 +79,21 @@ __device__ __forceinline__ void block_sum_gp(double (&g)[GPN], double* red, doub
     }
 }
 
+// Species sums of the column's adjoint weights: vetoed, tagged, and one per energy slice q
+// of the Eq. 4 terms (SA[q], 0 beyond the toy's slices).
 template <bool MULTI>
 __device__ __forceinline__ void column_weights(const Work& w, const Toy& T, int item, int i, int grp, bool ok,
-                                               double& Ssub, double& Stag, double& SA) {
-    const double* coef = w.coef + (size_t)item * 3 * KMAX;
-    Ssub = Stag = SA = 0.0;
+                                               double& Ssub, double& Stag, double (&SA)[MAX_ES]) {
+    const double* coef = w.coef + (size_t)item * (2 + w.nes) * KMAX;
+    Ssub = Stag = 0.0;
+    for (int q = 0; q < MAX_ES; ++q) SA[q] = 0.0;
     if (!ok) return;
     for (int k = 0; k < T.K; ++k) {
         if (!in_group<MULTI>(T, k, grp)) continue;
         const double s = T.shapes[(size_t)k * T.N + i];
         Ssub += coef[k] * s;
         Stag += coef[KMAX + k] * s;
-        SA += coef[2 * KMAX + k] * s;
+        for (int q = 0; q < T.n_es; ++q) SA[q] += coef[(2 + q) * KMAX + k] * s;
     }
 }
 
@@ -114,11 +117,12 @@ __global__ void __launch_bounds__(BCOLS) k_bwd_f64(Work w) {
         return;
     }
     const int r0 = max(rr.x, max(0, T.m_lo - T.L + 1)), r1 = min(rr.y, T.M);
-    double Ssub, Stag, SA;
+    double Ssub, Stag, SA[MAX_ES];
     column_weights<MULTI>(w, T, item, ig, grp, ok, Ssub, Stag, SA);
     const Col64 cc = ok ? w.col64[(size_t)item * w.Npad + i] : Col64{0.0, 1.0, 0.0, 0.0};
-    const double* rw = static_cast<const double*>(w.rowW) + (size_t)item * 3 * w.Mpad;
-    __shared__ double sW[3][RCH];
+    const double* rw = static_cast<const double*>(w.rowW) + (size_t)item * (2 + w.nes) * w.Mpad;
+    const int NES = T.n_es;
+    __shared__ double sW[2 + MAX_ES][RCH];   // wt_sub, wt_tag, G_W of each energy slice
     __shared__ double red[GPN * (BCOLS / 32)];
     double S0 = 0.0, S1 = 0.0, S2 = 0.0, Rs = 0.0, Rt = 0.0;
     double ta = 0.0, pa = 0.0, zpa = 0.0;
@@ -134,18 +138,16 @@ __global__ void __launch_bounds__(BCOLS) k_bwd_f64(Work w) {
     if (ok && r0 < r1) edge(r0, ta, pa, zpa, fa);
     for (int c0 = r0; c0 < r1; c0 += RCH) {
         const int nr = min(RCH, r1 - c0);
-        for (int j = tid; j < nr; j += BCOLS) {
-            sW[0][j] = rw[c0 + j];
-            sW[1][j] = rw[(size_t)w.Mpad + c0 + j];
-            sW[2][j] = rw[(size_t)2 * w.Mpad + c0 + j];
-        }
+        for (int j = tid; j < nr; j += BCOLS)
+            for (int r = 0; r < 2 + NES; ++r) sW[r][j] = rw[(size_t)r * w.Mpad + c0 + j];
         __syncthreads();
         if (ok) {
             for (int j = 0; j < nr; ++j) {
                 double tb, pb, zpb;
                 bool fb;
                 edge(c0 + j + 1, tb, pb, zpb, fb);
-                const double W = sW[0][j] * Ssub + sW[1][j] * Stag + sW[2][j] * SA;
+                double W = sW[0][j] * Ssub + sW[1][j] * Stag;
+                for (int q = 0; q < NES; ++q) W += sW[2 + q][j] * SA[q];
                 const double D = tb - ta + ((!fa && fb) ? 1.0 : 0.0);
                 S0 += W * D;
                 S1 -= W * (pb - pa);
@@ -169,7 +171,7 @@ __global__ void __launch_bounds__(BCOLS) k_bwd_f64(Work w) {
     block_sum_gp(g, red, gp);
 }
 
-template <bool MULTI>
+template <bool MULTI, bool MES>
 __global__ void __launch_bounds__(BCOLS, 7) k_bwd_f32(Work w) {
     // 1D item-major grid (a y dimension would cap the batch at 65535 items)
     const int cb = blockIdx.x % w.max_cb, item = blockIdx.x / w.max_cb, tid = threadIdx.x;
@@ -189,31 +191,41 @@ __global__ void __launch_bounds__(BCOLS, 7) k_bwd_f32(Work w) {
         return;
     }
     const int r0 = max(rr.x, max(0, T.m_lo - T.L + 1)), r1 = min(rr.y, T.M);
-    __shared__ float s_coef[3][KMAX];   // vetoed, tagged and window coefficients per species
+    // vetoed, tagged and the window (energy slice) coefficients per species; MES: several
+    // energy slices of the Eq. 4 terms, each with its own row weight G_W,q and coefficients
+    constexpr int NR = MES ? 2 + MAX_ES : 3;
+    const int NES = MES ? T.n_es : 1;
+    __shared__ float s_coef[NR][KMAX];
     __shared__ float s_c[2][KMAX];      // c_{vetoed,k}, c_{tagged,k}
     __shared__ double red[GPN * (BCOLS / 32)];
-    const double* coef = w.coef + (size_t)item * 3 * KMAX;
-    if (tid < 3 * KMAX) s_coef[tid / KMAX][tid % KMAX] = (float)coef[tid];
+    const double* coef = w.coef + (size_t)item * (2 + (MES ? w.nes : 1)) * KMAX;
+    if (tid < (2 + NES) * KMAX) s_coef[tid / KMAX][tid % KMAX] = (float)coef[tid];
     if (tid < KMAX) {
         const double t = (T.tag && tid < T.K) ? T.tag[tid] : 0.0;
         s_c[0][tid] = T.tag ? (float)(1.0 - t) : 1.f;
         s_c[1][tid] = (float)t;
     }
     __syncthreads();
-    // dNLL/dR[m,i] = Ssub wt_sub[m] + Stag wt_tag[m] + SA G_W[m]: the species sums in FP32
-    float Ssub = 0.f, Stag = 0.f, SA = 0.f;
+    // dNLL/dR[m,i] = Ssub wt_sub[m] + Stag wt_tag[m] + sum_q SA_q G_W,q[m]: the species sums in FP32
+    float Ssub = 0.f, Stag = 0.f, SA = 0.f, SAq[MES ? MAX_ES : 1];
+#pragma unroll
+    for (int q = 0; q < (MES ? MAX_ES : 1); ++q) SAq[q] = 0.f;
     if (ok)
         for (int k = 0; k < T.K; ++k) {
             if (!in_group<MULTI>(T, k, grp)) continue;
             const float sk = T.shapes32[(size_t)k * T.N + ig];
             Ssub = fmaf(s_coef[0][k], sk, Ssub);
             Stag = fmaf(s_coef[1][k], sk, Stag);
-            SA = fmaf(s_coef[2][k], sk, SA);
+            if (!MES) SA = fmaf(s_coef[2][k], sk, SA);
+            else
+#pragma unroll
+                for (int q = 0; q < (MES ? MAX_ES : 1); ++q)
+                    if (q < NES) SAq[q] = fmaf(s_coef[2 + q][k], sk, SAq[q]);
         }
     const float4 cf = ok ? w.colf[(size_t)item * w.Npad + i] : make_float4(0.f, 0.f, 0.f, 0.f);
     const ColG cg = ok ? w.colg[(size_t)item * w.Npad + i] : ColG{0.f, 0.f, 0.f, 0.f};
     const AdjCol ac = adj_col(cf, cg);
-    const float* rw = static_cast<const float*>(w.rowW) + (size_t)item * 3 * w.Mpad;
+    const float* rw = static_cast<const float*>(w.rowW) + (size_t)item * (2 + (MES ? w.nes : 1)) * w.Mpad;
     // the warp's rows: the union of its 32 columns' bands, their weights staged 64 rows at a
     // time in the warp's own shared memory (the warps of the block never wait for each other)
     const int2 band = ok ? w.colr[(size_t)item * w.Npad + i] : make_int2(0, 0);
@@ -221,7 +233,7 @@ __global__ void __launch_bounds__(BCOLS, 7) k_bwd_f32(Work w) {
     const int wr0 = max(r0, min(r1, __reduce_min_sync(0xffffffffu, live ? band.x : INT_MAX)));
     const int wr1 = min(r1, __reduce_max_sync(0xffffffffu, live ? band.y : 0));
     const int lane = tid & 31, wq = tid >> 5;
-    __shared__ float sW[BCOLS / 32][3][64];
+    __shared__ float sW[BCOLS / 32][NR][64];
     double S0 = 0.0, S1 = 0.0, S2 = 0.0, Rs = 0.0, Rt = 0.0;
     for (int c0 = wr0; c0 < wr1; c0 += RCH) {
         const int c1 = min(wr1, c0 + RCH);
@@ -232,6 +244,8 @@ __global__ void __launch_bounds__(BCOLS, 7) k_bwd_f32(Work w) {
                 sW[wq][0][j] = rw[s0 + j];
                 sW[wq][1][j] = rw[(size_t)w.Mpad + s0 + j];
                 sW[wq][2][j] = rw[(size_t)2 * w.Mpad + s0 + j];
+                if (MES)
+                    for (int q = 1; q < NES; ++q) sW[wq][2 + q][j] = rw[(size_t)(2 + q) * w.Mpad + s0 + j];
             }
             __syncwarp();
             if (ok) {
@@ -239,7 +253,15 @@ __global__ void __launch_bounds__(BCOLS, 7) k_bwd_f32(Work w) {
                     auto wts = [&](int k, float& ws, float& wt, float& W) {
                         ws = sW[wq][0][j + k];
                         wt = sW[wq][1][j + k];
-                        W = fmaf(ws, Ssub, fmaf(wt, Stag, sW[wq][2][j + k] * SA));
+                        if (!MES) {
+                            W = fmaf(ws, Ssub, fmaf(wt, Stag, sW[wq][2][j + k] * SA));
+                        } else {
+                            float a = 0.f;
+#pragma unroll
+                            for (int q = 0; q < (MES ? MAX_ES : 1); ++q)
+                                if (q < NES) a = fmaf(sW[wq][2 + q][j + k], SAq[q], a);
+                            W = fmaf(ws, Ssub, fmaf(wt, Stag, a));
+                        }
                     };
                     adj_run((float)(s0 + j), min(ADJ_RUN, ns - j), cf, cg, ac, wts, bs);
                 }
@@ -313,8 +335,11 @@ cudaError_t launch_bwd(const Work& w, int n, int max_cb, cudaStream_t s) {
         if (w.multi_set) k_bwd_f64<true><<<grid, BCOLS, 0, s>>>(w);
         else k_bwd_f64<false><<<grid, BCOLS, 0, s>>>(w);
     } else {
-        if (w.multi_set) k_bwd_f32<true><<<grid, BCOLS, 0, s>>>(w);
-        else k_bwd_f32<false><<<grid, BCOLS, 0, s>>>(w);
+        const bool mes = w.nes > 1;   // several energy slices of the Eq. 4 terms
+        if (w.multi_set && mes) k_bwd_f32<true, true><<<grid, BCOLS, 0, s>>>(w);
+        else if (w.multi_set) k_bwd_f32<true, false><<<grid, BCOLS, 0, s>>>(w);
+        else if (mes) k_bwd_f32<false, true><<<grid, BCOLS, 0, s>>>(w);
+        else k_bwd_f32<false, false><<<grid, BCOLS, 0, s>>>(w);
     }
     return cudaGetLastError();
 }

@@ -16,7 +16,9 @@
 // (bx_resp.cuh) and adds R S_h into Kahan-compensated accumulators at every term, so a row
 // sum of ~10^3 terms keeps an error of a few roundings with no systematic sign.  Column sums
 // of R Gg over a warp's 64 rows go through a padded warp-private shared buffer once per
-// 32 columns and are stored per half tile.
+// 32 columns and are stored per half tile.  With several energy slices of the Eq. 4 terms
+// (MES) the buffer holds R itself and the column sums are formed once per slice s with its
+// Gg_s.
 #include <math.h>
 
 #include "bx_df.cuh"
@@ -35,7 +37,7 @@ __device__ __forceinline__ void kahan_fma(float& acc, float& cmp, float a, float
     acc = t;
 }
 
-template <bool TAG, bool COLS>
+template <bool TAG, bool COLS, bool MES>
 __global__ void __launch_bounds__(F32_THREADS) k_fwd_f32(Work w) {
     // 1D item-major grid (a y dimension would cap the batch at 65535 items)
     const int tile = blockIdx.x % w.max_tiles, item = blockIdx.x / w.max_tiles, tid = threadIdx.x;
@@ -59,10 +61,17 @@ __global__ void __launch_bounds__(F32_THREADS) k_fwd_f32(Work w) {
 
     const int ra = g + lane, rb = ra + 32;
     const float mfa = (float)ra, mfb = (float)rb;
-    const float gga = (COLS && ra < M) ? (float)T.Gg[ra] : 0.f;
-    const float ggb = (COLS && rb < M) ? (float)T.Gg[rb] : 0.f;
+    const float gga = (COLS && !MES && ra < M) ? (float)T.Gg[ra] : 0.f;
+    const float ggb = (COLS && !MES && rb < M) ? (float)T.Gg[rb] : 0.f;
+    const int NES = MES ? T.n_es : 1;
+    __shared__ float sGg[MES ? 2 : 1][MES ? MAX_ES : 1][MES ? 64 : 1];   // Gg_s of the warp's 64 rows
+    if (MES)
+        for (int s = 0; s < NES; ++s) {
+            sGg[q][s][lane] = ra < M ? T.Gg32[(size_t)s * M + ra] : 0.f;
+            sGg[q][s][lane + 32] = rb < M ? T.Gg32[(size_t)s * M + rb] : 0.f;
+        }
     float sa = 0.f, csa = 0.f, ta = 0.f, cta = 0.f, sb = 0.f, csb = 0.f, tb = 0.f, ctb = 0.f;
-    float* apart = static_cast<float*>(w.apart) + (((size_t)item * w.max_tiles + tile) * 2 + q) * w.Npad;
+    float* apart = static_cast<float*>(w.apart) + (((size_t)item * w.max_tiles + tile) * 2 + q) * (MES ? w.nes : 1) * w.Npad;
 
     for (int grp = 0; grp < NGRP; ++grp) {
     const int2 cr = tile_range(w, item, grp, tile);
@@ -111,15 +120,31 @@ __global__ void __launch_bounds__(F32_THREADS) k_fwd_f32(Work w) {
                 if (TAG) kahan_fma(tb, ctb, Rb, S.y);
             }
             if (COLS) {
-                cb[lane][c] = Ra * gga;
-                cb[lane + 32][c] = Rb * ggb;
+                cb[lane][c] = MES ? Ra : Ra * gga;
+                cb[lane + 32][c] = MES ? Rb : Rb * ggb;
             }
         }
         __syncwarp();
-        if (COLS) {
+        if (COLS && !MES) {
             float s = 0.f;
             for (int j = 0; j < 64; ++j) s += cb[j][lane];
             if (lane < ncol) apart[c0 + lane] = s * sG[q][lane].A;
+            __syncwarp();
+        }
+        if (COLS && MES) {
+            float s[MAX_ES];
+#pragma unroll
+            for (int e = 0; e < MAX_ES; ++e) s[e] = 0.f;
+            for (int j = 0; j < 64; ++j) {
+                const float r = cb[j][lane];
+#pragma unroll
+                for (int e = 0; e < MAX_ES; ++e)
+                    if (e < NES) s[e] = fmaf(r, sGg[q][e][j], s[e]);
+            }
+            if (lane < ncol)
+#pragma unroll
+                for (int e = 0; e < MAX_ES; ++e)
+                    if (e < NES) apart[(size_t)e * w.Npad + c0 + lane] = s[e] * sG[q][lane].A;
             __syncwarp();
         }
     }
@@ -153,10 +178,13 @@ __global__ void __launch_bounds__(F32_THREADS) k_fwd_f32(Work w) {
 
 cudaError_t launch_fwd_f32(const Work& w, int n, int max_tiles, int any_tag, int any_cols, cudaStream_t s) {
     const unsigned grid = (unsigned)n * (unsigned)w.max_tiles;   // decoded with w.max_tiles
-    if (any_tag && any_cols) k_fwd_f32<true, true><<<grid, F32_THREADS, 0, s>>>(w);
-    else if (any_tag) k_fwd_f32<true, false><<<grid, F32_THREADS, 0, s>>>(w);
-    else if (any_cols) k_fwd_f32<false, true><<<grid, F32_THREADS, 0, s>>>(w);
-    else k_fwd_f32<false, false><<<grid, F32_THREADS, 0, s>>>(w);
+    const bool mes = w.nes > 1;   // several energy slices of the Eq. 4 terms
+    if (any_tag && any_cols && mes) k_fwd_f32<true, true, true><<<grid, F32_THREADS, 0, s>>>(w);
+    else if (any_cols && mes) k_fwd_f32<false, true, true><<<grid, F32_THREADS, 0, s>>>(w);
+    else if (any_tag && any_cols) k_fwd_f32<true, true, false><<<grid, F32_THREADS, 0, s>>>(w);
+    else if (any_tag) k_fwd_f32<true, false, false><<<grid, F32_THREADS, 0, s>>>(w);
+    else if (any_cols) k_fwd_f32<false, true, false><<<grid, F32_THREADS, 0, s>>>(w);
+    else k_fwd_f32<false, false, false><<<grid, F32_THREADS, 0, s>>>(w);
     return cudaGetLastError();
 }
 

@@ -1,7 +1,8 @@
 // bx_fwd_f64.cu -- Eq. 1 forward in plain FP64 on the CUDA cores (the reference GPU form).
 //
 // Same rate-first reductions as the FP32 kernel (row sums lambda_h[m] = sum_i R[m,i] S_h[i]
-// and per-tile column sums a_t[i] = sum_m R[m,i] Gg[m]), with the exact bin mass:
+// and per-tile column sums a_t,s[i] = sum_m R[m,i] Gg_s[m], one per energy slice s of the
+// Eq. 4 terms), with the exact bin mass:
 // unit = (row tile of TM output bins, item), thread = output bin.  For each chunk of
 // FCH64 columns of the tile's band, phase 1 evaluates the Gaussian tail mass at the TM + 1
 // bin edges of each column (one erfc per edge, shared by the two bins it bounds); phase 2
@@ -30,12 +31,15 @@ __global__ void __launch_bounds__(TM) k_fwd_f64(Work w) {
     __shared__ unsigned char sF[FCH64 * (TM + 1)];   // 1: edge at or above the mean
     __shared__ double2 sS[FCH64];
     __shared__ double sNorm[FCH64];
-    __shared__ double colbuf[COLS ? TM : 1][FCH64 + 1];
+    __shared__ double colbuf[COLS ? TM : 1][FCH64 + 1];   // R of the chunk's columns
+    __shared__ double sGg[COLS ? MAX_ES : 1][TM];          // Gg_s of the tile's rows
 
     const int m = m0 + tid;
-    const double gg = (COLS && m < M) ? T.Gg[m] : 0.0;
+    const int NES = T.n_es;
+    if (COLS)
+        for (int q = 0; q < NES; ++q) sGg[q][tid] = m < M ? T.Gg[(size_t)q * M + m] : 0.0;
     double ls = 0.0, lt = 0.0;
-    double* apart = static_cast<double*>(w.apart) + ((size_t)item * w.max_tiles + tile) * w.Npad;
+    double* apart = static_cast<double*>(w.apart) + ((size_t)item * w.max_tiles + tile) * w.nes * w.Npad;
 
     for (int grp = 0; grp < NGRP; ++grp) {
     const int2 cr = tile_range(w, item, grp, tile);
@@ -72,18 +76,23 @@ __global__ void __launch_bounds__(TM) k_fwd_f64(Work w) {
             const double R = D * sNorm[c];
             ls = fma(R, sS[c].x, ls);
             if (TAG) lt = fma(R, sS[c].y, lt);
-            if (COLS) colbuf[tid][c] = R * gg;
+            if (COLS) colbuf[tid][c] = R;
         }
         if (COLS) {
             __syncthreads();
-            // column c = tid / 8 summed by 8 threads over 16 rows each
+            // column c = tid / 8 summed by 8 threads over 16 rows each, once per energy slice
             const int c = tid >> 3, part = tid & 7;
-            double s = 0.0;
-            for (int j = 0; j < TM / 8; ++j) s += colbuf[part * (TM / 8) + j][c];
-            s += __shfl_xor_sync(0xffffffffu, s, 1);
-            s += __shfl_xor_sync(0xffffffffu, s, 2);
-            s += __shfl_xor_sync(0xffffffffu, s, 4);
-            if (part == 0 && c < ncol) apart[c0 + c] = s;
+            for (int q = 0; q < NES; ++q) {
+                double s = 0.0;
+                for (int j = 0; j < TM / 8; ++j) {
+                    const int r = part * (TM / 8) + j;
+                    s += colbuf[r][c] * sGg[q][r];
+                }
+                s += __shfl_xor_sync(0xffffffffu, s, 1);
+                s += __shfl_xor_sync(0xffffffffu, s, 2);
+                s += __shfl_xor_sync(0xffffffffu, s, 4);
+                if (part == 0 && c < ncol) apart[(size_t)q * w.Npad + c0 + c] = s;
+            }
         }
         __syncthreads();
     }

@@ -58,6 +58,7 @@ struct __align__(16) ColG {
 
 // Device description of one toy (dataset + its fixed model inputs).
 constexpr int MAX_SETS = 4;   // groups of species-specific quenching
+constexpr int MAX_ES = 4;     // energy slices of the Eq. 4 radial and pulse-shape terms
 
 struct Toy {
     int K, N, M, m_lo, nw, L, n_rad, n_psd, has_tag, nb, P;
@@ -66,6 +67,10 @@ struct Toy {
     // columns [c Ncs, c Ncs + N); Next = (n_set - 1) Ncs + N columns in use (n_set = 1: Ncs =
     // Next = N, the plain model)
     int n_set, Ncs, Next;
+    // energy slices of the Eq. 4 terms: slice s is the rows [es_lo[s], es_hi[s]) of the window,
+    // with its own radial and pulse-shape histogram (n_es = 1: the whole window)
+    int n_es;
+    int es_lo[MAX_ES], es_hi[MAX_ES];
     int set_of[KMAX];
     double xi[MAX_SETS];
     double dE, w, r_fid, r_iv, att_len;
@@ -77,8 +82,8 @@ struct Toy {
     const double* tag;        // [K] or nullptr
     const double* g;          // [L]
     const float* g32;         // [L]
-    const double* Gg;         // [M]: sum over window bins m' of g[m' - m] (0 <= m'-m < L)
-    const float* Gg32;        // [M]: the same in FP32, stored after Gg
+    const double* Gg;         // [n_es][M]: sum over the slice's window bins m' of g[m' - m] (0 <= m'-m < L)
+    const float* Gg32;        // [n_es][M]: the same in FP32, stored after Gg
     const double* cnt;        // [nb] data, concatenated (vetoed, tagged, radial, PSD, 2D slices)
     const float2* cnt32;      // [nb] the same as FP32 pairs hi + lo
     const int* rad_class;     // [K]
@@ -99,6 +104,8 @@ struct Col64 {
 // Workspace of a model: every array has `cap` item slots.
 struct Work {
     int cap, Npad, Mpad, nbmax, pstride, n_items, max_tiles, max_cb;
+    int nes;                  // energy slices of the Eq. 4 terms (the most of any toy, >= 1): the
+                              // slice stride of aW, apart, rowW and coef
     int precision;
     double band;
     unsigned long long watchdog_ns;
@@ -112,20 +119,20 @@ struct Work {
     ColG* colg;               // [cap][Npad]
     double2* colS;            // [cap][Npad]: S_vetoed[i], S_tagged[i] (FP64 model)
     float2* colS32;           // [cap][Npad]: A_i S_h[i] (vetoed, tagged) in FP32 for the rate-first FP32 forward
-    double* aW;               // [cap][Npad]: window mass sum_{m in W} R[m,i] (closed form) times 1/Phi;
+    double* aW;               // [cap][nes][Npad]: slice mass sum_{m in W_s} R[m,i] (closed form) times 1/Phi;
                               // as FP32 pairs (hi, lo) in the same bytes in the mixed-precision modes
     int2* colr;               // [cap][Npad]: band rows [r0, r1) of each column (empty: r0 >= r1)
     double* lam;              // [cap][2][Mpad]: lambda_h[m] (rate-first forward); FP32 pairs when lam_pairs
     int lam_pairs;            // rate-first mixed precision: the forward writes lam as FP32 pairs
     int multi_set;            // some toy has several quenching groups (selects the kernels that handle them)
-    void* apart;              // [cap][max_tiles][H][Npad]: column sums of R Gg per tile, FP64 (H = 1)
+    void* apart;              // [cap][max_tiles][H][nes][Npad]: column sums of R Gg_s per tile, FP64 (H = 1)
                               // or per half tile (one warp's 64 rows), FP32 (H = 2)
     int2* tile_cols;          // [cap][MAX_SETS][MAX_TILES]: column range of each forward tile, per
                               // quenching group (tile_range); only the toy's groups are written
     int2* cb_rows;            // [cap][MAX_CB]: row range of each backward column block
     void* v;                  // [cap][Mpad][US] float (TF32X3) or double (FP64)
-    void* rowW;               // [cap][3][Mpad] float or double: wt_sub, wt_tag, G_W
-    double* coef;             // [cap][3][KMAX]
+    void* rowW;               // [cap][2 + nes][Mpad] float or double: wt_sub, wt_tag, G_W of every slice
+    double* coef;             // [cap][2 + nes][KMAX]: vetoed, tagged, then each slice's Eq. 4 coefficients
     double* gmid;             // [cap][PMAX]
     double* gpart;            // [cap][MAX_CB][GPN]
     double* nll;              // [cap]

@@ -108,7 +108,8 @@ __global__ void __launch_bounds__(MID_THREADS, (sizeof(TV) == sizeof(float) && !
     const int item = blockIdx.x, tid = threadIdx.x;
     const Toy& T = w.toys[w.toy_of[item]];
     const int K = T.K, M = T.M, nw = T.nw, m_lo = T.m_lo, L = T.L, H = T.has_tag ? 2 : 1;
-    const int nrad = T.n_rad, npsd = T.n_psd, nb = T.nb;
+    const int nrad = T.n_rad, npsd = T.n_psd, nb = T.nb, NES = T.n_es;   // NES = 1 in the species mode
+    const int nradS = NES * nrad, npsdS = NES * npsd;                    // bins of all energy slices
     double* gmid = w.gmid + (size_t)item * PMAX;
     if (w.status[item]) {
         if (tid == 0) w.nll[item] = INFINITY;
@@ -126,7 +127,9 @@ __global__ void __launch_bounds__(MID_THREADS, (sizeof(TV) == sizeof(float) && !
     TV* wvT = puT + 2 * nw;                             // [H][nw] 1 - n/mu
     TV* gT = wvT + 2 * nw;                              // [L]
 
-    __shared__ double s_rs[KMAX], s_rt[KMAX], s_SA[2 * KMAX], s_beta[KMAX], s_gr[2 * KMAX];
+    // per energy slice q: s_SA[q][k] = sum v_k G_W,q, s_SA[q][KMAX + k] its d/deps; s_beta[q][k]
+    __shared__ double s_rs[KMAX], s_rt[KMAX], s_SA[MAX_ES][2 * KMAX], s_beta[MAX_ES][KMAX], s_gr[2 * KMAX];
+    __shared__ double s_aint[MAX_ES], s_aext[MAX_ES];
     __shared__ double s_pint[MAX_RAD], s_pext[MAX_RAD], s_dpext[MAX_RAD], s_mur[MAX_RAD], s_wr[MAX_RAD];
     __shared__ double s_F[MAX_RAD + 2], s_dF[MAX_RAD + 2];
     __shared__ double s_mup[MAX_PSD], s_wp[MAX_PSD];
@@ -184,13 +187,13 @@ __global__ void __launch_bounds__(MID_THREADS, (sizeof(TV) == sizeof(float) && !
 
     // Eq. 4: window marginals of the vetoed species spectra after pile-up
     const bool mv = nrad > 0 || npsd > 0;
-    if (mv) {
+    for (int qs = 0; mv && qs < NES; ++qs) {   // one pass per energy slice
         double part[2 * KMAX];
 #pragma unroll
         for (int k = 0; k < 2 * KMAX; ++k) part[k] = 0.0;
         if (species) {
             for (int m = tid; m < M; m += MID_THREADS) {
-                const double inW = m >= m_lo ? 1.0 : 0.0, gg = T.Gg[m];
+                const double inW = m >= T.es_lo[qs] && m < T.es_hi[qs] ? 1.0 : 0.0, gg = T.Gg[(size_t)qs * M + m];
                 const double GW = (1.0 - eps) * inW + eps * gg, dG = gg - inW;
                 const TV* vr = v + (size_t)m * US;
 #pragma unroll
@@ -205,8 +208,8 @@ __global__ void __launch_bounds__(MID_THREADS, (sizeof(TV) == sizeof(float) && !
             // sum_m v_k[m] G_W[m] = sum_i s_k[i] ((1 - eps) aW[i] + eps a[i]), a[i] from the
             // per-tile column sums of the forward (valid on each tile's band only)
             constexpr int HALF = sizeof(TV) == sizeof(float) ? 2 : 1;   // slots per tile
-            const TV* ap = static_cast<const TV*>(w.apart) + (size_t)item * w.max_tiles * HALF * w.Npad;
-            const double* aWi = w.aW + (size_t)item * w.Npad;
+            const TV* ap = static_cast<const TV*>(w.apart) + (size_t)item * w.max_tiles * HALF * w.nes * w.Npad;
+            const double* aWi = w.aW + ((size_t)item * w.nes + qs) * w.Npad;
             const int lane = tid & 31, wid = tid >> 5;
             {   // FP64 model (the rate-first FP32 mode runs k_mid32)
                 // column ie = grp Ncs + i of quenching group grp carries the species of that group
@@ -219,7 +222,7 @@ __global__ void __launch_bounds__(MID_THREADS, (sizeof(TV) == sizeof(float) && !
                     for (int t = 0; t < T.n_tiles; ++t) {
                         const int2 cr = tcols[t];
                         if (ie >= cr.x && ie < cr.y)
-                            for (int h = 0; h < HALF; ++h) ag += (double)ap[((size_t)t * HALF + h) * w.Npad + ie];
+                            for (int h = 0; h < HALF; ++h) ag += (double)ap[(((size_t)t * HALF + h) * w.nes + qs) * w.Npad + ie];
                     }
                     const double aw = aWi[ie];
                     const double GW = (1.0 - eps) * aw + eps * ag, dG = ag - aw;
@@ -241,30 +244,34 @@ __global__ void __launch_bounds__(MID_THREADS, (sizeof(TV) == sizeof(float) && !
             if (tid < 2 * KMAX) {
                 double v = 0.0;
                 for (int q = 0; q < MID_WARPS; ++q) v += red[q * 2 * KMAX + tid];
-                s_SA[tid] = v;
+                s_SA[qs][tid] = v;
             }
             __syncthreads();
         }
-        // s_SA[k] = sum v G_W, s_SA[KMAX+k] = sum v dG_W/deps
-        if (species) block_sum<2 * KMAX>(part, red, s_SA);
+        // s_SA[q][k] = sum v G_W,q, s_SA[q][KMAX+k] = sum v dG_W,q/deps
+        if (species) block_sum<2 * KMAX>(part, red, s_SA[qs]);
     }
     // radial bin probabilities (internal: uniform in volume; external: exponential from r_iv)
     if (nrad > 0) radial_probs(T, s_r, s_F, s_dF, s_pint, s_pext, s_dpext);
     __syncthreads();
-    if (mv && tid == 0) {
+    if (mv && tid < NES) {   // internal and external vetoed events of slice tid
         double aint = 0.0, aext = 0.0;
         for (int k = 0; k < K; ++k) {
-            const double A = s_rs[k] * s_SA[k];
+            const double A = s_rs[k] * s_SA[tid][k];
             if (nrad > 0 && T.rad_class[k] == BX_RAD_EXTERNAL) aext += A; else aint += A;
         }
-        s_misc[0] = aint;
-        s_misc[1] = aext;
+        s_aint[tid] = aint;
+        s_aext[tid] = aext;
     }
     __syncthreads();
-    for (int b = tid; b < nrad; b += MID_THREADS) s_mur[b] = s_misc[0] * s_pint[b] + s_misc[1] * s_pext[b];
-    for (int j = tid; j < npsd; j += MID_THREADS) {
+    for (int b = tid; b < nradS; b += MID_THREADS) {
+        const int q = b / nrad, r = b - q * nrad;
+        s_mur[b] = s_aint[q] * s_pint[r] + s_aext[q] * s_pext[r];
+    }
+    for (int j = tid; j < npsdS; j += MID_THREADS) {
+        const int q = j / npsd, r = j - q * npsd;
         double s = 0.0;
-        for (int k = 0; k < K; ++k) s += s_rs[k] * s_SA[k] * T.psd[(size_t)k * npsd + j];
+        for (int k = 0; k < K; ++k) s += s_rs[k] * s_SA[q][k] * T.psd[(size_t)k * npsd + r];
         s_mup[j] = s;
     }
     __syncthreads();
@@ -278,8 +285,8 @@ __global__ void __launch_bounds__(MID_THREADS, (sizeof(TV) == sizeof(float) && !
         const double n = T.cnt[b];
         double mu;
         if (b < nwin) mu = muw[b];
-        else if (b < nwin + nrad) mu = s_mur[b - nwin];
-        else mu = s_mup[b - nwin - nrad];
+        else if (b < nwin + nradS) mu = s_mur[b - nwin];
+        else mu = s_mup[b - nwin - nradS];
         double term, wb = 1.0;
         if (n == 0.0) term = mu;
         else if (!(mu > 0.0 && isfinite(mu))) { dom = 1; term = 0.0; }
@@ -296,8 +303,8 @@ __global__ void __launch_bounds__(MID_THREADS, (sizeof(TV) == sizeof(float) && !
                 const int h = b / nw, j = b % nw;
                 wvT[b] = (TV)wb;
                 geps += wb * ((double)puT[b] - lam[h * M + m_lo + j]);
-            } else if (b < nwin + nrad) s_wr[b - nwin] = wb;
-            else s_wp[b - nwin - nrad] = wb;
+            } else if (b < nwin + nradS) s_wr[b - nwin] = wb;
+            else s_wp[b - nwin - nradS] = wb;
         }
     }
     // merge the compensated partial sums
@@ -333,22 +340,21 @@ __global__ void __launch_bounds__(MID_THREADS, (sizeof(TV) == sizeof(float) && !
     }
 
     // ---- adjoint inputs
-    // beta_k = dNLL/dA_k = sum_rho w_rad p_k[rho] + sum_j w_psd q_k[j]
+    // beta_q,k = dNLL/dA_k^(q) = sum_rho w_rad,q p_k[rho] + sum_j w_psd,q q_k[j], per energy slice q
     if (mv) {
-        for (int k = wid; k < K; k += MID_WARPS) {
+        for (int qk = wid; qk < NES * K; qk += MID_WARPS) {
+            const int q = qk / K, k = qk - q * K;
             double s = 0.0;
             const bool ext = nrad > 0 && T.rad_class[k] == BX_RAD_EXTERNAL;
-            for (int b = lane; b < nrad; b += 32) s += s_wr[b] * (ext ? s_pext[b] : s_pint[b]);
-            for (int j = lane; j < npsd; j += 32) s += s_wp[j] * T.psd[(size_t)k * npsd + j];
+            for (int b = lane; b < nrad; b += 32) s += s_wr[q * nrad + b] * (ext ? s_pext[b] : s_pint[b]);
+            for (int j = lane; j < npsd; j += 32) s += s_wp[q * npsd + j] * T.psd[(size_t)k * npsd + j];
             s = warp_sum(s);
-            if (lane == 0) s_beta[k] = s;
+            if (lane == 0) s_beta[q][k] = s;
         }
-    } else if (tid < K) {
-        s_beta[tid] = 0.0;
     }
     __syncthreads();
     // pile-up-correlated weights wt_h[m] (adjoint of Eq. 2) and G_W[m], written per row
-    TV* rowW = static_cast<TV*>(w.rowW) + (size_t)item * 3 * w.Mpad;
+    TV* rowW = static_cast<TV*>(w.rowW) + (size_t)item * (2 + w.nes) * w.Mpad;
     TV* wt = lamT;   // lambda copies are no longer needed
     for (int idx = tid; idx < H * M; idx += MID_THREADS) {
         const int h = idx / M, m = idx % M;
@@ -361,10 +367,12 @@ __global__ void __launch_bounds__(MID_THREADS, (sizeof(TV) == sizeof(float) && !
         wt[idx] = val;
         rowW[(size_t)h * w.Mpad + m] = val;
     }
-    for (int m = tid; m < M; m += MID_THREADS) {
-        if (H == 1) rowW[(size_t)w.Mpad + m] = (TV)0;
-        const double inW = m >= m_lo ? 1.0 : 0.0;
-        rowW[(size_t)2 * w.Mpad + m] = mv ? (TV)((1.0 - eps) * inW + eps * T.Gg[m]) : (TV)0;
+    for (int j = tid; j < w.nes * M; j += MID_THREADS) {   // G_W,q[m] of every slice q (0 beyond the toy's)
+        const int q = j / M, m = j - q * M;
+        if (q == 0 && H == 1) rowW[(size_t)w.Mpad + m] = (TV)0;
+        const double inW = q < NES && m >= T.es_lo[q] && m < T.es_hi[q] ? 1.0 : 0.0;
+        rowW[(size_t)(2 + q) * w.Mpad + m] =
+            mv && q < NES ? (TV)((1.0 - eps) * inW + eps * T.Gg[(size_t)q * M + m]) : (TV)0;
     }
     __syncthreads();
     // rate gradient, part through the spectra: sum_h c_{h,k} sum_m wt_h[m] v_k[m]; only the
@@ -390,26 +398,30 @@ __global__ void __launch_bounds__(MID_THREADS, (sizeof(TV) == sizeof(float) && !
         s_gr[tid] = 0.0;
     }
     __syncthreads();
-    double* coef = w.coef + (size_t)item * 3 * KMAX;
+    double* coef = w.coef + (size_t)item * (2 + w.nes) * KMAX;
     if (tid < K) {
         const int k = tid;
         const double t = T.tag ? T.tag[k] : 0.0, csub = T.tag ? 1.0 - t : 1.0;
-        gmid[k] = csub * s_gr[k] + (H == 2 ? t * s_gr[KMAX + k] : 0.0) + (mv ? s_beta[k] * csub * s_SA[k] : 0.0);
+        double gk = csub * s_gr[k] + (H == 2 ? t * s_gr[KMAX + k] : 0.0);
+        for (int q = 0; mv && q < NES; ++q) gk += s_beta[q][k] * csub * s_SA[q][k];
+        gmid[k] = gk;
         coef[k] = s_rs[k];
         coef[KMAX + k] = s_rt[k];
-        coef[2 * KMAX + k] = mv ? s_beta[k] * s_rs[k] : 0.0;
     }
     if (tid >= K && tid < KMAX) {
         coef[tid] = 0.0;
         coef[KMAX + tid] = 0.0;
-        coef[2 * KMAX + tid] = 0.0;
+    }
+    for (int j = tid; j < w.nes * KMAX; j += MID_THREADS) {
+        const int q = j / KMAX, k = j - q * KMAX;
+        coef[(size_t)(2 + q) * KMAX + k] = mv && q < NES && k < K ? s_beta[q][k] * s_rs[k] : 0.0;
     }
     if (tid == 0) {
         double ge = s_misc[2];
-        if (mv)
-            for (int k = 0; k < K; ++k) ge += s_beta[k] * s_rs[k] * s_SA[KMAX + k];
+        for (int q = 0; mv && q < NES; ++q)
+            for (int k = 0; k < K; ++k) ge += s_beta[q][k] * s_rs[k] * s_SA[q][KMAX + k];
         double gs = 0.0;
-        for (int b = 0; b < nrad; ++b) gs += s_wr[b] * s_misc[1] * s_dpext[b];
+        for (int b = 0; b < nradS; ++b) gs += s_wr[b] * s_aext[b / nrad] * s_dpext[b % nrad];
         for (int j = K; j < K + 5; ++j) gmid[j] = 0.0;
         gmid[K + 5] = ge;
         gmid[K + 6] = gs;
@@ -528,12 +540,16 @@ __device__ __forceinline__ void bc_term_df(df n, df mu, Sum32& acc, float& wb) {
 // hands over lambda_h as FP32 pairs, the column stage the window masses aW; -lnL is a
 // compensated FP32 sum (TwoSum per term, merged across the block in FP64).  FP64 remains for
 // the radial and pulse-shape marginals (one value per bin, ~100 bins).
+// MES: several energy slices of the Eq. 4 terms (otherwise one, with compile-time strides).
+template <bool MES>
 __global__ void __launch_bounds__(MID_THREADS, 2) k_mid32(Work w, int want_grad, int want_mu) {
     extern __shared__ __align__(16) double dsm[];
     const int item = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const Toy& T = w.toys[w.toy_of[item]];
     const int K = T.K, M = T.M, nw = T.nw, m_lo = T.m_lo, L = T.L, H = T.has_tag ? 2 : 1;
-    const int nrad = T.n_rad, npsd = T.n_psd, nb = T.nb;
+    const int nrad = T.n_rad, npsd = T.n_psd, nb = T.nb, NES = MES ? T.n_es : 1;
+    const int WNES = MES ? w.nes : 1;   // slice stride of the workspace
+    const int nradS = NES * nrad, npsdS = NES * npsd;   // bins of all energy slices
     double* gmid = w.gmid + (size_t)item * PMAX;
     if (w.status[item]) {
         if (tid == 0) w.nll[item] = INFINITY;
@@ -558,7 +574,10 @@ __global__ void __launch_bounds__(MID_THREADS, 2) k_mid32(Work w, int want_grad,
     float2* colGW = reinterpret_cast<float2*>(wvP + 2 * wrow);   // [Next] G_W per column (8-byte aligned)
     float* coldG = reinterpret_cast<float*>(colGW + T.Next);     // [Next] dG_W/deps per column
 
-    __shared__ double s_rs[KMAX], s_rt[KMAX], s_SA[2 * KMAX], s_beta[KMAX];
+    // per energy slice q: s_SA[q][k] = sum v_k G_W,q, s_SA[q][KMAX + k] its d/deps; s_beta[q][k]
+    constexpr int XS = MES ? MAX_ES : 1;
+    __shared__ double s_rs[KMAX], s_rt[KMAX], s_SA[XS][2 * KMAX], s_beta[XS][KMAX];
+    __shared__ double s_aint[XS], s_aext[XS];
     __shared__ double s_pint[MAX_RAD], s_pext[MAX_RAD], s_dpext[MAX_RAD], s_mur[MAX_RAD], s_wr[MAX_RAD];
     __shared__ double s_F[MAX_RAD + 2], s_dF[MAX_RAD + 2];
     __shared__ double s_mup[MAX_PSD], s_wp[MAX_PSD];
@@ -606,15 +625,18 @@ __global__ void __launch_bounds__(MID_THREADS, 2) k_mid32(Work w, int want_grad,
     // products and sums in compensated FP32 (TwoProduct, TwoSum): the terms are non-negative
     // and the result is the exact sum to a few 1e-15 of its size.
     const bool mv = nrad > 0 || npsd > 0;
-    if (mv) {
-        const float* ap = static_cast<const float*>(w.apart) + (size_t)item * w.max_tiles * 2 * w.Npad;
-        const float2* aW2 = reinterpret_cast<const float2*>(w.aW + (size_t)item * w.Npad);
+    // one pass per energy slice q (its own masses aW_q and column sums a_q), the per-column
+    // buffers reused
+    for (int qs = 0; mv && qs < NES; ++qs) {
+        const float* ap = static_cast<const float*>(w.apart) + (size_t)item * w.max_tiles * 2 * WNES * w.Npad;
+        const float2* aW2 = reinterpret_cast<const float2*>(w.aW + ((size_t)item * WNES + qs) * w.Npad);
         for (int i = tid; i < T.Next; i += MID_THREADS) {   // every column of every quenching group
             const int2* tcols = w.tile_cols + ((size_t)item * MAX_SETS + (T.n_set > 1 ? i / T.Ncs : 0)) * MAX_TILES;
             float agf = 0.f;   // a few positive terms; enters G_W with weight eps
             for (int t = 0; t < T.n_tiles; ++t) {
                 const int2 cr = tcols[t];
-                if (i >= cr.x && i < cr.y) agf += ap[((size_t)t * 2) * w.Npad + i] + ap[((size_t)t * 2 + 1) * w.Npad + i];
+                if (i >= cr.x && i < cr.y)
+                    agf += ap[(((size_t)t * 2) * WNES + qs) * w.Npad + i] + ap[(((size_t)t * 2 + 1) * WNES + qs) * w.Npad + i];
             }
             const float2 a2 = aW2[i];
             const df aw{a2.x, a2.y};
@@ -637,29 +659,34 @@ __global__ void __launch_bounds__(MID_THREADS, 2) k_mid32(Work w, int want_grad,
             }
             a0 = a0.warp_reduce();
             a1 = a1.warp_reduce();
-            if (lane == 0) {   // s_SA[k] = sum v G_W, s_SA[KMAX + k] = sum v dG_W/deps
-                s_SA[k] = (double)a0.s + (double)a0.c;
-                s_SA[KMAX + k] = (double)a1.s + (double)a1.c;
+            if (lane == 0) {   // s_SA[q][k] = sum v G_W,q, s_SA[q][KMAX + k] = sum v dG_W,q/deps
+                s_SA[qs][k] = (double)a0.s + (double)a0.c;
+                s_SA[qs][KMAX + k] = (double)a1.s + (double)a1.c;
             }
         }
+        __syncthreads();   // colGW, coldG are reused by the next slice
     }
     // radial bin probabilities (internal: uniform in volume; external: exponential from r_iv)
     if (nrad > 0) radial_probs(T, s_r, s_F, s_dF, s_pint, s_pext, s_dpext);
     __syncthreads();
-    if (mv && tid == 0) {
+    if (mv && tid < NES) {   // internal and external vetoed events of slice tid
         double aint = 0.0, aext = 0.0;
         for (int k = 0; k < K; ++k) {
-            const double A = s_rs[k] * s_SA[k];
+            const double A = s_rs[k] * s_SA[tid][k];
             if (nrad > 0 && T.rad_class[k] == BX_RAD_EXTERNAL) aext += A; else aint += A;
         }
-        s_misc[0] = aint;
-        s_misc[1] = aext;
+        s_aint[tid] = aint;
+        s_aext[tid] = aext;
     }
     __syncthreads();
-    for (int b = tid; b < nrad; b += MID_THREADS) s_mur[b] = s_misc[0] * s_pint[b] + s_misc[1] * s_pext[b];
-    for (int j = tid; j < npsd; j += MID_THREADS) {
+    for (int b = tid; b < nradS; b += MID_THREADS) {
+        const int q = MES ? b / nrad : 0, r = b - q * nrad;
+        s_mur[b] = s_aint[q] * s_pint[r] + s_aext[q] * s_pext[r];
+    }
+    for (int j = tid; j < npsdS; j += MID_THREADS) {
+        const int q = MES ? j / npsd : 0, r = j - q * npsd;
         double v = 0.0;
-        for (int k = 0; k < K; ++k) v += s_rs[k] * s_SA[k] * T.psd[(size_t)k * npsd + j];
+        for (int k = 0; k < K; ++k) v += s_rs[k] * s_SA[q][k] * T.psd[(size_t)k * npsd + r];
         s_mup[j] = v;
     }
     __syncthreads();
@@ -677,7 +704,7 @@ __global__ void __launch_bounds__(MID_THREADS, 2) k_mid32(Work w, int want_grad,
             const float2 m2 = muw[b];
             mu = df{m2.x, m2.y};
         } else {
-            mu = df_from(b < nwin + nrad ? s_mur[b - nwin] : s_mup[b - nwin - nrad]);
+            mu = df_from(b < nwin + nradS ? s_mur[b - nwin] : s_mup[b - nwin - nradS]);
         }
         float wb = 1.0f;
         if (n.h == 0.f) {
@@ -694,8 +721,8 @@ __global__ void __launch_bounds__(MID_THREADS, 2) k_mid32(Work w, int want_grad,
                 const int h = b / nw, j = b % nw;
                 wvP[h * wrow + PAD_WV + j] = wb;
                 geps = fmaf(wb, puT[b] - lamP[h * lrow + PAD_LAM + m_lo + j], geps);
-            } else if (b < nwin + nrad) s_wr[b - nwin] = (double)wb;
-            else s_wp[b - nwin - nrad] = (double)wb;
+            } else if (b < nwin + nradS) s_wr[b - nwin] = (double)wb;
+            else s_wp[b - nwin - nradS] = (double)wb;
         }
     }
     acc = acc.warp_reduce();
@@ -725,23 +752,22 @@ __global__ void __launch_bounds__(MID_THREADS, 2) k_mid32(Work w, int want_grad,
     }
 
     // ---- adjoint inputs
-    // beta_k = dNLL/dA_k = sum_rho w_rad p_k[rho] + sum_j w_psd q_k[j]
+    // beta_q,k = dNLL/dA_k^(q) = sum_rho w_rad,q p_k[rho] + sum_j w_psd,q q_k[j], per energy slice q
     if (mv) {
-        for (int k = wid; k < K; k += MID_WARPS) {
+        for (int qk = wid; qk < NES * K; qk += MID_WARPS) {
+            const int q = MES ? qk / K : 0, k = qk - q * K;
             double v = 0.0;
             const bool ext = nrad > 0 && T.rad_class[k] == BX_RAD_EXTERNAL;
-            for (int b = lane; b < nrad; b += 32) v += s_wr[b] * (ext ? s_pext[b] : s_pint[b]);
-            for (int j = lane; j < npsd; j += 32) v += s_wp[j] * T.psd[(size_t)k * npsd + j];
+            for (int b = lane; b < nrad; b += 32) v += s_wr[q * nrad + b] * (ext ? s_pext[b] : s_pint[b]);
+            for (int j = lane; j < npsd; j += 32) v += s_wp[q * npsd + j] * T.psd[(size_t)k * npsd + j];
             v = warp_sum(v);
-            if (lane == 0) s_beta[k] = v;
+            if (lane == 0) s_beta[q][k] = v;
         }
-    } else if (tid < K) {
-        s_beta[tid] = 0.0;
     }
     __syncthreads();
     // pile-up-correlated weights wt_h[m] (adjoint of Eq. 2) and G_W[m], per row, in FP32:
     // wt_h[m] = (1 - eps) w_h[m] [m in W] + eps sum_d g[d] w_h[m + d]
-    float* rowW = static_cast<float*>(w.rowW) + (size_t)item * 3 * w.Mpad;
+    float* rowW = static_cast<float*>(w.rowW) + (size_t)item * (2 + WNES) * w.Mpad;
     const int ngm = (M + PR - 1) / PR;
     for (int q = tid; q < H * ngm; q += MID_THREADS) {
         const int h = q / ngm, m0 = (q % ngm) * PR, base = m0 - m_lo;   // window index at d = 0
@@ -758,31 +784,40 @@ __global__ void __launch_bounds__(MID_THREADS, 2) k_mid32(Work w, int want_grad,
             }
         }
     }
-    for (int m = tid; m < M; m += MID_THREADS) {
-        if (H == 1) rowW[(size_t)w.Mpad + m] = 0.f;
-        rowW[(size_t)2 * w.Mpad + m] = mv ? fmaf(epsf, T.Gg32[m], m >= m_lo ? omef : 0.f) : 0.f;
+    for (int j = tid; j < WNES * M; j += MID_THREADS) {   // G_W,q[m] of every slice q (0 beyond the toy's)
+        const int q = MES ? j / M : 0, m = j - q * M;
+        if (q == 0 && H == 1) rowW[(size_t)w.Mpad + m] = 0.f;
+        rowW[(size_t)(2 + q) * w.Mpad + m] =
+            mv && q < NES ? fmaf(epsf, T.Gg32[(size_t)q * M + m], m >= T.es_lo[q] && m < T.es_hi[q] ? omef : 0.f) : 0.f;
     }
     // the rate gradient through the spectra comes from the adjoint kernel
-    double* coef = w.coef + (size_t)item * 3 * KMAX;
+    double* coef = w.coef + (size_t)item * (2 + WNES) * KMAX;
     if (tid < K) {
         const int k = tid;
         const double csub = T.tag ? 1.0 - T.tag[k] : 1.0;
-        gmid[k] = mv ? s_beta[k] * csub * s_SA[k] : 0.0;
+        double gk = 0.0;
+        for (int q = 0; mv && q < NES; ++q) gk += s_beta[q][k] * csub * s_SA[q][k];
+        gmid[k] = gk;
         coef[k] = s_rs[k];
         coef[KMAX + k] = s_rt[k];
-        coef[2 * KMAX + k] = mv ? s_beta[k] * s_rs[k] : 0.0;
     }
     if (tid >= K && tid < KMAX) {
         coef[tid] = 0.0;
         coef[KMAX + tid] = 0.0;
-        coef[2 * KMAX + tid] = 0.0;
+    }
+    for (int j = tid; j < WNES * KMAX; j += MID_THREADS) {
+        const int q = MES ? j / KMAX : 0, k = j - q * KMAX;
+        coef[(size_t)(2 + q) * KMAX + k] = mv && q < NES && k < K ? s_beta[q][k] * s_rs[k] : 0.0;
     }
     if (tid == 0) {
         double ge = s_misc[2];
-        if (mv)
-            for (int k = 0; k < K; ++k) ge += s_beta[k] * s_rs[k] * s_SA[KMAX + k];
+        for (int q = 0; mv && q < NES; ++q)
+            for (int k = 0; k < K; ++k) ge += s_beta[q][k] * s_rs[k] * s_SA[q][KMAX + k];
         double gs = 0.0;
-        for (int b = 0; b < nrad; ++b) gs += s_wr[b] * s_misc[1] * s_dpext[b];
+        for (int b = 0; b < nradS; ++b) {
+            const int q = MES ? b / nrad : 0;
+            gs += s_wr[b] * s_aext[q] * s_dpext[b - q * nrad];
+        }
         for (int j = K; j < K + 5; ++j) gmid[j] = 0.0;
         gmid[K + 5] = ge;
         gmid[K + 6] = gs;
@@ -817,13 +852,16 @@ cudaError_t launch_mid(const Work& w, int n, int Mmax, int nwmax, int Lmax, int 
     const size_t smem32 = (size_t)2 * nwmax * sizeof(float2) +
                           (size_t)(mid32_gn(Lmax) + 2 * mid32_lrow(Mmax) + 2 * nwmax + 2 * mid32_wrow(nwmax)) * sizeof(float) +
                           (size_t)w.Npad * (sizeof(float2) + sizeof(float));
-    static size_t set32 = 0;
-    if (smem32 > set32) {
-        const cudaError_t e = cudaFuncSetAttribute(k_mid32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32);
+    static size_t set32[2] = {0, 0};
+    const int mes = w.nes > 1 ? 1 : 0;   // several energy slices of the Eq. 4 terms
+    if (smem32 > set32[mes]) {
+        const cudaError_t e = cudaFuncSetAttribute(mes ? k_mid32<true> : k_mid32<false>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32);
         if (e != cudaSuccess) return e;
-        set32 = smem32;
+        set32[mes] = smem32;
     }
-    k_mid32<<<n, MID_THREADS, smem32, s>>>(w, want_grad, want_mu);
+    if (mes) k_mid32<true><<<n, MID_THREADS, smem32, s>>>(w, want_grad, want_mu);
+    else k_mid32<false><<<n, MID_THREADS, smem32, s>>>(w, want_grad, want_mu);
     return cudaGetLastError();
 }
 

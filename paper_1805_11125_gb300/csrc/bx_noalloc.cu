@@ -107,6 +107,9 @@ extern "C" int bx_spectra_noalloc(int n_grid, double e_max, int n_species, const
     T.M = m_hi;
     T.m_lo = 0;
     T.nw = m_hi;
+    T.n_es = 1;   // one energy slice: the whole axis
+    T.es_lo[0] = 0;
+    T.es_hi[0] = m_hi;
     T.L = 1;
     T.has_tag = tag_frac ? 1 : 0;
     T.nb = m_hi * (1 + T.has_tag);
@@ -122,6 +125,7 @@ extern "C" int bx_spectra_noalloc(int n_grid, double e_max, int n_species, const
 
     Work w{};
     w.cap = 1;
+    w.nes = 1;
     w.Npad = ((n_grid + 127) / 128) * 128;
     w.Mpad = m_hi;
     w.pstride = T.P;

@@ -3,8 +3,8 @@
 // k_setup_toy (once per toy at model creation): FP32 copies of the shapes, the shapes
 //   split in three (hi on a grid per species row and k-block, TF32 mid and lo) in the
 //   tensor-core operand layout, FP32 pile-up spectrum,
-//   and the pile-up window marginal Gg[m] = sum_{m' in W, 0 <= m'-m < L} g[m'-m] (FP64, then
-//   an FP32 copy after it).
+//   and the pile-up window marginal of every energy slice W_s of the Eq. 4 terms,
+//   Gg_s[m] = sum_{m' in W_s, 0 <= m'-m < L} g[m'-m] (FP64, then an FP32 copy after them).
 // k_prep (FP64 model) and k_prep32 (mixed-precision modes), once per item: Eq. 1's Birks map
 //   and resolution on the true-energy grid (block-wide prefix sum), the column normalisation
 //   1/Phi(mu/sigma), the window masses, the rate-weighted spectra of Eq. 3 and the band limits
@@ -47,13 +47,14 @@ __global__ void k_setup_toy(Toy t, float* shapes32, float* S_tiles, float* g32, 
         }
     }
     for (int d = tid; d < t.L; d += nt) g32[d] = (float)t.g[d];
-    for (int m = tid; m < t.M; m += nt) {
+    for (int j = tid; j < t.n_es * t.M; j += nt) {   // one row per energy slice
+        const int q = j / t.M, m = j % t.M;
         double s = 0.0;
-        const int lo = m > t.m_lo ? m : t.m_lo;
-        const int hi = min(m + t.L - 1, t.M - 1);
+        const int lo = max(m, t.es_lo[q]);
+        const int hi = min(m + t.L - 1, t.es_hi[q] - 1);
         for (int mp = lo; mp <= hi; ++mp) s += t.g[mp - m];
-        Gg[m] = s;
-        reinterpret_cast<float*>(Gg + t.M)[m] = (float)s;
+        Gg[j] = s;
+        reinterpret_cast<float*>(Gg + (size_t)t.n_es * t.M)[j] = (float)s;
     }
 }
 
@@ -139,13 +140,13 @@ __global__ void __launch_bounds__(256) k_prep(Work w) {
     if (tid == 0 && (!(LY > 0.0) || ((T.n_rad > 0 || T.n_r2 > 0) && !(th[K + 6] > 0.0)))) s_bad = 1;
 
     const double w_ = T.w;
-    const double z_lo = T.m_lo * w_, z_hi = M * w_;
     const float wf = (float)w_, inv_wf = (float)(1.0 / w_), bandf = (float)w.band;
     const float e_min = -2.0f * wf, e_max = (M + 2.0f) * wf;
     Col64* col = w.col64 + (size_t)item * w.Npad;
     double2* cq = w.colq + (size_t)item * w.Npad;
     double2* cs = w.colS + (size_t)item * w.Npad;
-    double* aW = w.aW + (size_t)item * w.Npad;
+    double* aW = w.aW + (size_t)item * w.nes * w.Npad;   // [nes][Npad]: one mass per energy slice
+    const int NES = T.n_es;
     int2* cr = w.colr + (size_t)item * w.Npad;
     int bad = 0;
     unsigned long long inband = 0;
@@ -182,7 +183,7 @@ __global__ void __launch_bounds__(256) k_prep(Work w) {
                 col[ie] = Col64{0.0, 1.0, 0.0, 0.0};
                 cq[ie] = make_double2(0.0, 0.0);
                 cs[ie] = make_double2(0.0, 0.0);
-                aW[ie] = 0.0;
+                for (int q = 0; q < NES; ++q) aW[(size_t)q * w.Npad + ie] = 0.0;
                 cr[ie] = make_int2(0, 0);
             }
         }
@@ -215,8 +216,10 @@ __global__ void __launch_bounds__(256) k_prep(Work w) {
                 stag += t * sk;
             }
             cs[ie] = make_double2(ssub, stag);
-            // window mass of the column (Eq. 4 marginals)
-            aW[ie] = gauss_mass((z_lo - mu) * isig, (z_hi - mu) * isig) * norm;
+            // mass of the column in each energy slice of the window (Eq. 4 marginals)
+            for (int q = 0; q < NES; ++q)
+                aW[(size_t)q * w.Npad + ie] =
+                    gauss_mass((T.es_lo[q] * w_ - mu) * isig, (T.es_hi[q] * w_ - mu) * isig) * norm;
             // response band: rows whose bin lies within band * sigma of mu
             const float muf = (float)mu, sigf = (float)sig;
             const float lo_e = fminf(fmaxf(muf - bandf * sigf, e_min), e_max);
@@ -258,7 +261,7 @@ __global__ void __launch_bounds__(256) k_prep(Work w) {
         col[i] = Col64{0.0, 1.0, 0.0, 0.0};
         cq[i] = make_double2(0.0, 0.0);
         cs[i] = make_double2(0.0, 0.0);
-        aW[i] = 0.0;
+        for (int q = 0; q < NES; ++q) aW[(size_t)q * w.Npad + i] = 0.0;
         cr[i] = make_int2(0, 0);
     }
     if (bad) s_bad = 1;
@@ -279,6 +282,20 @@ constexpr float Z_F32 = 3.0f;
 constexpr float INV_SQRT_2PI_F = 0.39894228f;
 __device__ __forceinline__ float upper_tail32(float x) {
     return x >= (float)Q_CUT ? 0.f : 0.5f * erfcf(x * 0.70710678f);
+}
+
+// Gaussian mass of N(mu, sigma) between the npe edges e_lo < e_hi, as a double-float, from FP32
+// tails on the side away from the mean: the masses enter only the Eq. 4 marginals, where an
+// FP32 tail's rounding (<= ~6e-8 of the mass) averages over the several hundred columns near
+// a slice's edges to ~1e-9 of a marginal bin.
+__device__ __forceinline__ df slice_mass32(df e_lo, df e_hi, df mu, df isig) {
+    const df zad = df_mul(df_add(e_lo, df_neg(mu)), isig), zbd = df_mul(df_add(e_hi, df_neg(mu)), isig);
+    const float za = zad.h, zb = zbd.h;
+    if (za <= -(float)Q_CUT && zb >= (float)Q_CUT) return df{1.f, 0.f};
+    if (za >= (float)Q_CUT || zb <= -(float)Q_CUT) return df{0.f, 0.f};
+    if (za >= 0.f) return df_two_sum(upper_tail32(za), -upper_tail32(zb));
+    if (zb <= 0.f) return df_two_sum(upper_tail32(-zb), -upper_tail32(-za));
+    return df_add(df_two_sum(1.0f, -upper_tail32(zb)), df{-upper_tail32(-za), 0.f});
 }
 
 // Block-wide exclusive scan of two double-floats (256 threads); ta, tb receive the totals.
@@ -349,7 +366,7 @@ __global__ void __launch_bounds__(256, 3) k_prep32(Work w) {
     __shared__ int s_bad;
     __shared__ int s_tlo[MAX_SETS][MAX_TILES], s_thi[MAX_SETS][MAX_TILES], s_rlo[MAX_CB], s_rhi[MAX_CB];
     __shared__ float s_rate[4][KMAX];
-    __shared__ df s_par[11];   // LY, a, b, c, kB, dE, w S_EX2, 1/w, A's constant factor, window edges
+    __shared__ df s_par[10 + MAX_ES];   // LY, a, b, c, kB, dE, w S_EX2, 1/w, A's constant factor, slice edges
     if (tid == 0) s_bad = 0;
     for (int j = tid; j < MAX_SETS * MAX_TILES; j += blockDim.x) {
         s_tlo[j / MAX_TILES][j % MAX_TILES] = INT_MAX;
@@ -369,21 +386,22 @@ __global__ void __launch_bounds__(256, 3) k_prep32(Work w) {
         s_rate[2][tid] = rth;
         s_rate[3][tid] = (float)(rt - (double)rth);
     }
-    if (tid < 11) {
+    if (tid < 10 + T.n_es) {   // edges of the energy slices (npe): e_q = es_lo[q], e_S = es_hi[S - 1]
+        const int q = tid - 9;
         const double v = tid < 5    ? th[K + tid]
                          : tid == 5 ? T.dE
                          : tid == 6 ? T.w * S_EX2
                          : tid == 7 ? 1.0 / T.w
                          : tid == 8 ? 0.5 * INV_SQRT_2PI * GL_W_SCALE * T.w
-                         : tid == 9 ? T.m_lo * T.w
-                                    : T.M * T.w;
+                                    : (q < T.n_es ? T.es_lo[q] : T.es_hi[T.n_es - 1]) * T.w;
         s_par[tid] = df_from(v);
     }
     __syncthreads();
     if (tid < T.P && !isfinite(th[tid])) s_bad = 1;
     if (tid == 0 && (!(th[K] > 0.0) || ((T.n_rad > 0 || T.n_r2 > 0) && !(th[K + 6] > 0.0)))) s_bad = 1;
     const df LY = s_par[0], pa = s_par[1], pb = s_par[2], pc = s_par[3], kB = s_par[4], dE = s_par[5];
-    const df wS = s_par[6], iw = s_par[7], cAw = s_par[8], zlo = s_par[9], zhi = s_par[10];
+    const df wS = s_par[6], iw = s_par[7], cAw = s_par[8];
+    const int NES = T.n_es;
     const double w_ = T.w;
     const float wf = (float)w_, inv_wf = iw.h, bandf = (float)w.band;
     const float e_min = -2.0f * wf, e_max = (M + 2.0f) * wf;
@@ -392,7 +410,7 @@ __global__ void __launch_bounds__(256, 3) k_prep32(Work w) {
     float4* cf = w.colf + (size_t)item * w.Npad;
     ColG* cg = w.colg + (size_t)item * w.Npad;
     float2* cs32 = w.colS32 + (size_t)item * w.Npad;
-    float2* aW2 = reinterpret_cast<float2*>(w.aW + (size_t)item * w.Npad);   // FP32 pairs in this mode
+    float2* aW2 = reinterpret_cast<float2*>(w.aW + (size_t)item * w.nes * w.Npad);   // [nes][Npad] FP32 pairs
     int2* cr = w.colr + (size_t)item * w.Npad;
     const df gln{0.38729834f, (float)(0.38729833462074170 - (double)0.38729834f)};   // sqrt(3/5) / 2
     const df ln4{1.3862944f, (float)(1.3862943611198906 - (double)1.3862944f)};      // 2 ln 2
@@ -440,7 +458,7 @@ __global__ void __launch_bounds__(256, 3) k_prep32(Work w) {
                 cf[ie] = make_float4(0.f, 0.f, 0.f, 0.f);
                 cg[ie] = ColG{0.f, 0.f, 0.f, 0.f};
                 cs32[ie] = make_float2(0.f, 0.f);
-                aW2[ie] = make_float2(0.f, 0.f);
+                for (int q = 0; q < NES; ++q) aW2[(size_t)q * w.Npad + ie] = make_float2(0.f, 0.f);
                 cr[ie] = make_int2(0, 0);
             }
         }
@@ -507,20 +525,11 @@ __global__ void __launch_bounds__(256, 3) k_prep32(Work w) {
                 }
                 cs32[ie] = make_float2(df_mul(Ad, df_from(ssub)).h, df_mul(Ad, df_from(stag)).h);
             }
-            // window mass times 1/Phi, as an FP32 pair, from FP32 tails on the side away from the
-            // mean: the masses enter only the Eq. 4 marginals, where an FP32 tail's rounding
-            // (<= ~6e-8 of the mass) averages over the several hundred columns near the window's
-            // edges to ~1e-9 of a marginal bin
-            const df zad = df_mul(df_add(zlo, df_neg(mu)), isig), zbd = df_mul(df_add(zhi, df_neg(mu)), isig);
-            const float za = zad.h, zb = zbd.h;
-            df mass;
-            if (za <= -(float)Q_CUT && zb >= (float)Q_CUT) mass = df{1.f, 0.f};
-            else if (za >= (float)Q_CUT || zb <= -(float)Q_CUT) mass = df{0.f, 0.f};
-            else if (za >= 0.f) mass = df_two_sum(upper_tail32(za), -upper_tail32(zb));
-            else if (zb <= 0.f) mass = df_two_sum(upper_tail32(-zb), -upper_tail32(-za));
-            else mass = df_add(df_two_sum(1.0f, -upper_tail32(zb)), df{-upper_tail32(-za), 0.f});
-            const df aw = df_mul(mass, normd);
-            aW2[ie] = make_float2(aw.h, aw.l);
+            // slice masses times 1/Phi, as FP32 pairs
+            for (int q = 0; q < NES; ++q) {   // one mass per energy slice
+                const df aw = df_mul(slice_mass32(s_par[9 + q], s_par[10 + q], mu, isig), normd);
+                aW2[(size_t)q * w.Npad + ie] = make_float2(aw.h, aw.l);
+            }
             // response band
             const float lo_e = fminf(fmaxf(mu.h - bandf * sig.h, e_min), e_max);
             const float hi_e = fminf(fmaxf(mu.h + bandf * sig.h, e_min), e_max);
@@ -561,7 +570,7 @@ __global__ void __launch_bounds__(256, 3) k_prep32(Work w) {
         cf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         cg[i] = ColG{0.f, 0.f, 0.f, 0.f};
         cs32[i] = make_float2(0.f, 0.f);
-        aW2[i] = make_float2(0.f, 0.f);
+        for (int q = 0; q < NES; ++q) aW2[(size_t)q * w.Npad + i] = make_float2(0.f, 0.f);
         cr[i] = make_int2(0, 0);
     }
     if (bad) s_bad = 1;

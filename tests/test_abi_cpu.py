@@ -141,3 +141,37 @@ def test_quenching_group_rejections_on_host():
     with pytest.raises(bx.BxError) as e:
         bx.Model(s2, precision=bx.BX_FP32)
     assert e.value.status == bx.BX_EINVAL and "2D" in str(e.value)
+
+
+def test_energy_slice_rejections_on_host():
+    """Energy slices of the Eq. 4 terms: at most four, edges from 0 to the window's end and
+    strictly rising, slices x bins within the marginal buffers, and more than one slice only
+    with BX_FP32 / BX_FP64 and without 2D histograms (all checked before any device is
+    touched)."""
+    import dataclasses
+    s = I.config("small_sliced")
+    nw = s.n_window
+
+    def make(edges, spec=s, prec=bx.BX_FP32):
+        t = dataclasses.replace(spec, eslices=np.array(edges, dtype=np.int32))
+        t = t.with_counts(np.ones(t.n_bins_total))
+        return bx.Model(t, precision=prec)
+
+    with pytest.raises(bx.BxError) as e:
+        make(s.eslices, prec=bx.BX_TF32X3)
+    assert e.value.status == bx.BX_EINVAL and "energy slices" in str(e.value)
+    for edges in ([1, 60, nw], [0, 60, nw - 1], [0, 60, 60, nw], [0, 140, 60, nw]):
+        with pytest.raises(bx.BxError) as e:
+            make(edges)
+        assert e.value.status == bx.BX_EINVAL and ("energy slices" in str(e.value) or "eslice_edges" in str(e.value))
+    with pytest.raises(bx.BxError) as e:
+        make([0, 40, 80, 120, 160, nw])
+    assert e.value.status == bx.BX_EINVAL and "n_eslice" in str(e.value)
+    wide = dataclasses.replace(s, n_rad=100, rad_class=s.rad_class)
+    with pytest.raises(bx.BxError) as e:
+        make([0, 60, 140, nw], spec=wide)
+    assert e.value.status == bx.BX_EINVAL
+    s2 = I.config("small_2d")
+    with pytest.raises(bx.BxError) as e:
+        make([0, 50, s2.n_window], spec=s2)
+    assert e.value.status == bx.BX_EINVAL and "2D" in str(e.value)
