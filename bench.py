@@ -246,7 +246,8 @@ def run_ours(args):
         if args.toys > 0:
             fits["batched_toys"] = toy_fits(bx, I, args.toys, stream)
         disc = discrimination_leg(bx, I, stream, B=args.batch2d) if args.batch2d > 0 else None
-        fits["quenched"] = quenched_leg(bx, I, stream, B=args.batch) if args.quenched else None
+        fits["quenched"] = variant_leg(bx, I, "quenched", QUENCHED, stream, B=args.batch) if args.quenched else None
+        fits["sliced"] = variant_leg(bx, I, "sliced", SLICED, stream, B=args.batch) if args.sliced else None
     if rank != 0:
         return
     report(args, ws, B, total_ms, value, stage_ms, n_evals, entries, e2e, fp64_value, tc_value, clk, fits, disc)
@@ -390,12 +391,19 @@ def discrimination_leg(bx, I, stream, B=256, steps=5):
             "fit": {"wall_s": fit_s, "status": int(st), "evals": int(info[0]["n_evals"])}}
 
 
-def quenched_leg(bx, I, stream, B=1024, steps=5):
-    """Species-specific quenching (the alpha species at 2.3 MeV true energy, quenched with
-    150 kB; its own Birks map and response columns): -lnL + gradient evaluations/s of the
-    multivariate model with this response at the main leg's batch, FP32, and one FP32 fit."""
+QUENCHED = ("multivariate with species-specific quenching (alpha at 2.3 MeV, 150 kB): 2 quenching "
+            "groups of 2000 response columns")
+SLICED = ("multivariate with the radial and pulse-shape terms in 3 energy slices (100-250, 250-500, "
+          "500-1000 npe): 3 x (60 radial + 50 pulse-shape) bins")
+
+
+def variant_leg(bx, I, name, workload, stream, B=1024, steps=5):
+    """A variant of the multivariate model (species-specific quenching: the alpha species at
+    2.3 MeV true energy quenched with 150 kB, with its own Birks map and response columns; or
+    the Eq. 4 terms in several energy slices): -lnL + gradient evaluations/s at the main leg's
+    batch, FP32, and one FP32 fit."""
     import torch
-    s = make_dataset(bx, I, I.config("quenched"), seed=0)
+    s = make_dataset(bx, I, I.config(name), seed=0)
     m = bx.Model(s, precision=bx.BX_FP32, max_batch=B, stream=stream)
     pts = I.parameter_points(s.theta_true, B, rel=0.02, seed=410, free=s.default_free())
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -432,8 +440,7 @@ def quenched_leg(bx, I, stream, B=1024, steps=5):
     _, info, st = mf.fit(th0)
     fit_s = time.perf_counter() - t0
     mf.close()
-    return {"workload": "multivariate with species-specific quenching (alpha at 2.3 MeV, 150 kB): 2 quenching "
-                        "groups of 2000 response columns", "global_batch": B,
+    return {"workload": workload, "global_batch": B,
             "value": B * steps / (total / 1e3), "unit": "evals/s", "ms_per_step": total / steps,
             "stage_ms_per_launch": {k: round(v, 4) for k, v in per.items()},
             "fit": {"wall_s": fit_s, "status": int(st), "evals": int(info[0]["n_evals"])}}
@@ -509,6 +516,7 @@ def main():
     ap.add_argument("--toys", type=int, default=4096, help="batched toy fits in the fit leg (0: none)")
     ap.add_argument("--batch2d", type=int, default=256, help="batch of the 2D-model leg (0: none)")
     ap.add_argument("--quenched", type=int, default=1, help="species-quenching leg (0: none)")
+    ap.add_argument("--sliced", type=int, default=1, help="energy-sliced Eq. 4 leg (0: none)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -207,21 +207,29 @@ __global__ void __launch_bounds__(BCOLS, 7) k_bwd_f32(Work w) {
     }
     __syncthreads();
     // dNLL/dR[m,i] = Ssub wt_sub[m] + Stag wt_tag[m] + sum_q SA_q G_W,q[m]: the species sums in FP32
-    float Ssub = 0.f, Stag = 0.f, SA = 0.f, SAq[MES ? MAX_ES : 1];
+    float Ssub = 0.f, Stag = 0.f, SA = 0.f;
+    float SAq[MAX_ES] = {0.f, 0.f, 0.f, 0.f};   // MES: one sum per energy slice
+    if constexpr (MES) {
+        if (ok)
+            for (int k = 0; k < T.K; ++k) {
+                if (!in_group<MULTI>(T, k, grp)) continue;
+                const float sk = T.shapes32[(size_t)k * T.N + ig];
+                Ssub = fmaf(s_coef[0][k], sk, Ssub);
+                Stag = fmaf(s_coef[1][k], sk, Stag);
 #pragma unroll
-    for (int q = 0; q < (MES ? MAX_ES : 1); ++q) SAq[q] = 0.f;
-    if (ok)
-        for (int k = 0; k < T.K; ++k) {
-            if (!in_group<MULTI>(T, k, grp)) continue;
-            const float sk = T.shapes32[(size_t)k * T.N + ig];
-            Ssub = fmaf(s_coef[0][k], sk, Ssub);
-            Stag = fmaf(s_coef[1][k], sk, Stag);
-            if (!MES) SA = fmaf(s_coef[2][k], sk, SA);
-            else
-#pragma unroll
-                for (int q = 0; q < (MES ? MAX_ES : 1); ++q)
+                for (int q = 0; q < MAX_ES; ++q)
                     if (q < NES) SAq[q] = fmaf(s_coef[2 + q][k], sk, SAq[q]);
-        }
+            }
+    } else {
+        if (ok)
+            for (int k = 0; k < T.K; ++k) {
+                if (!in_group<MULTI>(T, k, grp)) continue;
+                const float sk = T.shapes32[(size_t)k * T.N + ig];
+                Ssub = fmaf(s_coef[0][k], sk, Ssub);
+                Stag = fmaf(s_coef[1][k], sk, Stag);
+                SA = fmaf(s_coef[2][k], sk, SA);
+            }
+    }
     const float4 cf = ok ? w.colf[(size_t)item * w.Npad + i] : make_float4(0.f, 0.f, 0.f, 0.f);
     const ColG cg = ok ? w.colg[(size_t)item * w.Npad + i] : ColG{0.f, 0.f, 0.f, 0.f};
     const AdjCol ac = adj_col(cf, cg);
@@ -244,26 +252,31 @@ __global__ void __launch_bounds__(BCOLS, 7) k_bwd_f32(Work w) {
                 sW[wq][0][j] = rw[s0 + j];
                 sW[wq][1][j] = rw[(size_t)w.Mpad + s0 + j];
                 sW[wq][2][j] = rw[(size_t)2 * w.Mpad + s0 + j];
-                if (MES)
+                if constexpr (MES)
                     for (int q = 1; q < NES; ++q) sW[wq][2 + q][j] = rw[(size_t)(2 + q) * w.Mpad + s0 + j];
             }
             __syncwarp();
             if (ok) {
                 for (int j = 0; j < ns; j += ADJ_RUN) {
-                    auto wts = [&](int k, float& ws, float& wt, float& W) {
-                        ws = sW[wq][0][j + k];
-                        wt = sW[wq][1][j + k];
-                        if (!MES) {
-                            W = fmaf(ws, Ssub, fmaf(wt, Stag, sW[wq][2][j + k] * SA));
-                        } else {
+                    if constexpr (MES) {
+                        auto wts = [&](int k, float& ws, float& wt, float& W) {
+                            ws = sW[wq][0][j + k];
+                            wt = sW[wq][1][j + k];
                             float a = 0.f;
 #pragma unroll
-                            for (int q = 0; q < (MES ? MAX_ES : 1); ++q)
+                            for (int q = 0; q < MAX_ES; ++q)
                                 if (q < NES) a = fmaf(sW[wq][2 + q][j + k], SAq[q], a);
                             W = fmaf(ws, Ssub, fmaf(wt, Stag, a));
-                        }
-                    };
-                    adj_run((float)(s0 + j), min(ADJ_RUN, ns - j), cf, cg, ac, wts, bs);
+                        };
+                        adj_run((float)(s0 + j), min(ADJ_RUN, ns - j), cf, cg, ac, wts, bs);
+                    } else {
+                        auto wts = [&](int k, float& ws, float& wt, float& W) {
+                            ws = sW[wq][0][j + k];
+                            wt = sW[wq][1][j + k];
+                            W = fmaf(ws, Ssub, fmaf(wt, Stag, sW[wq][2][j + k] * SA));
+                        };
+                        adj_run((float)(s0 + j), min(ADJ_RUN, ns - j), cf, cg, ac, wts, bs);
+                    }
                 }
             }
             __syncwarp();
