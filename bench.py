@@ -40,8 +40,8 @@ FWD_OPS_PER_ENTRY = 54
 BWD_OPS_PER_ENTRY = 38
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # DRAM bytes (read + write) per evaluation item of the two candidate dominant kernels, from one
-# ncu capture at 512 items (profiles/multivariate_fp32_b512_launches_and_kernels.md); the
-# traffic scales with the items of a launch.
+# ncu capture of the multivariate model at 512 items (--set full, one launch each); the traffic
+# scales with the items of a launch.
 TRAFFIC_PER_ITEM = {"k_fwd_f32": (45.5e6 + 3.3e6) / 512, "k_bwd_f32": (96.9e6 + 2.8e6) / 512}
 
 
