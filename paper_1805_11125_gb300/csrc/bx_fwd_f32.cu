@@ -21,6 +21,8 @@
 // Gg_s.
 #include <math.h>
 
+#include <type_traits>
+
 #include "bx_df.cuh"
 #include "bx_internal.cuh"
 #include "bx_resp.cuh"
@@ -55,8 +57,10 @@ __global__ void __launch_bounds__(F32_THREADS) k_fwd_f32(Work w) {
     __shared__ float4 sC[2][FCH32];
     __shared__ ColG sG[2][FCH32];
     __shared__ float2 sS[2][FCH32];
-    __shared__ int2 sR[2][FCH32];
-    __shared__ float colbuf[COLS ? 2 : 1][COLS ? 64 : 1][FCH32 + 1];
+    // column sums: one slice -> R Gg of the lane's two rows added (32 values per column);
+    // several slices (MES) -> R of each of the warp's 64 rows
+    constexpr int CBR = MES ? 64 : 32;
+    __shared__ float colbuf[COLS ? 2 : 1][COLS ? CBR : 1][FCH32 + 1];
     float(*cb)[FCH32 + 1] = colbuf[COLS ? q : 0];
 
     const int ra = g + lane, rb = ra + 32;
@@ -73,61 +77,79 @@ __global__ void __launch_bounds__(F32_THREADS) k_fwd_f32(Work w) {
     float sa = 0.f, csa = 0.f, ta = 0.f, cta = 0.f, sb = 0.f, csb = 0.f, tb = 0.f, ctb = 0.f;
     float* apart = static_cast<float*>(w.apart) + (((size_t)item * w.max_tiles + tile) * 2 + q) * (MES ? w.nes : 1) * w.Npad;
 
+    // one column's entries of the lane's rows: both row groups (the common case: two
+    // independent chains for the scheduler) or one of them
+    auto column = [&](auto wide_tag, bool inA, bool inB, const float4& cf, const ColG& cg, const float2 S,
+                      float& Ra, float& Rb) {
+        constexpr bool WIDE = decltype(wide_tag)::value;
+        if (inA && inB) {
+            Ra = resp_shape32<WIDE>(mfa, cf, cg);
+            Rb = resp_shape32<WIDE>(mfb, cf, cg);
+            kahan_fma(sa, csa, Ra, S.x);
+            kahan_fma(sb, csb, Rb, S.x);
+            if (TAG) {
+                kahan_fma(ta, cta, Ra, S.y);
+                kahan_fma(tb, ctb, Rb, S.y);
+            }
+        } else if (inA) {
+            Ra = resp_shape32<WIDE>(mfa, cf, cg);
+            kahan_fma(sa, csa, Ra, S.x);
+            if (TAG) kahan_fma(ta, cta, Ra, S.y);
+        } else {
+            Rb = resp_shape32<WIDE>(mfb, cf, cg);
+            kahan_fma(sb, csb, Rb, S.x);
+            if (TAG) kahan_fma(tb, ctb, Rb, S.y);
+        }
+    };
+
     for (int grp = 0; grp < NGRP; ++grp) {
     const int2 cr = tile_range(w, item, grp, tile);
     for (int c0 = cr.x; c0 < cr.y; c0 += FCH32) {
         const int ncol = min(FCH32, cr.y - c0);
+        // lane = column: stage its parameters and vote, for the warp's two 32-row groups,
+        // whether the column's band touches them (mA, mB) and whether |z| <= 1 at every row
+        // of the warp (mW: t = (m - floor(mu/w)) hs + c is linear in the row m, so its two
+        // end rows bound it)
+        unsigned mA, mB, mW;
         {
             const bool in = lane < ncol;
             const int i = c0 + lane;
-            sC[q][lane] = in ? colf[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-            sG[q][lane] = in ? colg[i] : ColG{0.f, 0.f, 0.f, 0.f};
+            const float4 cfl = in ? colf[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const ColG cgl = in ? colg[i] : ColG{0.f, 0.f, 0.f, 0.f};
+            sC[q][lane] = cfl;
+            sG[q][lane] = cgl;
             sS[q][lane] = in ? colS[i] : make_float2(0.f, 0.f);
-            sR[q][lane] = in ? colr[i] : make_int2(0, 0);
+            const int2 band = in ? colr[i] : make_int2(0, 0);
+            const float t0 = fmaf((float)g - cfl.x, cfl.z, cfl.y), t1 = fmaf(63.0f, cfl.z, t0);
+            mA = __ballot_sync(0xffffffffu, band.x < g + 32 && band.y > g);
+            mB = __ballot_sync(0xffffffffu, band.x < g + 64 && band.y > g + 32);
+            mW = __ballot_sync(0xffffffffu, cgl.kap * fmaxf(fabsf(t0), fabsf(t1)) <= 0.99f);
         }
         __syncwarp();
-        for (int c = 0; c < ncol; ++c) {
-            const int2 band = sR[q][c];
-            const bool inA = band.x < g + 32 && band.y > g;
-            const bool inB = band.x < g + 64 && band.y > g + 32;
-            if (!inA && !inB) {
-                if (COLS) {
-                    cb[lane][c] = 0.f;
-                    cb[lane + 32][c] = 0.f;
-                }
-                continue;
-            }
+        const unsigned mAny = mA | mB;
+        for (unsigned mr = mAny; mr; mr &= mr - 1u) {   // the columns whose band touches the warp
+            const int c = __ffs(mr) - 1;
             const float4 cf = sC[q][c];
             const ColG cg = sG[q][c];
             const float2 S = sS[q][c];
+            const bool inA = (mA >> c) & 1u, inB = (mB >> c) & 1u;
             float Ra = 0.f, Rb = 0.f;
-            if (inA && inB) {   // the common case: two independent chains for the scheduler
-                Ra = resp_shape32(mfa, cf, cg);
-                Rb = resp_shape32(mfb, cf, cg);
-                kahan_fma(sa, csa, Ra, S.x);
-                kahan_fma(sb, csb, Rb, S.x);
-                if (TAG) {
-                    kahan_fma(ta, cta, Ra, S.y);
-                    kahan_fma(tb, ctb, Rb, S.y);
-                }
-            } else if (inA) {
-                Ra = resp_shape32(mfa, cf, cg);
-                kahan_fma(sa, csa, Ra, S.x);
-                if (TAG) kahan_fma(ta, cta, Ra, S.y);
-            } else {
-                Rb = resp_shape32(mfb, cf, cg);
-                kahan_fma(sb, csb, Rb, S.x);
-                if (TAG) kahan_fma(tb, ctb, Rb, S.y);
-            }
+            if ((mW >> c) & 1u) column(std::true_type{}, inA, inB, cf, cg, S, Ra, Rb);
+            else column(std::false_type{}, inA, inB, cf, cg, S, Ra, Rb);
             if (COLS) {
-                cb[lane][c] = MES ? Ra : Ra * gga;
-                cb[lane + 32][c] = MES ? Rb : Rb * ggb;
+                if (MES) {
+                    cb[lane][c] = Ra;
+                    cb[lane + 32][c] = Rb;
+                } else {
+                    cb[lane][c] = fmaf(Rb, ggb, Ra * gga);
+                }
             }
         }
         __syncwarp();
         if (COLS && !MES) {
             float s = 0.f;
-            for (int j = 0; j < 64; ++j) s += cb[j][lane];
+            if ((mAny >> lane) & 1u)
+                for (int j = 0; j < 32; ++j) s += cb[j][lane];
             if (lane < ncol) apart[c0 + lane] = s * sG[q][lane].A;
             __syncwarp();
         }
@@ -135,12 +157,13 @@ __global__ void __launch_bounds__(F32_THREADS) k_fwd_f32(Work w) {
             float s[MAX_ES];
 #pragma unroll
             for (int e = 0; e < MAX_ES; ++e) s[e] = 0.f;
-            for (int j = 0; j < 64; ++j) {
-                const float r = cb[j][lane];
+            if ((mAny >> lane) & 1u)
+                for (int j = 0; j < 64; ++j) {
+                    const float r = cb[j][lane];
 #pragma unroll
-                for (int e = 0; e < MAX_ES; ++e)
-                    if (e < NES) s[e] = fmaf(r, sGg[q][e][j], s[e]);
-            }
+                    for (int e = 0; e < MAX_ES; ++e)
+                        if (e < NES) s[e] = fmaf(r, sGg[q][e][j], s[e]);
+                }
             if (lane < ncol)
 #pragma unroll
                 for (int e = 0; e < MAX_ES; ++e)

@@ -101,13 +101,16 @@ constexpr float INV_2LN2 = 0.72134752044448170f;   // kk = kap / (2 ln 2)
 // Response entry of output bin `mf` (row index as float) and one column, divided by the
 // column's amplitude A: the node sum 8 p0 + 5 (p- + p+).
 // cf = (floor(mu/w), c_hi, hs_hi, hs_lo); cg = (kap, Ck2, c_lo, A / 9).
+// WIDE: the caller has established |z| <= 1 for this row (the series branch), so the test
+// is skipped; the arithmetic is the same either way.
+template <bool WIDE = false>
 __device__ __forceinline__ float resp_shape32(float mf, const float4& cf, const ColG& cg) {
     float th, tl;
     centre_df(mf, cf, cg.c_lo, th, tl);
     const float p0 = centre_node(th, tl);
     const float z = cg.kap * th;
     float Sp;
-    if (fabsf(z) <= 1.0f) {
+    if (WIDE || fabsf(z) <= 1.0f) {
         Sp = p0 * cg.Ck2 * cosh_small(z * z);
     } else {
         float Sm;
