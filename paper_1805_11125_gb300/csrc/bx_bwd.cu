@@ -241,7 +241,11 @@ __global__ void __launch_bounds__(BCOLS, 7) k_bwd_f32(Work w) {
     const int wr0 = max(r0, min(r1, __reduce_min_sync(0xffffffffu, live ? band.x : INT_MAX)));
     const int wr1 = min(r1, __reduce_max_sync(0xffffffffu, live ? band.y : 0));
     const int lane = tid & 31, wq = tid >> 5;
-    __shared__ float sW[BCOLS / 32][NR][64];
+    // the plain model packs (wt_sub, wt_tag, G_W, -) per row (one 16-byte load); the others keep
+    // one row array per weight
+    constexpr bool PACK = !MES && !MULTI;
+    __shared__ float sW[BCOLS / 32][PACK ? 1 : NR][PACK ? 1 : 64];
+    __shared__ float4 sW4[BCOLS / 32][PACK ? 64 : 1];
     double S0 = 0.0, S1 = 0.0, S2 = 0.0, Rs = 0.0, Rt = 0.0;
     for (int c0 = wr0; c0 < wr1; c0 += RCH) {
         const int c1 = min(wr1, c0 + RCH);
@@ -249,11 +253,13 @@ __global__ void __launch_bounds__(BCOLS, 7) k_bwd_f32(Work w) {
         for (int s0 = c0; s0 < c1; s0 += 64) {
             const int ns = min(64, c1 - s0);
             for (int j = lane; j < ns; j += 32) {
-                sW[wq][0][j] = rw[s0 + j];
-                sW[wq][1][j] = rw[(size_t)w.Mpad + s0 + j];
-                sW[wq][2][j] = rw[(size_t)2 * w.Mpad + s0 + j];
-                if constexpr (MES)
-                    for (int q = 1; q < NES; ++q) sW[wq][2 + q][j] = rw[(size_t)(2 + q) * w.Mpad + s0 + j];
+                if constexpr (PACK) {
+                    sW4[wq][j] = make_float4(rw[s0 + j], rw[(size_t)w.Mpad + s0 + j], rw[(size_t)2 * w.Mpad + s0 + j], 0.f);
+                } else {
+                    sW[wq][0][j] = rw[s0 + j];
+                    sW[wq][1][j] = rw[(size_t)w.Mpad + s0 + j];
+                    for (int q = 0; q < NES; ++q) sW[wq][2 + q][j] = rw[(size_t)(2 + q) * w.Mpad + s0 + j];
+                }
             }
             __syncwarp();
             if (ok) {
@@ -267,6 +273,14 @@ __global__ void __launch_bounds__(BCOLS, 7) k_bwd_f32(Work w) {
                             for (int q = 0; q < MAX_ES; ++q)
                                 if (q < NES) a = fmaf(sW[wq][2 + q][j + k], SAq[q], a);
                             W = fmaf(ws, Ssub, fmaf(wt, Stag, a));
+                        };
+                        adj_run((float)(s0 + j), min(ADJ_RUN, ns - j), cf, cg, ac, wts, bs);
+                    } else if constexpr (PACK) {
+                        auto wts = [&](int k, float& ws, float& wt, float& W) {
+                            const float4 r = sW4[wq][j + k];
+                            ws = r.x;
+                            wt = r.y;
+                            W = fmaf(ws, Ssub, fmaf(wt, Stag, r.z * SA));
                         };
                         adj_run((float)(s0 + j), min(ADJ_RUN, ns - j), cf, cg, ac, wts, bs);
                     } else {
