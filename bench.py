@@ -35,9 +35,9 @@ WORKLOAD = ("multivariate spectral fit: K=15 species on a 2000-point 0-3 MeV gri
 # FP32 operations per in-band response entry of the forward kernel, counted from the source
 # (bx_resp.cuh resp_shape32 44, two Kahan row sums 8, column sum 2)
 FWD_OPS_PER_ENTRY = 54
-# adjoint kernel per entry of a run of 8 rows (bx_resp.cuh adj_run): recurrence 7, outer-node
-# products 2, basis sums 19 (AdjSums::add), weight 3, plus the exact start of the run (58) / 8
-BWD_OPS_PER_ENTRY = 38
+# adjoint kernel per entry of a run of 16 rows (bx_resp.cuh adj_run): recurrence 7, outer-node
+# products 2, basis sums 19 (AdjSums::add), weight 3, plus the exact start of the run (58) / 16
+BWD_OPS_PER_ENTRY = 35
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # DRAM bytes (read + write) per evaluation item of the two candidate dominant kernels, from one
 # ncu capture of the multivariate model at 512 items (--set full, one launch each); the traffic

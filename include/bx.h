@@ -205,7 +205,10 @@ typedef struct {
     int iters;                  /* accepted Newton steps */
     int n_evals;                /* NLL+gradient evaluations used */
     int status;                 /* BX_OK, BX_ENOTCONV or BX_EDOMAIN */
-    int n_at_bound;             /* free parameters held at a bound at the returned theta */
+    int n_at_bound;             /* free parameters held at a bound at the returned theta: on the
+                                   bound with the gradient pointing out of the box, so outside the
+                                   Newton step (a parameter resting on a bound with an inward or
+                                   zero gradient is not counted) */
     double damping;             /* Levenberg damping of the last fresh Hessian (scaled units;
                                    0: positive definite as measured) */
 } bx_fit_result;

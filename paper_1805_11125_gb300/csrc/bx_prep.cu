@@ -505,6 +505,7 @@ __global__ void __launch_bounds__(256, 3) k_prep32(Work w) {
             bool nz = false;   // a species of this group has support in the column
             if (T.shapes32) {
                 float ss = 0.f, st = 0.f;
+#pragma unroll 4
                 for (int k = 0; k < K; ++k) {
                     if (MULTI && T.set_of[k] != grp) continue;
                     const float sk = T.shapes32[(size_t)k * N + i];

@@ -148,23 +148,42 @@ __device__ __forceinline__ void resp_adjoint32(float mf, const float4& cf, const
 // Row recurrence of the adjoint's node sums down one column.  From row m to m + 1 the centre
 // node moves by hs in the scaled variable, so
 //   p0(m+1) = p0(m) rho(m),   rho(m) = 2^-(2 t0(m) hs + hs^2),   rho(m+1) = rho(m) C,  C = 2^(-2 hs^2),
-// and (cosh z, sinh z) of the outer nodes (z = kap t0) rotate by the fixed step kap hs.  A run of
-// ADJ_RUN rows starts from the exact evaluation of its first row (as resp_adjoint32), so the
-// FP32 recurrence error stays below ~1e-6 of an entry (it only enters gradient sums); columns
-// narrow enough for |z| > 1 within the run take the exact form row by row.
-constexpr int ADJ_RUN = 8;
+// and (cosh z, sinh z) of the outer nodes (z = kap t0) rotate by the fixed step kap hs.  The
+// per-column constants enter as their small parts, 1 - C and cosh(kap hs) - 1 (each from its
+// series, to ~1e-10 of the constant), so a constant's FP32 rounding does not compound along
+// the run: rho(m+1) = rho(m) - rho(m) (1 - C).  A run of ADJ_RUN rows starts from the exact
+// evaluation of its first row (as resp_adjoint32); the FP32 recurrence error then grows about
+// linearly along the run, to ~1e-6 of an entry at its end (it only enters gradient sums);
+// columns narrow enough for |z| > 1 within the run take the exact form row by row.
+constexpr int ADJ_RUN = 16;
 
 struct AdjCol {
-    float hs, hs2, C, A, B, kk, iCk2;   // hs, hs^2, 2^(-2 hs^2), cosh and sinh of kap hs, kap / (2 ln 2), 1 / Ck2
+    // hs, hs^2, 1 - 2^(-2 hs^2), cosh(kap hs) - 1, sinh(kap hs), kap / (2 ln 2), 1 / Ck2
+    float hs, hs2, dC, Am1, B, kk, iCk2;
 };
+
+// cosh(d) - 1 for s = d^2 <= 1 from its Taylor series through d^10 (truncation < 3e-7 of the
+// result at d = 1, below 1e-20 at the d ~ 1e-2 of the bench's columns)
+__device__ __forceinline__ float coshm1_small(float s) {
+    float c = 2.755731922e-07f;                          // 1/10!
+    c = fmaf(c, s, 2.480158730e-05f);                    // 1/8!
+    c = fmaf(c, s, 1.388888889e-03f);                    // 1/6!
+    c = fmaf(c, s, 4.166666667e-02f);                    // 1/4!
+    c = fmaf(c, s, 0.5f);
+    return c * s;
+}
 
 __device__ __forceinline__ AdjCol adj_col(const float4& cf, const ColG& cg) {
     AdjCol a;
     a.hs = cf.z;
     a.hs2 = cf.z * cf.z;
-    a.C = exp2_neg(-2.0f * a.hs2);
+    // 1 - 2^(-x / ln 2) = 1 - e^(-x), x = 2 ln 2 hs^2: its Taylor series where x is small
+    // (truncation x^6 / 720 < 3e-11 of the result for x < 0.05), else the difference
+    const float x = 1.3862944f * a.hs2;
+    a.dC = x < 0.05f ? x * fmaf(x, fmaf(x, fmaf(x, fmaf(x, 1.0f / 120.0f, -1.0f / 24.0f), 1.0f / 6.0f), -0.5f), 1.0f)
+                     : 1.0f - exp2_neg(-2.0f * a.hs2);
     const float d = cg.kap * cf.z, d2 = d * d;
-    a.A = cosh_small(d2);
+    a.Am1 = coshm1_small(d2);
     a.B = sinh_small(d, d2);
     a.kk = cg.kap * INV_2LN2;
     a.iCk2 = cg.Ck2 > 0.f ? 1.0f / cg.Ck2 : 0.f;
@@ -230,10 +249,10 @@ __device__ __forceinline__ void adj_run(float mf, int n, const float4& cf, const
                 wts(k, ws, wt, W);
                 s.add(t, p, p * ch, p * sh, ws, wt, W);
                 p *= rho;
-                rho *= ac.C;
+                rho = fmaf(-rho, ac.dC, rho);
                 t += ac.hs;
-                const float c2 = fmaf(ch, ac.A, sh * ac.B);
-                sh = fmaf(sh, ac.A, ch * ac.B);
+                const float c2 = fmaf(ch, ac.Am1, fmaf(sh, ac.B, ch));
+                sh = fmaf(sh, ac.Am1, fmaf(ch, ac.B, sh));
                 ch = c2;
             }
         }

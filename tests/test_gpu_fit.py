@@ -48,14 +48,19 @@ def test_asimov_fit_returns_truth(prec):
     assert st == bx.BX_OK, info
     _check_against(ref, out, info, s.P, s.default_free().astype(bool), 4, nsig=NSIG[prec])
     # diagnostics: the parameters held at a bound are the free ones on a bound of the returned
-    # theta (here the weakly constrained resolution constant c may end on its lower bound);
-    # a converged fit's last Hessian needed at most the damping with which convergence may be
-    # declared (1e-2 FP64, 1e-1 FP32, scaled units)
+    # theta whose gradient there points out of the box (here the weakly constrained resolution
+    # constant c may end on its lower bound; resting there with a vanishing gradient it is on the
+    # bound but not held); a converged fit's last Hessian needed at most the damping with which
+    # convergence may be declared (1e-2 FP64, 1e-1 FP32, scaled units)
     lo, hi = s.default_bounds()
     free = s.default_free().astype(bool)
     for j, r in enumerate(info):
         th = out[j, : s.P]
-        assert r["n_at_bound"] == int(np.count_nonzero(free & ((th <= lo) | (th >= hi)))), r
+        _, g = m.nll_grad(th)
+        g = g[: s.P]
+        held = free & (((th <= lo) & (g > 0)) | ((th >= hi) & (g < 0)))
+        assert r["n_at_bound"] == int(np.count_nonzero(held)), (r, th, g)
+        assert r["n_at_bound"] <= int(np.count_nonzero(free & ((th <= lo) | (th >= hi)))), r
         assert 0.0 <= r["damping"] <= (1e-2 if prec == bx.BX_FP64 else 1e-1), r
 
 
