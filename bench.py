@@ -42,7 +42,7 @@ SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # DRAM bytes (read + write) per evaluation item of the two candidate dominant kernels, from one
 # ncu capture of the multivariate model at 512 items (--set full, one launch each); the traffic
 # scales with the items of a launch.
-TRAFFIC_PER_ITEM = {"k_fwd_f32": (45.5e6 + 2.68e6) / 512, "k_bwd_f32": (96.9e6 + 3.54e6) / 512}
+TRAFFIC_PER_ITEM = {"k_fwd_f32": (45.5e6 + 2.85e6) / 512, "k_bwd_f32": (96.9e6 + 3.14e6) / 512}
 
 
 def job_throughput(local_ms: float, items_per_rank: int, steps: int, ws: int, device=None):
