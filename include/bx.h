@@ -136,6 +136,11 @@ typedef struct {
  * (BX_FP32, max_batch 1).  cuda_stream is a cudaStream_t (NULL = legacy default). */
 int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_options* opts,
                     void* cuda_stream, bx_model** out);
+/* (bx_model_create returns BX_EINVAL, with the sizes in bx_last_error, when one item's
+ * assembly stage would need more shared memory than the device allows a thread block: it
+ * holds the window's spectra, the full axis of Eq. 3 spectra, the pile-up spectrum and the
+ * per-column Eq. 4 weights.  On a GB300 that bounds e.g. an 8192-point grid to an axis of
+ * about 2000 bins; the 1D limits above are the upper bounds of each size alone.) */
 void bx_model_destroy(bx_model* model);
 int bx_model_set_stream(bx_model* model, void* cuda_stream);
 /* P = 7 + max_t K_t: the row stride of every theta / grad array */
@@ -166,7 +171,8 @@ int bx_expected(bx_model* model, int toy, const double* theta, double* mu);
 /* n independent evaluations: item j uses toy toy_idx[j] (host array; NULL = toy 0 for
  * every item) at theta[j*P .. j*P + P_t).  nll[n]; grad[n*P] or NULL (no adjoint).
  * device_ptrs = 0: theta/nll/grad are host memory, synchronous.
- * device_ptrs = 1: theta/nll/grad are device memory; the call only enqueues work. */
+ * device_ptrs = 1: theta/nll/grad are device memory; the call only enqueues work.
+ * n = 0 is an empty batch: BX_OK, nothing is read or written. */
 int bx_nll_batch(bx_model* model, int n, const int* toy_idx, const double* theta,
                  double* nll, double* grad, int device_ptrs);
 

@@ -394,6 +394,22 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
     w.win_kb = (m->nwmax + KB - 1) / KB;
     w.win_tiles = (m->nwmax + TM - 1) / TM;
     w.Lmax = m->Lmax;
+    if (!m->is2d) {   // the assembly stage holds one item's spectra and columns in shared memory
+        size_t need = 0, avail = 0;
+        const cudaError_t e = mid_smem_budget(w, m->Mmax, m->nwmax, m->Lmax, &need, &avail);
+        const int bad = e != cudaSuccess ? 1 : need > avail ? 2 : 0;
+        if (bad) {
+            cudaStreamSynchronize(m->stream);
+            const int nwm = m->nwmax, Mm = m->Mmax, Lm = m->Lmax, np = w.Npad;
+            free_model(m);
+            if (bad == 1) return bx_set_error(BX_ECUDA, "assembly kernel attributes: %s", cudaGetErrorString(e));
+            return bx_set_error(BX_EINVAL,
+                                "the assembly stage needs %zu B of shared memory per item (window %d, axis %d, "
+                                "pile-up %d, %d columns); the device allows %zu B: use a smaller window, axis, "
+                                "pile-up spectrum or grid",
+                                need, nwm, Mm, Lm, np, avail);
+        }
+    }
     const size_t tv = m->precision == BX_FP64 ? sizeof(double) : sizeof(float);
     const bool species = m->precision == BX_TF32X3;
     struct A {
@@ -631,7 +647,9 @@ extern "C" int bx_expected(bx_model* m, int toy, const double* theta, double* mu
 
 extern "C" int bx_nll_batch(bx_model* m, int n, const int* toy_idx, const double* theta, double* nll, double* grad,
                             int device_ptrs) {
-    if (!m || !theta || !nll) return bx_set_error(BX_EINVAL, "NULL argument");
+    if (!m) return bx_set_error(BX_EINVAL, "NULL argument");
+    if (n == 0) return BX_OK;   // an empty batch: nothing to evaluate
+    if (!theta || !nll) return bx_set_error(BX_EINVAL, "NULL argument");
     if (!device_ptrs) return eval_host(m, n, toy_idx, theta, grad != nullptr, 0, nll, grad);
     int st = bx_set_items(m, n, toy_idx);
     if (st) return st;

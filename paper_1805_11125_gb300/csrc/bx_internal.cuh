@@ -171,6 +171,9 @@ cudaError_t launch_prep(const Work& w, int n, cudaStream_t s);
 cudaError_t launch_fwd_f64(const Work& w, int n, int max_tiles, int any_tag, int any_cols, cudaStream_t s);
 cudaError_t launch_fwd_tc(const Work& w, int n, int max_tiles, cudaStream_t s);
 cudaError_t launch_fwd_f32(const Work& w, int n, int max_tiles, int any_tag, int any_cols, cudaStream_t s);
+// Dynamic shared memory the assembly kernel needs per item for these sizes, and the most the
+// device allows it (the opt-in limit less the kernel's static shared memory).
+cudaError_t mid_smem_budget(const Work& w, int Mmax, int nwmax, int Lmax, size_t* need, size_t* avail);
 cudaError_t launch_mid(const Work& w, int n, int Mmax, int nwmax, int Lmax, int want_grad, int want_mu,
                        cudaStream_t s);
 cudaError_t launch_bwd(const Work& w, int n, int max_cb, cudaStream_t s);

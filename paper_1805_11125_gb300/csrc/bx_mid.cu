@@ -839,29 +839,50 @@ static cudaError_t launch_mid_t(const Work& w, int n, size_t smem, int want_grad
     return cudaGetLastError();
 }
 
-cudaError_t launch_mid(const Work& w, int n, int Mmax, int nwmax, int Lmax, int want_grad, int want_mu,
-                       cudaStream_t s) {
-    const bool f32 = w.precision != BX_FP64;
-    const size_t tv = f32 ? sizeof(float) : sizeof(double);
-    const size_t smem = (size_t)(2 * Mmax + 2 * nwmax) * sizeof(double) +
-                        (size_t)(2 * Mmax + 4 * nwmax + Lmax) * tv + 64;
-    if (!f32) return launch_mid_t<double, false>(w, n, smem, want_grad, want_mu, s);
-    if (w.precision == BX_TF32X3) return launch_mid_t<float, true>(w, n, smem, want_grad, want_mu, s);
+// Dynamic shared memory of the assembly kernel the workspace's precision selects, for the
+// model's largest axis (Mmax), window (nwmax) and pile-up spectrum (Lmax).
+static size_t mid_dynamic_smem(const Work& w, int Mmax, int nwmax, int Lmax) {
+    if (w.precision != BX_FP32) {   // k_mid: lambda and mu in FP64, the rest in the kernel's type
+        const size_t tv = w.precision == BX_FP64 ? sizeof(double) : sizeof(float);
+        return (size_t)(2 * Mmax + 2 * nwmax) * sizeof(double) + (size_t)(2 * Mmax + 4 * nwmax + Lmax) * tv + 64;
+    }
     // k_mid32: mu pairs [2][nw], g, lambda rows, pile-up part [2][nw], weight rows (zero-padded),
     // G_W and dG_W/deps per column
-    const size_t smem32 = (size_t)2 * nwmax * sizeof(float2) +
-                          (size_t)(mid32_gn(Lmax) + 2 * mid32_lrow(Mmax) + 2 * nwmax + 2 * mid32_wrow(nwmax)) * sizeof(float) +
-                          (size_t)w.Npad * (sizeof(float2) + sizeof(float));
+    return (size_t)2 * nwmax * sizeof(float2) +
+           (size_t)(mid32_gn(Lmax) + 2 * mid32_lrow(Mmax) + 2 * nwmax + 2 * mid32_wrow(nwmax)) * sizeof(float) +
+           (size_t)w.Npad * (sizeof(float2) + sizeof(float));
+}
+
+cudaError_t mid_smem_budget(const Work& w, int Mmax, int nwmax, int Lmax, size_t* need, size_t* avail) {
+    *need = mid_dynamic_smem(w, Mmax, nwmax, Lmax);
+    cudaFuncAttributes fa{};
+    cudaError_t e;
+    if (w.precision == BX_FP64) e = cudaFuncGetAttributes(&fa, k_mid<double, false>);
+    else if (w.precision == BX_TF32X3) e = cudaFuncGetAttributes(&fa, k_mid<float, true>);
+    else e = w.nes > 1 ? cudaFuncGetAttributes(&fa, k_mid32<true>) : cudaFuncGetAttributes(&fa, k_mid32<false>);
+    if (e != cudaSuccess) return e;
+    int dev = 0, optin = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+    *avail = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+    return cudaSuccess;
+}
+
+cudaError_t launch_mid(const Work& w, int n, int Mmax, int nwmax, int Lmax, int want_grad, int want_mu,
+                       cudaStream_t s) {
+    const size_t smem = mid_dynamic_smem(w, Mmax, nwmax, Lmax);
+    if (w.precision == BX_FP64) return launch_mid_t<double, false>(w, n, smem, want_grad, want_mu, s);
+    if (w.precision == BX_TF32X3) return launch_mid_t<float, true>(w, n, smem, want_grad, want_mu, s);
     static size_t set32[2] = {0, 0};
     const int mes = w.nes > 1 ? 1 : 0;   // several energy slices of the Eq. 4 terms
-    if (smem32 > set32[mes]) {
+    if (smem > set32[mes]) {
         const cudaError_t e = cudaFuncSetAttribute(mes ? k_mid32<true> : k_mid32<false>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32);
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        set32[mes] = smem32;
+        set32[mes] = smem;
     }
-    if (mes) k_mid32<true><<<n, MID_THREADS, smem32, s>>>(w, want_grad, want_mu);
-    else k_mid32<false><<<n, MID_THREADS, smem32, s>>>(w, want_grad, want_mu);
+    if (mes) k_mid32<true><<<n, MID_THREADS, smem, s>>>(w, want_grad, want_mu);
+    else k_mid32<false><<<n, MID_THREADS, smem, s>>>(w, want_grad, want_mu);
     return cudaGetLastError();
 }
 
