@@ -397,7 +397,7 @@ SLICED = ("multivariate with the radial and pulse-shape terms in 3 energy slices
           "500-1000 npe): 3 x (60 radial + 50 pulse-shape) bins")
 
 
-def variant_leg(bx, I, name, workload, stream, B=1824, steps=5):
+def variant_leg(bx, I, name, workload, stream, B=2736, steps=5):
     """A variant of the multivariate model (species-specific quenching: the alpha species at
     2.3 MeV true energy quenched with 150 kB, with its own Birks map and response columns; or
     the Eq. 4 terms in several energy slices): -lnL + gradient evaluations/s at the main leg's
@@ -508,9 +508,9 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    # 1824 = 152 SMs x 12: the one-CTA-per-item stages (column stage at 3 CTAs per SM, assembly
-    # at 2) run in whole waves
-    ap.add_argument("--batch", type=int, default=1824)
+    # 2736 = 152 SMs x 18: whole waves for the forward (8 tiles per item at 18 CTAs per SM), the
+    # column stage (one CTA per item at 3 per SM) and the assembly (one per item at 2 per SM)
+    ap.add_argument("--batch", type=int, default=2736)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
