@@ -283,6 +283,52 @@ __device__ __forceinline__ void adj_run(float mf, int n, const float4& cf, const
     }
 }
 
+// The node sums P0, P1, P2 of resp_adjoint32 for rows mf .. mf + n - 1 (n <= ADJ_RUN) of one
+// column, by the row recurrence of adj_run from an exact start: f(k, P0, P1, P2) receives
+// row mf + k.  With u = p0 cosh z, v = p0 sinh z and o = 5 Ck2,
+//   P0 = o u + 8 p0,  P1 = o (t u - kk v) + 8 t p0,  P2 = o ((kk^2 + t^2) u - 2 kk t v) + 8 t^2 p0.
+// Columns narrow enough for |z| > 1 within the run take resp_adjoint32 row by row.
+template <typename F>
+__device__ __forceinline__ void adj_nodes_run(float mf, int n, const float4& cf, const ColG& cg, const AdjCol& ac,
+                                              F&& f) {
+    float th, tl;
+    centre_df(mf, cf, cg.c_lo, th, tl);
+    const float z0 = cg.kap * th, z1 = cg.kap * fmaf((float)(ADJ_RUN - 1), ac.hs, th);
+    if (fabsf(z0) <= 1.0f && fabsf(z1) <= 1.0f) {
+        float p = centre_node(th, tl);
+        float rho = exp2_neg(-fmaf(2.0f * th, ac.hs, ac.hs2));
+        const float q = z0 * z0;
+        float ch = cosh_small(q), sh = sinh_small(z0, q);
+        float t = th;
+        const float o = GL_W_OUT * cg.Ck2, kk = ac.kk, kk2 = ac.kk * ac.kk;
+#pragma unroll
+        for (int k = 0; k < ADJ_RUN; ++k) {
+            if (k < n) {
+                const float u = p * ch, v = p * sh, tp = t * p;
+                const float P0 = fmaf(o, u, GL_W_MID * p);
+                const float P1 = fmaf(o, fmaf(t, u, -kk * v), GL_W_MID * tp);
+                const float P2 = fmaf(o, fmaf(fmaf(t, t, kk2), u, -2.0f * kk * t * v), GL_W_MID * (t * tp));
+                f(k, P0, P1, P2);
+                p *= rho;
+                rho = fmaf(-rho, ac.dC, rho);
+                t += ac.hs;
+                const float c2 = fmaf(ch, ac.Am1, fmaf(sh, ac.B, ch));
+                sh = fmaf(sh, ac.Am1, fmaf(ch, ac.B, sh));
+                ch = c2;
+            }
+        }
+    } else {
+#pragma unroll 2
+        for (int k = 0; k < ADJ_RUN; ++k) {
+            if (k < n) {
+                float P0, P1, P2;
+                resp_adjoint32(mf + (float)k, cf, cg, P0, P1, P2);
+                f(k, P0, P1, P2);
+            }
+        }
+    }
+}
+
 #endif  // __CUDACC__
 
 }  // namespace bx
