@@ -204,7 +204,10 @@ def poisson_nll(counts, mu) -> float:
 
 
 def fit(spec, theta0, free=None, lo=None, hi=None, tol_edm=1e-12, max_iter=60):
-    """Damped Newton fit; returns dict(theta, nll, edm, iters, status, cov)."""
+    """Damped Newton fit; returns dict(theta, nll, edm, iters, status, cov).
+
+    Parity unpinned beyond two invariants (an Asimov fit returns theta_true; the expected and
+    observed totals agree at the optimum): the paper prints no fitted values."""
     m = _model(spec)
     P = spec.P
     free = spec.default_free() if free is None else free
