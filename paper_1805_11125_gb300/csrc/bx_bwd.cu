@@ -1,7 +1,8 @@
 // bx_bwd.cu -- adjoint of Eq. 1 and the gather of the final gradient.
 //
-// dNLL/dR[m,i] = sum_k s_k[i] (c0_k wt_sub[m] + c1_k wt_tag[m] + c2_k G_W[m]) = W[m,i]
-// (coefficients and row weights written by k_mid).  Thread = true-energy column i; it
+// dNLL/dR[m,i] = sum_k s_k[i] (c0_k wt_sub[m] + c1_k wt_tag[m] + sum_s c_{2+s,k} G_W,s[m]) = W[m,i]
+// (coefficients and row weights written by k_mid; one G_W per energy slice s of the Eq. 4
+// terms, one slice unless the model has several).  Thread = true-energy column i; it
 // recomputes the response of its band rows (nothing of the forward pass is stored) and
 // forms the column sums
 //     S0 = sum_m W R,   S1 = sum_m W norm dD/dmu_i,   S2 = sum_m W norm dD/dsigma_i,

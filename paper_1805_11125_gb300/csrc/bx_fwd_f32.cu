@@ -10,15 +10,17 @@
 // Unit = (row tile of TM output bins, item); 64 threads, warp q owning the two 32-row
 // groups m0 + 64q + [0, 32) and m0 + 64q + [32, 64), one row of each per thread.  The warps
 // never wait for each other: each stages 32 columns' parameters at a time in its own shared
-// memory and skips the columns whose band misses a row group, so the work follows each
-// column's own band rather than the union over the tile.
+// memory, lane = column, and the lanes vote three masks: the column's band touches row group
+// A, row group B, and |z| <= 1 holds at every row of the warp (the generator's series branch,
+// so the per-entry test is dropped).  The warp then visits only the set bits, so the work
+// follows each column's own band rather than the union over the tile.
 // Each thread generates the response of its bins with round-to-nearest FP32 arithmetic
 // (bx_resp.cuh) and adds R S_h into Kahan-compensated accumulators at every term, so a row
-// sum of ~10^3 terms keeps an error of a few roundings with no systematic sign.  Column sums
-// of R Gg over a warp's 64 rows go through a padded warp-private shared buffer once per
-// 32 columns and are stored per half tile.  With several energy slices of the Eq. 4 terms
-// (MES) the buffer holds R itself and the column sums are formed once per slice s with its
-// Gg_s.
+// sum of ~10^3 terms keeps an error of a few roundings with no systematic sign.  For the
+// column sums each lane adds R Gg of its two rows; the 32 lane values per column go through
+// a padded warp-private shared buffer once per 32 columns and are stored per half tile.
+// With several energy slices of the Eq. 4 terms (MES) the buffer holds R of all 64 rows and
+// the column sums are formed once per slice s with its Gg_s.
 #include <math.h>
 
 #include <type_traits>
