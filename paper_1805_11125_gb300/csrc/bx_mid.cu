@@ -10,7 +10,8 @@
 //          sum_m v_k G_W = sum_i s_k[i] ((1 - eps) aW[i] + eps a[i]), with the closed-form
 //          window mass aW[i] and the forward's column sums a[i]); radial bins
 //          sum_k A_k p_k[rho] (closed-form shell integrals) and pulse-shape bins
-//          sum_k A_k q_k[j];
+//          sum_k A_k q_k[j]; with several energy slices W_s of the window, one such
+//          marginal, radial and pulse-shape histogram per slice (G_W,s, aW_s, a_s);
 //   -lnL   sum of mu - n + n log1p((n - mu)/mu): the terms in FP64, or for the
 //          mixed-precision modes in a cancellation-free FP32 form where mu/2 <= n <= 2 mu
 //          and in double-float elsewhere; the sum in FP64 with Neumaier compensation inside
