@@ -35,6 +35,9 @@
  *         Y[m,b]   = sum_i R[m,i] T_r[i,b],  then Eq. 2 on every slice b
  *       with q_k[b] the radial bin probability of slice b (internal / external as for the
  *       radial term) or the pulse-shape bin probability.
+ *   3D  (the joint energy x radius x pulse-shape fit, the paper's multi-dimensional outlook):
+ *       the same with one slice per cell (rho, j) of the radius x pulse-shape grid,
+ *       q_k[(rho, j)] = p_k[rho] ps_k[j], normalised per species over the whole grid.
  *
  * Gradients come from forward-mode dual numbers carried through the same definition
  * (independent of any hand-written adjoint).  The fit is a damped Newton iteration on
@@ -114,6 +117,11 @@ typedef struct {
                                           [es_edges[s], es_edges[s+1]), edges from 0 to m_hi - m_lo;
                                           n_es = 0 -> one slice, the whole window.  The radial and
                                           pulse-shape counts are then [n_es][n_rad], [n_es][n_psd] */
+    int joint2;                        /* 2D slices as the joint grid of radius and pulse shape:
+                                          slice (rho, j) = rho n_p2 + j of the n_r2 x n_p2 grid is the
+                                          energy window of the events in radial bin rho and pulse-shape
+                                          bin j (the energy x radius x pulse-shape histogram); field
+                                          [n_grid][n_r2 n_p2], counts in n_r2_counts [n_r2 n_p2][nw] */
 } om_model;
 
 enum { OM_MAX_SETS = 4 };
@@ -144,10 +152,13 @@ int om_n_params(const om_model* m) { return m->K + 7; }
 
 static int n_slices(const om_model* m) { return m->n_es > 0 ? m->n_es : 1; }
 
+/* number of 2D slices: the radial and pulse-shape sets, or their joint grid */
+static int n_slices2(const om_model* m) { return m->joint2 ? m->n_r2 * m->n_p2 : m->n_r2 + m->n_p2; }
+
 int om_n_bins(const om_model* m) {
     int nw = m->m_hi - m->m_lo, S = n_slices(m);
     return nw + (m->tag_frac ? nw : 0) + S * (m->n_rad > 0 && m->rad_class ? m->n_rad : 0) +
-           S * (m->n_psd > 0 && m->psd_prob ? m->n_psd : 0) + (m->n_r2 + m->n_p2) * nw;
+           S * (m->n_psd > 0 && m->psd_prob ? m->n_psd : 0) + n_slices2(m) * nw;
 }
 
 static int check_model(const om_model* m) {
@@ -157,6 +168,7 @@ static int check_model(const om_model* m) {
     if (m->n_r2 < 0 || m->n_p2 < 0 || (m->n_r2 + m->n_p2 > 0 && !m->field) || (m->n_r2 > 0 && !m->rad_class) ||
         (m->n_p2 > 0 && !m->psd2))
         return OM_EINVAL;
+    if (m->joint2 && (m->n_r2 < 1 || m->n_p2 < 1)) return OM_EINVAL;   /* the joint grid needs both axes */
     if (m->quench) {
         for (int k = 0; k < m->K; ++k)
             if (!(m->quench[k] >= 0.0) || !isfinite(m->quench[k])) return OM_EINVAL;
@@ -274,7 +286,7 @@ static int stage_a1(const om_model* m, const dual* th, work* w, double xi) {
  * (set_of NULL: every species); with 2D slices also Y[m][b] = sum_i R[m,i] T_r[i][b]
  * (T_r: [N][B2], Y: [M][B2]). */
 static void stage_a23(const om_model* m, work* w, double* R_out, const dual* Tr, dual* Y, const int* set_of, int c) {
-    int N = m->n_grid, K = m->K, M = m->m_hi, B2 = m->n_r2 + m->n_p2;
+    int N = m->n_grid, K = m->K, M = m->m_hi, B2 = n_slices2(m);
     #pragma omp parallel for schedule(dynamic, 4)
     for (int r = 0; r < M; ++r) {
         dual* vr = w->v + (size_t)r * K;
@@ -297,9 +309,45 @@ static void stage_a23(const om_model* m, work* w, double* R_out, const dual* Tr,
     }
 }
 
+/* Templates of the joint energy x radius x pulse-shape grid: slice b = rho n_p2 + j,
+ *   T_r[i][b] = sum_k r_k (1 - t_k) s_k[i] p_k[rho] ps_k[j] (1 + amp u[i][b]) / N_k,
+ *   N_k = sum_i sum_b s_k[i] p_k[rho] ps_k[j] (1 + amp u[i][b]). */
+static int stage_joint_templates(const om_model* m, const dual* th, dual* Tr) {
+    int N = m->n_grid, K = m->K, nR = m->n_r2, nP = m->n_p2, B2 = nR * nP;
+    dual* p = calloc((size_t)nR, sizeof(dual));
+    dual* q = calloc((size_t)B2, sizeof(dual));
+    if (!p || !q) { free(p); free(q); return OM_ENOMEM; }
+    for (size_t j = 0; j < (size_t)N * B2; ++j) Tr[j] = dc(0.0);
+    for (int k = 0; k < K; ++k) {
+        radial_probs_n(m, nR, th[K + 6], m->rad_class[k], p);
+        for (int r = 0; r < nR; ++r)
+            for (int j = 0; j < nP; ++j) q[r * nP + j] = dscale(p[r], m->psd2[(size_t)k * nP + j]);
+        dual Nk = dc(0.0);
+        for (int i = 0; i < N; ++i) {
+            double s = m->shapes[(size_t)k * N + i];
+            if (s == 0.0) continue;
+            for (int b = 0; b < B2; ++b) dacc(&Nk, dscale(q[b], s * (1.0 + m->amp * m->field[(size_t)i * B2 + b])));
+        }
+        double ck = m->tag_frac ? 1.0 - m->tag_frac[k] : 1.0;
+        dual f = ddiv(dscale(th[k], ck), Nk);
+        for (int b = 0; b < B2; ++b) {
+            dual coef = dmul(f, q[b]);
+            for (int i = 0; i < N; ++i) {
+                double x = m->shapes[(size_t)k * N + i] * (1.0 + m->amp * m->field[(size_t)i * B2 + b]);
+                if (x != 0.0) daxpy(&Tr[(size_t)i * B2 + b], x, &coef);
+            }
+        }
+    }
+    free(p);
+    free(q);
+    return OM_OK;
+}
+
 /* 2D templates, rate-weighted: T_r[i][b] = sum_k r_k (1 - t_k) s_k[i] q_k[b] (1 + amp u[i][b]) / N_k,
- * N_k = sum_i sum_{b in the set of b} s_k[i] q_k[b] (1 + amp u[i][b]) (radial set, pulse-shape set). */
+ * N_k = sum_i sum_{b in the set of b} s_k[i] q_k[b] (1 + amp u[i][b]) (radial set, pulse-shape set).
+ * Joint grid: q_k[(rho, j)] = p_k[rho] ps_k[j] (radial times pulse-shape probability), one set. */
 static int stage_2d_templates(const om_model* m, const dual* th, dual* Tr) {
+    if (m->joint2) return stage_joint_templates(m, th, Tr);
     int N = m->n_grid, K = m->K, nR = m->n_r2, nP = m->n_p2, B2 = nR + nP;
     dual* q = calloc((size_t)B2, sizeof(dual));
     if (!q) return OM_ENOMEM;
@@ -359,7 +407,7 @@ static int evaluate(const om_model* m, const double* theta, int want_grad,
     dual* lam = calloc(M, sizeof(dual));
     dual* A = calloc((size_t)K * n_slices(m), sizeof(dual));
     dual* tmp = calloc(nw, sizeof(dual));
-    const int B2 = m->n_r2 + m->n_p2;
+    const int B2 = n_slices2(m);
     dual* Tr = B2 > 0 ? calloc((size_t)N * B2, sizeof(dual)) : NULL;
     dual* Y = B2 > 0 ? calloc((size_t)M * B2, sizeof(dual)) : NULL;
     if (!w.Q || !w.mu || !w.sig || !w.den || !w.v || !mu || !lam || !A || !tmp || (B2 > 0 && (!Tr || !Y))) {
@@ -446,8 +494,11 @@ static int evaluate(const om_model* m, const double* theta, int want_grad,
         if (m->tag_frac) { cnt[nh] = m->n_tag; len[nh++] = nw; }
         if (has_rad) { cnt[nh] = m->n_rad_counts; len[nh++] = S * m->n_rad; }
         if (has_psd) { cnt[nh] = m->n_psd_counts; len[nh++] = S * m->n_psd; }
-        if (m->n_r2 > 0) { cnt[nh] = m->n_r2_counts; len[nh++] = m->n_r2 * nw; }
-        if (m->n_p2 > 0) { cnt[nh] = m->n_p2_counts; len[nh++] = m->n_p2 * nw; }
+        if (m->joint2) { cnt[nh] = m->n_r2_counts; len[nh++] = B2 * nw; }
+        else {
+            if (m->n_r2 > 0) { cnt[nh] = m->n_r2_counts; len[nh++] = m->n_r2 * nw; }
+            if (m->n_p2 > 0) { cnt[nh] = m->n_p2_counts; len[nh++] = m->n_p2 * nw; }
+        }
         nsum acc; acc.s = dc(0.0); acc.c = dc(0.0);
         int jj = 0, dom = 0;
         for (int h = 0; h < nh; ++h)

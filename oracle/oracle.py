@@ -61,6 +61,7 @@ class _Model(C.Structure):
         ("psd2", C.c_void_p), ("n_r2_counts", C.c_void_p), ("n_p2_counts", C.c_void_p),
         ("quench", C.c_void_p),
         ("n_es", C.c_int), ("es_edges", C.c_void_p),
+        ("joint2", C.c_int),
     ]
 
 
@@ -103,7 +104,8 @@ class OracleModel:
             "n_sub": _arr(s.counts.get("sub")), "n_tag": _arr(s.counts.get("tag")),
             "n_rad": _arr(s.counts.get("rad")), "n_psd": _arr(s.counts.get("psd")),
             "field": _arr(s.field2d), "psd2": _arr(s.psd2d_prob),
-            "n_r2": _arr(s.counts.get("r2d")), "n_p2": _arr(s.counts.get("p2d")),
+            "n_r2": _arr(s.counts.get("j2d" if getattr(s, "joint2d", False) else "r2d")),
+            "n_p2": _arr(s.counts.get("p2d")),
             "quench": _arr(getattr(s, "quench", None)),
             "es_edges": _arr(getattr(s, "eslices", None), np.int32),
         }
@@ -118,7 +120,8 @@ class OracleModel:
             n_psd=s.n_psd, psd_prob=_ptr(k["psd_prob"]), n_psd_counts=_ptr(k["n_psd"]),
             n_r2=s.n_rad2d, n_p2=s.n_psd2d, field=_ptr(k["field"]), amp=s.field_amp, psd2=_ptr(k["psd2"]),
             n_r2_counts=_ptr(k["n_r2"]), n_p2_counts=_ptr(k["n_p2"]), quench=_ptr(k["quench"]),
-            n_es=0 if k["es_edges"] is None else len(k["es_edges"]) - 1, es_edges=_ptr(k["es_edges"]))
+            n_es=0 if k["es_edges"] is None else len(k["es_edges"]) - 1, es_edges=_ptr(k["es_edges"]),
+            joint2=1 if getattr(s, "joint2d", False) else 0)
         self.ref = C.byref(self.c)
 
     @property

@@ -74,7 +74,7 @@ class ModelSpec:
     # energy window each, templates s_k[i] q_k[b] (1 + field_amp u[i, b]) per slice set
     n_rad2d: int = 0                        # radial slices (uses rad_class, r_fid, r_iv, att_len)
     psd2d_prob: Optional[np.ndarray] = None  # [K, n_psd2d] pulse-shape bin probabilities
-    field2d: Optional[np.ndarray] = None     # [n_grid, n_rad2d + n_psd2d] smooth field u in [-1, 1]
+    field2d: Optional[np.ndarray] = None     # [n_grid, slices] smooth field u in [-1, 1]
     field_amp: float = 0.0
     # species-specific quenching: species k quenches with kB * quench[k] (None -> 1 for all)
     quench: Optional[np.ndarray] = None
@@ -82,6 +82,10 @@ class ModelSpec:
     # [eslices[s], eslices[s+1]), edges from 0 to n_window (None -> one slice, the window);
     # the radial and pulse-shape histograms are then one per slice, slice-major
     eslices: Optional[np.ndarray] = None
+    # the 2D slices as the joint grid of radius and pulse shape: slice (rho, j) = rho n_psd2d + j
+    # holds the energy window of the events in radial bin rho and pulse-shape bin j (the energy x
+    # radius x pulse-shape histogram, one histogram "j2d" instead of "r2d" and "p2d")
+    joint2d: bool = False
     theta_true: Optional[np.ndarray] = None
     species: List[str] = dataclasses.field(default_factory=list)
     counts: Dict[str, np.ndarray] = dataclasses.field(default_factory=dict)
@@ -116,7 +120,7 @@ class ModelSpec:
 
     @property
     def n_slices2d(self) -> int:
-        return self.n_rad2d + self.n_psd2d
+        return self.n_rad2d * self.n_psd2d if self.joint2d else self.n_rad2d + self.n_psd2d
 
     def hist_sizes(self) -> Dict[str, int]:
         """Histogram names and bin counts, in the order every evaluator concatenates them."""
@@ -127,6 +131,9 @@ class ModelSpec:
             out["rad"] = self.n_eslices * self.n_rad      # slice-major: [energy slice][radial bin]
         if self.psd_prob is not None:
             out["psd"] = self.n_eslices * self.n_psd      # slice-major: [energy slice][pulse-shape bin]
+        if self.joint2d:
+            out["j2d"] = self.n_slices2d * self.n_window  # slice-major: [rho][j][window bin]
+            return out
         if self.n_rad2d > 0:
             out["r2d"] = self.n_rad2d * self.n_window    # slice-major: [rho][window bin]
         if self.n_psd2d > 0:
@@ -356,6 +363,16 @@ def sliced(edges_npe=(100.0, 250.0, 500.0, 1000.0), name: str = "sliced", **kw) 
     return spec
 
 
+def joint(n_rad=12, n_psd=10, name: str = "joint", **kw) -> ModelSpec:
+    """The energy x radius x pulse-shape fit: the TFC-vetoed events binned jointly in energy (the
+    window), radius (n_rad bins) and pulse shape (n_psd bins), next to the two TFC energy spectra;
+    species templates s_k[i] p_k[rho] q_k[j] (1 + amp u[i, (rho, j)]), one slice per (rho, j)."""
+    spec = discrimination(n_rad2d=n_rad, n_psd2d=n_psd, name=name, **kw)
+    spec.joint2d = True
+    spec.field2d = np.ascontiguousarray(smooth_field(spec.n_grid, n_rad * n_psd, kw.get("seed", 0)))
+    return spec
+
+
 def discrimination(n_grid=2000, e_max=3.0, width=1.0, lo_npe=100.0, hi_npe=1000.0,
                    n_species=15, total=2e6, L=400, n_rad2d=60, n_psd2d=50, tag_eff=0.9, amp=0.05,
                    seed=0, name="discrimination") -> ModelSpec:
@@ -395,6 +412,9 @@ def config(name: str) -> ModelSpec:
     * ``sliced``   the multivariate model with the radial and pulse-shape terms in three
                   energy slices (100-250, 250-500, 500-1000 npe: Eq. 4's sums over radial
                   and pulse-shape terms); ``small_sliced`` its reduced grid.
+    * ``joint``    the energy x radius x pulse-shape fit: the TFC-vetoed events in 12 radial x 10
+                  pulse-shape bins of the 900-bin window (120 slices) next to the TFC spectra;
+                  ``small_joint`` its reduced grid with 6 x 5 slices.
     * ``small_plain`` / ``small_mv`` / ``small_2d`` reduced grids that the oracle evaluates in
       well under a second (a few seconds for ``small_2d``) but that still span several
       128-row tiles and ragged tails.
@@ -418,6 +438,11 @@ def config(name: str) -> ModelSpec:
         return quenched(name=name)
     if name == "sliced":
         return sliced(name=name)
+    if name == "joint":
+        return joint(name=name)
+    if name == "small_joint":
+        return joint(n_rad=6, n_psd=5, n_grid=520, width=3.0, lo_npe=120.0, hi_npe=900.0, n_species=9,
+                     total=3e5, L=90, name=name)
     if name == "small_sliced":
         return sliced(edges_npe=(120.0, 300.0, 540.0, 900.0), n_grid=520, width=3.0, lo_npe=120.0, hi_npe=900.0,
                       n_species=9, total=3e5, L=90, n_rad=20, n_psd=16, name=name)

@@ -557,3 +557,60 @@ def test_energy_slices_with_2d_slices_are_rejected():
     s = dataclasses.replace(s, eslices=np.array([0, 50, s.n_window], dtype=np.int32))
     with pytest.raises(RuntimeError):
         O.expected(s, s.theta_true)
+
+
+# ---- the joint energy x radius x pulse-shape grid
+
+def _joint_pair(amp=0.0):
+    """The small joint model and the separate 2D model with the same binning, both at amp."""
+    j = dataclasses.replace(I.config("small_joint"), field_amp=amp)
+    sep = dataclasses.replace(j, joint2d=False,
+                              field2d=np.ascontiguousarray(I.smooth_field(j.n_grid, j.n_rad2d + j.n_psd2d, 0)))
+    return j, sep
+
+
+def test_joint_grid_marginals_are_the_separate_2d_slices():
+    """With the field amplitude 0 the templates are separable, so the joint histogram summed over
+    pulse shape is the energy x radius histogram of the separate 2D model, summed over radius its
+    energy x pulse-shape histogram, and summed over both the TFC-vetoed spectrum (bin by bin)."""
+    j, sep = _joint_pair()
+    th = I.parameter_points(j.theta_true, 1, rel=0.03, seed=31, free=j.default_free())[0]
+    hj, hs = _split(j, O.expected(j, th)), _split(sep, O.expected(sep, th))
+    nR, nP, nw = j.n_rad2d, j.n_psd2d, j.n_window
+    grid = hj["j2d"].reshape(nR, nP, nw)
+    np.testing.assert_array_equal(hj["sub"], hs["sub"])
+    np.testing.assert_array_equal(hj["tag"], hs["tag"])
+    np.testing.assert_allclose(grid.sum(axis=1).ravel(), hs["r2d"], rtol=1e-11, atol=1e-12 * hs["r2d"].max())
+    np.testing.assert_allclose(grid.sum(axis=0).ravel(), hs["p2d"], rtol=1e-11, atol=1e-12 * hs["p2d"].max())
+    np.testing.assert_allclose(grid.sum(axis=(0, 1)), hj["sub"], rtol=1e-11, atol=1e-12 * hj["sub"].max())
+
+
+def test_joint_grid_is_linear_in_the_rates():
+    j, _ = _joint_pair(amp=0.05)
+    th = j.theta_true.copy()
+    a, b = th.copy(), th.copy()
+    a[: j.K // 2] = 0.0
+    b[j.K // 2: j.K] = 0.0
+    np.testing.assert_allclose(O.expected(j, a) + O.expected(j, b), O.expected(j, th), rtol=1e-12,
+                               atol=1e-12 * O.expected(j, th).max())
+
+
+def test_joint_grid_dual_gradient_matches_central_differences():
+    j, _ = _joint_pair(amp=0.05)
+    j = j.with_counts(I.poisson_counts(O.expected(j, j.theta_true), 6))
+    th = I.parameter_points(j.theta_true, 1, rel=0.02, seed=32, free=j.default_free())[0]
+    f, g = O.nll(j, th, grad=True)
+    for p in [0, j.K - 1, tail(j, "LY"), tail(j, "c"), tail(j, "kB"), tail(j, "eps"), tail(j, "s_r")]:
+        h = 1e-5 * abs(th[p])
+        tp, tm = th.copy(), th.copy()
+        tp[p] += h
+        tm[p] -= h
+        fd = (O.nll(j, tp) - O.nll(j, tm)) / (2 * h)
+        assert abs(fd - g[p]) * abs(th[p]) <= 1e-6 * (1 + abs(g[p] * th[p])), (p, fd, g[p])
+
+
+def test_joint_grid_needs_both_axes():
+    j, _ = _joint_pair()
+    bad = dataclasses.replace(j, psd2d_prob=None)   # no pulse-shape axis
+    with pytest.raises(RuntimeError):
+        O.expected(bad, j.theta_true)
