@@ -248,6 +248,8 @@ def run_ours(args):
         disc = discrimination_leg(bx, I, stream, B=args.batch2d) if args.batch2d > 0 else None
         fits["quenched"] = variant_leg(bx, I, "quenched", QUENCHED, stream, B=args.batch) if args.quenched else None
         fits["sliced"] = variant_leg(bx, I, "sliced", SLICED, stream, B=args.batch) if args.sliced else None
+        fits["joint_3d"] = (discrimination_leg(bx, I, stream, B=args.batch2d, name="joint", workload=JOINT,
+                                               n_slices=120) if args.joint and args.batch2d > 0 else None)
     if rank != 0:
         return
     report(args, ws, B, total_ms, value, stage_ms, n_evals, entries, e2e, fp64_value, tc_value, clk, fits, disc)
@@ -327,13 +329,20 @@ def toy_fits(bx, I, n_toys, stream):
             "recipe": "bins U{400..1200} x 2 npe from 150 npe, 6-15 species, 1e4-1e7 events, start theta_true (1 + 0.05 z)"}
 
 
-def discrimination_leg(bx, I, stream, B=256, steps=5):
-    """The discrimination regime (K = 15; TFC spectra and the 900 x 60 energy x radius and
-    900 x 50 energy x pulse-shape histograms, 100800 bins, 22 parameters): -lnL + gradient
-    evaluations/s of the tensor-core path (FP32 model, TF32 split GEMMs), the forward GEMM's
-    tensor throughput, and the wall time of one fit."""
+DISCRIMINATION = ("discrimination: K=15, TFC 2x900 + energy x radius 900x60 + energy x pulse-shape 900x50 "
+                  "(100800 bins), 22 parameters, 2e6 events")
+JOINT = ("energy x radius x pulse-shape: K=15, TFC 2x900 + the 900 x 12 x 10 joint histogram of the vetoed "
+         "events (109800 bins), 22 parameters, 2e6 events")
+
+
+def discrimination_leg(bx, I, stream, B=256, steps=5, name="discrimination", workload=DISCRIMINATION, n_slices=112):
+    """A 2D-slice model on the tensor cores: the discrimination regime (K = 15; TFC spectra and
+    the 900 x 60 energy x radius and 900 x 50 energy x pulse-shape histograms, 100800 bins, 22
+    parameters) or the joint energy x radius x pulse-shape grid (12 x 10 cells): -lnL + gradient
+    evaluations/s (FP32 model, TF32 split GEMMs), the forward GEMM's tensor throughput, and the
+    wall time of one fit."""
     import torch
-    s = I.config("discrimination")
+    s = I.config(name)
     gen = bx.Model(s.with_counts(np.zeros(s.n_bins_total)), precision=bx.BX_FP32, stream=stream)
     s = s.with_counts(I.poisson_counts(gen.expected(s.theta_true), 0))
     gen.close()
@@ -365,8 +374,8 @@ def discrimination_leg(bx, I, stream, B=256, steps=5):
         total += e0.elapsed_time(e1)
     stage_ms, n_evals, entries = m.profile(False)
     per = {k: v / max(n_evals, 1) for k, v in stage_ms.items()}
-    # forward GEMM: algorithmic 2 * (in-band response entries) * 112 slices per evaluation
-    alg = 2.0 * entries / max(n_evals, 1) * 112
+    # forward GEMM: algorithmic 2 * (in-band response entries) * slices per evaluation
+    alg = 2.0 * entries / max(n_evals, 1) * n_slices
     peaks = measured_peaks()
     tf32_peak = peaks.get("bf16_tflops", 1887.0) * (1.1 / 2.25)
     tc = alg / (per["forward"] / 1e3) / 1e12
@@ -379,14 +388,13 @@ def discrimination_leg(bx, I, stream, B=256, steps=5):
     fit_s = time.perf_counter() - t0
     mf.close()
     m.close()
-    return {"workload": "discrimination: K=15, TFC 2x900 + energy x radius 900x60 + energy x pulse-shape 900x50 "
-                        "(100800 bins), 22 parameters, 2e6 events", "global_batch": B,
+    return {"workload": workload, "global_batch": B,
             "value": B * steps / (total / 1e3), "unit": "evals/s", "ms_per_step": total / steps,
             "stage_ms_per_launch": {k: round(v, 4) for k, v in per.items()},
             "forward_gemm": {"bound": "tensor", "achieved": tc, "peak": tf32_peak, "unit": "TFLOP/s",
                              "frac": tc / tf32_peak,
                              "peak_basis": "measured bf16 burst x nominal TF32/BF16 ratio 1.1/2.25",
-                             "algorithmic": "2 x in-band response entries x 112 slices per evaluation, over the "
+                             "algorithmic": f"2 x in-band response entries x {n_slices} slices per evaluation, over the "
                                             "forward stage (templates + generation + GEMM)"},
             "fit": {"wall_s": fit_s, "status": int(st), "evals": int(info[0]["n_evals"])}}
 
@@ -519,6 +527,7 @@ def main():
     ap.add_argument("--batch2d", type=int, default=256, help="batch of the 2D-model leg (0: none)")
     ap.add_argument("--quenched", type=int, default=1, help="species-quenching leg (0: none)")
     ap.add_argument("--sliced", type=int, default=1, help="energy-sliced Eq. 4 leg (0: none)")
+    ap.add_argument("--joint", type=int, default=1, help="energy x radius x pulse-shape leg (0: none)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

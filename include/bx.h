@@ -122,6 +122,15 @@ typedef struct {
      * more than one slice requires BX_FP32 or BX_FP64 and no 2D histograms. */
     int n_eslice;
     const int* eslice_edges;    /* [n_eslice + 1], or NULL with n_eslice = 0 */
+    /* The 2D slices as the joint grid of radius and pulse shape (the energy x radius x
+     * pulse-shape fit of the paper's multi-dimensional outlook): with joint2d = 1, slice
+     * (rho, j) = rho * n_psd2d + j of the n_rad2d x n_psd2d grid is the energy window of the
+     * TFC-vetoed events in radial bin rho and pulse-shape bin j.  Templates
+     * s_k[i] p_k[rho] q_k[j] (1 + field_amp u[i][(rho, j)]), normalised per species over the
+     * grid.  Needs n_rad2d >= 1, n_psd2d >= 1 and n_rad2d * n_psd2d + 1 + (tag_frac != NULL)
+     * <= 128; field2d is [N][n_rad2d * n_psd2d], counts_rad2d [n_rad2d * n_psd2d][m_hi - m_lo]
+     * and counts_psd2d is not read. */
+    int joint2d;
 } bx_model_desc;
 
 typedef struct {

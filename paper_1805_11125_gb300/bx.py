@@ -41,6 +41,7 @@ class bx_model_desc(C.Structure):
         ("field_amp", C.c_double), ("counts_rad2d", _P), ("counts_psd2d", _P),
         ("quench", _P),
         ("n_eslice", C.c_int), ("eslice_edges", _P),
+        ("joint2d", C.c_int),
     ]
 
 
@@ -153,7 +154,8 @@ class Model:
                      sub=arr(s.counts.get("sub")), tagc=arr(s.counts.get("tag")),
                      rcls=arr(s.rad_class, np.int32), rad=arr(s.counts.get("rad")), psd=arr(s.psd_prob),
                      psdc=arr(s.counts.get("psd")), psd2=arr(s.psd2d_prob), field=arr(s.field2d),
-                     r2c=arr(s.counts.get("r2d")), p2c=arr(s.counts.get("p2d")),
+                     r2c=arr(s.counts.get("j2d" if getattr(s, "joint2d", False) else "r2d")),
+                     p2c=arr(s.counts.get("p2d")),
                      quench=arr(getattr(s, "quench", None)), es=arr(getattr(s, "eslices", None), np.int32))
             self._keep.append(k)
             has_rad = s.rad_class is not None and s.n_rad > 0
@@ -172,6 +174,7 @@ class Model:
             d.quench = _ptr(k["quench"])
             d.n_eslice = 0 if k["es"] is None else len(k["es"]) - 1
             d.eslice_edges = _ptr(k["es"])
+            d.joint2d = 1 if getattr(s, "joint2d", False) else 0
         opts = bx_options(precision, max_batch, band_sigmas, watchdog_s)
         h = C.c_void_p()
         _check(lib().bx_model_create(C.cast(descs, _P), len(specs), C.byref(opts), _stream_handle(stream),

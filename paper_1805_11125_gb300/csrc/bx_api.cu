@@ -130,24 +130,29 @@ static int validate_desc(const bx_model_desc& d, int t) {
             "toy %d: energy slices x bins exceed %d", t, MAX_RAD);
         if (d.n_eslice > 1) REQ(d.n_rad2d + d.n_psd2d == 0, "toy %d: energy slices with 2D histograms are not supported", t);
     }
-    REQ(d.n_rad2d >= 0 && d.n_psd2d >= 0, "toy %d: n_rad2d, n_psd2d must be >= 0", t);
+    REQ(d.n_rad2d >= 0 && d.n_psd2d >= 0 && d.n_rad2d <= NSL && d.n_psd2d <= NSL,
+        "toy %d: n_rad2d, n_psd2d must lie in [0, %d]", t, NSL);
+    REQ(d.joint2d == 0 || d.joint2d == 1, "toy %d: joint2d must be 0 or 1", t);
+    if (d.joint2d) REQ(d.n_rad2d >= 1 && d.n_psd2d >= 1, "toy %d: the joint grid needs n_rad2d, n_psd2d >= 1", t);
     if (d.n_rad2d + d.n_psd2d > 0) {
-        const int n_sl = 1 + (d.tag_frac ? 1 : 0) + d.n_rad2d + d.n_psd2d;
+        const int B2 = d.joint2d ? d.n_rad2d * d.n_psd2d : d.n_rad2d + d.n_psd2d;   // 2D slices
+        const int n_sl = 1 + (d.tag_frac ? 1 : 0) + B2;
         REQ(n_sl <= NSL, "toy %d: %d slices (TFC spectra + 2D) exceed %d", t, n_sl, NSL);
         REQ(d.n_rad == 0 && d.n_psd == 0, "toy %d: 2D histograms replace the n_rad / n_psd terms", t);
         REQ(d.field2d && std::isfinite(d.field_amp) && d.field_amp >= 0.0 && d.field_amp < 1.0,
             "toy %d: 2D histograms need field2d and 0 <= field_amp < 1", t);
-        for (size_t j = 0; j < (size_t)d.n_grid * (d.n_rad2d + d.n_psd2d); ++j)
+        for (size_t j = 0; j < (size_t)d.n_grid * B2; ++j)
             REQ(std::isfinite(d.field2d[j]) && std::fabs(d.field2d[j]) <= 1.0, "toy %d: field2d must lie in [-1, 1]", t);
         if (d.n_rad2d > 0) {
-            REQ(d.rad_class && d.counts_rad2d && finite_nonneg(d.counts_rad2d, (size_t)d.n_rad2d * nw),
+            const size_t nr = (size_t)(d.joint2d ? B2 : d.n_rad2d) * nw;   // the joint histogram in counts_rad2d
+            REQ(d.rad_class && d.counts_rad2d && finite_nonneg(d.counts_rad2d, nr),
                 "toy %d: energy x radius histogram needs rad_class and counts_rad2d", t);
             for (int k = 0; k < d.n_species; ++k) REQ(d.rad_class[k] == 0 || d.rad_class[k] == 1, "toy %d: rad_class[%d] must be 0 or 1", t, k);
             REQ(d.r_fid > 0.0 && d.r_iv >= d.r_fid && d.att_len > 0.0, "toy %d: radial geometry invalid", t);
         }
         if (d.n_psd2d > 0)
-            REQ(d.psd2d_prob && d.counts_psd2d && finite_nonneg(d.psd2d_prob, (size_t)d.n_species * d.n_psd2d) &&
-                    finite_nonneg(d.counts_psd2d, (size_t)d.n_psd2d * nw),
+            REQ(d.psd2d_prob && finite_nonneg(d.psd2d_prob, (size_t)d.n_species * d.n_psd2d) &&
+                    (d.joint2d || (d.counts_psd2d && finite_nonneg(d.counts_psd2d, (size_t)d.n_psd2d * nw))),
                 "toy %d: energy x pulse-shape histogram needs psd2d_prob and counts_psd2d", t);
     }
     if (d.n_psd > 0)
@@ -269,13 +274,15 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
         T.n_r2 = d.n_rad2d;
         T.n_p2 = d.n_psd2d;
         T.b_r2 = 1 + T.has_tag;
-        T.n_sl = (T.n_r2 + T.n_p2 > 0) ? T.b_r2 + T.n_r2 + T.n_p2 : 0;
+        T.joint2 = d.joint2d;
+        const int B2 = T.joint2 ? T.n_r2 * T.n_p2 : T.n_r2 + T.n_p2;   // 2D slices
+        T.n_sl = (T.n_r2 + T.n_p2 > 0) ? T.b_r2 + B2 : 0;
         T.n_es = d.n_eslice > 1 ? d.n_eslice : 1;
         for (int q = 0; q < T.n_es; ++q) {
             T.es_lo[q] = T.m_lo + (d.n_eslice > 1 ? d.eslice_edges[q] : 0);
             T.es_hi[q] = T.m_lo + (d.n_eslice > 1 ? d.eslice_edges[q + 1] : T.nw);
         }
-        T.nb = T.nw * (1 + T.has_tag) + T.n_es * (T.n_rad + T.n_psd) + (T.n_r2 + T.n_p2) * T.nw;
+        T.nb = T.nw * (1 + T.has_tag) + T.n_es * (T.n_rad + T.n_psd) + B2 * T.nw;
         T.P = T.K + 7;
         T.n_tiles = (T.M + TM - 1) / TM;
         T.n_set = quench_groups(d, T.xi, T.set_of);
@@ -293,8 +300,12 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
         if (T.has_tag) cnt.insert(cnt.end(), d.counts_tag, d.counts_tag + T.nw);
         if (T.n_rad) cnt.insert(cnt.end(), d.counts_rad, d.counts_rad + (size_t)T.n_es * T.n_rad);
         if (T.n_psd) cnt.insert(cnt.end(), d.counts_psd, d.counts_psd + (size_t)T.n_es * T.n_psd);
-        if (T.n_r2) cnt.insert(cnt.end(), d.counts_rad2d, d.counts_rad2d + (size_t)T.n_r2 * T.nw);
-        if (T.n_p2) cnt.insert(cnt.end(), d.counts_psd2d, d.counts_psd2d + (size_t)T.n_p2 * T.nw);
+        if (T.joint2) {
+            cnt.insert(cnt.end(), d.counts_rad2d, d.counts_rad2d + (size_t)B2 * T.nw);
+        } else {
+            if (T.n_r2) cnt.insert(cnt.end(), d.counts_rad2d, d.counts_rad2d + (size_t)T.n_r2 * T.nw);
+            if (T.n_p2) cnt.insert(cnt.end(), d.counts_psd2d, d.counts_psd2d + (size_t)T.n_p2 * T.nw);
+        }
         if ((st = upload(m, d.shapes, (size_t)T.K * T.N, &T.shapes))) break;
         if ((st = upload(m, d.stop_pow, (size_t)T.N, &T.stop_pow))) break;
         {
@@ -324,7 +335,6 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
             // template modulation per (column, slice) and its per-species column sums
             std::vector<float> ut((size_t)T.N * NSL, 0.f);
             std::vector<double> U2((size_t)T.K * NSL, 0.0);
-            const int B2 = T.n_r2 + T.n_p2;
             for (int i = 0; i < T.N; ++i)
                 for (int b = 0; b < T.n_sl; ++b) {
                     const double u = b < T.b_r2 ? 1.0 : 1.0 + d.field_amp * d.field2d[(size_t)i * B2 + (b - T.b_r2)];

@@ -91,6 +91,7 @@ struct Toy {
     // 2D model (n_sl > 0): slices b = 0 vetoed, [1 tagged], then n_r2 radial and n_p2
     // pulse-shape slices of the vetoed events; counts are slice-major [n_sl][nw]
     int n_sl, n_r2, n_p2, b_r2;   // b_r2: first radial slice
+    int joint2;                   // the 2D slices are the joint grid: slice b_r2 + rho n_p2 + j
     const float* ut;              // [N][NSL]: template modulation 1 + amp u[i][b] (1 for the TFC slices)
     const double* U2;             // [K][NSL]: sum_i s_k[i] ut[i][b] (slice-set normalisation)
     const double* psd2;           // [K][n_p2]

@@ -175,3 +175,24 @@ def test_energy_slice_rejections_on_host():
     with pytest.raises(bx.BxError) as e:
         make([0, 50, s2.n_window], spec=s2)
     assert e.value.status == bx.BX_EINVAL and "2D" in str(e.value)
+
+
+def test_joint_grid_rejections_on_host():
+    """The joint energy x radius x pulse-shape grid needs both axes and at most 128 slices with
+    the TFC spectra (checked before any device is touched)."""
+    import dataclasses
+    s = I.config("small_joint")
+
+    def make(spec):
+        spec = spec.with_counts(np.ones(spec.n_bins_total))
+        return bx.Model(spec, precision=bx.BX_FP32)
+
+    nopsd = dataclasses.replace(s, psd2d_prob=None)
+    with pytest.raises(bx.BxError) as e:
+        make(nopsd)
+    assert e.value.status == bx.BX_EINVAL and "joint grid" in str(e.value)
+    wide = I.joint(n_rad=12, n_psd=11, n_grid=520, width=3.0, lo_npe=120.0, hi_npe=900.0, n_species=9,
+                   total=3e5, L=90, name="too_many_cells")
+    with pytest.raises(bx.BxError) as e:
+        make(wide)
+    assert e.value.status == bx.BX_EINVAL and "exceed" in str(e.value)
