@@ -154,7 +154,8 @@ void bx_model_destroy(bx_model* model);
 int bx_model_set_stream(bx_model* model, void* cuda_stream);
 /* P = 7 + max_t K_t: the row stride of every theta / grad array */
 int bx_model_n_params(const bx_model* model);
-/* bins of toy t: window (+ window if tagged) + slices * (n_rad + n_psd) + (n_rad2d + n_psd2d) window */
+/* bins of toy t: window (+ window if tagged) + slices * (n_rad + n_psd) + B2 window, with
+ * B2 = n_rad2d + n_psd2d, or n_rad2d * n_psd2d for the joint grid */
 int bx_model_n_bins(const bx_model* model, int toy);
 /* Sticky device status (BX_OK or BX_ETIMEOUT) after synchronising the model's stream. */
 int bx_model_status(bx_model* model);
