@@ -614,3 +614,53 @@ def test_joint_grid_needs_both_axes():
     bad = dataclasses.replace(j, psd2d_prob=None)   # no pulse-shape axis
     with pytest.raises(RuntimeError):
         O.expected(bad, j.theta_true)
+
+
+# ---- template normalisation with the field on (Eq. 4 slice sets, count conservation)
+
+def _conserving(spec, amp):
+    """The spec on an axis wide enough for every species (window = whole axis from 0 npe, the
+    top 600 npe above the highest visible energy) at field amplitude amp."""
+    top = int(math.ceil((spec.e_max * 500.0 + 600.0) / spec.width))
+    return dataclasses.replace(spec, field_amp=amp, m_lo=0, m_hi=top)
+
+
+@pytest.mark.parametrize("amp", [0.05, 0.5])
+def test_2d_slice_sets_conserve_each_species_with_the_field_on(amp):
+    """With eps = 0 and an axis that holds every species' whole response (Eq. 1 columns of unit
+    mass), the energy x radius histogram summed over energy and over its slices holds exactly the
+    TFC-vetoed events r_k (1 - t_k) of species k, whatever the field does to the template's
+    energy shape per slice; likewise the energy x pulse-shape histogram.  A normalisation N_k
+    without the field factor (1 + amp u), or over the wrong slice set, breaks it by ~amp."""
+    s = _conserving(I.config("small_2d"), amp)
+    for k in range(s.K):
+        th = s.theta_true.copy()
+        th[: s.K] = 0.0
+        th[k] = 1234.5
+        th[tail(s, "eps")] = 0.0
+        th[tail(s, "s_r")] = 1.3                      # the external radial shape off its default
+        sub, r2, p2 = _split_2d(s, O.expected(s, th))
+        want = th[k] * (1.0 - s.tag_frac[k])
+        assert sub.sum() == pytest.approx(want, rel=1e-12)
+        assert r2.sum() == pytest.approx(want, rel=1e-12)
+        assert p2.sum() == pytest.approx(want, rel=1e-12)
+
+
+@pytest.mark.parametrize("amp", [0.05, 0.5])
+def test_joint_grid_conserves_each_species_with_the_field_on(amp):
+    """The joint grid holds the TFC-vetoed events r_k (1 - t_k) of each species once, summed over
+    energy and every radius x pulse-shape cell (one normalisation over the whole grid)."""
+    j, _ = _joint_pair(amp)
+    j = _conserving(j, amp)
+    nR, nP, nw = j.n_rad2d, j.n_psd2d, j.n_window
+    for k in range(j.K):
+        th = j.theta_true.copy()
+        th[: j.K] = 0.0
+        th[k] = 987.0
+        th[tail(j, "eps")] = 0.0
+        th[tail(j, "s_r")] = 0.8
+        h = _split(j, O.expected(j, th))
+        want = th[k] * (1.0 - j.tag_frac[k])
+        grid = h["j2d"].reshape(nR, nP, nw)
+        assert h["sub"].sum() == pytest.approx(want, rel=1e-12)
+        assert grid.sum() == pytest.approx(want, rel=1e-12)
