@@ -130,6 +130,28 @@ def make_dataset(bx, I, spec, seed=0):
     return spec.with_counts(I.poisson_counts(mu, seed))
 
 
+def oracle_fit(spec, gpu_fit=None):
+    """The oracle's own fit (FP64 C, damped Newton on dual-number gradients, EDM < 1e-12) of the
+    data the GPU's plain-model leg fitted, from theta_true; its wall time on the host cores and,
+    given the GPU's best fit, the largest difference of the free parameters in units of
+    max(1e-4 |theta|, 0.01 sigma) and |Delta(-2 lnL)|."""
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    r = O.fit(spec, spec.theta_true, tol_edm=1e-12)
+    out = {"config": spec.name, "wall_s": time.perf_counter() - t0, "iters": r["iters"], "status": r["status"],
+           "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))}
+    if gpu_fit is not None:
+        free = spec.default_free().astype(bool)
+        sig = np.sqrt(np.maximum(np.diag(r["cov"]), 0.0))
+        tol = np.maximum(1e-4 * np.abs(r["theta"]), 0.01 * sig)
+        for key, (th, nll) in gpu_fit.items():
+            d = np.abs(np.asarray(th)[: spec.P] - r["theta"])
+            out[key] = {"max_dtheta_over_tol": float(np.max(d[free] / tol[free])),
+                        "max_rel_rate_diff": float(np.max(d[: spec.K] / np.abs(r["theta"][: spec.K]))),
+                        "d2nll": 2.0 * abs(nll - r["nll"])}
+    return out
+
+
 def cpu_baseline(spec_name: str, seconds: float, seed: int = 0):
     """The oracle as it stands (FP64 C, dual-number gradient, OpenMP over output bins) on a
     bounded sample of the same workload: NLL+gradient at consecutive parameter points."""
@@ -239,9 +261,14 @@ def run_ours(args):
         raise bx.BxError(st, bx.lib().bx_last_error().decode())
     value, total_ms = job_throughput(sum(a.elapsed_time(b) for a, b in evs), B, args.steps, ws, dev)
 
+    ceil = ceilings(bx, stream) if not args.no_ceilings else None
     e2e, fp64_value, tc_value, fits, disc = None, None, None, None, None
+    plain = est = c5 = None
     if not args.no_extras:
-        e2e, fp64_value, tc_value = extras(bx, model, spec, pts, theta, stream, B, P, ws, args)
+        e2e, fp64_value, tc_value = extras(bx, model, spec, pts, theta, stream, B, P, ws, args, flush)
+        plain = plain_leg(bx, I, stream) if args.plain else None
+        est = estimators_leg(bx, I, stream, B=args.batch // 3) if args.estimators else None
+        c5 = differentiated_fit_leg(bx, I, stream, iters=args.c5_iters) if args.c5_iters > 0 else None
         fits = fit_times(bx, I, spec, stream)
         if args.toys > 0:
             fits["batched_toys"] = toy_fits(bx, I, args.toys, stream)
@@ -252,10 +279,31 @@ def run_ours(args):
                                                n_slices=120) if args.joint and args.batch2d > 0 else None)
     if rank != 0:
         return
-    report(args, ws, B, total_ms, value, stage_ms, n_evals, entries, e2e, fp64_value, tc_value, clk, fits, disc)
+    report(args, ws, B, total_ms, value, stage_ms, n_evals, entries, e2e, fp64_value, tc_value, clk, fits, disc,
+           ceil=ceil, plain=plain, est=est, c5=c5)
 
 
-def extras(bx, model, spec, pts, theta, stream, B, P, ws, args):
+def ceilings(bx, stream):
+    """The roofline's denominators, measured here: input-free microkernels (bx_ceiling) of the
+    forward's FP32 bin-mass routine alone and with its per-entry accumulation (entries/s), and
+    FP64 / FP32 FMA throughput; each timed after a warm-up launch, clocks sampled meanwhile."""
+    import torch
+    out = {}
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for name, which, reps, unit in (("resp", bx.BX_CEIL_RESP, 96, "Gentries/s"),
+                                        ("resp_acc", bx.BX_CEIL_RESP_ACC, 96, "Gentries/s"),
+                                        ("fp64_fma", bx.BX_CEIL_FMA64, 8, "TFLOP/s"),
+                                        ("fp32_fma", bx.BX_CEIL_FMA32, 96, "TFLOP/s")):
+            best = 0.0
+            for _ in range(3):
+                ms, units = bx.bx_ceiling(which, reps, stream)
+                best = max(best, units / (ms / 1e3))
+            out[name] = {"value": best / (1e9 if unit == "Gentries/s" else 1e12), "unit": unit}
+    out["clocks"] = clk.summary()
+    return out
+
+
+def extras(bx, model, spec, pts, theta, stream, B, P, ws, args, flush):
     import torch
     # end to end through the public call with host buffers (pinned), copies inside the region
     th_h = torch.tensor(pts, dtype=torch.float64).pin_memory()
@@ -273,19 +321,23 @@ def extras(bx, model, spec, pts, theta, stream, B, P, ws, args):
     e2e = {"value": ws * B * e2e_steps / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": B * P * 8,
            "d2h_bytes_per_step": B * 8 + B * P * 8}
 
-    # the FP64 GPU form of the same evaluation
-    B64 = min(B, 256)
-    m64 = bx.Model(spec, precision=bx.BX_FP64, max_batch=B64, stream=stream)
-    th64 = theta[:B64].contiguous()
-    m64.nll_batch(th64, grad=True)
+    # the FP64 GPU form of the same evaluation, with the main leg's protocol: the same batch of
+    # points, W warm-up steps, the L2 flushed before each timed step, CUDA events around each step
+    m64 = bx.Model(spec, precision=bx.BX_FP64, max_batch=B, stream=stream)
+    for _ in range(args.warmup):
+        m64.nll_batch(theta, grad=True)
     torch.cuda.synchronize()
+    steps64 = min(args.steps, args.fp64_steps)
+    total64 = 0.0
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(3):
-        m64.nll_batch(th64, grad=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    fp64_value = ws * B64 * 3 / (e0.elapsed_time(e1) / 1e3)
+    for _ in range(steps64):
+        flush.zero_()
+        e0.record(stream)
+        m64.nll_batch(theta, grad=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total64 += e0.elapsed_time(e1)
+    fp64_value = ws * B * steps64 / (total64 / 1e3)
     m64.close()
 
     # the tensor-core species-resolved form (BX_TF32X3) of the same evaluation
@@ -454,6 +506,144 @@ def variant_leg(bx, I, name, workload, stream, B=2736, steps=5):
             "fit": {"wall_s": fit_s, "status": int(st), "evals": int(info[0]["n_evals"])}}
 
 
+PLAIN = "plain single spectrum: K=8 on a 2000-point grid, 400 bins of 2 npe over 150-950 npe, 1e6 events, pile-up L=400"
+ESTIMATORS = ("three energy estimators (npe, charge, nhits) of the multivariate dataset: 3 x 2 TFC spectra of "
+              "~900 bins, radial 60 and pulse-shape 50 on the first, 30 joint parameters")
+
+
+def timed_batches(bx, m, theta, stream, steps, flush, grad=True):
+    """Mean -lnL (+ gradient) evaluations/s of one batch on the device: 2 warm-up calls, then
+    `steps` calls with the L2 flushed before each, CUDA events around each on the stream."""
+    import torch
+    for _ in range(2):
+        m.nll_batch(theta, grad=grad)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    total = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        e0.record(stream)
+        m.nll_batch(theta, grad=grad)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1)
+    return theta.shape[0] * steps / (total / 1e3)
+
+
+def plain_leg(bx, I, stream, n_points=1000, steps=5):
+    """The plain single-spectrum model: -lnL + gradient at 1000 seeded points theta_true (1 + 0.02 z)
+    in one batch (FP64 and FP32), then one fit from theta_true (1 + 0.1 z): FP64, and FP32 polished
+    by FP64.  Returns (the JSON record, the data spec, the GPU best fits) -- the CPU-baseline leg
+    fits the same data with the oracle."""
+    import torch
+    s = make_dataset(bx, I, I.config("plain"), seed=0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    pts = I.parameter_points(s.theta_true, n_points, rel=0.02, seed=500, free=s.default_free())
+    theta = torch.tensor(pts, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    out = {"workload": PLAIN, "points": n_points}
+    for name, prec in (("fp64", bx.BX_FP64), ("fp32", bx.BX_FP32)):
+        m = bx.Model(s, precision=prec, max_batch=n_points, stream=stream)
+        out[name + "_evals_per_s"] = timed_batches(bx, m, theta, stream, steps, flush)
+        m.close()
+    th0 = I.parameter_points(s.theta_true, 1, rel=0.1, seed=501, free=s.default_free())
+    m64 = bx.Model(s, precision=bx.BX_FP64, max_batch=8 + 2 * s.P, stream=stream)
+    m32 = bx.Model(s, precision=bx.BX_FP32, max_batch=8 + 2 * s.P, stream=stream)
+    m64.fit(th0)
+    m32.fit(th0)
+    t0 = time.perf_counter()
+    t64, i64, st64 = m64.fit(th0)
+    out["fit_fp64_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    t32, i32, st32 = m32.fit(th0)
+    tm, im, stm = m64.fit(t32)
+    out["fit_mixed_s"] = time.perf_counter() - t0
+    out["fit_status"] = [int(st64), int(stm)]
+    out["fit_evals"] = {"fp64": int(i64[0]["n_evals"]), "fp32": int(i32[0]["n_evals"]), "polish": int(im[0]["n_evals"])}
+    m64.close()
+    m32.close()
+    return out, s, {"fp64": (t64[0], i64[0]["nll"]), "mixed": (tm[0], im[0]["nll"])}
+
+
+def estimators_leg(bx, I, stream, B=912, steps=5):
+    """Three energy estimators of the multivariate dataset fitted jointly (bx_model_create_estimators):
+    joint -lnL + gradient evaluations/s at B points (each = 3 estimator evaluations in the same
+    launch), FP32 and FP64, and one joint fit (FP32, polished by FP64) from theta_true (1 + 0.05 z)."""
+    import torch
+    specs = [make_dataset(bx, I, sp, seed=600 + e) for e, sp in enumerate(I.estimators("multivariate"))]
+    th_true = I.estimator_theta(specs)
+    free = np.concatenate([specs[0].default_free(), np.ones(4 * (len(specs) - 1), dtype=np.uint8)])
+    dev = torch.device("cuda", torch.cuda.current_device())
+    theta = torch.tensor(I.parameter_points(th_true, B, rel=0.02, seed=601, free=free), dtype=torch.float64,
+                         device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    out = {"workload": ESTIMATORS, "global_batch": B, "unit": "joint evals/s"}
+    for name, prec in (("fp32", bx.BX_FP32), ("fp64", bx.BX_FP64)):
+        m = bx.Model(specs, precision=prec, max_batch=B, stream=stream, n_est=len(specs))
+        out[name + "_value"] = timed_batches(bx, m, theta, stream, steps if prec == bx.BX_FP32 else 1, flush)
+        m.close()
+    P = th_true.shape[0]
+    m32 = bx.Model(specs, precision=bx.BX_FP32, max_batch=8 + 2 * P, stream=stream, n_est=len(specs))
+    m64 = bx.Model(specs, precision=bx.BX_FP64, max_batch=8 + 2 * P, stream=stream, n_est=len(specs))
+    th0 = I.parameter_points(th_true, 1, rel=0.05, seed=602, free=free)
+    m32.fit(th0)
+    t0 = time.perf_counter()
+    t32, i32, st32 = m32.fit(th0)
+    tm, im, stm = m64.fit(t32)
+    out["fit"] = {"wall_s": time.perf_counter() - t0, "status": [int(st32), int(stm)],
+                  "evals": int(i32[0]["n_evals"]) + int(im[0]["n_evals"]), "parameters": int(P)}
+    m32.close()
+    m64.close()
+    return out
+
+
+def differentiated_fit_leg(bx, I, stream, iters=1000):
+    """The 2D discrimination model (22 parameters) minimised by a quasi-Newton method through the
+    autograd interface: torch.optim.LBFGS (strong-Wolfe line search, history 30) on bx.BxNLL, whose
+    gradient is the hand-written adjoint (the response regenerated in the adjoint kernel, never
+    stored), for up to `iters` iterations from theta_true (1 + 0.02 z); compared with the device
+    Newton fit (bx_fit) from the same start."""
+    import torch
+    s = I.config("discrimination")
+    gen = bx.Model(s.with_counts(np.zeros(s.n_bins_total)), precision=bx.BX_FP32, stream=stream)
+    s = s.with_counts(I.poisson_counts(gen.expected(s.theta_true), 0))
+    gen.close()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    free = s.default_free().astype(bool)
+    th0 = I.parameter_points(s.theta_true, 1, rel=0.02, seed=700, free=s.default_free())[0]
+    m = bx.Model(s, precision=bx.BX_FP32, max_batch=1, stream=stream)
+    base = torch.tensor(th0, dtype=torch.float64, device=dev)
+    scale = torch.tensor(np.where(free, np.abs(th0), 0.0), dtype=torch.float64, device=dev)
+    u = torch.zeros(s.P, dtype=torch.float64, device=dev, requires_grad=True)
+    opt = torch.optim.LBFGS([u], lr=1.0, max_iter=iters, max_eval=2 * iters, tolerance_grad=0.0,
+                            tolerance_change=0.0, history_size=30, line_search_fn="strong_wolfe")
+    calls = [0]
+
+    def closure():
+        opt.zero_grad()
+        f = bx.BxNLL.apply((base + scale * u)[None, :], m).sum()
+        f.backward()
+        calls[0] += 1
+        return f
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    opt.step(closure)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    st = opt.state[u]
+    th = (base + scale * u).detach().cpu().numpy()
+    nll = m.nll(th)
+    m.close()
+    mf = bx.Model(s, precision=bx.BX_FP32, max_batch=8 + 2 * s.P, stream=stream)
+    _, info, fst = mf.fit(th0)
+    mf.close()
+    return {"workload": DISCRIMINATION, "minimiser": "torch.optim.LBFGS(strong_wolfe) on bx.BxNLL (FP32 model)",
+            "iterations": int(st.get("n_iter", 0)), "evaluations": calls[0], "wall_s": wall,
+            "evals_per_s": calls[0] / wall, "nll": nll, "nll_device_newton": float(info[0]["nll"]),
+            "device_newton_status": int(fst), "d2nll_vs_device_newton": 2.0 * (nll - float(info[0]["nll"]))}
+
+
 def fit_times(bx, I, spec, stream):
     """Full-fit wall time of one multivariate fit started at theta_true (1 + 0.1 z): FP32, FP64,
     and FP32 polished by FP64 (host wall clock around bx_fit, second call on a warm model)."""
@@ -484,21 +674,34 @@ def fit_times(bx, I, spec, stream):
 
 
 def report(args, ws, B, total_ms, value, stage_ms, n_evals, entries, e2e, fp64_value, tc_value, clk, fits=None,
-           disc=None):
-    # roofline of the dominant kernel (ALU-bound: FP32 issue rate of 152 SMs x 128 lanes)
+           disc=None, ceil=None, plain=None, est=None, c5=None):
+    # roofline of the dominant kernel, the rate-first forward: in-band response entries it
+    # generated and contracted per second against the measured ceiling of its bin-mass routine
     per_launch = {k: v / max(n_evals, 1) for k, v in stage_ms.items()}
-    dom = max(("forward", "adjoint"), key=lambda k: per_launch[k])
-    ops = (FWD_OPS_PER_ENTRY if dom == "forward" else BWD_OPS_PER_ENTRY) * entries / max(n_evals, 1)
-    peak = SMS * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
-    achieved = ops / (per_launch[dom] / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": "k_fwd_f32" if dom == "forward" else "k_bwd_f32",
-                "achieved": achieved, "peak": peak, "unit": "Top/s", "frac": achieved / peak,
-                "traffic": TRAFFIC_PER_ITEM["k_fwd_f32" if dom == "forward" else "k_bwd_f32"] * B,
-                "entries_per_launch": entries / max(n_evals, 1),
-                "ops_per_entry": FWD_OPS_PER_ENTRY if dom == "forward" else BWD_OPS_PER_ENTRY,
-                "peak_basis": "FP32 issue rate 152 SMs x 128 lanes x 2070 MHz (derived, not measured)",
-                "stage_ms_per_launch": {k: round(v, 4) for k, v in per_launch.items()}}
+    ent = entries / max(n_evals, 1)
+    achieved = ent / (per_launch["forward"] / 1e3) / 1e9
+    issue_peak = SMS * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
+    roofline = {"bound": "alu", "kernel": "k_fwd_f32", "achieved": achieved, "unit": "Gentries/s",
+                "traffic": TRAFFIC_PER_ITEM["k_fwd_f32"] * B, "entries_per_launch": ent,
+                "stage_ms_per_launch": {k: round(v, 4) for k, v in per_launch.items()},
+                "issue_rate": {"achieved": FWD_OPS_PER_ENTRY * ent / (per_launch["forward"] / 1e3) / 1e12,
+                               "peak": issue_peak, "unit": "Top/s", "ops_per_entry": FWD_OPS_PER_ENTRY,
+                               "basis": "FP32 ops per entry counted from the source / 152 SMs x 128 lanes x 2070 MHz"}}
+    if ceil:
+        peak = ceil["resp"]["value"]
+        roofline.update({"peak": peak, "frac": achieved / peak,
+                         "peak_basis": "measured: input-free microkernel of the forward's FP32 bin-mass routine "
+                                       "(bx_ceiling BX_CEIL_RESP), this process, this GPU",
+                         "frac_vs_entry_with_accumulation": achieved / ceil["resp_acc"]["value"]})
+        roofline["issue_rate"]["frac_of_measured_fp32_fma"] = (roofline["issue_rate"]["achieved"] /
+                                                               (ceil["fp32_fma"]["value"] / 2.0))
+    else:
+        roofline.update({"peak": issue_peak, "frac": roofline["issue_rate"]["achieved"] / issue_peak,
+                         "unit": "Top/s", "achieved": roofline["issue_rate"]["achieved"],
+                         "peak_basis": "FP32 issue rate (derived, not measured)"})
     cb = None if args.no_cpu_baseline else cpu_baseline("multivariate", args.cpu_seconds)
+    if cb is not None and plain is not None:
+        cb["oracle_fit"] = oracle_fit(plain[1], plain[2])
     line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -506,8 +709,9 @@ def report(args, ws, B, total_ms, value, stage_ms, n_evals, entries, e2e, fp64_v
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}"},
             "fp64_gpu_value": fp64_value, "mixed_over_fp64": value / fp64_value if fp64_value else None,
             "tf32x3_gpu_value": tc_value,
-            "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "fit": fits, "discrimination_2d": disc,
-            "gpu_launches": 5 * args.steps, "clocks": clk.summary()}
+            "roofline": roofline, "ceilings": ceil, "cpu_baseline": cb, "e2e": e2e, "fit": fits,
+            "discrimination_2d": disc, "plain": plain[0] if plain else None, "estimators": est,
+            "differentiated_fit": c5, "gpu_launches": 5 * args.steps, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
 
@@ -528,6 +732,11 @@ def main():
     ap.add_argument("--quenched", type=int, default=1, help="species-quenching leg (0: none)")
     ap.add_argument("--sliced", type=int, default=1, help="energy-sliced Eq. 4 leg (0: none)")
     ap.add_argument("--joint", type=int, default=1, help="energy x radius x pulse-shape leg (0: none)")
+    ap.add_argument("--plain", type=int, default=1, help="plain single-spectrum leg: 1000 points + one fit (0: none)")
+    ap.add_argument("--estimators", type=int, default=1, help="three-energy-estimator leg (0: none)")
+    ap.add_argument("--c5-iters", type=int, default=1000, help="quasi-Newton iterations of the autograd leg (0: none)")
+    ap.add_argument("--fp64-steps", type=int, default=10, help="timed steps of the FP64 GPU form (main protocol)")
+    ap.add_argument("--no-ceilings", action="store_true", help="skip the ceiling microkernels")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -150,6 +150,23 @@ int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_options* op
  * holds the window's spectra, the full axis of Eq. 3 spectra, the pile-up spectrum and the
  * per-column Eq. 4 weights.  On a GB300 that bounds e.g. an 8192-point grid to an axis of
  * about 2000 bins; the 1D limits above are the upper bounds of each size alone.) */
+/* Several energy estimators of each dataset, fitted jointly (Sec. 3: the charge, the number of
+ * detected photons and the number of fired channels are each an observable N_x with its own
+ * response R_x of Eq. 1).  descs holds n_data x n_est descriptions, dataset-major: descs[t n_est + e]
+ * is estimator e of dataset t, with its own bin width, window, random-trigger spectrum and data.
+ * The estimators of a dataset share the events, so their grids, species shapes, stopping power,
+ * tag fractions and quenching must be identical (BX_EINVAL otherwise); only estimator 0 may carry
+ * the radial and pulse-shape terms, and none 2D histograms or energy slices; 1 <= n_est <= 4.
+ * The rates, kB, eps and s_r are shared; each estimator has its own LY, a, b, c.  Every call then
+ * takes datasets as toys (toy_idx in [0, n_data)) and the joint parameter vector
+ *   theta = [r_0 .. r_{K-1}, LY_0, a_0, b_0, c_0, kB, eps, s_r, LY_1, a_1, b_1, c_1, ..., c_{n_est-1}]
+ * (P = K + 7 + 4 (n_est - 1); n_est = 1 is bx_model_create): -lnL is the sum of the estimators'
+ * -lnL (each evaluated at [r, LY_e, a_e, b_e, c_e, kB, eps, s_r]), its gradient is in the joint
+ * layout, bx_expected returns the estimators' bins one estimator after the other, and bx_fit fits
+ * the joint vector (free_mask, lo, hi in the joint layout of the largest K).  max_batch counts
+ * datasets; the workspace holds max_batch x n_est evaluation items. */
+int bx_model_create_estimators(const bx_model_desc* descs, int n_data, int n_est, const bx_options* opts,
+                               void* cuda_stream, bx_model** out);
 void bx_model_destroy(bx_model* model);
 int bx_model_set_stream(bx_model* model, void* cuda_stream);
 /* P = 7 + max_t K_t: the row stride of every theta / grad array */
@@ -212,7 +229,8 @@ typedef struct {
                                    parameters held at a bound are 0 */
 } bx_fit_opts;
 /* free_mask/lo/hi are given in the layout of a toy with max K species: slots 0..Kmax-1 are
- * rates, Kmax..Kmax+6 the seven response/pile-up/radial parameters; a toy with K_t < Kmax
+ * rates, Kmax..Kmax+6 the seven response/pile-up/radial parameters (then LY, a, b, c of every
+ * further energy estimator of a bx_model_create_estimators model); a toy with K_t < Kmax
  * species uses its first K_t rate slots. */
 
 typedef struct {
@@ -258,13 +276,29 @@ int bx_selftest_watchdog(double budget_s);
  * caller: shapes [K][n_grid], stop_pow [n_grid], tag_frac [K] or NULL, theta [K + 7],
  * lambda [m_hi] or [2][m_hi].  Limits of the fixed scratch: n_grid <= 4096, m_hi <= 4096,
  * K <= 16 (BX_EINVAL beyond).  The work is enqueued on cuda_stream and the call returns.
- * Its scratch is one 481 KiB static device array per device, whose address is looked up on
+ * Its scratch is one 530 KiB static device array per device, whose address is looked up on
  * the first call made on that device (make it before any stream capture); all calls share
- * it, so calls that overlap on the GPU race.  Invalid response parameters (sigma^2 <= 0)
- * leave lambda unwritten. */
+ * it, so calls that overlap on the GPU race.  A parameter point outside the model's domain
+ * (non-finite theta, LY <= 0, sigma^2 <= 0 at a grid point) fills lambda with NaN; the call
+ * itself still returns BX_OK, because the check runs on the device after it has returned. */
 int bx_spectra_noalloc(int n_grid, double e_max, int n_species, const double* shapes,
                        const double* stop_pow, const double* tag_frac, double width, int m_hi,
                        const double* theta, double* lambda, void* cuda_stream);
+
+/* Ceilings of the roofline (measurement tools; the paper has no counterpart).  Runs one
+ * input-free microkernel on the current device, on cuda_stream, over a grid of whole waves
+ * (every SM full), after one shorter warm-up launch, and returns its CUDA-event time in *ms
+ * and the units it completed in *units:
+ *   BX_CEIL_RESP      response entries of the FP32 bin-mass routine of the forward (Eq. 1,
+ *                     3-point Gauss-Legendre, the branch of in-band entries) alone;
+ *   BX_CEIL_RESP_ACC  response entries with the forward's accumulation per entry (two
+ *                     compensated row sums and one column-sum FMA);
+ *   BX_CEIL_FMA64     FP64 floating-point operations (FMA = 2);
+ *   BX_CEIL_FMA32     FP32 floating-point operations (FMA = 2).
+ * reps (1 .. 2^20) scales the work: 512 entries, or 1024 flops, per thread and rep.
+ * Allocates and frees a small device buffer; synchronises the stream. */
+enum { BX_CEIL_RESP = 0, BX_CEIL_RESP_ACC = 1, BX_CEIL_FMA64 = 2, BX_CEIL_FMA32 = 3 };
+int bx_ceiling(int which, int reps, void* cuda_stream, double* ms, double* units);
 
 const char* bx_last_error(void);
 const char* bx_status_string(int status);

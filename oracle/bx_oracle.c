@@ -638,17 +638,97 @@ static int cholesky_solve(int n, double* A, const double* b, double* x) {
 
 /* Damped Newton fit.  info[0] = -lnL, info[1] = EDM, info[2] = iterations, info[3] = status.
  * cov (P x P, may be NULL): inverse Hessian on the free set at the optimum (0 elsewhere). */
+/* -lnL (and gradient) of the objective a fit minimises: one model, or the several energy
+ * estimators of one dataset (om_nll_est). */
+typedef int (*om_objective)(const void* ctx, const double* theta, double* f, double* g);
+
+typedef struct { const om_model* m; int E; } est_ctx;
+
+static int obj_single(const void* ctx, const double* theta, double* f, double* g) {
+    return om_nll((const om_model*)ctx, theta, f, g);
+}
+
+static int fit_core(om_objective om_obj, const void* ctx, int P, const double* theta0, const unsigned char* free_mask,
+                    const double* lo, const double* hi, double tol_edm, int max_iter,
+                    double* theta_out, double* info, double* cov);
+
 int om_fit(const om_model* m, const double* theta0, const unsigned char* free_mask,
            const double* lo, const double* hi, double tol_edm, int max_iter,
            double* theta_out, double* info, double* cov) {
-    int P = m->K + 7, st = OM_ENOTCONV, it;
+    return fit_core(obj_single, m, m->K + 7, theta0, free_mask, lo, hi, tol_edm, max_iter, theta_out, info, cov);
+}
+
+/* Several energy estimators of one dataset (Sec. 3: the charge, the number of detected
+ * photons and the number of fired channels, each an observable N_x with its own response
+ * R_x of Eq. 1), fitted jointly.  Reading: the estimators see the same events, so the
+ * deposited-energy spectra and everything that acts on them before the detector response
+ * are shared -- the rates, the Birks constant kB, the pile-up probability eps and the radial
+ * scale s_r -- while each estimator has its own response parameters (LY, a, b, c), binning,
+ * window, random-trigger spectrum and data; -lnL is the sum of the estimators' -lnL (their
+ * histograms enter as separate terms, as the several terms of Eq. 4 do).  The radial and
+ * pulse-shape terms belong to estimator 0 only.  Joint parameter vector (P = K + 7 + 4 (E - 1)):
+ *   [r_0 .. r_{K-1}, LY_0, a_0, b_0, c_0, kB, eps, s_r, LY_1, a_1, b_1, c_1, ..., c_{E-1}]
+ * so that E = 1 is the single model.  Estimator e is evaluated at
+ *   [r_0 .. r_{K-1}, LY_e, a_e, b_e, c_e, kB, eps, s_r]. */
+int om_est_theta(int K, int e, const double* theta, double* th_e) {
+    for (int k = 0; k < K; ++k) th_e[k] = theta[k];
+    const int src = e == 0 ? K : K + 7 + 4 * (e - 1);
+    for (int j = 0; j < 4; ++j) th_e[K + j] = theta[src + j];
+    for (int j = 4; j < 7; ++j) th_e[K + j] = theta[K + j];
+    return OM_OK;
+}
+
+int om_nll_est(const om_model* ms, int E, const double* theta, double* nll, double* grad) {
+    if (E < 1) return OM_EINVAL;
+    const int K = ms[0].K, P = K + 7 + 4 * (E - 1);
+    if (P > OPMAX) return OM_EINVAL;
+    for (int e = 1; e < E; ++e)
+        if (ms[e].K != K || ms[e].n_rad > 0 || ms[e].n_psd > 0 || ms[e].n_r2 + ms[e].n_p2 > 0) return OM_EINVAL;
+    double f = 0.0, fe, th[OPMAX], ge[OPMAX];
+    if (grad) memset(grad, 0, (size_t)P * sizeof(double));
+    int st = OM_OK;
+    for (int e = 0; e < E; ++e) {
+        om_est_theta(K, e, theta, th);
+        const int s = om_nll(&ms[e], th, &fe, grad ? ge : NULL);
+        if (s && s != OM_EDOMAIN) return s;
+        if (s) st = s;
+        f += fe;
+        if (grad) {
+            const int src = e == 0 ? K : K + 7 + 4 * (e - 1);
+            for (int k = 0; k < K; ++k) grad[k] += ge[k];
+            for (int j = 0; j < 4; ++j) grad[src + j] += ge[K + j];
+            for (int j = 4; j < 7; ++j) grad[K + j] += ge[K + j];
+        }
+    }
+    *nll = f;
+    return st;
+}
+
+static int obj_est(const void* ctx, const double* theta, double* f, double* g) {
+    const est_ctx* c = (const est_ctx*)ctx;
+    return om_nll_est(c->m, c->E, theta, f, g);
+}
+
+int om_fit_est(const om_model* ms, int E, const double* theta0, const unsigned char* free_mask,
+               const double* lo, const double* hi, double tol_edm, int max_iter,
+               double* theta_out, double* info, double* cov) {
+    if (E < 1 || ms[0].K + 7 + 4 * (E - 1) > OPMAX) return OM_EINVAL;
+    est_ctx c = {ms, E};
+    return fit_core(obj_est, &c, ms[0].K + 7 + 4 * (E - 1), theta0, free_mask, lo, hi, tol_edm, max_iter,
+                    theta_out, info, cov);
+}
+
+static int fit_core(om_objective om_obj, const void* ctx, int P, const double* theta0, const unsigned char* free_mask,
+                    const double* lo, const double* hi, double tol_edm, int max_iter,
+                    double* theta_out, double* info, double* cov) {
+    int st = OM_ENOTCONV, it;
     double th[OPMAX], g[OPMAX], gp[OPMAX], gm[OPMAX], tp[OPMAX], H[OPMAX * OPMAX], Hc[OPMAX * OPMAX];
     double step[OPMAX], rhs[OPMAX], f = 0, edm = INFINITY;
     int idx[OPMAX], nf = 0;
     memcpy(th, theta0, P * sizeof(double));
     for (int j = 0; j < P; ++j) th[j] = fmin(fmax(th[j], lo[j]), hi[j]);
     for (it = 0; it < max_iter; ++it) {
-        int e = om_nll(m, th, &f, g);
+        int e = om_obj(ctx, th, &f, g);
         if (e) { st = e; break; }
         nf = 0;
         for (int j = 0; j < P; ++j) {
@@ -667,10 +747,10 @@ int om_fit(const om_model* m, const double* theta0, const unsigned char* free_ma
             if (up == dn) return OM_EINVAL;
             memcpy(tp, th, P * sizeof(double)); tp[j] = up;
             double fd;
-            if ((e = om_nll(m, tp, &fd, gp))) return e;
+            if ((e = om_obj(ctx, tp, &fd, gp))) return e;
             memcpy(tp, th, P * sizeof(double)); tp[j] = dn;
             if (dn == th[j]) memcpy(gm, g, P * sizeof(double));
-            else if ((e = om_nll(m, tp, &fd, gm))) return e;
+            else if ((e = om_obj(ctx, tp, &fd, gm))) return e;
             for (int b = 0; b < nf; ++b) H[b * nf + a] = (gp[idx[b]] - gm[idx[b]]) / (up - dn);
         }
         for (int a = 0; a < nf; ++a)
@@ -704,7 +784,7 @@ int om_fit(const om_model* m, const double* theta0, const unsigned char* free_ma
         for (int ls = 0; ls < 50; ++ls) {
             memcpy(tp, th, P * sizeof(double));
             for (int a = 0; a < nf; ++a) { int j = idx[a]; tp[j] = fmin(fmax(th[j] + alpha * step[a], lo[j]), hi[j]); }
-            e = om_nll(m, tp, &fn, NULL);
+            e = om_obj(ctx, tp, &fn, NULL);
             if (!e && fn <= f + 1e-4 * alpha * slope) { ok = 1; break; }
             alpha *= 0.5;
         }

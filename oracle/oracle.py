@@ -12,6 +12,9 @@ Functions follow the paper's steps (arXiv:1805.11125 Sec. 3):
 ``poisson_nll`` (the binned Poisson sum alone), ``radial`` (Eq. 4 radial term) and
 ``fit`` (the minimisation of Sec. 4).  Models with 2D energy x radius / energy x pulse-shape
 histograms (the discrimination regime) are evaluated through the same entry points.
+``est_theta``, ``nll_estimators``, ``expected_estimators`` and ``fit_estimators`` evaluate and
+fit several energy estimators of one dataset jointly (Sec. 3: charge, detected photons, fired
+channels; shared rates, kB, eps and s_r, per-estimator LY, a, b, c).
 """
 from __future__ import annotations
 
@@ -80,6 +83,9 @@ def lib():
             _lib.om_poisson_nll.argtypes = [C.c_int, P, P, P]
             _lib.om_fit.argtypes = [P, P, P, P, P, C.c_double, C.c_int, P, P, P]
             _lib.om_n_bins.argtypes = [P]
+            _lib.om_est_theta.argtypes = [C.c_int, C.c_int, P, P]
+            _lib.om_nll_est.argtypes = [P, C.c_int, P, P, P]
+            _lib.om_fit_est.argtypes = [P, C.c_int, P, P, P, P, C.c_double, C.c_int, P, P, P]
         return _lib
 
 
@@ -223,4 +229,75 @@ def fit(spec, theta0, free=None, lo=None, hi=None, tol_edm=1e-12, max_iter=60):
     cov = np.zeros((P, P))
     lib().om_fit(m.ref, _ptr(th0), _ptr(fr), _ptr(l), _ptr(h), float(tol_edm), int(max_iter),
                  _ptr(out), _ptr(info), _ptr(cov))
+    return dict(theta=out, nll=info[0], edm=info[1], iters=int(info[2]), status=int(info[3]), cov=cov)
+
+
+# ---- several energy estimators of one dataset (Sec. 3), fitted jointly
+
+class _Estimators:
+    """The estimators' C models as one contiguous array (estimator 0 first)."""
+
+    def __init__(self, specs):
+        self.models = [OracleModel(s) for s in specs]
+        self.arr = (_Model * len(specs))(*[m.c for m in self.models])
+        self.E = len(specs)
+        self.K = specs[0].K
+        self.P = self.K + 7 + 4 * (self.E - 1)
+
+
+def est_theta(K: int, e: int, theta) -> np.ndarray:
+    """The parameter vector of estimator e ([r, LY_e, a_e, b_e, c_e, kB, eps, s_r]) taken from
+    the joint vector [r, LY_0, a_0, b_0, c_0, kB, eps, s_r, LY_1, a_1, b_1, c_1, ...]."""
+    th = _arr(theta)
+    out = np.zeros(K + 7)
+    lib().om_est_theta(int(K), int(e), _ptr(th), _ptr(out))
+    return out
+
+
+def nll_estimators(specs, theta, grad: bool = False):
+    """Joint -lnL of the estimators (the sum of each estimator's -lnL at its own parameter
+    vector) and, with ``grad``, its gradient in the joint layout."""
+    m = specs if isinstance(specs, _Estimators) else _Estimators(specs)
+    th = _arr(theta)
+    f = np.zeros(1)
+    g = np.zeros(m.P) if grad else None
+    st = lib().om_nll_est(m.arr, m.E, _ptr(th), _ptr(f), _ptr(g))
+    if st not in (0, OM_EDOMAIN):
+        raise RuntimeError(f"om_nll_est status {st}")
+    return (f[0], g) if grad else f[0]
+
+
+def expected_estimators(specs, theta) -> np.ndarray:
+    """Expected counts of every estimator's bins, estimator after estimator."""
+    K = specs[0].K
+    return np.concatenate([expected(s, est_theta(K, e, theta)) for e, s in enumerate(specs)])
+
+
+def estimator_defaults(specs):
+    """Free mask and bounds of the joint layout: those of estimator 0's single model, then
+    LY, a, b, c of every further estimator with the bounds of LY, a, b, c."""
+    free = specs[0].default_free()
+    lo, hi = specs[0].default_bounds()
+    K = specs[0].K
+    for _ in specs[1:]:
+        free = np.concatenate([free, np.ones(4, dtype=np.uint8)])
+        lo = np.concatenate([lo, lo[K:K + 4]])
+        hi = np.concatenate([hi, hi[K:K + 4]])
+    return free, lo, hi
+
+
+def fit_estimators(specs, theta0, free=None, lo=None, hi=None, tol_edm=1e-12, max_iter=60):
+    """The joint fit of the estimators by the same damped Newton method as :func:`fit`.
+    Parity unpinned beyond its invariants (an Asimov fit returns theta_true)."""
+    m = _Estimators(specs)
+    dfree, dlo, dhi = estimator_defaults(specs)
+    free = dfree if free is None else free
+    lo = dlo if lo is None else lo
+    hi = dhi if hi is None else hi
+    th0, fr, l, h = _arr(theta0), _arr(free, np.uint8), _arr(lo), _arr(hi)
+    out = np.zeros(m.P)
+    info = np.zeros(4)
+    cov = np.zeros((m.P, m.P))
+    lib().om_fit_est(m.arr, m.E, _ptr(th0), _ptr(fr), _ptr(l), _ptr(h), float(tol_edm), int(max_iter),
+                     _ptr(out), _ptr(info), _ptr(cov))
     return dict(theta=out, nll=info[0], edm=info[1], iters=int(info[2]), status=int(info[3]), cov=cov)

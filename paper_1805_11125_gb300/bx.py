@@ -72,6 +72,7 @@ _lock = threading.Lock()
 # (name, restype, argtypes) of every entry point declared in include/bx.h
 SIGNATURES = [
     ("bx_model_create", C.c_int, [_P, C.c_int, _P, _P, _P]),
+    ("bx_model_create_estimators", C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P]),
     ("bx_model_destroy", None, [_P]),
     ("bx_model_set_stream", C.c_int, [_P, _P]),
     ("bx_model_n_params", C.c_int, [_P]),
@@ -86,6 +87,7 @@ SIGNATURES = [
     ("bx_selftest_tensor_core", C.c_int, [_P]),
     ("bx_selftest_watchdog", C.c_int, [C.c_double]),
     ("bx_spectra_noalloc", C.c_int, [C.c_int, C.c_double, C.c_int, _P, _P, _P, C.c_double, C.c_int, _P, _P, _P]),
+    ("bx_ceiling", C.c_int, [C.c_int, C.c_int, _P, _P, _P]),
     ("bx_last_error", C.c_char_p, []),
     ("bx_status_string", C.c_char_p, [C.c_int]),
 ]
@@ -143,7 +145,9 @@ class Model:
     """A bx_model built from one or more :class:`ModelSpec` (toys)."""
 
     def __init__(self, specs, precision: int = BX_FP32, max_batch: int = 1, band_sigmas: float = 0.0,
-                 watchdog_s: float = 0.0, stream=None):
+                 watchdog_s: float = 0.0, stream=None, n_est: int = 1):
+        """n_est > 1: ``specs`` are n_data x n_est energy estimators, dataset-major
+        (bx_model_create_estimators); toys are then datasets and theta the joint vector."""
         specs = list(specs) if isinstance(specs, (list, tuple)) else [specs]
         self.specs = specs
         self._keep = []
@@ -177,8 +181,13 @@ class Model:
             d.joint2d = 1 if getattr(s, "joint2d", False) else 0
         opts = bx_options(precision, max_batch, band_sigmas, watchdog_s)
         h = C.c_void_p()
-        _check(lib().bx_model_create(C.cast(descs, _P), len(specs), C.byref(opts), _stream_handle(stream),
-                                     C.byref(h)))
+        if n_est == 1:
+            _check(lib().bx_model_create(C.cast(descs, _P), len(specs), C.byref(opts), _stream_handle(stream),
+                                         C.byref(h)))
+        else:
+            _check(lib().bx_model_create_estimators(C.cast(descs, _P), len(specs) // n_est, n_est, C.byref(opts),
+                                                    _stream_handle(stream), C.byref(h)))
+        self.n_est = n_est
         self.h = h
         self.precision = precision
         self.max_batch = max_batch
@@ -409,6 +418,16 @@ class BxNLL:
 
             cls._fn = _F
         return cls._fn.apply(theta, model)
+
+
+BX_CEIL_RESP, BX_CEIL_RESP_ACC, BX_CEIL_FMA64, BX_CEIL_FMA32 = 0, 1, 2, 3
+
+
+def bx_ceiling(which: int, reps: int, stream=None):
+    """(ms, units) of one ceiling microkernel launch (see include/bx.h)."""
+    ms, units = np.zeros(1), np.zeros(1)
+    _check(lib().bx_ceiling(int(which), int(reps), _stream_handle(stream), _ptr(ms), _ptr(units)))
+    return float(ms[0]), float(units[0])
 
 
 def bx_selftest_watchdog(budget_s: float = 0.05) -> int:

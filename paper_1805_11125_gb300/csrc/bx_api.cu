@@ -198,8 +198,10 @@ static void free_model(bx_model* m) {
     delete m;
 }
 
-extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_options* opts, void* cuda_stream,
-                               bx_model** out) {
+// n_est > 1: the toys are n_toys / n_est datasets of n_est energy estimators each (validated by
+// bx_model_create_estimators); the workspace holds max_batch x n_est internal items.
+static int model_create(const bx_model_desc* descs, int n_toys, const bx_options* opts, void* cuda_stream, int n_est,
+                        bx_model** out) {
     if (!out) return bx_set_error(BX_EINVAL, "out is NULL");
     *out = nullptr;
     if (!descs || n_toys < 1) return bx_set_error(BX_EINVAL, "need at least one model description");
@@ -254,6 +256,8 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
     m->n_toys = n_toys;
     m->precision = o.precision;
     m->cap = o.max_batch;
+    m->n_est = n_est;
+    m->n_data = n_toys / n_est;
     m->band = o.band_sigmas;
     m->watchdog_ns = (unsigned long long)(o.watchdog_s * 1e9);
     m->toys_h.resize(n_toys);
@@ -333,15 +337,18 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
         if ((st = upload(m, T.n_psd ? d.psd_prob : nullptr, (size_t)T.K * T.n_psd, &T.psd))) break;
         if (T.n_sl) {
             // template modulation per (column, slice) and its per-species column sums
-            std::vector<float> ut((size_t)T.N * NSL, 0.f);
+            std::vector<float> ut((size_t)T.N * NSL, 0.f), utl((size_t)T.N * NSL, 0.f);
             std::vector<double> U2((size_t)T.K * NSL, 0.0);
             for (int i = 0; i < T.N; ++i)
                 for (int b = 0; b < T.n_sl; ++b) {
                     const double u = b < T.b_r2 ? 1.0 : 1.0 + d.field_amp * d.field2d[(size_t)i * B2 + (b - T.b_r2)];
-                    ut[(size_t)i * NSL + b] = (float)u;
+                    const float uh = (float)u;
+                    ut[(size_t)i * NSL + b] = uh;
+                    utl[(size_t)i * NSL + b] = (float)(u - (double)uh);
                     for (int k = 0; k < T.K; ++k) U2[(size_t)k * NSL + b] += d.shapes[(size_t)k * T.N + i] * u;
                 }
             if ((st = upload(m, ut.data(), ut.size(), &T.ut))) break;
+            if ((st = upload(m, utl.data(), utl.size(), &T.utl))) break;
             if ((st = upload(m, U2.data(), U2.size(), &T.U2))) break;
             if ((st = upload(m, T.n_p2 ? d.psd2d_prob : nullptr, (size_t)T.K * T.n_p2, &T.psd2))) break;
             if (T.n_r2 && !T.rad_class && (st = upload(m, d.rad_class, (size_t)T.K, &T.rad_class))) break;
@@ -349,16 +356,18 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
             CU(cudaStreamSynchronize(m->stream));
         }
         void *s32, *stiles, *g32, *gg;
-        if ((st = alloc_dev(m, &s32, (size_t)T.K * T.N * sizeof(float)))) break;
+        if ((st = alloc_dev(m, &s32, 2 * (size_t)T.K * T.N * sizeof(float)))) break;   // hi, then lo
         if ((st = alloc_dev(m, &stiles, (size_t)T.n_kb * 3 * US * KB * sizeof(float)))) break;
         if ((st = alloc_dev(m, &g32, (size_t)T.L * sizeof(float)))) break;
         if ((st = alloc_dev(m, &gg, (size_t)T.n_es * T.M * (sizeof(double) + sizeof(float))))) break;
         T.shapes32 = static_cast<float*>(s32);
+        T.shapes32l = static_cast<float*>(s32) + (size_t)T.K * T.N;
         T.S_tiles = static_cast<float*>(stiles);
         T.g32 = static_cast<float*>(g32);
         T.Gg = static_cast<double*>(gg);
         T.Gg32 = reinterpret_cast<float*>(static_cast<double*>(gg) + (size_t)T.n_es * T.M);
-        cudaError_t e = launch_setup_toy(T, static_cast<float*>(s32), static_cast<float*>(stiles),
+        cudaError_t e = launch_setup_toy(T, static_cast<float*>(s32), const_cast<float*>(T.shapes32l),
+                                         static_cast<float*>(stiles),
                                          static_cast<float*>(g32), static_cast<double*>(gg), m->stream);
         if (e != cudaSuccess) st = bx_set_error(BX_ECUDA, "set-up kernel: %s", cudaGetErrorString(e));
         m->Kmax = std::max(m->Kmax, T.K);
@@ -378,15 +387,16 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
         free_model(m);
         return st;
     }
-    m->P = m->Kmax + 7;
-    const int cap = m->cap;
+    m->Pi = m->Kmax + 7;
+    m->P = m->Pi + 4 * (m->n_est - 1);
+    const int cap = m->cap * m->n_est;   // internal items
     Work& w = m->w;
     w = Work{};
     w.cap = cap;
     w.Npad = ((m->Nmax + 127) / 128) * 128;
     w.Mpad = ((m->Mmax + 127) / 128) * 128;
     w.nbmax = m->nbmax;
-    w.pstride = m->P;
+    w.pstride = m->Pi;
     w.precision = m->precision;
     w.lam_pairs = m->precision == BX_FP32;
     w.multi_set = 0;
@@ -433,14 +443,15 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
         {(void**)&w.colf, sizeof(float4) * cap * w.Npad},
         {(void**)&w.colg, sizeof(ColG) * cap * w.Npad},
         {(void**)&w.colS, sizeof(double2) * cap * w.Npad},
-        {(void**)&w.colS32, sizeof(float2) * cap * w.Npad},
+        {(void**)&w.colS32, sizeof(float4) * cap * w.Npad},
+        {(void**)&w.colAl, sizeof(float) * cap * w.Npad},
         {(void**)&w.aW, sizeof(double) * cap * w.nes * w.Npad},
         {(void**)&w.colr, sizeof(int2) * cap * w.Npad},
         {(void**)&w.lam, sizeof(double) * cap * 2 * w.Mpad},
         {(void**)&w.apart, m->any_cols && !species ? 2 * sizeof(float) * cap * m->max_tiles * w.nes * w.Npad : 16},
         {(void**)&w.tile_cols, sizeof(int2) * cap * MAX_SETS * MAX_TILES},
         {(void**)&w.cb_rows, sizeof(int2) * cap * MAX_CB},
-        {(void**)&w.v, species ? tv * cap * w.Mpad * US : 16},
+        {(void**)&w.v, species ? 2 * tv * cap * w.Mpad * US : 16},   // hi, lo planes
         {(void**)&w.rowW, tv * cap * (2 + w.nes) * w.Mpad},
         {(void**)&w.coef, sizeof(double) * cap * (2 + w.nes) * KMAX},
         {(void**)&w.gmid, sizeof(double) * cap * PMAX},
@@ -450,17 +461,22 @@ extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_
         {(void**)&w.status, sizeof(int) * cap},
         {(void**)&w.err, sizeof(unsigned)},
         {(void**)&w.units, sizeof(unsigned long long)},
-        {(void**)&w.coef2d, m->is2d ? sizeof(float) * cap * 3 * KMAX * NSL : 16},
+        {(void**)&w.coef2d, m->is2d ? sizeof(float) * cap * 4 * KMAX * NSL : 16},
         {(void**)&w.tr2d, m->is2d ? sizeof(float) * cap * (w.Npad / KB) * 3 * NSL * KB : 16},
-        {(void**)&w.y2d, m->is2d ? sizeof(float) * cap * (w.Mpad / KB) * 2 * NSL * KB : 16},
+        {(void**)&w.trmax2d, m->is2d ? sizeof(unsigned) * cap * NSL : 16},
+        {(void**)&w.y2d, m->is2d ? sizeof(float) * cap * (w.Mpad / KB) * 3 * NSL * KB : 16},
         {(void**)&w.w2d, m->is2d ? sizeof(float) * cap * ((m->nwmax + KB - 1) / KB) * 2 * NSL * KB : 16},
         {(void**)&w.wt2d, m->is2d ? sizeof(float) * cap * (w.Mpad / KB) * 2 * NSL * KB : 16},
         {(void**)&w.nll2d, m->is2d ? sizeof(double) * cap * MAX_TILES * 2 : 16},
         {(void**)&w.geps2d, m->is2d ? sizeof(double) * cap * MAX_TILES : 16},
         {(void**)&w.gpart2d, m->is2d ? sizeof(double) * cap * MAX_CB * (GPN + 1) : 16},
-        {(void**)&m->theta_d, sizeof(double) * cap * m->P},
-        {(void**)&m->nll_d, sizeof(double) * cap},
-        {(void**)&m->grad_d, sizeof(double) * cap * m->P},
+        {(void**)&m->theta_d, sizeof(double) * m->cap * m->P},
+        {(void**)&m->nll_d, sizeof(double) * m->cap},
+        {(void**)&m->grad_d, sizeof(double) * m->cap * m->P},
+        {(void**)&m->est_theta, m->n_est > 1 ? sizeof(double) * cap * m->Pi : 16},
+        {(void**)&m->est_nll, m->n_est > 1 ? sizeof(double) * cap : 16},
+        {(void**)&m->est_grad, m->n_est > 1 ? sizeof(double) * cap * m->Pi : 16},
+        {(void**)&m->est_skip, m->n_est > 1 ? (size_t)cap : 16},
     };
     for (auto& a : plan)
         if ((st = alloc_dev(m, a.p, a.bytes))) break;
@@ -496,9 +512,61 @@ extern "C" int bx_model_set_stream(bx_model* m, void* s) {
 
 extern "C" int bx_model_n_params(const bx_model* m) { return m ? m->P : 0; }
 
+extern "C" int bx_model_create(const bx_model_desc* descs, int n_toys, const bx_options* opts, void* cuda_stream,
+                               bx_model** out) {
+    return model_create(descs, n_toys, opts, cuda_stream, 1, out);
+}
+
+// The estimators of one dataset see the same events: the same species shapes on the same grid,
+// stopping power, tag fractions and quenching; only estimator 0 carries the radial and
+// pulse-shape terms, and none carries 2D histograms or energy slices.
+static int validate_estimators(const bx_model_desc* d, int n_data, int n_est) {
+    if (n_data < 1 || n_est < 1 || n_est > MAX_EST)
+        return bx_set_error(BX_EINVAL, "need n_data >= 1 and 1 <= n_est <= %d", MAX_EST);
+    for (int t = 0; t < n_data; ++t) {
+        const bx_model_desc& a = d[(size_t)t * n_est];
+        for (int e = 0; e < n_est; ++e) {
+            const bx_model_desc& b = d[(size_t)t * n_est + e];
+            if (b.n_rad2d + b.n_psd2d > 0 || b.n_eslice > 1)
+                return bx_set_error(BX_EINVAL, "dataset %d estimator %d: estimators take no 2D histograms or energy slices",
+                                    t, e);
+            if (e == 0) continue;
+            if (b.n_rad > 0 || b.n_psd > 0)
+                return bx_set_error(BX_EINVAL, "dataset %d estimator %d: the radial and pulse-shape terms belong to "
+                                               "estimator 0", t, e);
+            const size_t kn = (size_t)a.n_species * a.n_grid;
+            const bool same = b.n_grid == a.n_grid && b.e_max == a.e_max && b.n_species == a.n_species &&
+                              b.shapes && a.shapes && !memcmp(b.shapes, a.shapes, kn * sizeof(double)) && b.stop_pow &&
+                              a.stop_pow && !memcmp(b.stop_pow, a.stop_pow, (size_t)a.n_grid * sizeof(double)) &&
+                              (!a.tag_frac) == (!b.tag_frac) &&
+                              (!a.tag_frac || !memcmp(a.tag_frac, b.tag_frac, (size_t)a.n_species * sizeof(double))) &&
+                              (!a.quench) == (!b.quench) &&
+                              (!a.quench || !memcmp(a.quench, b.quench, (size_t)a.n_species * sizeof(double)));
+            if (!same)
+                return bx_set_error(BX_EINVAL, "dataset %d estimator %d: grid, species shapes, stopping power, tag "
+                                               "fractions and quenching must equal estimator 0's", t, e);
+        }
+    }
+    return BX_OK;
+}
+
+extern "C" int bx_model_create_estimators(const bx_model_desc* descs, int n_data, int n_est, const bx_options* opts,
+                                          void* cuda_stream, bx_model** out) {
+    if (!out) return bx_set_error(BX_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!descs) return bx_set_error(BX_EINVAL, "need at least one model description");
+    int st = validate_estimators(descs, n_data, n_est);
+    if (st) return st;
+    return model_create(descs, n_data * n_est, opts, cuda_stream, n_est, out);
+}
+
+int bx_public_P(const bx_model* m, int t) { return m->toys_h[(size_t)t * m->n_est].P + 4 * (m->n_est - 1); }
+
 extern "C" int bx_model_n_bins(const bx_model* m, int toy) {
-    if (!m || toy < 0 || toy >= m->n_toys) return 0;
-    return m->toys_h[toy].nb;
+    if (!m || toy < 0 || toy >= m->n_data) return 0;
+    int nb = 0;
+    for (int e = 0; e < m->n_est; ++e) nb += m->toys_h[(size_t)toy * m->n_est + e].nb;
+    return nb;
 }
 
 // Read and clear the sticky device error word (synchronises the stream).
@@ -520,20 +588,27 @@ extern "C" int bx_model_status(bx_model* m) {
 
 // ------------------------------------------------------------------ evaluation
 
+// Public items j = 0..n-1 of datasets toy_idx[j]; with E estimators internal item j E + e is
+// estimator e of dataset toy_idx[j] (toy toy_idx[j] E + e).  m->toy_tmp holds the public list.
 int bx_set_items(bx_model* m, int n, const int* toy_idx) {
     if (n < 1 || n > m->cap) return bx_set_error(BX_EINVAL, "n = %d out of [1, max_batch = %d]", n, m->cap);
     std::vector<int>& tmp = m->toy_tmp;
     tmp.assign(n, 0);
     if (toy_idx)
         for (int j = 0; j < n; ++j) {
-            if (toy_idx[j] < 0 || toy_idx[j] >= m->n_toys)
-                return bx_set_error(BX_EINVAL, "toy_idx[%d] = %d out of [0, %d)", j, toy_idx[j], m->n_toys);
+            if (toy_idx[j] < 0 || toy_idx[j] >= m->n_data)
+                return bx_set_error(BX_EINVAL, "toy_idx[%d] = %d out of [0, %d)", j, toy_idx[j], m->n_data);
             tmp[j] = toy_idx[j];
         }
-    if (!std::equal(tmp.begin(), tmp.end(), m->toy_cached.begin())) {
-        // pageable source: the copy has consumed tmp when the call returns
-        CU(cudaMemcpyAsync((void*)m->w.toy_of, tmp.data(), sizeof(int) * n, cudaMemcpyHostToDevice, m->stream));
-        std::copy(tmp.begin(), tmp.end(), m->toy_cached.begin());
+    const int E = m->n_est;
+    std::vector<int> internal((size_t)n * E);
+    for (int j = 0; j < n; ++j)
+        for (int e = 0; e < E; ++e) internal[(size_t)j * E + e] = tmp[j] * E + e;
+    if (!std::equal(internal.begin(), internal.end(), m->toy_cached.begin())) {
+        // pageable source: the copy has consumed the list when the call returns
+        CU(cudaMemcpyAsync((void*)m->w.toy_of, internal.data(), sizeof(int) * internal.size(), cudaMemcpyHostToDevice,
+                           m->stream));
+        std::copy(internal.begin(), internal.end(), m->toy_cached.begin());
     }
     return BX_OK;
 }
@@ -552,37 +627,59 @@ static int prof_mark(bx_model* m, int stage) {
     return BX_OK;
 }
 
-int bx_enqueue_eval(bx_model* m, int n, const double* theta_dev, int tstride, int want_grad, int want_mu,
-                    double* nll_dev, double* grad_dev) {
+static int enqueue_items(bx_model* m, int n, const double* theta_dev, int tstride, int want_grad, int want_mu,
+                         double* nll_dev, double* grad_dev) {
     Work w = m->w;
     w.theta = theta_dev;
     w.tstride = tstride;
     w.n_items = n;
     cudaStream_t s = m->stream;
     int st;
+    BxRange eval_range("bx_eval");
     if ((st = prof_mark(m, 0))) return st;
-    CU(launch_prep(w, n, s));
+    { BxRange r("bx_prep"); CU(launch_prep(w, n, s)); }
     if ((st = prof_mark(m, 1))) return st;
     if (m->is2d) {
-        CU(launch_eval2d(w, n, want_grad, want_mu, 1, s));
+        { BxRange r("bx_forward_2d"); CU(launch_eval2d(w, n, want_grad, want_mu, 1, s)); }
         if ((st = prof_mark(m, 2))) return st;
-        CU(launch_eval2d(w, n, want_grad, want_mu, 2, s));
+        { BxRange r("bx_pileup_nll_2d"); CU(launch_eval2d(w, n, want_grad, want_mu, 2, s)); }
         if ((st = prof_mark(m, 3))) return st;
-        if (want_grad) CU(launch_eval2d(w, n, want_grad, want_mu, 3, s));
+        if (want_grad) { BxRange r("bx_adjoint_2d"); CU(launch_eval2d(w, n, want_grad, want_mu, 3, s)); }
         if ((st = prof_mark(m, 4))) return st;
-        CU(launch_gather2d(w, n, nll_dev, grad_dev, want_grad, s));
+        { BxRange r("bx_gather"); CU(launch_gather2d(w, n, nll_dev, grad_dev, want_grad, s)); }
         return prof_mark(m, 5);
     }
-    if (m->precision == BX_FP64) CU(launch_fwd_f64(w, n, m->max_tiles, m->any_tag, m->any_cols, s));
-    else if (m->precision == BX_FP32) CU(launch_fwd_f32(w, n, m->max_tiles, m->any_tag, m->any_cols, s));
-    else CU(launch_fwd_tc(w, n, m->max_tiles, s));
+    {
+        BxRange r("bx_forward");
+        if (m->precision == BX_FP64) CU(launch_fwd_f64(w, n, m->max_tiles, m->any_tag, m->any_cols, s));
+        else if (m->precision == BX_FP32) CU(launch_fwd_f32(w, n, m->max_tiles, m->any_tag, m->any_cols, s));
+        else CU(launch_fwd_tc(w, n, m->max_tiles, s));
+    }
     if ((st = prof_mark(m, 2))) return st;
-    CU(launch_mid(w, n, m->Mmax, m->nwmax, m->Lmax, want_grad, want_mu, s));
+    { BxRange r("bx_assembly"); CU(launch_mid(w, n, m->Mmax, m->nwmax, m->Lmax, want_grad, want_mu, s)); }
     if ((st = prof_mark(m, 3))) return st;
-    if (want_grad) CU(launch_bwd(w, n, m->max_cb, s));
+    if (want_grad) { BxRange r("bx_adjoint"); CU(launch_bwd(w, n, m->max_cb, s)); }
     if ((st = prof_mark(m, 4))) return st;
-    CU(launch_gather(w, n, nll_dev, grad_dev, want_grad, s));
+    { BxRange r("bx_gather"); CU(launch_gather(w, n, nll_dev, grad_dev, want_grad, s)); }
     if ((st = prof_mark(m, 5))) return st;
+    return BX_OK;
+}
+
+// n public items: with several estimators, expanded to n E internal items (k_est_split), evaluated
+// by the regular kernels, and joined (k_est_join: -lnL summed, gradients mapped back).
+int bx_enqueue_eval(bx_model* m, int n, const double* theta_dev, int tstride, int want_grad, int want_mu,
+                    double* nll_dev, double* grad_dev) {
+    if (m->n_est == 1) return enqueue_items(m, n, theta_dev, tstride, want_grad, want_mu, nll_dev, grad_dev);
+    const int E = m->n_est;
+    const unsigned char* pub_skip = m->w.skip;
+    CU(launch_est_split(theta_dev, tstride, n, E, m->w.toys, m->w.toy_of, pub_skip, m->est_theta, m->Pi,
+                        pub_skip ? m->est_skip : nullptr, m->stream));
+    m->w.skip = pub_skip ? m->est_skip : nullptr;
+    const int st = enqueue_items(m, n * E, m->est_theta, m->Pi, want_grad, want_mu, m->est_nll, m->est_grad);
+    m->w.skip = pub_skip;
+    if (st) return st;
+    CU(launch_est_join(m->est_nll, m->est_grad, m->Pi, n, E, m->w.toys, m->w.toy_of, nll_dev, grad_dev, m->P,
+                       want_grad, m->stream));
     return BX_OK;
 }
 
@@ -616,7 +713,7 @@ static int eval_host(bx_model* m, int n, const int* toy_idx, const double* theta
     const int P = m->P;
     for (int j = 0; j < n; ++j) {
         const int t = m->toy_tmp[j];
-        for (int q = 0; q < m->toys_h[t].P; ++q)
+        for (int q = 0; q < bx_public_P(m, t); ++q)
             if (!std::isfinite(theta[(size_t)j * P + q]))
                 return bx_set_error(BX_EINVAL, "theta[%d][%d] is not finite", j, q);
     }
@@ -646,11 +743,17 @@ extern "C" int bx_nll_grad(bx_model* m, const double* theta, double* nll, double
 
 extern "C" int bx_expected(bx_model* m, int toy, const double* theta, double* mu) {
     if (!m || !theta || !mu) return bx_set_error(BX_EINVAL, "NULL argument");
-    if (toy < 0 || toy >= m->n_toys) return bx_set_error(BX_EINVAL, "toy %d out of range", toy);
+    if (toy < 0 || toy >= m->n_data) return bx_set_error(BX_EINVAL, "toy %d out of range", toy);
     double nll;
     int st = eval_host(m, 1, &toy, theta, 0, 1, &nll, nullptr);
     if (st && st != BX_EDOMAIN) return st;
-    CU(cudaMemcpyAsync(mu, m->w.mu, sizeof(double) * m->toys_h[toy].nb, cudaMemcpyDeviceToHost, m->stream));
+    size_t off = 0;
+    for (int e = 0; e < m->n_est; ++e) {   // internal item e: estimator e, its bins after the previous ones
+        const int nb = m->toys_h[(size_t)toy * m->n_est + e].nb;
+        CU(cudaMemcpyAsync(mu + off, m->w.mu + (size_t)e * m->nbmax, sizeof(double) * nb, cudaMemcpyDeviceToHost,
+                           m->stream));
+        off += nb;
+    }
     CU(cudaStreamSynchronize(m->stream));
     return BX_OK;
 }

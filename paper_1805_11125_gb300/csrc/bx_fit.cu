@@ -40,6 +40,8 @@ using namespace bx;
 namespace {
 
 constexpr int NLS = 8;   // line-search trial steps per iteration: 1, 1/2, ..., 1/128
+// parameters of a fit: K + 7, plus 4 per further energy estimator
+constexpr int PFMAX = KMAX + 7 + 4 * (MAX_EST - 1);
 
 enum { PH_START = 0, PH_HESS = 1, PH_LS = 2, PH_DONE = 3 };
 
@@ -69,6 +71,14 @@ constexpr double EDM_FLOOR_FP32 = 1e-5;
 // rate stepped to zero could empty a bin).
 constexpr double HSIG_FP32 = 1.0;
 
+// Trust region of the response, pile-up and radial parameters.  Far from the optimum the Newton
+// step of these nearly degenerate parameters can be many times their value (the light yield,
+// the resolution terms and kB trade off against each other), and a line search along it may
+// accept a point from which the fit runs onto the bounds: a 5%-off start of the small joint
+// model walked the resolution term b to 25 times its value with four parameters held at bounds.
+// Near the optimum every step is well inside the region (a few standard deviations at most).
+constexpr double TR_REL = 0.5, TR_SIG = 2.0;
+
 struct FitCtl {
     int phase, iters, evals, status, max_evals, fails, n_bound;
     double edm, edm0, tol, mu_min, mu_used, hrel, mu_conv, hsig, mu_fresh;
@@ -76,8 +86,8 @@ struct FitCtl {
 
 struct FitDev {
     int n, P, S;
-    const Toy* toys;
-    const int* toy_of;      // per slot
+    const int* Pf;          // per fit: parameters of its dataset's row (K_t + 7 + 4 (E - 1))
+    const int* Kf;          // per fit: rates (K_t), the parameters before the trust-region ones
     double *theta, *g, *f;  // accepted state per fit
     double *H, *V, *d;      // per fit
     double *lo, *hi;        // per fit
@@ -96,8 +106,8 @@ struct FitDev {
 // Returns the mu used, or -1 when even mu = 1e8 fails.
 __device__ double damped_inverse(const double* H, const unsigned char* act, int n, int P, double mu_min, double* V,
                                  double* L) {
-    int idx[PMAX], nf = 0;
-    double D[PMAX];
+    int idx[PFMAX], nf = 0;
+    double D[PFMAX];
     for (int i = 0; i < n; ++i)
         if (act[i]) {
             const double h = fabs(H[IDX(i, i)]);
@@ -123,7 +133,7 @@ __device__ double damped_inverse(const double* H, const unsigned char* act, int 
                 }
             }
         if (!ok) continue;
-        double col[PMAX];
+        double col[PFMAX];
         for (int c = 0; c < nf; ++c) {
             for (int i = 0; i < nf; ++i) {
                 double t = (i == c) ? 1.0 : 0.0;
@@ -149,8 +159,7 @@ __global__ void k_fit(FitDev F) {
     FitCtl c = F.ctl[jf];
     if (c.phase == PH_DONE) return;
     const size_t s0 = (size_t)jf * S;   // first slot of this fit
-    const Toy& T = F.toys[F.toy_of[s0]];
-    const int Pt = T.P;
+    const int Pt = F.Pf[jf], Kt = F.Kf[jf];
     double* th = F.theta + (size_t)jf * P;
     double* g = F.g + (size_t)jf * P;
     double* V = F.V + (size_t)jf * P * P;
@@ -205,10 +214,10 @@ __global__ void k_fit(FitDev F) {
         }
     }
     if (newdir) {
-        unsigned char act[PMAX];
+        unsigned char act[PFMAX];
         for (int i = 0; i < Pt; ++i)
             act[i] = fr[i] && !((th[i] <= lo[i] && g[i] > 0.0) || (th[i] >= hi[i] && g[i] < 0.0));
-        double L[PMAX * PMAX];
+        double L[PFMAX * PFMAX];
         const double mu = damped_inverse(H, act, Pt, P, fresh ? 0.0 : c.mu_min, V, L);
         double gd = 0.0;
         if (mu >= 0.0) {
@@ -238,8 +247,18 @@ __global__ void k_fit(FitDev F) {
                 c.status = BX_OK;
             } else {
                 c.phase = PH_LS;
+                // trust region of the response, pile-up and radial parameters (everything after the
+                // rates): a trial step moves none of them by more than TR_REL of its magnitude or
+                // TR_SIG of its standard deviation under the current Hessian, whichever is larger
+                double amax = 1.0;
+                for (int i = Kt; i < Pt; ++i)
+                    if (act[i] && d[i] != 0.0) {
+                        const double v = V[IDX(i, i)];
+                        const double lim = fmax(TR_REL * fabs(th[i]), v > 0.0 && isfinite(v) ? TR_SIG * sqrt(v) : 0.0);
+                        if (lim > 0.0) amax = fmin(amax, lim / fabs(d[i]));
+                    }
                 for (int k = 0; k < NLS; ++k) {
-                    const double a = ldexp(1.0, -k);
+                    const double a = amax * ldexp(1.0, -k);
                     double* tk = slot_t(k);
                     for (int i = 0; i < Pt; ++i) tk[i] = fr[i] ? fmin(fmax(th[i] + a * d[i], lo[i]), hi[i]) : th[i];
                     F.skip[s0 + k] = 0;
@@ -322,6 +341,7 @@ static int fit_alloc(bx_model* m) {
         {(void**)&D.lo, n * P * 8},    {(void**)&D.hi, n * P * 8},     {(void**)&D.fr, n * P},
         {(void**)&D.tt, ns * P * 8},   {(void**)&D.ft, ns * 8},        {(void**)&D.gt, ns * P * 8},
         {(void**)&D.skip, ns},         {(void**)&D.ctl, n * sizeof(FitCtl)}, {(void**)&D.active, 16},
+        {(void**)&D.Pf, n * sizeof(int)},     {(void**)&D.Kf, n * sizeof(int)},
     };
     for (auto& a : plan) {
         CUF(cudaMalloc(a.p, a.bytes));
@@ -331,8 +351,6 @@ static int fit_alloc(bx_model* m) {
     CUF(cudaStreamCreateWithFlags(&s->fs, cudaStreamNonBlocking));
     D.P = s->P;
     D.S = s->S;
-    D.toys = m->w.toys;
-    D.toy_of = m->w.toy_of;
     return BX_OK;
 }
 
@@ -384,6 +402,7 @@ static int fit_capture(bx_model* m, int n, int ipl) {
 extern "C" int bx_fit(bx_model* m, int n, const int* toy_idx, const double* theta0, const bx_fit_opts* opts,
                       double* theta_out, bx_fit_result* res) {
     if (!m || !theta0 || !theta_out || !res) return bx_set_error(BX_EINVAL, "bx_fit: NULL argument");
+    BxRange range("bx_fit");
     bx_fit_opts o{};
     if (opts) o = *opts;
     if (o.tol_edm == 0.0) o.tol_edm = 1e-8;
@@ -396,7 +415,7 @@ extern "C" int bx_fit(bx_model* m, int n, const int* toy_idx, const double* thet
         return bx_set_error(BX_EINVAL, "bx_fit: %d fits need max_batch >= %lld (%d evaluation slots per fit)", n,
                             (long long)n * S, S);
     for (int j = 0; j < n; ++j)
-        if (toy_idx && (toy_idx[j] < 0 || toy_idx[j] >= m->n_toys))
+        if (toy_idx && (toy_idx[j] < 0 || toy_idx[j] >= m->n_data))
             return bx_set_error(BX_EINVAL, "bx_fit: toy_idx[%d] out of range", j);
     std::vector<int> slot_toy((size_t)n * S);
     for (int j = 0; j < n; ++j)
@@ -409,20 +428,28 @@ extern "C" int bx_fit(bx_model* m, int n, const int* toy_idx, const double* thet
     std::vector<double> lo((size_t)n * P, -INFINITY), hi((size_t)n * P, INFINITY), th((size_t)n * S * P, 0.0);
     std::vector<unsigned char> fr((size_t)n * P, 0), skip((size_t)n * S, 1);
     std::vector<FitCtl> ctl(n);
+    std::vector<int> Pf(n), Kf(n);
     const double hrel = m->precision == BX_FP64 ? 1e-3 : 1e-2;   // FD step of the Hessian
     for (int j = 0; j < n; ++j) {
-        const Toy& T = m->toys_h[toy_idx ? toy_idx[j] : 0];
-        for (int p = 0; p < T.P; ++p) {
+        const int t = toy_idx ? toy_idx[j] : 0;
+        const Toy& T = m->toys_h[(size_t)t * m->n_est];   // estimator 0 of the dataset
+        Pf[j] = bx_public_P(m, t);
+        Kf[j] = T.K;
+        for (int p = 0; p < Pf[j]; ++p) {
             const int q = p < T.K ? p : Kmax + (p - T.K);   // slot in the Kmax layout of the options
             double l, h;
             unsigned char f;
+            static const double dl[7] = {50.0, 0.0, 0.0, 1e-3, 0.0, 0.0, 0.05};
+            static const double dh[7] = {INFINITY, INFINITY, INFINITY, INFINITY, INFINITY, 1.0, INFINITY};
             if (p < T.K) { l = 0.0; h = INFINITY; f = 1; }
-            else {
-                static const double dl[7] = {50.0, 0.0, 0.0, 1e-3, 0.0, 0.0, 0.05};
-                static const double dh[7] = {INFINITY, INFINITY, INFINITY, INFINITY, INFINITY, 1.0, INFINITY};
+            else if (p < T.K + 7) {
                 l = dl[p - T.K];
                 h = dh[p - T.K];
                 f = (p - T.K == 6) ? (T.n_rad > 0 || T.n_r2 > 0) : 1;
+            } else {   // LY, a, b, c of a further energy estimator
+                l = dl[(p - T.K - 7) % 4];
+                h = dh[(p - T.K - 7) % 4];
+                f = 1;
             }
             if (o.lo) l = o.lo[q];
             if (o.hi) h = o.hi[q];
@@ -449,6 +476,8 @@ extern "C" int bx_fit(bx_model* m, int n, const int* toy_idx, const double* thet
     CUF(cudaMemcpyAsync(D.fr, fr.data(), fr.size(), cudaMemcpyHostToDevice, s->fs));
     CUF(cudaMemcpyAsync(D.skip, skip.data(), skip.size(), cudaMemcpyHostToDevice, s->fs));
     CUF(cudaMemcpyAsync(D.ctl, ctl.data(), ctl.size() * sizeof(FitCtl), cudaMemcpyHostToDevice, s->fs));
+    CUF(cudaMemcpyAsync((void*)D.Pf, Pf.data(), Pf.size() * sizeof(int), cudaMemcpyHostToDevice, s->fs));
+    CUF(cudaMemcpyAsync((void*)D.Kf, Kf.data(), Kf.size() * sizeof(int), cudaMemcpyHostToDevice, s->fs));
     CUF(cudaMemsetAsync(D.H, 0, (size_t)n * P * P * 8, s->fs));
     CUF(cudaStreamSynchronize(s->fs));
     if ((st = fit_capture(m, n, o.iters_per_launch))) return st;

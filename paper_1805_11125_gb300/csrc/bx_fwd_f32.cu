@@ -34,8 +34,10 @@ namespace bx {
 constexpr int F32_THREADS = TM / 2;
 constexpr int FCH32 = 32;
 
-__device__ __forceinline__ void kahan_fma(float& acc, float& cmp, float a, float b) {
-    const float y = fmaf(a, b, -cmp);
+// acc += a (b + bl), Kahan-compensated: bl is the low part of the column's double-float spectrum,
+// so that the one rounding per term is the product's (independent from entry to entry)
+__device__ __forceinline__ void kahan_fma(float& acc, float& cmp, float a, float b, float bl) {
+    const float y = fmaf(a, b, fmaf(a, bl, -cmp));
     const float t = __fadd_rn(acc, y);
     cmp = __fsub_rn(__fsub_rn(t, acc), y);
     acc = t;
@@ -52,13 +54,13 @@ __global__ void __launch_bounds__(F32_THREADS) k_fwd_f32(Work w) {
     const size_t cbase = (size_t)item * w.Npad;
     const float4* colf = w.colf + cbase;
     const ColG* colg = w.colg + cbase;
-    const float2* colS = w.colS32 + cbase;
+    const float4* colS = w.colS32 + cbase;
     const int2* colr = w.colr + cbase;
     const int lane = tid & 31, q = tid >> 5, g = m0 + 64 * q;
     // warp-private staging of 32 columns at a time (no block-wide barrier)
     __shared__ float4 sC[2][FCH32];
     __shared__ ColG sG[2][FCH32];
-    __shared__ float2 sS[2][FCH32];
+    __shared__ float4 sS[2][FCH32];
     // column sums: one slice -> R Gg of the lane's two rows added (32 values per column);
     // several slices (MES) -> R of each of the warp's 64 rows
     constexpr int CBR = MES ? 64 : 32;
@@ -81,26 +83,26 @@ __global__ void __launch_bounds__(F32_THREADS) k_fwd_f32(Work w) {
 
     // one column's entries of the lane's rows: both row groups (the common case: two
     // independent chains for the scheduler) or one of them
-    auto column = [&](auto wide_tag, bool inA, bool inB, const float4& cf, const ColG& cg, const float2 S,
+    auto column = [&](auto wide_tag, bool inA, bool inB, const float4& cf, const ColG& cg, const float4 S,
                       float& Ra, float& Rb) {
         constexpr bool WIDE = decltype(wide_tag)::value;
         if (inA && inB) {
             Ra = resp_shape32<WIDE>(mfa, cf, cg);
             Rb = resp_shape32<WIDE>(mfb, cf, cg);
-            kahan_fma(sa, csa, Ra, S.x);
-            kahan_fma(sb, csb, Rb, S.x);
+            kahan_fma(sa, csa, Ra, S.x, S.z);
+            kahan_fma(sb, csb, Rb, S.x, S.z);
             if (TAG) {
-                kahan_fma(ta, cta, Ra, S.y);
-                kahan_fma(tb, ctb, Rb, S.y);
+                kahan_fma(ta, cta, Ra, S.y, S.w);
+                kahan_fma(tb, ctb, Rb, S.y, S.w);
             }
         } else if (inA) {
             Ra = resp_shape32<WIDE>(mfa, cf, cg);
-            kahan_fma(sa, csa, Ra, S.x);
-            if (TAG) kahan_fma(ta, cta, Ra, S.y);
+            kahan_fma(sa, csa, Ra, S.x, S.z);
+            if (TAG) kahan_fma(ta, cta, Ra, S.y, S.w);
         } else {
             Rb = resp_shape32<WIDE>(mfb, cf, cg);
-            kahan_fma(sb, csb, Rb, S.x);
-            if (TAG) kahan_fma(tb, ctb, Rb, S.y);
+            kahan_fma(sb, csb, Rb, S.x, S.z);
+            if (TAG) kahan_fma(tb, ctb, Rb, S.y, S.w);
         }
     };
 
@@ -120,7 +122,7 @@ __global__ void __launch_bounds__(F32_THREADS) k_fwd_f32(Work w) {
             const ColG cgl = in ? colg[i] : ColG{0.f, 0.f, 0.f, 0.f};
             sC[q][lane] = cfl;
             sG[q][lane] = cgl;
-            sS[q][lane] = in ? colS[i] : make_float2(0.f, 0.f);
+            sS[q][lane] = in ? colS[i] : make_float4(0.f, 0.f, 0.f, 0.f);
             const int2 band = in ? colr[i] : make_int2(0, 0);
             const float t0 = fmaf((float)g - cfl.x, cfl.z, cfl.y), t1 = fmaf(63.0f, cfl.z, t0);
             mA = __ballot_sync(0xffffffffu, band.x < g + 32 && band.y > g);
@@ -133,7 +135,7 @@ __global__ void __launch_bounds__(F32_THREADS) k_fwd_f32(Work w) {
             const int c = __ffs(mr) - 1;
             const float4 cf = sC[q][c];
             const ColG cg = sG[q][c];
-            const float2 S = sS[q][c];
+            const float4 S = sS[q][c];
             const bool inA = (mA >> c) & 1u, inB = (mB >> c) & 1u;
             float Ra = 0.f, Rb = 0.f;
             if ((mW >> c) & 1u) column(std::true_type{}, inA, inB, cf, cg, S, Ra, Rb);

@@ -37,6 +37,7 @@ struct __align__(128) SmemTC {
     float B[2][S3_FLOATS];      // species tiles
     float4 colf[KB];
     ColG colg[KB];
+    float colal[KB];
     float rowmax[4][TM];
     uint64_t mma_bar[2];
     uint64_t b_bar[2];
@@ -119,6 +120,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_fwd_tc(Work w) {
     const int nblk = cr.x < cr.y ? (cr.y - 1) / KB + 1 - kb0 : 0;
     const float4* colf = w.colf + (size_t)item * w.Npad;
     const ColG* colg = w.colg + (size_t)item * w.Npad;
+    const float* colal = w.colAl + (size_t)item * w.Npad;
     const float* Sg = T.S_tiles + (size_t)kb0 * S3_FLOATS;
     float acc[8], cmp[8];
 #pragma unroll
@@ -153,6 +155,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_fwd_tc(Work w) {
                 const bool in = i < T.N;
                 sm.colf[tid] = in ? colf[i] : make_float4(0.f, 0.f, 0.f, 0.f);
                 sm.colg[tid] = in ? colg[i] : ColG{0.f, 0.f, 0.f, 0.f};
+                sm.colal[tid] = in ? colal[i] : 0.f;
             }
             tc_fence_after();
             __syncthreads();
@@ -169,7 +172,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_fwd_tc(Work w) {
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int c = 8 * h + q;
-                x[q] = (row_ok && ibase + c < T.N) ? resp_exact32(mf, sm.colf[c], sm.colg[c]) : 0.f;
+                x[q] = (row_ok && ibase + c < T.N) ? resp_amp32(mf, sm.colf[c], sm.colg[c], sm.colal[c]) : 0.f;
                 mx = fmaxf(mx, x[q]);
             }
             sm.rowmax[h][r] = mx;
@@ -219,12 +222,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_fwd_tc(Work w) {
     if (warp < 8) {
         const int row = m0 + (warp & 3) * 32 + (tid & 31);
         if (row < T.M) {
+            // the Kahan sum acc - cmp as a normalised pair: hi plane, then the lo plane cap x Mpad x US later
             float* vrow = static_cast<float*>(w.v) + ((size_t)item * w.Mpad + row) * US + (warp >> 2) * 8;
-            float o[8];
+            float* vlow = vrow + (size_t)w.cap * w.Mpad * US;
+            float o[8], l[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) o[q] = ok ? __fsub_rn(acc[q], cmp[q]) : 0.f;
+            for (int q = 0; q < 8; ++q) {
+                o[q] = ok ? __fsub_rn(acc[q], cmp[q]) : 0.f;
+                l[q] = ok ? __fsub_rn(__fsub_rn(acc[q], o[q]), cmp[q]) : 0.f;
+            }
             *reinterpret_cast<float4*>(vrow) = make_float4(o[0], o[1], o[2], o[3]);
             *reinterpret_cast<float4*>(vrow + 4) = make_float4(o[4], o[5], o[6], o[7]);
+            *reinterpret_cast<float4*>(vlow) = make_float4(l[0], l[1], l[2], l[3]);
+            *reinterpret_cast<float4*>(vlow + 4) = make_float4(l[4], l[5], l[6], l[7]);
         }
     }
 }

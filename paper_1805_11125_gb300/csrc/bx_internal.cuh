@@ -76,6 +76,7 @@ struct Toy {
     double dE, w, r_fid, r_iv, att_len;
     const double* shapes;     // [K][N]
     const float* shapes32;    // [K][N]
+    const float* shapes32l;   // [K][N]: shapes - shapes32 (shapes32 + shapes32l is the FP64 shape to ~2^-48)
     const float* S_tiles;     // [n_kb][3][US*KB]: shapes split in three (split3), UMMA K-major
     const double* stop_pow;   // [N]
     const float2* stop32;     // [N]: the same as FP32 pairs hi + lo (nullptr: split on the fly)
@@ -93,6 +94,7 @@ struct Toy {
     int n_sl, n_r2, n_p2, b_r2;   // b_r2: first radial slice
     int joint2;                   // the 2D slices are the joint grid: slice b_r2 + rho n_p2 + j
     const float* ut;              // [N][NSL]: template modulation 1 + amp u[i][b] (1 for the TFC slices)
+    const float* utl;             // [N][NSL]: (1 + amp u[i][b]) - ut[i][b], the low parts
     const double* U2;             // [K][NSL]: sum_i s_k[i] ut[i][b] (slice-set normalisation)
     const double* psd2;           // [K][n_p2]
 };
@@ -119,7 +121,10 @@ struct Work {
     float4* colf;             // [cap][Npad]: (floor(mu/w), c_hi, hs_hi, hs_lo): hs = w/sig*S_EX2, c = (1/2 - frac(mu/w)) hs
     ColG* colg;               // [cap][Npad]
     double2* colS;            // [cap][Npad]: S_vetoed[i], S_tagged[i] (FP64 model)
-    float2* colS32;           // [cap][Npad]: A_i S_h[i] (vetoed, tagged) in FP32 for the rate-first FP32 forward
+    float4* colS32;           // [cap][Npad]: A_i S_h[i] for the rate-first FP32 forward as double-float pairs
+                              // (vetoed hi, tagged hi, vetoed lo, tagged lo)
+    float* colAl;             // [cap][Npad]: A_i - colg[i].A, the low part of the column amplitude (the
+                              // tensor-core forwards generate R = A_i x shape with it)
     double* aW;               // [cap][nes][Npad]: slice mass sum_{m in W_s} R[m,i] (closed form) times 1/Phi;
                               // as FP32 pairs (hi, lo) in the same bytes in the mixed-precision modes
     int2* colr;               // [cap][Npad]: band rows [r0, r1) of each column (empty: r0 >= r1)
@@ -131,7 +136,7 @@ struct Work {
     int2* tile_cols;          // [cap][MAX_SETS][MAX_TILES]: column range of each forward tile, per
                               // quenching group (tile_range); only the toy's groups are written
     int2* cb_rows;            // [cap][MAX_CB]: row range of each backward column block
-    void* v;                  // [cap][Mpad][US] float (TF32X3) or double (FP64)
+    void* v;                  // [2][cap][Mpad][US] float (TF32X3): species spectra v_k[m] as hi and lo planes
     void* rowW;               // [cap][2 + nes][Mpad] float or double: wt_sub, wt_tag, G_W of every slice
     double* coef;             // [cap][2 + nes][KMAX]: vetoed, tagged, then each slice's Eq. 4 coefficients
     double* gmid;             // [cap][PMAX]
@@ -144,9 +149,11 @@ struct Work {
     int count_units;
     const unsigned char* skip;   // [cap] or nullptr: items flagged 1 are not evaluated (-lnL = +inf)
     // 2D model buffers (UMMA K-major tiles of TF32 hi | lo halves, NSL slices x KB)
-    float* coef2d;            // [cap][3][KMAX][NSL]: r_k dT/dr_k, dT/dr_k, dT/ds_r coefficients
+    float* coef2d;            // [cap][4][KMAX][NSL]: r_k dT/dr_k, dT/dr_k, r_k dT/ds_r coefficients, and the
+                              // low part of the first (r_k dT/dr_k = plane 0 + plane 3 to ~2^-48)
     float* tr2d;              // [cap][tr_kb][3][NSL][KB]: rate-weighted templates (hi | mid | lo)
-    float* y2d;               // [cap][row_kb][2][NSL][KB]: Y = R T_r over output rows
+    unsigned* trmax2d;        // [cap][NSL]: largest |T_r[i,b]| of each slice over all columns (FP32 bits)
+    float* y2d;               // [cap][row_kb][3][NSL][KB]: Y = R T_r over output rows (TF32 hi | lo, FP32 remainder)
     float* w2d;               // [cap][win_kb][2][NSL][KB]: 1 - n/mu over window rows
     float* wt2d;              // [cap][row_kb][2][NSL][KB]: pile-up-correlated weights over rows
     double* nll2d;            // [cap][MAX_TILES][2]: compensated -lnL partials per window tile
@@ -166,7 +173,7 @@ __device__ __forceinline__ int2 tile_range(const Work& w, int item, int grp, int
 constexpr int STATUS_SKIPPED = 1;   // item status of a skipped evaluation
 
 // ------------------------------------------------------------------ launchers (host)
-cudaError_t launch_setup_toy(const Toy& t, float* shapes32, float* S_tiles, float* g32, double* Gg,
+cudaError_t launch_setup_toy(const Toy& t, float* shapes32, float* shapes32l, float* S_tiles, float* g32, double* Gg,
                              cudaStream_t s);
 cudaError_t launch_prep(const Work& w, int n, cudaStream_t s);
 cudaError_t launch_fwd_f64(const Work& w, int n, int max_tiles, int any_tag, int any_cols, cudaStream_t s);
@@ -181,6 +188,12 @@ cudaError_t launch_bwd(const Work& w, int n, int max_cb, cudaStream_t s);
 cudaError_t launch_gather(const Work& w, int n, double* nll_out, double* grad_out, int want_grad, cudaStream_t s);
 cudaError_t launch_eval2d(const Work& w, int n, int want_grad, int want_mu, int stage, cudaStream_t s);
 cudaError_t launch_gather2d(const Work& w, int n, double* nll_out, double* grad_out, int want_grad, cudaStream_t s);
+// several energy estimators: public item j = internal items j E .. j E + E - 1
+constexpr int MAX_EST = 4;
+cudaError_t launch_est_split(const double* theta, int tstride, int n, int E, const Toy* toys, const int* toy_of,
+                             const unsigned char* skip, double* th_int, int Pi, unsigned char* skip_int, cudaStream_t s);
+cudaError_t launch_est_join(const double* nll_int, const double* grad_int, int Pi, int n, int E, const Toy* toys,
+                            const int* toy_of, double* nll, double* grad, int P, int want_grad, cudaStream_t s);
 cudaError_t launch_umma_selftest(const float* A, const float* B, float* D, unsigned* err, cudaStream_t s);
 cudaError_t launch_watchdog_selftest(unsigned* err, unsigned long long budget_ns, cudaStream_t s);
 
@@ -301,6 +314,12 @@ struct Grid {
 };
 __device__ __forceinline__ Grid hi_grid(float mx) {
     const int e = ((__float_as_int(mx) >> 23) & 0xFF) - 127 - 7;
+    if (!(mx > 7.8886091e-31f)) return Grid{0.f, 0.f};   // 2^-100
+    return Grid{__int_as_float((127 - e) << 23), __int_as_float((127 + e) << 23)};
+}
+// The same with a 7-bit hi (|hi / 2^e| <= 128): 2^e = 2^(exponent of mx - 6).
+__device__ __forceinline__ Grid hi_grid7(float mx) {
+    const int e = ((__float_as_int(mx) >> 23) & 0xFF) - 127 - 6;
     if (!(mx > 7.8886091e-31f)) return Grid{0.f, 0.f};   // 2^-100
     return Grid{__int_as_float((127 - e) << 23), __int_as_float((127 + e) << 23)};
 }

@@ -2,8 +2,18 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <vector>
+
+// NVTX range around a host-side scope (stage launches, fits): shown by Nsight Systems on the
+// host timeline, next to the kernels the scope enqueued
+struct BxRange {
+    explicit BxRange(const char* name) { nvtxRangePushA(name); }
+    ~BxRange() { nvtxRangePop(); }
+    BxRange(const BxRange&) = delete;
+    BxRange& operator=(const BxRange&) = delete;
+};
 
 #include "bx_internal.cuh"
 
@@ -26,6 +36,14 @@ struct bx_model {
     double* nll_d = nullptr;
     double* grad_d = nullptr;
     FitState* fit = nullptr;
+    // several energy estimators per dataset (bx_model_create_estimators): toys t E .. t E + E - 1 are
+    // the estimators of dataset t; a public item (one dataset at one joint parameter vector of P =
+    // Pi + 4 (E - 1) entries) is evaluated as E internal items of Pi = Kmax + 7 parameters each
+    int n_est = 1, n_data = 0, Pi = 0;
+    double* est_theta = nullptr;        // [cap E][Pi]
+    double* est_nll = nullptr;          // [cap E]
+    double* est_grad = nullptr;         // [cap E][Pi]
+    unsigned char* est_skip = nullptr;  // [cap E]
     // stage timing (bx_model_profile): events recorded between the stage launches
     int prof_on = 0;
     std::vector<cudaEvent_t> prof_ev;   // 6 per recorded evaluation
@@ -39,4 +57,6 @@ int bx_set_items(bx_model* m, int n, const int* toy_idx);
 int bx_enqueue_eval(bx_model* m, int n, const double* theta_dev, int tstride, int want_grad, int want_mu,
                     double* nll_dev, double* grad_dev);
 int bx_take_device_error(bx_model* m);
+// parameters of public item rows of dataset t (K_t + 7 + 4 (E - 1))
+int bx_public_P(const bx_model* m, int t);
 void bx_fit_free(bx_model* m);

@@ -17,7 +17,12 @@
 //   * every call on a device shares the one array, so calls that overlap on the GPU (two
 //     streams, two host threads) race: serialise them;
 //   * the array keeps whatever the last call left in it; each call re-initialises everything
-//     it reads.
+//     it reads: the dataset descriptor arrives as a kernel argument (copied at launch, so the
+//     call never waits on a host-to-device copy from pageable memory), and the status words
+//     are rewritten before the stages run;
+//   * a parameter point outside the model's domain (non-finite theta, LY <= 0, sigma^2 <= 0)
+//     fills lambda with NaN, so stale contents of the caller's buffer are never mistaken for
+//     spectra.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -45,7 +50,8 @@ struct NoAllocScratch {
     float4 colf[NA_MAX_GRID];
     ColG colg[NA_MAX_GRID];
     double2 colS[NA_MAX_GRID];
-    float2 colS32[NA_MAX_GRID];
+    float4 colS32[NA_MAX_GRID];
+    float colAl[NA_MAX_GRID];
     double aW[NA_MAX_GRID];
     int2 colr[NA_MAX_GRID];
     int2 tile_cols[MAX_TILES];
@@ -57,8 +63,23 @@ void* g_scratch_addr[NA_MAX_DEVICES] = {};
 
 }  // namespace
 
-// 481 KiB per device that loads the library, held until the process exits.
+// 530 KiB per device that loads the library, held until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
+
+// Store the dataset descriptor (passed by value) and clear the status words of the scratch.
+__global__ void k_noalloc_begin(Toy t, NoAllocScratch* scr) {
+    scr->toy = t;
+    scr->toy_of = 0;
+    scr->status = 0;
+    scr->err = 0u;
+}
+
+// After the forward: when the column stage rejected the parameter point, lambda is NaN.
+__global__ void k_noalloc_end(const NoAllocScratch* scr, double* lambda, int n) {
+    if (scr->status == 0) return;
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) lambda[j] = nan;
+}
 
 static int noalloc_scratch(NoAllocScratch** out) {
     int dev = 0;
@@ -144,6 +165,7 @@ extern "C" int bx_spectra_noalloc(int n_grid, double e_max, int n_species, const
     w.colg = scr->colg;
     w.colS = scr->colS;
     w.colS32 = scr->colS32;
+    w.colAl = scr->colAl;
     w.aW = scr->aW;
     w.colr = scr->colr;
     w.tile_cols = scr->tile_cols;
@@ -154,12 +176,15 @@ extern "C" int bx_spectra_noalloc(int n_grid, double e_max, int n_species, const
     w.units = &scr->units;
     w.count_units = 0;
 
-    // the descriptor comes from a stack variable: a pageable copy has consumed it on return
-    cudaError_t e = cudaMemcpyAsync(&scr->toy, &T, sizeof(Toy), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(&scr->toy_of, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(&scr->err, 0, sizeof(unsigned), s);
+    k_noalloc_begin<<<1, 1, 0, s>>>(T, scr);
+    cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = launch_prep(w, 1, s);
     if (e == cudaSuccess) e = launch_fwd_f32(w, 1, T.n_tiles, T.has_tag, 0, s);
+    if (e == cudaSuccess) {
+        const int n = m_hi * (1 + T.has_tag);
+        k_noalloc_end<<<(n + 255) / 256, 256, 0, s>>>(scr, lambda, n);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return bx_set_error(BX_ECUDA, "bx_spectra_noalloc: %s", cudaGetErrorString(e));
     return BX_OK;
 }

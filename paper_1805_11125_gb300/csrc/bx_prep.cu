@@ -19,27 +19,34 @@
 
 namespace bx {
 
-__global__ void k_setup_toy(Toy t, float* shapes32, float* S_tiles, float* g32, double* Gg) {
+__global__ void k_setup_toy(Toy t, float* shapes32, float* shapes32l, float* S_tiles, float* g32, double* Gg) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
-    for (int j = tid; j < t.K * t.N; j += nt) shapes32[j] = (float)t.shapes[j];
+    for (int j = tid; j < t.K * t.N; j += nt) {
+        const float h = (float)t.shapes[j];
+        shapes32[j] = h;
+        shapes32l[j] = (float)(t.shapes[j] - (double)h);
+    }
     // species tile of k-block kb for the tensor-core forward: part p (hi | mid | lo), species
-    // row n split on its own grid over the k-block (split3), column c; K-major, no swizzle:
+    // row n split on its own grid over the k-block (split3, from the FP64 shape: the three parts
+    // hold it to ~2^-30 of the row's largest value), column c; K-major, no swizzle:
     // 8 x (4 x 4 B) core matrices, K step US * 16 B, 8-row step 128 B
     const int per_kb = 3 * US * KB;
     for (int j = tid; j < t.n_kb * US; j += nt) {
         const int kb = j / US, n = j % US;
-        float v[KB];
+        double v[KB];
         float mx = 0.f;
         for (int c = 0; c < KB; ++c) {
             const int i = kb * KB + c;
-            v[c] = (n < t.K && i < t.N) ? (float)t.shapes[(size_t)n * t.N + i] : 0.f;
-            mx = fmaxf(mx, fabsf(v[c]));
+            v[c] = (n < t.K && i < t.N) ? t.shapes[(size_t)n * t.N + i] : 0.0;
+            mx = fmaxf(mx, fabsf((float)v[c]));
         }
         const Grid g = hi_grid(mx);
         float* tile = S_tiles + (size_t)kb * per_kb;
         for (int c = 0; c < KB; ++c) {
-            float hi, mid, lo;
-            split3(v[c], g, hi, mid, lo);
+            const float hi = rintf((float)v[c] * g.inv) * g.scale;
+            const double r = v[c] - (double)hi;
+            const float mid = tf32_rna((float)r);
+            const float lo = tf32_rna((float)(r - (double)mid));
             const int o = (c / 4) * (US * 4) + n * 4 + (c % 4);
             tile[o] = hi;
             tile[US * KB + o] = mid;
@@ -58,9 +65,9 @@ __global__ void k_setup_toy(Toy t, float* shapes32, float* S_tiles, float* g32, 
     }
 }
 
-cudaError_t launch_setup_toy(const Toy& t, float* shapes32, float* S_tiles, float* g32, double* Gg,
+cudaError_t launch_setup_toy(const Toy& t, float* shapes32, float* shapes32l, float* S_tiles, float* g32, double* Gg,
                              cudaStream_t s) {
-    k_setup_toy<<<152, 256, 0, s>>>(t, shapes32, S_tiles, g32, Gg);
+    k_setup_toy<<<152, 256, 0, s>>>(t, shapes32, shapes32l, S_tiles, g32, Gg);
     return cudaGetLastError();
 }
 
@@ -409,10 +416,12 @@ __global__ void __launch_bounds__(256, 3) k_prep32(Work w) {
     double2* cq = w.colq + (size_t)item * w.Npad;
     float4* cf = w.colf + (size_t)item * w.Npad;
     ColG* cg = w.colg + (size_t)item * w.Npad;
-    float2* cs32 = w.colS32 + (size_t)item * w.Npad;
+    float4* cs32 = w.colS32 + (size_t)item * w.Npad;
+    float* cAl = w.colAl + (size_t)item * w.Npad;
     float2* aW2 = reinterpret_cast<float2*>(w.aW + (size_t)item * w.nes * w.Npad);   // [nes][Npad] FP32 pairs
     int2* cr = w.colr + (size_t)item * w.Npad;
     const df gln{0.38729834f, (float)(0.38729833462074170 - (double)0.38729834f)};   // sqrt(3/5) / 2
+    const df ln2d{0.6931471824645996f, -1.9046542121259336e-09f};                      // ln 2
     const df ln4{1.3862944f, (float)(1.3862943611198906 - (double)1.3862944f)};      // 2 ln 2
     int bad = 0;
     unsigned long long inband = 0;
@@ -457,7 +466,8 @@ __global__ void __launch_bounds__(256, 3) k_prep32(Work w) {
                 cq[ie] = make_double2(0.0, 0.0);
                 cf[ie] = make_float4(0.f, 0.f, 0.f, 0.f);
                 cg[ie] = ColG{0.f, 0.f, 0.f, 0.f};
-                cs32[ie] = make_float2(0.f, 0.f);
+                cs32[ie] = make_float4(0.f, 0.f, 0.f, 0.f);
+                cAl[ie] = 0.f;
                 for (int q = 0; q < NES; ++q) aW2[(size_t)q * w.Npad + ie] = make_float2(0.f, 0.f);
                 cr[ie] = make_int2(0, 0);
             }
@@ -498,34 +508,53 @@ __global__ void __launch_bounds__(256, 3) k_prep32(Work w) {
             const df cc = df_mul(df_addf(df_neg(frac), 0.5f), hs);
             cf[ie] = make_float4(jf, cc.h, hs.h, hs.l);
             const df kk = df_mul(gln, hs), kq = df_mul(kk, kk);
-            const df Ad = df_mul(df_mul(cAw, isig), normd);
-            cg[ie] = ColG{df_mul(ln4, kk).h, 2.0f * exp2_neg(-kq.h, -kq.l), cc.l, Ad.h};
-            // rate-weighted spectra of the vetoed (or single) and tagged events (Eq. 3), times the
-            // column amplitude A (the FP32 forward generates R / A)
-            bool nz = false;   // a species of this group has support in the column
-            if (T.shapes32) {
-                float ss = 0.f, st = 0.f;
-#pragma unroll 4
-                for (int k = 0; k < K; ++k) {
-                    if (MULTI && T.set_of[k] != grp) continue;
-                    const float sk = T.shapes32[(size_t)k * N + i];
-                    nz |= sk != 0.f;
-                    ss = fmaf(s_rate[0][k], sk, fmaf(s_rate[1][k], sk, ss));
-                    st = fmaf(s_rate[2][k], sk, fmaf(s_rate[3][k], sk, st));
+            // Ck2 = 2 2^(-kk^2) as a double-float: for kk^2 ln2 < 1/100 from the series of e^(-x)
+            // through x^4 (truncation < 1e-12), else FP32.  The forward multiplies by its FP32 value
+            // Ck2.h; the error Ck2.l, the same at every row of the column, is folded into the column
+            // amplitude: R / A = 8 p0 + 5 Ck2 p0 cosh z, with cosh z = 1 + O(1e-2) over the band,
+            // so A (8 + 5 Ck2) / (8 + 5 Ck2.h) leaves ~1e-2 Ck2.l of it.
+            df Ck2;
+            {
+                const df x = df_mul(kq, ln2d);
+                if (x.h < 0.01f) {
+                    const float x2 = x.h * x.h;
+                    const float tail = x2 * fmaf(x.h, fmaf(x.h, 1.0f / 24.0f, -1.0f / 6.0f), 0.5f);
+                    Ck2 = df_addf(df_neg(x), 1.0f);
+                    Ck2 = df_addf(Ck2, tail);
+                    Ck2 = df{2.0f * Ck2.h, 2.0f * Ck2.l};
+                } else {
+                    Ck2 = df{2.0f * exp2_neg(-kq.h, -kq.l), 0.0f};
                 }
-                cs32[ie] = make_float2(df_mulf(Ad, ss).h, df_mulf(Ad, st).h);
-            } else {   // a descriptor without FP32 shapes
-                double ssub = 0.0, stag = 0.0;
-                for (int k = 0; k < K; ++k) {
-                    if (MULTI && T.set_of[k] != grp) continue;
-                    nz |= T.shapes[(size_t)k * N + i] != 0.0;
-                    const double sk = T.shapes[(size_t)k * N + i] * th[k];
-                    const double t = T.tag ? T.tag[k] : 0.0;
-                    ssub += (T.tag ? 1.0 - t : 1.0) * sk;
-                    stag += t * sk;
-                }
-                cs32[ie] = make_float2(df_mul(Ad, df_from(ssub)).h, df_mul(Ad, df_from(stag)).h);
             }
+            const df Ad0 = df_mul(df_mul(cAw, isig), normd);
+            const float node_w = fmaf(GL_W_OUT, Ck2.h, GL_W_MID);   // 8 + 5 Ck2.h
+            const df Ad = df_mul(Ad0, df_fast(1.0f, GL_W_OUT * Ck2.l / node_w));
+            cg[ie] = ColG{df_mul(ln4, kk).h, Ck2.h, cc.l, Ad.h};
+            cAl[ie] = Ad.l;
+            // rate-weighted spectra of the vetoed (or single) and tagged events (Eq. 3) in
+            // double-float from the split shapes and rates, times the column amplitude A (the FP32
+            // forward generates R / A); kept as double-float pairs, so that no rounding of a
+            // column's spectrum (shared by every row of its band) reaches the expected counts
+            bool nz = false;   // a species of this group has support in the column
+            df ss{0.f, 0.f}, st{0.f, 0.f};
+            for (int k = 0; k < K; ++k) {
+                if (MULTI && T.set_of[k] != grp) continue;
+                df sk;
+                if (T.shapes32) {   // the model's split copy
+                    sk.h = T.shapes32[(size_t)k * N + i];
+                    if (sk.h == 0.f) continue;
+                    sk.l = T.shapes32l[(size_t)k * N + i];
+                } else {            // a descriptor with FP64 shapes only
+                    const double x = T.shapes[(size_t)k * N + i];
+                    if (x == 0.0) continue;
+                    sk = df_from(x);
+                }
+                nz = true;
+                ss = df_add(ss, df_mul(df{s_rate[0][k], s_rate[1][k]}, sk));
+                st = df_add(st, df_mul(df{s_rate[2][k], s_rate[3][k]}, sk));
+            }
+            const df As = df_mul(Ad, ss), At = df_mul(Ad, st);
+            cs32[ie] = make_float4(As.h, At.h, As.l, At.l);
             // slice masses times 1/Phi, as FP32 pairs
             for (int q = 0; q < NES; ++q) {   // one mass per energy slice
                 const df aw = df_mul(slice_mass32(s_par[9 + q], s_par[10 + q], mu, isig), normd);
@@ -570,7 +599,8 @@ __global__ void __launch_bounds__(256, 3) k_prep32(Work w) {
         cq[i] = make_double2(0.0, 0.0);
         cf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         cg[i] = ColG{0.f, 0.f, 0.f, 0.f};
-        cs32[i] = make_float2(0.f, 0.f);
+        cs32[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        cAl[i] = 0.f;
         for (int q = 0; q < NES; ++q) aW2[(size_t)q * w.Npad + i] = make_float2(0.f, 0.f);
         cr[i] = make_int2(0, 0);
     }

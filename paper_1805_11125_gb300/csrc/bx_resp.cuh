@@ -122,6 +122,12 @@ __device__ __forceinline__ float resp_shape32(float mf, const float4& cf, const 
 __device__ __forceinline__ float resp_exact32(float mf, const float4& cf, const ColG& cg) {
     return cg.A * resp_shape32(mf, cf, cg);
 }
+// The same with the column amplitude as a double-float A + al (al: the low part of the
+// column's amplitude): one rounding per entry, and no rounding of A shared by the whole column.
+__device__ __forceinline__ float resp_amp32(float mf, const float4& cf, const ColG& cg, float al) {
+    const float sh = resp_shape32(mf, cf, cg);
+    return fmaf(sh, al, cg.A * sh);
+}
 
 // The three node sums of the adjoint: P0 = sum w_j p_j, P1 = sum w_j t_j p_j,
 // P2 = sum w_j t_j^2 p_j (t in the scaled variable, weights 8, 5, 5), same nodes as the forward.

@@ -219,8 +219,10 @@ def stopping_power(E: np.ndarray) -> np.ndarray:
     return 1.9 * (1.0 + (0.1 / E) ** 0.95)
 
 
-def pileup_spectrum(L: int, width: float) -> np.ndarray:
-    x = np.arange(L) * width
+def pileup_spectrum(L: int, width: float, scale: float = 1.0) -> np.ndarray:
+    """Random-trigger spectrum in bins of ``width`` of an observable whose unit is ``scale``
+    photoelectrons (1 for npe; the ratio of light yields for another energy estimator)."""
+    x = np.arange(L) * width * scale
     g = np.exp(-x / 30.0) + 0.1 * np.exp(-((x - 100.0) ** 2) / (2 * 20.0 ** 2))
     return g / g.sum()
 
@@ -395,6 +397,54 @@ def discrimination(n_grid=2000, e_max=3.0, width=1.0, lo_npe=100.0, hi_npe=1000.
                      field_amp=amp, species=names[:K])
     spec.theta_true = _theta(_rates(rng, K, total))
     return spec
+
+
+# Energy estimators (Sec. 3: the charge, the number of detected photons and the number of fired
+# channels, each an observable with its own response of Eq. 1).  Synthetic stand-ins: each
+# estimator's light yield in its own units per MeV, its resolution parameters, and its window
+# (the npe window scaled by the ratio of light yields); 1-unit bins of the base configuration's
+# width.  Estimator 0 is the base configuration itself.
+ESTIMATORS = {
+    "npe": dict(LY=500.0, a=1.1, b=2e-4, c=4.0),
+    "charge": dict(LY=490.0, a=1.45, b=2e-4, c=6.0),
+    "nhits": dict(LY=430.0, a=0.95, b=1.5e-4, c=3.0),
+}
+EST_TAIL = ("LY", "a", "b", "c")
+
+
+def estimators(base: str = "multivariate", names=("npe", "charge", "nhits")) -> List[ModelSpec]:
+    """One dataset seen by several energy estimators: the base configuration's species, stopping
+    power, tag fractions and rates for every estimator; per estimator its own response parameters
+    (``ESTIMATORS``), window (the base window scaled by LY_e / LY_0) and random-trigger spectrum (in
+    its units).  The radial and pulse-shape terms stay with estimator 0.  Each spec's theta_true is
+    the estimator's own vector [r, LY_e, a_e, b_e, c_e, kB, eps, s_r]; the joint vector is
+    :func:`estimator_theta`."""
+    b = config(base)
+    out = []
+    ly0 = ESTIMATORS[names[0]]["LY"]
+    for e, n in enumerate(names):
+        par = ESTIMATORS[n]
+        f = par["LY"] / ly0
+        m_lo, m_hi = int(round(b.m_lo * f)), int(round(b.m_hi * f))
+        kw = dict(name=f"{base}:{n}", m_lo=m_lo, m_hi=m_hi, pileup=pileup_spectrum(b.L, b.width, 1.0 / f),
+                  counts={})
+        if e > 0:
+            kw.update(rad_class=None, n_rad=0, psd_prob=None)
+        spec = dataclasses.replace(b, **kw)
+        th = b.theta_true.copy()
+        for j, t in enumerate(EST_TAIL):
+            th[b.K + j] = par[t]
+        spec.theta_true = th
+        out.append(spec)
+    return out
+
+
+def estimator_theta(specs: List[ModelSpec]) -> np.ndarray:
+    """The joint parameter vector of the estimators' true values:
+    [r_0 .. r_{K-1}, LY_0, a_0, b_0, c_0, kB, eps, s_r, LY_1, a_1, b_1, c_1, ...]."""
+    K = specs[0].K
+    parts = [specs[0].theta_true] + [s.theta_true[K:K + 4] for s in specs[1:]]
+    return np.concatenate(parts)
 
 
 def config(name: str) -> ModelSpec:

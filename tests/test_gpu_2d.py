@@ -4,7 +4,7 @@ the TFC spectra, all as slices of tensor-core GEMMs) against the FP64 oracle, th
 Tolerances as for the FP32 mode: per-bin relative 1e-5 (absolute 1e-8 max(mu) below
 1e-3 max(mu)), |Delta(-2 lnL)| <= 1e-3, gradient |Delta g_j| |theta_j| <= 1e-3 (1 + |g_j theta_j|).
 The forward GEMM carries no systematic error (its hi*hi products are exact in the tensor
-core's accumulator); the test also bounds the mean signed per-bin error at 5e-8.
+core's accumulator); the test also bounds the mean signed per-bin error at 1e-8.
 """
 import dataclasses
 
@@ -42,7 +42,7 @@ def test_2d_expected_counts_per_bin(name):
         ok, wr, wa = per_bin_ok(mg, mo, rel=1e-5, abs_frac=1e-8)
         assert ok, (wr, wa)
         big = mo >= 1e-3 * mo.max()
-        assert abs(float(np.mean((mg[big] - mo[big]) / mo[big]))) <= 5e-8
+        assert abs(float(np.mean((mg[big] - mo[big]) / mo[big]))) <= 1e-8
 
 
 @pytest.mark.parametrize("name", ["small_2d", "discrimination"])

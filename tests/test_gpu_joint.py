@@ -2,7 +2,7 @@
 the tensor-core path of the 2D model) against the FP64 oracle, through the C ABI.  Tolerances as
 for the 2D model (tests/test_gpu_2d.py): per-bin relative 1e-5 (absolute 1e-8 max(mu) below
 1e-3 max(mu)), |Delta(-2 lnL)| <= 1e-3, gradient |Delta g_j| |theta_j| <= 1e-3 (1 + |g_j theta_j|),
-mean signed per-bin error <= 5e-8."""
+mean signed per-bin error <= 1e-8."""
 import dataclasses
 
 import numpy as np
@@ -46,7 +46,7 @@ def test_joint_expected_counts_per_bin(name):
         ok, wr, wa = per_bin_ok(mg, mo, rel=1e-5, abs_frac=1e-8)
         assert ok, (wr, wa)
         big = mo >= 1e-3 * mo.max()
-        assert abs(float(np.mean((mg[big] - mo[big]) / mo[big]))) <= 5e-8
+        assert abs(float(np.mean((mg[big] - mo[big]) / mo[big]))) <= 1e-8
 
 
 def test_joint_nll_and_gradient():
@@ -61,15 +61,14 @@ def test_joint_nll_and_gradient():
 
 
 def test_joint_full_size_nll():
-    """At theta_true |Delta(-2 lnL)| <= 1e-3.  Away from the optimum a per-bin relative bias delta
-    adds 2 delta |sum mu - sum n| (it cancels where sum mu = sum n): the bound there is
-    1e-3 + 2 (5e-8) |sum mu - sum n|, with the mean-bias bound the expected-counts test holds."""
+    """|Delta(-2 lnL)| <= 1e-3 at theta_true and at two points 2% away (there a per-bin relative
+    bias delta would add 2 delta |sum mu - sum n|, ~4.5e4 events here: the forward's exact
+    accumulation keeps the mean per-bin error at ~1e-10)."""
     s = dataset("joint")
     m = model("joint")
     assert 2 * abs(m.nll(s.theta_true) - O.nll(s, s.theta_true)) <= 1e-3
-    th = points(s, 1, seed=103)[0]
-    excess = abs(O.expected(s, th).sum() - s.counts_vector().sum())
-    assert 2 * abs(m.nll(th) - O.nll(s, th)) <= 1e-3 + 2 * 5e-8 * excess
+    for th in points(s, 2, seed=103):
+        assert 2 * abs(m.nll(th) - O.nll(s, th)) <= 1e-3
 
 
 def test_joint_marginals_against_the_separate_2d_model():

@@ -3,7 +3,7 @@
 Tolerances (derived from the arithmetic of each precision mode):
   * expected counts per bin: relative 1e-5 on bins with mu >= 1e-3 max(mu), absolute
     1e-8 max(mu) below (FP64 path: 1e-10 relative);
-  * mean signed relative error over the bins with mu >= 1e-3 max(mu): <= 5e-8 in the
+  * mean signed relative error over the bins with mu >= 1e-3 max(mu): <= 1e-8 in the
     mixed-precision modes (no systematic error: the Baker-Cousins sum turns a bias b into
     Delta(-2 lnL) ~ 2 b |sum(mu - n)|);
   * -lnL: |Delta(-2 lnL)| <= 1e-3 (FP64 path: 1e-7);
@@ -25,8 +25,8 @@ pytestmark = pytest.mark.gpu
 
 PRECS = [bx.BX_FP64, bx.BX_FP32, bx.BX_TF32X3]
 TOL = {bx.BX_FP64: dict(rel=1e-10, abs=1e-12, d2nll=1e-7, grad=1e-9, bias=1e-12),
-       bx.BX_FP32: dict(rel=1e-5, abs=1e-8, d2nll=1e-3, grad=1e-3, bias=5e-8),
-       bx.BX_TF32X3: dict(rel=1e-5, abs=1e-8, d2nll=1e-3, grad=1e-3, bias=5e-8)}
+       bx.BX_FP32: dict(rel=1e-5, abs=1e-8, d2nll=1e-3, grad=1e-3, bias=1e-8),
+       bx.BX_TF32X3: dict(rel=1e-5, abs=1e-8, d2nll=1e-3, grad=1e-3, bias=1e-8)}
 
 
 def d2nll_tol(prec, spec, theta):
@@ -77,8 +77,8 @@ def test_nll_and_gradient(name, prec):
 @pytest.mark.parametrize("prec", [bx.BX_FP32, bx.BX_TF32X3])
 def test_nll_far_from_the_optimum(prec):
     """Points 6% (rms) away from theta_true, where hundreds of bins have |n - mu| between mu/4
-    and mu (the wider range of the FP32 Baker-Cousins series) and -lnL is ~1e5:
-    |Delta(-2 lnL)| within 1e-3 plus 2e-8 of -lnL (FP32 relative rounding of larger terms)."""
+    and mu, the Baker-Cousins terms reach a few hundred and -lnL is ~1e5: |Delta(-2 lnL)| <= 1e-3
+    all the same (the bound of every other point)."""
     s = dataset("multivariate")
     m = model("multivariate", prec)
     n = s.counts_vector()
@@ -89,7 +89,7 @@ def test_nll_far_from_the_optimum(prec):
         assert np.count_nonzero((np.abs(x) > 0.25) & (x >= -0.5) & (x <= 1.0)) > 300
         f, g = m.nll_grad(t)
         fo, go = O.nll(s, t, grad=True)
-        assert 2 * abs(f - fo) <= 1e-3 + 2e-8 * abs(fo), (f, fo)
+        assert 2 * abs(f - fo) <= 1e-3, (f, fo)
         ok, worst = grad_ok(g[: s.P], go, t, TOL[prec]["grad"])
         assert ok, worst
 

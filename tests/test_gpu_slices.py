@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 
 PRECS = [bx.BX_FP64, bx.BX_FP32]
 TOL = {bx.BX_FP64: dict(rel=1e-10, abs=1e-12, d2nll=1e-7, grad=1e-9, bias=1e-12),
-       bx.BX_FP32: dict(rel=1e-5, abs=1e-8, d2nll=1e-3, grad=1e-3, bias=5e-8)}
+       bx.BX_FP32: dict(rel=1e-5, abs=1e-8, d2nll=1e-3, grad=1e-3, bias=1e-8)}
 
 _models = {}
 

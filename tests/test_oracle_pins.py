@@ -664,3 +664,88 @@ def test_joint_grid_conserves_each_species_with_the_field_on(amp):
         grid = h["j2d"].reshape(nR, nP, nw)
         assert h["sub"].sum() == pytest.approx(want, rel=1e-12)
         assert grid.sum() == pytest.approx(want, rel=1e-12)
+
+
+# ---- several energy estimators of one dataset (Sec. 3), fitted jointly
+
+def _est_specs(base="small_mv", names=("npe", "charge", "nhits"), seed=40):
+    sp = I.estimators(base, names)
+    return [s.with_counts(I.poisson_counts(O.expected(s, s.theta_true), seed + e)) for e, s in enumerate(sp)]
+
+
+def test_one_estimator_is_the_single_model():
+    """E = 1: the joint -lnL and gradient are the single model's, bit for bit."""
+    s = _est_specs(names=("npe",))
+    th = I.parameter_points(s[0].theta_true, 1, rel=0.02, seed=50, free=s[0].default_free())[0]
+    f, g = O.nll_estimators(s, th, grad=True)
+    f1, g1 = O.nll(s[0], th, grad=True)
+    assert f == f1
+    np.testing.assert_array_equal(g, g1)
+
+
+def test_estimators_sum_their_own_models():
+    """Each estimator enters at its own parameter vector [r, LY_e, a_e, b_e, c_e, kB, eps, s_r]:
+    the joint -lnL is the sum of the single models evaluated there, and the joint gradient puts
+    each estimator's LY, a, b, c derivatives in its own slots and sums the shared ones."""
+    s = _est_specs()
+    K = s[0].K
+    th = I.estimator_theta(s) * (1.0 + 0.02 * np.random.default_rng(3).standard_normal(K + 7 + 8))
+    th[K + 6] = 1.0
+    f, g = O.nll_estimators(s, th, grad=True)
+    parts = []
+    for e, sp in enumerate(s):
+        the = np.concatenate([th[:K], th[K:K + 4] if e == 0 else th[K + 7 + 4 * (e - 1):K + 7 + 4 * e], th[K + 4:K + 7]])
+        np.testing.assert_array_equal(O.est_theta(K, e, th), the)
+        parts.append(O.nll(sp, the, grad=True))
+    assert f == pytest.approx(sum(p[0] for p in parts), rel=1e-15)
+    np.testing.assert_allclose(g[:K], sum(p[1][:K] for p in parts), rtol=1e-13)
+    np.testing.assert_allclose(g[K + 4:K + 7], sum(p[1][K + 4:K + 7] for p in parts), rtol=1e-13, atol=1e-12)
+    for e in range(3):
+        o = K if e == 0 else K + 7 + 4 * (e - 1)
+        np.testing.assert_array_equal(g[o:o + 4], parts[e][1][K:K + 4])
+
+
+def test_identical_estimators_double_the_likelihood():
+    """Two copies of one estimator: twice its -lnL, twice its rate gradient, and each copy's own
+    response-parameter gradient equal to the single model's."""
+    one = _est_specs(base="small_plain", names=("npe",))   # no radial / pulse-shape term to count once
+    two = [one[0], one[0]]
+    K = one[0].K
+    th1 = one[0].theta_true * 1.01
+    th2 = np.concatenate([th1, th1[K:K + 4]])
+    f1, g1 = O.nll(one[0], th1, grad=True)
+    f2, g2 = O.nll_estimators(two, th2, grad=True)
+    assert f2 == pytest.approx(2 * f1, rel=1e-15)
+    np.testing.assert_allclose(g2[:K], 2 * g1[:K], rtol=1e-15)
+    np.testing.assert_array_equal(g2[K:K + 4], g1[K:K + 4])
+    np.testing.assert_array_equal(g2[K + 7:K + 11], g1[K:K + 4])
+
+
+def test_estimators_dual_gradient_matches_central_differences():
+    s = _est_specs()
+    K = s[0].K
+    th = I.estimator_theta(s)
+    th = th * (1.0 + 0.02 * np.random.default_rng(4).standard_normal(th.shape[0]))
+    th[K + 6] = 1.0
+    f, g = O.nll_estimators(s, th, grad=True)
+    for p in [0, K - 1, K, K + 3, K + 4, K + 5, K + 7, K + 10, K + 11, K + 14]:
+        h = 1e-5 * abs(th[p])
+        tp, tm = th.copy(), th.copy()
+        tp[p] += h
+        tm[p] -= h
+        fd = (O.nll_estimators(s, tp) - O.nll_estimators(s, tm)) / (2 * h)
+        assert abs(fd - g[p]) * abs(th[p]) <= 1e-6 * (1 + abs(g[p] * th[p])), (p, fd, g[p])
+
+
+def test_estimators_asimov_fit_returns_truth():
+    """Asimov data in every estimator: the joint fit returns the joint true vector."""
+    sp = I.estimators("small_mv", ("npe", "nhits"))
+    sp = [s.with_counts(O.expected(s, s.theta_true)) for s in sp]
+    th_true = I.estimator_theta(sp)
+    free, _, _ = O.estimator_defaults(sp)
+    th0 = I.parameter_points(th_true, 1, rel=0.01, seed=51, free=free)[0]
+    r = O.fit_estimators(sp, th0, tol_edm=1e-14)
+    assert r["status"] == 0
+    m = free.astype(bool)
+    np.testing.assert_allclose(r["theta"][m], th_true[m], rtol=2e-5)
+    assert r["nll"] < 1e-8
