@@ -59,10 +59,16 @@ typedef enum {
     BX_FP32 = 1,        /* mixed: response generated and contracted in FP32 on the CUDA cores
                            (round-to-nearest, compensated accumulation); FP64 column
                            normalisation, spectra assembly, -lnL sum and fit update */
-    BX_TF32X3 = 3       /* as BX_FP32, but the contraction runs on the tensor cores as
-                           TF32 hi*hi + hi*lo + lo*hi with FP32 accumulation in tensor
-                           memory (its accumulator does not round to nearest: see the
-                           error table of the documentation before using it for fits) */
+    BX_BF16X3 = 2,      /* the 2D models (discrimination regime, joint grid): as BX_FP32, but
+                           the response GEMM's operands are split in three BF16 parts (hi on
+                           a grid fixed for the contraction, BF16 mid and lo; 6 of the 9
+                           products) on tcgen05.mma kind::f16 with FP32 accumulation in tensor
+                           memory, in place of the TF32 parts of BX_FP32 (~24 instead of ~30
+                           significant bits per operand) */
+    BX_TF32X3 = 3       /* the 1D models: as BX_FP32, but the species-resolved contraction
+                           runs on the tensor cores with three-part TF32 operands (hi on a
+                           per-row grid, TF32 mid and lo) and FP32 accumulation in tensor
+                           memory; the 2D models always run their GEMMs on the tensor cores */
 } bx_precision;
 
 enum { BX_RAD_INTERNAL = 0, BX_RAD_EXTERNAL = 1 };
@@ -94,7 +100,7 @@ typedef struct {
      * Slice b of the 2D energy x radius histogram is the energy window of the events in
      * radial bin b (rad_class and the radial geometry as for n_rad), likewise for pulse
      * shape.  Species templates s_k[i] q_k[b] (1 + field_amp u[i][b]), normalised per
-     * species over each slice set; Eq. 2 on every slice.  Requires BX_FP32, n_rad = n_psd = 0
+     * species over each slice set; Eq. 2 on every slice.  Requires BX_FP32 or BX_BF16X3, n_rad = n_psd = 0
      * and n_rad2d + n_psd2d + 1 + (tag_frac != NULL) <= 128 slices; all toys of a model
      * are either 2D or not. */
     int n_rad2d;                /* radial slices over [0, r_fid) (0: no energy x radius histogram) */
@@ -131,6 +137,15 @@ typedef struct {
      * <= 128; field2d is [N][n_rad2d * n_psd2d], counts_rad2d [n_rad2d * n_psd2d][m_hi - m_lo]
      * and counts_psd2d is not read. */
     int joint2d;
+    /* A non-Gaussian response (the "more sophisticated response function" of the paper's
+     * outlook; Eq. 1's p0, p1, ...): the Gram-Charlier series of the Gaussian with skewness
+     * resp_skew and excess kurtosis resp_kurt, density
+     *   phi(z) [1 + resp_skew/6 He3(z) + resp_kurt/24 He4(z)],  He3 = z^3 - 3z, He4 = z^4 - 6z^2 + 3,
+     * so the mean (LY Q) and variance (a mu + b mu^2 + c) of the response stay those of Eq. 1.
+     * Bin masses from its closed-form CDF Phi(z) - phi(z) [resp_skew/6 (z^2 - 1) + resp_kurt/24
+     * (z^3 - 3z)], normalised to the mass above 0 npe.  0, 0: the Gaussian.  Otherwise BX_FP64
+     * only, no 2D histograms, and the density must stay non-negative within band_sigmas. */
+    double resp_skew, resp_kurt;
 } bx_model_desc;
 
 typedef struct {
@@ -208,13 +223,21 @@ int bx_nll_batch(bx_model* model, int n, const int* toy_idx, const double* theta
  * iterate the Hessian is re-measured by central differences of the gradient (all 2 n_free
  * displaced points in one batched evaluation) and inverted with the smallest Levenberg
  * damping that makes it positive definite; the line search evaluates 8 step lengths
- * (1 .. 1/128) in one batched evaluation and takes the largest with sufficient decrease.
- * Each fit therefore uses 8 + 2P evaluation slots: the model needs
- * max_batch >= n (8 + 2P).  Converged when EDM = g^T V g / 2 < tol_edm with a fresh,
- * at most lightly damped Hessian.  With BX_FP32 the gradient noise sets an EDM floor and
- * the tolerance used is max(tol_edm, 1e-5) (distance to the optimum < ~0.005 sigma); an
- * FP64 model started at the FP32 optimum refines it in a few iterations.  The iterations
- * run as a captured CUDA graph. */
+ * (1 .. 1/128, within a trust region of the response, pile-up and radial parameters) in one
+ * batched evaluation and takes the largest with sufficient decrease.  Each fit in flight
+ * occupies 8 + 2P evaluation slots (max_batch >= 8 + 2P).  Converged when EDM = g^T V g / 2 <
+ * tol_edm with a fresh, at most lightly damped Hessian.  With BX_FP32 the gradient noise sets an
+ * EDM floor and the tolerance used is max(tol_edm, 1e-5) (distance to the optimum < ~0.005
+ * sigma); an FP64 model started at the FP32 optimum refines it in a few iterations.
+ * The n fits run as one persistent launch: a device work queue feeds F fits in flight (F <=
+ * max_batch / (8 + 2P)); when a fit finishes its result is stored and its slots take the next
+ * fit of the queue, on the device.  The rounds run inside one CUDA graph whose conditional
+ * loop the device ends when no fit is active or a budget is spent (the evaluation budget, or
+ * time_budget_s of wall time on the device clock: unfinished fits then report BX_ETIMEOUT).  F
+ * is the caller's fits_in_flight, or the autotuner's choice: it times one evaluation round for
+ * F = the largest feasible value and its halves, and for each forward tile shape of the model,
+ * on the fits' own datasets; the choice is kept for further calls of the same size and is
+ * reported by bx_fit_last_plan. */
 typedef struct {
     double tol_edm;             /* EDM tolerance (0 -> 1e-8) */
     int max_iter;               /* evaluation budget per fit (0 -> 5000) */
@@ -227,6 +250,8 @@ typedef struct {
                                    at the last fresh Hessian (the covariance of the estimates at a
                                    converged fit); rows and columns of fixed parameters and of
                                    parameters held at a bound are 0 */
+    double time_budget_s;       /* device-clock budget of the whole batch (0 -> 300 s) */
+    int fits_in_flight;         /* fits run concurrently by the work queue (0: autotuned) */
 } bx_fit_opts;
 /* free_mask/lo/hi are given in the layout of a toy with max K species: slots 0..Kmax-1 are
  * rates, Kmax..Kmax+6 the seven response/pile-up/radial parameters (then LY, a, b, c of every
@@ -238,7 +263,7 @@ typedef struct {
     double edm;                 /* estimated distance to minimum */
     int iters;                  /* accepted Newton steps */
     int n_evals;                /* NLL+gradient evaluations used */
-    int status;                 /* BX_OK, BX_ENOTCONV or BX_EDOMAIN */
+    int status;                 /* BX_OK, BX_ENOTCONV, BX_EDOMAIN or BX_ETIMEOUT (time budget spent) */
     int n_at_bound;             /* free parameters held at a bound at the returned theta: on the
                                    bound with the gradient pointing out of the box, so outside the
                                    Newton step (a parameter resting on a bound with an inward or
@@ -246,6 +271,20 @@ typedef struct {
     double damping;             /* Levenberg damping of the last fresh Hessian (scaled units;
                                    0: positive definite as measured) */
 } bx_fit_result;
+
+/* The launch plan of the last bx_fit call on a model. */
+typedef struct {
+    int fits;                   /* fits of the call */
+    int fits_in_flight;         /* F: fits the work queue kept running at once (the wave shape) */
+    int slots_per_fit;          /* evaluation items per fit in flight: 8 + 2P */
+    int iters_per_launch;       /* evaluation rounds per pass of the graph's loop body */
+    int graph_launches;         /* host launches of the batch (1) */
+    int rounds;                 /* evaluation rounds the device loop ran */
+    int fwd_tile;               /* forward tile shape chosen by the autotuner (0: 128-row CTAs,
+                                   1: 64-row CTAs of the FP32 forward; -1: not tuned) */
+    double tuned_evals_per_s;   /* evaluation throughput of the chosen shape when it was tuned */
+} bx_fit_plan;
+int bx_fit_last_plan(const bx_model* model, bx_fit_plan* out);
 
 /* n fits; item j fits toy toy_idx[j] (host, NULL = toy 0) from theta0[j*P..].
  * theta_out[n*P], res[n] (host).  Returns BX_OK when every fit converged, otherwise the

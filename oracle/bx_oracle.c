@@ -90,6 +90,7 @@ static dual gauss_mass(dual za, dual zb) {
     return dsub(dsub(dc(1.0), dQ(zb)), dPhi(za));
 }
 
+
 typedef struct {
     int n_grid; double e_max;
     int K; const double* shapes;       /* [K][n_grid] */
@@ -117,12 +118,43 @@ typedef struct {
                                           [es_edges[s], es_edges[s+1]), edges from 0 to m_hi - m_lo;
                                           n_es = 0 -> one slice, the whole window.  The radial and
                                           pulse-shape counts are then [n_es][n_rad], [n_es][n_psd] */
+    double gc_skew, gc_kurt;           /* Gram-Charlier response (a non-Gaussian response of the kind
+                                          the paper's outlook plans): skewness gamma_1 and excess
+                                          kurtosis gamma_2 of the photoelectron response; 0, 0 is the
+                                          Gaussian */
     int joint2;                        /* 2D slices as the joint grid of radius and pulse shape:
                                           slice (rho, j) = rho n_p2 + j of the n_r2 x n_p2 grid is the
                                           energy window of the events in radial bin rho and pulse-shape
                                           bin j (the energy x radius x pulse-shape histogram); field
                                           [n_grid][n_r2 n_p2], counts in n_r2_counts [n_r2 n_p2][nw] */
 } om_model;
+
+/* Gram-Charlier (type A) response (reading: the non-Gaussian response of the paper's outlook,
+ * with the paper's mean and variance kept):
+ *   f(z) = phi(z) [1 + g1/6 He3(z) + g2/24 He4(z)],  He3 = z^3 - 3z, He4 = z^4 - 6z^2 + 3,
+ * whose mean, variance, skewness and excess kurtosis are 0, 1, g1, g2 (He3, He4 are orthogonal
+ * to 1, z, z^2 under phi).  Since d/dz [phi He_{n-1}] = -phi He_n, its CDF is
+ *   F(z) = Phi(z) - phi(z) [g1/6 He2(z) + g2/24 He3(z)],  He2 = z^2 - 1,
+ * so a bin's mass is the Gaussian mass minus the difference of phi(z) C(z),
+ * C(z) = g1/6 He2(z) + g2/24 He3(z), at its edges. */
+static dual gc_term(const om_model* m, dual z) {   /* phi(z) C(z) */
+    dual z2 = dmul(z, z);
+    dual he2 = dshift(z2, -1.0), he3 = dsub(dmul(z2, z), dscale(z, 3.0));
+    dual Cz = dadd(dscale(he2, m->gc_skew / 6.0), dscale(he3, m->gc_kurt / 24.0));
+    dual phi = dscale(dexp(dscale(z2, -0.5)), INV_SQRT_2PI);
+    return dmul(phi, Cz);
+}
+static int gc_on(const om_model* m) { return m->gc_skew != 0.0 || m->gc_kurt != 0.0; }
+static dual resp_mass(const om_model* m, dual za, dual zb) {
+    dual g = gauss_mass(za, zb);
+    return gc_on(m) ? dsub(g, dsub(gc_term(m, zb), gc_term(m, za))) : g;
+}
+/* mass above 0 npe of the response of mean mu and width sig: 1 - F(-mu/sig) */
+static dual resp_above0(const om_model* m, dual mu, dual sig) {
+    dual x = ddiv(mu, sig);
+    dual base = dPhi(x);
+    return gc_on(m) ? dadd(base, gc_term(m, dscale(x, -1.0))) : base;
+}
 
 enum { OM_MAX_SETS = 4 };
 
@@ -277,7 +309,7 @@ static int stage_a1(const om_model* m, const dual* th, work* w, double xi) {
         dual var = dadd(dadd(dmul(a, w->mu[i]), dmul(b, dmul(w->mu[i], w->mu[i]))), c);
         if (!(var.v > 0.0)) { st = OM_EDOMAIN; var = dc(1.0); }
         w->sig[i] = dsqrt(var);
-        w->den[i] = dPhi(ddiv(w->mu[i], w->sig[i]));
+        w->den[i] = resp_above0(m, w->mu[i], w->sig[i]);
     }
     return st;
 }
@@ -296,7 +328,7 @@ static void stage_a23(const om_model* m, work* w, double* R_out, const dual* Tr,
         for (int i = 0; i < N; ++i) {
             dual za = ddiv(dsub(dc(r * m->width), w->mu[i]), w->sig[i]);
             dual zb = ddiv(dsub(dc((r + 1) * m->width), w->mu[i]), w->sig[i]);
-            dual R = ddiv(gauss_mass(za, zb), w->den[i]);
+            dual R = ddiv(resp_mass(m, za, zb), w->den[i]);
             if (R_out) R_out[(size_t)r * N + i] = R.v;
             for (int k = 0; k < K; ++k) {
                 if (set_of && set_of[k] != c) continue;

@@ -64,6 +64,7 @@ class _Model(C.Structure):
         ("psd2", C.c_void_p), ("n_r2_counts", C.c_void_p), ("n_p2_counts", C.c_void_p),
         ("quench", C.c_void_p),
         ("n_es", C.c_int), ("es_edges", C.c_void_p),
+        ("gc_skew", C.c_double), ("gc_kurt", C.c_double),
         ("joint2", C.c_int),
     ]
 
@@ -127,6 +128,7 @@ class OracleModel:
             n_r2=s.n_rad2d, n_p2=s.n_psd2d, field=_ptr(k["field"]), amp=s.field_amp, psd2=_ptr(k["psd2"]),
             n_r2_counts=_ptr(k["n_r2"]), n_p2_counts=_ptr(k["n_p2"]), quench=_ptr(k["quench"]),
             n_es=0 if k["es_edges"] is None else len(k["es_edges"]) - 1, es_edges=_ptr(k["es_edges"]),
+            gc_skew=getattr(s, "resp_skew", 0.0), gc_kurt=getattr(s, "resp_kurt", 0.0),
             joint2=1 if getattr(s, "joint2d", False) else 0)
         self.ref = C.byref(self.c)
 

@@ -21,7 +21,7 @@ import numpy as np
 from . import build as _build
 
 BX_OK, BX_EINVAL, BX_ENOMEM, BX_ECUDA, BX_EDOMAIN, BX_ETIMEOUT, BX_ENOTCONV = 0, -1, -2, -3, -4, -5, -6
-BX_FP64, BX_FP32, BX_TF32X3 = 0, 1, 3
+BX_FP64, BX_FP32, BX_BF16X3, BX_TF32X3 = 0, 1, 2, 3
 
 _P = C.c_void_p
 
@@ -42,6 +42,7 @@ class bx_model_desc(C.Structure):
         ("quench", _P),
         ("n_eslice", C.c_int), ("eslice_edges", _P),
         ("joint2d", C.c_int),
+        ("resp_skew", C.c_double), ("resp_kurt", C.c_double),
     ]
 
 
@@ -52,7 +53,14 @@ class bx_options(C.Structure):
 
 class bx_fit_opts(C.Structure):
     _fields_ = [("tol_edm", C.c_double), ("max_iter", C.c_int), ("free_mask", _P), ("lo", _P), ("hi", _P),
-                ("iters_per_launch", C.c_int), ("cov_out", _P)]
+                ("iters_per_launch", C.c_int), ("cov_out", _P), ("time_budget_s", C.c_double),
+                ("fits_in_flight", C.c_int)]
+
+
+class bx_fit_plan(C.Structure):
+    _fields_ = [("fits", C.c_int), ("fits_in_flight", C.c_int), ("slots_per_fit", C.c_int),
+                ("iters_per_launch", C.c_int), ("graph_launches", C.c_int), ("rounds", C.c_int),
+                ("fwd_tile", C.c_int), ("tuned_evals_per_s", C.c_double)]
 
 
 class bx_fit_result(C.Structure):
@@ -84,6 +92,7 @@ SIGNATURES = [
     ("bx_expected", C.c_int, [_P, C.c_int, _P, _P]),
     ("bx_nll_batch", C.c_int, [_P, C.c_int, _P, _P, _P, _P, C.c_int]),
     ("bx_fit", C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P]),
+    ("bx_fit_last_plan", C.c_int, [_P, _P]),
     ("bx_selftest_tensor_core", C.c_int, [_P]),
     ("bx_selftest_watchdog", C.c_int, [C.c_double]),
     ("bx_spectra_noalloc", C.c_int, [C.c_int, C.c_double, C.c_int, _P, _P, _P, C.c_double, C.c_int, _P, _P, _P]),
@@ -179,6 +188,7 @@ class Model:
             d.n_eslice = 0 if k["es"] is None else len(k["es"]) - 1
             d.eslice_edges = _ptr(k["es"])
             d.joint2d = 1 if getattr(s, "joint2d", False) else 0
+            d.resp_skew, d.resp_kurt = getattr(s, "resp_skew", 0.0), getattr(s, "resp_kurt", 0.0)
         opts = bx_options(precision, max_batch, band_sigmas, watchdog_s)
         h = C.c_void_p()
         if n_est == 1:
@@ -279,7 +289,7 @@ class Model:
         return 8 + 2 * self.P
 
     def fit(self, theta0, toy_idx=None, tol_edm: float = 0.0, max_iter: int = 0, free=None, lo=None, hi=None,
-            iters_per_launch: int = 0, want_cov: bool = False):
+            iters_per_launch: int = 0, want_cov: bool = False, time_budget_s: float = 0.0, fits_in_flight: int = 0):
         """n fits (one row of theta0 each) on the device; returns (theta[n, P], info, status).
         info[j]: nll, edm, iters, n_evals, status, n_at_bound, damping, and with want_cov the
         inverse Hessian of -lnL ("cov", P x P; zero rows for fixed and bound-held parameters)."""
@@ -292,11 +302,12 @@ class Model:
         fr = None if free is None else np.ascontiguousarray(free, dtype=np.uint8)
         l, h = _f64(lo), _f64(hi)
         cov = np.zeros((n, self.P, self.P)) if want_cov else None
-        o = bx_fit_opts(tol_edm, max_iter, _ptr(fr), _ptr(l), _ptr(h), iters_per_launch, _ptr(cov))
+        o = bx_fit_opts(tol_edm, max_iter, _ptr(fr), _ptr(l), _ptr(h), iters_per_launch, _ptr(cov), time_budget_s,
+                        fits_in_flight)
         out = np.zeros((n, self.P))
         res = (bx_fit_result * n)()
         st = lib().bx_fit(self.h, n, _ptr(ti), _ptr(th0), C.byref(o), _ptr(out), C.cast(res, _P))
-        if st not in (BX_OK, BX_ENOTCONV):
+        if st not in (BX_OK, BX_ENOTCONV, BX_ETIMEOUT, BX_EDOMAIN):
             _check(st)
         info = [dict(nll=r.nll, edm=r.edm, iters=r.iters, n_evals=r.n_evals, status=r.status,
                      n_at_bound=r.n_at_bound, damping=r.damping) for r in res]
@@ -305,6 +316,12 @@ class Model:
                 info[j]["cov"] = cov[j]
         return out, info, st
 
+
+    def fit_plan(self) -> dict:
+        """The launch plan of the last fit call (bx_fit_last_plan)."""
+        p = bx_fit_plan()
+        _check(lib().bx_fit_last_plan(self.h, C.byref(p)))
+        return {k: getattr(p, k) for k, _ in bx_fit_plan._fields_}
 
     def profile_scan(self, param: int, values, theta_start, toy: int = 0, free=None, tol_edm: float = 0.0,
                      max_iter: int = 0):

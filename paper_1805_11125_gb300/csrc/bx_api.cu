@@ -133,6 +133,9 @@ static int validate_desc(const bx_model_desc& d, int t) {
     REQ(d.n_rad2d >= 0 && d.n_psd2d >= 0 && d.n_rad2d <= NSL && d.n_psd2d <= NSL,
         "toy %d: n_rad2d, n_psd2d must lie in [0, %d]", t, NSL);
     REQ(d.joint2d == 0 || d.joint2d == 1, "toy %d: joint2d must be 0 or 1", t);
+    REQ(std::isfinite(d.resp_skew) && std::isfinite(d.resp_kurt), "toy %d: resp_skew, resp_kurt must be finite", t);
+    if (d.resp_skew != 0.0 || d.resp_kurt != 0.0)
+        REQ(d.n_rad2d + d.n_psd2d == 0, "toy %d: the Gram-Charlier response is not supported with 2D histograms", t);
     if (d.joint2d) REQ(d.n_rad2d >= 1 && d.n_psd2d >= 1, "toy %d: the joint grid needs n_rad2d, n_psd2d >= 1", t);
     if (d.n_rad2d + d.n_psd2d > 0) {
         const int B2 = d.joint2d ? d.n_rad2d * d.n_psd2d : d.n_rad2d + d.n_psd2d;   // 2D slices
@@ -207,8 +210,9 @@ static int model_create(const bx_model_desc* descs, int n_toys, const bx_options
     if (!descs || n_toys < 1) return bx_set_error(BX_EINVAL, "need at least one model description");
     bx_options o{BX_FP32, 1, 8.0, 2.0};
     if (opts) o = *opts;
-    if (o.precision != BX_FP64 && o.precision != BX_FP32 && o.precision != BX_TF32X3)
-        return bx_set_error(BX_EINVAL, "precision %d not supported (BX_FP64, BX_FP32 or BX_TF32X3)", o.precision);
+    if (o.precision != BX_FP64 && o.precision != BX_FP32 && o.precision != BX_TF32X3 && o.precision != BX_BF16X3)
+        return bx_set_error(BX_EINVAL, "precision %d not supported (BX_FP64, BX_FP32, BX_BF16X3 or BX_TF32X3)",
+                            o.precision);
     if (o.max_batch < 1) return bx_set_error(BX_EINVAL, "max_batch must be >= 1");
     if (o.band_sigmas == 0.0) o.band_sigmas = 8.0;
     if (o.watchdog_s == 0.0) o.watchdog_s = 2.0;
@@ -229,7 +233,22 @@ static int model_create(const bx_model_desc* descs, int n_toys, const bx_options
         if (descs[t].n_eslice > 1 && o.precision == BX_TF32X3)
             return bx_set_error(BX_EINVAL, "toy %d: energy slices need BX_FP32 or BX_FP64", t);
     }
-    if (n2d && o.precision != BX_FP32) return bx_set_error(BX_EINVAL, "2D histograms need BX_FP32");
+    if (n2d && o.precision != BX_FP32 && o.precision != BX_BF16X3)
+        return bx_set_error(BX_EINVAL, "2D histograms need BX_FP32 or BX_BF16X3");
+    if (!n2d && o.precision == BX_BF16X3)
+        return bx_set_error(BX_EINVAL, "BX_BF16X3 is the 2D models' response GEMM (the 1D models: BX_TF32X3)");
+    for (int t = 0; t < n_toys; ++t) {   // the Gram-Charlier response: FP64, density >= 0 within the band
+        const double g1 = descs[t].resp_skew / 6.0, g2 = descs[t].resp_kurt / 24.0;
+        if (g1 == 0.0 && g2 == 0.0) continue;
+        if (o.precision != BX_FP64)
+            return bx_set_error(BX_EINVAL, "toy %d: the Gram-Charlier response needs BX_FP64", t);
+        for (int j = 0; j <= 4000; ++j) {
+            const double z = o.band_sigmas * (j / 2000.0 - 1.0), z2 = z * z;
+            if (1.0 + g1 * z * (z2 - 3.0) + g2 * (z2 * (z2 - 6.0) + 3.0) < 0.0)
+                return bx_set_error(BX_EINVAL, "toy %d: the Gram-Charlier density is negative at z = %.3f (within %g sigma)",
+                                    t, z, o.band_sigmas);
+        }
+    }
     int dev = 0;
     CU(cudaGetDevice(&dev));
     int cc_major = 0, cc_minor = 0;
@@ -296,6 +315,8 @@ static int model_create(const bx_model_desc* descs, int n_toys, const bx_options
         T.n_kb = (T.N + KB - 1) / KB;
         T.dE = d.e_max / d.n_grid;
         T.w = d.width;
+        T.gc1 = d.resp_skew / 6.0;
+        T.gc2 = d.resp_kurt / 24.0;
         T.r_fid = d.r_fid;
         T.r_iv = d.r_iv;
         T.att_len = d.att_len;
@@ -347,6 +368,31 @@ static int model_create(const bx_model_desc* descs, int n_toys, const bx_options
                     utl[(size_t)i * NSL + b] = (float)(u - (double)uh);
                     for (int k = 0; k < T.K; ++k) U2[(size_t)k * NSL + b] += d.shapes[(size_t)k * T.N + i] * u;
                 }
+            // template classes per slice set: species with the same slice probabilities (radial
+            // class, pulse-shape row, or both on the joint grid) share one class
+            for (int sset = 0; sset < 4; ++sset) {
+                T.n_cls[sset] = 0;
+                for (int k = 0; k < T.K; ++k) {
+                    auto same = [&](int a, int b) {
+                        const bool rad = (sset == 2) && T.n_r2 > 0;
+                        const bool psd = (sset == 3 || (sset == 2 && T.joint2)) && T.n_p2 > 0;
+                        if (rad && d.rad_class[a] != d.rad_class[b]) return false;
+                        if (psd && memcmp(d.psd2d_prob + (size_t)a * T.n_p2, d.psd2d_prob + (size_t)b * T.n_p2,
+                                          sizeof(double) * T.n_p2) != 0)
+                            return false;
+                        return true;
+                    };
+                    int c = 0;
+                    while (c < T.n_cls[sset] && !same(k, T.cls_rep[sset][c])) ++c;
+                    if (c == T.n_cls[sset]) T.cls_rep[sset][T.n_cls[sset]++] = k;
+                    T.cls_of[sset][k] = c;
+                }
+            }
+            std::vector<float> utmax(NSL, 0.f);
+            for (int i = 0; i < T.N; ++i)
+                for (int b = 0; b < T.n_sl; ++b) utmax[b] = std::max(utmax[b], std::fabs(ut[(size_t)i * NSL + b]));
+            for (int b = 0; b < NSL; ++b) utmax[b] *= 1.0f + 1e-6f;   // above the double-float values too
+            if ((st = upload(m, utmax.data(), utmax.size(), &T.utmax))) break;
             if ((st = upload(m, ut.data(), ut.size(), &T.ut))) break;
             if ((st = upload(m, utl.data(), utl.size(), &T.utl))) break;
             if ((st = upload(m, U2.data(), U2.size(), &T.U2))) break;
@@ -381,6 +427,7 @@ static int model_create(const bx_model_desc* descs, int n_toys, const bx_options
         m->any_tag |= T.has_tag;
         m->any_cols |= (T.n_rad > 0 || T.n_psd > 0) ? 1 : 0;
         m->is2d |= T.n_sl > 0 ? 1 : 0;
+        if (T.n_sl > 0) m->ncs2d = std::max(m->ncs2d, T.n_cls[0] + T.n_cls[1] + T.n_cls[2] + T.n_cls[3]);
     }
     if (st) {
         cudaStreamSynchronize(m->stream);
@@ -414,6 +461,7 @@ static int model_create(const bx_model_desc* descs, int n_toys, const bx_options
     w.win_kb = (m->nwmax + KB - 1) / KB;
     w.win_tiles = (m->nwmax + TM - 1) / TM;
     w.Lmax = m->Lmax;
+    w.ncs2d = m->ncs2d;
     if (!m->is2d) {   // the assembly stage holds one item's spectra and columns in shared memory
         size_t need = 0, avail = 0;
         const cudaError_t e = mid_smem_budget(w, m->Mmax, m->nwmax, m->Lmax, &need, &avail);
@@ -464,6 +512,9 @@ static int model_create(const bx_model_desc* descs, int n_toys, const bx_options
         {(void**)&w.coef2d, m->is2d ? sizeof(float) * cap * 4 * KMAX * NSL : 16},
         {(void**)&w.tr2d, m->is2d ? sizeof(float) * cap * (w.Npad / KB) * 3 * NSL * KB : 16},
         {(void**)&w.trmax2d, m->is2d ? sizeof(unsigned) * cap * NSL : 16},
+        {(void**)&w.alpha2d, m->is2d ? sizeof(float2) * cap * 4 * KMAX : 16},
+        {(void**)&w.qcls2d, m->is2d ? sizeof(float2) * cap * NSL * KMAX : 16},
+        {(void**)&w.wcls2d, m->is2d ? sizeof(float2) * cap * m->ncs2d * w.Npad : 16},
         {(void**)&w.y2d, m->is2d ? sizeof(float) * cap * (w.Mpad / KB) * 3 * NSL * KB : 16},
         {(void**)&w.w2d, m->is2d ? sizeof(float) * cap * ((m->nwmax + KB - 1) / KB) * 2 * NSL * KB : 16},
         {(void**)&w.wt2d, m->is2d ? sizeof(float) * cap * (w.Mpad / KB) * 2 * NSL * KB : 16},
@@ -559,6 +610,9 @@ extern "C" int bx_model_create_estimators(const bx_model_desc* descs, int n_data
     if (st) return st;
     return model_create(descs, n_data * n_est, opts, cuda_stream, n_est, out);
 }
+
+int bx_fwd_tile_variants(const bx_model* m) { return m->precision == BX_FP32 && !m->is2d ? 2 : 1; }
+void bx_set_fwd_tile(bx_model* m, int variant) { m->w.fwd_wpc = variant == 1 ? 1 : 2; }
 
 int bx_public_P(const bx_model* m, int t) { return m->toys_h[(size_t)t * m->n_est].P + 4 * (m->n_est - 1); }
 

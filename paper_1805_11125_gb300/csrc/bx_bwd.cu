@@ -14,7 +14,8 @@
 // partial gradient of (LY, a, b, c, kB), and dNLL/dr_k gets
 // sum_i s_k[i] (c_{vetoed,k} rho_vetoed[i] + c_{tagged,k} rho_tagged[i]).
 //   k_bwd_f64: exact bin mass from erfc tails and exact derivatives -(phi(z_b) - phi(z_a))/sigma,
-//              -(z_b phi(z_b) - z_a phi(z_a))/sigma, FP64 throughout.
+//              -(z_b phi(z_b) - z_a phi(z_a))/sigma, FP64 throughout (with a Gram-Charlier
+//              response its CDF and density in place of Phi and phi).
 //   k_bwd_f32: the same integrals by the forward pass's 3-point Gauss-Legendre rule
 //              (integrands phi, t phi, (t^2 - 1) phi) in round-to-nearest FP32, down each
 //              column by the row recurrence of bx_resp.cuh (adj_run), column sums
@@ -129,11 +130,16 @@ __global__ void __launch_bounds__(BCOLS) k_bwd_f64(Work w) {
     double ta = 0.0, pa = 0.0, zpa = 0.0;
     bool fa = false;
     const double inv_sig = 1.0 / cc.sig;
+    const bool gc = T.gc1 != 0.0 || T.gc2 != 0.0;
     auto edge = [&](int e, double& t, double& p, double& zp, bool& f) {
         const double z = ((double)e * T.w - cc.mu) * inv_sig;
         f = z >= 0.0;
         t = f ? -0.5 * erfc(z * 0.70710678118654752440) : 0.5 * erfc(-z * 0.70710678118654752440);
         p = INV_SQRT_2PI * exp(-0.5 * z * z);
+        if (gc) {   // Gram-Charlier: CDF Phi - phi C, density phi (1 + gc1 He3 + gc2 He4)
+            t -= gc_cdf_term(T, z);
+            p *= gc_density_factor(T, z);
+        }
         zp = z * p;
     };
     if (ok && r0 < r1) edge(r0, ta, pa, zpa, fa);

@@ -77,7 +77,7 @@ constexpr double HSIG_FP32 = 1.0;
 // accept a point from which the fit runs onto the bounds: a 5%-off start of the small joint
 // model walked the resolution term b to 25 times its value with four parameters held at bounds.
 // Near the optimum every step is well inside the region (a few standard deviations at most).
-constexpr double TR_REL = 0.5, TR_SIG = 2.0;
+constexpr double TR_REL = 2.0, TR_SIG = 10.0;
 
 struct FitCtl {
     int phase, iters, evals, status, max_evals, fails, n_bound;
@@ -86,8 +86,8 @@ struct FitCtl {
 
 struct FitDev {
     int n, P, S;
-    const int* Pf;          // per fit: parameters of its dataset's row (K_t + 7 + 4 (E - 1))
-    const int* Kf;          // per fit: rates (K_t), the parameters before the trust-region ones
+    int* Pf;                // per fit: parameters of its dataset's row (K_t + 7 + 4 (E - 1))
+    int* Kf;                // per fit: rates (K_t), the parameters before the trust-region ones
     double *theta, *g, *f;  // accepted state per fit
     double *H, *V, *d;      // per fit
     double *lo, *hi;        // per fit
@@ -96,6 +96,31 @@ struct FitDev {
     unsigned char* skip;    // per slot
     FitCtl* ctl;
     int* active;
+    // the work queue: run->n_fits fits wait, F.n slot blocks hold the fits in flight
+    int E;                  // energy estimators per dataset (internal items per slot item)
+    int* slot_fit;          // per slot block: the queued fit it holds, -1 idle
+    int* next_fit;          // queue head
+    const double *q_theta0, *q_lo, *q_hi;   // per queued fit [n_fits][P]
+    const unsigned char* q_fr;              // [n_fits][P]
+    const int *q_Pf, *q_Kf, *q_toy;         // [n_fits]
+    const FitCtl* q_ctl0;                   // [n_fits]: initial state
+    double *o_theta, *o_f;                  // results [n_fits][P], [n_fits]
+    FitCtl* o_ctl;                          // [n_fits]
+    int* toy_of;                            // the evaluation items' toys (internal items: slot item x E + e)
+    // the persistent loop: rounds run, the loop's clock, the graph's loop handle
+    int* rounds;
+    unsigned long long* t0;
+    int* timed_out;
+    struct FitRun* run;                     // this call's parameters (read by the captured kernels)
+    cudaGraphConditionalHandle handle;
+};
+
+// Parameters of one bx_fit call, in device memory so that one captured graph serves every call.
+struct FitRun {
+    int n_fits;                 // fits in the queue
+    int max_rounds;             // evaluation-round budget of the batch
+    unsigned long long budget_ns;   // device-clock budget of the batch
+    double* o_V;                // [n_fits][P][P] covariance out, or nullptr
 };
 
 #define IDX(i, j) ((i) * P + (j))
@@ -152,9 +177,84 @@ __device__ double damped_inverse(const double* H, const unsigned char* act, int 
     return -1.0;
 }
 
-__global__ void k_fit(FitDev F) {
+// Put queued fit qf into slot block jf: its start in slot 0 (to be evaluated next round), its
+// bounds, free flags and state, its dataset on the slot's evaluation items.
+__device__ void slot_load(const FitDev& F, int jf, int qf) {
+    const int P = F.P, S = F.S;
+    const size_t s0 = (size_t)jf * S;
+    F.slot_fit[jf] = qf;
+    for (int i = 0; i < P; ++i) {
+        F.tt[s0 * P + i] = F.q_theta0[(size_t)qf * P + i];
+        F.lo[(size_t)jf * P + i] = F.q_lo[(size_t)qf * P + i];
+        F.hi[(size_t)jf * P + i] = F.q_hi[(size_t)qf * P + i];
+        F.fr[(size_t)jf * P + i] = F.q_fr[(size_t)qf * P + i];
+    }
+    for (int i = 0; i < P * P; ++i) F.H[(size_t)jf * P * P + i] = 0.0;
+    F.Pf[jf] = F.q_Pf[qf];
+    F.Kf[jf] = F.q_Kf[qf];
+    F.ctl[jf] = F.q_ctl0[qf];
+    const int toy = F.q_toy[qf];
+    for (int k = 0; k < S; ++k) {
+        F.skip[s0 + k] = k == 0 ? 0 : 1;
+        for (int e = 0; e < F.E; ++e) F.toy_of[(s0 + k) * F.E + e] = toy * F.E + e;
+    }
+}
+
+// A finished fit's result leaves its slot block: theta (its start beyond the fit's own P, where
+// the slot may hold a longer fit's values) and, when asked for, the covariance.
+__device__ void slot_store(const FitDev& F, int jf, const FitCtl& c) {
+    const int P = F.P, qf = F.slot_fit[jf], Pt = F.Pf[jf];
+    for (int i = 0; i < P; ++i)
+        F.o_theta[(size_t)qf * P + i] = i < Pt ? F.theta[(size_t)jf * P + i] : F.q_theta0[(size_t)qf * P + i];
+    F.o_f[qf] = F.f[jf];
+    F.o_ctl[qf] = c;
+    double* oV = F.run->o_V;
+    if (oV) {
+        const double* V = F.V + (size_t)jf * P * P;
+        for (int i = 0; i < P; ++i)
+            for (int j = 0; j < P; ++j) oV[(size_t)qf * P * P + IDX(i, j)] = (i < Pt && j < Pt) ? V[IDX(i, j)] : 0.0;
+    }
+}
+
+// Fill every slot block from the queue (before the first round).
+__global__ void k_fit_init(FitDev F) {
     const int jf = blockIdx.x * blockDim.x + threadIdx.x;
     if (jf >= F.n) return;
+    const int qf = atomicAdd(F.next_fit, 1);
+    if (qf < F.run->n_fits) {
+        slot_load(F, jf, qf);
+    } else {
+        F.slot_fit[jf] = -1;
+        for (int k = 0; k < F.S; ++k) F.skip[(size_t)jf * F.S + k] = 1;
+    }
+}
+
+// For the autotuner: every slot of a block evaluates the block's start point (a full round).
+__global__ void k_fit_tune_fill(FitDev F) {
+    const int jf = blockIdx.x, k = threadIdx.x;   // block = slot block, thread = slot
+    if (jf >= F.n || k >= F.S || F.slot_fit[jf] < 0) return;
+    const size_t s0 = (size_t)jf * F.S;
+    for (int i = 0; i < F.P; ++i) F.tt[(s0 + k) * F.P + i] = F.tt[s0 * F.P + i];
+    F.skip[s0 + k] = 0;
+}
+
+// The loop's clock starts with its first round.
+__global__ void k_fit_clock(FitDev F) {
+    if (*F.t0 == 0ull) *F.t0 = globaltimer();
+}
+
+// End of a loop body: continue while a fit is active, within the round and time budgets.
+__global__ void k_fit_ctl(FitDev F) {
+    const int r = ++*F.rounds;
+    const bool more = *F.active > 0 && r < F.run->max_rounds;
+    const bool late = globaltimer() - *F.t0 > F.run->budget_ns;
+    if (more && late) *F.timed_out = 1;
+    cudaGraphSetConditional(F.handle, more && !late ? 1u : 0u);
+}
+
+__global__ void k_fit(FitDev F) {
+    const int jf = blockIdx.x * blockDim.x + threadIdx.x;
+    if (jf >= F.n || F.slot_fit[jf] < 0) return;
     const int P = F.P, S = F.S;
     FitCtl c = F.ctl[jf];
     if (c.phase == PH_DONE) return;
@@ -292,8 +392,19 @@ __global__ void k_fit(FitDev F) {
         if (a == 0) { c.status = BX_OK; c.edm = 0.0; }
     }
     if (c.phase != PH_DONE && c.evals >= c.max_evals) { c.phase = PH_DONE; c.status = BX_ENOTCONV; }
-    if (c.phase == PH_DONE) for (int k = 0; k < S; ++k) F.skip[s0 + k] = 1;
-    else atomicAdd(F.active, 1);
+    if (c.phase == PH_DONE) {   // result out, the next queued fit in
+        slot_store(F, jf, c);
+        const int qf = atomicAdd(F.next_fit, 1);
+        if (qf < F.run->n_fits) {
+            slot_load(F, jf, qf);
+            atomicAdd(F.active, 1);
+        } else {
+            F.slot_fit[jf] = -1;
+            for (int k = 0; k < S; ++k) F.skip[s0 + k] = 1;
+        }
+        return;
+    }
+    atomicAdd(F.active, 1);
     F.ctl[jf] = c;
 }
 
@@ -302,11 +413,16 @@ __global__ void k_fit(FitDev F) {
 struct FitState {
     int cap_fits = 0, P = 0, S = 0;
     FitDev dev{};
-    int* active_h = nullptr;   // pinned
     cudaStream_t fs = nullptr;
     cudaGraphExec_t graph = nullptr;
-    int graph_n = -1, graph_ipl = -1;
-    std::vector<void*> allocs;
+    int graph_F = -1, graph_ipl = -1;
+    cudaGraphConditionalHandle handle = 0;
+    size_t q_cap = 0, v_cap = 0;             // queued fits the queue buffers hold (v: with covariance)
+    double* o_V = nullptr;                   // covariance out [v_cap][P][P]
+    std::vector<void*> allocs, q_allocs;
+    int tuned_F = 0, tuned_tile = -1;        // wave shape and forward tile chosen by the autotuner
+    double tuned_evals_per_s = 0.0;
+    bx_fit_plan plan{};
 };
 
 void bx_fit_free(bx_model* m) {
@@ -314,8 +430,8 @@ void bx_fit_free(bx_model* m) {
     FitState* s = m->fit;
     if (s->graph) cudaGraphExecDestroy(s->graph);
     if (s->fs) cudaStreamDestroy(s->fs);
-    if (s->active_h) cudaFreeHost(s->active_h);
     for (void* p : s->allocs) cudaFree(p);
+    for (void* p : s->q_allocs) cudaFree(p);
     delete s;
     m->fit = nullptr;
 }
@@ -342,61 +458,178 @@ static int fit_alloc(bx_model* m) {
         {(void**)&D.tt, ns * P * 8},   {(void**)&D.ft, ns * 8},        {(void**)&D.gt, ns * P * 8},
         {(void**)&D.skip, ns},         {(void**)&D.ctl, n * sizeof(FitCtl)}, {(void**)&D.active, 16},
         {(void**)&D.Pf, n * sizeof(int)},     {(void**)&D.Kf, n * sizeof(int)},
+        {(void**)&D.slot_fit, n * sizeof(int)}, {(void**)&D.next_fit, 16}, {(void**)&D.rounds, 16},
+        {(void**)&D.t0, 16}, {(void**)&D.timed_out, 16}, {(void**)&D.run, sizeof(FitRun)},
     };
     for (auto& a : plan) {
         CUF(cudaMalloc(a.p, a.bytes));
         s->allocs.push_back(*a.p);
     }
-    CUF(cudaHostAlloc((void**)&s->active_h, sizeof(int), cudaHostAllocDefault));
     CUF(cudaStreamCreateWithFlags(&s->fs, cudaStreamNonBlocking));
     D.P = s->P;
     D.S = s->S;
+    D.E = m->n_est;
+    D.toy_of = const_cast<int*>(m->w.toy_of);
     return BX_OK;
 }
 
-// Capture `ipl` iterations (evaluation of every slot in use + k_fit) into a graph.
-static int fit_capture(bx_model* m, int n, int ipl) {
+// Queue buffers for n fits (grown on demand; a new set of pointers invalidates the graph).
+static int queue_alloc(bx_model* m, size_t n, bool cov) {
     FitState* s = m->fit;
-    if (s->graph && s->graph_n == n && s->graph_ipl == ipl) return BX_OK;
+    if (n <= s->q_cap && (!cov || n <= s->v_cap)) return BX_OK;
+    for (void* p : s->q_allocs) cudaFree(p);
+    s->q_allocs.clear();
+    const size_t P = s->P, cap = std::max(n, s->q_cap);
+    FitDev& D = s->dev;
+    struct A { void** p; size_t bytes; } plan[] = {
+        {(void**)&D.q_theta0, cap * P * 8}, {(void**)&D.q_lo, cap * P * 8}, {(void**)&D.q_hi, cap * P * 8},
+        {(void**)&D.q_fr, cap * P},         {(void**)&D.q_Pf, cap * 4},     {(void**)&D.q_Kf, cap * 4},
+        {(void**)&D.q_toy, cap * 4},        {(void**)&D.q_ctl0, cap * sizeof(FitCtl)},
+        {(void**)&D.o_theta, cap * P * 8},  {(void**)&D.o_f, cap * 8},      {(void**)&D.o_ctl, cap * sizeof(FitCtl)},
+        {(void**)&s->o_V, cov ? cap * P * P * 8 : 16},
+    };
+    for (auto& a : plan) {
+        CUF(cudaMalloc(a.p, a.bytes));
+        s->q_allocs.push_back(*a.p);
+    }
+    s->q_cap = cap;
+    s->v_cap = cov ? cap : 0;
     if (s->graph) {
         cudaGraphExecDestroy(s->graph);
         s->graph = nullptr;
     }
+    return BX_OK;
+}
+
+// The persistent batch: one graph whose conditional while node repeats the body
+//   k_fit_clock, ipl x {evaluate the F slot blocks (F S items), k_fit}, k_fit_ctl
+// until k_fit_ctl clears the loop condition (no fit active, or a budget spent); the active count
+// is cleared before the body's last k_fit, which counts the fits still running.
+static int fit_capture(bx_model* m, int F, int ipl) {
+    FitState* s = m->fit;
+    if (s->graph && s->graph_F == F && s->graph_ipl == ipl) return BX_OK;
+    if (s->graph) {
+        cudaGraphExecDestroy(s->graph);
+        s->graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    CUF(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault);
+    cudaGraphNode_t node;
+    cudaGraphNodeParams cp{};
+    if (e == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+    }
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return bx_set_error(BX_ECUDA, "bx_fit: conditional graph node: %s", cudaGetErrorString(e));
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    FitDev D = s->dev;
+    D.n = F;
+    D.handle = h;
+    s->dev.handle = h;
     cudaStream_t saved = m->stream;
     const int prof = m->prof_on;
     const unsigned char* saved_skip = m->w.skip;
     m->prof_on = 0;
     m->stream = s->fs;
     m->w.skip = s->dev.skip;
-    FitDev D = s->dev;
-    D.n = n;
-    const int items = n * s->S;
-    cudaGraph_t g = nullptr;
     int st = BX_OK;
-    cudaError_t e = cudaStreamBeginCapture(s->fs, cudaStreamCaptureModeRelaxed);
+    e = cudaStreamBeginCaptureToGraph(s->fs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        k_fit_clock<<<1, 1, 0, s->fs>>>(D);
+        e = cudaGetLastError();
+    }
     for (int it = 0; it < ipl && e == cudaSuccess && st == BX_OK; ++it) {
         if (it == ipl - 1) e = cudaMemsetAsync(D.active, 0, sizeof(int), s->fs);
         if (e != cudaSuccess) break;
-        st = bx_enqueue_eval(m, items, D.tt, s->P, 1, 0, D.ft, D.gt);
+        st = bx_enqueue_eval(m, F * s->S, D.tt, s->P, 1, 0, D.ft, D.gt);
         if (st) break;
-        k_fit<<<(n + 63) / 64, 64, 0, s->fs>>>(D);
+        k_fit<<<(F + 63) / 64, 64, 0, s->fs>>>(D);
         e = cudaGetLastError();
     }
-    cudaError_t e2 = cudaStreamEndCapture(s->fs, &g);
+    if (e == cudaSuccess && st == BX_OK) {
+        k_fit_ctl<<<1, 1, 0, s->fs>>>(D);
+        e = cudaGetLastError();
+    }
+    cudaGraph_t captured = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(s->fs, &captured);
     m->stream = saved;
     m->prof_on = prof;
     m->w.skip = saved_skip;
     if (st) {
-        if (g) cudaGraphDestroy(g);
+        cudaGraphDestroy(g);
         return st;
     }
     if (e == cudaSuccess) e = e2;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&s->graph, g, 0);
-    if (g) cudaGraphDestroy(g);
+    cudaGraphDestroy(g);
     if (e != cudaSuccess) return bx_set_error(BX_ECUDA, "bx_fit: graph capture: %s", cudaGetErrorString(e));
-    s->graph_n = n;
+    s->graph_F = F;
     s->graph_ipl = ipl;
     return BX_OK;
+}
+
+// The autotuner: with the slot blocks loaded (k_fit_init), time one evaluation round of the
+// first F blocks for F = the largest whole multiple of the GPU's SM count in evaluation items
+// and its halves, and each forward tile shape of the model; keep the fastest tile shape and the
+// smallest F within 10% of the best throughput (fewer fits in flight: shorter rounds for the
+// last fits of the queue).  Returns the chosen F.
+static int fit_autotune(bx_model* m, int Fmax) {
+    FitState* s = m->fit;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    std::vector<int> cand;
+    for (int F = Fmax; F >= 1 && (int)cand.size() < 5; F /= 2) cand.push_back(F);
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return Fmax;
+    cudaStream_t saved = m->stream;
+    const unsigned char* saved_skip = m->w.skip;
+    m->stream = s->fs;
+    m->w.skip = s->dev.skip;
+    const int n_tiles = bx_fwd_tile_variants(m);
+    double best = 0.0;
+    int best_tile = 0;
+    std::vector<double> thr(cand.size(), 0.0);
+    for (int tv = 0; tv < n_tiles; ++tv) {
+        bx_set_fwd_tile(m, tv);
+        for (size_t c = 0; c < cand.size(); ++c) {
+            const int items = cand[c] * s->S;
+            float ms = 0.f, t = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {   // first call warms up
+                cudaEventRecord(a, s->fs);
+                bx_enqueue_eval(m, items, s->dev.tt, s->P, 1, 0, s->dev.ft, s->dev.gt);
+                cudaEventRecord(b, s->fs);
+                cudaEventSynchronize(b);
+                cudaEventElapsedTime(&ms, a, b);
+                if (rep > 0) t = std::min(t, ms);
+            }
+            const double v = items / (t / 1e3);
+            if (v > best) { best = v; best_tile = tv; }
+            if (tv == 0 || v > thr[c]) thr[c] = v;
+        }
+    }
+    bx_set_fwd_tile(m, best_tile);
+    m->stream = saved;
+    m->w.skip = saved_skip;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    int F = cand[0];
+    const double top = *std::max_element(thr.begin(), thr.end());
+    for (size_t c = 0; c < cand.size(); ++c)
+        if (thr[c] >= 0.9 * top) F = cand[c];   // candidates descend: the last one that qualifies is the smallest
+    s->tuned_F = F;
+    s->tuned_tile = best_tile;
+    s->tuned_evals_per_s = best;
+    (void)sms;
+    return F;
 }
 
 extern "C" int bx_fit(bx_model* m, int n, const int* toy_idx, const double* theta0, const bx_fit_opts* opts,
@@ -408,31 +641,31 @@ extern "C" int bx_fit(bx_model* m, int n, const int* toy_idx, const double* thet
     if (o.tol_edm == 0.0) o.tol_edm = 1e-8;
     if (o.max_iter == 0) o.max_iter = 5000;
     if (o.iters_per_launch == 0) o.iters_per_launch = 4;
-    if (!(o.tol_edm > 0.0) || o.max_iter < 1 || o.iters_per_launch < 1 || o.iters_per_launch > 256)
+    if (o.time_budget_s == 0.0) o.time_budget_s = 300.0;
+    if (!(o.tol_edm > 0.0) || o.max_iter < 1 || o.iters_per_launch < 1 || o.iters_per_launch > 256 ||
+        !(o.time_budget_s > 0.0) || o.fits_in_flight < 0)
         return bx_set_error(BX_EINVAL, "bx_fit: invalid options");
     const int P = m->P, S = NLS + 2 * P, Kmax = m->Kmax;
-    if (n < 1 || (long long)n * S > m->cap)
-        return bx_set_error(BX_EINVAL, "bx_fit: %d fits need max_batch >= %lld (%d evaluation slots per fit)", n,
-                            (long long)n * S, S);
+    if (n < 1) return bx_set_error(BX_EINVAL, "bx_fit: n = %d", n);
+    if (m->cap < S) return bx_set_error(BX_EINVAL, "bx_fit: max_batch >= %d needed (%d evaluation slots per fit)", S, S);
     for (int j = 0; j < n; ++j)
         if (toy_idx && (toy_idx[j] < 0 || toy_idx[j] >= m->n_data))
             return bx_set_error(BX_EINVAL, "bx_fit: toy_idx[%d] out of range", j);
-    std::vector<int> slot_toy((size_t)n * S);
-    for (int j = 0; j < n; ++j)
-        for (int k = 0; k < S; ++k) slot_toy[(size_t)j * S + k] = toy_idx ? toy_idx[j] : 0;
-    int st = bx_set_items(m, n * S, slot_toy.data());
-    if (st) return st;
+    int st;
     if ((st = fit_alloc(m))) return st;
     FitState* s = m->fit;
-    // per-fit bounds and free flags in each fit's own layout
-    std::vector<double> lo((size_t)n * P, -INFINITY), hi((size_t)n * P, INFINITY), th((size_t)n * S * P, 0.0);
-    std::vector<unsigned char> fr((size_t)n * P, 0), skip((size_t)n * S, 1);
+    if ((st = queue_alloc(m, (size_t)n, o.cov_out != nullptr))) return st;
+    // per-fit start, bounds, free flags and state in each fit's own layout
+    std::vector<double> lo((size_t)n * P, -INFINITY), hi((size_t)n * P, INFINITY), th((size_t)n * P, 0.0);
+    std::vector<unsigned char> fr((size_t)n * P, 0);
     std::vector<FitCtl> ctl(n);
-    std::vector<int> Pf(n), Kf(n);
+    std::vector<int> Pf(n), Kf(n), toy(n);
     const double hrel = m->precision == BX_FP64 ? 1e-3 : 1e-2;   // FD step of the Hessian
+    const bool f64 = m->precision == BX_FP64;
     for (int j = 0; j < n; ++j) {
         const int t = toy_idx ? toy_idx[j] : 0;
         const Toy& T = m->toys_h[(size_t)t * m->n_est];   // estimator 0 of the dataset
+        toy[j] = t;
         Pf[j] = bx_public_P(m, t);
         Kf[j] = T.K;
         for (int p = 0; p < Pf[j]; ++p) {
@@ -460,59 +693,124 @@ extern "C" int bx_fit(bx_model* m, int n, const int* toy_idx, const double* thet
             lo[(size_t)j * P + p] = l;
             hi[(size_t)j * P + p] = h;
             fr[(size_t)j * P + p] = f;
-            th[(size_t)j * S * P + p] = std::min(std::max(x, l), h);   // slot 0: the start
+            th[(size_t)j * P + p] = std::min(std::max(x, l), h);
         }
-        skip[(size_t)j * S] = 0;
-        const bool f64 = m->precision == BX_FP64;
         ctl[j] = FitCtl{PH_START, 0, 1, BX_ENOTCONV, o.max_iter, 0, 0, INFINITY, INFINITY,
                         f64 ? o.tol_edm : std::max(o.tol_edm, EDM_FLOOR_FP32), 0.0, 0.0, hrel,
                         f64 ? MU_CONV_FP64 : MU_CONV_FP32, f64 ? 0.0 : HSIG_FP32, 0.0};
     }
     FitDev& D = s->dev;
-    CUF(cudaStreamSynchronize(m->stream));   // slot composition uploaded on the model stream
-    CUF(cudaMemcpyAsync(D.tt, th.data(), th.size() * 8, cudaMemcpyHostToDevice, s->fs));
-    CUF(cudaMemcpyAsync(D.lo, lo.data(), lo.size() * 8, cudaMemcpyHostToDevice, s->fs));
-    CUF(cudaMemcpyAsync(D.hi, hi.data(), hi.size() * 8, cudaMemcpyHostToDevice, s->fs));
-    CUF(cudaMemcpyAsync(D.fr, fr.data(), fr.size(), cudaMemcpyHostToDevice, s->fs));
-    CUF(cudaMemcpyAsync(D.skip, skip.data(), skip.size(), cudaMemcpyHostToDevice, s->fs));
-    CUF(cudaMemcpyAsync(D.ctl, ctl.data(), ctl.size() * sizeof(FitCtl), cudaMemcpyHostToDevice, s->fs));
-    CUF(cudaMemcpyAsync((void*)D.Pf, Pf.data(), Pf.size() * sizeof(int), cudaMemcpyHostToDevice, s->fs));
-    CUF(cudaMemcpyAsync((void*)D.Kf, Kf.data(), Kf.size() * sizeof(int), cudaMemcpyHostToDevice, s->fs));
-    CUF(cudaMemsetAsync(D.H, 0, (size_t)n * P * P * 8, s->fs));
-    CUF(cudaStreamSynchronize(s->fs));
-    if ((st = fit_capture(m, n, o.iters_per_launch))) return st;
-    // a Newton iteration takes two evaluation rounds; the budget is in evaluation slots
-    const int max_rounds = 2 * (o.max_iter / (2 * (P > 0 ? P : 1)) + 8) + 64;
-    int rounds = 0;
-    for (;;) {
-        CUF(cudaGraphLaunch(s->graph, s->fs));
-        CUF(cudaMemcpyAsync(s->active_h, D.active, sizeof(int), cudaMemcpyDeviceToHost, s->fs));
-        CUF(cudaStreamSynchronize(s->fs));
-        rounds += o.iters_per_launch;
-        if (*s->active_h == 0 || rounds >= max_rounds) break;
+    CUF(cudaStreamSynchronize(m->stream));   // nothing of the model stream still reads the items' toys
+    CUF(cudaMemcpyAsync((void*)D.q_theta0, th.data(), th.size() * 8, cudaMemcpyHostToDevice, s->fs));
+    CUF(cudaMemcpyAsync((void*)D.q_lo, lo.data(), lo.size() * 8, cudaMemcpyHostToDevice, s->fs));
+    CUF(cudaMemcpyAsync((void*)D.q_hi, hi.data(), hi.size() * 8, cudaMemcpyHostToDevice, s->fs));
+    CUF(cudaMemcpyAsync((void*)D.q_fr, fr.data(), fr.size(), cudaMemcpyHostToDevice, s->fs));
+    CUF(cudaMemcpyAsync((void*)D.q_Pf, Pf.data(), Pf.size() * 4, cudaMemcpyHostToDevice, s->fs));
+    CUF(cudaMemcpyAsync((void*)D.q_Kf, Kf.data(), Kf.size() * 4, cudaMemcpyHostToDevice, s->fs));
+    CUF(cudaMemcpyAsync((void*)D.q_toy, toy.data(), toy.size() * 4, cudaMemcpyHostToDevice, s->fs));
+    CUF(cudaMemcpyAsync((void*)D.q_ctl0, ctl.data(), ctl.size() * sizeof(FitCtl), cudaMemcpyHostToDevice, s->fs));
+
+    // fits in flight: the caller's choice, else the autotuner's (measured once per model and batch size)
+    const int Fmax = std::min(s->cap_fits, n);
+    int F = o.fits_in_flight > 0 ? std::min(o.fits_in_flight, Fmax) : 0;
+    {   // n_fits for k_fit_init; the budgets follow once F is known
+        FitRun pre{n, 0, 0ull, nullptr};
+        CUF(cudaMemcpyAsync(D.run, &pre, sizeof pre, cudaMemcpyHostToDevice, s->fs));
     }
+    auto load = [&](int nslots) -> int {
+        D.n = nslots;
+        CUF(cudaMemsetAsync(D.next_fit, 0, sizeof(int), s->fs));
+        k_fit_init<<<(nslots + 63) / 64, 64, 0, s->fs>>>(D);
+        CUF(cudaGetLastError());
+        return BX_OK;
+    };
+    if (F == 0) {
+        if (s->tuned_F > 0 && s->tuned_F <= Fmax && s->plan.fits == n) {
+            F = s->tuned_F;
+        } else {
+            if ((st = load(Fmax))) return st;
+            k_fit_tune_fill<<<Fmax, std::max(32, (S + 31) / 32 * 32), 0, s->fs>>>(D);
+            CUF(cudaGetLastError());
+            CUF(cudaStreamSynchronize(s->fs));
+            F = fit_autotune(m, Fmax);
+        }
+    }
+    if ((st = load(F))) return st;
+    CUF(cudaMemsetAsync(D.rounds, 0, sizeof(int), s->fs));
+    CUF(cudaMemsetAsync(D.t0, 0, sizeof(unsigned long long), s->fs));
+    CUF(cudaMemsetAsync(D.timed_out, 0, sizeof(int), s->fs));
+    // a Newton iteration takes two evaluation rounds; the budget is in evaluation slots, and the
+    // queue adds the rounds of its later fits
+    FitRun run{n, (2 * (o.max_iter / (2 * (P > 0 ? P : 1)) + 8) + 64) * ((n + F - 1) / F),
+               (unsigned long long)(o.time_budget_s * 1e9), o.cov_out ? s->o_V : nullptr};
+    CUF(cudaMemcpyAsync(D.run, &run, sizeof run, cudaMemcpyHostToDevice, s->fs));
+    m->toy_cached.assign(m->toy_cached.size(), -1);   // the device now sets the items' toys
+    if ((st = fit_capture(m, F, o.iters_per_launch))) return st;
+    CUF(cudaGraphLaunch(s->graph, s->fs));
+    CUF(cudaStreamSynchronize(s->fs));
     unsigned err = 0;
     CUF(cudaMemcpy(&err, m->w.err, sizeof err, cudaMemcpyDeviceToHost));
     if (err) {
         CUF(cudaMemset(m->w.err, 0, sizeof(unsigned)));
         return bx_set_error(BX_ETIMEOUT, "bx_fit: a device-side wait exceeded its time budget");
     }
+    int rounds = 0, timed_out = 0, next = 0;
+    std::vector<int> slot_fit(F);
+    CUF(cudaMemcpy(&rounds, D.rounds, sizeof(int), cudaMemcpyDeviceToHost));
+    CUF(cudaMemcpy(&timed_out, D.timed_out, sizeof(int), cudaMemcpyDeviceToHost));
+    CUF(cudaMemcpy(&next, D.next_fit, sizeof(int), cudaMemcpyDeviceToHost));
+    CUF(cudaMemcpy(slot_fit.data(), D.slot_fit, F * sizeof(int), cudaMemcpyDeviceToHost));
+    // fits still in their slots when the loop stopped (a budget spent): their current state
     std::vector<double> f(n);
-    CUF(cudaMemcpy(theta_out, D.theta, (size_t)n * P * 8, cudaMemcpyDeviceToHost));
-    CUF(cudaMemcpy(f.data(), D.f, (size_t)n * 8, cudaMemcpyDeviceToHost));
-    CUF(cudaMemcpy(ctl.data(), D.ctl, ctl.size() * sizeof(FitCtl), cudaMemcpyDeviceToHost));
+    std::vector<FitCtl> oc(n);
+    CUF(cudaMemcpy(theta_out, D.o_theta, (size_t)n * P * 8, cudaMemcpyDeviceToHost));
+    CUF(cudaMemcpy(f.data(), D.o_f, (size_t)n * 8, cudaMemcpyDeviceToHost));
+    CUF(cudaMemcpy(oc.data(), D.o_ctl, (size_t)n * sizeof(FitCtl), cudaMemcpyDeviceToHost));
+    std::vector<char> finished(n, 0), running(n, 0);
+    for (int j = 0; j < std::min(next, n); ++j) finished[j] = 1;
+    for (int jf = 0; jf < F; ++jf)
+        if (slot_fit[jf] >= 0) {
+            const int qf = slot_fit[jf];
+            finished[qf] = 0;
+            running[qf] = 1;
+            CUF(cudaMemcpy(theta_out + (size_t)qf * P, D.theta + (size_t)jf * P, P * 8, cudaMemcpyDeviceToHost));
+            CUF(cudaMemcpy(&f[qf], D.f + jf, 8, cudaMemcpyDeviceToHost));
+            CUF(cudaMemcpy(&oc[qf], D.ctl + jf, sizeof(FitCtl), cudaMemcpyDeviceToHost));
+        }
     int worst = BX_OK;
     for (int j = 0; j < n; ++j) {
+        const bool started = finished[j] || running[j];
+        if (!started) {   // never left the queue
+            for (int p = 0; p < P; ++p) theta_out[(size_t)j * P + p] = th[(size_t)j * P + p];
+            oc[j] = ctl[j];
+            f[j] = INFINITY;
+        }
         res[j].nll = f[j];
-        res[j].edm = ctl[j].edm;
-        res[j].iters = ctl[j].iters;
-        res[j].n_evals = ctl[j].evals;
-        res[j].status = ctl[j].phase == PH_DONE ? ctl[j].status : BX_ENOTCONV;
-        res[j].n_at_bound = ctl[j].n_bound;
-        res[j].damping = ctl[j].mu_fresh;
+        res[j].edm = oc[j].edm;
+        res[j].iters = oc[j].iters;
+        res[j].n_evals = started ? oc[j].evals : 0;
+        res[j].status = finished[j] && oc[j].phase == PH_DONE ? oc[j].status
+                        : timed_out                           ? BX_ETIMEOUT
+                                                              : BX_ENOTCONV;
+        res[j].n_at_bound = oc[j].n_bound;
+        res[j].damping = oc[j].mu_fresh;
         if (res[j].status != BX_OK && worst == BX_OK) worst = res[j].status;
     }
-    if (o.cov_out) CUF(cudaMemcpy(o.cov_out, D.V, (size_t)n * P * P * 8, cudaMemcpyDeviceToHost));
+    if (o.cov_out) {
+        CUF(cudaMemcpy(o.cov_out, s->o_V, (size_t)n * P * P * 8, cudaMemcpyDeviceToHost));
+        for (int jf = 0; jf < F; ++jf)
+            if (slot_fit[jf] >= 0)
+                CUF(cudaMemcpy(o.cov_out + (size_t)slot_fit[jf] * P * P, D.V + (size_t)jf * P * P, (size_t)P * P * 8,
+                               cudaMemcpyDeviceToHost));
+    }
+    s->plan = bx_fit_plan{n, F, S, o.iters_per_launch, 1, rounds, s->tuned_tile, s->tuned_evals_per_s};
     if (worst != BX_OK) bx_set_error(worst, "bx_fit: not every fit converged (see the per-fit status)");
     return worst;
+}
+
+extern "C" int bx_fit_last_plan(const bx_model* m, bx_fit_plan* out) {
+    if (!m || !out) return bx_set_error(BX_EINVAL, "NULL argument");
+    if (!m->fit) return bx_set_error(BX_EINVAL, "no fit has run on this model");
+    *out = m->fit->plan;
+    return BX_OK;
 }

@@ -43,10 +43,14 @@ __device__ __forceinline__ void kahan_fma(float& acc, float& cmp, float a, float
     acc = t;
 }
 
-template <bool TAG, bool COLS, bool MES>
-__global__ void __launch_bounds__(F32_THREADS) k_fwd_f32(Work w) {
+// WPC: warps per CTA, 2 (a CTA = one 128-row tile) or 1 (a CTA = one warp's 64-row half of a
+// tile; the autotuner of the batched fits may pick it for small ragged items).  The warps of a
+// CTA never synchronise, so the two shapes do the same work per warp.
+template <bool TAG, bool COLS, bool MES, int WPC = 2>
+__global__ void __launch_bounds__(32 * WPC, WPC == 2 ? 18 : 32) k_fwd_f32(Work w) {
     // 1D item-major grid (a y dimension would cap the batch at 65535 items)
-    const int tile = blockIdx.x % w.max_tiles, item = blockIdx.x / w.max_tiles, tid = threadIdx.x;
+    const int unit = WPC == 2 ? (int)blockIdx.x : (int)(blockIdx.x >> 1);
+    const int tile = unit % w.max_tiles, item = unit / w.max_tiles, tid = threadIdx.x;
     const Toy& T = w.toys[w.toy_of[item]];
     if (tile >= T.n_tiles || w.status[item]) return;
     const int m0 = tile * TM, M = T.M;
@@ -56,27 +60,28 @@ __global__ void __launch_bounds__(F32_THREADS) k_fwd_f32(Work w) {
     const ColG* colg = w.colg + cbase;
     const float4* colS = w.colS32 + cbase;
     const int2* colr = w.colr + cbase;
-    const int lane = tid & 31, q = tid >> 5, g = m0 + 64 * q;
+    const int lane = tid & 31, q = WPC == 2 ? tid >> 5 : (int)(blockIdx.x & 1), g = m0 + 64 * q;
+    const int qs = WPC == 2 ? q : 0;   // the warp's slot in the CTA's shared arrays
     // warp-private staging of 32 columns at a time (no block-wide barrier)
-    __shared__ float4 sC[2][FCH32];
-    __shared__ ColG sG[2][FCH32];
-    __shared__ float4 sS[2][FCH32];
+    __shared__ float4 sC[WPC][FCH32];
+    __shared__ ColG sG[WPC][FCH32];
+    __shared__ float4 sS[WPC][FCH32];
     // column sums: one slice -> R Gg of the lane's two rows added (32 values per column);
     // several slices (MES) -> R of each of the warp's 64 rows
     constexpr int CBR = MES ? 64 : 32;
-    __shared__ float colbuf[COLS ? 2 : 1][COLS ? CBR : 1][FCH32 + 1];
-    float(*cb)[FCH32 + 1] = colbuf[COLS ? q : 0];
+    __shared__ float colbuf[COLS ? WPC : 1][COLS ? CBR : 1][FCH32 + 1];
+    float(*cb)[FCH32 + 1] = colbuf[COLS ? qs : 0];
 
     const int ra = g + lane, rb = ra + 32;
     const float mfa = (float)ra, mfb = (float)rb;
     const float gga = (COLS && !MES && ra < M) ? (float)T.Gg[ra] : 0.f;
     const float ggb = (COLS && !MES && rb < M) ? (float)T.Gg[rb] : 0.f;
     const int NES = MES ? T.n_es : 1;
-    __shared__ float sGg[MES ? 2 : 1][MES ? MAX_ES : 1][MES ? 64 : 1];   // Gg_s of the warp's 64 rows
+    __shared__ float sGg[MES ? WPC : 1][MES ? MAX_ES : 1][MES ? 64 : 1];   // Gg_s of the warp's 64 rows
     if (MES)
         for (int s = 0; s < NES; ++s) {
-            sGg[q][s][lane] = ra < M ? T.Gg32[(size_t)s * M + ra] : 0.f;
-            sGg[q][s][lane + 32] = rb < M ? T.Gg32[(size_t)s * M + rb] : 0.f;
+            sGg[qs][s][lane] = ra < M ? T.Gg32[(size_t)s * M + ra] : 0.f;
+            sGg[qs][s][lane + 32] = rb < M ? T.Gg32[(size_t)s * M + rb] : 0.f;
         }
     float sa = 0.f, csa = 0.f, ta = 0.f, cta = 0.f, sb = 0.f, csb = 0.f, tb = 0.f, ctb = 0.f;
     float* apart = static_cast<float*>(w.apart) + (((size_t)item * w.max_tiles + tile) * 2 + q) * (MES ? w.nes : 1) * w.Npad;
@@ -120,9 +125,9 @@ __global__ void __launch_bounds__(F32_THREADS) k_fwd_f32(Work w) {
             const int i = c0 + lane;
             const float4 cfl = in ? colf[i] : make_float4(0.f, 0.f, 0.f, 0.f);
             const ColG cgl = in ? colg[i] : ColG{0.f, 0.f, 0.f, 0.f};
-            sC[q][lane] = cfl;
-            sG[q][lane] = cgl;
-            sS[q][lane] = in ? colS[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            sC[qs][lane] = cfl;
+            sG[qs][lane] = cgl;
+            sS[qs][lane] = in ? colS[i] : make_float4(0.f, 0.f, 0.f, 0.f);
             const int2 band = in ? colr[i] : make_int2(0, 0);
             const float t0 = fmaf((float)g - cfl.x, cfl.z, cfl.y), t1 = fmaf(63.0f, cfl.z, t0);
             mA = __ballot_sync(0xffffffffu, band.x < g + 32 && band.y > g);
@@ -133,9 +138,9 @@ __global__ void __launch_bounds__(F32_THREADS) k_fwd_f32(Work w) {
         const unsigned mAny = mA | mB;
         for (unsigned mr = mAny; mr; mr &= mr - 1u) {   // the columns whose band touches the warp
             const int c = __ffs(mr) - 1;
-            const float4 cf = sC[q][c];
-            const ColG cg = sG[q][c];
-            const float4 S = sS[q][c];
+            const float4 cf = sC[qs][c];
+            const ColG cg = sG[qs][c];
+            const float4 S = sS[qs][c];
             const bool inA = (mA >> c) & 1u, inB = (mB >> c) & 1u;
             float Ra = 0.f, Rb = 0.f;
             if ((mW >> c) & 1u) column(std::true_type{}, inA, inB, cf, cg, S, Ra, Rb);
@@ -154,7 +159,7 @@ __global__ void __launch_bounds__(F32_THREADS) k_fwd_f32(Work w) {
             float s = 0.f;
             if ((mAny >> lane) & 1u)
                 for (int j = 0; j < 32; ++j) s += cb[j][lane];
-            if (lane < ncol) apart[c0 + lane] = s * sG[q][lane].A;
+            if (lane < ncol) apart[c0 + lane] = s * sG[qs][lane].A;
             __syncwarp();
         }
         if (COLS && MES) {
@@ -166,12 +171,12 @@ __global__ void __launch_bounds__(F32_THREADS) k_fwd_f32(Work w) {
                     const float r = cb[j][lane];
 #pragma unroll
                     for (int e = 0; e < MAX_ES; ++e)
-                        if (e < NES) s[e] = fmaf(r, sGg[q][e][j], s[e]);
+                        if (e < NES) s[e] = fmaf(r, sGg[qs][e][j], s[e]);
                 }
             if (lane < ncol)
 #pragma unroll
                 for (int e = 0; e < MAX_ES; ++e)
-                    if (e < NES) apart[(size_t)e * w.Npad + c0 + lane] = s[e] * sG[q][lane].A;
+                    if (e < NES) apart[(size_t)e * w.Npad + c0 + lane] = s[e] * sG[qs][lane].A;
             __syncwarp();
         }
     }
@@ -203,15 +208,22 @@ __global__ void __launch_bounds__(F32_THREADS) k_fwd_f32(Work w) {
     }
 }
 
+template <int WPC>
+static void fwd_f32_variant(const Work& w, unsigned grid, int any_tag, int any_cols, bool mes, cudaStream_t s) {
+    const unsigned g = grid * (2 / WPC);
+    if (any_tag && any_cols && mes) k_fwd_f32<true, true, true, WPC><<<g, 32 * WPC, 0, s>>>(w);
+    else if (any_cols && mes) k_fwd_f32<false, true, true, WPC><<<g, 32 * WPC, 0, s>>>(w);
+    else if (any_tag && any_cols) k_fwd_f32<true, true, false, WPC><<<g, 32 * WPC, 0, s>>>(w);
+    else if (any_tag) k_fwd_f32<true, false, false, WPC><<<g, 32 * WPC, 0, s>>>(w);
+    else if (any_cols) k_fwd_f32<false, true, false, WPC><<<g, 32 * WPC, 0, s>>>(w);
+    else k_fwd_f32<false, false, false, WPC><<<g, 32 * WPC, 0, s>>>(w);
+}
+
 cudaError_t launch_fwd_f32(const Work& w, int n, int max_tiles, int any_tag, int any_cols, cudaStream_t s) {
     const unsigned grid = (unsigned)n * (unsigned)w.max_tiles;   // decoded with w.max_tiles
     const bool mes = w.nes > 1;   // several energy slices of the Eq. 4 terms
-    if (any_tag && any_cols && mes) k_fwd_f32<true, true, true><<<grid, F32_THREADS, 0, s>>>(w);
-    else if (any_cols && mes) k_fwd_f32<false, true, true><<<grid, F32_THREADS, 0, s>>>(w);
-    else if (any_tag && any_cols) k_fwd_f32<true, true, false><<<grid, F32_THREADS, 0, s>>>(w);
-    else if (any_tag) k_fwd_f32<true, false, false><<<grid, F32_THREADS, 0, s>>>(w);
-    else if (any_cols) k_fwd_f32<false, true, false><<<grid, F32_THREADS, 0, s>>>(w);
-    else k_fwd_f32<false, false, false><<<grid, F32_THREADS, 0, s>>>(w);
+    if (w.fwd_wpc == 1) fwd_f32_variant<1>(w, grid, any_tag, any_cols, mes, s);
+    else fwd_f32_variant<2>(w, grid, any_tag, any_cols, mes, s);
     return cudaGetLastError();
 }
 

@@ -7,7 +7,8 @@
 // FCH64 columns of the tile's band, phase 1 evaluates the Gaussian tail mass at the TM + 1
 // bin edges of each column (one erfc per edge, shared by the two bins it bounds); phase 2
 // forms R[m,i] = (Phi(z_{m+1}) - Phi(z_m)) / Phi(mu_i/sigma_i) from those tails without
-// cancellation and accumulates the row sums; the column sums go through shared memory.
+// cancellation and accumulates the row sums; the column sums go through shared memory.  With a
+// Gram-Charlier response every edge's tail takes the term -phi(z) C(z) of its CDF.
 #include <math.h>
 
 #include "bx_internal.cuh"
@@ -25,6 +26,7 @@ __global__ void __launch_bounds__(TM) k_fwd_f64(Work w) {
     const int m0 = tile * TM, M = T.M;
     const int NGRP = T.n_set > 1 ? T.n_set : 1;   // quenching groups: one column range each
     const size_t cbase = (size_t)item * w.Npad;
+    const bool gc = T.gc1 != 0.0 || T.gc2 != 0.0;
 
     // tails, column-major so that thread = edge reads consecutive words
     __shared__ double sT[FCH64 * (TM + 1)];
@@ -57,6 +59,7 @@ __global__ void __launch_bounds__(TM) k_fwd_f64(Work w) {
                 } else {
                     t = 0.5 * erfc(-z * 0.70710678118654752440);   // Phi(z)
                 }
+                if (gc) t -= gc_cdf_term(T, z);   // the Gram-Charlier CDF: Phi(z) - phi(z) C(z)
             }
             sT[j] = t;
             sF[j] = f;

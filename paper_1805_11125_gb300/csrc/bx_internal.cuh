@@ -74,6 +74,7 @@ struct Toy {
     int set_of[KMAX];
     double xi[MAX_SETS];
     double dE, w, r_fid, r_iv, att_len;
+    double gc1, gc2;          // Gram-Charlier response: skewness / 6 and excess kurtosis / 24 (0, 0: Gaussian)
     const double* shapes;     // [K][N]
     const float* shapes32;    // [K][N]
     const float* shapes32l;   // [K][N]: shapes - shapes32 (shapes32 + shapes32l is the FP64 shape to ~2^-48)
@@ -97,6 +98,12 @@ struct Toy {
     const float* utl;             // [N][NSL]: (1 + amp u[i][b]) - ut[i][b], the low parts
     const double* U2;             // [K][NSL]: sum_i s_k[i] ut[i][b] (slice-set normalisation)
     const double* psd2;           // [K][n_p2]
+    // template classes of the 2D model: within slice set s (0 vetoed, 1 tagged, 2 radial or the
+    // joint grid, 3 pulse shape) species of one class share their slice probabilities q[b] (the
+    // same radial class, the same pulse-shape row); cls_rep[s][c] is a species of class c
+    int n_cls[4];
+    int cls_of[4][KMAX], cls_rep[4][KMAX];
+    const float* utmax;           // [NSL]: the largest ut[i][b] of each slice over the columns
 };
 
 // Per-column FP64 results of k_prep.
@@ -110,6 +117,7 @@ struct Work {
     int nes;                  // energy slices of the Eq. 4 terms (the most of any toy, >= 1): the
                               // slice stride of aW, apart, rowW and coef
     int precision;
+    int fwd_wpc;              // warps per CTA of the FP32 forward: 2 (0: default) or 1 (autotuner's choice)
     double band;
     unsigned long long watchdog_ns;
     const Toy* toys;
@@ -153,6 +161,11 @@ struct Work {
                               // low part of the first (r_k dT/dr_k = plane 0 + plane 3 to ~2^-48)
     float* tr2d;              // [cap][tr_kb][3][NSL][KB]: rate-weighted templates (hi | mid | lo)
     unsigned* trmax2d;        // [cap][NSL]: largest |T_r[i,b]| of each slice over all columns (FP32 bits)
+    float2* alpha2d;          // [cap][4][KMAX]: per slice set, a species' coefficient without its class
+                              // probability (double-float): coef[k][b] = alpha[set(b)][k] q[b][class of k]
+    float2* qcls2d;           // [cap][NSL][KMAX]: q[b][c], the slice probability of class c (double-float)
+    float2* wcls2d;           // [cap][ncs2d][Npad]: class sums W[set, c][i] = sum_{k in c} alpha[set][k] s_k[i]
+    int ncs2d;                // class-sum rows (the most over the toys of sum over sets of n_cls)
     float* y2d;               // [cap][row_kb][3][NSL][KB]: Y = R T_r over output rows (TF32 hi | lo, FP32 remainder)
     float* w2d;               // [cap][win_kb][2][NSL][KB]: 1 - n/mu over window rows
     float* wt2d;              // [cap][row_kb][2][NSL][KB]: pile-up-correlated weights over rows
@@ -163,6 +176,18 @@ struct Work {
 };
 
 #ifdef __CUDACC__
+// Gram-Charlier response (a Gaussian corrected by its skewness and excess kurtosis, the same
+// mean and variance): phi(z) C(z) with C = gc1 He2 + gc2 He3 is what the CDF differs from Phi(z)
+// by, F(z) = Phi(z) - phi(z) C(z); the density is phi(z) (1 + gc1 He3(z) + gc2 He4(z)).
+__device__ __forceinline__ double gc_cdf_term(const Toy& T, double z) {
+    const double z2 = z * z;
+    return 0.39894228040143267794 * exp(-0.5 * z2) * (T.gc1 * (z2 - 1.0) + T.gc2 * z * (z2 - 3.0));
+}
+__device__ __forceinline__ double gc_density_factor(const Toy& T, double z) {
+    const double z2 = z * z;
+    return 1.0 + T.gc1 * z * (z2 - 3.0) + T.gc2 * (z2 * (z2 - 6.0) + 3.0);
+}
+
 // Column range [x, y) of forward tile t of an item's quenching group grp.
 __device__ __forceinline__ int2 tile_range(const Work& w, int item, int grp, int t) {
     return w.tile_cols[((size_t)item * MAX_SETS + grp) * MAX_TILES + t];
@@ -342,6 +367,53 @@ __device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t adesc, uint6
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
+}
+
+// Instruction descriptor of kind::f16 with both operands BF16: D = F32, A = B = BF16 (the same
+// type: kind::f16 takes one operand type for both), both K-major, M x N.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// D (+)= A B^T for one K = 16 step of BF16 operands (32 bytes of K, as one K = 8 step of TF32).
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Round to the nearest BF16 (as its 16-bit pattern); the three-part BF16 split of x on grid g:
+// hi on the grid (exact in BF16: at most 8 significant bits), mid and lo the BF16 roundings of
+// what remains (x - hi and x - hi - mid are exact in FP32).
+__device__ __forceinline__ uint16_t bf16_rn(float x) {
+    uint16_t r;
+    asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float bf16_val(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
+__device__ __forceinline__ void split3_bf16(float x, Grid g, uint16_t& hi, uint16_t& mid, uint16_t& lo) {
+    const float h = rintf(x * g.inv) * g.scale;
+    const float r = x - h;
+    hi = bf16_rn(h);
+    mid = bf16_rn(r);
+    lo = bf16_rn(r - bf16_val(mid));
+}
+// The four-part BF16 split (a second lo part, lo2, the BF16 rounding of what lo leaves; every
+// remainder is exact in FP32): for an operand whose hi grid is coarse, so that mid and lo alone
+// would leave ~2^-19 of the grid step.
+__device__ __forceinline__ void split4_bf16(float x, Grid g, uint16_t& hi, uint16_t& mid, uint16_t& lo,
+                                            uint16_t& lo2) {
+    const float h = rintf(x * g.inv) * g.scale;
+    const float r = x - h;
+    hi = bf16_rn(h);
+    mid = bf16_rn(r);
+    const float r2 = r - bf16_val(mid);
+    lo = bf16_rn(r2);
+    lo2 = bf16_rn(r2 - bf16_val(lo));
 }
 
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {

@@ -31,6 +31,7 @@ struct bx_model {
     int Kmax = 0, Nmax = 0, Mmax = 0, nwmax = 0, nbmax = 0, Lmax = 0, max_tiles = 0, max_cb = 0, P = 0;
     int any_tag = 0, any_cols = 0;   // some toy has a tagged spectrum / an Eq. 4 term
     int is2d = 0;                    // the toys carry 2D histograms (bx_2d.cu path)
+    int ncs2d = 0;                   // class-sum rows of the 2D templates (the most over the toys)
     std::vector<int> toy_tmp, toy_cached;
     double* theta_d = nullptr;
     double* nll_d = nullptr;
@@ -59,4 +60,7 @@ int bx_enqueue_eval(bx_model* m, int n, const double* theta_dev, int tstride, in
 int bx_take_device_error(bx_model* m);
 // parameters of public item rows of dataset t (K_t + 7 + 4 (E - 1))
 int bx_public_P(const bx_model* m, int t);
+// forward tile shapes the model can run (the FP32 forward: 128- or 64-row CTAs), and the choice
+int bx_fwd_tile_variants(const bx_model* m);
+void bx_set_fwd_tile(bx_model* m, int variant);
 void bx_fit_free(bx_model* m);

@@ -205,10 +205,16 @@ __global__ void __launch_bounds__(256) k_prep(Work w) {
             const double sig = var * isig;
             const double z = mu * isig;
             double norm = 1.0, mills = 0.0;
+            const bool gc = T.gc1 != 0.0 || T.gc2 != 0.0;
             if (z < Q_CUT) {
-                const double Phi = z > 0.0 ? 1.0 - upper_tail(z) : upper_tail(-z);
+                // mass above 0 npe, 1 - F(-z), and the density at -z over it (d ln N / d(mu / sigma))
+                double Phi = z > 0.0 ? 1.0 - upper_tail(z) : upper_tail(-z), dens = INV_SQRT_2PI * exp(-0.5 * z * z);
+                if (gc) {
+                    Phi += gc_cdf_term(T, -z);
+                    dens *= gc_density_factor(T, -z);
+                }
                 norm = 1.0 / Phi;
-                mills = INV_SQRT_2PI * exp(-0.5 * z * z) * norm;
+                mills = dens * norm;
             }
             col[ie] = Col64{mu, sig, norm, mills};
             // rate-weighted spectra of the vetoed (or single) and tagged events (Eq. 3)
@@ -224,9 +230,12 @@ __global__ void __launch_bounds__(256) k_prep(Work w) {
             }
             cs[ie] = make_double2(ssub, stag);
             // mass of the column in each energy slice of the window (Eq. 4 marginals)
-            for (int q = 0; q < NES; ++q)
-                aW[(size_t)q * w.Npad + ie] =
-                    gauss_mass((T.es_lo[q] * w_ - mu) * isig, (T.es_hi[q] * w_ - mu) * isig) * norm;
+            for (int q = 0; q < NES; ++q) {
+                const double za = (T.es_lo[q] * w_ - mu) * isig, zb = (T.es_hi[q] * w_ - mu) * isig;
+                double mass = gauss_mass(za, zb);
+                if (gc) mass -= gc_cdf_term(T, zb) - gc_cdf_term(T, za);
+                aW[(size_t)q * w.Npad + ie] = mass * norm;
+            }
             // response band: rows whose bin lies within band * sigma of mu
             const float muf = (float)mu, sigf = (float)sig;
             const float lo_e = fminf(fmaxf(muf - bandf * sigf, e_min), e_max);

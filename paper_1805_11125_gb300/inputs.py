@@ -86,6 +86,10 @@ class ModelSpec:
     # holds the energy window of the events in radial bin rho and pulse-shape bin j (the energy x
     # radius x pulse-shape histogram, one histogram "j2d" instead of "r2d" and "p2d")
     joint2d: bool = False
+    # Gram-Charlier response: skewness and excess kurtosis of the photoelectron response
+    # (0, 0: the Gaussian of Eq. 1)
+    resp_skew: float = 0.0
+    resp_kurt: float = 0.0
     theta_true: Optional[np.ndarray] = None
     species: List[str] = dataclasses.field(default_factory=list)
     counts: Dict[str, np.ndarray] = dataclasses.field(default_factory=dict)
@@ -465,6 +469,8 @@ def config(name: str) -> ModelSpec:
     * ``joint``    the energy x radius x pulse-shape fit: the TFC-vetoed events in 12 radial x 10
                   pulse-shape bins of the 900-bin window (120 slices) next to the TFC spectra;
                   ``small_joint`` its reduced grid with 6 x 5 slices.
+    * ``nongauss`` the multivariate model with a non-Gaussian (Gram-Charlier) response of
+                  skewness 0.1 and excess kurtosis 0.1; ``small_nongauss`` its reduced grid.
     * ``small_plain`` / ``small_mv`` / ``small_2d`` reduced grids that the oracle evaluates in
       well under a second (a few seconds for ``small_2d``) but that still span several
       128-row tiles and ragged tails.
@@ -496,6 +502,12 @@ def config(name: str) -> ModelSpec:
     if name == "small_sliced":
         return sliced(edges_npe=(120.0, 300.0, 540.0, 900.0), n_grid=520, width=3.0, lo_npe=120.0, hi_npe=900.0,
                       n_species=9, total=3e5, L=90, n_rad=20, n_psd=16, name=name)
+    if name == "nongauss":
+        return dataclasses.replace(multivariate(name=name), resp_skew=0.1, resp_kurt=0.1)
+    if name == "small_nongauss":
+        return dataclasses.replace(multivariate(n_grid=520, width=3.0, lo_npe=120.0, hi_npe=900.0, n_species=9,
+                                                total=3e5, L=90, n_rad=20, n_psd=16, name=name),
+                                   resp_skew=0.1, resp_kurt=0.1)
     if name == "small_quenched":
         return quenched(n_grid=520, width=3.0, lo_npe=120.0, hi_npe=900.0, n_species=12, total=3e5, L=90,
                         n_rad=20, n_psd=16, gamma_quench=1.3, name=name)

@@ -76,7 +76,8 @@ def test_quench_of_one_is_the_plain_model(prec):
 @pytest.mark.parametrize("prec", PRECS)
 def test_quenched_fit_agrees_with_oracle(prec):
     """Fits of the quenched model on the device against the oracle's Newton fit: every free
-    parameter within max(1e-4 |theta|, nsig sigma), nsig = 0.01 (FP64), 0.05 (FP32)."""
+    parameter within max(1e-4 |theta|, nsig sigma), nsig = 0.01 (FP64), 0.05 (FP32); a rate the
+    oracle holds at its bound 0 within 5e-4 / g (g its gradient there: at most 1e-3 in -2 lnL)."""
     s = dataset("small_quenched")
     ref = O.fit(s, s.theta_true, tol_edm=1e-14)
     assert ref["status"] == 0
@@ -87,8 +88,14 @@ def test_quenched_fit_agrees_with_oracle(prec):
     out, info, st = m.fit(th0, tol_edm=1e-8, max_iter=5000)
     sig = np.sqrt(np.maximum(np.diag(ref["cov"]), 0.0))
     tol = np.maximum(1e-4 * np.abs(ref["theta"]), nsig * sig)
+    at_bound = free & (sig == 0.0)
+    if at_bound.any():
+        _, g = O.nll(s, ref["theta"], grad=True)
+        assert np.all(g[at_bound] > 0.0), g[at_bound]
+        tol[at_bound] = 5e-4 / g[at_bound]
     for j in range(4):
         assert info[j]["status"] == bx.BX_OK, info[j]
         d = np.abs(out[j, : s.P] - ref["theta"])
-        assert np.all(d[free] <= tol[free]), (np.argmax(d[free] / tol[free]), (d[free] / tol[free]).max())
+        bad = np.nonzero(free & (d > tol))[0]
+        assert bad.size == 0, (j, bad, d[bad], tol[bad], out[j, bad], ref["theta"][bad])
     m.close()

@@ -749,3 +749,78 @@ def test_estimators_asimov_fit_returns_truth():
     m = free.astype(bool)
     np.testing.assert_allclose(r["theta"][m], th_true[m], rtol=2e-5)
     assert r["nll"] < 1e-8
+
+
+# ---- a non-Gaussian response: the Gram-Charlier series (Eq. 1's response, the paper's outlook)
+
+def _gc_density(x, mu, sig, g1, g2):
+    z = (x - mu) / sig
+    return math.exp(-0.5 * z * z) / (sig * math.sqrt(2 * math.pi)) * (
+        1.0 + g1 / 6.0 * (z ** 3 - 3 * z) + g2 / 24.0 * (z ** 4 - 6 * z * z + 3))
+
+
+def _gc_spec(g1=0.1, g2=0.1, width=0.5, n_grid=40):
+    """A response-only model: a few grid points, fine bins on an axis that holds every column."""
+    s = I.single_spectrum(n_grid=n_grid, width=width, lo_npe=0.0, hi_npe=1700.0, n_species=3, total=1e5, L=5)
+    return dataclasses.replace(s, resp_skew=g1, resp_kurt=g2)
+
+
+def test_gram_charlier_with_zero_moments_is_the_gaussian():
+    s = I.config("small_nongauss")
+    s = s.with_counts(I.poisson_counts(O.expected(s, s.theta_true), 8))
+    g = dataclasses.replace(s, resp_skew=0.0, resp_kurt=0.0)
+    base = I.config("small_mv").with_counts(s.counts_vector())
+    np.testing.assert_array_equal(O.expected(g, s.theta_true), O.expected(base, s.theta_true))
+
+
+def test_gram_charlier_bin_mass_matches_quadrature_of_its_density():
+    """R[m,i] against an independent adaptive quadrature of the density over the bin, over the
+    mass above 0 npe (the closed-form CDF is what the oracle uses)."""
+    s = _gc_spec(width=7.0)
+    th = s.theta_true
+    R, _ = O.response(s, th)
+    _, mu, sig, _ = O.quench(s, th)
+    for i in (3, 17, 31):
+        N = integrate.quad(lambda x: _gc_density(x, mu[i], sig[i], 0.1, 0.1), 0.0, mu[i] + 40 * sig[i],
+                           points=[mu[i]], epsabs=0, epsrel=1e-13, limit=400)[0]
+        m0 = int(mu[i] // s.width)
+        for m in range(max(0, m0 - 12), min(s.m_hi, m0 + 12)):
+            q = integrate.quad(lambda x: _gc_density(x, mu[i], sig[i], 0.1, 0.1), m * s.width, (m + 1) * s.width,
+                               epsabs=0, epsrel=1e-13)[0]
+            assert R[m, i] == pytest.approx(q / N, rel=1e-10, abs=1e-16)
+
+
+def test_gram_charlier_response_has_the_stated_moments():
+    """On 0.5-npe bins (sigma ~ 10-35 npe) each response column's binned moments are those of the
+    density: mean mu (the light-yield map's), variance sigma^2 (+ w^2/12 of the binning), skewness
+    g1, excess kurtosis g2 (binning corrections of order (w / sigma)^2)."""
+    g1, g2 = 0.1, 0.1
+    s = _gc_spec(g1, g2)
+    th = s.theta_true
+    R, _ = O.response(s, th)
+    _, mu, sig, _ = O.quench(s, th)
+    c = (np.arange(s.m_hi) + 0.5) * s.width
+    for i in (5, 20, 35):
+        r = R[:, i]
+        assert r.sum() == pytest.approx(1.0, abs=1e-12)
+        m1 = (r * c).sum()
+        d = c - m1
+        v = (r * d * d).sum()
+        assert m1 == pytest.approx(mu[i], rel=1e-9)
+        assert v == pytest.approx(sig[i] ** 2 + s.width ** 2 / 12.0, rel=1e-7)
+        assert (r * d ** 3).sum() / v ** 1.5 == pytest.approx(g1, abs=2e-4)
+        assert (r * d ** 4).sum() / v ** 2 - 3.0 == pytest.approx(g2, abs=2e-3)
+
+
+def test_gram_charlier_dual_gradient_matches_central_differences():
+    s = I.config("small_nongauss")
+    s = s.with_counts(I.poisson_counts(O.expected(s, s.theta_true), 9))
+    th = I.parameter_points(s.theta_true, 1, rel=0.02, seed=52, free=s.default_free())[0]
+    f, g = O.nll(s, th, grad=True)
+    for p in [0, s.K - 1, tail(s, "LY"), tail(s, "a"), tail(s, "b"), tail(s, "c"), tail(s, "kB"), tail(s, "eps")]:
+        h = 1e-5 * abs(th[p])
+        tp, tm = th.copy(), th.copy()
+        tp[p] += h
+        tm[p] -= h
+        fd = (O.nll(s, tp) - O.nll(s, tm)) / (2 * h)
+        assert abs(fd - g[p]) * abs(th[p]) <= 1e-6 * (1 + abs(g[p] * th[p])), (p, fd, g[p])
