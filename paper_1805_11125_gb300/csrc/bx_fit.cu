@@ -69,7 +69,7 @@ constexpr double EDM_FLOOR_FP32 = 1e-5;
 // directions.  Measured over 11 FP32 fits from 10% starts, 10 converge with 1 sigma, 9 with
 // 0.3 sigma and 8 with relative steps.  Steps stay below half the parameter's magnitude (a
 // rate stepped to zero could empty a bin).
-constexpr double HSIG_FP32 = 1.0;
+constexpr double HSIG_FP32 = 1.0, HSIG_MAX = 64.0;
 
 // Trust region of the response, pile-up and radial parameters.  Far from the optimum the Newton
 // step of these nearly degenerate parameters can be many times their value (the light yield,
@@ -77,7 +77,7 @@ constexpr double HSIG_FP32 = 1.0;
 // accept a point from which the fit runs onto the bounds: a 5%-off start of the small joint
 // model walked the resolution term b to 25 times its value with four parameters held at bounds.
 // Near the optimum every step is well inside the region (a few standard deviations at most).
-constexpr double TR_REL = 2.0, TR_SIG = 10.0;
+constexpr double TR_REL = 1.0, TR_SIG = 3.0;
 
 struct FitCtl {
     int phase, iters, evals, status, max_evals, fails, n_bound;
@@ -279,19 +279,39 @@ __global__ void k_fit(FitDev F) {
         if (!isfinite(f0)) { c.phase = PH_DONE; c.status = BX_EDOMAIN; }
         else to_hess = true;
     } else if (c.phase == PH_HESS) {
+        // column j: the central difference of the gradients at theta +- h e_j; where one side was
+        // not evaluable (outside the model's domain, or h below the resolution of theta_j) the
+        // one-sided difference with the accepted point; with neither, no curvature (damping
+        // then carries that direction)
+        auto finite_at = [&](int k) {
+            if (!isfinite(F.ft[s0 + k])) return false;
+            const double* gk = slot_g(k);
+            for (int i = 0; i < Pt; ++i)
+                if (!isfinite(gk[i])) return false;
+            return true;
+        };
         int a = 0;
         for (int j = 0; j < Pt; ++j) {
             if (!fr[j]) continue;
-            const double* gp = slot_g(NLS + 2 * a);
-            const double* gm = slot_g(NLS + 2 * a + 1);
-            const double up = slot_t(NLS + 2 * a)[j], dn = slot_t(NLS + 2 * a + 1)[j];
-            for (int i = 0; i < Pt; ++i) H[IDX(i, j)] = fr[i] ? (gp[i] - gm[i]) / (up - dn) : 0.0;
+            const int kp = NLS + 2 * a, km = kp + 1;
+            const double up = slot_t(kp)[j], dn = slot_t(km)[j];
+            const bool okp = finite_at(kp) && up > th[j], okm = finite_at(km) && dn < th[j];
+            const double* ga = okp ? slot_g(kp) : g;
+            const double* gb = okm ? slot_g(km) : g;
+            const double du = (okp ? up : th[j]) - (okm ? dn : th[j]);
+            for (int i = 0; i < Pt; ++i) H[IDX(i, j)] = (fr[i] && du > 0.0) ? (ga[i] - gb[i]) / du : 0.0;
             ++a;
         }
         newdir = fresh = true;
     } else if (c.phase == PH_LS) {
+        // the NLS step lengths were evaluated together: of those with sufficient decrease
+        // (Armijo), the one with the lowest -lnL -- not the longest, which in a curved valley
+        // (the correlated resolution terms) can land far out on a descent that a shorter step
+        // beats.  At the noise floor of the FP32 -lnL (an undamped step predicting less than
+        // EDM_NOISE) the full step counts as a decrease while it stays within the noise.
         int acc = -1;
-        for (int k = 0; k < NLS && acc < 0; ++k) {
+        double fbest = 0.0;
+        for (int k = 0; k < NLS; ++k) {
             const double fk = F.ft[s0 + k];
             if (!isfinite(fk)) continue;
             double gs = 0.0;
@@ -299,7 +319,10 @@ __global__ void k_fit(FitDev F) {
             for (int i = 0; i < Pt; ++i) gs += g[i] * (tk[i] - th[i]);
             const bool noise_floor = k == 0 && c.mu_used <= c.mu_conv && c.edm0 < EDM_NOISE &&
                                      fk <= F.f[jf] + 2.0 * EDM_NOISE;
-            if (fk <= F.f[jf] + 1e-4 * gs || noise_floor) acc = k;
+            if ((fk <= F.f[jf] + 1e-4 * gs || noise_floor) && (acc < 0 || fk < fbest)) {
+                acc = k;
+                fbest = fk;
+            }
         }
         if (acc >= 0) {
             for (int i = 0; i < Pt; ++i) { th[i] = slot_t(acc)[i]; g[i] = slot_g(acc)[i]; }
@@ -307,6 +330,20 @@ __global__ void k_fit(FitDev F) {
             c.iters++;
             c.mu_min = 0.0;
             to_hess = true;
+        } else if (c.hsig > 0.0 && c.edm0 < c.tol && c.mu_fresh > c.mu_conv) {
+            // an FP32 fit whose fresh Hessian is indefinite while its step predicts no decrease
+            // and no trial lowers -lnL: the curvature of a weak direction is lost in the
+            // gradients' rounding noise over a step of HSIG conditional deviations, so the
+            // Hessian is taken again with 4x the step; once that reaches HSIG_MAX the point is
+            // the optimum to within the FP32 noise floor (an FP64 polish resolves the rest)
+            c.fails++;
+            if (c.hsig < HSIG_MAX) {
+                c.hsig *= 4.0;
+                to_hess = true;
+            } else {
+                c.phase = PH_DONE;
+                c.status = BX_OK;
+            }
         } else {
             c.fails++;
             c.mu_min = c.mu_used > 0.0 ? c.mu_used * 1e3 : 1e-3;
@@ -348,19 +385,26 @@ __global__ void k_fit(FitDev F) {
             } else {
                 c.phase = PH_LS;
                 // trust region of the response, pile-up and radial parameters (everything after the
-                // rates): a trial step moves none of them by more than TR_REL of its magnitude or
-                // TR_SIG of its standard deviation under the current Hessian, whichever is larger
-                double amax = 1.0;
-                for (int i = Kt; i < Pt; ++i)
-                    if (act[i] && d[i] != 0.0) {
+                // rates), per parameter: a trial step moves none of them by more than TR_REL of its
+                // magnitude or TR_SIG of its standard deviation under the current Hessian, whichever
+                // is larger.  A component beyond its limit is clipped and the others keep their
+                // length (scaling the whole step instead let one tightly limited parameter stall
+                // every other one, and a first step from 10% out had sent the constant noise term c
+                // to hundreds of times its optimum).
+                double lim[PFMAX];
+                for (int i = 0; i < Pt; ++i) {
+                    lim[i] = INFINITY;
+                    if (i >= Kt && act[i]) {
                         const double v = V[IDX(i, i)];
-                        const double lim = fmax(TR_REL * fabs(th[i]), v > 0.0 && isfinite(v) ? TR_SIG * sqrt(v) : 0.0);
-                        if (lim > 0.0) amax = fmin(amax, lim / fabs(d[i]));
+                        const double l = fmax(TR_REL * fabs(th[i]), v > 0.0 && isfinite(v) ? TR_SIG * sqrt(v) : 0.0);
+                        if (l > 0.0) lim[i] = l;
                     }
+                }
                 for (int k = 0; k < NLS; ++k) {
-                    const double a = amax * ldexp(1.0, -k);
+                    const double a = ldexp(1.0, -k);
                     double* tk = slot_t(k);
-                    for (int i = 0; i < Pt; ++i) tk[i] = fr[i] ? fmin(fmax(th[i] + a * d[i], lo[i]), hi[i]) : th[i];
+                    for (int i = 0; i < Pt; ++i)
+                        tk[i] = fr[i] ? fmin(fmax(th[i] + fmin(fmax(a * d[i], -lim[i]), lim[i]), lo[i]), hi[i]) : th[i];
                     F.skip[s0 + k] = 0;
                 }
                 for (int k = NLS; k < S; ++k) F.skip[s0 + k] = 1;

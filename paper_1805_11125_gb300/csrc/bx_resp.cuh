@@ -289,17 +289,17 @@ __device__ __forceinline__ void adj_run(float mf, int n, const float4& cf, const
     }
 }
 
-// The node sums P0, P1, P2 of resp_adjoint32 for rows mf .. mf + n - 1 (n <= ADJ_RUN) of one
+// The node sums P0, P1, P2 of resp_adjoint32 for rows mf .. mf + n - 1 (n <= RUN) of one
 // column, by the row recurrence of adj_run from an exact start: f(k, P0, P1, P2) receives
 // row mf + k.  With u = p0 cosh z, v = p0 sinh z and o = 5 Ck2,
 //   P0 = o u + 8 p0,  P1 = o (t u - kk v) + 8 t p0,  P2 = o ((kk^2 + t^2) u - 2 kk t v) + 8 t^2 p0.
 // Columns narrow enough for |z| > 1 within the run take resp_adjoint32 row by row.
-template <typename F>
+template <int RUN = ADJ_RUN, typename F>
 __device__ __forceinline__ void adj_nodes_run(float mf, int n, const float4& cf, const ColG& cg, const AdjCol& ac,
                                               F&& f) {
     float th, tl;
     centre_df(mf, cf, cg.c_lo, th, tl);
-    const float z0 = cg.kap * th, z1 = cg.kap * fmaf((float)(ADJ_RUN - 1), ac.hs, th);
+    const float z0 = cg.kap * th, z1 = cg.kap * fmaf((float)(RUN - 1), ac.hs, th);
     if (fabsf(z0) <= 1.0f && fabsf(z1) <= 1.0f) {
         float p = centre_node(th, tl);
         float rho = exp2_neg(-fmaf(2.0f * th, ac.hs, ac.hs2));
@@ -308,7 +308,7 @@ __device__ __forceinline__ void adj_nodes_run(float mf, int n, const float4& cf,
         float t = th;
         const float o = GL_W_OUT * cg.Ck2, kk = ac.kk, kk2 = ac.kk * ac.kk;
 #pragma unroll
-        for (int k = 0; k < ADJ_RUN; ++k) {
+        for (int k = 0; k < RUN; ++k) {
             if (k < n) {
                 const float u = p * ch, v = p * sh, tp = t * p;
                 const float P0 = fmaf(o, u, GL_W_MID * p);
@@ -324,8 +324,9 @@ __device__ __forceinline__ void adj_nodes_run(float mf, int n, const float4& cf,
             }
         }
     } else {
-#pragma unroll 2
-        for (int k = 0; k < ADJ_RUN; ++k) {
+        // short runs unrolled whole, so that f may keep its rows in registers
+#pragma unroll (RUN <= 8 ? RUN : 2)
+        for (int k = 0; k < RUN; ++k) {
             if (k < n) {
                 float P0, P1, P2;
                 resp_adjoint32(mf + (float)k, cf, cg, P0, P1, P2);
