@@ -236,8 +236,13 @@ int bx_nll_batch(bx_model* model, int n, const int* toy_idx, const double* theta
  * time_budget_s of wall time on the device clock: unfinished fits then report BX_ETIMEOUT).  F
  * is the caller's fits_in_flight, or the autotuner's choice: it times one evaluation round for
  * F = the largest feasible value and its halves, and for each forward tile shape of the model,
- * on the fits' own datasets; the choice is kept for further calls of the same size and is
- * reported by bx_fit_last_plan. */
+ * on the fits' own datasets, and takes the largest F within 10% of the best rate; the choice is
+ * kept for further calls of the same size and is reported by bx_fit_last_plan.
+ * Steps: the 8 trial lengths of a line search are evaluated together and the best point with
+ * sufficient decrease is taken; each non-rate component of a step is clipped to
+ * max(|theta_i|, 3 sigma_i).  A BX_FP32 fit whose fresh Hessian is indefinite while no trial
+ * lowers -lnL retakes the Hessian with 4x larger steps, and past 64 conditional deviations
+ * stops with BX_OK at its noise floor. */
 typedef struct {
     double tol_edm;             /* EDM tolerance (0 -> 1e-8) */
     int max_iter;               /* evaluation budget per fit (0 -> 5000) */

@@ -665,10 +665,14 @@ static int fit_autotune(bx_model* m, int Fmax) {
     m->w.skip = saved_skip;
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    int F = cand[0];
+    // the largest wave within 10% of the best rate: the timed rounds have every slot busy, while
+    // a fit's rounds in flight use a third of its slots on average (8 trials or 2 P Hessian
+    // points of 8 + 2 P), so a wave that only just fills the GPU here starves it in the loop
+    // (4096 toys: 256 in flight ran at 226k evaluations/s against 447k with all of them)
+    int F = cand.back();
     const double top = *std::max_element(thr.begin(), thr.end());
-    for (size_t c = 0; c < cand.size(); ++c)
-        if (thr[c] >= 0.9 * top) F = cand[c];   // candidates descend: the last one that qualifies is the smallest
+    for (size_t c = cand.size(); c-- > 0;)
+        if (thr[c] >= 0.9 * top) F = cand[c];   // candidates descend: the last one found is the largest
     s->tuned_F = F;
     s->tuned_tile = best_tile;
     s->tuned_evals_per_s = best;

@@ -47,7 +47,7 @@ __device__ __forceinline__ void kahan_fma(float& acc, float& cmp, float a, float
 // tile; the autotuner of the batched fits may pick it for small ragged items).  The warps of a
 // CTA never synchronise, so the two shapes do the same work per warp.
 template <bool TAG, bool COLS, bool MES, int WPC = 2>
-__global__ void __launch_bounds__(32 * WPC, WPC == 2 ? 18 : 32) k_fwd_f32(Work w) {
+__global__ void __launch_bounds__(32 * WPC) k_fwd_f32(Work w) {
     // 1D item-major grid (a y dimension would cap the batch at 65535 items)
     const int unit = WPC == 2 ? (int)blockIdx.x : (int)(blockIdx.x >> 1);
     const int tile = unit % w.max_tiles, item = unit / w.max_tiles, tid = threadIdx.x;
