@@ -40,9 +40,10 @@ FWD_OPS_PER_ENTRY = 54
 BWD_OPS_PER_ENTRY = 35
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # DRAM bytes (read + write) per evaluation item of the two candidate dominant kernels, from one
-# ncu capture of the multivariate model at 512 items (--set full, one launch each); the traffic
-# scales with the items of a launch.
-TRAFFIC_PER_ITEM = {"k_fwd_f32": (45.5e6 + 2.85e6) / 512, "k_bwd_f32": (96.9e6 + 3.14e6) / 512}
+# ncu capture of the multivariate model at 512 items each (k_fwd_f32: SpeedOfLight and
+# MemoryWorkloadAnalysis sections, dram__bytes.sum.per_second x duration; k_bwd_f32: --set full);
+# the traffic scales with the items of a launch.
+TRAFFIC_PER_ITEM = {"k_fwd_f32": 74.00264e9 * 775.68e-6 / 512, "k_bwd_f32": (96.9e6 + 3.14e6) / 512}
 
 
 def job_throughput(local_ms: float, items_per_rank: int, steps: int, ws: int, device=None):
@@ -729,6 +730,7 @@ def stored_fit_comparison(spec, fits):
     free = spec.default_free().astype(bool)
     tol = np.maximum(1e-4 * np.abs(ref), 0.01 * sig)
     rates = free[: spec.K] & (np.abs(ref[: spec.K]) > 0)
+    free = free & (tol > 0)   # a rate the oracle holds at its bound 0 has no sigma: left out here
     out = {"oracle_fit_s_on_writer_host": g.get("fit_s")}
     for k, (th, nll) in fits.items():
         d = np.abs(np.asarray(th)[: spec.P] - ref)

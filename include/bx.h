@@ -321,7 +321,7 @@ int bx_selftest_watchdog(double budget_s);
  * lambda [m_hi] or [2][m_hi].  Limits of the fixed scratch: n_grid <= 4096, m_hi <= 4096,
  * K <= 16 (BX_EINVAL beyond).  The work is enqueued on cuda_stream and the call returns.
  * Its scratch is one 530 KiB static device array per device, whose address is looked up on
- * the first call made on that device (make it before any stream capture); all calls share
+ * the first call made on that device; all calls share
  * it, so calls that overlap on the GPU race.  A parameter point outside the model's domain
  * (non-finite theta, LY <= 0, sigma^2 <= 0 at a grid point) fills lambda with NaN; the call
  * itself still returns BX_OK, because the check runs on the device after it has returned. */

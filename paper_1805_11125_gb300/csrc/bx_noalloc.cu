@@ -13,7 +13,7 @@
 //
 // Consequences for the caller:
 //   * the array's device address is looked up once per device, on the first call made with
-//     that device current; make that first call before any stream capture;
+//     that device current;
 //   * every call on a device shares the one array, so calls that overlap on the GPU (two
 //     streams, two host threads) race: serialise them;
 //   * the array keeps whatever the last call left in it; each call re-initialises everything
