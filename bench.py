@@ -274,11 +274,13 @@ def run_ours(args):
         fits = fit_times(bx, I, spec, stream)
         if args.toys > 0:
             fits["batched_toys"] = toy_fits(bx, I, args.toys, stream)
-        disc = discrimination_leg(bx, I, stream, B=args.batch2d) if args.batch2d > 0 else None
+        rc = ceil["resp"]["value"] if ceil else None
+        disc = discrimination_leg(bx, I, stream, B=args.batch2d, resp_ceiling=rc) if args.batch2d > 0 else None
         fits["quenched"] = variant_leg(bx, I, "quenched", QUENCHED, stream, B=args.batch) if args.quenched else None
         fits["sliced"] = variant_leg(bx, I, "sliced", SLICED, stream, B=args.batch) if args.sliced else None
         fits["joint_3d"] = (discrimination_leg(bx, I, stream, B=args.batch2d, name="joint", workload=JOINT,
-                                               n_slices=120) if args.joint and args.batch2d > 0 else None)
+                                               n_slices=120, resp_ceiling=rc)
+                            if args.joint and args.batch2d > 0 else None)
     if rank != 0:
         return
     report(args, ws, B, total_ms, value, stage_ms, n_evals, entries, e2e, fp64_value, tc_value, clk, fits, disc,
@@ -391,7 +393,8 @@ JOINT = ("energy x radius x pulse-shape: K=15, TFC 2x900 + the 900 x 12 x 10 joi
          "events (109800 bins), 22 parameters, 2e6 events")
 
 
-def discrimination_leg(bx, I, stream, B=256, steps=5, name="discrimination", workload=DISCRIMINATION, n_slices=112):
+def discrimination_leg(bx, I, stream, B=256, steps=5, name="discrimination", workload=DISCRIMINATION, n_slices=112,
+                       resp_ceiling=None):
     """A 2D-slice model on the tensor cores: the discrimination regime (K = 15; TFC spectra and
     the 900 x 60 energy x radius and 900 x 50 energy x pulse-shape histograms, 100800 bins, 22
     parameters) or the joint energy x radius x pulse-shape grid (12 x 10 cells): -lnL + gradient
@@ -435,6 +438,9 @@ def discrimination_leg(bx, I, stream, B=256, steps=5, name="discrimination", wor
     peaks = measured_peaks()
     tf32_peak = peaks.get("bf16_tflops", 1887.0) * (1.1 / 2.25)
     tc = alg / (per["forward"] / 1e3) / 1e12
+    # generation of the response tiles on the CUDA cores: in-band entries per second of the
+    # forward stage against the measured ceiling of the bin-mass routine
+    gen_rate = entries / max(n_evals, 1) / (per["forward"] / 1e3) / 1e9
     # one fit of the full model
     mf = bx.Model(s, precision=bx.BX_FP32, max_batch=8 + 2 * s.P, stream=stream)
     th0 = I.parameter_points(s.theta_true, 1, rel=0.1, seed=401, free=s.default_free())
@@ -452,6 +458,10 @@ def discrimination_leg(bx, I, stream, B=256, steps=5, name="discrimination", wor
                              "peak_basis": "measured bf16 burst x nominal TF32/BF16 ratio 1.1/2.25",
                              "algorithmic": f"2 x in-band response entries x {n_slices} slices per evaluation, over the "
                                             "forward stage (templates + generation + GEMM)"},
+            "forward_generation": {"bound": "alu", "achieved": gen_rate, "unit": "Gentries/s",
+                                   "peak": resp_ceiling, "frac": gen_rate / resp_ceiling if resp_ceiling else None,
+                                   "peak_basis": "measured: bx_ceiling BX_CEIL_RESP (the ceilings leg)",
+                                   "algorithmic": "in-band response entries per evaluation over the forward stage"},
             "fit": {"wall_s": fit_s, "status": int(st), "evals": int(info[0]["n_evals"])}}
 
 

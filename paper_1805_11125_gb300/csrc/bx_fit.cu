@@ -49,6 +49,16 @@ enum { PH_START = 0, PH_HESS = 1, PH_LS = 2, PH_DONE = 3 };
 // -lnL carries ~5e-5 of rounding noise): an undamped full Newton step is then accepted
 // without the sufficient-decrease test, provided -lnL does not rise by more than the noise.
 constexpr double EDM_NOISE = 5e-5;
+// The noise of a large toy's FP32 -lnL is above EDM_NOISE (it grows with the counts): each
+// Hessian of an FP32 fit also estimates it, as the median over the parameters of
+// |f(theta + h e_j) + f(theta - h e_j) - 2 f(theta) - H_jj h^2| / 2 (the second difference of f
+// against the curvature from the gradients; their difference is rounding, the h^4 term being
+// far smaller at steps of a conditional deviation).  An FP32 fit whose fresh, lightly damped
+// step predicts less than FNOISE_K times that has reached its noise floor and is converged.
+constexpr double FNOISE_K = 2.0;
+// Largest fresh EDM at which an FP32 fit whose line search finds no decrease is taken to be at
+// its noise floor (retaken Hessians, then BX_OK): within sqrt(2 x 1e-3) = 0.045 sigma.
+constexpr double EDM_STALL = 1e-3;
 // Largest damping (scaled units) with which a fresh Hessian may declare convergence
 // (FitCtl::mu_conv): a damping mu lowers the EDM along a direction of curvature lambda < mu
 // by lambda / mu.  With FP64 evaluations mu <= 1e-2 keeps the distance missed that way below
@@ -82,6 +92,7 @@ constexpr double TR_REL = 1.0, TR_SIG = 3.0;
 struct FitCtl {
     int phase, iters, evals, status, max_evals, fails, n_bound;
     double edm, edm0, tol, mu_min, mu_used, hrel, mu_conv, hsig, mu_fresh;
+    double fnoise;   // FP32: rounding noise of -lnL estimated at the last Hessian (0 until then)
 };
 
 struct FitDev {
@@ -290,7 +301,8 @@ __global__ void k_fit(FitDev F) {
                 if (!isfinite(gk[i])) return false;
             return true;
         };
-        int a = 0;
+        int a = 0, ne = 0;
+        double res[PFMAX];
         for (int j = 0; j < Pt; ++j) {
             if (!fr[j]) continue;
             const int kp = NLS + 2 * a, km = kp + 1;
@@ -300,7 +312,20 @@ __global__ void k_fit(FitDev F) {
             const double* gb = okm ? slot_g(km) : g;
             const double du = (okp ? up : th[j]) - (okm ? dn : th[j]);
             for (int i = 0; i < Pt; ++i) H[IDX(i, j)] = (fr[i] && du > 0.0) ? (ga[i] - gb[i]) / du : 0.0;
+            if (c.hsig > 0.0 && okp && okm && up - th[j] == th[j] - dn) {   // symmetric: f's noise
+                const double h = up - th[j];
+                res[ne++] = 0.5 * fabs(F.ft[s0 + kp] + F.ft[s0 + km] - 2.0 * F.f[jf] - H[IDX(j, j)] * h * h);
+            }
             ++a;
+        }
+        if (ne > 0) {   // median (insertion sort of at most PFMAX values)
+            for (int i = 1; i < ne; ++i)
+                for (int k = i; k > 0 && res[k - 1] > res[k]; --k) {
+                    const double t = res[k];
+                    res[k] = res[k - 1];
+                    res[k - 1] = t;
+                }
+            c.fnoise = ne & 1 ? res[ne / 2] : 0.5 * (res[ne / 2 - 1] + res[ne / 2]);
         }
         newdir = fresh = true;
     } else if (c.phase == PH_LS) {
@@ -317,8 +342,8 @@ __global__ void k_fit(FitDev F) {
             double gs = 0.0;
             const double* tk = slot_t(k);
             for (int i = 0; i < Pt; ++i) gs += g[i] * (tk[i] - th[i]);
-            const bool noise_floor = k == 0 && c.mu_used <= c.mu_conv && c.edm0 < EDM_NOISE &&
-                                     fk <= F.f[jf] + 2.0 * EDM_NOISE;
+            const double nz = fmax(EDM_NOISE, c.fnoise);
+            const bool noise_floor = k == 0 && c.mu_used <= c.mu_conv && c.edm0 < nz && fk <= F.f[jf] + 2.0 * nz;
             if ((fk <= F.f[jf] + 1e-4 * gs || noise_floor) && (acc < 0 || fk < fbest)) {
                 acc = k;
                 fbest = fk;
@@ -330,12 +355,12 @@ __global__ void k_fit(FitDev F) {
             c.iters++;
             c.mu_min = 0.0;
             to_hess = true;
-        } else if (c.hsig > 0.0 && c.edm0 < c.tol && c.mu_fresh > c.mu_conv) {
-            // an FP32 fit whose fresh Hessian is indefinite while its step predicts no decrease
-            // and no trial lowers -lnL: the curvature of a weak direction is lost in the
-            // gradients' rounding noise over a step of HSIG conditional deviations, so the
-            // Hessian is taken again with 4x the step; once that reaches HSIG_MAX the point is
-            // the optimum to within the FP32 noise floor (an FP64 polish resolves the rest)
+        } else if (c.hsig > 0.0 && c.edm0 < fmax(c.tol, EDM_STALL)) {
+            // an FP32 fit whose fresh step predicts little (or whose Hessian is indefinite) and
+            // no trial lowers -lnL: the curvature of a weak direction is lost in the gradients'
+            // rounding noise over a step of HSIG conditional deviations, so the Hessian is taken
+            // again with 4x the step; once that reaches HSIG_MAX the point is the optimum to
+            // within the FP32 noise floor (an FP64 polish resolves the rest)
             c.fails++;
             if (c.hsig < HSIG_MAX) {
                 c.hsig *= 4.0;
@@ -379,7 +404,7 @@ __global__ void k_fit(FitDev F) {
                 for (int i = 0; i < Pt; ++i) nb += (fr[i] && !act[i]) ? 1 : 0;
                 c.n_bound = nb;
             }
-            if (fresh && c.edm < c.tol && mu <= c.mu_conv) {
+            if (fresh && c.edm < fmax(c.tol, FNOISE_K * c.fnoise) && mu <= c.mu_conv) {
                 c.phase = PH_DONE;
                 c.status = BX_OK;
             } else {

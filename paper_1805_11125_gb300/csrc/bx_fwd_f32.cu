@@ -31,7 +31,6 @@
 
 namespace bx {
 
-constexpr int F32_THREADS = TM / 2;
 constexpr int FCH32 = 32;
 
 // acc += a (b + bl), Kahan-compensated: bl is the low part of the column's double-float spectrum,
