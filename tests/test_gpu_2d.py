@@ -90,7 +90,7 @@ def test_2d_without_field_matches_the_1d_path():
 
 def test_2d_fit_agrees_with_oracle():
     """FP32 fits of the 2D model on the device against the oracle's Newton fit:
-    |d theta| <= max(1e-4 |theta|, 0.05 sigma) (the FP32 noise floor), -2 lnL within P 0.05^2.
+    |d theta| <= max(1e-4 |theta|, 0.05 sigma) (the FP32 noise floor), -2 lnL within 1e-3.
     Asimov data (n = mu(theta_true)): with Poisson data this small model's resolution and
     radial parameters are so weakly constrained that the likelihood has several minima on the
     bounds, and two correct minimisers may end in different ones; with Asimov data the
@@ -109,7 +109,7 @@ def test_2d_fit_agrees_with_oracle():
         assert info[j]["status"] == bx.BX_OK, info[j]
         d = np.abs(out[j, : s.P] - ref["theta"])
         assert np.all(d[free] <= tol[free]), (d[free] / tol[free]).max()
-        assert 2 * abs(info[j]["nll"] - ref["nll"]) <= max(1e-3, s.P * 0.05 ** 2)
+        assert 2 * abs(info[j]["nll"] - ref["nll"]) <= 1e-3
     m.close()
 
 

@@ -125,7 +125,8 @@ def test_batched_fits_of_different_toys():
 def test_profile_likelihood_scan_matches_the_oracle(prec):
     """Profile of one rate (the paper's use of the fit: limits on rare-signal rates): at each
     scan value the other 20 parameters are refitted; the GPU's minimised -lnL at each point
-    agrees with the oracle's constrained fit and the profile is minimal at the global fit."""
+    agrees with the oracle's constrained fit (|Delta(-2 lnL)| <= 1e-3, FP32 as FP64) and the
+    profile is minimal at the global fit."""
     s = dataset("small_mv")
     ref = O.fit(s, s.theta_true, tol_edm=1e-14)
     j = 1
@@ -137,7 +138,7 @@ def test_profile_likelihood_scan_matches_the_oracle(prec):
     assert np.all(th[:, j] == vals)
     free = s.default_free().copy()
     free[j] = 0
-    tol = 1e-3 if prec == bx.BX_FP64 else max(1e-3, s.P * 0.05 ** 2)
+    tol = 1e-3
     for k, v in enumerate(vals):
         t0 = ref["theta"].copy()
         t0[j] = v

@@ -103,7 +103,8 @@ def test_joint_batch_equals_single_calls():
 
 def test_joint_fit_agrees_with_oracle():
     """FP32 fits of the small joint model on Asimov data (the optimum is theta_true, interior and
-    unique) against the oracle's Newton fit: |d theta| <= max(1e-4 |theta|, 0.05 sigma)."""
+    unique) against the oracle's Newton fit: |d theta| <= max(1e-4 |theta|, 0.05 sigma) (the FP32
+    noise floor), -2 lnL within 1e-3."""
     s = I.config("small_joint")
     s = s.with_counts(O.expected(s, s.theta_true))
     ref = O.fit(s, s.theta_true, tol_edm=1e-14)
@@ -118,5 +119,5 @@ def test_joint_fit_agrees_with_oracle():
         assert info[k]["status"] == bx.BX_OK, info[k]
         d = np.abs(out[k, : s.P] - ref["theta"])
         assert np.all(d[free] <= tol[free]), (d[free] / tol[free]).max()
-        assert 2 * abs(info[k]["nll"] - ref["nll"]) <= max(1e-3, s.P * 0.05 ** 2)
+        assert 2 * abs(info[k]["nll"] - ref["nll"]) <= 1e-3
     m.close()
