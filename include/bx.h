@@ -137,14 +137,16 @@ typedef struct {
      * <= 128; field2d is [N][n_rad2d * n_psd2d], counts_rad2d [n_rad2d * n_psd2d][m_hi - m_lo]
      * and counts_psd2d is not read. */
     int joint2d;
-    /* A non-Gaussian response (the "more sophisticated response function" of the paper's
-     * outlook; Eq. 1's p0, p1, ...): the Gram-Charlier series of the Gaussian with skewness
+    /* A non-Gaussian response (of the kind the paper's outlook plans for Eq. 1): the
+     * Gram-Charlier series of the Gaussian with skewness
      * resp_skew and excess kurtosis resp_kurt, density
      *   phi(z) [1 + resp_skew/6 He3(z) + resp_kurt/24 He4(z)],  He3 = z^3 - 3z, He4 = z^4 - 6z^2 + 3,
      * so the mean (LY Q) and variance (a mu + b mu^2 + c) of the response stay those of Eq. 1.
      * Bin masses from its closed-form CDF Phi(z) - phi(z) [resp_skew/6 (z^2 - 1) + resp_kurt/24
-     * (z^3 - 3z)], normalised to the mass above 0 npe.  0, 0: the Gaussian.  Otherwise BX_FP64
-     * only, no 2D histograms, and the density must stay non-negative within band_sigmas. */
+     * (z^3 - 3z)], normalised to the mass above 0 npe (BX_FP32: the generator's three quadrature
+     * nodes, each density times the polynomial factor; the adjoint row by row).  0, 0: the
+     * Gaussian.  Otherwise BX_FP64 or BX_FP32, no 2D histograms, and the density must stay
+     * non-negative within band_sigmas. */
     double resp_skew, resp_kurt;
 } bx_model_desc;
 

@@ -237,11 +237,11 @@ static int model_create(const bx_model_desc* descs, int n_toys, const bx_options
         return bx_set_error(BX_EINVAL, "2D histograms need BX_FP32 or BX_BF16X3");
     if (!n2d && o.precision == BX_BF16X3)
         return bx_set_error(BX_EINVAL, "BX_BF16X3 is the 2D models' response GEMM (the 1D models: BX_TF32X3)");
-    for (int t = 0; t < n_toys; ++t) {   // the Gram-Charlier response: FP64, density >= 0 within the band
+    for (int t = 0; t < n_toys; ++t) {   // the Gram-Charlier response: FP64 or FP32, density >= 0 within the band
         const double g1 = descs[t].resp_skew / 6.0, g2 = descs[t].resp_kurt / 24.0;
         if (g1 == 0.0 && g2 == 0.0) continue;
-        if (o.precision != BX_FP64)
-            return bx_set_error(BX_EINVAL, "toy %d: the Gram-Charlier response needs BX_FP64", t);
+        if (o.precision != BX_FP64 && o.precision != BX_FP32)
+            return bx_set_error(BX_EINVAL, "toy %d: the Gram-Charlier response needs BX_FP64 or BX_FP32", t);
         for (int j = 0; j <= 4000; ++j) {
             const double z = o.band_sigmas * (j / 2000.0 - 1.0), z2 = z * z;
             if (1.0 + g1 * z * (z2 - 3.0) + g2 * (z2 * (z2 - 6.0) + 3.0) < 0.0)
@@ -448,9 +448,11 @@ static int model_create(const bx_model_desc* descs, int n_toys, const bx_options
     w.lam_pairs = m->precision == BX_FP32;
     w.multi_set = 0;
     w.nes = 1;
+    w.gc = 0;
     for (const Toy& T : m->toys_h) {
         w.multi_set |= T.n_set > 1 ? 1 : 0;
         w.nes = std::max(w.nes, T.n_es);
+        w.gc |= (T.gc1 != 0.0 || T.gc2 != 0.0) ? 1 : 0;
     }
     w.band = m->band;
     w.watchdog_ns = m->watchdog_ns;

@@ -178,7 +178,9 @@ __global__ void __launch_bounds__(BCOLS) k_bwd_f64(Work w) {
     block_sum_gp(g, red, gp);
 }
 
-template <bool MULTI, bool MES>
+// GC: the Gram-Charlier response, whose node sums are taken row by row (resp_adjoint32_gc): the
+// row recurrence of the Gaussian does not carry the polynomial factor.
+template <bool MULTI, bool MES, bool GC = false>
 __global__ void __launch_bounds__(BCOLS, 7) k_bwd_f32(Work w) {
     // 1D item-major grid (a y dimension would cap the batch at 65535 items)
     const int cb = blockIdx.x % w.max_cb, item = blockIdx.x / w.max_cb, tid = threadIdx.x;
@@ -254,9 +256,11 @@ __global__ void __launch_bounds__(BCOLS, 7) k_bwd_f32(Work w) {
     __shared__ float sW[BCOLS / 32][PACK ? 1 : NR][PACK ? 1 : 64];
     __shared__ float4 sW4[BCOLS / 32][PACK ? 64 : 1];
     double S0 = 0.0, S1 = 0.0, S2 = 0.0, Rs = 0.0, Rt = 0.0;
+    const float gc3 = GC ? (float)T.gc1 : 0.f, gc4 = GC ? (float)T.gc2 : 0.f;
     for (int c0 = wr0; c0 < wr1; c0 += RCH) {
         const int c1 = min(wr1, c0 + RCH);
         AdjSums bs;
+        float q0 = 0.f, q1 = 0.f, q2 = 0.f, qs = 0.f, qt = 0.f;   // GC: the chunk's node sums
         for (int s0 = c0; s0 < c1; s0 += 64) {
             const int ns = min(64, c1 - s0);
             for (int j = lane; j < ns; j += 32) {
@@ -269,7 +273,36 @@ __global__ void __launch_bounds__(BCOLS, 7) k_bwd_f32(Work w) {
                 }
             }
             __syncwarp();
-            if (ok) {
+            if (GC && ok) {   // row by row
+                for (int j = 0; j < ns; ++j) {
+                    float ws, wt, W;
+                    if constexpr (MES) {
+                        ws = sW[wq][0][j];
+                        wt = sW[wq][1][j];
+                        float a = 0.f;
+#pragma unroll
+                        for (int q = 0; q < MAX_ES; ++q)
+                            if (q < NES) a = fmaf(sW[wq][2 + q][j], SAq[q], a);
+                        W = fmaf(ws, Ssub, fmaf(wt, Stag, a));
+                    } else if constexpr (PACK) {
+                        const float4 rr = sW4[wq][j];
+                        ws = rr.x;
+                        wt = rr.y;
+                        W = fmaf(ws, Ssub, fmaf(wt, Stag, rr.z * SA));
+                    } else {
+                        ws = sW[wq][0][j];
+                        wt = sW[wq][1][j];
+                        W = fmaf(ws, Ssub, fmaf(wt, Stag, sW[wq][2][j] * SA));
+                    }
+                    float P0, P1, P2;
+                    resp_adjoint32_gc((float)(s0 + j), cf, cg, gc3, gc4, P0, P1, P2);
+                    q0 = fmaf(W, P0, q0);
+                    q1 = fmaf(W, P1, q1);
+                    q2 = fmaf(W, P2, q2);
+                    qs = fmaf(ws, P0, qs);
+                    qt = fmaf(wt, P0, qt);
+                }
+            } else if (ok) {
                 for (int j = 0; j < ns; j += ADJ_RUN) {
                     if constexpr (MES) {
                         auto wts = [&](int k, float& ws, float& wt, float& W) {
@@ -303,7 +336,15 @@ __global__ void __launch_bounds__(BCOLS, 7) k_bwd_f32(Work w) {
             __syncwarp();
         }
         float p0, p1, p2, ps, pt;
-        bs.node(cg.Ck2, ac.kk, p0, p1, p2, ps, pt);
+        if (GC) {
+            p0 = q0;
+            p1 = q1;
+            p2 = q2;
+            ps = qs;
+            pt = qt;
+        } else {
+            bs.node(cg.Ck2, ac.kk, p0, p1, p2, ps, pt);
+        }
         S0 += p0;
         S1 += p1;
         S2 += p2;
@@ -370,7 +411,12 @@ cudaError_t launch_bwd(const Work& w, int n, int max_cb, cudaStream_t s) {
         else k_bwd_f64<false><<<grid, BCOLS, 0, s>>>(w);
     } else {
         const bool mes = w.nes > 1;   // several energy slices of the Eq. 4 terms
-        if (w.multi_set && mes) k_bwd_f32<true, true><<<grid, BCOLS, 0, s>>>(w);
+        if (w.gc) {   // the Gram-Charlier response (one quenching group)
+            if (w.multi_set && mes) k_bwd_f32<true, true, true><<<grid, BCOLS, 0, s>>>(w);
+            else if (w.multi_set) k_bwd_f32<true, false, true><<<grid, BCOLS, 0, s>>>(w);
+            else if (mes) k_bwd_f32<false, true, true><<<grid, BCOLS, 0, s>>>(w);
+            else k_bwd_f32<false, false, true><<<grid, BCOLS, 0, s>>>(w);
+        } else if (w.multi_set && mes) k_bwd_f32<true, true><<<grid, BCOLS, 0, s>>>(w);
         else if (w.multi_set) k_bwd_f32<true, false><<<grid, BCOLS, 0, s>>>(w);
         else if (mes) k_bwd_f32<false, true><<<grid, BCOLS, 0, s>>>(w);
         else k_bwd_f32<false, false><<<grid, BCOLS, 0, s>>>(w);

@@ -45,7 +45,8 @@ __device__ __forceinline__ void kahan_fma(float& acc, float& cmp, float a, float
 // WPC: warps per CTA, 2 (a CTA = one 128-row tile) or 1 (a CTA = one warp's 64-row half of a
 // tile; the autotuner of the batched fits may pick it for small ragged items).  The warps of a
 // CTA never synchronise, so the two shapes do the same work per warp.
-template <bool TAG, bool COLS, bool MES, int WPC = 2>
+// GC: the Gram-Charlier response (resp_shape32_gc, the toy's skewness and kurtosis terms).
+template <bool TAG, bool COLS, bool MES, int WPC = 2, bool GC = false>
 __global__ void __launch_bounds__(32 * WPC) k_fwd_f32(Work w) {
     // 1D item-major grid (a y dimension would cap the batch at 65535 items)
     const int unit = WPC == 2 ? (int)blockIdx.x : (int)(blockIdx.x >> 1);
@@ -87,12 +88,17 @@ __global__ void __launch_bounds__(32 * WPC) k_fwd_f32(Work w) {
 
     // one column's entries of the lane's rows: both row groups (the common case: two
     // independent chains for the scheduler) or one of them
+    const float gc3 = GC ? (float)T.gc1 : 0.f, gc4 = GC ? (float)T.gc2 : 0.f;
+    auto shape = [&](auto wide_tag, float mf, const float4& cf, const ColG& cg) {
+        constexpr bool WIDE = decltype(wide_tag)::value;
+        if constexpr (GC) return resp_shape32_gc<WIDE>(mf, cf, cg, gc3, gc4);
+        else return resp_shape32<WIDE>(mf, cf, cg);
+    };
     auto column = [&](auto wide_tag, bool inA, bool inB, const float4& cf, const ColG& cg, const float4 S,
                       float& Ra, float& Rb) {
-        constexpr bool WIDE = decltype(wide_tag)::value;
         if (inA && inB) {
-            Ra = resp_shape32<WIDE>(mfa, cf, cg);
-            Rb = resp_shape32<WIDE>(mfb, cf, cg);
+            Ra = shape(wide_tag, mfa, cf, cg);
+            Rb = shape(wide_tag, mfb, cf, cg);
             kahan_fma(sa, csa, Ra, S.x, S.z);
             kahan_fma(sb, csb, Rb, S.x, S.z);
             if (TAG) {
@@ -100,11 +106,11 @@ __global__ void __launch_bounds__(32 * WPC) k_fwd_f32(Work w) {
                 kahan_fma(tb, ctb, Rb, S.y, S.w);
             }
         } else if (inA) {
-            Ra = resp_shape32<WIDE>(mfa, cf, cg);
+            Ra = shape(wide_tag, mfa, cf, cg);
             kahan_fma(sa, csa, Ra, S.x, S.z);
             if (TAG) kahan_fma(ta, cta, Ra, S.y, S.w);
         } else {
-            Rb = resp_shape32<WIDE>(mfb, cf, cg);
+            Rb = shape(wide_tag, mfb, cf, cg);
             kahan_fma(sb, csb, Rb, S.x, S.z);
             if (TAG) kahan_fma(tb, ctb, Rb, S.y, S.w);
         }
@@ -207,21 +213,22 @@ __global__ void __launch_bounds__(32 * WPC) k_fwd_f32(Work w) {
     }
 }
 
-template <int WPC>
+template <int WPC, bool GC = false>
 static void fwd_f32_variant(const Work& w, unsigned grid, int any_tag, int any_cols, bool mes, cudaStream_t s) {
     const unsigned g = grid * (2 / WPC);
-    if (any_tag && any_cols && mes) k_fwd_f32<true, true, true, WPC><<<g, 32 * WPC, 0, s>>>(w);
-    else if (any_cols && mes) k_fwd_f32<false, true, true, WPC><<<g, 32 * WPC, 0, s>>>(w);
-    else if (any_tag && any_cols) k_fwd_f32<true, true, false, WPC><<<g, 32 * WPC, 0, s>>>(w);
-    else if (any_tag) k_fwd_f32<true, false, false, WPC><<<g, 32 * WPC, 0, s>>>(w);
-    else if (any_cols) k_fwd_f32<false, true, false, WPC><<<g, 32 * WPC, 0, s>>>(w);
-    else k_fwd_f32<false, false, false, WPC><<<g, 32 * WPC, 0, s>>>(w);
+    if (any_tag && any_cols && mes) k_fwd_f32<true, true, true, WPC, GC><<<g, 32 * WPC, 0, s>>>(w);
+    else if (any_cols && mes) k_fwd_f32<false, true, true, WPC, GC><<<g, 32 * WPC, 0, s>>>(w);
+    else if (any_tag && any_cols) k_fwd_f32<true, true, false, WPC, GC><<<g, 32 * WPC, 0, s>>>(w);
+    else if (any_tag) k_fwd_f32<true, false, false, WPC, GC><<<g, 32 * WPC, 0, s>>>(w);
+    else if (any_cols) k_fwd_f32<false, true, false, WPC, GC><<<g, 32 * WPC, 0, s>>>(w);
+    else k_fwd_f32<false, false, false, WPC, GC><<<g, 32 * WPC, 0, s>>>(w);
 }
 
 cudaError_t launch_fwd_f32(const Work& w, int n, int max_tiles, int any_tag, int any_cols, cudaStream_t s) {
     const unsigned grid = (unsigned)n * (unsigned)w.max_tiles;   // decoded with w.max_tiles
     const bool mes = w.nes > 1;   // several energy slices of the Eq. 4 terms
-    if (w.fwd_wpc == 1) fwd_f32_variant<1>(w, grid, any_tag, any_cols, mes, s);
+    if (w.gc) fwd_f32_variant<2, true>(w, grid, any_tag, any_cols, mes, s);   // one tile shape for GC models
+    else if (w.fwd_wpc == 1) fwd_f32_variant<1>(w, grid, any_tag, any_cols, mes, s);
     else fwd_f32_variant<2>(w, grid, any_tag, any_cols, mes, s);
     return cudaGetLastError();
 }

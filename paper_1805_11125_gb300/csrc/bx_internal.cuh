@@ -118,6 +118,7 @@ struct Work {
                               // slice stride of aW, apart, rowW and coef
     int precision;
     int fwd_wpc;              // warps per CTA of the FP32 forward: 2 (0: default) or 1 (autotuner's choice)
+    int gc;                   // some toy has a Gram-Charlier response (the FP32 kernels' GC instantiations)
     double band;
     unsigned long long watchdog_ns;
     const Toy* toys;

@@ -368,7 +368,7 @@ __device__ void block_scan_df(df& a, df& b, df& ta, df& tb, float* sh) {
 // Z_F32 = 3 sigma (1/Phi, phi/Phi; FP32 tails beyond) and for the FP64 copies of mu, sigma, Q,
 // dQ/dkB that the adjoint's chain rule reads (formed on the integer pipe, f2d).  The window
 // masses come from FP32 tails and go out as FP32 pairs.
-template <bool MULTI>
+template <bool MULTI, bool GC = false>
 __global__ void __launch_bounds__(256, 3) k_prep32(Work w) {
     const int item = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
     if (w.skip && w.skip[item]) {
@@ -495,11 +495,16 @@ __global__ void __launch_bounds__(256, 3) k_prep32(Work w) {
             const double mud = df_to_double(mu), sigd = df_to_double(sig);
             double norm = 1.0, mills = 0.0;
             df normd{1.f, 0.f};
-            if (z.h < Z_F32) {
+            const bool gc = GC && (T.gc1 != 0.0 || T.gc2 != 0.0);   // Gram-Charlier: FP64 to Q_CUT (its terms)
+            if (z.h < Z_F32 || (gc && z.h < (float)Q_CUT)) {
                 const double zd = df_to_double(z);
-                const double Phi = zd > 0.0 ? 1.0 - upper_tail(zd) : upper_tail(-zd);
+                double Phi = zd > 0.0 ? 1.0 - upper_tail(zd) : upper_tail(-zd), dens = INV_SQRT_2PI * exp(-0.5 * zd * zd);
+                if (gc) {
+                    Phi += gc_cdf_term(T, -zd);
+                    dens *= gc_density_factor(T, -zd);
+                }
                 norm = 1.0 / Phi;
-                mills = INV_SQRT_2PI * exp(-0.5 * zd * zd) * norm;
+                mills = dens * norm;
                 normd = df_from(norm);
             } else if (z.h < (float)Q_CUT) {   // Q(z) <= 1.3e-3
                 const float q = upper_tail32(z.h), qn = q / (1.0f - q);
@@ -566,7 +571,14 @@ __global__ void __launch_bounds__(256, 3) k_prep32(Work w) {
             cs32[ie] = make_float4(As.h, At.h, As.l, At.l);
             // slice masses times 1/Phi, as FP32 pairs
             for (int q = 0; q < NES; ++q) {   // one mass per energy slice
-                const df aw = df_mul(slice_mass32(s_par[9 + q], s_par[10 + q], mu, isig), normd);
+                df aw;
+                if (gc) {   // Gram-Charlier: the mass in FP64 from the CDF F = Phi - phi C
+                    const double mudd = df_to_double(mu), isd = df_to_double(isig);
+                    const double za = (df_to_double(s_par[9 + q]) - mudd) * isd, zb = (df_to_double(s_par[10 + q]) - mudd) * isd;
+                    aw = df_from((gauss_mass(za, zb) - (gc_cdf_term(T, zb) - gc_cdf_term(T, za))) * norm);
+                } else {
+                    aw = df_mul(slice_mass32(s_par[9 + q], s_par[10 + q], mu, isig), normd);
+                }
                 aW2[(size_t)q * w.Npad + ie] = make_float2(aw.h, aw.l);
             }
             // response band
@@ -629,7 +641,10 @@ cudaError_t launch_prep(const Work& w, int n, cudaStream_t s) {
         if (w.multi_set) k_prep<true><<<n, 256, 0, s>>>(w);
         else k_prep<false><<<n, 256, 0, s>>>(w);
     } else {
-        if (w.multi_set) k_prep32<true><<<n, 256, 0, s>>>(w);
+        if (w.gc) {
+            if (w.multi_set) k_prep32<true, true><<<n, 256, 0, s>>>(w);
+            else k_prep32<false, true><<<n, 256, 0, s>>>(w);
+        } else if (w.multi_set) k_prep32<true><<<n, 256, 0, s>>>(w);
         else k_prep32<false><<<n, 256, 0, s>>>(w);
     }
     return cudaGetLastError();

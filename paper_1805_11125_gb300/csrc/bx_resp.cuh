@@ -119,6 +119,77 @@ __device__ __forceinline__ float resp_shape32(float mf, const float4& cf, const 
     return fmaf(GL_W_OUT, Sp, GL_W_MID * p0);
 }
 // Response entry R[m, i] of output bin `mf` and one column.
+// Gram-Charlier response (density phi(z) g(z), g = 1 + c3 He3(z) + c4 He4(z), c3 = skewness / 6,
+// c4 = excess kurtosis / 24): the same three nodes, each density times g at its standard score
+// z = t / S_EX2.  With Sp = p- + p+ and Sm = p- - p+ (p- at t0 - kk, p+ at t0 + kk):
+//   p- g- + p+ g+ = Sp (g- + g+) / 2 + Sm (g- - g+) / 2.
+__device__ __forceinline__ float gc_factor(float z, float c3, float c4) {
+    const float z2 = z * z;
+    return fmaf(c3, z * (z2 - 3.0f), fmaf(c4, fmaf(z2, z2 - 6.0f, 3.0f), 1.0f));
+}
+__device__ __forceinline__ float gc_slope(float z, float c3, float c4) {   // dg/dz = 3 c3 He2 + 4 c4 He3
+    const float z2 = z * z;
+    return fmaf(3.0f * c3, z2 - 1.0f, 4.0f * c4 * z * (z2 - 3.0f));
+}
+constexpr float INV_S_EX2 = 1.17741002251547469101f;   // 1 / S_EX2 = sqrt(2 ln 2)
+
+template <bool WIDE = false>
+__device__ __forceinline__ float resp_shape32_gc(float mf, const float4& cf, const ColG& cg, float c3, float c4) {
+    float th, tl;
+    centre_df(mf, cf, cg.c_lo, th, tl);
+    const float p0 = centre_node(th, tl);
+    const float z = cg.kap * th, kk = cg.kap * INV_2LN2;
+    float Sp, Sm;
+    if (WIDE || fabsf(z) <= 1.0f) {
+        const float q = z * z, f = p0 * cg.Ck2;
+        Sp = f * cosh_small(q);
+        Sm = f * sinh_small(z, q);
+    } else {
+        outer_direct(th, kk, Sp, Sm);
+    }
+    const float z0 = th * INV_S_EX2, d = kk * INV_S_EX2;
+    const float gm = gc_factor(z0 - d, c3, c4), gp = gc_factor(z0 + d, c3, c4);
+    const float outer = fmaf(Sp, gm + gp, Sm * (gm - gp)) * 0.5f;
+    return fmaf(GL_W_OUT, outer, GL_W_MID * p0 * gc_factor(z0, c3, c4));
+}
+
+// The adjoint node sums of the Gram-Charlier response for one row: with the standard score z of
+// each node, P0 = sum w p g, P1 = S_EX2 sum w p (z g - g'), P2 = S_EX2^2 sum w p (z^2 g - z g')
+// (g = 1 gives resp_adjoint32's sums), so that the chain rule of the Gaussian adjoint applies
+// unchanged: d(p g)/dmu ~ p (z g - g'), d(p g / sigma)/dsigma ~ p ((z^2 - 1) g - z g').
+__device__ __forceinline__ void resp_adjoint32_gc(float mf, const float4& cf, const ColG& cg, float c3, float c4,
+                                                  float& P0, float& P1, float& P2) {
+    float th, tl;
+    centre_df(mf, cf, cg.c_lo, th, tl);
+    const float p0 = centre_node(th, tl);
+    const float z = cg.kap * th, kk = cg.kap * INV_2LN2;
+    float Sp, Sm;
+    if (fabsf(z) <= 1.0f) {
+        const float q = z * z, f = p0 * cg.Ck2;
+        Sp = f * cosh_small(q);
+        Sm = f * sinh_small(z, q);
+    } else {
+        outer_direct(th, kk, Sp, Sm);
+    }
+    const float pm = 0.5f * (Sp + Sm), pp = 0.5f * (Sp - Sm);
+    const float z0 = th * INV_S_EX2, d = kk * INV_S_EX2, zm = z0 - d, zp = z0 + d;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    auto node = [&](float w, float p, float zz) {
+        const float g = gc_factor(zz, c3, c4), gs = gc_slope(zz, c3, c4);
+        const float a = fmaf(zz, g, -gs);    // z g - g'
+        s0 = fmaf(w * p, g, s0);
+        s1 = fmaf(w * p, a, s1);
+        s2 = fmaf(w * p, zz * a, s2);        // z^2 g - z g'
+    };
+    node(GL_W_MID, p0, z0);
+    node(GL_W_OUT, pm, zm);
+    node(GL_W_OUT, pp, zp);
+    constexpr float SE = 0.84932180028801904272f;   // S_EX2
+    P0 = s0;
+    P1 = SE * s1;
+    P2 = (SE * SE) * s2;
+}
+
 __device__ __forceinline__ float resp_exact32(float mf, const float4& cf, const ColG& cg) {
     return cg.A * resp_shape32(mf, cf, cg);
 }

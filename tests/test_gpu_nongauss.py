@@ -1,8 +1,11 @@
-"""The non-Gaussian (Gram-Charlier) response on the GPU (BX_FP64) against the oracle, through the
-C ABI: expected counts per bin (relative 1e-10), -lnL (|Delta(-2 lnL)| <= 1e-7) and gradient
+"""The non-Gaussian (Gram-Charlier) response on the GPU against the oracle, through the C ABI.
+BX_FP64: expected counts per bin (relative 1e-10), -lnL (|Delta(-2 lnL)| <= 1e-7) and gradient
 (|Delta g_j| |theta_j| <= 1e-9 (1 + |g_j theta_j|)) of the reduced and the full-size model,
-batch = single calls, the fit against the oracle's fit, and the rejections (FP32, a density
-that turns negative within the band)."""
+batch = single calls, the fit against the oracle's fit.  BX_FP32 (the generator's Gram-Charlier
+nodes, the row-by-row adjoint) with the mixed modes' bounds: per bin 1e-5 relative (1e-8 max(mu)
+absolute), mean signed per-bin error 1e-8, |Delta(-2 lnL)| <= 1e-3, gradient 1e-3 (1 + |g theta|),
+and its fit polished in FP64 against the oracle's.  The rejections (BX_TF32X3, a density that
+turns negative within the band)."""
 import dataclasses
 
 import numpy as np
@@ -17,10 +20,10 @@ pytestmark = pytest.mark.gpu
 _models = {}
 
 
-def model(name, max_batch=8):
-    key = (name, max_batch)
+def model(name, max_batch=8, prec=bx.BX_FP64):
+    key = (name, max_batch, prec)
     if key not in _models:
-        _models[key] = bx.Model(dataset(name), precision=bx.BX_FP64, max_batch=max_batch)
+        _models[key] = bx.Model(dataset(name), precision=prec, max_batch=max_batch)
     return _models[key]
 
 
@@ -91,10 +94,55 @@ def test_nongauss_fit_agrees_with_oracle():
     m.close()
 
 
+@pytest.mark.parametrize("name", ["small_nongauss", "nongauss"])
+def test_nongauss_fp32_expected_counts(name):
+    s = dataset(name)
+    m = model(name, prec=bx.BX_FP32)
+    for th in [s.theta_true] + list(points(s, 2, seed=124)):
+        mg, mo = m.expected(th), O.expected(s, th)
+        ok, wr, wa = per_bin_ok(mg, mo, rel=1e-5, abs_frac=1e-8)
+        assert ok, (wr, wa)
+        big = mo >= 1e-3 * mo.max()
+        assert abs(float(np.mean((mg[big] - mo[big]) / mo[big]))) <= 1e-8
+
+
+@pytest.mark.parametrize("name", ["small_nongauss", "nongauss"])
+def test_nongauss_fp32_nll_and_gradient(name):
+    s = dataset(name)
+    m = model(name, prec=bx.BX_FP32)
+    for th in [s.theta_true] + list(points(s, 2, seed=125)):
+        f, g = m.nll_grad(th)
+        fo, go = O.nll(s, th, grad=True)
+        assert 2 * abs(f - fo) <= 1e-3, (f, fo)
+        ok, worst = grad_ok(g[: s.P], go, th, tol=1e-3)
+        assert ok, worst
+
+
+def test_nongauss_fp32_fit_polished_in_fp64_agrees_with_oracle():
+    s = dataset("small_nongauss")
+    ref = O.fit(s, s.theta_true, tol_edm=1e-14)
+    m32 = bx.Model(s, precision=bx.BX_FP32, max_batch=2 * (8 + 2 * s.P))
+    m64 = bx.Model(s, precision=bx.BX_FP64, max_batch=2 * (8 + 2 * s.P))
+    th0 = I.parameter_points(s.theta_true, 2, rel=0.03, seed=126, free=s.default_free())
+    out32, info32, st32 = m32.fit(th0)
+    assert st32 == bx.BX_OK, info32
+    out, info, st = m64.fit(out32, tol_edm=1e-9)
+    free = s.default_free().astype(bool)
+    sig = np.sqrt(np.maximum(np.diag(ref["cov"]), 0.0))
+    tol = np.maximum(1e-4 * np.abs(ref["theta"]), 0.01 * sig)
+    for k in range(2):
+        assert info[k]["status"] == bx.BX_OK, info[k]
+        d = np.abs(out[k, : s.P] - ref["theta"])
+        assert np.all(d[free] <= tol[free]), (d[free] / tol[free]).max()
+        assert 2 * abs(info[k]["nll"] - ref["nll"]) <= 1e-3
+    m32.close()
+    m64.close()
+
+
 def test_nongauss_rejections():
     s = dataset("small_nongauss")
     with pytest.raises(bx.BxError) as e:
-        bx.Model(s, precision=bx.BX_FP32)
+        bx.Model(s, precision=bx.BX_TF32X3)
     assert e.value.status == bx.BX_EINVAL
     bad = dataclasses.replace(s, resp_skew=0.6, resp_kurt=0.0)   # 1 + 0.1 (z^3 - 3z) < 0 below z ~ -2.5
     with pytest.raises(bx.BxError) as e:
