@@ -617,7 +617,7 @@ def estimators_leg(bx, I, stream, B=912, steps=5):
 def differentiated_fit_leg(bx, I, stream, iters=1000):
     """The 2D discrimination model (22 parameters) minimised by a quasi-Newton method through the
     autograd interface: BFGS (inverse-Hessian updates, Armijo backtracking, box bounds by
-    projection) on scaled parameters, every value and gradient from bx.BxNLL -- the hand-written
+    projection with the active set held) on scaled parameters, every value and gradient from bx.BxNLL -- the hand-written
     adjoint behind torch.autograd.Function, the response regenerated in the adjoint kernel, never
     stored -- for up to `iters` iterations from theta_true (1 + 0.02 z); it stops early only when
     no step decreases -lnL any more (the FP32 noise floor).  Compared with the device Newton fit
@@ -656,10 +656,14 @@ def differentiated_fit_leg(bx, I, stream, iters=1000):
     Hinv = np.eye(s.P) * 1e-4
     it, fails = 0, 0
     while it < iters and fails < 3:
-        d = -Hinv @ g
-        if g @ d >= 0:
+        # active set: a parameter on a bound whose gradient points outward stays there this step
+        th = th0 + scale * u
+        held = (scale == 0) | ((th <= lo) & (g > 0)) | ((th >= hi) & (g < 0))
+        gp = np.where(held, 0.0, g)
+        d = np.where(held, 0.0, -Hinv @ gp)
+        if gp @ d >= 0:
             Hinv = np.eye(s.P) * 1e-4
-            d = -Hinv @ g
+            d = np.where(held, 0.0, -Hinv @ gp)
         a, ok = 1.0, False
         for _ in range(30):
             un = project(u + a * d)
@@ -673,7 +677,7 @@ def differentiated_fit_leg(bx, I, stream, iters=1000):
             Hinv = np.eye(s.P) * 1e-4
             continue
         fails = 0
-        sv, yv = un - u, gn - g
+        sv, yv = un - u, np.where(held, 0.0, gn - g)
         sy = sv @ yv
         if sy > 1e-30:
             rho = 1.0 / sy
