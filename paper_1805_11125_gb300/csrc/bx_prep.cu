@@ -551,21 +551,36 @@ __global__ void __launch_bounds__(256, 3) k_prep32(Work w) {
             // column's spectrum (shared by every row of its band) reaches the expected counts
             bool nz = false;   // a species of this group has support in the column
             df ss{0.f, 0.f}, st{0.f, 0.f};
-            for (int k = 0; k < K; ++k) {
-                if (MULTI && T.set_of[k] != grp) continue;
-                df sk;
-                if (T.shapes32) {   // the model's split copy
-                    sk.h = T.shapes32[(size_t)k * N + i];
-                    if (sk.h == 0.f) continue;
-                    sk.l = T.shapes32l[(size_t)k * N + i];
-                } else {            // a descriptor with FP64 shapes only
+            if (T.shapes32) {   // the model's split copy: four species' loads in flight at a time
+                for (int k0 = 0; k0 < K; k0 += 4) {
+                    float hv[4], lv[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int k = k0 + q;
+                        const bool use = k < K && (!MULTI || T.set_of[k] == grp);
+                        hv[q] = use ? T.shapes32[(size_t)k * N + i] : 0.f;
+                        lv[q] = use ? T.shapes32l[(size_t)k * N + i] : 0.f;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if (hv[q] == 0.f) continue;
+                        const int k = k0 + q;
+                        const df sk{hv[q], lv[q]};
+                        nz = true;
+                        ss = df_add(ss, df_mul(df{s_rate[0][k], s_rate[1][k]}, sk));
+                        st = df_add(st, df_mul(df{s_rate[2][k], s_rate[3][k]}, sk));
+                    }
+                }
+            } else {            // a descriptor with FP64 shapes only
+                for (int k = 0; k < K; ++k) {
+                    if (MULTI && T.set_of[k] != grp) continue;
                     const double x = T.shapes[(size_t)k * N + i];
                     if (x == 0.0) continue;
-                    sk = df_from(x);
+                    const df sk = df_from(x);
+                    nz = true;
+                    ss = df_add(ss, df_mul(df{s_rate[0][k], s_rate[1][k]}, sk));
+                    st = df_add(st, df_mul(df{s_rate[2][k], s_rate[3][k]}, sk));
                 }
-                nz = true;
-                ss = df_add(ss, df_mul(df{s_rate[0][k], s_rate[1][k]}, sk));
-                st = df_add(st, df_mul(df{s_rate[2][k], s_rate[3][k]}, sk));
             }
             const df As = df_mul(Ad, ss), At = df_mul(Ad, st);
             cs32[ie] = make_float4(As.h, At.h, As.l, At.l);
