@@ -220,23 +220,43 @@ __global__ void __launch_bounds__(BCOLS, 7) k_bwd_f32(Work w) {
     float SAq[MAX_ES] = {0.f, 0.f, 0.f, 0.f};   // MES: one sum per energy slice
     if constexpr (MES) {
         if (ok)
-            for (int k = 0; k < T.K; ++k) {
-                if (!in_group<MULTI>(T, k, grp)) continue;
-                const float sk = T.shapes32[(size_t)k * T.N + ig];
-                Ssub = fmaf(s_coef[0][k], sk, Ssub);
-                Stag = fmaf(s_coef[1][k], sk, Stag);
+            for (int k0 = 0; k0 < T.K; k0 += 4) {
+                float skv[4];
 #pragma unroll
-                for (int q = 0; q < MAX_ES; ++q)
-                    if (q < NES) SAq[q] = fmaf(s_coef[2 + q][k], sk, SAq[q]);
+                for (int q4 = 0; q4 < 4; ++q4) {
+                    const int k = k0 + q4;
+                    skv[q4] = (k < T.K && in_group<MULTI>(T, k, grp)) ? T.shapes32[(size_t)k * T.N + ig] : 0.f;
+                }
+#pragma unroll
+                for (int q4 = 0; q4 < 4; ++q4) {
+                    const int k = k0 + q4;
+                    if (k >= T.K) continue;
+                    const float sk = skv[q4];
+                    Ssub = fmaf(s_coef[0][k], sk, Ssub);
+                    Stag = fmaf(s_coef[1][k], sk, Stag);
+#pragma unroll
+                    for (int q = 0; q < MAX_ES; ++q)
+                        if (q < NES) SAq[q] = fmaf(s_coef[2 + q][k], sk, SAq[q]);
+                }
             }
     } else {
-        if (ok)
-            for (int k = 0; k < T.K; ++k) {
-                if (!in_group<MULTI>(T, k, grp)) continue;
-                const float sk = T.shapes32[(size_t)k * T.N + ig];
-                Ssub = fmaf(s_coef[0][k], sk, Ssub);
-                Stag = fmaf(s_coef[1][k], sk, Stag);
-                SA = fmaf(s_coef[2][k], sk, SA);
+        if (ok)   // four species' loads in flight at a time (a loop of load-then-use waits on each)
+            for (int k0 = 0; k0 < T.K; k0 += 4) {
+                float sk[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int k = k0 + q;
+                    sk[q] = (k < T.K && in_group<MULTI>(T, k, grp)) ? T.shapes32[(size_t)k * T.N + ig] : 0.f;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int k = k0 + q;
+                    if (k < T.K) {
+                        Ssub = fmaf(s_coef[0][k], sk[q], Ssub);
+                        Stag = fmaf(s_coef[1][k], sk[q], Stag);
+                        SA = fmaf(s_coef[2][k], sk[q], SA);
+                    }
+                }
             }
     }
     const float4 cf = ok ? w.colf[(size_t)item * w.Npad + i] : make_float4(0.f, 0.f, 0.f, 0.f);
