@@ -456,7 +456,8 @@ struct Kahan4 {
 };
 
 // Convolution out_j = sum_{d < dend} g[d] x[base + j - d], j < PR.  g: 16-byte aligned, zero
-// from L up to a multiple of PR; x readable (zero) from base - dend - 10 to base + PR - 1.
+// from L up to a multiple of PR; x readable (zero) from base - dend - 10 to base + PR - 1, and
+// x + base - 7 16-byte aligned (the four values entering per PR taps come as one float4).
 __device__ __forceinline__ void conv_block(const float* g, const float* x, int base, int dend, Kahan4& k) {
     float xw[2 * PR - 1];   // xw[t] = x[base - d0 - 3 + t]
 #pragma unroll
@@ -471,8 +472,11 @@ __device__ __forceinline__ void conv_block(const float* g, const float* x, int b
             for (int j = 0; j < PR; ++j) k.p[j] = fmaf(gg[t], xw[3 + j - t], k.p[j]);
 #pragma unroll
         for (int t = 2 * PR - 2; t >= PR; --t) xw[t] = xw[t - PR];
-#pragma unroll
-        for (int t = 0; t < PR; ++t) xw[t] = x[base - d0 - 7 + t];
+        const float4 xn = *reinterpret_cast<const float4*>(x + base - d0 - 7);   // 16-byte aligned (mid32_padl)
+        xw[0] = xn.x;
+        xw[1] = xn.y;
+        xw[2] = xn.z;
+        xw[3] = xn.w;
         if (++cnt == PBLK) {
             k.fold();
             cnt = 0;
@@ -482,7 +486,7 @@ __device__ __forceinline__ void conv_block(const float* g, const float* x, int b
 }
 
 // Correlation out_j = sum_{d0s <= d < dend} g[d] y[base + j + d], j < PR, d0s a multiple of
-// PR.  y readable (zero) from base + d0s to base + dend + 9.
+// PR.  y readable (zero) from base + d0s to base + dend + 9, y + base + 7 16-byte aligned.
 __device__ __forceinline__ void corr_block(const float* g, const float* y, int base, int d0s, int dend, Kahan4& k) {
     float yw[2 * PR - 1];   // yw[t] = y[base + d0 + t]
 #pragma unroll
@@ -497,8 +501,11 @@ __device__ __forceinline__ void corr_block(const float* g, const float* y, int b
             for (int j = 0; j < PR; ++j) k.p[j] = fmaf(gg[t], yw[j + t], k.p[j]);
 #pragma unroll
         for (int t = 0; t < PR - 1; ++t) yw[t] = yw[t + PR];
-#pragma unroll
-        for (int t = PR - 1; t < 2 * PR - 1; ++t) yw[t] = y[base + d0 + PR + t];
+        const float4 yn = *reinterpret_cast<const float4*>(y + base + d0 + 2 * PR - 1);   // aligned (mid32_padw)
+        yw[PR - 1] = yn.x;
+        yw[PR] = yn.y;
+        yw[PR + 1] = yn.z;
+        yw[PR + 2] = yn.w;
         if (++cnt == PBLK) {
             k.fold();
             cnt = 0;
@@ -508,11 +515,15 @@ __device__ __forceinline__ void corr_block(const float* g, const float* y, int b
 }
 
 // Zero padding of the pile-up operands in shared memory
-constexpr int PAD_LAM = 16;   // before each lambda row (and 4 after)
-constexpr int PAD_WV = 8;     // before each weight row (and 16 after)
-__host__ __device__ constexpr int mid32_lrow(int M) { return PAD_LAM + M + 4; }
-__host__ __device__ constexpr int mid32_wrow(int nw) { return PAD_WV + nw + 16; }
+// (at least 16 / 8 before each lambda / weight row, chosen by the item's m_lo so that the window
+// values conv_block and corr_block fetch per four taps start on a 16-byte boundary; rows of a
+// multiple of four floats, at least 4 / 16 zeros after)
+__host__ __device__ constexpr int mid32_padl(int m_lo) { return 16 + ((7 - m_lo) & 3); }
+__host__ __device__ constexpr int mid32_padw(int m_lo) { return 8 + ((m_lo + 1) & 3); }
+__host__ __device__ constexpr int mid32_lrow(int M) { return (19 + M + 4 + 3) & ~3; }
+__host__ __device__ constexpr int mid32_wrow(int nw) { return (11 + nw + 16 + 3) & ~3; }
 __host__ __device__ constexpr int mid32_gn(int L) { return ((L + PR - 1) / PR) * PR + PR; }
+__host__ __device__ constexpr int mid32_pun(int nw) { return (2 * nw + 3) & ~3; }   // the [2][nw] pile-up part
 
 // Baker-Cousins term from double-float n and mu in double-float (bc_term_far: ln(n/mu) to
 // ~2e-11, so a term's absolute error is ~2e-11 n |n/mu - 1|); the term goes into a compensated
@@ -561,11 +572,12 @@ __global__ void __launch_bounds__(MID_THREADS, 2) k_mid32(Work w, int want_grad,
     const float2* lamg = reinterpret_cast<const float2*>(w.lam + (size_t)item * 2 * w.Mpad);
 
     const int lrow = mid32_lrow(M), wrow = mid32_wrow(nw), gn = mid32_gn(L);
+    const int padl = mid32_padl(m_lo), padw = mid32_padw(m_lo);
     float2* muw = reinterpret_cast<float2*>(dsm);          // [H][nw] mu as FP32 pairs
     float* gT = reinterpret_cast<float*>(muw + 2 * nw);     // [gn] g, zero-padded (16-byte aligned)
     float* lamP = gT + gn;                                  // [H][lrow] FP32 lambda, zero-padded
     float* puT = lamP + 2 * lrow;                           // [H][nw] pile-up convolution part
-    float* wvP = puT + 2 * nw;                              // [H][wrow] 1 - n/mu, zero-padded
+    float* wvP = puT + mid32_pun(nw);                       // [H][wrow] 1 - n/mu, zero-padded (16-byte aligned)
     float2* colGW = reinterpret_cast<float2*>(wvP + 2 * wrow);   // [Next] G_W per column (8-byte aligned)
     float* coldG = reinterpret_cast<float*>(colGW + T.Next);     // [Next] dG_W/deps per column
 
@@ -588,7 +600,7 @@ __global__ void __launch_bounds__(MID_THREADS, 2) k_mid32(Work w, int want_grad,
     }
     for (int d = tid; d < gn; d += MID_THREADS) gT[d] = d < L ? T.g32[d] : 0.f;
     for (int q = tid; q < 2 * lrow; q += MID_THREADS) {
-        const int h = q / lrow, m = q % lrow - PAD_LAM;
+        const int h = q / lrow, m = q % lrow - padl;
         lamP[q] = (h < H && m >= 0 && m < M) ? lamg[(size_t)h * w.Mpad + m].x : 0.f;
     }
     for (int q = tid; q < 2 * wrow; q += MID_THREADS) wvP[q] = 0.f;
@@ -602,7 +614,7 @@ __global__ void __launch_bounds__(MID_THREADS, 2) k_mid32(Work w, int want_grad,
     for (int q = tid; q < H * ngw; q += MID_THREADS) {
         const int h = q / ngw, j0 = (q % ngw) * PR, m0 = m_lo + j0;
         Kahan4 k;
-        conv_block(gT, lamP + h * lrow + PAD_LAM, m0, min(L, m0 + PR), k);
+        conv_block(gT, lamP + h * lrow + padl, m0, min(L, m0 + PR), k);
 #pragma unroll
         for (int j = 0; j < PR; ++j)
             if (j0 + j < nw) {
@@ -714,8 +726,8 @@ __global__ void __launch_bounds__(MID_THREADS, 2) k_mid32(Work w, int want_grad,
         if (want_grad) {
             if (b < nwin) {
                 const int h = b / nw, j = b % nw;
-                wvP[h * wrow + PAD_WV + j] = wb;
-                geps = fmaf(wb, puT[b] - lamP[h * lrow + PAD_LAM + m_lo + j], geps);
+                wvP[h * wrow + padw + j] = wb;
+                geps = fmaf(wb, puT[b] - lamP[h * lrow + padl + m_lo + j], geps);
             } else if (b < nwin + nradS) s_wr[b - nwin] = (double)wb;
             else s_wp[b - nwin - nradS] = (double)wb;
         }
@@ -767,7 +779,7 @@ __global__ void __launch_bounds__(MID_THREADS, 2) k_mid32(Work w, int want_grad,
     for (int q = tid; q < H * ngm; q += MID_THREADS) {
         const int h = q / ngm, m0 = (q % ngm) * PR, base = m0 - m_lo;   // window index at d = 0
         const int d0s = max(0, -(base + PR - 1)) / PR * PR, dend = min(L, nw - base);
-        const float* wh = wvP + h * wrow + PAD_WV;
+        const float* wh = wvP + h * wrow + padw;
         Kahan4 k;
         if (dend > d0s) corr_block(gT, wh, base, d0s, dend, k);
 #pragma unroll
@@ -844,7 +856,7 @@ static size_t mid_dynamic_smem(const Work& w, int Mmax, int nwmax, int Lmax) {
     // k_mid32: mu pairs [2][nw], g, lambda rows, pile-up part [2][nw], weight rows (zero-padded),
     // G_W and dG_W/deps per column
     return (size_t)2 * nwmax * sizeof(float2) +
-           (size_t)(mid32_gn(Lmax) + 2 * mid32_lrow(Mmax) + 2 * nwmax + 2 * mid32_wrow(nwmax)) * sizeof(float) +
+           (size_t)(mid32_gn(Lmax) + 2 * mid32_lrow(Mmax) + mid32_pun(nwmax) + 2 * mid32_wrow(nwmax)) * sizeof(float) +
            (size_t)w.Npad * (sizeof(float2) + sizeof(float));
 }
 
