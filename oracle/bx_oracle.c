@@ -16,6 +16,11 @@
  *       with species-specific quenching (the "next" response variant: alpha or gamma
  *       species quench differently) species k uses kB quench[k]; the species are grouped by
  *       multiplier and every group has its own map and response (a2)
+ *       with a position-dependent response (the "next" response variant; reading: the light
+ *       yield depends on where in the detector an event happens, the fiducial volume is cut
+ *       into radial shells, shell rho has the light yield LY f_rho, and species k puts the
+ *       fixed fraction q_k[rho] of its events into shell rho) every shell has its own map and
+ *       response, and v_k[m] = sum_rho q_k[rho] sum_i R_rho[m,i] s_k[i] in a3
  *   a2  response of Eq. 1, bin-integrated Gaussian in npe, normalised to the mass above 0:
  *         R[m,i] = (Phi(z_{m+1,i}) - Phi(z_{m,i})) / Phi(mu_i / sigma_i),
  *         z_{m,i} = (m w - mu_i) / sigma_i
@@ -127,6 +132,10 @@ typedef struct {
                                           energy window of the events in radial bin rho and pulse-shape
                                           bin j (the energy x radius x pulse-shape histogram); field
                                           [n_grid][n_r2 n_p2], counts in n_r2_counts [n_r2 n_p2][nw] */
+    int n_shell;                       /* position-dependent response: radial shells (0: none) */
+    const double* shell_ly;            /* [n_shell] light-yield factor f_rho of each shell (> 0) */
+    const double* shell_frac;          /* [K][n_shell] fraction q_k[rho] of species k's events in
+                                          shell rho (>= 0) */
 } om_model;
 
 /* Gram-Charlier (type A) response (reading: the non-Gaussian response of the paper's outlook,
@@ -210,6 +219,17 @@ static int check_model(const om_model* m) {
         if (n == 0 || (n > 1 && m->n_r2 + m->n_p2 > 0)) return OM_EINVAL;   /* 2D slices: one set only */
     }
     if (m->n_es < 0 || (m->n_es > 0 && (!m->es_edges || m->n_r2 + m->n_p2 > 0))) return OM_EINVAL;
+    if (m->n_shell < 0 || m->n_shell > OM_MAX_SETS) return OM_EINVAL;
+    if (m->n_shell > 0) {   /* shells: 1D histograms and one Birks multiplier only */
+        if (!m->shell_ly || !m->shell_frac || m->n_r2 + m->n_p2 > 0) return OM_EINVAL;
+        double xi[OM_MAX_SETS];
+        int set_of[OPMAX];
+        if (quench_sets(m, xi, set_of) != 1) return OM_EINVAL;
+        for (int r = 0; r < m->n_shell; ++r)
+            if (!(m->shell_ly[r] > 0.0) || !isfinite(m->shell_ly[r])) return OM_EINVAL;
+        for (int j = 0; j < m->K * m->n_shell; ++j)
+            if (!(m->shell_frac[j] >= 0.0) || !isfinite(m->shell_frac[j])) return OM_EINVAL;
+    }
     if (m->n_es > 0) {   /* the slices partition the window */
         if (m->es_edges[0] != 0 || m->es_edges[m->n_es] != m->m_hi - m->m_lo) return OM_EINVAL;
         for (int q = 0; q < m->n_es; ++q)
@@ -293,11 +313,12 @@ typedef struct {
 
 static void work_free(work* w) { free(w->Q); free(w->mu); free(w->sig); free(w->den); free(w->v); }
 
-/* a1: quenching + light yield + resolution for the species of Birks multiplier xi (kB xi);
- * returns OM_EDOMAIN if sigma^2 <= 0 anywhere. */
-static int stage_a1(const om_model* m, const dual* th, work* w, double xi) {
+/* a1: quenching + light yield + resolution for the species of Birks multiplier xi (kB xi),
+ * light yield LY f (f: the factor of a radial shell, else 1); returns OM_EDOMAIN if
+ * sigma^2 <= 0 anywhere. */
+static int stage_a1(const om_model* m, const dual* th, work* w, double xi, double f) {
     int N = m->n_grid, K = m->K;
-    dual LY = th[K], a = th[K + 1], b = th[K + 2], c = th[K + 3], kB = dscale(th[K + 4], xi);
+    dual LY = dscale(th[K], f), a = th[K + 1], b = th[K + 2], c = th[K + 3], kB = dscale(th[K + 4], xi);
     double dE = m->e_max / N;
     dual run = dc(0.0);
     int st = OM_OK;
@@ -316,14 +337,16 @@ static int stage_a1(const om_model* m, const dual* th, work* w, double xi) {
 
 /* a2 + a3: v_k[m] = sum_i R[m,i] s_k[i] for every m in [0, m_hi) and the species of set c
  * (set_of NULL: every species); with 2D slices also Y[m][b] = sum_i R[m,i] T_r[i][b]
- * (T_r: [N][B2], Y: [M][B2]). */
-static void stage_a23(const om_model* m, work* w, double* R_out, const dual* Tr, dual* Y, const int* set_of, int c) {
+ * (T_r: [N][B2], Y: [M][B2]).  Radial shell rho >= 0 (R the shell's response): every species
+ * k gets q_k[rho] sum_i R[m,i] s_k[i] added to v_k[m] (zeroed at rho = 0). */
+static void stage_a23(const om_model* m, work* w, double* R_out, const dual* Tr, dual* Y, const int* set_of, int c,
+                      int rho) {
     int N = m->n_grid, K = m->K, M = m->m_hi, B2 = n_slices2(m);
     #pragma omp parallel for schedule(dynamic, 4)
     for (int r = 0; r < M; ++r) {
         dual* vr = w->v + (size_t)r * K;
         for (int k = 0; k < K; ++k)
-            if (!set_of || set_of[k] == c) vr[k] = dc(0.0);
+            if (rho < 0 ? (!set_of || set_of[k] == c) : rho == 0) vr[k] = dc(0.0);
         if (Y) for (int b = 0; b < B2; ++b) Y[(size_t)r * B2 + b] = dc(0.0);
         for (int i = 0; i < N; ++i) {
             dual za = ddiv(dsub(dc(r * m->width), w->mu[i]), w->sig[i]);
@@ -331,8 +354,9 @@ static void stage_a23(const om_model* m, work* w, double* R_out, const dual* Tr,
             dual R = ddiv(resp_mass(m, za, zb), w->den[i]);
             if (R_out) R_out[(size_t)r * N + i] = R.v;
             for (int k = 0; k < K; ++k) {
-                if (set_of && set_of[k] != c) continue;
+                if (rho < 0 && set_of && set_of[k] != c) continue;
                 double s = m->shapes[(size_t)k * N + i];
+                if (rho >= 0) s *= m->shell_frac[(size_t)k * m->n_shell + rho];
                 if (s != 0.0) daxpy(&vr[k], s, &R);
             }
             if (Y)
@@ -452,10 +476,18 @@ static int evaluate(const om_model* m, const double* theta, int want_grad,
         int set_of[OPMAX];
         const int nset = quench_sets(m, xi, set_of);
         if (B2 > 0 && (st = stage_2d_templates(m, th, Tr))) goto done;
-        for (int c = 0; c < nset; ++c) {   /* one Birks map and response per set of species */
-            st = stage_a1(m, th, &w, xi[c]);
-            if (st) goto done;
-            stage_a23(m, &w, NULL, Tr, Y, set_of, c);
+        if (m->n_shell > 0) {
+            for (int r = 0; r < m->n_shell; ++r) {   /* one light-yield map and response per shell */
+                st = stage_a1(m, th, &w, 1.0, m->shell_ly[r]);
+                if (st) goto done;
+                stage_a23(m, &w, NULL, NULL, NULL, NULL, 0, r);
+            }
+        } else {
+            for (int c = 0; c < nset; ++c) {   /* one Birks map and response per set of species */
+                st = stage_a1(m, th, &w, xi[c], 1.0);
+                if (st) goto done;
+                stage_a23(m, &w, NULL, Tr, Y, set_of, c, -1);
+            }
         }
     }
 
@@ -570,7 +602,7 @@ int om_quench(const om_model* m, const double* theta, double* Q, double* mu, dou
     for (int j = 0; j < K + 7; ++j) th[j] = dc(theta[j]);
     work w; memset(&w, 0, sizeof w);
     w.Q = calloc(N, sizeof(dual)); w.mu = calloc(N, sizeof(dual)); w.sig = calloc(N, sizeof(dual)); w.den = calloc(N, sizeof(dual));
-    st = stage_a1(m, th, &w, 1.0);   /* the map of unit Birks multiplier */
+    st = stage_a1(m, th, &w, 1.0, 1.0);   /* the map of unit Birks multiplier */
     for (int i = 0; i < N; ++i) {
         if (Q) Q[i] = w.Q[i].v;
         if (mu) mu[i] = w.mu[i].v;
@@ -596,8 +628,8 @@ int om_response(const om_model* m, const double* theta, double* R, double* v) {
     int set_of[OPMAX];
     const int nset = quench_sets(m, xi, set_of);
     for (int c = 0; c < nset && !st; ++c) {   /* R of the first set */
-        st = stage_a1(m, th, &w, xi[c]);
-        if (!st) stage_a23(m, &w, c == 0 ? R : NULL, NULL, NULL, set_of, c);
+        st = stage_a1(m, th, &w, xi[c], 1.0);
+        if (!st) stage_a23(m, &w, c == 0 ? R : NULL, NULL, NULL, set_of, c, -1);
     }
     if (!st && v) for (size_t j = 0; j < (size_t)M * K; ++j) v[j] = w.v[j].v;
     work_free(&w);

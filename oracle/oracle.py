@@ -66,6 +66,7 @@ class _Model(C.Structure):
         ("n_es", C.c_int), ("es_edges", C.c_void_p),
         ("gc_skew", C.c_double), ("gc_kurt", C.c_double),
         ("joint2", C.c_int),
+        ("n_shell", C.c_int), ("shell_ly", C.c_void_p), ("shell_frac", C.c_void_p),
     ]
 
 
@@ -115,6 +116,8 @@ class OracleModel:
             "n_p2": _arr(s.counts.get("p2d")),
             "quench": _arr(getattr(s, "quench", None)),
             "es_edges": _arr(getattr(s, "eslices", None), np.int32),
+            "shell_ly": _arr(getattr(s, "shell_ly", None)),
+            "shell_frac": _arr(getattr(s, "shell_frac", None)),
         }
         k = self._keep
         has_rad = s.rad_class is not None and s.n_rad > 0
@@ -129,7 +132,9 @@ class OracleModel:
             n_r2_counts=_ptr(k["n_r2"]), n_p2_counts=_ptr(k["n_p2"]), quench=_ptr(k["quench"]),
             n_es=0 if k["es_edges"] is None else len(k["es_edges"]) - 1, es_edges=_ptr(k["es_edges"]),
             gc_skew=getattr(s, "resp_skew", 0.0), gc_kurt=getattr(s, "resp_kurt", 0.0),
-            joint2=1 if getattr(s, "joint2d", False) else 0)
+            joint2=1 if getattr(s, "joint2d", False) else 0,
+            n_shell=0 if k["shell_ly"] is None else len(k["shell_ly"]), shell_ly=_ptr(k["shell_ly"]),
+            shell_frac=_ptr(k["shell_frac"]))
         self.ref = C.byref(self.c)
 
     @property

@@ -90,6 +90,11 @@ class ModelSpec:
     # (0, 0: the Gaussian of Eq. 1)
     resp_skew: float = 0.0
     resp_kurt: float = 0.0
+    # position-dependent response: the fiducial volume in radial shells, shell rho with the light
+    # yield LY shell_ly[rho]; species k puts the fraction shell_frac[k, rho] of its events there
+    # (None: one response for the whole volume)
+    shell_ly: Optional[np.ndarray] = None
+    shell_frac: Optional[np.ndarray] = None
     theta_true: Optional[np.ndarray] = None
     species: List[str] = dataclasses.field(default_factory=list)
     counts: Dict[str, np.ndarray] = dataclasses.field(default_factory=dict)
@@ -357,6 +362,25 @@ def quenched(alpha_true: float = 2.3, alpha_quench: float = 150.0, gamma_quench:
     return spec
 
 
+def shelled(ly=(1.03, 1.01, 0.99, 0.97), name: str = "shelled", **kw) -> ModelSpec:
+    """The multivariate model with a position-dependent response: the fiducial sphere in
+    len(ly) shells of equal volume, the light yield LY ly[rho] in shell rho (falling towards the
+    vessel).  Internal species fill the shells in proportion to their volume (a fraction
+    1/len(ly) each); external species follow the density exp(-(r_iv - r) / att_len) of the
+    radial term at s_r = 1, integrated over each shell by the midpoint rule on 4000 points."""
+    spec = multivariate(name=name, **kw)
+    n = len(ly)
+    edges = spec.r_fid * (np.arange(n + 1) / n) ** (1.0 / 3.0)
+    r = (np.arange(4000) + 0.5) * (spec.r_fid / 4000)
+    dens = r * r * np.exp(-(spec.r_iv - r) / spec.att_len)
+    ext = np.array([dens[(r >= edges[j]) & (r < edges[j + 1])].sum() for j in range(n)])
+    ext /= ext.sum()
+    frac = np.where((spec.rad_class == RAD_EXTERNAL)[:, None], ext[None, :], 1.0 / n)
+    spec.shell_ly = np.asarray(ly, dtype=np.float64)
+    spec.shell_frac = np.ascontiguousarray(frac, dtype=np.float64)
+    return spec
+
+
 def sliced(edges_npe=(100.0, 250.0, 500.0, 1000.0), name: str = "sliced", **kw) -> ModelSpec:
     """The multivariate model with Eq. 4's radial and pulse-shape terms in several energy
     slices: one radial and one pulse-shape histogram of the TFC-vetoed events per slice of
@@ -471,6 +495,9 @@ def config(name: str) -> ModelSpec:
                   ``small_joint`` its reduced grid with 6 x 5 slices.
     * ``nongauss`` the multivariate model with a non-Gaussian (Gram-Charlier) response of
                   skewness 0.1 and excess kurtosis 0.1; ``small_nongauss`` its reduced grid.
+    * ``shelled``  the multivariate model with a position-dependent response: four radial shells
+                  of equal volume with light yields 1.03, 1.01, 0.99, 0.97 LY; ``small_shelled``
+                  its reduced grid.
     * ``small_plain`` / ``small_mv`` / ``small_2d`` reduced grids that the oracle evaluates in
       well under a second (a few seconds for ``small_2d``) but that still span several
       128-row tiles and ragged tails.
@@ -508,6 +535,11 @@ def config(name: str) -> ModelSpec:
         return dataclasses.replace(multivariate(n_grid=520, width=3.0, lo_npe=120.0, hi_npe=900.0, n_species=9,
                                                 total=3e5, L=90, n_rad=20, n_psd=16, name=name),
                                    resp_skew=0.1, resp_kurt=0.1)
+    if name == "shelled":
+        return shelled(name=name)
+    if name == "small_shelled":
+        return shelled(n_grid=520, width=3.0, lo_npe=120.0, hi_npe=900.0, n_species=9, total=3e5, L=90,
+                       n_rad=20, n_psd=16, name=name)
     if name == "small_quenched":
         return quenched(n_grid=520, width=3.0, lo_npe=120.0, hi_npe=900.0, n_species=12, total=3e5, L=90,
                         n_rad=20, n_psd=16, gamma_quench=1.3, name=name)

@@ -824,3 +824,107 @@ def test_gram_charlier_dual_gradient_matches_central_differences():
         tm[p] -= h
         fd = (O.nll(s, tp) - O.nll(s, tm)) / (2 * h)
         assert abs(fd - g[p]) * abs(th[p]) <= 1e-6 * (1 + abs(g[p] * th[p])), (p, fd, g[p])
+
+
+# ------------------------------------------------------- position-dependent response (shells)
+
+def _shell_spec(counts=True):
+    s = I.config("small_shelled")
+    if counts:
+        s = s.with_counts(I.poisson_counts(O.expected(s, s.theta_true), 21))
+    return s
+
+
+def test_shells_of_unit_light_yield_are_the_base_model():
+    """Shells whose light-yield factors are all 1 and whose fractions sum to 1 for every species
+    give every bin, -lnL and gradient of the model without shells (the shells' responses are
+    then identical, so only the summation order differs)."""
+    s = _shell_spec()
+    base = dataclasses.replace(s, shell_ly=None, shell_frac=None)
+    fr = np.tile([0.3, 0.7], (s.K, 1))
+    flat = dataclasses.replace(s, shell_ly=np.ones(2), shell_frac=fr)
+    th = I.parameter_points(s.theta_true, 1, rel=0.02, seed=61, free=s.default_free())[0]
+    mb = O.expected(base, th)
+    np.testing.assert_allclose(O.expected(flat, th), mb, rtol=1e-13, atol=1e-15 * mb.max())
+    fb, gb = O.nll(base, th, grad=True)
+    ff, gf = O.nll(flat, th, grad=True)
+    assert ff == pytest.approx(fb, rel=1e-13)
+    np.testing.assert_allclose(gf, gb, rtol=1e-9, atol=1e-9 * np.abs(gb).max())
+
+
+def test_one_shell_is_a_rescaled_light_yield():
+    """One shell of light-yield factor f holding every event is the base model with LY replaced by
+    f LY: the same bins and -lnL, the same gradient in every parameter but LY, and f times the
+    base model's LY derivative (mu = f LY Q)."""
+    s = _shell_spec()
+    f = 1.07
+    one = dataclasses.replace(s, shell_ly=np.array([f]), shell_frac=np.ones((s.K, 1)))
+    base = dataclasses.replace(s, shell_ly=None, shell_frac=None)
+    th = I.parameter_points(s.theta_true, 1, rel=0.02, seed=62, free=s.default_free())[0]
+    th2 = th.copy()
+    th2[tail(s, "LY")] *= f
+    np.testing.assert_allclose(O.expected(one, th), O.expected(base, th2), rtol=1e-13, atol=0)
+    f1, g1 = O.nll(one, th, grad=True)
+    f2, g2 = O.nll(base, th2, grad=True)
+    assert f1 == pytest.approx(f2, rel=1e-14)
+    scale = np.ones(s.P)
+    scale[tail(s, "LY")] = f
+    np.testing.assert_allclose(g1, scale * g2, rtol=1e-12, atol=1e-12 * np.abs(g2).max())
+
+
+def test_shells_decompose_into_base_models():
+    """Expected counts are linear in the rates and in each species' spectrum, so a model with
+    three shells and species-dependent fractions is the sum, over species k and shell rho, of
+    q_k[rho] times the base model with LY scaled by the shell's factor and only r_k kept (every
+    bin: vetoed, tagged, radial, pulse shape)."""
+    s = _shell_spec(counts=False)
+    rng = np.random.default_rng(63)
+    ly = np.array([1.05, 1.0, 0.93])
+    fr = rng.uniform(0.0, 1.0, (s.K, 3))
+    fr[0] = [1.0, 0.0, 0.0]
+    fr[1] = [0.0, 0.0, 2.0]
+    shells = dataclasses.replace(s, shell_ly=ly, shell_frac=fr)
+    base = dataclasses.replace(s, shell_ly=None, shell_frac=None)
+    th = s.theta_true.copy()
+    total = np.zeros(s.n_bins_total)
+    for k in range(s.K):
+        for r in range(3):
+            if fr[k, r] == 0.0:
+                continue
+            t = th.copy()
+            t[: s.K] = np.where(np.arange(s.K) == k, th[: s.K], 0.0)
+            t[tail(s, "LY")] = th[tail(s, "LY")] * ly[r]
+            total += fr[k, r] * O.expected(base, t)
+    np.testing.assert_allclose(O.expected(shells, th), total, rtol=1e-12, atol=1e-12 * total.max())
+
+
+def test_shells_dual_gradient_matches_central_differences():
+    s = _shell_spec()
+    th = I.parameter_points(s.theta_true, 1, rel=0.02, seed=64, free=s.default_free())[0]
+    f, g = O.nll(s, th, grad=True)
+    ext = int(np.nonzero(s.rad_class == I.RAD_EXTERNAL)[0][0])
+    for p in [0, ext, tail(s, "LY"), tail(s, "a"), tail(s, "c"), tail(s, "kB"), tail(s, "eps")]:
+        h = 1e-5 * abs(th[p])
+        tp, tm = th.copy(), th.copy()
+        tp[p] += h
+        tm[p] -= h
+        fd = (O.nll(s, tp) - O.nll(s, tm)) / (2 * h)
+        assert abs(fd - g[p]) * abs(th[p]) <= 1e-6 * (1 + abs(g[p] * th[p])), (p, fd, g[p])
+
+
+@pytest.mark.parametrize("bad", ["ly0", "frac_neg", "quench", "2d"])
+def test_bad_shells_are_rejected(bad):
+    s = _shell_spec(counts=False)
+    if bad == "ly0":
+        s = dataclasses.replace(s, shell_ly=np.array([1.0, 0.0, 1.0, 1.0]))
+    elif bad == "frac_neg":
+        fr = s.shell_frac.copy()
+        fr[2, 1] = -0.1
+        s = dataclasses.replace(s, shell_frac=fr)
+    elif bad == "quench":
+        s = dataclasses.replace(s, quench=np.where(np.arange(s.K) == 0, 2.0, 1.0))
+    else:
+        d = I.config("small_2d")
+        s = dataclasses.replace(d, shell_ly=np.ones(2), shell_frac=np.full((d.K, 2), 0.5))
+    with pytest.raises(RuntimeError):
+        O.expected(s, s.theta_true)
