@@ -280,6 +280,8 @@ def run_ours(args):
         fits["sliced"] = variant_leg(bx, I, "sliced", SLICED, stream, B=args.batch) if args.sliced else None
         fits["nongauss"] = (variant_leg(bx, I, "nongauss", NONGAUSS, stream, B=args.batch)
                             if args.nongauss else None)
+        fits["shelled"] = (variant_leg(bx, I, "shelled", SHELLED, stream, B=args.batch)
+                           if args.shelled else None)
         fits["joint_3d"] = (discrimination_leg(bx, I, stream, B=args.batch2d, name="joint", workload=JOINT,
                                                n_slices=120, resp_ceiling=rc)
                             if args.joint and args.batch2d > 0 else None)
@@ -472,12 +474,16 @@ QUENCHED = ("multivariate with species-specific quenching (alpha at 2.3 MeV, 150
 SLICED = ("multivariate with the radial and pulse-shape terms in 3 energy slices (100-250, 250-500, "
           "500-1000 npe): 3 x (60 radial + 50 pulse-shape) bins")
 NONGAUSS = ("multivariate with a Gram-Charlier photoelectron response (skewness 0.1, excess kurtosis 0.1)")
+SHELLED = ("multivariate with a position-dependent response: 4 equal-volume radial shells of light yield "
+           "1.03, 1.01, 0.99, 0.97 LY (internal species 1/4 per shell, external near the vessel), "
+           "4 x 2000 response columns")
 
 
 def variant_leg(bx, I, name, workload, stream, B=2736, steps=5):
     """A variant of the multivariate model (species-specific quenching: the alpha species at
     2.3 MeV true energy quenched with 150 kB, with its own Birks map and response columns; the
-    Eq. 4 terms in several energy slices; or a Gram-Charlier response): -lnL + gradient
+    Eq. 4 terms in several energy slices; a Gram-Charlier response; or a position-dependent
+    response in four radial shells, each with its own columns): -lnL + gradient
     evaluations/s at the main leg's batch, FP32, and one FP32 fit."""
     import torch
     s = make_dataset(bx, I, I.config(name), seed=0)
@@ -816,6 +822,7 @@ def main():
     ap.add_argument("--sliced", type=int, default=1, help="energy-sliced Eq. 4 leg (0: none)")
     ap.add_argument("--joint", type=int, default=1, help="energy x radius x pulse-shape leg (0: none)")
     ap.add_argument("--nongauss", type=int, default=1, help="Gram-Charlier response leg (0: none)")
+    ap.add_argument("--shelled", type=int, default=1, help="position-dependent response leg (0: none)")
     ap.add_argument("--plain", type=int, default=1, help="plain single-spectrum leg: 1000 points + one fit (0: none)")
     ap.add_argument("--estimators", type=int, default=1, help="three-energy-estimator leg (0: none)")
     ap.add_argument("--c5-iters", type=int, default=1000, help="quasi-Newton iterations of the autograd leg (0: none)")

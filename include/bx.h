@@ -148,6 +148,20 @@ typedef struct {
      * Gaussian.  Otherwise BX_FP64 or BX_FP32, no 2D histograms, and the density must stay
      * non-negative within band_sigmas. */
     double resp_skew, resp_kurt;
+    /* A position-dependent response (the other response variant of the paper's outlook for
+     * Eq. 1; reading: the light yield depends on where an event happens).  The fiducial volume
+     * is cut into n_shell radial shells; events in shell rho see the light yield LY shell_ly[rho]
+     * (same a, b, c, kB), and species k puts the fixed fraction shell_frac[k][rho] of its events
+     * into shell rho (e.g. uniform in volume for internal species, near the vessel for external
+     * ones; the rows normally sum to 1), so its spectrum becomes
+     *   v_k[m] = sum_rho shell_frac[k][rho] sum_i R_rho[m,i] s_k[i],
+     * R_rho Eq. 1's response with mu_i = LY shell_ly[rho] Q_i.  Every shell has its own response
+     * columns.  0 = off; 1 <= n_shell <= 4 requires BX_FP32 or BX_FP64, no 2D histograms, a single
+     * Birks multiplier (quench NULL or all equal), one energy estimator, and
+     * (n_shell - 1) * ceil(n_grid / 128) * 128 + n_grid <= 8192 columns. */
+    int n_shell;
+    const double* shell_ly;     /* [n_shell] light-yield factor of each shell (> 0) */
+    const double* shell_frac;   /* [K][n_shell] fraction of species k's events in each shell (>= 0) */
 } bx_model_desc;
 
 typedef struct {

@@ -43,6 +43,7 @@ class bx_model_desc(C.Structure):
         ("n_eslice", C.c_int), ("eslice_edges", _P),
         ("joint2d", C.c_int),
         ("resp_skew", C.c_double), ("resp_kurt", C.c_double),
+        ("n_shell", C.c_int), ("shell_ly", _P), ("shell_frac", _P),
     ]
 
 
@@ -169,7 +170,8 @@ class Model:
                      psdc=arr(s.counts.get("psd")), psd2=arr(s.psd2d_prob), field=arr(s.field2d),
                      r2c=arr(s.counts.get("j2d" if getattr(s, "joint2d", False) else "r2d")),
                      p2c=arr(s.counts.get("p2d")),
-                     quench=arr(getattr(s, "quench", None)), es=arr(getattr(s, "eslices", None), np.int32))
+                     quench=arr(getattr(s, "quench", None)), es=arr(getattr(s, "eslices", None), np.int32),
+                     shly=arr(getattr(s, "shell_ly", None)), shfr=arr(getattr(s, "shell_frac", None)))
             self._keep.append(k)
             has_rad = s.rad_class is not None and s.n_rad > 0
             d.n_grid, d.e_max, d.n_species = s.n_grid, s.e_max, s.K
@@ -189,6 +191,8 @@ class Model:
             d.eslice_edges = _ptr(k["es"])
             d.joint2d = 1 if getattr(s, "joint2d", False) else 0
             d.resp_skew, d.resp_kurt = getattr(s, "resp_skew", 0.0), getattr(s, "resp_kurt", 0.0)
+            d.n_shell = 0 if k["shly"] is None else len(k["shly"])
+            d.shell_ly, d.shell_frac = _ptr(k["shly"]), _ptr(k["shfr"])
         opts = bx_options(precision, max_batch, band_sigmas, watchdog_s)
         h = C.c_void_p()
         if n_est == 1:

@@ -137,6 +137,20 @@ static int validate_desc(const bx_model_desc& d, int t) {
     if (d.resp_skew != 0.0 || d.resp_kurt != 0.0)
         REQ(d.n_rad2d + d.n_psd2d == 0, "toy %d: the Gram-Charlier response is not supported with 2D histograms", t);
     if (d.joint2d) REQ(d.n_rad2d >= 1 && d.n_psd2d >= 1, "toy %d: the joint grid needs n_rad2d, n_psd2d >= 1", t);
+    REQ(d.n_shell >= 0 && d.n_shell <= MAX_SETS, "toy %d: n_shell %d out of [0, %d]", t, d.n_shell, MAX_SETS);
+    if (d.n_shell > 0) {   // the position-dependent response
+        REQ(d.shell_ly && d.shell_frac, "toy %d: n_shell > 0 needs shell_ly and shell_frac", t);
+        for (int r = 0; r < d.n_shell; ++r)
+            REQ(std::isfinite(d.shell_ly[r]) && d.shell_ly[r] > 0.0, "toy %d: shell_ly[%d] must be > 0", t, r);
+        REQ(finite_nonneg(d.shell_frac, (size_t)d.n_species * d.n_shell), "toy %d: shell_frac negative or not finite", t);
+        REQ(d.n_rad2d + d.n_psd2d == 0, "toy %d: radial response shells with 2D histograms are not supported", t);
+        double xi[MAX_SETS];
+        int set_of[KMAX];
+        REQ(quench_groups(d, xi, set_of) == 1, "toy %d: radial response shells need a single Birks multiplier", t);
+        const int ncs = (d.n_grid + BCOLS - 1) / BCOLS * BCOLS;
+        REQ((d.n_shell - 1) * ncs + d.n_grid <= MAX_CB * BCOLS, "toy %d: %d response shells of %d columns exceed %d",
+            t, d.n_shell, d.n_grid, MAX_CB * BCOLS);
+    }
     if (d.n_rad2d + d.n_psd2d > 0) {
         const int B2 = d.joint2d ? d.n_rad2d * d.n_psd2d : d.n_rad2d + d.n_psd2d;   // 2D slices
         const int n_sl = 1 + (d.tag_frac ? 1 : 0) + B2;
@@ -232,6 +246,8 @@ static int model_create(const bx_model_desc* descs, int n_toys, const bx_options
             return bx_set_error(BX_EINVAL, "toy %d: quenching groups need BX_FP32 or BX_FP64", t);
         if (descs[t].n_eslice > 1 && o.precision == BX_TF32X3)
             return bx_set_error(BX_EINVAL, "toy %d: energy slices need BX_FP32 or BX_FP64", t);
+        if (descs[t].n_shell > 0 && o.precision != BX_FP32 && o.precision != BX_FP64)
+            return bx_set_error(BX_EINVAL, "toy %d: radial response shells need BX_FP32 or BX_FP64", t);
     }
     if (n2d && o.precision != BX_FP32 && o.precision != BX_BF16X3)
         return bx_set_error(BX_EINVAL, "2D histograms need BX_FP32 or BX_BF16X3");
@@ -309,6 +325,15 @@ static int model_create(const bx_model_desc* descs, int n_toys, const bx_options
         T.P = T.K + 7;
         T.n_tiles = (T.M + TM - 1) / TM;
         T.n_set = quench_groups(d, T.xi, T.set_of);
+        T.n_shell = d.n_shell;
+        if (T.n_shell > 0) {   // the sets are the radial shells, all with the one Birks multiplier
+            T.n_set = T.n_shell;
+            for (int c = 0; c < T.n_shell; ++c) {
+                T.xi[c] = T.xi[0];
+                T.lyf[c] = d.shell_ly[c];
+                for (int k = 0; k < T.K; ++k) T.shw[c][k] = d.shell_frac[(size_t)k * d.n_shell + c];
+            }
+        }
         T.Ncs = T.n_set > 1 ? (T.N + BCOLS - 1) / BCOLS * BCOLS : T.N;
         T.Next = (T.n_set - 1) * T.Ncs + T.N;
         T.n_cb = (T.Next + BCOLS - 1) / BCOLS;
@@ -449,8 +474,10 @@ static int model_create(const bx_model_desc* descs, int n_toys, const bx_options
     w.multi_set = 0;
     w.nes = 1;
     w.gc = 0;
+    w.shells = 0;
     for (const Toy& T : m->toys_h) {
-        w.multi_set |= T.n_set > 1 ? 1 : 0;
+        w.shells |= T.n_shell > 0 ? 1 : 0;
+        w.multi_set |= (T.n_set > 1 || T.n_shell > 0) ? 1 : 0;
         w.nes = std::max(w.nes, T.n_es);
         w.gc |= (T.gc1 != 0.0 || T.gc2 != 0.0) ? 1 : 0;
     }
@@ -580,9 +607,9 @@ static int validate_estimators(const bx_model_desc* d, int n_data, int n_est) {
         const bx_model_desc& a = d[(size_t)t * n_est];
         for (int e = 0; e < n_est; ++e) {
             const bx_model_desc& b = d[(size_t)t * n_est + e];
-            if (b.n_rad2d + b.n_psd2d > 0 || b.n_eslice > 1)
-                return bx_set_error(BX_EINVAL, "dataset %d estimator %d: estimators take no 2D histograms or energy slices",
-                                    t, e);
+            if (b.n_rad2d + b.n_psd2d > 0 || b.n_eslice > 1 || (n_est > 1 && b.n_shell > 0))
+                return bx_set_error(BX_EINVAL, "dataset %d estimator %d: estimators take no 2D histograms, energy "
+                                               "slices or radial response shells", t, e);
             if (e == 0) continue;
             if (b.n_rad > 0 || b.n_psd > 0)
                 return bx_set_error(BX_EINVAL, "dataset %d estimator %d: the radial and pulse-shape terms belong to "

@@ -46,24 +46,31 @@ __device__ __forceinline__ void chain_rule(const Col64& cc, const double2& q, co
     g[4] = Gmu * LY * q.y;                  // kB
 }
 
-// A column's place among the quenching groups: column ie is grid point ig of group grp;
-// species k contributes to it only if it belongs to that group.
-template <bool MULTI>
-__device__ __forceinline__ bool in_group(const Toy& T, int k, int grp) { return !MULTI || T.set_of[k] == grp; }
+// A column's place among the sets: column ie is grid point ig of set grp (a quenching group or a
+// radial shell); species k contributes to it with the weight set_weight(T, k, grp).
 
-// rate part: g[5 + k] = s_k[i] (c_vetoed,k rho_vetoed + c_tagged,k rho_tagged) for the species of
-// the column's group (grid point i, group grp)
+// rate part: g[5 + k] = w_k s_k[i] (c_vetoed,k rho_vetoed + c_tagged,k rho_tagged) for the species
+// of the column's set (grid point i, set grp, weight w_k)
 template <bool MULTI>
 __device__ __forceinline__ void rate_part(const Toy& T, int i, int grp, double rs, double rt, double (&g)[GPN]) {
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
-        if (k < T.K && in_group<MULTI>(T, k, grp)) {
+        const double wk = k < T.K ? set_weight<MULTI>(T, k, grp) : 0.0;
+        if (wk != 0.0) {
             const double t = T.tag ? T.tag[k] : 0.0;
-            g[5 + k] = T.shapes[(size_t)k * T.N + i] * ((T.tag ? 1.0 - t : 1.0) * rs + t * rt);
+            g[5 + k] = wk * T.shapes[(size_t)k * T.N + i] * ((T.tag ? 1.0 - t : 1.0) * rs + t * rt);
         } else {
             g[5 + k] = 0.0;
         }
     }
+}
+
+// FP32 shape of species k at grid point ig times its weight wk in the column's set (0 outside
+// its quenching group: no load)
+template <bool MULTI>
+__device__ __forceinline__ float shape_w(const Toy& T, int k, int ig, float wk) {
+    if (!MULTI) return T.shapes32[(size_t)k * T.N + ig];
+    return wk != 0.f ? wk * T.shapes32[(size_t)k * T.N + ig] : 0.f;
 }
 
 __device__ __forceinline__ void block_sum_gp(double (&g)[GPN], double* red, double* out) {
@@ -91,8 +98,9 @@ __device__ __forceinline__ void column_weights(const Work& w, const Toy& T, int 
     for (int q = 0; q < MAX_ES; ++q) SA[q] = 0.0;
     if (!ok) return;
     for (int k = 0; k < T.K; ++k) {
-        if (!in_group<MULTI>(T, k, grp)) continue;
-        const double s = T.shapes[(size_t)k * T.N + i];
+        const double wk = set_weight<MULTI>(T, k, grp);
+        if (wk == 0.0) continue;
+        const double s = wk * T.shapes[(size_t)k * T.N + i];
         Ssub += coef[k] * s;
         Stag += coef[KMAX + k] * s;
         for (int q = 0; q < T.n_es; ++q) SA[q] += coef[(2 + q) * KMAX + k] * s;
@@ -206,9 +214,13 @@ __global__ void __launch_bounds__(BCOLS, 7) k_bwd_f32(Work w) {
     const int NES = MES ? T.n_es : 1;
     __shared__ float s_coef[NR][KMAX];
     __shared__ float s_c[2][KMAX];      // c_{vetoed,k}, c_{tagged,k}
+    __shared__ float s_w[KMAX];         // MULTI: the species' weights in the block's set of columns
     __shared__ double red[GPN * (BCOLS / 32)];
     const double* coef = w.coef + (size_t)item * (2 + (MES ? w.nes : 1)) * KMAX;
     if (tid < (2 + NES) * KMAX) s_coef[tid / KMAX][tid % KMAX] = (float)coef[tid];
+    // (a block's columns with support all lie in one set: Ncs is a multiple of BCOLS with several
+    // sets, and with one set every column below N is set 0)
+    if (MULTI && tid < KMAX) s_w[tid] = tid < T.K ? (float)set_weight<true>(T, tid, (cb * BCOLS) / T.Ncs) : 0.f;
     if (tid < KMAX) {
         const double t = (T.tag && tid < T.K) ? T.tag[tid] : 0.0;
         s_c[0][tid] = T.tag ? (float)(1.0 - t) : 1.f;
@@ -225,7 +237,7 @@ __global__ void __launch_bounds__(BCOLS, 7) k_bwd_f32(Work w) {
 #pragma unroll
                 for (int q4 = 0; q4 < 4; ++q4) {
                     const int k = k0 + q4;
-                    skv[q4] = (k < T.K && in_group<MULTI>(T, k, grp)) ? T.shapes32[(size_t)k * T.N + ig] : 0.f;
+                    skv[q4] = k < T.K ? shape_w<MULTI>(T, k, ig, s_w[k]) : 0.f;
                 }
 #pragma unroll
                 for (int q4 = 0; q4 < 4; ++q4) {
@@ -246,7 +258,7 @@ __global__ void __launch_bounds__(BCOLS, 7) k_bwd_f32(Work w) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int k = k0 + q;
-                    sk[q] = (k < T.K && in_group<MULTI>(T, k, grp)) ? T.shapes32[(size_t)k * T.N + ig] : 0.f;
+                    sk[q] = k < T.K ? shape_w<MULTI>(T, k, ig, s_w[k]) : 0.f;
                 }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -409,7 +421,7 @@ __global__ void __launch_bounds__(BCOLS, 7) k_bwd_f32(Work w) {
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
         if (k < T.K && rates) {
-            const float sk = (ok && in_group<MULTI>(T, k, grp)) ? T.shapes32[(size_t)k * T.N + ig] : 0.f;
+            const float sk = ok ? shape_w<MULTI>(T, k, ig, s_w[k]) : 0.f;
             const float v = warp_sum(sk * fmaf(s_c[0][k], rho_s, s_c[1][k] * rho_t));
             if (lane == 0) red[wid * GPN + 5 + k] = (double)v;
         } else if (lane == 0) {

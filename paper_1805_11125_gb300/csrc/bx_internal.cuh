@@ -57,7 +57,7 @@ struct __align__(16) ColG {
 };
 
 // Device description of one toy (dataset + its fixed model inputs).
-constexpr int MAX_SETS = 4;   // groups of species-specific quenching
+constexpr int MAX_SETS = 4;   // groups of species-specific quenching, or radial shells of the response
 constexpr int MAX_ES = 4;     // energy slices of the Eq. 4 radial and pulse-shape terms
 
 struct Toy {
@@ -73,6 +73,12 @@ struct Toy {
     int es_lo[MAX_ES], es_hi[MAX_ES];
     int set_of[KMAX];
     double xi[MAX_SETS];
+    // position-dependent response (n_shell > 0): the sets are radial shells instead of quenching
+    // groups; shell c has the light yield LY lyf[c] (folded into its columns' Q) and carries every
+    // species k with the weight shw[c][k], the species' fraction of events in the shell
+    int n_shell;
+    double lyf[MAX_SETS];
+    double shw[MAX_SETS][KMAX];
     double dE, w, r_fid, r_iv, att_len;
     double gc1, gc2;          // Gram-Charlier response: skewness / 6 and excess kurtosis / 24 (0, 0: Gaussian)
     const double* shapes;     // [K][N]
@@ -105,6 +111,13 @@ struct Toy {
     int cls_of[4][KMAX], cls_rep[4][KMAX];
     const float* utmax;           // [NSL]: the largest ut[i][b] of each slice over the columns
 };
+
+// Weight of species k in the columns of set grp: a quenching group carries its own species
+// (1, others 0), a radial shell every species with its fraction of events in the shell.
+template <bool MULTI>
+__host__ __device__ __forceinline__ double set_weight(const Toy& T, int k, int grp) {
+    return !MULTI ? 1.0 : T.n_shell ? T.shw[grp][k] : (T.set_of[k] == grp ? 1.0 : 0.0);
+}
 
 // Per-column FP64 results of k_prep.
 struct Col64 {
@@ -156,6 +169,7 @@ struct Work {
     unsigned* err;            // sticky error word
     unsigned long long* units;   // in-band response entries evaluated (counted when count_units)
     int count_units;
+    int shells;               // some toy has radial response shells (k_prep32's SHELL instantiations)
     const unsigned char* skip;   // [cap] or nullptr: items flagged 1 are not evaluated (-lnL = +inf)
     // 2D model buffers (UMMA K-major tiles of TF32 hi | lo halves, NSL slices x KB)
     float* coef2d;            // [cap][4][KMAX][NSL]: r_k dT/dr_k, dT/dr_k, r_k dT/ds_r coefficients, and the

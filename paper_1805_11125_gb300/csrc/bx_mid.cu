@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(MID_THREADS, (sizeof(TV) == sizeof(float) && !
             const int lane = tid & 31, wid = tid >> 5;
             {   // FP64 model (the rate-first FP32 mode runs k_mid32)
                 // column ie = grp Ncs + i of quenching group grp carries the species of that group
-                const int NS = T.n_set > 1 ? T.n_set : 1;
+                // (of radial shell grp: every species, with its fraction in the shell)
                 for (int ie = tid; ie < T.Next; ie += MID_THREADS) {
                     const int grp = ie / T.Ncs, i = ie - grp * T.Ncs;
                     if (i >= T.N) continue;
@@ -230,8 +230,10 @@ __global__ void __launch_bounds__(MID_THREADS, (sizeof(TV) == sizeof(float) && !
                     const double GW = (1.0 - eps) * aw + eps * ag, dG = ag - aw;
 #pragma unroll
                     for (int k = 0; k < KMAX; ++k)
-                        if (k < K && (NS == 1 || T.set_of[k] == grp)) {
-                            const double x = T.shapes[(size_t)k * T.N + i];
+                        if (k < K) {
+                            const double wk = set_weight<true>(T, k, grp);
+                            if (wk == 0.0) continue;
+                            const double x = T.shapes[(size_t)k * T.N + i] * wk;
                             part[k] += x * GW;
                             part[KMAX + k] += x * dG;
                         }
@@ -655,20 +657,31 @@ __global__ void __launch_bounds__(MID_THREADS, 2) k_mid32(Work w, int want_grad,
         }
         __syncthreads();
         for (int k = wid; k < K; k += MID_WARPS) {
-            Sum32 a0, a1;
             const float* sk = T.shapes32 + (size_t)k * T.N;
-            const int off = T.n_set > 1 ? T.set_of[k] * T.Ncs : 0;   // the columns of k's quenching group
-            for (int i = lane; i < T.N; i += 32) {
-                const float x = sk[i];
-                const float2 g2 = colGW[off + i];
-                a0.add_prod(x, g2.x, g2.y);
-                a1.add_prod(x, coldG[off + i], 0.f);
+            // the columns of k's quenching group, or of every radial shell (weighted in FP64 by the
+            // species' fraction of events in the shell)
+            const int c_lo = T.n_shell ? 0 : (T.n_set > 1 ? T.set_of[k] : 0);
+            const int c_hi = T.n_shell ? T.n_set : c_lo + 1;
+            double A0 = 0.0, A1 = 0.0;
+            for (int c = c_lo; c < c_hi; ++c) {
+                const double wk = T.n_shell ? T.shw[c][k] : 1.0;
+                if (wk == 0.0) continue;
+                const int off = c * T.Ncs;
+                Sum32 a0, a1;
+                for (int i = lane; i < T.N; i += 32) {
+                    const float x = sk[i];
+                    const float2 g2 = colGW[off + i];
+                    a0.add_prod(x, g2.x, g2.y);
+                    a1.add_prod(x, coldG[off + i], 0.f);
+                }
+                a0 = a0.warp_reduce();
+                a1 = a1.warp_reduce();
+                A0 += wk * ((double)a0.s + (double)a0.c);
+                A1 += wk * ((double)a1.s + (double)a1.c);
             }
-            a0 = a0.warp_reduce();
-            a1 = a1.warp_reduce();
             if (lane == 0) {   // s_SA[q][k] = sum v G_W,q, s_SA[q][KMAX + k] = sum v dG_W,q/deps
-                s_SA[qs][k] = (double)a0.s + (double)a0.c;
-                s_SA[qs][KMAX + k] = (double)a1.s + (double)a1.c;
+                s_SA[qs][k] = A0;
+                s_SA[qs][KMAX + k] = A1;
             }
         }
         __syncthreads();   // colGW, coldG are reused by the next slice

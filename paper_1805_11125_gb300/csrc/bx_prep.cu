@@ -158,11 +158,13 @@ __global__ void __launch_bounds__(256) k_prep(Work w) {
     int bad = 0;
     unsigned long long inband = 0;
     // species-specific quenching: one pass per group grp of species, with Birks constant
-    // kB xi[grp], into the group's columns [grp Ncs, grp Ncs + N)
+    // kB xi[grp], into the group's columns [grp Ncs, grp Ncs + N); a position-dependent
+    // response: one pass per radial shell, with light yield LY lyf[grp]
     const int NS = MULTI ? T.n_set : 1;
     for (int grp = 0; grp < NS; ++grp) {
     const int off = grp * T.Ncs;
     const double xi = MULTI ? T.xi[grp] : 1.0, kBc = kB * xi;
+    const double lyf = MULTI && T.n_shell ? T.lyf[grp] : 1.0;
     double carry_x = 0.0, carry_y = 0.0;
     for (int c0 = 0; c0 < N; c0 += 256) {
         const int i = c0 + tid, ie = off + i;
@@ -184,7 +186,7 @@ __global__ void __launch_bounds__(256) k_prep(Work w) {
         if (MULTI && in) {   // a group's column without support: only the scan above is needed
             bool nz = false;
             for (int k = 0; k < K; ++k)
-                if (T.set_of[k] == grp) nz |= T.shapes[(size_t)k * N + i] != 0.0;
+                if (set_weight<MULTI>(T, k, grp) != 0.0) nz |= T.shapes[(size_t)k * N + i] != 0.0;
             if (!nz) {
                 live = false;
                 col[ie] = Col64{0.0, 1.0, 0.0, 0.0};
@@ -195,7 +197,12 @@ __global__ void __launch_bounds__(256) k_prep(Work w) {
             }
         }
         if (live) {
-            const double Q = carry_x + ex + 0.5 * x, dQ = carry_y + ey + 0.5 * y;
+            // (a radial shell's light-yield factor folded into Q: mu = LY Q, dmu/dLY = Q)
+            double Q = carry_x + ex + 0.5 * x, dQ = carry_y + ey + 0.5 * y;
+            if (MULTI) {
+                Q *= lyf;
+                dQ *= lyf;
+            }
             cq[ie] = make_double2(Q, dQ);
             const double mu = LY * Q;
             const double var = fma(fma(b, mu, a), mu, c);
@@ -221,9 +228,10 @@ __global__ void __launch_bounds__(256) k_prep(Work w) {
             double ssub = 0.0, stag = 0.0;
             bool nz = false;   // a species of this group has support in the column
             for (int k = 0; k < K; ++k) {
-                if (MULTI && T.set_of[k] != grp) continue;
+                const double wk = set_weight<MULTI>(T, k, grp);
+                if (wk == 0.0) continue;
                 nz |= T.shapes[(size_t)k * N + i] != 0.0;
-                const double sk = T.shapes[(size_t)k * N + i] * th[k];
+                const double sk = T.shapes[(size_t)k * N + i] * th[k] * wk;
                 const double t = T.tag ? T.tag[k] : 0.0;
                 ssub += (T.tag ? 1.0 - t : 1.0) * sk;
                 stag += t * sk;
@@ -368,7 +376,9 @@ __device__ void block_scan_df(df& a, df& b, df& ta, df& tb, float* sh) {
 // Z_F32 = 3 sigma (1/Phi, phi/Phi; FP32 tails beyond) and for the FP64 copies of mu, sigma, Q,
 // dQ/dkB that the adjoint's chain rule reads (formed on the integer pipe, f2d).  The window
 // masses come from FP32 tails and go out as FP32 pairs.
-template <bool MULTI, bool GC = false>
+// SHELL: the sets are the radial shells of a position-dependent response (every species in every
+// set with its fraction, a light-yield factor per set) instead of quenching groups.
+template <bool MULTI, bool GC = false, bool SHELL = false>
 __global__ void __launch_bounds__(256, 3) k_prep32(Work w) {
     const int item = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
     if (w.skip && w.skip[item]) {
@@ -381,7 +391,10 @@ __global__ void __launch_bounds__(256, 3) k_prep32(Work w) {
     __shared__ float sh[72];
     __shared__ int s_bad;
     __shared__ int s_tlo[MAX_SETS][MAX_TILES], s_thi[MAX_SETS][MAX_TILES], s_rlo[MAX_CB], s_rhi[MAX_CB];
-    __shared__ float s_rate[4][KMAX];
+    // rates times the tag fractions (vetoed, tagged) as FP32 pairs, per set of columns times the
+    // species' weight in the set (0 outside its quenching group, its fraction in a radial shell)
+    constexpr int NSR = MULTI ? MAX_SETS : 1;
+    __shared__ float s_rate[NSR][4][KMAX];
     __shared__ df s_par[10 + MAX_ES];   // LY, a, b, c, kB, dE, w S_EX2, 1/w, A's constant factor, slice edges
     if (tid == 0) s_bad = 0;
     for (int j = tid; j < MAX_SETS * MAX_TILES; j += blockDim.x) {
@@ -389,18 +402,19 @@ __global__ void __launch_bounds__(256, 3) k_prep32(Work w) {
         s_thi[j / MAX_TILES][j % MAX_TILES] = INT_MIN;
     }
     for (int j = tid; j < MAX_CB; j += blockDim.x) { s_rlo[j] = INT_MAX; s_rhi[j] = INT_MIN; }
-    if (tid < KMAX) {
+    if (tid < NSR * KMAX) {
+        const int k = tid % KMAX, c = tid / KMAX;
         double rs = 0.0, rt = 0.0;
-        if (tid < K) {
-            const double t = T.tag ? T.tag[tid] : 0.0;
-            rs = th[tid] * (T.tag ? 1.0 - t : 1.0);
-            rt = th[tid] * t;
+        if (k < K && (!MULTI || c < T.n_set)) {
+            const double t = T.tag ? T.tag[k] : 0.0, wk = (SHELL ? T.shw[c][k] : set_weight<MULTI>(T, k, c));
+            rs = th[k] * (T.tag ? 1.0 - t : 1.0) * wk;
+            rt = th[k] * t * wk;
         }
         const float rsh = (float)rs, rth = (float)rt;
-        s_rate[0][tid] = rsh;
-        s_rate[1][tid] = (float)(rs - (double)rsh);
-        s_rate[2][tid] = rth;
-        s_rate[3][tid] = (float)(rt - (double)rth);
+        s_rate[c][0][k] = rsh;
+        s_rate[c][1][k] = (float)(rs - (double)rsh);
+        s_rate[c][2][k] = rth;
+        s_rate[c][3][k] = (float)(rt - (double)rth);
     }
     if (tid < 10 + T.n_es) {   // edges of the energy slices (npe): e_q = es_lo[q], e_S = es_hi[S - 1]
         const int q = tid - 9;
@@ -439,6 +453,8 @@ __global__ void __launch_bounds__(256, 3) k_prep32(Work w) {
     const int NS = MULTI ? T.n_set : 1;
     for (int grp = 0; grp < NS; ++grp) {
     const int off = grp * T.Ncs;
+    constexpr bool shell = MULTI && SHELL;   // a radial shell: light yield LY lyf[grp]
+    const df lyf = shell ? df_from(T.lyf[grp]) : df{1.f, 0.f};
     const df xid = MULTI ? df_from(T.xi[grp]) : df{1.f, 0.f};
     const df kBc = MULTI ? df_mul(kB, xid) : kB;
     df carry_x{0.f, 0.f}, carry_y{0.f, 0.f};
@@ -465,7 +481,10 @@ __global__ void __launch_bounds__(256, 3) k_prep32(Work w) {
         int r0 = 0, r1 = 0;
         bool valid = false;
         bool live = in;
-        if (MULTI && in) {   // a group's column without support: only the scan above is needed
+        // a quenching group's column without support: only the scan above is needed (radial
+        // shells carry every species: their columns without support are dropped after the
+        // spectra below, like any other)
+        if (MULTI && !shell && in) {
             bool nz = false;
             for (int k = 0; k < K; ++k)
                 if (T.set_of[k] == grp) nz |= T.shapes[(size_t)k * N + i] != 0.0;
@@ -482,8 +501,12 @@ __global__ void __launch_bounds__(256, 3) k_prep32(Work w) {
             }
         }
         if (live) {
-            const df Q = df_add(df_add(carry_x, ex), df{0.5f * x.h, 0.5f * x.l});
-            const df dQ = df_add(df_add(carry_y, ey), df{0.5f * y.h, 0.5f * y.l});
+            df Q = df_add(df_add(carry_x, ex), df{0.5f * x.h, 0.5f * x.l});
+            df dQ = df_add(df_add(carry_y, ey), df{0.5f * y.h, 0.5f * y.l});
+            if (shell) {   // the shell's light-yield factor folded into Q: mu = LY Q, dmu/dLY = Q
+                Q = df_mul(Q, lyf);
+                dQ = df_mul(dQ, lyf);
+            }
             cq[ie] = make_double2(df_to_double(Q), df_to_double(dQ));
             const df mu = df_mul(LY, Q);
             const df var = df_add(df_mul(df_add(df_mul(pb, mu), pa), mu), pc);
@@ -557,29 +580,31 @@ __global__ void __launch_bounds__(256, 3) k_prep32(Work w) {
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const int k = k0 + q;
-                        const bool use = k < K && (!MULTI || T.set_of[k] == grp);
+                        const bool use = k < K && (!MULTI || (SHELL ? T.shw[grp][k] != 0.0 : T.set_of[k] == grp));
                         hv[q] = use ? T.shapes32[(size_t)k * N + i] : 0.f;
                         lv[q] = use ? T.shapes32l[(size_t)k * N + i] : 0.f;
                     }
+                    const float(&rg)[4][KMAX] = s_rate[MULTI ? grp : 0];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         if (hv[q] == 0.f) continue;
                         const int k = k0 + q;
                         const df sk{hv[q], lv[q]};
                         nz = true;
-                        ss = df_add(ss, df_mul(df{s_rate[0][k], s_rate[1][k]}, sk));
-                        st = df_add(st, df_mul(df{s_rate[2][k], s_rate[3][k]}, sk));
+                        ss = df_add(ss, df_mul(df{rg[0][k], rg[1][k]}, sk));
+                        st = df_add(st, df_mul(df{rg[2][k], rg[3][k]}, sk));
                     }
                 }
             } else {            // a descriptor with FP64 shapes only
+                const float(&rg)[4][KMAX] = s_rate[MULTI ? grp : 0];
                 for (int k = 0; k < K; ++k) {
-                    if (MULTI && T.set_of[k] != grp) continue;
+                    if (MULTI && (SHELL ? T.shw[grp][k] == 0.0 : T.set_of[k] != grp)) continue;
                     const double x = T.shapes[(size_t)k * N + i];
                     if (x == 0.0) continue;
                     const df sk = df_from(x);
                     nz = true;
-                    ss = df_add(ss, df_mul(df{s_rate[0][k], s_rate[1][k]}, sk));
-                    st = df_add(st, df_mul(df{s_rate[2][k], s_rate[3][k]}, sk));
+                    ss = df_add(ss, df_mul(df{rg[0][k], rg[1][k]}, sk));
+                    st = df_add(st, df_mul(df{rg[2][k], rg[3][k]}, sk));
                 }
             }
             const df As = df_mul(Ad, ss), At = df_mul(Ad, st);
@@ -656,7 +681,10 @@ cudaError_t launch_prep(const Work& w, int n, cudaStream_t s) {
         if (w.multi_set) k_prep<true><<<n, 256, 0, s>>>(w);
         else k_prep<false><<<n, 256, 0, s>>>(w);
     } else {
-        if (w.gc) {
+        if (w.shells) {   // radial shells of the response (their own instantiations)
+            if (w.gc) k_prep32<true, true, true><<<n, 256, 0, s>>>(w);
+            else k_prep32<true, false, true><<<n, 256, 0, s>>>(w);
+        } else if (w.gc) {
             if (w.multi_set) k_prep32<true, true><<<n, 256, 0, s>>>(w);
             else k_prep32<false, true><<<n, 256, 0, s>>>(w);
         } else if (w.multi_set) k_prep32<true><<<n, 256, 0, s>>>(w);
