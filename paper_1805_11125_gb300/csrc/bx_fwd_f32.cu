@@ -89,16 +89,24 @@ __global__ void __launch_bounds__(32 * WPC) k_fwd_f32(Work w) {
     // one column's entries of the lane's rows: both row groups (the common case: two
     // independent chains for the scheduler) or one of them
     const float gc3 = GC ? (float)T.gc1 : 0.f, gc4 = GC ? (float)T.gc2 : 0.f;
-    auto shape = [&](auto wide_tag, float mf, const float4& cf, const ColG& cg) {
+    auto shape_t = [&](auto wide_tag, float th, float tl, const ColG& cg) {
         constexpr bool WIDE = decltype(wide_tag)::value;
-        if constexpr (GC) return resp_shape32_gc<WIDE>(mf, cf, cg, gc3, gc4);
-        else return resp_shape32<WIDE>(mf, cf, cg);
+        if constexpr (GC) return resp_shape32_gc_t<WIDE>(th, tl, cg, gc3, gc4);
+        else return resp_shape32_t<WIDE>(th, tl, cg);
+    };
+    auto shape = [&](auto wide_tag, float mf, const float4& cf, const ColG& cg) {
+        float th, tl;
+        centre_df(mf, cf, cg.c_lo, th, tl);
+        return shape_t(wide_tag, th, tl, cg);
     };
     auto column = [&](auto wide_tag, bool inA, bool inB, const float4& cf, const ColG& cg, const float4 S,
                       float& Ra, float& Rb) {
-        if (inA && inB) {
-            Ra = shape(wide_tag, mfa, cf, cg);
-            Rb = shape(wide_tag, mfb, cf, cg);
+        if (inA && inB) {   // row B's centre from row A's: one double-float add
+            float tha, tla, thb, tlb;
+            centre_df(mfa, cf, cg.c_lo, tha, tla);
+            centre_step32(tha, tla, cf, thb, tlb);
+            Ra = shape_t(wide_tag, tha, tla, cg);
+            Rb = shape_t(wide_tag, thb, tlb, cg);
             kahan_fma(sa, csa, Ra, S.x, S.z);
             kahan_fma(sb, csb, Rb, S.x, S.z);
             if (TAG) {

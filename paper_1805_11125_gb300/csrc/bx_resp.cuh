@@ -104,9 +104,7 @@ constexpr float INV_2LN2 = 0.72134752044448170f;   // kk = kap / (2 ln 2)
 // WIDE: the caller has established |z| <= 1 for this row (the series branch), so the test
 // is skipped; the arithmetic is the same either way.
 template <bool WIDE = false>
-__device__ __forceinline__ float resp_shape32(float mf, const float4& cf, const ColG& cg) {
-    float th, tl;
-    centre_df(mf, cf, cg.c_lo, th, tl);
+__device__ __forceinline__ float resp_shape32_t(float th, float tl, const ColG& cg) {
     const float p0 = centre_node(th, tl);
     const float z = cg.kap * th;
     float Sp;
@@ -117,6 +115,21 @@ __device__ __forceinline__ float resp_shape32(float mf, const float4& cf, const 
         outer_direct(th, cg.kap * INV_2LN2, Sp, Sm);
     }
     return fmaf(GL_W_OUT, Sp, GL_W_MID * p0);
+}
+template <bool WIDE = false>
+__device__ __forceinline__ float resp_shape32(float mf, const float4& cf, const ColG& cg) {
+    float th, tl;
+    centre_df(mf, cf, cg.c_lo, th, tl);
+    return resp_shape32_t<WIDE>(th, tl, cg);
+}
+// The centre of row m + 32 from that of row m: t + 32 hs as a double-float (32 hs is exact).
+__device__ __forceinline__ void centre_step32(float th, float tl, const float4& cf, float& uh, float& ul) {
+    const float d = 32.0f * cf.z;
+    const float s = __fadd_rn(th, d);
+    const float bb = __fsub_rn(s, th);
+    const float err = __fadd_rn(__fsub_rn(th, __fsub_rn(s, bb)), __fsub_rn(d, bb));
+    uh = s;
+    ul = __fadd_rn(err, fmaf(32.0f, cf.w, tl));
 }
 // Response entry R[m, i] of output bin `mf` and one column.
 // Gram-Charlier response (density phi(z) g(z), g = 1 + c3 He3(z) + c4 He4(z), c3 = skewness / 6,
@@ -134,9 +147,7 @@ __device__ __forceinline__ float gc_slope(float z, float c3, float c4) {   // dg
 constexpr float INV_S_EX2 = 1.17741002251547469101f;   // 1 / S_EX2 = sqrt(2 ln 2)
 
 template <bool WIDE = false>
-__device__ __forceinline__ float resp_shape32_gc(float mf, const float4& cf, const ColG& cg, float c3, float c4) {
-    float th, tl;
-    centre_df(mf, cf, cg.c_lo, th, tl);
+__device__ __forceinline__ float resp_shape32_gc_t(float th, float tl, const ColG& cg, float c3, float c4) {
     const float p0 = centre_node(th, tl);
     const float z = cg.kap * th, kk = cg.kap * INV_2LN2;
     float Sp, Sm;
@@ -151,6 +162,12 @@ __device__ __forceinline__ float resp_shape32_gc(float mf, const float4& cf, con
     const float gm = gc_factor(z0 - d, c3, c4), gp = gc_factor(z0 + d, c3, c4);
     const float outer = fmaf(Sp, gm + gp, Sm * (gm - gp)) * 0.5f;
     return fmaf(GL_W_OUT, outer, GL_W_MID * p0 * gc_factor(z0, c3, c4));
+}
+template <bool WIDE = false>
+__device__ __forceinline__ float resp_shape32_gc(float mf, const float4& cf, const ColG& cg, float c3, float c4) {
+    float th, tl;
+    centre_df(mf, cf, cg.c_lo, th, tl);
+    return resp_shape32_gc_t<WIDE>(th, tl, cg, c3, c4);
 }
 
 // The adjoint node sums of the Gram-Charlier response for one row: with the standard score z of
