@@ -240,7 +240,8 @@ int bx_nll_batch(bx_model* model, int n, const int* toy_idx, const double* theta
  * displaced points in one batched evaluation) and inverted with the smallest Levenberg
  * damping that makes it positive definite; the line search evaluates 8 step lengths
  * (1 .. 1/128, within a trust region of the response, pile-up and radial parameters) in one
- * batched evaluation and takes the largest with sufficient decrease.  Each fit in flight
+ * batched evaluation and takes the one with the lowest -lnL among those with sufficient
+ * decrease.  Each fit in flight
  * occupies 8 + 2P evaluation slots (max_batch >= 8 + 2P).  Converged when EDM = g^T V g / 2 <
  * tol_edm with a fresh, at most lightly damped Hessian.  With BX_FP32 the gradient noise sets an
  * EDM floor and the tolerance used is max(tol_edm, 1e-5) (distance to the optimum < ~0.005
@@ -258,7 +259,9 @@ int bx_nll_batch(bx_model* model, int n, const int* toy_idx, const double* theta
  * sufficient decrease is taken; each non-rate component of a step is clipped to
  * max(|theta_i|, 3 sigma_i).  A BX_FP32 fit whose fresh Hessian is indefinite while no trial
  * lowers -lnL retakes the Hessian with 4x larger steps, and past 64 conditional deviations
- * stops with BX_OK at its noise floor. */
+ * stops with BX_OK at its noise floor.  A damping runaway (no damping up to 1e8 helps) retakes
+ * the Hessian with 4x larger steps, at most 3 times, before the fit ends with BX_ENOTCONV; a fit
+ * still running after every 25 accepted steps doubles its finite-difference step. */
 typedef struct {
     double tol_edm;             /* EDM tolerance (0 -> 1e-8) */
     int max_iter;               /* evaluation budget per fit (0 -> 5000) */
