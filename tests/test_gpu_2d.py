@@ -131,7 +131,7 @@ def test_2d_adjoint_through_autograd_matches_oracle_and_central_differences():
     g = t.grad[0].cpu().numpy()
     fd0, gd = m.nll_grad(th)
     np.testing.assert_array_equal(g, gd)
-    assert float(f0[0]) == fd0
+    assert float(f0.detach()[0]) == fd0
     fo, go = O.nll(s, th, grad=True)
     ok = np.abs(g[: s.P] - go) * np.abs(th) <= 1e-3 * (1 + np.abs(go * th))
     assert np.all(ok), np.nonzero(~ok)[0]
