@@ -47,9 +47,10 @@
  * Gradients come from forward-mode dual numbers carried through the same definition
  * (independent of any hand-written adjoint).  The fit is a damped Newton iteration on
  * the dual-number gradient with a central-difference Hessian, box bounds by projection.
- * The fit is pinned by two invariants only (an Asimov fit returns theta_true; at the
- * optimum the expected and observed totals agree); beyond them its parity is unpinned:
- * the paper prints no fitted values.
+ * The fit is pinned by two invariants (an Asimov fit returns theta_true; at the optimum
+ * the expected and observed totals agree) and one closed form (a single free rate of a
+ * one-species model ends at sum(n) / sum(u) on any data); beyond them its parity is
+ * unpinned: the paper prints no fitted values.
  */
 #include <math.h>
 #include <stdlib.h>

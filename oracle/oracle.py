@@ -222,8 +222,9 @@ def poisson_nll(counts, mu) -> float:
 def fit(spec, theta0, free=None, lo=None, hi=None, tol_edm=1e-12, max_iter=60):
     """Damped Newton fit; returns dict(theta, nll, edm, iters, status, cov).
 
-    Parity unpinned beyond two invariants (an Asimov fit returns theta_true; the expected and
-    observed totals agree at the optimum): the paper prints no fitted values."""
+    Pinned by two invariants (an Asimov fit returns theta_true; the expected and observed
+    totals agree at the optimum) and one closed form (a single free rate of a one-species model
+    ends at sum(n) / sum(u)); parity unpinned beyond them: the paper prints no fitted values."""
     m = _model(spec)
     P = spec.P
     free = spec.default_free() if free is None else free

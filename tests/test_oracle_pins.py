@@ -331,6 +331,32 @@ def test_fit_normalisation_invariant_at_optimum():
     assert mu.sum() == pytest.approx(s.counts_vector().sum(), rel=1e-9)
 
 
+def test_fit_single_free_rate_has_the_closed_form_optimum():
+    """One species (the other rates fixed at 0) with only its rate free: mu = r u in every bin
+    (Eq. 2-4 are linear in the spectra), so d(-lnL)/dr = sum u - sum n / r and the maximum
+    likelihood rate is sum(n) / sum(u), whatever the data.  The data here come from another
+    response (LY 3 % higher) and another rate, with Poisson noise."""
+    s = I.config("small_mv")
+    j = 3
+    th = s.theta_true.copy()
+    th[: s.K] = 0.0
+    th[j] = 1.0
+    u = O.expected(s, th)
+    gen = th.copy()
+    gen[j] = 1.2e5
+    gen[tail(s, "LY")] *= 1.03
+    n = I.poisson_counts(O.expected(s, gen), 17)
+    s = s.with_counts(n)
+    free = np.zeros(s.P, dtype=np.uint8)
+    free[j] = 1
+    th0 = th.copy()
+    th0[j] = 0.7e5
+    r = O.fit(s, th0, free=free, tol_edm=1e-16)
+    assert r["status"] == 0
+    assert r["theta"][j] == pytest.approx(n.sum() / u.sum(), rel=1e-9)
+    np.testing.assert_array_equal(np.delete(r["theta"], j), np.delete(th0, j))
+
+
 # ------------------------------------------------------------- 2D histograms (discrimination)
 
 def _split_2d(s, mu):
