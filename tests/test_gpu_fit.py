@@ -197,3 +197,33 @@ def test_toy_study_pulls(prec):
         assert np.all(np.isfinite(p))
         assert abs(float(np.mean(p))) <= 4.0 / np.sqrt(len(p)), (k, float(np.mean(p)))
         assert 0.8 <= float(np.std(p)) <= 1.2, (k, float(np.std(p)))
+
+
+@pytest.mark.parametrize("prec", [bx.BX_FP64, bx.BX_FP32])
+def test_single_free_rate_fit_has_the_closed_form_optimum(prec):
+    """One species (the other rates 0) with only its rate free: mu = r u, so the optimum is
+    sum(n) / sum(u) (u from the oracle at r = 1) on data from another response and rate.  The
+    FP64 fit reaches it within 1e-9; an FP32 fit stops at EDM < 1e-5 (its floor), i.e. within
+    sqrt(2 x 1e-5 / sum(n)) relative (-lnL = sum(n) (dr / r)^2 / 2 near the optimum)."""
+    s = I.config("small_mv")
+    j = 3
+    th = s.theta_true.copy()
+    th[: s.K] = 0.0
+    th[j] = 1.0
+    u = O.expected(s, th)
+    gen = th.copy()
+    gen[j] = 1.2e5
+    gen[s.K + I.PARAM_TAIL.index("LY")] *= 1.03
+    n = I.poisson_counts(O.expected(s, gen), 17)
+    s = s.with_counts(n)
+    free = np.zeros(s.P, dtype=np.uint8)
+    free[j] = 1
+    th0 = th.copy()
+    th0[j] = 0.7e5
+    m = bx.Model(s, precision=prec, max_batch=8 + 2 * s.P)
+    out, info, st = m.fit(th0, free=free, tol_edm=1e-12)
+    m.close()
+    assert info[0]["status"] == bx.BX_OK, info[0]
+    rel = 1e-9 if prec == bx.BX_FP64 else np.sqrt(2 * 1e-5 / n.sum())
+    assert out[0, j] == pytest.approx(n.sum() / u.sum(), rel=rel)
+    np.testing.assert_array_equal(np.delete(out[0, : s.P], j), np.delete(th0, j))
