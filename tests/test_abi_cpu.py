@@ -196,3 +196,36 @@ def test_joint_grid_rejections_on_host():
     with pytest.raises(bx.BxError) as e:
         make(wide)
     assert e.value.status == bx.BX_EINVAL and "exceed" in str(e.value)
+
+
+def test_radial_shell_rejections_on_host():
+    """The position-dependent response: at most four shells, light-yield factors > 0, fractions
+    finite and >= 0, a single Birks multiplier, no 2D histograms, BX_FP32 / BX_FP64 only, one
+    energy estimator (all checked before any device is touched)."""
+    import dataclasses
+    s = I.config("small_shelled")
+    s = s.with_counts(np.ones(s.n_bins_total))
+    bad = [
+        (dataclasses.replace(s, shell_ly=np.ones(5), shell_frac=np.full((s.K, 5), 0.2)), bx.BX_FP32, "n_shell"),
+        (dataclasses.replace(s, shell_ly=np.array([1.0, 0.0, 1.0, 1.0])), bx.BX_FP32, "shell_ly"),
+        (dataclasses.replace(s, shell_frac=np.where(np.arange(4)[None, :] == 2, -0.1, 0.25) * np.ones((s.K, 1))),
+         bx.BX_FP64, "shell_frac"),
+        (dataclasses.replace(s, quench=np.where(np.arange(s.K) == 0, 2.0, 1.0)), bx.BX_FP32, "Birks"),
+        (s, bx.BX_TF32X3, "shells"),
+    ]
+    for spec, prec, msg in bad:
+        with pytest.raises(bx.BxError) as e:
+            bx.Model(spec, precision=prec)
+        assert e.value.status == bx.BX_EINVAL and msg in str(e.value), str(e.value)
+    d = I.config("small_2d")
+    d = dataclasses.replace(d, shell_ly=np.ones(2), shell_frac=np.full((d.K, 2), 0.5))
+    d = d.with_counts(np.ones(d.n_bins_total))
+    with pytest.raises(bx.BxError) as e:
+        bx.Model(d, precision=bx.BX_FP32)
+    assert e.value.status == bx.BX_EINVAL and "2D" in str(e.value)
+    est = [dataclasses.replace(e_, shell_ly=np.ones(2), shell_frac=np.full((e_.K, 2), 0.5))
+           for e_ in I.estimators("small_mv", names=("npe", "charge"))]
+    est = [e_.with_counts(np.ones(e_.n_bins_total)) for e_ in est]
+    with pytest.raises(bx.BxError) as e:
+        bx.Model(est, precision=bx.BX_FP32, n_est=len(est))
+    assert e.value.status == bx.BX_EINVAL and "shells" in str(e.value)
