@@ -282,9 +282,9 @@ __global__ void __launch_bounds__(BCOLS, 7) k_bwd_f32(Work w) {
     const int wr0 = max(r0, min(r1, __reduce_min_sync(0xffffffffu, live ? band.x : INT_MAX)));
     const int wr1 = min(r1, __reduce_max_sync(0xffffffffu, live ? band.y : 0));
     const int lane = tid & 31, wq = tid >> 5;
-    // the plain model packs (wt_sub, wt_tag, G_W, -) per row (one 16-byte load); the others keep
-    // one row array per weight
-    constexpr bool PACK = !MES && !MULTI;
+    // one energy slice: (wt_sub, wt_tag, G_W, -) packed per row (one 16-byte load; the row
+    // weights do not depend on the column's set); several slices keep one row array per weight
+    constexpr bool PACK = !MES;
     __shared__ float sW[BCOLS / 32][PACK ? 1 : NR][PACK ? 1 : 64];
     __shared__ float4 sW4[BCOLS / 32][PACK ? 64 : 1];
     double S0 = 0.0, S1 = 0.0, S2 = 0.0, Rs = 0.0, Rt = 0.0;
