@@ -1,5 +1,6 @@
 """The position-dependent response (radial shells, each with its own light-yield factor, every
-species spread over them by fixed fractions) on the GPU against the oracle, through the C ABI.
+species spread over them by fixed fractions) on the GPU against the oracle, through the C ABI
+(also together with the Gram-Charlier response).
 BX_FP64: expected counts per bin (relative 1e-10), -lnL (|Delta(-2 lnL)| <= 1e-7) and gradient
 (|Delta g_j| |theta_j| <= 1e-9 (1 + |g_j theta_j|)) of the reduced and the full-size model, one
 shell and four, batch = single calls, the fit against the oracle's fit.  BX_FP32 with the mixed
@@ -178,3 +179,23 @@ def test_shells_rejections():
     with pytest.raises(bx.BxError) as e:
         bx.Model(d, precision=bx.BX_FP32)
     assert e.value.status == bx.BX_EINVAL
+
+
+@pytest.mark.parametrize("prec", [bx.BX_FP64, bx.BX_FP32])
+def test_shells_with_the_gram_charlier_response(prec):
+    """Radial shells together with the non-Gaussian response (each shell's columns with the
+    Gram-Charlier bin masses) against the oracle, with each precision's bounds."""
+    s = dataclasses.replace(I.config("small_shelled"), resp_skew=0.1, resp_kurt=0.1)
+    s = s.with_counts(I.poisson_counts(O.expected(s, s.theta_true), 5))
+    m = bx.Model(s, precision=prec)
+    rel, gtol, ftol = (1e-10, 1e-9, 1e-7) if prec == bx.BX_FP64 else (1e-5, 1e-3, 1e-3)
+    for th in [s.theta_true] + list(points(s, 2, seed=139)):
+        mg, mo = m.expected(th), O.expected(s, th)
+        ok, wr, wa = per_bin_ok(mg, mo, rel=rel, abs_frac=1e-8)
+        assert ok, (wr, wa)
+        f, g = m.nll_grad(th)
+        fo, go = O.nll(s, th, grad=True)
+        assert 2 * abs(f - fo) <= ftol, (f, fo)
+        ok, worst = grad_ok(g[: s.P], go, th, tol=gtol)
+        assert ok, worst
+    m.close()
