@@ -1,6 +1,6 @@
 """The position-dependent response (radial shells, each with its own light-yield factor, every
 species spread over them by fixed fractions) on the GPU against the oracle, through the C ABI
-(also together with the Gram-Charlier response).
+(also together with the Gram-Charlier response and with energy slices of the Eq. 4 terms).
 BX_FP64: expected counts per bin (relative 1e-10), -lnL (|Delta(-2 lnL)| <= 1e-7) and gradient
 (|Delta g_j| |theta_j| <= 1e-9 (1 + |g_j theta_j|)) of the reduced and the full-size model, one
 shell and four, batch = single calls, the fit against the oracle's fit.  BX_FP32 with the mixed
@@ -190,6 +190,27 @@ def test_shells_with_the_gram_charlier_response(prec):
     m = bx.Model(s, precision=prec)
     rel, gtol, ftol = (1e-10, 1e-9, 1e-7) if prec == bx.BX_FP64 else (1e-5, 1e-3, 1e-3)
     for th in [s.theta_true] + list(points(s, 2, seed=139)):
+        mg, mo = m.expected(th), O.expected(s, th)
+        ok, wr, wa = per_bin_ok(mg, mo, rel=rel, abs_frac=1e-8)
+        assert ok, (wr, wa)
+        f, g = m.nll_grad(th)
+        fo, go = O.nll(s, th, grad=True)
+        assert 2 * abs(f - fo) <= ftol, (f, fo)
+        ok, worst = grad_ok(g[: s.P], go, th, tol=gtol)
+        assert ok, worst
+    m.close()
+
+
+@pytest.mark.parametrize("prec", [bx.BX_FP64, bx.BX_FP32])
+def test_shells_with_energy_slices(prec):
+    """Radial shells together with Eq. 4's terms in three energy slices (each slice's window
+    masses per shell column, the species sums weighted per shell) against the oracle."""
+    sh = I.config("small_shelled")
+    s = dataclasses.replace(I.config("small_sliced"), shell_ly=sh.shell_ly, shell_frac=sh.shell_frac)
+    s = s.with_counts(I.poisson_counts(O.expected(s, s.theta_true), 6))
+    m = bx.Model(s, precision=prec)
+    rel, gtol, ftol = (1e-10, 1e-9, 1e-7) if prec == bx.BX_FP64 else (1e-5, 1e-3, 1e-3)
+    for th in [s.theta_true] + list(points(s, 2, seed=141)):
         mg, mo = m.expected(th), O.expected(s, th)
         ok, wr, wa = per_bin_ok(mg, mo, rel=rel, abs_frac=1e-8)
         assert ok, (wr, wa)
