@@ -878,6 +878,19 @@ def test_shells_of_unit_light_yield_are_the_base_model():
     np.testing.assert_allclose(gf, gb, rtol=1e-9, atol=1e-9 * np.abs(gb).max())
 
 
+@pytest.mark.parametrize("base_name", ["small_nongauss", "small_sliced"])
+def test_unit_shells_leave_the_other_variants_unchanged(base_name):
+    """Unit-factor shells on the Gram-Charlier model and on the energy-sliced model reproduce
+    those models (bins and -lnL): the shells compose with the other variants."""
+    b = I.config(base_name)
+    b = b.with_counts(I.poisson_counts(O.expected(b, b.theta_true), 22))
+    flat = dataclasses.replace(b, shell_ly=np.ones(3), shell_frac=np.tile([0.2, 0.5, 0.3], (b.K, 1)))
+    th = I.parameter_points(b.theta_true, 1, rel=0.02, seed=65, free=b.default_free())[0]
+    mb = O.expected(b, th)
+    np.testing.assert_allclose(O.expected(flat, th), mb, rtol=1e-13, atol=1e-15 * mb.max())
+    assert O.nll(flat, th) == pytest.approx(O.nll(b, th), rel=1e-13)
+
+
 def test_one_shell_is_a_rescaled_light_yield():
     """One shell of light-yield factor f holding every event is the base model with LY replaced by
     f LY: the same bins and -lnL, the same gradient in every parameter but LY, and f times the
